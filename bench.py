@@ -1,0 +1,359 @@
+"""Benchmark of the FMM poroelastic DDM hot path on GB300.
+
+Workload: randomly distributed pressurised fractures, 200 non-intersecting
+cracks (seeded rejection sampling) in a 200 m x 200 m box, lengths U[2, 10] m,
+orientations U[0, pi), 100 constant elements each: N = 20,000 elements,
+60,000 unknowns.  G = 6 GPa, nu = 0.2, nu_u = 0.33, B = 0.8, k = 1e-18 m^2,
+mu = 1e-3 Pa s; fracture pressure 10 MPa, sigma_H = 30 MPa, sigma_h = 25 MPa;
+one time element of 10 s.  FMM with n = 8 Chebyshev nodes per dimension,
+leaf size 32, FP32 pair/M2L arithmetic, FP64 Krylov.
+
+A timed step is one FMM influence product y = [K(dt)] x over all N elements
+(inputs resident in HBM; L2 flushed between steps); value = N / step time in
+Melem/s.  The same run also reports the full time-step solve (tree build,
+right-hand side, GMRES to 1e-5, SIFs) as solves/s with p50/p99 latency, the
+dense on-the-fly product (conventional PDDM on the GPU), the error of the
+FMM product against the FP64 CPU oracle on sampled rows, the roofline of
+the dominant kernel and the oracle timed on the host cores.
+
+--impl reference times the FP64 CPU oracle on bounded samples of the same
+workload (the method has no reference implementation to install).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FMM matvec Melem/s & solves/s vs dense GPU DDM at <=1e-3 rel err; p50/p99"
+WORKLOAD = "random pressurised fractures: 200 cracks x 100 elements (N=20000), dt=10 s"
+DT = 10.0
+LOADS = dict(sigma_H=30e6, sigma_h=25e6, p_f=10e6, p0=0.0)
+# FP32 operations of one point-kernel evaluation between two Chebyshev
+# nodes in M2L (elastic potency kernel, poroelastic transient with both
+# series branches' common path, fluid source, 4x4 accumulation), counted from
+# kernel_math.cuh; see DESIGN.md "roofline".
+M2L_FLOP_PER_NODE_PAIR = 220
+P2P_FLOP_PER_PAIR = 520
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n-cheb", type=int, default=8)
+    ap.add_argument("--leaf", type=int, default=32)
+    ap.add_argument("--solves", type=int, default=10)
+    ap.add_argument("--oracle-rows", type=int, default=12)
+    ap.add_argument("--no-oracle", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def alu_peak_tflops(sm_mhz):
+    """FP32 FMA peak: 152 SMs x 128 FP32 lanes x 2 flop x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def oracle_sample(xy, x, rows_elems):
+    import oracle
+    mat = __import__("paper_1812_05087_gb300.inputs", fromlist=["x"]).material_tuple()
+    N = xy.shape[1]
+    rows = np.concatenate([rows_elems + b * N for b in range(3)])
+    t0 = time.perf_counter()
+    A = oracle.assemble_rows(mat, xy, DT, rows)
+    dt = time.perf_counter() - t0
+    return A @ x, rows, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    from paper_1812_05087_gb300 import inputs
+    xy, _ = inputs.random_fractures()
+    N = xy.shape[1]
+    x = inputs.unknowns(N, seed=99)
+    rng = np.random.default_rng(0)
+    k = max(1, args.oracle_rows // 3)
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle_sample(xy, x, rng.choice(N, 1, replace=False))
+    times = []
+    for _ in range(args.steps):
+        _, _, dt = oracle_sample(xy, x, rng.choice(N, k, replace=False))
+        times.append(dt)
+    per_elem = sum(times) / (k * args.steps)
+    v = 1.0 / per_elem / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Melem/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_rows_per_step": 3 * k},
+            "cpu_baseline": {"value": v, "unit": "Melem/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{k} target elements (3 rows each) x {N} source elements per step"},
+            "e2e": {"value": v, "unit": "Melem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_1812_05087_gb300 import inputs
+    from paper_1812_05087_gb300.ddm import Context
+
+    xy, segs = inputs.random_fractures(seed=inputs.SEED + rank)
+    N = xy.shape[1]
+    tips = inputs.tips_of(segs)
+    stream = torch.cuda.current_stream()
+    ctx = Context(inputs.MATERIAL, n_cheb=args.n_cheb, leaf_size=args.leaf)
+    d_xy = torch.as_tensor(xy, dtype=torch.float64, device="cuda")
+    tree = ctx.build_tree(d_xy)
+    info = tree.info()
+    x_h = inputs.unknowns(N, seed=99)
+    x = torch.as_tensor(x_h, device="cuda")
+    y = torch.empty_like(x)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(fn, K, W):
+        for _ in range(W):
+            fn()
+        barrier()
+        ts = []
+        for _ in range(K):
+            flush.add_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            ts.append((a, b))
+        barrier()
+        return [a.elapsed_time(b) for a, b in ts]
+
+    # ---------------- FMM product (value)
+    fmm = lambda: ctx.matvec(tree, x, 0.0, DT, mode="fmm", out=y)
+    ctx.profile_read()
+    with Clocks(local) as clk:
+        t_fmm = timed(fmm, args.steps, args.warmup)
+    launches = ctx.profile_read()
+    n_launch_fmm = sum(v[1] for v in launches.values())
+    per_matvec_launches = n_launch_fmm / (args.steps + args.warmup)
+    # stage breakdown with events (separate pass)
+    ctx.profile(True)
+    for _ in range(3):
+        fmm()
+    stages = ctx.profile_read()
+    ctx.profile(False)
+    ms_fmm = float(np.mean(t_fmm))
+    y_fmm = y.cpu().numpy()
+
+    # ---------------- dense product on the GPU (conventional PDDM)
+    dense = lambda: ctx.matvec(tree, x, 0.0, DT, mode="dense", out=y)
+    t_dense = timed(dense, max(2, args.steps // 5), 2)
+    y_dense = y.cpu().numpy()
+    ms_dense = float(np.mean(t_dense))
+
+    # ---------------- full time-step solves
+    def solve(mode):
+        tr = ctx.build_tree(d_xy)
+        b = ctx.rhs(tr, system="pressure", **LOADS)
+        sol, inf = ctx.gmres_solve(tr, DT, b, system="pressure", tol=1e-5, mode=mode, raise_on_notconv=False)
+        ctx.sif(tr, sol, tips)
+        tr.close()
+        return inf
+
+    lat, infos = [], []
+    for i in range(args.solves + 2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        infos.append(solve("fmm"))
+        torch.cuda.synchronize()
+        if i >= 2:
+            lat.append(time.perf_counter() - t0)
+    lat_ms = sorted(1e3 * v for v in lat)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    dinfo = solve("dense")
+    torch.cuda.synchronize()
+    dense_solve_ms = 1e3 * (time.perf_counter() - t0)
+
+    # ---------------- end to end through the C ABI with host buffers
+    xh = torch.as_tensor(x_h).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+
+    def e2e():
+        x.copy_(xh, non_blocking=True)
+        ctx.matvec(tree, x, 0.0, DT, mode="fmm", out=y)
+        yh.copy_(y, non_blocking=True)
+
+    t_e2e = timed(e2e, args.steps, args.warmup)
+    ms_e2e = float(np.mean(t_e2e))
+
+    # ---------------- roofline of the dominant kernel
+    st = {k: v for k, v in stages.items() if v[1] > 0}
+    dom = max(st, key=lambda k: st[k][0])
+    dom_ms = st[dom][0] / max(1, st[dom][1])
+    n = args.n_cheb
+    clocks = clk.summary()
+    sm_mhz = clocks["sm_mhz"] or peaks().get("sm_max_mhz", 2070.0)
+    if dom == "m2l":
+        flop = info["n_m2l_pairs"] * n ** 4 * M2L_FLOP_PER_NODE_PAIR
+    elif dom == "leaf":
+        flop = info["n_p2p_pairs"] * P2P_FLOP_PER_PAIR
+    else:
+        flop = None
+    achieved = flop / (dom_ms * 1e-3) / 1e12 if flop else None
+    peak = alu_peak_tflops(sm_mhz)
+    roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if achieved else None, "traffic": None,
+            "peak_note": f"FP32 FMA peak 152 SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz (median SM clock under load)",
+            "ms_per_launch": dom_ms}
+
+    # ---------------- accuracy + CPU baseline (oracle on sampled rows)
+    err = cpu = None
+    if rank == 0 and not args.no_oracle:
+        rng = np.random.default_rng(1)
+        k = max(1, args.oracle_rows // 3)
+        elems = rng.choice(N, k, replace=False)
+        ref, rows, dt_or = oracle_sample(xy, x_h, elems)
+        e_f = np.abs(y_fmm[rows] - ref)
+        e_d = np.abs(y_dense[rows] - ref)
+        scale = [np.abs(ref[b * k:(b + 1) * k]).max() for b in range(3)]
+        err = {"fmm_vs_oracle": max(e_f[b * k:(b + 1) * k].max() / scale[b] for b in range(3)),
+               "dense_vs_oracle": max(e_d[b * k:(b + 1) * k].max() / scale[b] for b in range(3)),
+               "rows": int(rows.size)}
+        import oracle
+        cpu = {"value": k / dt_or / 1e6, "unit": "Melem/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"{k} target elements (3 rows each) x {N} sources, FP64 adaptive element quadrature"}
+
+    # ---------------- max over ranks
+    tot_ms = ms_fmm
+    if dist:
+        tt = torch.tensor([ms_fmm, ms_e2e], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        tot_ms, ms_e2e = float(tt[0]), float(tt[1])
+    if rank != 0:
+        return
+    value = world * N / (tot_ms * 1e-3) / 1e6
+    solves_s = 1e3 / float(np.mean(lat_ms))
+    line = {
+        "metric": METRIC, "value": value, "unit": "Melem/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "n_cheb": n, "leaf": args.leaf, "depth": info["depth"],
+                   "m2l_pairs": info["n_m2l_pairs"], "p2p_pairs": info["n_p2p_pairs"],
+                   "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
+        "solves_per_s": world * solves_s, "solve_p50_ms": lat_ms[len(lat_ms) // 2],
+        "solve_p99_ms": lat_ms[min(len(lat_ms) - 1, int(0.99 * len(lat_ms)))],
+        "gmres_iterations": infos[-1]["iterations"], "gmres_rel_residual": infos[-1]["rel_residual"],
+        "dense_melem_s": world * N / (ms_dense * 1e-3) / 1e6, "dense_ms_per_matvec": ms_dense,
+        "dense_solve_ms": dense_solve_ms, "dense_gmres_iterations": dinfo["iterations"],
+        "fmm_speedup_vs_dense": ms_dense / ms_fmm,
+        "error": err,
+        "stages_ms_per_matvec": {k: v[0] / 3 for k, v in stages.items() if v[1] > 0},
+        "roofline": roof, "cpu_baseline": cpu,
+        "e2e": {"value": world * N / (ms_e2e * 1e-3) / 1e6, "unit": "Melem/s",
+                "h2d_bytes_per_step": int(x.numel() * 8), "d2h_bytes_per_step": int(y.numel() * 8)},
+        "gpu_launches": int(round(per_matvec_launches * args.steps)),
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,197 @@
+/*
+ * ddm.h - C ABI of the GB300 (sm_103a) fast multipole, fully coupled
+ * poroelastic displacement discontinuity method (2D, constant spatial and
+ * constant temporal elements).
+ *
+ * The library computes the matrix-free influence product of paper
+ * Eqs. (2.3)-(2.5) - stress (sigma_s, sigma_n) and pore pressure p at every
+ * element midpoint caused by shear DD, normal DD and fluid source on every
+ * element - with the black-box (Chebyshev) fast multipole method of paper
+ * Sec. 3, and uses it in the two places of the paper's algorithm (Sec. 4):
+ * the time-marching history sum and the GMRES solve of each time step.
+ *
+ * Conventions (all calls):
+ *   - SI units; tension-positive stress; pore pressure positive.
+ *   - Element e runs from (x0[e], y0[e]) to (x1[e], y1[e]); its tangent t
+ *     points from the first to the second end point, its normal n is t
+ *     rotated by +90 degrees.  D = u(+) - u(-), + face on the side n points
+ *     to; D_n > 0 opens the crack.  D_q is the fluid source strength per unit
+ *     element length (m^2/s per m).
+ *   - Unknown vectors have 3N doubles in blocks [Ds(N), Dn(N), Dq(N)];
+ *     result vectors have 3N doubles [sigma_s(N), sigma_n(N), p(N)], each at
+ *     the element midpoint, stresses resolved in that element's (t, n) frame.
+ *   - K(tau) is the response to a source switched on at time 0 and held,
+ *     observed at time tau (K(tau <= 0) = 0).  A source held constant over
+ *     the time element (t_a, t_b] seen at time t_obs contributes
+ *     [K(t_obs - t_a) - K(t_obs - t_b)] x.
+ *
+ * Memory and streams:
+ *   - Every d_* pointer is DEVICE memory on the context's device, owned by
+ *     the caller, contiguous, 8-byte aligned, and must stay valid until the
+ *     enqueued work has finished.  Every h_* pointer is host memory read
+ *     before the call returns.
+ *   - Trees, workspaces, Chebyshev expansions and Krylov bases are owned by
+ *     the library.
+ *   - Work is enqueued on the stream given to ddm_create and calls return
+ *     without synchronising, except where a call's comment says it
+ *     synchronises (tree build and GMRES read small values back).
+ *
+ * Errors: no C++ exception crosses this boundary.  Invalid arguments give
+ * DDM_EINVAL, allocation failures DDM_ENOMEM, CUDA runtime errors DDM_ECUDA;
+ * ddm_last_error() returns a message for the last failing call on a context.
+ */
+#ifndef DDM_GB300_H
+#define DDM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DDM_OK = 0,
+    DDM_EINVAL = 1,
+    DDM_ENOMEM = 2,
+    DDM_ENOTCONV = 3,   /* GMRES did not reach tol; solution and residual still written */
+    DDM_ETIMEOUT = 4,   /* a bounded device wait expired */
+    DDM_ECUDA = 5,
+    DDM_PENDING = 6     /* ddm_poll: request still running */
+} ddm_status;
+
+/* Poroelastic rock (paper Table 1 quantities): shear modulus G, drained and
+ * undrained Poisson ratios, Skempton B, permeability k (m^2) and fluid
+ * viscosity mu (Pa s).  Biot alpha, M and the diffusivity c follow from
+ * these (Biot / Rice-Cleary plane strain). */
+typedef struct {
+    double G, nu, nu_u, B, perm, visc;
+} ddm_material;
+
+/* FMM controls (paper Sec. 3): n_cheb = Chebyshev nodes per dimension
+ * (n^2 per cell), leaf_size = the "prescribed number" of elements above
+ * which a cell is split, max_depth caps the quadtree depth (0 = automatic).
+ * quad_near = Gauss points per element for the fluid-source near field
+ * (0 = 6). */
+typedef struct {
+    int n_cheb;
+    int leaf_size;
+    int max_depth;
+    int quad_near;
+} ddm_fmm_params;
+
+typedef struct ddm_ctx ddm_ctx;
+typedef struct ddm_tree ddm_tree;
+
+/* Create a context bound to the current CUDA device and the given stream
+ * (a cudaStream_t, or NULL for the legacy default stream). */
+ddm_status ddm_create(ddm_ctx **out, const ddm_material *mat, const ddm_fmm_params *prm,
+                      void *cuda_stream);
+void ddm_destroy(ddm_ctx *ctx);
+const char *ddm_last_error(const ddm_ctx *ctx);
+
+/* Build the quadtree of paper Sec. 3.1 over the element midpoints: level-0
+ * square covering all midpoints, uniform depth (smallest depth whose leaves
+ * hold <= leaf_size elements, capped so that no element is longer than a
+ * quarter of a leaf), empty ("zero") cells dropped, children in Z order,
+ * neighbour and interaction lists of paper Sec. 3.1.  Built on the device
+ * (Morton keys + radix sort).  d_xy: 4N doubles [x0(N), y0(N), x1(N), y1(N)].
+ * Synchronises the stream.  The tree keeps its own copy of the geometry. */
+ddm_status ddm_build_tree(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **out);
+void ddm_tree_destroy(ddm_tree *tree);
+
+typedef struct {
+    int64_t n_elements;
+    int depth;             /* leaf level L */
+    int64_t n_cells;       /* non-empty cells, all levels */
+    int64_t n_leaves;
+    int64_t n_m2l_pairs;   /* interaction-list entries, all levels */
+    int64_t n_p2p_pairs;   /* (target element, source element) near pairs */
+    double root_half_width;
+} ddm_tree_info;
+ddm_status ddm_tree_get_info(const ddm_tree *tree, ddm_tree_info *info);
+
+#define DDM_MODE_FMM 0     /* Chebyshev FMM (paper Sec. 3) */
+#define DDM_MODE_DENSE 1   /* every pair evaluated on the fly (conventional PDDM) */
+
+/* d_y = [K(tau_hi) - K(tau_lo)] d_x  (paper Eqs. 2.3-2.5, left-hand sums for
+ * tau_lo = 0, tau_hi = dt; one history term otherwise).  0 <= tau_lo < tau_hi.
+ * d_x, d_y: 3N doubles, caller element order, must not overlap. */
+ddm_status ddm_matvec(ddm_ctx *ctx, const ddm_tree *tree, double tau_lo, double tau_hi,
+                      const double *d_x, double *d_y, int mode);
+
+/* Time-history double sum of paper Eqs. (2.3)-(2.5) (applied with FMM as in
+ * paper Sec. 4):  d_rhs -= sum_{eta=1}^{H} [K(t_{H+1} - t_{eta-1})
+ *                                          - K(t_{H+1} - t_eta)] D^eta
+ * d_hist: H x 3N doubles, row eta-1 = D^eta (caller element order);
+ * h_times: H + 2 host doubles t_0 < t_1 < ... < t_{H+1} (t_{H+1} = the
+ * current observation time). */
+ddm_status ddm_history_apply(ddm_ctx *ctx, const ddm_tree *tree, const double *d_hist,
+                             const double *h_times, int H, double *d_rhs, int mode);
+
+#define DDM_SYS_PRESSURE 0     /* unknowns Ds, Dn, Dq; rows sigma_s, sigma_n, p (3N) */
+#define DDM_SYS_IMPERMEABLE 1  /* unknowns Ds, Dn (Dq given); rows sigma_s, sigma_n (2N) */
+#define DDM_SYS_RATE 2         /* unknowns Ds, Dn (Dq given); rows sigma_s, sigma_n + p (2N) */
+
+/* Known right-hand side of the first step (paper Sec. 4): far-field stresses
+ * transformed to each element face and added to the hydraulic load.
+ * sigma_H along x and sigma_h along y are compression positive.  With p_f the
+ * fracture fluid pressure and p0 the initial pore pressure:
+ *   PRESSURE:    [-tau_inf, -(p_f - s_nn_inf), p_f - p0]
+ *   IMPERMEABLE: [-tau_inf, -(p_f - s_nn_inf), 0]
+ *   RATE:        [-tau_inf, -(p0 - s_nn_inf), 0]   (second row is sigma_n + p)
+ * d_pf: N doubles of per-element fluid pressure, or NULL to use p_f. */
+typedef struct {
+    double sigma_H, sigma_h, p_f, p0;
+    int system;
+} ddm_loads;
+ddm_status ddm_rhs(ddm_ctx *ctx, const ddm_tree *tree, const ddm_loads *loads, const double *d_pf,
+                   double *d_rhs);
+
+typedef struct {
+    int system;        /* DDM_SYS_* */
+    int restart;       /* Krylov basis size before restart (default 50) */
+    int max_iters;     /* total iterations (default 1000) */
+    double tol;        /* relative residual ||b - A x|| / ||b|| (default 1e-6, paper Sec. 5) */
+    int mode;          /* DDM_MODE_FMM or DDM_MODE_DENSE for the products */
+} ddm_gmres_params;
+typedef struct {
+    int iterations;
+    int restarts;
+    double rel_residual;   /* true residual of the returned x (recomputed) */
+    int converged;
+} ddm_gmres_info;
+
+/* Solve [K(dt)] x = rhs restricted to the chosen system with restarted GMRES
+ * (paper Sec. 4, "modified GMRES with FMM products") in FP64, right
+ * block-Jacobi preconditioned by each element's own 3x3 (2x2) block.
+ * d_rhs: 3N doubles (rows not in the system are ignored).  d_x: 3N doubles,
+ * in: initial guess (and the prescribed Dq for 2N systems), out: solution.
+ * Returns DDM_ENOTCONV (x and info still written) when max_iters is reached
+ * or when three restarts in a row fail to halve the true residual: the
+ * pair kernels are FP32, so the true relative residual of a product is
+ * floored near 1e-6 and a smaller tol may be unattainable.
+ * Synchronises the stream (reads the Hessenberg columns back). */
+ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const double *d_rhs,
+                           double *d_x, const ddm_gmres_params *prm, ddm_gmres_info *info);
+
+/* Stress intensity factors from the tip element DDs (paper Eq. 2.6, Olson):
+ * K = 0.806 E / (4 (1 - nu^2)) sqrt(pi / (2 a)) D, a = half-length of the tip
+ * element, (E, nu) drained.  d_tip: n element indices; d_KI, d_KII: n doubles. */
+ddm_status ddm_sif(ddm_ctx *ctx, const ddm_tree *tree, const double *d_x, const int64_t *d_tip,
+                   int n, double *d_KI, double *d_KII);
+
+/* Stage timing for profiling (no counterpart in the paper): when enabled,
+ * CUDA events bracket each stage on the context stream.  ddm_profile_read
+ * synchronises the stream and returns, per stage, the summed milliseconds
+ * (ms[DDM_NSTAGES]) and the number of kernel launches (counted whether or
+ * not timing is enabled) since the last read, then resets both.
+ * Stages: 0 charges, 1 own element, 2 P2M, 3 M2M, 4 M2L, 5 L2L, 6 leaf
+ * (L2P + P2P), 7 dense product, 8 GMRES vector kernels, 9 tree build. */
+#define DDM_NSTAGES 10
+ddm_status ddm_profile(ddm_ctx *ctx, int enable);
+ddm_status ddm_profile_read(ddm_ctx *ctx, double *ms, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DDM_GB300_H */

@@ -1,0 +1,484 @@
+// C ABI of the library: context, tree handles, products, history sum,
+// right-hand side, GMRES (FP64, device-resident Krylov basis) and SIFs.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+ddm_status ctx_fail(ddm_ctx *ctx, ddm_status st, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    return st;
+}
+
+void prof_begin(ddm_ctx *ctx, int stage) {
+    if (!ctx->prof.on) return;
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, ctx->stream);
+    ctx->prof.open_stage = stage;
+    ctx->prof.open_ev = e;
+}
+void prof_end(ddm_ctx *ctx, int stage, int launches) {
+    ctx->prof.launches[stage] += launches;
+    if (!ctx->prof.on || ctx->prof.open_stage != stage) return;
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, ctx->stream);
+    ctx->prof.ev.push_back({stage, {ctx->prof.open_ev, e}});
+    ctx->prof.open_stage = -1;
+}
+
+namespace {
+
+// S_n(xi_a, x): Chebyshev cardinal function at the roots of T_n (paper Sec. 3.2)
+double cheb_S(int n, double xa, double x) {
+    double s = 1.0 / n, t0a = 1, t1a = xa, t0 = 1, t1 = x;
+    for (int k = 1; k < n; ++k) {
+        s += 2.0 / n * t1a * t1;
+        double t2a = 2 * xa * t1a - t0a, t2 = 2 * x * t1 - t0;
+        t0a = t1a; t1a = t2a; t0 = t1; t1 = t2;
+    }
+    return s;
+}
+
+ddm_status valid_material(const ddm_material *m) {
+    if (!m) return DDM_EINVAL;
+    if (!(m->G > 0) || !(m->nu >= 0) || !(m->nu < m->nu_u) || !(m->nu_u < 0.5) || !(m->B > 0) || !(m->B <= 1) ||
+        !(m->perm > 0) || !(m->visc > 0))
+        return DDM_EINVAL;
+    return DDM_OK;
+}
+
+// ------------------------------------------------------------- small kernels
+__global__ void k_rhs(const double *xy, int64_t n, ddm_loads L, const double *pf, double *b) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    double dx = xy[2 * n + e] - xy[e], dy = xy[3 * n + e] - xy[n + e];
+    double len = hypot(dx, dy), tx = dx / len, ty = dy / len, nx = -ty, ny = tx;
+    double sxx = -L.sigma_H, syy = -L.sigma_h;            // tension positive far field
+    double snn = sxx * nx * nx + syy * ny * ny, tau = sxx * tx * nx + syy * ty * ny;
+    double p_f = pf ? pf[e] : L.p_f;
+    b[e] = -tau;
+    b[n + e] = (L.system == DDM_SYS_RATE) ? (-L.p0 - snn) : (-p_f - snn);
+    b[2 * n + e] = (L.system == DDM_SYS_PRESSURE) ? (p_f - L.p0) : 0.0;
+}
+
+__global__ void k_sif(const double *xy, int64_t n, const double *x, const int64_t *tip, int m, double G, double nu,
+                      double *KI, double *KII) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    int64_t e = tip[i];
+    double a = 0.5 * hypot(xy[2 * n + e] - xy[e], xy[3 * n + e] - xy[n + e]);
+    double E = 2.0 * G * (1.0 + nu);
+    double f = 0.806 * E / (4.0 * (1.0 - nu * nu)) * sqrt(M_PI / (2.0 * a));
+    KI[i] = f * x[n + e];
+    KII[i] = f * x[e];
+}
+
+// --- GMRES helpers (FP64).  Reduced vectors (length nu) live in the first
+// ncomp blocks of N of a 3N vector layout.
+constexpr int RT = 256;
+__global__ void k_dots(const double *V, int64_t ld, int nv, const double *w, int64_t len, double *h) {
+    __shared__ double s[RT];
+    int v = blockIdx.y;
+    double acc = 0;
+    for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < len; i += (int64_t)gridDim.x * RT)
+        acc += V[v * ld + i] * w[i];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = RT / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(&h[v], s[0]);
+}
+__global__ void k_sub(const double *V, int64_t ld, int nv, const double *h, double *w, int64_t len, double *hacc) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (blockIdx.x == 0 && threadIdx.x < nv && hacc) hacc[threadIdx.x] += h[threadIdx.x];
+    if (i >= len) return;
+    double s = 0;
+    for (int v = 0; v < nv; ++v) s += h[v] * V[v * ld + i];
+    w[i] -= s;
+}
+__global__ void k_scale_to(const double *w, int64_t len, const double *nrm2, double *out, double *hcol_j1) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double nrm = sqrt(*nrm2);
+    if (i == 0) *hcol_j1 = nrm;
+    if (i >= len) return;
+    out[i] = nrm > 0 ? w[i] / nrm : 0.0;
+}
+// z = M^-1 v (block Jacobi with the own-element blocks, inverted per element)
+__global__ void k_precond(const double *Minv, int64_t n, int nc, const double *v, double *z) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    double in[3] = {0, 0, 0};
+    for (int c = 0; c < nc; ++c) in[c] = v[c * n + e];
+    for (int r = 0; r < nc; ++r) {
+        double s = 0;
+        for (int c = 0; c < nc; ++c) s += Minv[9 * e + 3 * r + c] * in[c];
+        z[r * n + e] = s;
+    }
+}
+// inverse of the system's own-element block (3x3, or the 2x2 of the 2N systems)
+__global__ void k_invert(const double *blk, int64_t n, int sys, double *Minv) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const double *B = blk + 9 * e;
+    double *O = Minv + 9 * e;
+    for (int k = 0; k < 9; ++k) O[k] = 0;
+    if (sys == DDM_SYS_PRESSURE) {
+        double a = B[0], b = B[1], c = B[2], d = B[3], f = B[4], g = B[5], h = B[6], i = B[7], j = B[8];
+        double A = f * j - g * i, Bc = -(d * j - g * h), C = d * i - f * h;
+        double det = a * A + b * Bc + c * C;
+        double id = 1.0 / det;
+        O[0] = A * id; O[1] = -(b * j - c * i) * id; O[2] = (b * g - c * f) * id;
+        O[3] = Bc * id; O[4] = (a * j - c * h) * id; O[5] = -(a * g - c * d) * id;
+        O[6] = C * id; O[7] = -(a * i - b * h) * id; O[8] = (a * f - b * d) * id;
+    } else {
+        double a = B[0], b = B[1], c = B[3], d = B[4];
+        if (sys == DDM_SYS_RATE) { c += B[6]; d += B[7]; }
+        double id = 1.0 / (a * d - b * c);
+        O[0] = d * id; O[1] = -b * id; O[3] = -c * id; O[4] = a * id;
+    }
+}
+// restrict a 3N product to the system rows (RATE: sigma_n + p)
+// (combine = 1 for products, 0 for a right-hand side, whose rows are already
+// the system's)
+__global__ void k_restrict(const double *y, int64_t n, int sys, int combine, double *out) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    out[e] = y[e];
+    out[n + e] = y[n + e] + (combine && sys == DDM_SYS_RATE ? y[2 * n + e] : 0.0);
+    if (sys == DDM_SYS_PRESSURE) out[2 * n + e] = y[2 * n + e];
+}
+__global__ void k_axpy(double a, const double *x, double *y, int64_t len) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < len) y[i] += a * x[i];
+}
+__global__ void k_comb(const double *V, int64_t ld, int nv, const double *yv, double *out, int64_t len) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= len) return;
+    double s = 0;
+    for (int v = 0; v < nv; ++v) s += yv[v] * V[v * ld + i];
+    out[i] = s;
+}
+
+inline unsigned nblk(int64_t len, int t = 256) { return (unsigned)((len + t - 1) / t); }
+
+}  // namespace
+
+struct GmresWork {
+    int64_t cap_len = 0;
+    int cap_m = 0;
+    double *V = nullptr, *w = nullptr, *z = nullptr, *full = nullptr, *y3 = nullptr, *b = nullptr;
+    double *h = nullptr, *hcol = nullptr, *nrm = nullptr, *Minv = nullptr, *yv = nullptr;
+    void release() {
+        double *ps[] = {V, w, z, full, y3, b, h, hcol, nrm, Minv, yv};
+        for (double *p : ps)
+            if (p) cudaFree(p);
+        *this = GmresWork();
+    }
+};
+
+extern "C" {
+
+ddm_status ddm_create(ddm_ctx **out, const ddm_material *mat, const ddm_fmm_params *prm, void *cuda_stream) {
+    if (!out) return DDM_EINVAL;
+    *out = nullptr;
+    if (valid_material(mat) != DDM_OK) return DDM_EINVAL;
+    ddm_fmm_params p = prm ? *prm : ddm_fmm_params{8, 32, 0, 6};
+    if (p.n_cheb <= 0) p.n_cheb = 8;
+    if (p.leaf_size <= 0) p.leaf_size = 32;
+    if (p.quad_near <= 0) p.quad_near = 6;
+    if (p.n_cheb < 2 || p.n_cheb > DDM_MAX_CHEB || p.quad_near > 16 || p.max_depth < 0) return DDM_EINVAL;
+    ddm_ctx *c = new (std::nothrow) ddm_ctx();
+    if (!c) return DDM_ENOMEM;
+    c->mat = *mat;
+    c->prm = p;
+    c->stream = (cudaStream_t)cuda_stream;
+    if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return DDM_ECUDA; }
+    const ddm_material &m = *mat;
+    double G = m.G, nu = m.nu, nuu = m.nu_u, B = m.B;
+    double alpha = 3 * (nuu - nu) / (B * (1 - 2 * nu) * (1 + nuu));
+    double eta = alpha * (1 - 2 * nu) / (2 * (1 - nu));
+    double M = 2 * G * (nuu - nu) / (alpha * alpha * (1 - 2 * nuu) * (1 - 2 * nu));
+    double S = alpha * eta / G + 1 / M;
+    double kappa = m.perm / m.visc;
+    double kpsi = alpha * eta / (G * S);
+    KConst<double> kd;
+    kd.G2 = 2 * G;
+    kd.Cel = G / (2 * M_PI * (1 - nu));
+    kd.Ce = (1 - 2 * nu) / (2 * M_PI * (1 - nu));
+    kd.K2 = kpsi * kd.Ce / 4;
+    kd.aS = alpha / S;
+    kd.eta = eta;
+    kd.i4pk = 1 / (4 * M_PI * kappa);
+    kd.c = kappa / S;
+    c->kd = kd;
+    c->kf = KConst<float>{(float)kd.G2, (float)kd.Cel, (float)kd.Ce, (float)kd.K2, (float)kd.aS, (float)kd.eta,
+                          (float)kd.i4pk, (float)kd.c};
+    // M2M / L2L transfer matrices T[q][a][a'] = S_n(xi_a, (xi_a' + q)/2)
+    int n = p.n_cheb;
+    std::vector<double> xi(n);
+    for (int j = 0; j < n; ++j) xi[j] = cos((2 * j + 1) * M_PI / (2.0 * n));
+    std::vector<float> T(2 * n * n);
+    for (int q = 0; q < 2; ++q)
+        for (int a = 0; a < n; ++a)
+            for (int ap = 0; ap < n; ++ap)
+                T[q * n * n + a * n + ap] = (float)cheb_S(n, xi[a], 0.5 * (xi[ap] + (q ? 1.0 : -1.0)));
+    if (cudaMalloc(&c->cheb_T, T.size() * sizeof(float)) != cudaSuccess) { delete c; return DDM_ENOMEM; }
+    cudaMemcpy(c->cheb_T, T.data(), T.size() * sizeof(float), cudaMemcpyHostToDevice);
+    c->gm = new GmresWork();
+    *out = c;
+    return DDM_OK;
+}
+
+void ddm_destroy(ddm_ctx *ctx) {
+    if (!ctx) return;
+    if (ctx->cheb_T) cudaFree(ctx->cheb_T);
+    if (ctx->gm) { ctx->gm->release(); delete ctx->gm; }
+    delete ctx;
+}
+
+const char *ddm_last_error(const ddm_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+ddm_status ddm_profile(ddm_ctx *ctx, int enable) {
+    if (!ctx) return DDM_EINVAL;
+    ctx->prof.on = enable ? 1 : 0;
+    return DDM_OK;
+}
+
+ddm_status ddm_profile_read(ddm_ctx *ctx, double *ms, int64_t *launches) {
+    if (!ctx || !ms || !launches) return DDM_EINVAL;
+    DDM_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < DDM_NSTAGES; ++k) { ms[k] = 0.0; launches[k] = ctx->prof.launches[k]; ctx->prof.launches[k] = 0; }
+    for (auto &p : ctx->prof.ev) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, p.second.first, p.second.second);
+        ms[p.first] += t;
+        cudaEventDestroy(p.second.first);
+        cudaEventDestroy(p.second.second);
+    }
+    ctx->prof.ev.clear();
+    return DDM_OK;
+}
+
+ddm_status ddm_build_tree(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **out) {
+    if (!ctx) return DDM_EINVAL;
+    return tree_build(ctx, d_xy, n, out);
+}
+
+void ddm_tree_destroy(ddm_tree *tree) { tree_free(tree); }
+
+ddm_status ddm_tree_get_info(const ddm_tree *t, ddm_tree_info *info) {
+    if (!t || !info) return DDM_EINVAL;
+    info->n_elements = t->n;
+    info->depth = t->depth;
+    info->n_cells = t->n_cells;
+    info->n_leaves = t->lvl_off[t->depth + 1] - t->lvl_off[t->depth];
+    info->n_m2l_pairs = t->n_m2l;
+    info->n_p2p_pairs = t->n_p2p;
+    info->root_half_width = t->h0;
+    return DDM_OK;
+}
+
+ddm_status ddm_matvec(ddm_ctx *ctx, const ddm_tree *tree, double tau_lo, double tau_hi, const double *d_x, double *d_y,
+                      int mode) {
+    if (!ctx || !tree || !d_x || !d_y || d_x == d_y || (mode != DDM_MODE_FMM && mode != DDM_MODE_DENSE))
+        return ctx_fail(ctx, DDM_EINVAL, "ddm_matvec: bad arguments");
+    return op_apply(ctx, const_cast<ddm_tree *>(tree), tau_lo, tau_hi, d_x, d_y, mode, 0, 1.0);
+}
+
+ddm_status ddm_history_apply(ddm_ctx *ctx, const ddm_tree *tree, const double *d_hist, const double *h_times, int H,
+                             double *d_rhs, int mode) {
+    if (!ctx || !tree || H < 0 || (H > 0 && (!d_hist || !h_times)) || !d_rhs)
+        return ctx_fail(ctx, DDM_EINVAL, "ddm_history_apply: bad arguments");
+    if (H == 0) return DDM_OK;
+    for (int k = 0; k <= H; ++k)
+        if (!(h_times[k + 1] > h_times[k])) return ctx_fail(ctx, DDM_EINVAL, "ddm_history_apply: times must increase");
+    ddm_tree *t = const_cast<ddm_tree *>(tree);
+    int64_t N = t->n;
+    double tobs = h_times[H + 1];
+    for (int eta = 1; eta <= H; ++eta) {
+        double lo = tobs - h_times[eta], hi = tobs - h_times[eta - 1];
+        ddm_status st = op_apply(ctx, t, lo, hi, d_hist + (int64_t)(eta - 1) * 3 * N, d_rhs, mode, 1, -1.0);
+        if (st) return st;
+    }
+    return DDM_OK;
+}
+
+ddm_status ddm_rhs(ddm_ctx *ctx, const ddm_tree *tree, const ddm_loads *loads, const double *d_pf, double *d_rhs) {
+    if (!ctx || !tree || !loads || !d_rhs || loads->system < 0 || loads->system > 2)
+        return ctx_fail(ctx, DDM_EINVAL, "ddm_rhs: bad arguments");
+    k_rhs<<<nblk(tree->n), 256, 0, ctx->stream>>>(tree->xy_caller, tree->n, *loads, d_pf, d_rhs);
+    DDM_CUDA_TRY(ctx, cudaGetLastError());
+    return DDM_OK;
+}
+
+ddm_status ddm_sif(ddm_ctx *ctx, const ddm_tree *tree, const double *d_x, const int64_t *d_tip, int n, double *d_KI,
+                   double *d_KII) {
+    if (!ctx || !tree || !d_x || n < 0 || (n > 0 && (!d_tip || !d_KI || !d_KII)))
+        return ctx_fail(ctx, DDM_EINVAL, "ddm_sif: bad arguments");
+    if (n == 0) return DDM_OK;
+    k_sif<<<nblk(n), 256, 0, ctx->stream>>>(tree->xy_caller, tree->n, d_x, d_tip, n, ctx->mat.G, ctx->mat.nu, d_KI,
+                                            d_KII);
+    DDM_CUDA_TRY(ctx, cudaGetLastError());
+    return DDM_OK;
+}
+
+ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const double *d_rhs, double *d_x,
+                           const ddm_gmres_params *prm, ddm_gmres_info *info) {
+    if (!ctx || !tree || !d_rhs || !d_x || !(dt > 0)) return ctx_fail(ctx, DDM_EINVAL, "ddm_gmres_solve: bad arguments");
+    ddm_gmres_params P = prm ? *prm : ddm_gmres_params{DDM_SYS_PRESSURE, 50, 1000, 1e-6, DDM_MODE_FMM};
+    if (P.restart <= 0) P.restart = 50;
+    if (P.max_iters <= 0) P.max_iters = 1000;
+    if (!(P.tol > 0)) P.tol = 1e-6;
+    if (P.system < 0 || P.system > 2 || P.restart > 500) return ctx_fail(ctx, DDM_EINVAL, "ddm_gmres_solve: bad params");
+    ddm_tree *t = const_cast<ddm_tree *>(tree);
+    cudaStream_t s = ctx->stream;
+    int64_t N = t->n;
+    int nc = P.system == DDM_SYS_PRESSURE ? 3 : 2;
+    int64_t len = nc * N;
+    int m = P.restart;
+    GmresWork &g = *ctx->gm;
+    if (g.cap_len < len || g.cap_m < m) {
+        g.release();
+        size_t v3 = 3 * N * sizeof(double);
+        bool ok = cudaMalloc(&g.V, (size_t)(m + 1) * len * sizeof(double)) == cudaSuccess &&
+                  cudaMalloc(&g.w, v3) == cudaSuccess && cudaMalloc(&g.z, v3) == cudaSuccess &&
+                  cudaMalloc(&g.full, v3) == cudaSuccess && cudaMalloc(&g.y3, v3) == cudaSuccess &&
+                  cudaMalloc(&g.b, v3) == cudaSuccess && cudaMalloc(&g.h, (m + 2) * sizeof(double)) == cudaSuccess &&
+                  cudaMalloc(&g.hcol, (m + 2) * sizeof(double)) == cudaSuccess &&
+                  cudaMalloc(&g.nrm, sizeof(double)) == cudaSuccess &&
+                  cudaMalloc(&g.Minv, 9 * N * sizeof(double)) == cudaSuccess &&
+                  cudaMalloc(&g.yv, (m + 1) * sizeof(double)) == cudaSuccess;
+        if (!ok) { g.release(); return ctx_fail(ctx, DDM_ENOMEM, "GMRES workspace allocation failed"); }
+        g.cap_len = len; g.cap_m = m;
+    }
+    int mode = P.mode, sys = P.system;
+    ddm_status st;
+    // operator y(len) = restrict(A(dt) [v; 0]) ; the 3N layout keeps blocks of N
+    auto apply = [&](const double *v, double *out) -> ddm_status {
+        DDM_CUDA_TRY(ctx, cudaMemsetAsync(g.full, 0, 3 * N * sizeof(double), s));
+        DDM_CUDA_TRY(ctx, cudaMemcpyAsync(g.full, v, len * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        ddm_status e = op_apply(ctx, t, 0.0, dt, g.full, g.y3, mode, 0, 1.0);
+        if (e) return e;
+        k_restrict<<<nblk(N), 256, 0, s>>>(g.y3, N, sys, 1, out);
+        return DDM_OK;
+    };
+    auto norm = [&](const double *v, double &out) -> ddm_status {
+        DDM_CUDA_TRY(ctx, cudaMemsetAsync(g.nrm, 0, sizeof(double), s));
+        k_dots<<<dim3(std::min<unsigned>(nblk(len), 1024), 1), RT, 0, s>>>(v, len, 1, v, len, g.nrm);
+        DDM_CUDA_TRY(ctx, cudaMemcpyAsync(&out, g.nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+        DDM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        out = sqrt(out);
+        return DDM_OK;
+    };
+    // preconditioner
+    if ((st = self_blocks(ctx, t, dt))) return st;
+    k_invert<<<nblk(N), 256, 0, s>>>(t->self_blk, N, sys, g.Minv);
+    // b = restrict(rhs) - restrict(A [0; 0; Dq]) for the 2N systems
+    k_restrict<<<nblk(N), 256, 0, s>>>(d_rhs, N, sys, 0, g.b);
+    if (sys != DDM_SYS_PRESSURE) {
+        DDM_CUDA_TRY(ctx, cudaMemsetAsync(g.full, 0, 2 * N * sizeof(double), s));
+        DDM_CUDA_TRY(ctx, cudaMemcpyAsync(g.full + 2 * N, d_x + 2 * N, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        if ((st = op_apply(ctx, t, 0.0, dt, g.full, g.y3, mode, 0, 1.0))) return st;
+        k_restrict<<<nblk(N), 256, 0, s>>>(g.y3, N, sys, 1, g.w);
+        k_axpy<<<nblk(len), 256, 0, s>>>(-1.0, g.w, g.b, len);
+    }
+    double bnorm;
+    if ((st = norm(g.b, bnorm))) return st;
+    if (bnorm == 0) bnorm = 1;
+    int iters = 0, restarts = 0;
+    double rel = 1e300;
+    std::vector<double> H((m + 1) * m), cs(m), sn(m), gv(m + 1), hc(m + 2);
+    bool conv = false;
+    double best = 1e300;
+    int stall = 0;
+    while (iters < P.max_iters) {
+        // r = b - A x
+        if ((st = apply(d_x, g.w))) return st;
+        k_axpy<<<nblk(len), 256, 0, s>>>(-1.0, g.b, g.w, len);          // w = A x - b
+        double beta;
+        if ((st = norm(g.w, beta))) return st;
+        rel = beta / bnorm;
+        if (rel < P.tol) { conv = true; break; }
+        // the true residual of an FP32-accurate operator stops falling at its
+        // rounding floor: stop after three restarts without a 2x decrease
+        if (rel < 0.5 * best) { best = rel; stall = 0; }
+        else if (++stall >= 3) break;
+        // v0 = -w / beta
+        DDM_CUDA_TRY(ctx, cudaMemsetAsync(g.V, 0, len * sizeof(double), s));
+        k_axpy<<<nblk(len), 256, 0, s>>>(-1.0 / beta, g.w, g.V, len);
+        std::fill(gv.begin(), gv.end(), 0.0);
+        gv[0] = beta;
+        int j = 0;
+        for (; j < m && iters < P.max_iters; ++j, ++iters) {
+            double *vj = g.V + (int64_t)j * len;
+            k_precond<<<nblk(N), 256, 0, s>>>(g.Minv, N, nc, vj, g.z);
+            if ((st = apply(g.z, g.w))) return st;
+            prof_end(ctx, 8, 8);      // precond, restrict, 2x(dots, sub), norm, scale
+            // CGS2 against V[0..j]
+            DDM_CUDA_TRY(ctx, cudaMemsetAsync(g.hcol, 0, (m + 2) * sizeof(double), s));
+            for (int pass = 0; pass < 2; ++pass) {
+                DDM_CUDA_TRY(ctx, cudaMemsetAsync(g.h, 0, (m + 2) * sizeof(double), s));
+                k_dots<<<dim3(std::min<unsigned>(nblk(len), 256), j + 1), RT, 0, s>>>(g.V, len, j + 1, g.w, len, g.h);
+                k_sub<<<nblk(len), 256, 0, s>>>(g.V, len, j + 1, g.h, g.w, len, g.hcol);
+            }
+            DDM_CUDA_TRY(ctx, cudaMemsetAsync(g.nrm, 0, sizeof(double), s));
+            k_dots<<<dim3(std::min<unsigned>(nblk(len), 1024), 1), RT, 0, s>>>(g.w, len, 1, g.w, len, g.nrm);
+            k_scale_to<<<nblk(len), 256, 0, s>>>(g.w, len, g.nrm, g.V + (int64_t)(j + 1) * len, g.hcol + j + 1);
+            DDM_CUDA_TRY(ctx, cudaMemcpyAsync(hc.data(), g.hcol, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
+            DDM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+            // Givens rotations on the new column
+            for (int i = 0; i < j; ++i) {
+                double a = cs[i] * hc[i] + sn[i] * hc[i + 1];
+                hc[i + 1] = -sn[i] * hc[i] + cs[i] * hc[i + 1];
+                hc[i] = a;
+            }
+            double r = hypot(hc[j], hc[j + 1]);
+            cs[j] = r > 0 ? hc[j] / r : 1.0;
+            sn[j] = r > 0 ? hc[j + 1] / r : 0.0;
+            hc[j] = r;
+            hc[j + 1] = 0;
+            gv[j + 1] = -sn[j] * gv[j];
+            gv[j] = cs[j] * gv[j];
+            for (int i = 0; i <= j; ++i) H[i * m + j] = hc[i];
+            rel = fabs(gv[j + 1]) / bnorm;
+            if (rel < P.tol || r == 0) { ++j; ++iters; break; }
+        }
+        // least squares: upper triangular solve, x += M^-1 V y
+        std::vector<double> yv(j, 0.0);
+        for (int i = j - 1; i >= 0; --i) {
+            double sum = gv[i];
+            for (int k = i + 1; k < j; ++k) sum -= H[i * m + k] * yv[k];
+            yv[i] = sum / H[i * m + i];
+        }
+        if (j > 0) {
+            DDM_CUDA_TRY(ctx, cudaMemcpyAsync(g.yv, yv.data(), j * sizeof(double), cudaMemcpyHostToDevice, s));
+            k_comb<<<nblk(len), 256, 0, s>>>(g.V, len, j, g.yv, g.w, len);
+            k_precond<<<nblk(N), 256, 0, s>>>(g.Minv, N, nc, g.w, g.z);
+            k_axpy<<<nblk(len), 256, 0, s>>>(1.0, g.z, d_x, len);
+            DDM_CUDA_TRY(ctx, cudaStreamSynchronize(s));    // yv host buffer goes out of scope
+        }
+        ++restarts;
+        if (rel < P.tol) {
+            // confirm with the true residual
+            continue;
+        }
+    }
+    if (info) {
+        info->iterations = iters;
+        info->restarts = restarts;
+        info->rel_residual = rel;
+        info->converged = conv ? 1 : 0;
+    }
+    DDM_CUDA_TRY(ctx, cudaGetLastError());
+    return conv ? DDM_OK : ctx_fail(ctx, DDM_ENOTCONV, "GMRES did not converge");
+}
+
+}  // extern "C"

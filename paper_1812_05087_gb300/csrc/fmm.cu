@@ -1,0 +1,620 @@
+// Influence products of paper Eqs. (2.3)-(2.5) on the GPU.
+//
+//  FMM path (paper Sec. 3, black-box Chebyshev FMM, uniform quadtree):
+//    charges  : gather x (caller order) into sorted per-element DD vectors
+//    self     : each element on its own midpoint, FP64 closed form
+//    P2M      : W_m = sum_j int_elem b_j S_n(ybar_m, y(s)) ds    (leaves)
+//    M2M      : W^parent += S_n(ybar^I, ybar^J) W^J            (upward)
+//    M2L      : g^I = sum_{J in IntList(I)} K(xbar^I, ybar^J) W^J   (levels >= 2)
+//    L2L      : f^child = g^child + S_n(xbar^child, xbar^parent) f^parent
+//    leaf     : L2P + P2P over the neighbour leaves (closed-form element
+//               integrals near, Gauss points of the point kernel far)
+//  Dense path: every (target, source) pair on the fly (conventional PDDM).
+//
+// Charges are 4 components per element: potency density sym(D (x) n) (3)
+// and fluid source q; potentials are global (sxx, syy, sxy, p), rotated to
+// the target element frame at the end.
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "internal.h"
+#include "kernel_math.cuh"
+
+namespace {
+
+constexpr int MAXGL = 16;
+struct GLTab {
+    float xn[MAXGL], wn[MAXGL];   // near rule (fluid source), quad_near points
+    float xf[3], wf[3];           // far rule, 3 points
+    float xc[MAXGL], wc[MAXGL];   // P2M rule, n_cheb points
+    float cheb[DDM_MAX_CHEB], bw[DDM_MAX_CHEB];
+    int nn, nc;
+};
+__constant__ GLTab c_gl;
+
+// Gauss-Legendre nodes/weights on [-1, 1] (Newton on P_n), FP64 on the host.
+void gauss_legendre(int n, double *x, double *w) {
+    for (int i = 0; i < n; ++i) {
+        double z = cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1, p1 = z;
+            for (int k = 2; k <= n; ++k) { double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k; p0 = p1; p1 = p2; }
+            dp = n * (z * p1 - p0) / (z * z - 1);
+            double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-15) break;
+        }
+        x[i] = z;
+        w[i] = 2 / ((1 - z * z) * dp * dp);
+    }
+}
+
+// Chebyshev cardinal functions S_n(xi_a, x) = l_a(x) at the roots of T_n,
+// barycentric form (stable also slightly outside [-1, 1]).
+template <int NMAX>
+__device__ __forceinline__ void cardinal(float x, int n, float *out) {
+    float s = 0.f;
+    int hit = -1;
+    for (int j = 0; j < n; ++j) {
+        float d = x - c_gl.cheb[j];
+        if (fabsf(d) < 1e-7f) hit = j;
+        float v = c_gl.bw[j] / d;
+        out[j] = v;
+        s += v;
+    }
+    if (hit >= 0) {
+        for (int j = 0; j < n; ++j) out[j] = (j == hit) ? 1.f : 0.f;
+        return;
+    }
+    float is = 1.f / s;
+    for (int j = 0; j < n; ++j) out[j] *= is;
+}
+
+// ----------------------------------------------------------------- charges
+__global__ void k_charges(const double *x, const int64_t *perm, const float4 *frame, int64_t n, float4 *chg) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t e = perm[i];
+    float4 f = frame[i];
+    float Ds = (float)x[e], Dn = (float)x[n + e], Dq = (float)x[2 * n + e];
+    // D = Ds t + Dn n, n = (-ty, tx)
+    chg[i] = make_float4(Ds * f.x - Dn * f.y, Ds * f.y + Dn * f.x, Dq, 0.f);
+}
+
+// --------------------------------------------------------- own element (FP64)
+__device__ void self_field(const KConst<double> &k, const Win<double> &w, double a, double tx, double ty,
+                           double Ds, double Dn, double Dq, double out[3]) {
+    double nx = -ty, ny = tx;
+    double Dx = Ds * tx + Dn * nx, Dy = Ds * ty + Dn * ny;
+    double g[4] = {0, 0, 0, 0};
+    disl_field<double>(k, a * tx, a * ty, Dx, Dy, w, 1.0, g);      // target - start = a t
+    disl_field<double>(k, -a * tx, -a * ty, Dx, Dy, w, -1.0, g);   // target - end   = -a t
+    double ss, sn;
+    to_local<double>(tx, ty, g, ss, sn);
+    double p = g[3];
+    // fluid source on its own element: closed forms along the line,
+    // int E1(s^2/4ct) ds and int F(s^2/4ct) ds over [-a, a]
+    if (Dq != 0.0) {
+        for (int side = 0; side < 2; ++side) {
+            double ct = side == 0 ? w.ct_hi : w.ct_lo;
+            if (ct <= 0.0) continue;
+            double sg = side == 0 ? 1.0 : -1.0;
+            double s4 = sqrt(4.0 * ct), A = a / s4;
+            double sp = 1.7724538509055160273 * erf(A);
+            double IE1 = 2.0 * s4 * (A * e1<double>(A * A) + sp);
+            double IF = 2.0 * s4 * (sp - (-expm1(-A * A)) / A);
+            sn += sg * (-k.eta * k.i4pk * Dq * (IE1 - IF));
+            p += sg * k.i4pk * Dq * IE1;
+        }
+    }
+    out[0] = ss; out[1] = sn; out[2] = p;
+}
+
+__global__ void k_self(KConst<double> k, Win<double> w, const double *x, const double *xy, int64_t n, double scale,
+                       int overwrite, double *y) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    double dx = xy[2 * n + e] - xy[e], dy = xy[3 * n + e] - xy[n + e];
+    double L = hypot(dx, dy);
+    double o[3];
+    self_field(k, w, 0.5 * L, dx / L, dy / L, x[e], x[n + e], x[2 * n + e], o);
+    for (int r = 0; r < 3; ++r) {
+        double v = scale * o[r];
+        if (overwrite) y[r * n + e] = v; else y[r * n + e] += v;
+    }
+}
+
+// own 3x3 blocks (rows sigma_s, sigma_n, p; columns Ds, Dn, Dq), caller order
+__global__ void k_self_blocks(KConst<double> k, Win<double> w, const double *xy, int64_t n, double *blk) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    double dx = xy[2 * n + e] - xy[e], dy = xy[3 * n + e] - xy[n + e];
+    double L = hypot(dx, dy);
+    for (int c = 0; c < 3; ++c) {
+        double o[3];
+        self_field(k, w, 0.5 * L, dx / L, dy / L, c == 0, c == 1, c == 2, o);
+        for (int r = 0; r < 3; ++r) blk[9 * e + 3 * r + c] = o[r];
+    }
+}
+
+// ---------------------------------------------------------------------- P2M
+constexpr int P2M_T = 128;
+__global__ void __launch_bounds__(P2M_T) k_p2m(const int32_t *cstart, const int32_t *cend, int64_t loff,
+                                               const float4 *grel, const float4 *frame, const float4 *chg,
+                                               float hL, int n, float *W) {
+    __shared__ float sx[P2M_T][DDM_MAX_CHEB], sy[P2M_T][DDM_MAX_CHEB], wd[P2M_T][4];
+    int64_t cell = loff + blockIdx.x;
+    int s0 = cstart[cell], s1 = cend[cell];
+    int nq = c_gl.nc, n2 = n * n;
+    int npts = (s1 - s0) * nq;
+    float acc[8];
+    for (int k = 0; k < 8; ++k) acc[k] = 0.f;
+    float ih = 1.f / hL;
+    for (int base = 0; base < npts; base += P2M_T) {
+        int p = base + threadIdx.x;
+        if (p < npts) {
+            int e = s0 + p / nq, g = p % nq;
+            float4 r = grel[e], f = frame[e], c = chg[e];
+            float xi = c_gl.xc[g];
+            float px = 0.5f * (r.x + r.z) + xi * f.z * f.x, py = 0.5f * (r.y + r.w) + xi * f.z * f.y;
+            cardinal<DDM_MAX_CHEB>(px * ih, n, sx[threadIdx.x]);
+            cardinal<DDM_MAX_CHEB>(py * ih, n, sy[threadIdx.x]);
+            float wt = c_gl.wc[g] * f.z;           // ds = a dxi
+            float nx = -f.y, ny = f.x;
+            wd[threadIdx.x][0] = wt * c.x * nx;
+            wd[threadIdx.x][1] = wt * c.y * ny;
+            wd[threadIdx.x][2] = wt * 0.5f * (c.x * ny + c.y * nx);
+            wd[threadIdx.x][3] = wt * c.z;
+        }
+        __syncthreads();
+        int cnt = min(P2M_T, npts - base);
+        for (int ent = threadIdx.x, slot = 0; ent < n2 && slot < 2; ent += P2M_T, ++slot) {
+            int a = ent / n, b = ent % n;
+            float s0_ = 0, s1_ = 0, s2_ = 0, s3_ = 0;
+            for (int q = 0; q < cnt; ++q) {
+                float v = sx[q][a] * sy[q][b];
+                s0_ += v * wd[q][0]; s1_ += v * wd[q][1]; s2_ += v * wd[q][2]; s3_ += v * wd[q][3];
+            }
+            acc[4 * slot] += s0_; acc[4 * slot + 1] += s1_; acc[4 * slot + 2] += s2_; acc[4 * slot + 3] += s3_;
+        }
+        __syncthreads();
+    }
+    float *Wc = W + cell * 4 * n2;
+    for (int ent = threadIdx.x, slot = 0; ent < n2 && slot < 2; ent += P2M_T, ++slot)
+        for (int c = 0; c < 4; ++c) Wc[c * n2 + ent] = acc[4 * slot + c];
+}
+
+// ---------------------------------------------------------------------- M2M
+// one block per child cell; adds S_n(ybar^parent, ybar^child) W^child to the parent
+__global__ void k_m2m(int64_t off, const int32_t *cix, const int32_t *ciy, const int32_t *parent,
+                      const float *T, int n, float *W) {
+    extern __shared__ float sm[];
+    float *wc = sm, *tmp = sm + 4 * n * n;
+    int64_t cell = off + blockIdx.x;
+    int n2 = n * n;
+    const float *Wc = W + cell * 4 * n2;
+    for (int i = threadIdx.x; i < 4 * n2; i += blockDim.x) wc[i] = Wc[i];
+    __syncthreads();
+    const float *Tx = T + ((cix[cell] & 1) ? n2 : 0), *Ty = T + ((ciy[cell] & 1) ? n2 : 0);
+    // tmp[c][a][b'] = sum_a' Tx[a][a'] wc[c][a'][b']
+    for (int i = threadIdx.x; i < 4 * n2; i += blockDim.x) {
+        int c = i / n2, a = (i / n) % n, b = i % n;
+        float s = 0;
+        for (int ap = 0; ap < n; ++ap) s += Tx[a * n + ap] * wc[c * n2 + ap * n + b];
+        tmp[i] = s;
+    }
+    __syncthreads();
+    float *Wp = W + (int64_t)parent[cell] * 4 * n2;
+    for (int i = threadIdx.x; i < 4 * n2; i += blockDim.x) {
+        int c = i / n2, a = (i / n) % n, b = i % n;
+        float s = 0;
+        for (int bp = 0; bp < n; ++bp) s += Ty[b * n + bp] * tmp[c * n2 + a * n + bp];
+        atomicAdd(&Wp[i], s);
+    }
+}
+
+// ---------------------------------------------------------------------- L2L
+// one block per child cell: f^child += S_n(xbar^child in parent) f^parent
+__global__ void k_l2l(int64_t off, const int32_t *cix, const int32_t *ciy, const int32_t *parent,
+                      const float *T, int n, float *F) {
+    extern __shared__ float sm[];
+    float *fp = sm, *tmp = sm + 4 * n * n;
+    int64_t cell = off + blockIdx.x;
+    int n2 = n * n;
+    const float *Fp = F + (int64_t)parent[cell] * 4 * n2;
+    for (int i = threadIdx.x; i < 4 * n2; i += blockDim.x) fp[i] = Fp[i];
+    __syncthreads();
+    const float *Tx = T + ((cix[cell] & 1) ? n2 : 0), *Ty = T + ((ciy[cell] & 1) ? n2 : 0);
+    // child node a' takes sum_a T[a][a'] (transpose of M2M)
+    for (int i = threadIdx.x; i < 4 * n2; i += blockDim.x) {
+        int c = i / n2, ap = (i / n) % n, b = i % n;
+        float s = 0;
+        for (int a = 0; a < n; ++a) s += Tx[a * n + ap] * fp[c * n2 + a * n + b];
+        tmp[i] = s;
+    }
+    __syncthreads();
+    float *Fc = F + cell * 4 * n2;
+    for (int i = threadIdx.x; i < 4 * n2; i += blockDim.x) {
+        int c = i / n2, ap = (i / n) % n, bp = i % n;
+        float s = 0;
+        for (int b = 0; b < n; ++b) s += Ty[b * n + bp] * tmp[c * n2 + ap * n + b];
+        Fc[i] += s;
+    }
+}
+
+// ---------------------------------------------------------------------- M2L
+// one block per target cell (levels >= 2), one thread per target node.
+struct LevelTab {
+    int64_t off[DDM_MAX_LEVELS + 2];
+    int L;
+};
+__global__ void k_m2l(KConst<float> k, Win<float> w, LevelTab lt, int64_t first, const int32_t *iloff,
+                      const int32_t *ilidx, const int32_t *cix, const int32_t *ciy, double h0, int n,
+                      const float *W, float *F) {
+    extern __shared__ float sw[];      // 4 n^2 source weights
+    int64_t cell = first + blockIdx.x;
+    int lvl = 0;
+    while (lvl < lt.L && cell >= lt.off[lvl + 1]) ++lvl;
+    int n2 = n * n;
+    float h = (float)(h0 / (double)(1 << lvl)), wl = 2.f * h;
+    int m = threadIdx.x;
+    int a = m / n, b = m % n;
+    float xa = (m < n2) ? h * c_gl.cheb[a] : 0.f, yb = (m < n2) ? h * c_gl.cheb[b] : 0.f;
+    float acc[4] = {0, 0, 0, 0};
+    int ixI = cix[cell], iyI = ciy[cell];
+    for (int q = iloff[cell]; q < iloff[cell + 1]; ++q) {
+        int32_t J = ilidx[q];
+        const float *WJ = W + (int64_t)J * 4 * n2;
+        __syncthreads();
+        for (int i = threadIdx.x; i < 4 * n2; i += blockDim.x) sw[i] = WJ[i];
+        __syncthreads();
+        if (m < n2) {
+            float ox = wl * (float)(ixI - cix[J]) + xa, oy = wl * (float)(iyI - ciy[J]) + yb;
+            for (int ap = 0; ap < n; ++ap) {
+                float zx = ox - h * c_gl.cheb[ap];
+                for (int bp = 0; bp < n; ++bp) {
+                    int mp = ap * n + bp;
+                    float zy = oy - h * c_gl.cheb[bp];
+                    pot_kernel<float>(k, zx, zy, sw[mp], sw[n2 + mp], sw[2 * n2 + mp], sw[3 * n2 + mp], w, acc);
+                }
+            }
+        }
+    }
+    if (m < n2) {
+        float *Fc = F + cell * 4 * n2;
+        for (int c = 0; c < 4; ++c) Fc[c * n2 + m] = acc[c];
+    }
+}
+
+// ----------------------------------------------------------- leaf L2P + P2P
+struct SrcTile {
+    float x0, y0, x1, y1;      // end points in the target leaf frame
+    float Dx, Dy, q, a;        // DD vector, source strength, half-length
+    float tx, ty;              // tangent
+    int idx;                   // sorted index
+};
+
+__device__ __forceinline__ void q_point(const KConst<float> &k, float zx, float zy, float q, const Win<float> &w,
+                                        float acc[4]) {
+    for (int side = 0; side < 2; ++side) {
+        float ct = side == 0 ? w.ct_hi : w.ct_lo;
+        if (ct <= 0.f) continue;
+        float s = side == 0 ? 1.f : -1.f;
+        float x2 = zx * zx, y2 = zy * zy, r2 = x2 + y2;
+        float u = r2 / (4.f * ct);
+        float e, F0, F1, F2;
+        f_funcs<float>(u, e, F0, F1, F2);
+        float E1 = e1<float>(u);
+        float pre = s * q * k.i4pk, nn = 2.f * F0 / r2;
+        acc[0] -= pre * k.eta * (nn * x2 + E1 - F0);
+        acc[1] -= pre * k.eta * (nn * y2 + E1 - F0);
+        acc[2] -= pre * k.eta * (nn * zx * zy);
+        acc[3] += pre * E1;
+    }
+}
+
+// near/far element integral of one source element at target m (target
+// frame coordinates); self pairs are excluded by the caller
+__device__ __forceinline__ void pair_field(const KConst<float> &k, const Win<float> &w, float mx, float my,
+                                           const SrcTile &s, float acc[4]) {
+    float cxs = 0.5f * (s.x0 + s.x1), cys = 0.5f * (s.y0 + s.y1);
+    float dx = mx - cxs, dy = my - cys;
+    float r2 = dx * dx + dy * dy;
+    if (r2 > 64.f * s.a * s.a) {
+        // far: 3-point Gauss rule of the point kernel
+        float nx = -s.ty, ny = s.tx;
+        float Pxx = s.Dx * nx, Pyy = s.Dy * ny, Pxy = 0.5f * (s.Dx * ny + s.Dy * nx);
+#pragma unroll
+        for (int g = 0; g < 3; ++g) {
+            float sg = c_gl.xf[g] * s.a, wt = c_gl.wf[g] * s.a;
+            pot_kernel<float>(k, dx - sg * s.tx, dy - sg * s.ty, wt * Pxx, wt * Pyy, wt * Pxy, wt * s.q, w, acc);
+        }
+    } else {
+        disl_field<float>(k, mx - s.x0, my - s.y0, s.Dx, s.Dy, w, 1.f, acc);
+        disl_field<float>(k, mx - s.x1, my - s.y1, s.Dx, s.Dy, w, -1.f, acc);
+        if (s.q != 0.f) {
+            for (int g = 0; g < c_gl.nn; ++g) {
+                float sg = c_gl.xn[g] * s.a, wt = c_gl.wn[g] * s.a;
+                q_point(k, dx - sg * s.tx, dy - sg * s.ty, wt * s.q, w, acc);
+            }
+        }
+    }
+}
+
+constexpr int LEAF_T = 32;
+__global__ void __launch_bounds__(LEAF_T) k_leaf(KConst<float> k, Win<float> w, int64_t loff, const int32_t *cstart,
+                                                 const int32_t *cend, const int32_t *cix, const int32_t *ciy,
+                                                 const int32_t *nboff, const int32_t *nbidx, const float4 *grel,
+                                                 const float4 *frame, const float4 *chg, const int64_t *perm,
+                                                 float wL, int n, const float *F, int use_far, int64_t N,
+                                                 double scale, double *y) {
+    __shared__ SrcTile tile[LEAF_T];
+    __shared__ float sf[4 * DDM_MAX_CHEB * DDM_MAX_CHEB];
+    int leaf = blockIdx.x;
+    int64_t cell = loff + leaf;
+    int t0 = cstart[cell], t1 = cend[cell];
+    int n2 = n * n;
+    if (use_far)
+        for (int i = threadIdx.x; i < 4 * n2; i += LEAF_T) sf[i] = F[cell * 4 * n2 + i];
+    int ixI = cix[cell], iyI = ciy[cell];
+    float hL = 0.5f * wL;
+    for (int tb = t0; tb < t1; tb += LEAF_T) {
+        int ti = tb + threadIdx.x;
+        bool act = ti < t1;
+        float mx = 0, my = 0, ttx = 1, tty = 0;
+        if (act) {
+            float4 r = grel[ti], f = frame[ti];
+            mx = 0.5f * (r.x + r.z); my = 0.5f * (r.y + r.w);
+            ttx = f.x; tty = f.y;
+        }
+        double accd[4] = {0, 0, 0, 0};
+        for (int q = nboff[leaf]; q < nboff[leaf + 1]; ++q) {
+            int64_t J = loff + nbidx[q];
+            float ox = wL * (float)(cix[J] - ixI), oy = wL * (float)(ciy[J] - iyI);
+            int s0 = cstart[J], s1 = cend[J];
+            for (int sb = s0; sb < s1; sb += LEAF_T) {
+                __syncthreads();
+                int sj = sb + threadIdx.x;
+                if (sj < s1) {
+                    float4 r = grel[sj], f = frame[sj], c = chg[sj];
+                    SrcTile s;
+                    s.x0 = r.x + ox; s.y0 = r.y + oy; s.x1 = r.z + ox; s.y1 = r.w + oy;
+                    s.Dx = c.x; s.Dy = c.y; s.q = c.z; s.a = f.z; s.tx = f.x; s.ty = f.y; s.idx = sj;
+                    tile[threadIdx.x] = s;
+                }
+                __syncthreads();
+                int cnt = min(LEAF_T, s1 - sb);
+                if (act) {
+                    float acc[4] = {0, 0, 0, 0};      // one tile in FP32, tiles summed in FP64
+                    for (int j = 0; j < cnt; ++j) {
+                        if (tile[j].idx == ti) continue;
+                        pair_field(k, w, mx, my, tile[j], acc);
+                    }
+                    for (int c = 0; c < 4; ++c) accd[c] += (double)acc[c];
+                }
+            }
+        }
+        float acc[4] = {0, 0, 0, 0};
+        if (act && use_far) {
+            float cx_[DDM_MAX_CHEB], cy_[DDM_MAX_CHEB];
+            cardinal<DDM_MAX_CHEB>(mx / hL, n, cx_);
+            cardinal<DDM_MAX_CHEB>(my / hL, n, cy_);
+            for (int a = 0; a < n; ++a)
+                for (int b = 0; b < n; ++b) {
+                    float v = cx_[a] * cy_[b];
+                    int m = a * n + b;
+                    acc[0] += v * sf[m]; acc[1] += v * sf[n2 + m]; acc[2] += v * sf[2 * n2 + m]; acc[3] += v * sf[3 * n2 + m];
+                }
+        }
+        if (act) {
+            double g[4], ss, sn;
+            for (int c = 0; c < 4; ++c) g[c] = accd[c] + (double)acc[c];
+            to_local<double>((double)ttx, (double)tty, g, ss, sn);
+            int64_t e = perm[ti];
+            y[e] += scale * ss;
+            y[N + e] += scale * sn;
+            y[2 * N + e] += scale * g[3];
+        }
+    }
+}
+
+// -------------------------------------------------------------------- dense
+constexpr int DN_T = 128;
+__global__ void __launch_bounds__(DN_T) k_dense(KConst<float> k, Win<float> w, int64_t loff, const int32_t *elem_leaf,
+                                                const int32_t *cix, const int32_t *ciy, const float4 *grel,
+                                                const float4 *frame, const float4 *chg, const int64_t *perm,
+                                                float wL, int64_t N, int64_t chunk, double scale, double *y) {
+    __shared__ SrcTile tile[DN_T];
+    __shared__ int sjx[DN_T], sjy[DN_T];
+    int64_t ti = blockIdx.x * (int64_t)DN_T + threadIdx.x;
+    bool act = ti < N;
+    float mx = 0, my = 0, ttx = 1, tty = 0;
+    int ixI = 0, iyI = 0;
+    if (act) {
+        float4 r = grel[ti], f = frame[ti];
+        mx = 0.5f * (r.x + r.z); my = 0.5f * (r.y + r.w);
+        ttx = f.x; tty = f.y;
+        int32_t c = elem_leaf[ti];
+        ixI = cix[loff + c]; iyI = ciy[loff + c];
+    }
+    double accd[4] = {0, 0, 0, 0};
+    int64_t s0 = blockIdx.y * chunk;
+    int64_t s1 = s0 + chunk < N ? s0 + chunk : N;
+    for (int64_t sb = s0; sb < s1; sb += DN_T) {
+        __syncthreads();
+        int64_t sj = sb + threadIdx.x;
+        if (sj < s1) {
+            float4 r = grel[sj], f = frame[sj], c = chg[sj];
+            SrcTile s;
+            s.x0 = r.x; s.y0 = r.y; s.x1 = r.z; s.y1 = r.w;
+            s.Dx = c.x; s.Dy = c.y; s.q = c.z; s.a = f.z; s.tx = f.x; s.ty = f.y; s.idx = (int)sj;
+            tile[threadIdx.x] = s;
+            int32_t cl = elem_leaf[sj];
+            sjx[threadIdx.x] = cix[loff + cl];
+            sjy[threadIdx.x] = ciy[loff + cl];
+        }
+        __syncthreads();
+        int cnt = (int)(s1 - sb < DN_T ? s1 - sb : DN_T);
+        if (act) {
+            float acc[4] = {0, 0, 0, 0};          // one tile in FP32, tiles summed in FP64
+            for (int j = 0; j < cnt; ++j) {
+                if (tile[j].idx == (int)ti) continue;
+                SrcTile s = tile[j];
+                float ox = wL * (float)(sjx[j] - ixI), oy = wL * (float)(sjy[j] - iyI);
+                s.x0 += ox; s.y0 += oy; s.x1 += ox; s.y1 += oy;
+                pair_field(k, w, mx, my, s, acc);
+            }
+            for (int c = 0; c < 4; ++c) accd[c] += (double)acc[c];
+        }
+    }
+    if (act) {
+        double ss, sn;
+        to_local<double>((double)ttx, (double)tty, accd, ss, sn);
+        int64_t e = perm[ti];
+        atomicAdd(&y[e], scale * ss);
+        atomicAdd(&y[N + e], scale * sn);
+        atomicAdd(&y[2 * N + e], scale * accd[3]);
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------- host
+static ddm_status upload_tables(ddm_ctx *ctx) {
+    static thread_local int last_n = -1, last_q = -1, last_dev = -1;
+    int n = ctx->prm.n_cheb, nq = ctx->prm.quad_near;
+    if (n == last_n && nq == last_q && ctx->device == last_dev) return DDM_OK;
+    GLTab h;
+    memset(&h, 0, sizeof(h));
+    double x[MAXGL], wt[MAXGL];
+    gauss_legendre(nq, x, wt);
+    for (int i = 0; i < nq; ++i) { h.xn[i] = (float)x[i]; h.wn[i] = (float)wt[i]; }
+    h.nn = nq;
+    gauss_legendre(3, x, wt);
+    for (int i = 0; i < 3; ++i) { h.xf[i] = (float)x[i]; h.wf[i] = (float)wt[i]; }
+    gauss_legendre(n, x, wt);
+    for (int i = 0; i < n; ++i) { h.xc[i] = (float)x[i]; h.wc[i] = (float)wt[i]; }
+    h.nc = n;
+    for (int j = 0; j < n; ++j) {
+        double th = (2 * j + 1) * M_PI / (2.0 * n);
+        h.cheb[j] = (float)cos(th);
+        h.bw[j] = (float)(((j & 1) ? -1.0 : 1.0) * sin(th));
+    }
+    DDM_CUDA_TRY(ctx, cudaMemcpyToSymbolAsync(c_gl, &h, sizeof(h), 0, cudaMemcpyHostToDevice, ctx->stream));
+    last_n = n; last_q = nq; last_dev = ctx->device;
+    return DDM_OK;
+}
+
+ddm_status ensure_workspace(ddm_ctx *ctx, ddm_tree *t) {
+    int n = ctx->prm.n_cheb;
+    if (t->ncheb_alloc == n && t->W) return DDM_OK;
+    if (t->W) cudaFree(t->W);
+    if (t->Fl) cudaFree(t->Fl);
+    t->W = t->Fl = nullptr;
+    size_t sz = (size_t)t->n_cells * 4 * n * n * sizeof(float);
+    if (cudaMalloc(&t->W, sz) != cudaSuccess || cudaMalloc(&t->Fl, sz) != cudaSuccess)
+        return ctx_fail(ctx, DDM_ENOMEM, "FMM workspace allocation failed");
+    t->ncheb_alloc = n;
+    return DDM_OK;
+}
+
+template <class T>
+static Win<T> make_win(const ddm_ctx *ctx, double lo, double hi) {
+    Win<T> w;
+    double c = ctx->kd.c;
+    w.ct_hi = (T)(c * hi);
+    w.ct_lo = (T)(lo > 0.0 ? c * lo : 0.0);
+    w.elastic = lo > 0.0 ? 0 : 1;
+    return w;
+}
+
+ddm_status self_blocks(ddm_ctx *ctx, ddm_tree *t, double dt) {
+    if (t->self_dt == dt) return DDM_OK;
+    int64_t n = t->n;
+    k_self_blocks<<<(n + 255) / 256, 256, 0, ctx->stream>>>(ctx->kd, make_win<double>(ctx, 0.0, dt), t->xy_caller, n,
+                                                            t->self_blk);
+    DDM_CUDA_TRY(ctx, cudaGetLastError());
+    t->self_dt = dt;
+    return DDM_OK;
+}
+
+ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const double *x, double *y, int mode,
+                    int accumulate, double scale) {
+    if (!(hi > lo) || lo < 0.0) return ctx_fail(ctx, DDM_EINVAL, "matvec: need 0 <= tau_lo < tau_hi");
+    ddm_status st = upload_tables(ctx);
+    if (st) return st;
+    st = ensure_workspace(ctx, t);
+    if (st) return st;
+    cudaStream_t s = ctx->stream;
+    int64_t N = t->n;
+    int n = ctx->prm.n_cheb, n2 = n * n;
+    const int TB = 256;
+    KConst<float> kf = ctx->kf;
+    Win<float> wf = make_win<float>(ctx, lo, hi);
+    Win<double> wd = make_win<double>(ctx, lo, hi);
+    prof_begin(ctx, 0);
+    k_charges<<<(N + TB - 1) / TB, TB, 0, s>>>(x, t->perm, t->g_frame, N, t->chg);
+    prof_end(ctx, 0, 1);
+    // own elements (FP64 closed form), caller order
+    prof_begin(ctx, 1);
+    k_self<<<(N + TB - 1) / TB, TB, 0, s>>>(ctx->kd, wd, x, t->xy_caller, N, scale, accumulate ? 0 : 1, y);
+    prof_end(ctx, 1, 1);
+    int L = t->depth;
+    int64_t loff = t->lvl_off[L], nleaf = t->lvl_off[L + 1] - loff;
+    float wL = (float)(2.0 * t->h0 / (double)(1 << L));
+    if (mode == DDM_MODE_DENSE) {
+        int64_t tiles = (N + DN_T - 1) / DN_T;
+        int64_t chunks = std::max<int64_t>(1, std::min<int64_t>((4 * 152 + tiles - 1) / tiles, (N + DN_T - 1) / DN_T));
+        int64_t chunk = ((N + chunks - 1) / chunks + DN_T - 1) / DN_T * DN_T;
+        chunks = (N + chunk - 1) / chunk;
+        prof_begin(ctx, 7);
+        k_dense<<<dim3((unsigned)tiles, (unsigned)chunks), DN_T, 0, s>>>(kf, wf, loff, t->elem_leaf, t->cell_ix, t->cell_iy,
+                                                                        t->g_rel, t->g_frame, t->chg, t->perm, wL, N,
+                                                                        chunk, scale, y);
+        prof_end(ctx, 7, 1);
+        DDM_CUDA_TRY(ctx, cudaGetLastError());
+        return DDM_OK;
+    }
+    int use_far = L >= 2;
+    if (use_far) {
+        float hL = 0.5f * wL;
+        // upward pass
+        DDM_CUDA_TRY(ctx, cudaMemsetAsync(t->W, 0, (size_t)t->n_cells * 4 * n2 * sizeof(float), s));
+        prof_begin(ctx, 2);
+        k_p2m<<<(unsigned)nleaf, P2M_T, 0, s>>>(t->cell_start, t->cell_end, loff, t->g_rel, t->g_frame, t->chg, hL, n,
+                                                t->W);
+        prof_end(ctx, 2, 1);
+        size_t sm2 = 8 * n2 * sizeof(float);
+        prof_begin(ctx, 3);
+        for (int l = L; l >= 3; --l) {
+            int64_t off = t->lvl_off[l], nc = t->lvl_off[l + 1] - off;
+            k_m2m<<<(unsigned)nc, 128, sm2, s>>>(off, t->cell_ix, t->cell_iy, t->cell_parent, ctx->cheb_T, n, t->W);
+        }
+        prof_end(ctx, 3, L - 2);
+        // M2L on every level >= 2 in one launch
+        LevelTab lt;
+        for (int l = 0; l <= L + 1 && l < DDM_MAX_LEVELS + 2; ++l) lt.off[l] = t->lvl_off[l];
+        lt.L = L;
+        int64_t first = t->lvl_off[2], ncm = t->lvl_off[L + 1] - first;
+        int thr = ((n2 + 31) / 32) * 32;
+        prof_begin(ctx, 4);
+        k_m2l<<<(unsigned)ncm, thr, 4 * n2 * sizeof(float), s>>>(kf, wf, lt, first, t->il_off, t->il_idx, t->cell_ix,
+                                                                t->cell_iy, t->h0, n, t->W, t->Fl);
+        prof_end(ctx, 4, 1);
+        // downward pass
+        prof_begin(ctx, 5);
+        for (int l = 3; l <= L; ++l) {
+            int64_t off = t->lvl_off[l], nc = t->lvl_off[l + 1] - off;
+            k_l2l<<<(unsigned)nc, 128, sm2, s>>>(off, t->cell_ix, t->cell_iy, t->cell_parent, ctx->cheb_T, n, t->Fl);
+        }
+        prof_end(ctx, 5, L - 2);
+    }
+    prof_begin(ctx, 6);
+    k_leaf<<<(unsigned)nleaf, LEAF_T, 0, s>>>(kf, wf, loff, t->cell_start, t->cell_end, t->cell_ix, t->cell_iy, t->nb_off,
+                                             t->nb_idx, t->g_rel, t->g_frame, t->chg, t->perm, wL, n, t->Fl, use_far, N,
+                                             scale, y);
+    prof_end(ctx, 6, 1);
+    DDM_CUDA_TRY(ctx, cudaGetLastError());
+    return DDM_OK;
+}

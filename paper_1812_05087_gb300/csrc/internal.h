@@ -1,0 +1,118 @@
+// Internal structures shared by the translation units of the library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/ddm.h"
+
+#define DDM_MAX_CHEB 16
+#define DDM_MAX_LEVELS 18
+
+// Kernel constants derived from the material (Biot / Rice-Cleary plane
+// strain), in the precision T of the arithmetic that uses them.
+template <class T>
+struct KConst {
+    T G2;      // 2G
+    T Cel;     // G / (2 pi (1 - nu))           drained elastic DD prefactor
+    T Ce;      // (1 - 2 nu) / (2 pi (1 - nu))   drained dilatation prefactor
+    T K2;      // kpsi * Ce / 4                   displacement-potential prefactor
+    T aS;      // alpha / S                        undrained pore-pressure coefficient
+    T eta;     // poroelastic stress coefficient alpha (1 - 2nu) / (2 (1 - nu))
+    T i4pk;    // 1 / (4 pi kappa)                 line-source pressure prefactor
+    T c;       // hydraulic diffusivity kappa / S
+};
+
+// Time window of one product: [K(tau_hi) - K(tau_lo)], K(0) = 0.
+// ct_* = c * tau_*; elastic = 1 when tau_lo == 0 (the drained elastic part
+// cancels between two positive times).
+template <class T>
+struct Win {
+    T ct_hi, ct_lo;
+    int elastic;
+};
+
+struct ddm_tree {
+    int64_t n;                 // elements
+    int depth;                 // leaf level L
+    double cx, cy, h0;         // root square centre and half-width
+    // per level l = 0..L: non-empty cells [lvl_off[l], lvl_off[l+1])
+    std::vector<int64_t> lvl_off;
+    int64_t n_cells;
+    // device arrays
+    int64_t *perm;             // sorted position -> caller element index
+    uint32_t *cell_key;        // Morton key of each cell at its level (cells sorted by level, key)
+    int32_t *cell_ix, *cell_iy;// integer cell coordinates at the cell's level
+    int32_t *cell_start, *cell_end;   // sorted element range
+    int32_t *cell_parent;      // global cell index of the parent (-1 at level 0)
+    int32_t *il_off, *il_idx;  // interaction lists (CSR over cells)
+    int32_t *nb_off, *nb_idx;  // neighbour lists of leaves incl. self (CSR over leaves, leaf-local)
+    int32_t *elem_leaf;        // sorted element -> leaf index (leaf-local)
+    // sorted element geometry, FP32 relative to the element's leaf centre
+    float4 *g_rel;             // (x0, y0, x1, y1) rel. to leaf centre
+    float4 *g_frame;           // (tx, ty, half-length, 0)
+    double *xy_sorted;         // 4 x n FP64 absolute end points (sorted order)
+    double *xy_caller;         // 4 x n FP64 end points, caller order (copy of the input)
+    double *self_blk;          // 9 x n FP64 own-element blocks at the last dt (cache)
+    double self_dt;            // dt of the cached self blocks (<0: none)
+    int64_t n_m2l, n_p2p;
+    // per-tree workspaces
+    float *W;                  // multipole weights, 4 n^2 per cell
+    float *Fl;                 // local expansions, 4 n^2 per cell
+    float4 *chg;               // sorted charges (Dx, Dy, q, 0) per element
+    int ncheb_alloc;
+};
+
+struct GmresWork;
+
+// Optional stage timing (CUDA events on the context stream) and launch
+// counting.  Stages: 0 charges, 1 self, 2 p2m, 3 m2m, 4 m2l, 5 l2l, 6 leaf,
+// 7 dense, 8 krylov vector kernels, 9 tree build.
+#define DDM_NSTAGES 10
+struct Prof {
+    int on = 0;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
+    long long launches[DDM_NSTAGES] = {0};
+    int open_stage = -1;
+    cudaEvent_t open_ev = nullptr;
+};
+
+struct ddm_ctx {
+    int device;
+    cudaStream_t stream;
+    ddm_material mat;
+    ddm_fmm_params prm;
+    KConst<float> kf;
+    KConst<double> kd;
+    std::string err;
+    // Chebyshev tables (device): nodes, M2M/L2L transfer matrices T[q][a][a']
+    float *cheb_nodes;         // n
+    float *cheb_bw;            // barycentric weights, n
+    float *cheb_T;             // 2 x n x n
+    GmresWork *gm;
+    Prof prof;
+};
+
+// begin/end a profiled stage (no-ops unless profiling is on); count launches
+void prof_begin(ddm_ctx *ctx, int stage);
+void prof_end(ddm_ctx *ctx, int stage, int launches);
+
+// error helpers
+ddm_status ctx_fail(ddm_ctx *ctx, ddm_status st, const std::string &msg);
+#define DDM_CUDA_TRY(ctx, call)                                                        \
+    do {                                                                               \
+        cudaError_t _e = (call);                                                       \
+        if (_e != cudaSuccess)                                                         \
+            return ctx_fail(ctx, DDM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(_e)); \
+    } while (0)
+
+// tree.cu
+ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **out);
+void tree_free(ddm_tree *t);
+
+// fmm.cu: y = [K(hi) - K(lo)] x  (caller order), accumulate: y += s * (...)
+ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double tau_lo, double tau_hi, const double *d_x,
+                    double *d_y, int mode, int accumulate, double scale);
+ddm_status self_blocks(ddm_ctx *ctx, ddm_tree *t, double dt);   // fills t->self_blk (caller order)
+ddm_status ensure_workspace(ddm_ctx *ctx, ddm_tree *t);

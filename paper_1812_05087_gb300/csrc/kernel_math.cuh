@@ -1,0 +1,229 @@
+// Device arithmetic of the poroelastic displacement discontinuity kernels
+// (influence coefficients of paper Eqs. 2.3-2.5), GB300 path.
+//
+// Everything is written in the global (x, y) frame for a source placed at
+// the origin and a target at z = (x, y):
+//
+//  * pot_kernel: point source given by its potency (Pxx, Pyy, Pxy) = ds *
+//    sym(D (x) n) of a DD vector D across normal n, plus a fluid source q ds.
+//    Used for the far field (M2L between Chebyshev nodes, Gauss points of
+//    distant elements).  Terms:
+//      - drained elastic stress, a homogeneous degree -2 rational function,
+//      - poroelastic transient: stress 2G(grad grad psi - I lap psi) of the
+//        potential psi = K2 [a(z) g(r^2) + tr(P) Ein(u)], u = r^2/(4 c t),
+//        a(z) = (Pyy - Pxx)(x^2 - y^2) - 4 Pxy x y,  g = (1 - F(u))/r^2,
+//        F(u) = (1 - e^-u)/u; the Ein term is the diffusion of the point
+//        dilatation that the crack opening volume puts at the source,
+//      - pore pressure -(alpha/S) Ce [a P(2,u)/r^4 - tr(P) e^-u/(4ct)],
+//        P(2,u) = 1 - (1+u) e^-u,
+//      - fluid source: p = q E1(u)/(4 pi kappa),
+//        sigma = -eta q/(4 pi kappa) [2 F n n + (E1 - F) I].
+//  * disl_field: a DD held on the half line starting at the origin (a
+//    poroelastic edge dislocation).  A constant-DD element [y1, y2] is
+//    disl(x - y1) - disl(x - y2) exactly, at all times and distances, its own
+//    midpoint included (the delta lines of the point dilatation cancel along
+//    the half line, so the transient needs only e^-u).
+//
+// All transient functions are evaluated without cancellation: series below
+// u = 1, closed forms above.
+#pragma once
+#include <cuda_runtime.h>
+#include "internal.h"
+
+#define DEV __device__ __forceinline__
+
+template <class T> DEV T dexp(T x);
+template <> DEV float dexp<float>(float x) { return expf(x); }
+template <> DEV double dexp<double>(double x) { return exp(x); }
+template <class T> DEV T dlog(T x);
+template <> DEV float dlog<float>(float x) { return logf(x); }
+template <> DEV double dlog<double>(double x) { return log(x); }
+
+template <class T> struct Prec;
+template <> struct Prec<float> { static constexpr int NS = 11; static constexpr int NE = 16; static constexpr int NC = 10; };
+template <> struct Prec<double> { static constexpr int NS = 22; static constexpr int NE = 40; static constexpr int NC = 60; };
+
+// e^-u, F, F', F'' with F(u) = (1 - e^-u)/u.
+template <class T>
+DEV void f_funcs(T u, T &e, T &F0, T &F1, T &F2) {
+    e = dexp<T>(-u);
+    if (u < T(1)) {
+        // F = sum (-u)^k/(k+1)!, F' = sum (k+1)(-1)^(k+1) u^k/(k+2)!,
+        // F'' = sum (k+1)(k+2)(-1)^k u^k/(k+3)!   (Horner, highest term first)
+        T a = 0, b = 0, c = 0;
+#pragma unroll
+        for (int k = Prec<T>::NS; k >= 0; --k) {
+            T f1 = 1, f2 = 1, f3 = 1;
+#pragma unroll
+            for (int j = 2; j <= k + 1; ++j) f1 *= T(j);
+            f2 = f1 * T(k + 2);
+            f3 = f2 * T(k + 3);
+            T sg = (k & 1) ? T(-1) : T(1);
+            a = a * u + sg / f1;
+            b = b * u - sg * T(k + 1) / f2;
+            c = c * u + sg * T((k + 1) * (k + 2)) / f3;
+        }
+        F0 = a; F1 = b; F2 = c;
+    } else {
+        T iu = T(1) / u;
+        F0 = (T(1) - e) * iu;
+        F1 = (e - F0) * iu;
+        F2 = -(e + T(2) * F1) * iu;
+    }
+}
+
+// ghat = (1 - F)/u and its two derivatives; P2h = P(2,u)/u^2.
+template <class T>
+DEV void g_funcs(T u, T e, T F0, T F1, T F2, T &g0, T &g1, T &g2, T &p2h) {
+    if (u < T(1)) {
+        // ghat = sum (-1)^k u^k/(k+2)!, ghat' = sum_{k>=1} (-1)^k k u^(k-1)/(k+2)!,
+        // ghat'' = sum_{k>=2} (-1)^k k(k-1) u^(k-2)/(k+2)!,
+        // P2h = sum_{k>=2} (-1)^k (k-1) u^(k-2)/k!
+        T a = 0, b = 0, c = 0, d = 0;
+#pragma unroll
+        for (int k = Prec<T>::NS + 2; k >= 0; --k) {
+            T fk = 1;
+#pragma unroll
+            for (int j = 2; j <= k; ++j) fk *= T(j);
+            T fk2 = fk * T(k + 1) * T(k + 2);
+            T sg = (k & 1) ? T(-1) : T(1);
+            a = a * u + sg / fk2;
+            if (k >= 1) b = b * u + sg * T(k) / fk2;
+            if (k >= 2) c = c * u + sg * T(k * (k - 1)) / fk2;
+            if (k >= 2) d = d * u + sg * T(k - 1) / fk;
+        }
+        g0 = a; g1 = b; g2 = c; p2h = d;
+    } else {
+        T iu = T(1) / u;
+        g0 = (T(1) - F0) * iu;
+        g1 = -(F1 + g0) * iu;
+        g2 = -(F2 + T(2) * g1) * iu;
+        p2h = (T(1) - (T(1) + u) * e) * iu * iu;
+    }
+}
+
+// Exponential integral E1(u), u > 0: Ein series minus log below 2.5,
+// continued fraction (even contraction, bottom-up) above.
+template <class T>
+DEV T e1(T u) {
+    if (u < T(2.5)) {
+        T s = 0;
+#pragma unroll
+        for (int k = Prec<T>::NE; k >= 1; --k) {
+            T fk = 1;
+#pragma unroll
+            for (int j = 2; j <= k; ++j) fk *= T(j);
+            T sg = (k & 1) ? T(1) : T(-1);
+            s = s * u + sg / (T(k) * fk);
+        }
+        s *= u;   // Ein(u)
+        return s - dlog<T>(u) - T(0.57721566490153286061);
+    }
+    if (u > T(700)) return T(0);
+    T f = u + T(2 * Prec<T>::NC + 1);
+#pragma unroll
+    for (int k = Prec<T>::NC; k >= 1; --k) f = u + T(2 * k - 1) - T(k * k) / f;
+    return dexp<T>(-u) / f;
+}
+
+// ---------------------------------------------------------------------------
+// point kernel, potency form
+// ---------------------------------------------------------------------------
+template <class T>
+DEV void pot_transient(const KConst<T> &k, T x, T y, T Pxx, T Pyy, T Pxy, T q, T ct, T s,
+                       T acc[4]) {
+    T x2 = x * x, y2 = y * y, xy = x * y, r2 = x2 + y2;
+    T g0c = T(1) / (T(4) * ct);                // gamma0 = 1/(4ct)
+    T u = r2 * g0c;
+    T e, F0, F1, F2, gh0, gh1, gh2, p2h;
+    f_funcs<T>(u, e, F0, F1, F2);
+    g_funcs<T>(u, e, F0, F1, F2, gh0, gh1, gh2, p2h);
+    T dP = Pyy - Pxx, trP = Pxx + Pyy;
+    T a = dP * (x2 - y2) - T(4) * Pxy * xy;
+    T ax = T(2) * dP * x - T(4) * Pxy * y;
+    T ay = -T(2) * dP * y - T(4) * Pxy * x;
+    T axx = T(2) * dP, axy = -T(4) * Pxy;
+    T g = g0c * gh0, g1 = g0c * g0c * gh1, g2 = g0c * g0c * g0c * gh2;
+    T m0a = T(2) * g0c * F0 * trP, m0b = T(4) * g0c * g0c * F1 * trP;
+    T pxx = axx * g + T(4) * ax * x * g1 + T(2) * a * g1 + T(4) * a * x2 * g2 + m0a + m0b * x2;
+    T pyy = -axx * g + T(4) * ay * y * g1 + T(2) * a * g1 + T(4) * a * y2 * g2 + m0a + m0b * y2;
+    T pxy = axy * g + T(2) * (ax * y + ay * x) * g1 + T(4) * a * xy * g2 + m0b * xy;
+    T sk = s * k.K2 * k.G2;
+    acc[0] -= sk * pyy;                         // 2G (psi_xx - lap psi) = -2G psi_yy
+    acc[1] -= sk * pxx;
+    acc[2] += sk * pxy;
+    acc[3] -= s * k.aS * k.Ce * (a * g0c * g0c * p2h - trP * g0c * e);
+    if (q != T(0)) {
+        T E1 = e1<T>(u);
+        T pre = s * q * k.i4pk;
+        T nn = T(2) * F0 / r2;
+        acc[0] -= pre * k.eta * (nn * x2 + E1 - F0);
+        acc[1] -= pre * k.eta * (nn * y2 + E1 - F0);
+        acc[2] -= pre * k.eta * (nn * xy);
+        acc[3] += pre * E1;
+    }
+}
+
+template <class T>
+DEV void pot_kernel(const KConst<T> &k, T x, T y, T Pxx, T Pyy, T Pxy, T q, const Win<T> &w,
+                    T acc[4]) {
+    if (w.elastic) {
+        T x2 = x * x, y2 = y * y, xy = x * y, r2 = x2 + y2;
+        T ir2 = T(1) / r2;
+        T C = k.Cel * ir2 * ir2 * ir2;
+        T A1 = x2 * x2, B1 = y2 * y2, Cm = x2 * y2;
+        acc[0] -= C * (Pxx * (T(3) * A1 - T(6) * Cm - B1) + Pyy * (-A1 + T(6) * Cm - B1) +
+                       Pxy * xy * (T(12) * x2 - T(4) * y2));
+        acc[1] += C * (Pxx * (A1 - T(6) * Cm + B1) + Pyy * (A1 + T(6) * Cm - T(3) * B1) +
+                       Pxy * xy * (T(4) * x2 - T(12) * y2));
+        acc[2] += C * (Pxx * xy * (-T(6) * x2 + T(2) * y2) + T(2) * Pxy * (A1 - T(6) * Cm + B1) +
+                       Pyy * xy * (T(2) * x2 - T(6) * y2));
+    }
+    pot_transient<T>(k, x, y, Pxx, Pyy, Pxy, q, w.ct_hi, T(1), acc);
+    if (w.ct_lo > T(0)) pot_transient<T>(k, x, y, Pxx, Pyy, Pxy, q, w.ct_lo, T(-1), acc);
+}
+
+// ---------------------------------------------------------------------------
+// half-line DD (edge dislocation), DD vector (Dx, Dy)
+// ---------------------------------------------------------------------------
+template <class T>
+DEV void disl_transient(const KConst<T> &k, T zx, T zy, T Dx, T Dy, T ct, T s, T acc[4]) {
+    T r2 = zx * zx + zy * zy;
+    T beta = T(1) / (T(2) * ct);
+    T u = T(0.5) * r2 * beta;
+    T e, F0, F1, F2;
+    f_funcs<T>(u, e, F0, F1, F2);
+    T V1 = F0 + F1, V2 = F1 + F2;
+    T l = Dx * zy - Dy * zx, lx = -Dy, ly = Dx;
+    T cm = -k.K2 * beta;
+    T lb = l * beta * V2;
+    T pxx = cm * (T(2) * lx * zx * V1 + lb * zx * zx + l * V1);
+    T pyy = cm * (T(2) * ly * zy * V1 + lb * zy * zy + l * V1);
+    T pxy = cm * ((lx * zy + ly * zx) * V1 + lb * zx * zy);
+    T sk = s * k.G2;
+    acc[0] -= sk * pyy;
+    acc[1] -= sk * pxx;
+    acc[2] += sk * pxy;
+    acc[3] -= s * k.aS * k.Ce * l / r2 * (u * F0);      // 1 - e^-u = u F(u)
+}
+
+template <class T>
+DEV void disl_field(const KConst<T> &k, T zx, T zy, T Dx, T Dy, const Win<T> &w, T s, T acc[4]) {
+    if (w.elastic) {
+        T x2 = zx * zx, y2 = zy * zy, r2 = x2 + y2;
+        T C = s * k.Cel / (r2 * r2);
+        acc[0] += C * (Dx * zy * (T(3) * x2 + y2) - Dy * zx * (x2 - y2));
+        acc[1] -= C * (Dx * zy * (x2 - y2) + Dy * zx * (x2 + T(3) * y2));
+        acc[2] -= C * (x2 - y2) * (Dx * zx + Dy * zy);
+    }
+    disl_transient<T>(k, zx, zy, Dx, Dy, w.ct_hi, s, acc);
+    if (w.ct_lo > T(0)) disl_transient<T>(k, zx, zy, Dx, Dy, w.ct_lo, -s, acc);
+}
+
+// rotate a global (sxx, syy, sxy) into the target frame: (sigma_s, sigma_n)
+template <class T>
+DEV void to_local(T tx, T ty, const T g[4], T &ss, T &sn) {
+    T nx = -ty, ny = tx;
+    sn = g[0] * nx * nx + T(2) * g[2] * nx * ny + g[1] * ny * ny;
+    ss = g[0] * tx * nx + g[2] * (tx * ny + ty * nx) + g[1] * ty * ny;
+}

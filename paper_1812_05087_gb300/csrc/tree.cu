@@ -1,0 +1,514 @@
+// Quadtree of paper Sec. 3.1 built on the device: Morton keys of the element
+// midpoints, LSD radix sort, unique key prefixes per level (empty "zero"
+// cells never appear), parent links, neighbour lists (cells sharing a vertex)
+// and interaction lists (children of the parent's neighbours that are not
+// neighbours).  Uniform depth; children in Z order (left-right, then
+// bottom-top).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "internal.h"
+
+namespace {
+
+thread_local long long tl_launches = 0;   // kernel launches of the current build
+constexpr int KEY_LEVELS = 16;          // 16 levels -> 32-bit keys
+constexpr int SCAN_BLOCK = 1024;
+
+__device__ __forceinline__ uint32_t spread2(uint32_t v) {   // 16 bits -> even bit positions
+    v &= 0xFFFFu;
+    v = (v | (v << 8)) & 0x00FF00FFu;
+    v = (v | (v << 4)) & 0x0F0F0F0Fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+__device__ __forceinline__ uint32_t compact2(uint32_t v) {
+    v &= 0x55555555u;
+    v = (v | (v >> 1)) & 0x33333333u;
+    v = (v | (v >> 2)) & 0x0F0F0F0Fu;
+    v = (v | (v >> 4)) & 0x00FF00FFu;
+    v = (v | (v >> 8)) & 0x0000FFFFu;
+    return v;
+}
+// Z order: x in the even bits, y in the odd bits, so children run
+// bottom-left, bottom-right, top-left, top-right.
+__device__ __forceinline__ uint32_t morton(uint32_t ix, uint32_t iy) { return spread2(ix) | (spread2(iy) << 1); }
+
+// ---------------------------------------------------------------- reductions
+__global__ void k_bbox(const double *xy, int64_t n, double *part) {
+    __shared__ double s[6][256];
+    double mnx = 1e300, mny = 1e300, mxx = -1e300, mxy = -1e300, lmax = 0.0, bad = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double x0 = xy[i], y0 = xy[n + i], x1 = xy[2 * n + i], y1 = xy[3 * n + i];
+        double cx = 0.5 * (x0 + x1), cy = 0.5 * (y0 + y1);
+        double L = hypot(x1 - x0, y1 - y0);
+        if (!(L > 0.0) || !isfinite(cx) || !isfinite(cy)) bad = 1.0;
+        mnx = fmin(mnx, cx); mny = fmin(mny, cy); mxx = fmax(mxx, cx); mxy = fmax(mxy, cy);
+        lmax = fmax(lmax, L);
+    }
+    int t = threadIdx.x;
+    s[0][t] = mnx; s[1][t] = mny; s[2][t] = -mxx; s[3][t] = -mxy; s[4][t] = -lmax; s[5][t] = -bad;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (t < w)
+            for (int k = 0; k < 6; ++k) s[k][t] = fmin(s[k][t], s[k][t + w]);
+        __syncthreads();
+    }
+    if (t < 6) part[blockIdx.x * 6 + t] = s[t][0];
+}
+
+__global__ void k_keys(const double *xy, int64_t n, double x0, double y0, double w16, uint32_t *key,
+                       int32_t *idx) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double cx = 0.5 * (xy[i] + xy[2 * n + i]), cy = 0.5 * (xy[n + i] + xy[3 * n + i]);
+    double fx = floor((cx - x0) / w16), fy = floor((cy - y0) / w16);
+    uint32_t ix = (uint32_t)fmin(fmax(fx, 0.0), 65535.0), iy = (uint32_t)fmin(fmax(fy, 0.0), 65535.0);
+    key[i] = morton(ix, iy);
+    idx[i] = (int32_t)i;
+}
+
+// -------------------------------------------------------------------- scans
+// exclusive scan of int32 in tiles of SCAN_BLOCK; tile sums to `sums`
+__global__ void k_scan_tiles(const int32_t *in, int32_t *out, int64_t n, int32_t *sums) {
+    __shared__ int32_t s[SCAN_BLOCK];
+    int t = threadIdx.x;
+    int64_t i = blockIdx.x * (int64_t)SCAN_BLOCK + t;
+    int32_t v = i < n ? in[i] : 0;
+    s[t] = v;
+    __syncthreads();
+    for (int off = 1; off < SCAN_BLOCK; off <<= 1) {
+        int32_t a = t >= off ? s[t - off] : 0;
+        __syncthreads();
+        s[t] += a;
+        __syncthreads();
+    }
+    if (i < n) out[i] = s[t] - v;
+    if (t == SCAN_BLOCK - 1) sums[blockIdx.x] = s[t];
+}
+__global__ void k_scan_add(int32_t *out, int64_t n, const int32_t *offs) {
+    int64_t i = blockIdx.x * (int64_t)SCAN_BLOCK + threadIdx.x;
+    if (i < n) out[i] += offs[blockIdx.x];
+}
+
+struct Scratch {      // simple bump allocations freed at the end of the build
+    std::vector<void *> ptrs;
+    cudaError_t err = cudaSuccess;
+    template <class T> T *get(size_t count) {
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+        if (e != cudaSuccess) { err = e; return nullptr; }
+        ptrs.push_back(p);
+        return (T *)p;
+    }
+    ~Scratch() { for (void *p : ptrs) cudaFree(p); }
+};
+
+// exclusive scan, returns the total (synchronises)
+cudaError_t scan_excl(Scratch &S, cudaStream_t st, const int32_t *in, int32_t *out, int64_t n,
+                      int32_t *total) {
+    int64_t nb = (n + SCAN_BLOCK - 1) / SCAN_BLOCK;
+    if (nb == 0) { *total = 0; return cudaSuccess; }
+    int32_t *sums = S.get<int32_t>(nb), *soff = S.get<int32_t>(nb);
+    if (S.err) return S.err;
+    k_scan_tiles<<<nb, SCAN_BLOCK, 0, st>>>(in, out, n, sums); ++tl_launches;
+    if (nb > 1) {
+        int32_t tot = 0;
+        cudaError_t e = scan_excl(S, st, sums, soff, nb, &tot);
+        if (e) return e;
+        k_scan_add<<<nb, SCAN_BLOCK, 0, st>>>(out, n, soff); ++tl_launches;
+        *total = tot;
+        return cudaGetLastError();
+    }
+    int32_t h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, sums, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e) return e;
+    e = cudaStreamSynchronize(st);
+    *total = h;
+    return e;
+}
+
+// ------------------------------------------------------------- radix sort
+// LSD radix sort of (key, value) pairs, 8 bits per pass, stable.
+constexpr int RS_TILE = 256;
+__global__ void k_rs_hist(const uint32_t *key, int64_t n, int shift, int32_t *hist, int64_t ntiles) {
+    __shared__ int32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t i = blockIdx.x * (int64_t)RS_TILE + threadIdx.x;
+    if (i < n) atomicAdd(&h[(key[i] >> shift) & 255u], 1);
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];   // digit-major
+}
+__global__ void k_rs_scatter(const uint32_t *key, const int32_t *val, int64_t n, int shift,
+                             const int32_t *offs, int64_t ntiles, uint32_t *key2, int32_t *val2) {
+    __shared__ int32_t wc[8][256];       // per-warp digit counts
+    __shared__ int32_t base[256];
+    int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    for (int k = t; k < 8 * 256; k += RS_TILE) (&wc[0][0])[k] = 0;
+    __syncthreads();
+    int64_t i = blockIdx.x * (int64_t)RS_TILE + t;
+    bool ok = i < n;
+    uint32_t k = ok ? key[i] : 0u;
+    uint32_t d = ok ? ((k >> shift) & 255u) : 256u;
+    unsigned mask = __match_any_sync(0xFFFFFFFFu, d);
+    int rank = __popc(mask & ((1u << lane) - 1u));
+    if (ok && rank == 0) wc[w][d] = __popc(mask);
+    __syncthreads();
+    // per digit: exclusive prefix over warps (stable: lower warps first)
+    {
+        int run = 0;
+        for (int ww = 0; ww < 8; ++ww) { int c = wc[ww][t]; wc[ww][t] = run; run += c; }
+        base[t] = offs[(int64_t)t * ntiles + blockIdx.x];
+    }
+    __syncthreads();
+    if (ok) {
+        int64_t pos = base[d] + wc[w][d] + rank;
+        key2[pos] = k;
+        val2[pos] = val[i];
+    }
+}
+
+cudaError_t radix_sort(Scratch &S, cudaStream_t st, uint32_t *key, int32_t *val, int64_t n, int bits) {
+    int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
+    uint32_t *k2 = S.get<uint32_t>(n);
+    int32_t *v2 = S.get<int32_t>(n), *hist = S.get<int32_t>(256 * ntiles), *offs = S.get<int32_t>(256 * ntiles);
+    if (S.err) return S.err;
+    uint32_t *ka = key, *kb = k2;
+    int32_t *va = val, *vb = v2;
+    int passes = (bits + 7) / 8;
+    for (int p = 0; p < passes; ++p) {
+        int shift = 8 * p;
+        k_rs_hist<<<ntiles, RS_TILE, 0, st>>>(ka, n, shift, hist, ntiles); ++tl_launches;
+        int32_t tot;
+        cudaError_t e = scan_excl(S, st, hist, offs, 256 * ntiles, &tot);
+        if (e) return e;
+        k_rs_scatter<<<ntiles, RS_TILE, 0, st>>>(ka, va, n, shift, offs, ntiles, kb, vb); ++tl_launches;
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    if (ka != key) {
+        cudaMemcpyAsync(key, ka, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(val, va, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+    }
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- levels
+// longest run of equal key prefixes at every level (leaf occupancy)
+__global__ void k_runmax(const uint32_t *key, int64_t n, int Lmax, int32_t *runmax) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int L = 0; L <= Lmax; ++L) {
+        int sh = 2 * (KEY_LEVELS - L);
+        uint32_t p = sh >= 32 ? 0u : (key[i] >> sh);
+        if (i > 0 && (sh >= 32 ? 0u : (key[i - 1] >> sh)) == p) continue;
+        int64_t lo = i, hi = n;     // first index with a different prefix
+        while (hi - lo > 1) {
+            int64_t mid = (lo + hi) / 2;
+            uint32_t pm = sh >= 32 ? 0u : (key[mid] >> sh);
+            if (pm == p) lo = mid; else hi = mid;
+        }
+        atomicMax(&runmax[L], (int32_t)(hi - i));
+    }
+}
+
+__global__ void k_flags(const uint32_t *key, int64_t n, int sh, int32_t *flag) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t p = sh >= 32 ? 0u : key[i] >> sh;
+    flag[i] = (i == 0 || (sh >= 32 ? 0u : key[i - 1] >> sh) != p) ? 1 : 0;
+}
+// cells of one level: start, key, coordinates; element -> cell (level-local)
+__global__ void k_cells(const uint32_t *key, int64_t n, int sh, const int32_t *flag, const int32_t *ex,
+                        int64_t off, int32_t *cstart, uint32_t *ckey, int32_t *cix, int32_t *ciy,
+                        int32_t *elem_cell) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t c = ex[i] + flag[i] - 1;
+    elem_cell[i] = c;
+    if (flag[i]) {
+        uint32_t p = sh >= 32 ? 0u : key[i] >> sh;
+        cstart[off + c] = (int32_t)i;
+        ckey[off + c] = p;
+        cix[off + c] = (int32_t)compact2(p);
+        ciy[off + c] = (int32_t)compact2(p >> 1);
+    }
+}
+__global__ void k_cell_end(const int32_t *cstart, int32_t *cend, int64_t off, int64_t ncell, int64_t n) {
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    cend[off + c] = (c + 1 < ncell) ? cstart[off + c + 1] : (int32_t)n;
+}
+__global__ void k_parent(const int32_t *cstart, int64_t off, int64_t ncell, const int32_t *elem_cell_up,
+                         int64_t off_up, int32_t *parent) {
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    parent[off + c] = (int32_t)(off_up + elem_cell_up[cstart[off + c]]);
+}
+
+__device__ int32_t find_key(const uint32_t *ckey, int64_t off, int64_t ncell, uint32_t k) {
+    int64_t lo = 0, hi = ncell;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) / 2;
+        if (ckey[off + mid] < k) lo = mid + 1; else hi = mid;
+    }
+    return (lo < ncell && ckey[off + lo] == k) ? (int32_t)lo : -1;
+}
+
+// neighbours of each leaf (incl. itself): pass 0 counts, pass 1 fills
+__global__ void k_neigh(const uint32_t *ckey, const int32_t *cix, const int32_t *ciy, int64_t off,
+                        int64_t ncell, int side, const int32_t *nboff, int32_t *nbidx, int32_t *cnt) {
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    int ix = cix[off + c], iy = ciy[off + c], m = 0;
+    for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+            int jx = ix + dx, jy = iy + dy;
+            if (jx < 0 || jy < 0 || jx >= side || jy >= side) continue;
+            int32_t j = find_key(ckey, off, ncell, spread2(jx) | (spread2(jy) << 1));
+            if (j < 0) continue;
+            if (nbidx) nbidx[nboff[c] + m] = j;
+            ++m;
+        }
+    if (cnt) cnt[c] = m;
+}
+
+// interaction lists of the cells of one level (global cell indices)
+__global__ void k_ilist(const uint32_t *ckey, const int32_t *cix, const int32_t *ciy, int64_t off,
+                        int64_t ncell, int side, const int32_t *iloff, int32_t *ilidx, int32_t *cnt) {
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    int ix = cix[off + c], iy = ciy[off + c], px = ix >> 1, py = iy >> 1, m = 0;
+    int pside = side >> 1;
+    for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+            int qx = px + dx, qy = py + dy;
+            if (qx < 0 || qy < 0 || qx >= pside || qy >= pside) continue;
+            for (int ch = 0; ch < 4; ++ch) {
+                int jx = 2 * qx + (ch & 1), jy = 2 * qy + (ch >> 1);
+                if (abs(jx - ix) <= 1 && abs(jy - iy) <= 1) continue;    // neighbour (or itself)
+                int32_t j = find_key(ckey, off, ncell, spread2(jx) | (spread2(jy) << 1));
+                if (j < 0) continue;
+                if (ilidx) ilidx[iloff[off + c] + m] = (int32_t)(off + j);
+                ++m;
+            }
+        }
+    if (cnt) cnt[off + c] = m;
+}
+
+__global__ void k_geom(const double *xy, int64_t n, const int32_t *idx, const int32_t *elem_leaf,
+                       const int32_t *cix, const int32_t *ciy, int64_t loff, double x0, double y0,
+                       double wl, int64_t *perm, float4 *g_rel, float4 *g_frame, double *xys) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t e = idx[i];
+    perm[i] = e;
+    double ax = xy[e], ay = xy[n + e], bx = xy[2 * n + e], by = xy[3 * n + e];
+    xys[i] = ax; xys[n + i] = ay; xys[2 * n + i] = bx; xys[3 * n + i] = by;
+    int32_t c = elem_leaf[i];
+    double ccx = x0 + (cix[loff + c] + 0.5) * wl, ccy = y0 + (ciy[loff + c] + 0.5) * wl;
+    g_rel[i] = make_float4((float)(ax - ccx), (float)(ay - ccy), (float)(bx - ccx), (float)(by - ccy));
+    double L = hypot(bx - ax, by - ay);
+    g_frame[i] = make_float4((float)((bx - ax) / L), (float)((by - ay) / L), (float)(0.5 * L), 0.f);
+}
+
+__global__ void k_p2p_count(const int32_t *cstart, const int32_t *cend, int64_t loff, int64_t nleaf,
+                            const int32_t *nboff, const int32_t *nbidx, unsigned long long *tot) {
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= nleaf) return;
+    long long nt = cend[loff + c] - cstart[loff + c], ns = 0;
+    for (int k = nboff[c]; k < nboff[c + 1]; ++k) ns += cend[loff + nbidx[k]] - cstart[loff + nbidx[k]];
+    atomicAdd(tot, (unsigned long long)(nt * ns));
+}
+
+}  // namespace
+
+#define TRY(call)                                                                   \
+    do {                                                                            \
+        cudaError_t _e = (call);                                                    \
+        if (_e != cudaSuccess) {                                                    \
+            tree_free(t);                                                           \
+            return ctx_fail(ctx, _e == cudaErrorMemoryAllocation ? DDM_ENOMEM : DDM_ECUDA, \
+                            std::string("tree build: ") + #call + ": " + cudaGetErrorString(_e)); \
+        }                                                                           \
+    } while (0)
+
+void tree_free(ddm_tree *t) {
+    if (!t) return;
+    void *ps[] = {t->perm, t->cell_key, t->cell_ix, t->cell_iy, t->cell_start, t->cell_end, t->cell_parent,
+                  t->il_off, t->il_idx, t->nb_off, t->nb_idx, t->elem_leaf, t->g_rel, t->g_frame,
+                  t->xy_sorted, t->xy_caller, t->self_blk, t->W, t->Fl, t->chg};
+    for (void *p : ps)
+        if (p) cudaFree(p);
+    delete t;
+}
+
+ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **out) {
+    if (!ctx || !d_xy || !out || n <= 0 || n > (int64_t)1 << 30)
+        return ctx_fail(ctx, DDM_EINVAL, "ddm_build_tree: bad arguments");
+    cudaStream_t st = ctx->stream;
+    ddm_tree *t = new ddm_tree();
+    t->n = n;
+    t->self_dt = -1.0;
+    Scratch S;
+    tl_launches = 0;
+    prof_begin(ctx, 9);
+    const int TB = 256;
+    int64_t nbk = (n + TB - 1) / TB;
+
+    // bounding square of the midpoints
+    int nbb = (int)std::min<int64_t>(nbk, 1024);
+    double *part = S.get<double>(6 * nbb);
+    TRY(S.err);
+    k_bbox<<<nbb, 256, 0, st>>>(d_xy, n, part); ++tl_launches;
+    std::vector<double> hp(6 * nbb);
+    TRY(cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    TRY(cudaStreamSynchronize(st));
+    double mnx = 1e300, mny = 1e300, mxx = -1e300, mxy = -1e300, lmax = 0, bad = 0;
+    for (int b = 0; b < nbb; ++b) {
+        mnx = std::min(mnx, hp[6 * b]); mny = std::min(mny, hp[6 * b + 1]);
+        mxx = std::max(mxx, -hp[6 * b + 2]); mxy = std::max(mxy, -hp[6 * b + 3]);
+        lmax = std::max(lmax, -hp[6 * b + 4]); bad = std::max(bad, -hp[6 * b + 5]);
+    }
+    if (bad > 0) { tree_free(t); return ctx_fail(ctx, DDM_EINVAL, "ddm_build_tree: zero-length or non-finite element"); }
+    double span = std::max(std::max(mxx - mnx, mxy - mny), 4.0 * lmax);
+    double h0 = 0.5 * span * (1.0 + 1e-9) + 1e-300;
+    t->cx = 0.5 * (mnx + mxx); t->cy = 0.5 * (mny + mxy); t->h0 = h0;
+    double X0 = t->cx - h0, Y0 = t->cy - h0;
+
+    // keys at 16 levels, sort
+    uint32_t *key = S.get<uint32_t>(n);
+    int32_t *idx = S.get<int32_t>(n);
+    TRY(S.err);
+    double w16 = 2.0 * h0 / 65536.0;
+    k_keys<<<nbk, TB, 0, st>>>(d_xy, n, X0, Y0, w16, key, idx); ++tl_launches;
+    TRY(radix_sort(S, st, key, idx, n, 32));
+
+    // depth: smallest L whose leaves hold <= leaf_size, capped so that the
+    // longest element is at most a quarter of a leaf
+    int Lcap = (int)std::floor(std::log2(2.0 * h0 / (4.0 * lmax)) + 1e-12);
+    Lcap = std::max(0, std::min(Lcap, KEY_LEVELS));
+    if (ctx->prm.max_depth > 0) Lcap = std::min(Lcap, ctx->prm.max_depth);
+    int32_t *runmax = S.get<int32_t>(KEY_LEVELS + 1);
+    TRY(S.err);
+    TRY(cudaMemsetAsync(runmax, 0, (KEY_LEVELS + 1) * sizeof(int32_t), st));
+    k_runmax<<<nbk, TB, 0, st>>>(key, n, Lcap, runmax); ++tl_launches;
+    int32_t hrun[KEY_LEVELS + 1];
+    TRY(cudaMemcpyAsync(hrun, runmax, sizeof(hrun), cudaMemcpyDeviceToHost, st));
+    TRY(cudaStreamSynchronize(st));
+    int L = Lcap;
+    for (int l = 0; l <= Lcap; ++l)
+        if (hrun[l] <= ctx->prm.leaf_size) { L = l; break; }
+    t->depth = L;
+
+    // cells of every level
+    std::vector<int32_t *> ecell(L + 1);
+    int32_t *flag = S.get<int32_t>(n), *ex = S.get<int32_t>(n);
+    TRY(S.err);
+    std::vector<int64_t> ncl(L + 1);
+    t->lvl_off.assign(L + 2, 0);
+    for (int l = 0; l <= L; ++l) {
+        k_flags<<<nbk, TB, 0, st>>>(key, n, 2 * (KEY_LEVELS - l), flag); ++tl_launches;
+        int32_t tot;
+        TRY(scan_excl(S, st, flag, ex, n, &tot));
+        ncl[l] = tot;
+        t->lvl_off[l + 1] = t->lvl_off[l] + tot;
+        ecell[l] = S.get<int32_t>(n);
+        TRY(S.err);
+        TRY(cudaMemcpyAsync(ecell[l], ex, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+        // stash flags in ecell temporarily: ecell = ex + flag - 1 computed in k_cells later
+        int32_t *fl = S.get<int32_t>(n);
+        TRY(S.err);
+        TRY(cudaMemcpyAsync(fl, flag, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+        ecell.push_back(fl);   // keep alive; index L+1+l
+    }
+    int64_t NC = t->lvl_off[L + 1];
+    t->n_cells = NC;
+    TRY(cudaMalloc(&t->cell_key, NC * sizeof(uint32_t)));
+    TRY(cudaMalloc(&t->cell_ix, NC * sizeof(int32_t)));
+    TRY(cudaMalloc(&t->cell_iy, NC * sizeof(int32_t)));
+    TRY(cudaMalloc(&t->cell_start, NC * sizeof(int32_t)));
+    TRY(cudaMalloc(&t->cell_end, NC * sizeof(int32_t)));
+    TRY(cudaMalloc(&t->cell_parent, NC * sizeof(int32_t)));
+    for (int l = 0; l <= L; ++l) {
+        int32_t *fl = ecell[L + 1 + l];
+        int32_t *exl = ecell[l];
+        int32_t *elem_cell = S.get<int32_t>(n);
+        TRY(S.err);
+        k_cells<<<nbk, TB, 0, st>>>(key, n, 2 * (KEY_LEVELS - l), fl, exl, t->lvl_off[l], t->cell_start,
+                                   t->cell_key, t->cell_ix, t->cell_iy, elem_cell); ++tl_launches;
+        ecell[l] = elem_cell;
+        int64_t nc = ncl[l];
+        k_cell_end<<<(nc + TB - 1) / TB, TB, 0, st>>>(t->cell_start, t->cell_end, t->lvl_off[l], nc, n); ++tl_launches;
+    }
+    TRY(cudaMemsetAsync(t->cell_parent, 0xFF, sizeof(int32_t), st));   // root: -1
+    for (int l = 1; l <= L; ++l) {
+        int64_t nc = ncl[l];
+        k_parent<<<(nc + TB - 1) / TB, TB, 0, st>>>(t->cell_start, t->lvl_off[l], nc, ecell[l - 1],
+                                                   t->lvl_off[l - 1], t->cell_parent); ++tl_launches;
+    }
+
+    // neighbours of leaves
+    int64_t nleaf = ncl[L], loff = t->lvl_off[L];
+    int side = 1 << L;
+    int32_t *cnt = S.get<int32_t>(std::max<int64_t>(NC, nleaf) + 1);
+    TRY(S.err);
+    TRY(cudaMalloc(&t->nb_off, (nleaf + 1) * sizeof(int32_t)));
+    int64_t lb = (nleaf + TB - 1) / TB;
+    k_neigh<<<lb, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, loff, nleaf, side, nullptr, nullptr, cnt); ++tl_launches;
+    int32_t nbtot;
+    TRY(scan_excl(S, st, cnt, t->nb_off, nleaf, &nbtot));
+    TRY(cudaMemcpyAsync(t->nb_off + nleaf, &nbtot, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    TRY(cudaMalloc(&t->nb_idx, std::max(nbtot, 1) * sizeof(int32_t)));
+    k_neigh<<<lb, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, loff, nleaf, side, t->nb_off, t->nb_idx, nullptr); ++tl_launches;
+
+    // interaction lists, levels >= 2
+    TRY(cudaMemsetAsync(cnt, 0, NC * sizeof(int32_t), st));
+    for (int l = 2; l <= L; ++l) {
+        int64_t nc = ncl[l];
+        k_ilist<<<(nc + TB - 1) / TB, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, t->lvl_off[l], nc,
+                                                  1 << l, nullptr, nullptr, cnt); ++tl_launches;
+    }
+    TRY(cudaMalloc(&t->il_off, (NC + 1) * sizeof(int32_t)));
+    int32_t iltot;
+    TRY(scan_excl(S, st, cnt, t->il_off, NC, &iltot));
+    TRY(cudaMemcpyAsync(t->il_off + NC, &iltot, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    TRY(cudaMalloc(&t->il_idx, std::max(iltot, 1) * sizeof(int32_t)));
+    for (int l = 2; l <= L; ++l) {
+        int64_t nc = ncl[l];
+        k_ilist<<<(nc + TB - 1) / TB, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, t->lvl_off[l], nc,
+                                                  1 << l, t->il_off, t->il_idx, nullptr); ++tl_launches;
+    }
+    t->n_m2l = iltot;
+
+    // sorted geometry
+    TRY(cudaMalloc(&t->perm, n * sizeof(int64_t)));
+    TRY(cudaMalloc(&t->elem_leaf, n * sizeof(int32_t)));
+    TRY(cudaMalloc(&t->g_rel, n * sizeof(float4)));
+    TRY(cudaMalloc(&t->g_frame, n * sizeof(float4)));
+    TRY(cudaMalloc(&t->xy_sorted, 4 * n * sizeof(double)));
+    TRY(cudaMalloc(&t->self_blk, 9 * n * sizeof(double)));
+    TRY(cudaMalloc(&t->xy_caller, 4 * n * sizeof(double)));
+    TRY(cudaMemcpyAsync(t->xy_caller, d_xy, 4 * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    TRY(cudaMalloc(&t->chg, n * sizeof(float4)));
+    TRY(cudaMemcpyAsync(t->elem_leaf, ecell[L], n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    double wl = 2.0 * h0 / (double)side;
+    k_geom<<<nbk, TB, 0, st>>>(d_xy, n, idx, t->elem_leaf, t->cell_ix, t->cell_iy, loff, X0, Y0, wl, t->perm,
+                              t->g_rel, t->g_frame, t->xy_sorted); ++tl_launches;
+    unsigned long long *ptot = S.get<unsigned long long>(1);
+    TRY(S.err);
+    TRY(cudaMemsetAsync(ptot, 0, sizeof(unsigned long long), st));
+    k_p2p_count<<<lb, TB, 0, st>>>(t->cell_start, t->cell_end, loff, nleaf, t->nb_off, t->nb_idx, ptot); ++tl_launches;
+    unsigned long long hp2p = 0;
+    TRY(cudaMemcpyAsync(&hp2p, ptot, sizeof(hp2p), cudaMemcpyDeviceToHost, st));
+    TRY(cudaGetLastError());
+    TRY(cudaStreamSynchronize(st));
+    t->n_p2p = (int64_t)hp2p;
+    prof_end(ctx, 9, (int)tl_launches);
+    *out = t;
+    return DDM_OK;
+}

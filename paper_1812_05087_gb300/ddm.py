@@ -1,0 +1,297 @@
+"""Thin Python binding of the C ABI in include/ddm.h.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library (libddm_gb300.so, built for sm_103a).  Device buffers are torch CUDA
+tensors (float64, contiguous); the library is loaded from the package's
+_build directory and there is no fallback: a missing library raises.
+
+The functions carry the C names (ddm_create, ddm_build_tree, ddm_matvec,
+ddm_history_apply, ddm_rhs, ddm_gmres_solve, ddm_sif, ...); ``Context`` and
+``Tree`` wrap them for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+DDM_OK, DDM_EINVAL, DDM_ENOMEM, DDM_ENOTCONV, DDM_ETIMEOUT, DDM_ECUDA, DDM_PENDING = range(7)
+MODE_FMM, MODE_DENSE = 0, 1
+SYS_PRESSURE, SYS_IMPERMEABLE, SYS_RATE = 0, 1, 2
+_MODES = {"fmm": MODE_FMM, "dense": MODE_DENSE}
+_SYSTEMS = {"pressure": SYS_PRESSURE, "impermeable": SYS_IMPERMEABLE, "rate": SYS_RATE}
+EXPORTS = ("ddm_create", "ddm_destroy", "ddm_last_error", "ddm_build_tree", "ddm_tree_destroy",
+           "ddm_tree_get_info", "ddm_matvec", "ddm_history_apply", "ddm_rhs", "ddm_gmres_solve", "ddm_sif",
+           "ddm_profile", "ddm_profile_read")
+NSTAGES = 10
+STAGES = ("charges", "self", "p2m", "m2m", "m2l", "l2l", "leaf", "dense", "krylov", "tree")
+
+
+class ddm_material(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("G", "nu", "nu_u", "B", "perm", "visc")]
+
+
+class ddm_fmm_params(ctypes.Structure):
+    _fields_ = [("n_cheb", ctypes.c_int), ("leaf_size", ctypes.c_int), ("max_depth", ctypes.c_int),
+                ("quad_near", ctypes.c_int)]
+
+
+class ddm_tree_info(ctypes.Structure):
+    _fields_ = [("n_elements", ctypes.c_int64), ("depth", ctypes.c_int), ("n_cells", ctypes.c_int64),
+                ("n_leaves", ctypes.c_int64), ("n_m2l_pairs", ctypes.c_int64), ("n_p2p_pairs", ctypes.c_int64),
+                ("root_half_width", ctypes.c_double)]
+
+
+class ddm_loads(ctypes.Structure):
+    _fields_ = [("sigma_H", ctypes.c_double), ("sigma_h", ctypes.c_double), ("p_f", ctypes.c_double),
+                ("p0", ctypes.c_double), ("system", ctypes.c_int)]
+
+
+class ddm_gmres_params(ctypes.Structure):
+    _fields_ = [("system", ctypes.c_int), ("restart", ctypes.c_int), ("max_iters", ctypes.c_int),
+                ("tol", ctypes.c_double), ("mode", ctypes.c_int)]
+
+
+class ddm_gmres_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("converged", ctypes.c_int)]
+
+
+_lib = None
+_lock = threading.Lock()
+_VP = ctypes.c_void_p
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libddm_gb300.so (building it with nvcc if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"CUDA library not built: {path}")
+            _build.build()
+        L = ctypes.CDLL(path)
+        L.ddm_create.argtypes = [ctypes.POINTER(_VP), ctypes.POINTER(ddm_material), ctypes.POINTER(ddm_fmm_params), _VP]
+        L.ddm_destroy.argtypes = [_VP]
+        L.ddm_destroy.restype = None
+        L.ddm_last_error.argtypes = [_VP]
+        L.ddm_last_error.restype = ctypes.c_char_p
+        L.ddm_build_tree.argtypes = [_VP, _VP, ctypes.c_int64, ctypes.POINTER(_VP)]
+        L.ddm_tree_destroy.argtypes = [_VP]
+        L.ddm_tree_destroy.restype = None
+        L.ddm_tree_get_info.argtypes = [_VP, ctypes.POINTER(ddm_tree_info)]
+        L.ddm_matvec.argtypes = [_VP, _VP, ctypes.c_double, ctypes.c_double, _VP, _VP, ctypes.c_int]
+        L.ddm_history_apply.argtypes = [_VP, _VP, _VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int, _VP, ctypes.c_int]
+        L.ddm_rhs.argtypes = [_VP, _VP, ctypes.POINTER(ddm_loads), _VP, _VP]
+        L.ddm_gmres_solve.argtypes = [_VP, _VP, ctypes.c_double, _VP, _VP, ctypes.POINTER(ddm_gmres_params),
+                                      ctypes.POINTER(ddm_gmres_info)]
+        L.ddm_sif.argtypes = [_VP, _VP, _VP, _VP, ctypes.c_int, _VP, _VP]
+        L.ddm_profile.argtypes = [_VP, ctypes.c_int]
+        L.ddm_profile_read.argtypes = [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+        for name in EXPORTS:
+            fn = getattr(L, name)
+            if fn.restype is ctypes.c_int or name in ("ddm_create", "ddm_build_tree", "ddm_tree_get_info",
+                                                      "ddm_matvec", "ddm_history_apply", "ddm_rhs",
+                                                      "ddm_gmres_solve", "ddm_sif", "ddm_profile",
+                                                      "ddm_profile_read"):
+                fn.restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+class DDMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"ddm status {status}: {msg}")
+        self.status = status
+
+
+def _check(ctx_ptr, st, what):
+    if st != DDM_OK:
+        msg = load().ddm_last_error(ctx_ptr).decode(errors="replace") if ctx_ptr else ""
+        raise DDMError(st, f"{what}: {msg}")
+
+
+def _dev(t: torch.Tensor, n=None, name="tensor") -> int:
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name} must have {n} elements, got {t.numel()}")
+    return t.data_ptr()
+
+
+# ---------------------------------------------------------------- C names
+def ddm_create(material, n_cheb=8, leaf_size=32, max_depth=0, quad_near=6, stream=None):
+    L = load()
+    if isinstance(material, dict):
+        material = [material[k] for k in ("G", "nu", "nu_u", "B", "perm", "visc")]
+    m = ddm_material(*[float(v) for v in material])
+    p = ddm_fmm_params(int(n_cheb), int(leaf_size), int(max_depth), int(quad_near))
+    s = (stream or torch.cuda.current_stream()).cuda_stream
+    out = _VP()
+    st = L.ddm_create(ctypes.byref(out), ctypes.byref(m), ctypes.byref(p), _VP(s))
+    if st != DDM_OK:
+        raise DDMError(st, "ddm_create failed (invalid material or parameters?)")
+    return out
+
+
+def ddm_destroy(ctx):
+    load().ddm_destroy(ctx)
+
+
+def ddm_build_tree(ctx, xy: torch.Tensor):
+    n = xy.numel() // 4
+    out = _VP()
+    _check(ctx, load().ddm_build_tree(ctx, _VP(_dev(xy, 4 * n, "xy")), n, ctypes.byref(out)), "ddm_build_tree")
+    return out
+
+
+def ddm_tree_destroy(tree):
+    load().ddm_tree_destroy(tree)
+
+
+def ddm_tree_get_info(tree) -> dict:
+    info = ddm_tree_info()
+    st = load().ddm_tree_get_info(tree, ctypes.byref(info))
+    if st != DDM_OK:
+        raise DDMError(st, "ddm_tree_get_info")
+    return {k: getattr(info, k) for k, _ in ddm_tree_info._fields_}
+
+
+def ddm_matvec(ctx, tree, tau_lo, tau_hi, x, y, mode=MODE_FMM):
+    n = y.numel()
+    _check(ctx, load().ddm_matvec(ctx, tree, float(tau_lo), float(tau_hi), _VP(_dev(x, n, "x")),
+                                  _VP(_dev(y, n, "y")), int(mode)), "ddm_matvec")
+
+
+def ddm_history_apply(ctx, tree, hist, times, H, rhs, mode=MODE_FMM):
+    tt = (ctypes.c_double * (H + 2))(*[float(v) for v in times])
+    hp = _VP(_dev(hist, None, "hist")) if H > 0 else _VP(0)
+    _check(ctx, load().ddm_history_apply(ctx, tree, hp, tt, int(H), _VP(_dev(rhs, None, "rhs")), int(mode)),
+           "ddm_history_apply")
+
+
+def ddm_rhs(ctx, tree, sigma_H, sigma_h, p_f, p0, system, rhs, pf=None):
+    ld = ddm_loads(float(sigma_H), float(sigma_h), float(p_f), float(p0), int(system))
+    pp = _VP(_dev(pf, None, "pf")) if pf is not None else _VP(0)
+    _check(ctx, load().ddm_rhs(ctx, tree, ctypes.byref(ld), pp, _VP(_dev(rhs, None, "rhs"))), "ddm_rhs")
+
+
+def ddm_gmres_solve(ctx, tree, dt, rhs, x, system=SYS_PRESSURE, restart=50, max_iters=1000, tol=1e-6,
+                    mode=MODE_FMM, raise_on_notconv=True) -> dict:
+    prm = ddm_gmres_params(int(system), int(restart), int(max_iters), float(tol), int(mode))
+    info = ddm_gmres_info()
+    st = load().ddm_gmres_solve(ctx, tree, float(dt), _VP(_dev(rhs, None, "rhs")), _VP(_dev(x, None, "x")),
+                                ctypes.byref(prm), ctypes.byref(info))
+    res = {k: getattr(info, k) for k, _ in ddm_gmres_info._fields_}
+    if st == DDM_ENOTCONV and not raise_on_notconv:
+        return res
+    _check(ctx, st, "ddm_gmres_solve")
+    return res
+
+
+def ddm_sif(ctx, tree, x, tips: torch.Tensor, KI, KII):
+    n = tips.numel()
+    if not (tips.is_cuda and tips.dtype == torch.int64 and tips.is_contiguous()):
+        raise ValueError("tips must be a contiguous int64 CUDA tensor")
+    _check(ctx, load().ddm_sif(ctx, tree, _VP(_dev(x, None, "x")), _VP(tips.data_ptr()), int(n),
+                               _VP(_dev(KI, n, "KI")), _VP(_dev(KII, n, "KII"))), "ddm_sif")
+
+
+def ddm_profile(ctx, enable=True):
+    _check(ctx, load().ddm_profile(ctx, int(bool(enable))), "ddm_profile")
+
+
+def ddm_profile_read(ctx) -> dict:
+    ms = (ctypes.c_double * NSTAGES)()
+    n = (ctypes.c_int64 * NSTAGES)()
+    _check(ctx, load().ddm_profile_read(ctx, ms, n), "ddm_profile_read")
+    return {STAGES[k]: (ms[k], n[k]) for k in range(NSTAGES)}
+
+
+# ---------------------------------------------------------------- wrappers
+class Tree:
+    def __init__(self, ctx: "Context", xy: torch.Tensor):
+        self.ctx = ctx
+        self.n = xy.numel() // 4
+        self.ptr = ddm_build_tree(ctx.ptr, xy)
+
+    def info(self) -> dict:
+        return ddm_tree_get_info(self.ptr)
+
+    def close(self):
+        if self.ptr:
+            ddm_tree_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Context:
+    """A library context on the current CUDA device and stream."""
+
+    def __init__(self, material, n_cheb=8, leaf_size=32, max_depth=0, quad_near=6, stream=None):
+        self.ptr = ddm_create(material, n_cheb, leaf_size, max_depth, quad_near, stream)
+
+    def build_tree(self, xy: torch.Tensor) -> Tree:
+        return Tree(self, xy.contiguous())
+
+    def matvec(self, tree: Tree, x, tau_lo=0.0, tau_hi=1.0, mode="fmm", out=None):
+        out = torch.empty_like(x) if out is None else out
+        ddm_matvec(self.ptr, tree.ptr, tau_lo, tau_hi, x, out, _MODES[mode])
+        return out
+
+    def history_apply(self, tree: Tree, hist, times, rhs, mode="fmm"):
+        H = 0 if hist is None else hist.shape[0]
+        ddm_history_apply(self.ptr, tree.ptr, hist, times, H, rhs, _MODES[mode])
+        return rhs
+
+    def rhs(self, tree: Tree, sigma_H=0.0, sigma_h=0.0, p_f=0.0, p0=0.0, system="pressure", pf=None, out=None):
+        out = torch.empty(3 * tree.n, dtype=torch.float64, device="cuda") if out is None else out
+        ddm_rhs(self.ptr, tree.ptr, sigma_H, sigma_h, p_f, p0, _SYSTEMS[system], out, pf)
+        return out
+
+    def gmres_solve(self, tree: Tree, dt, rhs, x=None, system="pressure", restart=50, max_iters=1000, tol=1e-6,
+                    mode="fmm", raise_on_notconv=True):
+        x = torch.zeros(3 * tree.n, dtype=torch.float64, device="cuda") if x is None else x
+        info = ddm_gmres_solve(self.ptr, tree.ptr, dt, rhs, x, _SYSTEMS[system], restart, max_iters, tol,
+                               _MODES[mode], raise_on_notconv)
+        return x, info
+
+    def sif(self, tree: Tree, x, tips):
+        tips = torch.as_tensor(tips, dtype=torch.int64, device="cuda").contiguous()
+        KI = torch.empty(tips.numel(), dtype=torch.float64, device="cuda")
+        KII = torch.empty_like(KI)
+        ddm_sif(self.ptr, tree.ptr, x, tips, KI, KII)
+        return KI, KII
+
+    def profile(self, enable=True):
+        ddm_profile(self.ptr, enable)
+
+    def profile_read(self) -> dict:
+        return ddm_profile_read(self.ptr)
+
+    def close(self):
+        if self.ptr:
+            ddm_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,158 @@
+"""Seeded synthetic inputs (geometry, materials, loads, unknown vectors).
+
+This module holds none of the method's arithmetic: it only draws fracture
+geometries and vectors from fixed seeds, with the shapes, sizes and
+distributions of the workloads the paper studies (a single pressurised crack,
+randomly distributed pressurised fractures, parallel hydraulic fractures from
+a horizontal well, batches of uneven fracture sets).  The paper's own
+geometries are not published, so these stand in for them.
+
+Geometry arrays are (4, N) float64: rows x0, y0, x1, y1 (element end points);
+elements of one fracture are consecutive and run from one tip to the other.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+SEED = 1812
+
+# Rock of the synthetic workloads: G = 6 GPa, nu = 0.2, nu_u = 0.33, B = 0.8,
+# k = 1e-18 m^2, mu = 1e-3 Pa s.
+MATERIAL = {"G": 6e9, "nu": 0.2, "nu_u": 0.33, "B": 0.8, "perm": 1e-18, "visc": 1e-3}
+# Westerly granite as printed in the paper's Table 1 (c follows from k/mu).
+WESTERLY = {"G": 15e9, "nu": 0.25, "nu_u": 0.331, "B": 0.81, "perm": 4e-19, "visc": 1e-3}
+
+
+def material_tuple(m=MATERIAL):
+    return tuple(float(m[k]) for k in ("G", "nu", "nu_u", "B", "perm", "visc"))
+
+
+def discretise(p0, p1, n):
+    """n equal constant elements from p0 to p1 -> (4, n)."""
+    s = np.linspace(0.0, 1.0, n + 1)
+    x = p0[0] + s * (p1[0] - p0[0])
+    y = p0[1] + s * (p1[1] - p0[1])
+    return np.stack([x[:-1], y[:-1], x[1:], y[1:]])
+
+
+def single_crack(n=200, a=1.0, angle=0.0, center=(0.0, 0.0)):
+    """Straight crack of half-length a, n uniform elements."""
+    c, s = math.cos(angle), math.sin(angle)
+    p0 = (center[0] - a * c, center[1] - a * s)
+    p1 = (center[0] + a * c, center[1] + a * s)
+    return discretise(p0, p1, n)
+
+
+def _seg_dist(a0, a1, b0, b1):
+    """Minimum distance between segments (0 if they intersect)."""
+    def orient(p, q, r):
+        return (q[0] - p[0]) * (r[1] - p[1]) - (q[1] - p[1]) * (r[0] - p[0])
+
+    o1, o2 = orient(a0, a1, b0), orient(a0, a1, b1)
+    o3, o4 = orient(b0, b1, a0), orient(b0, b1, a1)
+    if o1 * o2 < 0 and o3 * o4 < 0:
+        return 0.0
+
+    def pt_seg(p, s0, s1):
+        d = (s1[0] - s0[0], s1[1] - s0[1])
+        L2 = d[0] * d[0] + d[1] * d[1]
+        t = 0.0 if L2 == 0 else max(0.0, min(1.0, ((p[0] - s0[0]) * d[0] + (p[1] - s0[1]) * d[1]) / L2))
+        return math.hypot(p[0] - s0[0] - t * d[0], p[1] - s0[1] - t * d[1])
+
+    return min(pt_seg(a0, b0, b1), pt_seg(a1, b0, b1), pt_seg(b0, a0, a1), pt_seg(b1, a0, a1))
+
+
+def random_fracture_segments(n_frac=200, box=200.0, lmin=2.0, lmax=10.0, elems=100, seed=SEED,
+                             max_tries=200000):
+    """Rejection-sampled non-intersecting cracks in a box x box square:
+    centre uniform (whole segment inside), length U[lmin, lmax], angle
+    U[0, pi); a candidate is rejected if it intersects an accepted crack or
+    lies closer to it than one element length of either.  Returns a list of
+    (p0, p1, n_elems)."""
+    rng = np.random.default_rng(seed)
+    segs = []
+    tries = 0
+    while len(segs) < n_frac:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("random_fracture_segments: could not place all fractures")
+        L = rng.uniform(lmin, lmax)
+        th = rng.uniform(0.0, math.pi)
+        hx, hy = 0.5 * L * math.cos(th), 0.5 * L * math.sin(th)
+        cx = rng.uniform(abs(hx), box - abs(hx))
+        cy = rng.uniform(abs(hy), box - abs(hy))
+        p0, p1 = (cx - hx, cy - hy), (cx + hx, cy + hy)
+        ok = True
+        for (q0, q1, _) in segs:
+            sep = max(L, math.hypot(q1[0] - q0[0], q1[1] - q0[1])) / elems
+            if _seg_dist(p0, p1, q0, q1) < sep:
+                ok = False
+                break
+        if ok:
+            segs.append((p0, p1, elems))
+    return segs
+
+
+def assemble(segs):
+    return np.concatenate([discretise(p0, p1, n) for (p0, p1, n) in segs], axis=1)
+
+
+def tips_of(segs):
+    """Indices of the first and last element of every fracture."""
+    out, k = [], 0
+    for (_, _, n) in segs:
+        out += [k, k + n - 1]
+        k += n
+    return np.array(out, dtype=np.int64)
+
+
+def random_fractures(n_frac=200, box=200.0, elems=100, seed=SEED):
+    segs = random_fracture_segments(n_frac, box, 2.0, 10.0, elems, seed)
+    return assemble(segs), segs
+
+
+def parallel_fractures(n_frac=10, spacing=20.0, half_length=100.0, elems=2000):
+    """Transverse fractures of a horizontal well along y: fracture k lies on
+    y = k * spacing, x in [-half_length, half_length]."""
+    segs = [((-half_length, k * spacing), (half_length, k * spacing), elems) for k in range(n_frac)]
+    return assemble(segs), segs
+
+
+def batch_problems(n_problems=512, nmin=100, nmax=20000, seed=SEED + 4):
+    """Uneven fracture sets: N log-uniform in [nmin, nmax], fracture count
+    U{1..100} capped at N/10, box side scaled with sqrt(N / 20000) * 200 m so
+    the element density stays comparable; 1-10 time steps each."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_problems):
+        N = int(round(math.exp(rng.uniform(math.log(nmin), math.log(nmax)))))
+        nf = int(min(rng.integers(1, 101), max(1, N // 10)))
+        per = max(10, N // nf)
+        box = 200.0 * math.sqrt(N / 20000.0) + 12.0
+        segs = random_fracture_segments(nf, box, 2.0, min(10.0, box / 2), per, seed=int(rng.integers(1 << 30)))
+        out.append({"xy": assemble(segs), "segs": segs, "steps": int(rng.integers(1, 11))})
+    return out
+
+
+def serving_trace(duration=60.0, rate=50.0, nmin=1000, nmax=200000, seed=SEED + 5):
+    """Poisson arrivals with N log-uniform in [nmin, nmax] and 1-100 steps."""
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > duration:
+            break
+        N = int(round(math.exp(rng.uniform(math.log(nmin), math.log(nmax)))))
+        out.append({"t": t, "N": N, "steps": int(rng.integers(1, 101)), "seed": int(rng.integers(1 << 30))})
+    return out
+
+
+def unknowns(n, seed=SEED, dd_scale=1e-4, q_scale=1e-9):
+    """Random unknown vector [Ds, Dn, Dq] with physical magnitudes."""
+    rng = np.random.default_rng(seed)
+    x = rng.standard_normal(3 * n)
+    x[:2 * n] *= dd_scale
+    x[2 * n:] *= q_scale
+    return x
