@@ -112,6 +112,8 @@ ddm_status ddm_tree_get_info(const ddm_tree *tree, ddm_tree_info *info);
 
 #define DDM_MODE_FMM 0     /* Chebyshev FMM (paper Sec. 3) */
 #define DDM_MODE_DENSE 1   /* every pair evaluated on the fly (conventional PDDM) */
+#define DDM_MODE_PRECISE 16 /* OR-ed flag: DD kernels of close pairs (< 2 element
+                               lengths) in FP64, for accurate residuals */
 
 /* d_y = [K(tau_hi) - K(tau_lo)] d_x  (paper Eqs. 2.3-2.5, left-hand sums for
  * tau_lo = 0, tau_hi = dt; one history term otherwise).  0 <= tau_lo < tau_hi.
@@ -166,10 +168,11 @@ typedef struct {
  * block-Jacobi preconditioned by each element's own 3x3 (2x2) block.
  * d_rhs: 3N doubles (rows not in the system are ignored).  d_x: 3N doubles,
  * in: initial guess (and the prescribed Dq for 2N systems), out: solution.
- * Returns DDM_ENOTCONV (x and info still written) when max_iters is reached
- * or when three restarts in a row fail to halve the true residual: the
- * pair kernels are FP32, so the true relative residual of a product is
- * floored near 1e-6 and a smaller tol may be unattainable.
+ * Mixed precision: Arnoldi steps use the FP32-pair operator; the true
+ * residual at every restart (and the convergence test) uses the operator
+ * with DDM_MODE_PRECISE.  Returns DDM_ENOTCONV (x and info still written)
+ * when max_iters is reached or three restarts in a row fail to reduce the
+ * true residual by 10%.
  * Synchronises the stream (reads the Hessenberg columns back). */
 ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const double *d_rhs,
                            double *d_x, const ddm_gmres_params *prm, ddm_gmres_info *info);

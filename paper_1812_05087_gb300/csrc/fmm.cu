@@ -315,9 +315,13 @@ __device__ __forceinline__ void q_point(const KConst<float> &k, float zx, float 
 }
 
 // near/far element integral of one source element at target m (target
-// frame coordinates); self pairs are excluded by the caller
-__device__ __forceinline__ void pair_field(const KConst<float> &k, const Win<float> &w, float mx, float my,
-                                           const SrcTile &s, float acc[4]) {
+// frame coordinates); self pairs are excluded by the caller.  PRECISE: the
+// DD part of close pairs (centre distance < 2 element lengths), whose
+// contributions nearly cancel for smooth openings, in FP64.
+template <bool PRECISE>
+__device__ __forceinline__ void pair_field(const KConst<float> &k, const KConst<double> &kd, const Win<float> &w,
+                                           const Win<double> &wd, float mx, float my, const SrcTile &s,
+                                           float acc[4], double accd[4]) {
     float cxs = 0.5f * (s.x0 + s.x1), cys = 0.5f * (s.y0 + s.y1);
     float dx = mx - cxs, dy = my - cys;
     float r2 = dx * dx + dy * dy;
@@ -331,8 +335,13 @@ __device__ __forceinline__ void pair_field(const KConst<float> &k, const Win<flo
             pot_kernel<float>(k, dx - sg * s.tx, dy - sg * s.ty, wt * Pxx, wt * Pyy, wt * Pxy, wt * s.q, w, acc);
         }
     } else {
-        disl_field<float>(k, mx - s.x0, my - s.y0, s.Dx, s.Dy, w, 1.f, acc);
-        disl_field<float>(k, mx - s.x1, my - s.y1, s.Dx, s.Dy, w, -1.f, acc);
+        if (PRECISE && r2 < 16.f * s.a * s.a) {
+            disl_field<double>(kd, (double)(mx - s.x0), (double)(my - s.y0), (double)s.Dx, (double)s.Dy, wd, 1.0, accd);
+            disl_field<double>(kd, (double)(mx - s.x1), (double)(my - s.y1), (double)s.Dx, (double)s.Dy, wd, -1.0, accd);
+        } else {
+            disl_field<float>(k, mx - s.x0, my - s.y0, s.Dx, s.Dy, w, 1.f, acc);
+            disl_field<float>(k, mx - s.x1, my - s.y1, s.Dx, s.Dy, w, -1.f, acc);
+        }
         if (s.q != 0.f) {
             for (int g = 0; g < c_gl.nn; ++g) {
                 float sg = c_gl.xn[g] * s.a, wt = c_gl.wn[g] * s.a;
@@ -343,7 +352,8 @@ __device__ __forceinline__ void pair_field(const KConst<float> &k, const Win<flo
 }
 
 constexpr int LEAF_T = 32;
-__global__ void __launch_bounds__(LEAF_T) k_leaf(KConst<float> k, Win<float> w, int64_t loff, const int32_t *cstart,
+template <bool PRECISE>
+__global__ void __launch_bounds__(LEAF_T) k_leaf(KConst<float> k, KConst<double> kd, Win<float> w, Win<double> wd, int64_t loff, const int32_t *cstart,
                                                  const int32_t *cend, const int32_t *cix, const int32_t *ciy,
                                                  const int32_t *nboff, const int32_t *nbidx, const float4 *grel,
                                                  const float4 *frame, const float4 *chg, const int64_t *perm,
@@ -389,7 +399,7 @@ __global__ void __launch_bounds__(LEAF_T) k_leaf(KConst<float> k, Win<float> w, 
                     float acc[4] = {0, 0, 0, 0};      // one tile in FP32, tiles summed in FP64
                     for (int j = 0; j < cnt; ++j) {
                         if (tile[j].idx == ti) continue;
-                        pair_field(k, w, mx, my, tile[j], acc);
+                        pair_field<PRECISE>(k, kd, w, wd, mx, my, tile[j], acc, accd);
                     }
                     for (int c = 0; c < 4; ++c) accd[c] += (double)acc[c];
                 }
@@ -421,7 +431,8 @@ __global__ void __launch_bounds__(LEAF_T) k_leaf(KConst<float> k, Win<float> w, 
 
 // -------------------------------------------------------------------- dense
 constexpr int DN_T = 128;
-__global__ void __launch_bounds__(DN_T) k_dense(KConst<float> k, Win<float> w, int64_t loff, const int32_t *elem_leaf,
+template <bool PRECISE>
+__global__ void __launch_bounds__(DN_T) k_dense(KConst<float> k, KConst<double> kd, Win<float> w, Win<double> wd, int64_t loff, const int32_t *elem_leaf,
                                                 const int32_t *cix, const int32_t *ciy, const float4 *grel,
                                                 const float4 *frame, const float4 *chg, const int64_t *perm,
                                                 float wL, int64_t N, int64_t chunk, double scale, double *y) {
@@ -463,7 +474,7 @@ __global__ void __launch_bounds__(DN_T) k_dense(KConst<float> k, Win<float> w, i
                 SrcTile s = tile[j];
                 float ox = wL * (float)(sjx[j] - ixI), oy = wL * (float)(sjy[j] - iyI);
                 s.x0 += ox; s.y0 += oy; s.x1 += ox; s.y1 += oy;
-                pair_field(k, w, mx, my, s, acc);
+                pair_field<PRECISE>(k, kd, w, wd, mx, my, s, acc, accd);
             }
             for (int c = 0; c < 4; ++c) accd[c] += (double)acc[c];
         }
@@ -541,6 +552,8 @@ ddm_status self_blocks(ddm_ctx *ctx, ddm_tree *t, double dt) {
 
 ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const double *x, double *y, int mode,
                     int accumulate, double scale) {
+    const bool precise = (mode & DDM_MODE_PRECISE) != 0;
+    mode &= ~DDM_MODE_PRECISE;
     if (!(hi > lo) || lo < 0.0) return ctx_fail(ctx, DDM_EINVAL, "matvec: need 0 <= tau_lo < tau_hi");
     ddm_status st = upload_tables(ctx);
     if (st) return st;
@@ -569,7 +582,8 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
         int64_t chunk = ((N + chunks - 1) / chunks + DN_T - 1) / DN_T * DN_T;
         chunks = (N + chunk - 1) / chunk;
         prof_begin(ctx, 7);
-        k_dense<<<dim3((unsigned)tiles, (unsigned)chunks), DN_T, 0, s>>>(kf, wf, loff, t->elem_leaf, t->cell_ix, t->cell_iy,
+        auto kdn = precise ? k_dense<true> : k_dense<false>;
+        kdn<<<dim3((unsigned)tiles, (unsigned)chunks), DN_T, 0, s>>>(kf, ctx->kd, wf, wd, loff, t->elem_leaf, t->cell_ix, t->cell_iy,
                                                                         t->g_rel, t->g_frame, t->chg, t->perm, wL, N,
                                                                         chunk, scale, y);
         prof_end(ctx, 7, 1);
@@ -611,7 +625,8 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
         prof_end(ctx, 5, L - 2);
     }
     prof_begin(ctx, 6);
-    k_leaf<<<(unsigned)nleaf, LEAF_T, 0, s>>>(kf, wf, loff, t->cell_start, t->cell_end, t->cell_ix, t->cell_iy, t->nb_off,
+    auto klf = precise ? k_leaf<true> : k_leaf<false>;
+    klf<<<(unsigned)nleaf, LEAF_T, 0, s>>>(kf, ctx->kd, wf, wd, loff, t->cell_start, t->cell_end, t->cell_ix, t->cell_iy, t->nb_off,
                                              t->nb_idx, t->g_rel, t->g_frame, t->chg, t->perm, wL, n, t->Fl, use_far, N,
                                              scale, y);
     prof_end(ctx, 6, 1);

@@ -20,9 +20,10 @@ import torch
 from . import build as _build
 
 DDM_OK, DDM_EINVAL, DDM_ENOMEM, DDM_ENOTCONV, DDM_ETIMEOUT, DDM_ECUDA, DDM_PENDING = range(7)
-MODE_FMM, MODE_DENSE = 0, 1
+MODE_FMM, MODE_DENSE, MODE_PRECISE = 0, 1, 16
 SYS_PRESSURE, SYS_IMPERMEABLE, SYS_RATE = 0, 1, 2
-_MODES = {"fmm": MODE_FMM, "dense": MODE_DENSE}
+_MODES = {"fmm": MODE_FMM, "dense": MODE_DENSE, "fmm+precise": MODE_FMM | MODE_PRECISE,
+          "dense+precise": MODE_DENSE | MODE_PRECISE}
 _SYSTEMS = {"pressure": SYS_PRESSURE, "impermeable": SYS_IMPERMEABLE, "rate": SYS_RATE}
 EXPORTS = ("ddm_create", "ddm_destroy", "ddm_last_error", "ddm_build_tree", "ddm_tree_destroy",
            "ddm_tree_get_info", "ddm_matvec", "ddm_history_apply", "ddm_rhs", "ddm_gmres_solve", "ddm_sif",
