@@ -138,6 +138,18 @@ __global__ void k_self_blocks(KConst<double> k, Win<double> w, const double *xy,
     }
 }
 
+// own element through cached 3x3 blocks (caller order)
+__global__ void k_self_apply(const double *blk, const double *x, int64_t n, double scale, int overwrite, double *y) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const double *B = blk + 9 * e;
+    double a = x[e], b = x[n + e], c = x[2 * n + e];
+    for (int r = 0; r < 3; ++r) {
+        double v = scale * (B[3 * r] * a + B[3 * r + 1] * b + B[3 * r + 2] * c);
+        if (overwrite) y[r * n + e] = v; else y[r * n + e] += v;
+    }
+}
+
 // ---------------------------------------------------------------------- P2M
 constexpr int P2M_T = 128;
 __global__ void __launch_bounds__(P2M_T) k_p2m(const int32_t *cstart, const int32_t *cend, int64_t loff,
@@ -244,46 +256,70 @@ __global__ void k_l2l(int64_t off, const int32_t *cix, const int32_t *ciy, const
 }
 
 // ---------------------------------------------------------------------- M2L
-// one block per target cell (levels >= 2), one thread per target node.
+// One block (4 warps) per target cell at levels >= 2; the warps take
+// interleaved entries of the interaction list, each lane owns NPL target
+// nodes and evaluates the kernel against all n^2 source nodes of the entry
+// (weights staged in shared memory); the four warps' sums are reduced in
+// shared memory at the end.
 struct LevelTab {
     int64_t off[DDM_MAX_LEVELS + 2];
     int L;
 };
-__global__ void k_m2l(KConst<float> k, Win<float> w, LevelTab lt, int64_t first, const int32_t *iloff,
-                      const int32_t *ilidx, const int32_t *cix, const int32_t *ciy, double h0, int n,
-                      const float *W, float *F) {
-    extern __shared__ float sw[];      // 4 n^2 source weights
+constexpr int M2L_W = 4;
+template <int NPL>
+__global__ void __launch_bounds__(32 * M2L_W) k_m2l(KConst<float> k, Win<float> w, LevelTab lt, int64_t first,
+                                                   const int32_t *iloff, const int32_t *ilidx, const int32_t *cix,
+                                                   const int32_t *ciy, double h0, int n, const float *W, float *F) {
+    extern __shared__ float sm[];            // M2L_W x 4 n^2 (weights, then partial sums)
+    int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int n2 = n * n;
+    float *sw = sm + wid * 4 * n2;
     int64_t cell = first + blockIdx.x;
     int lvl = 0;
     while (lvl < lt.L && cell >= lt.off[lvl + 1]) ++lvl;
-    int n2 = n * n;
     float h = (float)(h0 / (double)(1 << lvl)), wl = 2.f * h;
-    int m = threadIdx.x;
-    int a = m / n, b = m % n;
-    float xa = (m < n2) ? h * c_gl.cheb[a] : 0.f, yb = (m < n2) ? h * c_gl.cheb[b] : 0.f;
-    float acc[4] = {0, 0, 0, 0};
     int ixI = cix[cell], iyI = ciy[cell];
-    for (int q = iloff[cell]; q < iloff[cell + 1]; ++q) {
+    float acc[NPL][4];
+    float tx[NPL], ty[NPL];
+#pragma unroll
+    for (int r = 0; r < NPL; ++r) {
+        int m = lane + 32 * r;
+        acc[r][0] = acc[r][1] = acc[r][2] = acc[r][3] = 0.f;
+        tx[r] = m < n2 ? h * c_gl.cheb[m / n] : 0.f;
+        ty[r] = m < n2 ? h * c_gl.cheb[m % n] : 0.f;
+    }
+    for (int q = iloff[cell] + wid; q < iloff[cell + 1]; q += M2L_W) {
         int32_t J = ilidx[q];
         const float *WJ = W + (int64_t)J * 4 * n2;
-        __syncthreads();
-        for (int i = threadIdx.x; i < 4 * n2; i += blockDim.x) sw[i] = WJ[i];
-        __syncthreads();
-        if (m < n2) {
-            float ox = wl * (float)(ixI - cix[J]) + xa, oy = wl * (float)(iyI - ciy[J]) + yb;
-            for (int ap = 0; ap < n; ++ap) {
-                float zx = ox - h * c_gl.cheb[ap];
-                for (int bp = 0; bp < n; ++bp) {
-                    int mp = ap * n + bp;
-                    float zy = oy - h * c_gl.cheb[bp];
-                    pot_kernel<float>(k, zx, zy, sw[mp], sw[n2 + mp], sw[2 * n2 + mp], sw[3 * n2 + mp], w, acc);
-                }
+        __syncwarp();
+        for (int i = lane; i < 4 * n2; i += 32) sw[i] = WJ[i];
+        __syncwarp();
+        float ox = wl * (float)(ixI - cix[J]), oy = wl * (float)(iyI - ciy[J]);
+        for (int ap = 0; ap < n; ++ap) {
+            float sx = ox - h * c_gl.cheb[ap];
+            for (int bp = 0; bp < n; ++bp) {
+                int mp = ap * n + bp;
+                float sy = oy - h * c_gl.cheb[bp];
+                float w0 = sw[mp], w1 = sw[n2 + mp], w2 = sw[2 * n2 + mp], w3 = sw[3 * n2 + mp];
+#pragma unroll
+                for (int r = 0; r < NPL; ++r)
+                    if (lane + 32 * r < n2) pot_kernel<float>(k, tx[r] + sx, ty[r] + sy, w0, w1, w2, w3, w, acc[r]);
             }
         }
     }
-    if (m < n2) {
-        float *Fc = F + cell * 4 * n2;
-        for (int c = 0; c < 4; ++c) Fc[c * n2 + m] = acc[c];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < NPL; ++r) {
+        int m = lane + 32 * r;
+        if (m < n2)
+            for (int c = 0; c < 4; ++c) sm[wid * 4 * n2 + c * n2 + m] = acc[r][c];
+    }
+    __syncthreads();
+    float *Fc = F + cell * 4 * n2;
+    for (int i = threadIdx.x; i < 4 * n2; i += 32 * M2L_W) {
+        float v = 0.f;
+        for (int ww = 0; ww < M2L_W; ++ww) v += sm[ww * 4 * n2 + i];
+        Fc[i] = v;
     }
 }
 
@@ -302,11 +338,13 @@ __device__ __forceinline__ void q_point(const KConst<float> &k, float zx, float 
         if (ct <= 0.f) continue;
         float s = side == 0 ? 1.f : -1.f;
         float x2 = zx * zx, y2 = zy * zy, r2 = x2 + y2;
-        float u = r2 / (4.f * ct);
+        float ir2 = 1.f / r2;
+        float g0c = side == 0 ? w.g_hi : w.g_lo;
+        float u = r2 * g0c, iu = 4.f * ct * ir2;
         float e, F0, F1, F2;
-        f_funcs<float>(u, e, F0, F1, F2);
-        float E1 = e1<float>(u);
-        float pre = s * q * k.i4pk, nn = 2.f * F0 / r2;
+        f_funcs<float>(u, iu, e, F0, F1, F2);
+        float E1 = e1f(u, iu);
+        float pre = s * q * k.i4pk, nn = 2.f * F0 * ir2;
         acc[0] -= pre * k.eta * (nn * x2 + E1 - F0);
         acc[1] -= pre * k.eta * (nn * y2 + E1 - F0);
         acc[2] -= pre * k.eta * (nn * zx * zy);
@@ -351,82 +389,95 @@ __device__ __forceinline__ void pair_field(const KConst<float> &k, const KConst<
     }
 }
 
-constexpr int LEAF_T = 32;
+// Near field + L2P.  One warp per group of 32 consecutive (Morton-sorted)
+// targets; the warp streams the union of the neighbour leaves of its
+// targets through shared memory and every lane evaluates the same source
+// against its own target (skipping sources whose leaf is not adjacent to the
+// target's leaf, and its own element).  FP32 within a 32-source tile, FP64
+// across tiles.  Then L2P from the target's leaf expansion.
+constexpr int NEAR_W = 4;
+constexpr int NEAR_T = 32 * NEAR_W;
 template <bool PRECISE>
-__global__ void __launch_bounds__(LEAF_T) k_leaf(KConst<float> k, KConst<double> kd, Win<float> w, Win<double> wd, int64_t loff, const int32_t *cstart,
-                                                 const int32_t *cend, const int32_t *cix, const int32_t *ciy,
-                                                 const int32_t *nboff, const int32_t *nbidx, const float4 *grel,
-                                                 const float4 *frame, const float4 *chg, const int64_t *perm,
-                                                 float wL, int n, const float *F, int use_far, int64_t N,
-                                                 double scale, double *y) {
-    __shared__ SrcTile tile[LEAF_T];
-    __shared__ float sf[4 * DDM_MAX_CHEB * DDM_MAX_CHEB];
-    int leaf = blockIdx.x;
-    int64_t cell = loff + leaf;
-    int t0 = cstart[cell], t1 = cend[cell];
-    int n2 = n * n;
-    if (use_far)
-        for (int i = threadIdx.x; i < 4 * n2; i += LEAF_T) sf[i] = F[cell * 4 * n2 + i];
-    int ixI = cix[cell], iyI = ciy[cell];
-    float hL = 0.5f * wL;
-    for (int tb = t0; tb < t1; tb += LEAF_T) {
-        int ti = tb + threadIdx.x;
-        bool act = ti < t1;
-        float mx = 0, my = 0, ttx = 1, tty = 0;
-        if (act) {
-            float4 r = grel[ti], f = frame[ti];
-            mx = 0.5f * (r.x + r.z); my = 0.5f * (r.y + r.w);
-            ttx = f.x; tty = f.y;
-        }
-        double accd[4] = {0, 0, 0, 0};
-        for (int q = nboff[leaf]; q < nboff[leaf + 1]; ++q) {
-            int64_t J = loff + nbidx[q];
-            float ox = wL * (float)(cix[J] - ixI), oy = wL * (float)(ciy[J] - iyI);
-            int s0 = cstart[J], s1 = cend[J];
-            for (int sb = s0; sb < s1; sb += LEAF_T) {
-                __syncthreads();
-                int sj = sb + threadIdx.x;
-                if (sj < s1) {
-                    float4 r = grel[sj], f = frame[sj], c = chg[sj];
-                    SrcTile s;
-                    s.x0 = r.x + ox; s.y0 = r.y + oy; s.x1 = r.z + ox; s.y1 = r.w + oy;
-                    s.Dx = c.x; s.Dy = c.y; s.q = c.z; s.a = f.z; s.tx = f.x; s.ty = f.y; s.idx = sj;
-                    tile[threadIdx.x] = s;
+__global__ void __launch_bounds__(NEAR_T) k_near(KConst<float> k, KConst<double> kd, Win<float> w, Win<double> wd,
+                                                 int64_t loff, int64_t ngroups, const int32_t *goff,
+                                                 const int32_t *gleaf, const int32_t *cstart, const int32_t *cend,
+                                                 const int32_t *cix, const int32_t *ciy, const int32_t *elem_leaf,
+                                                 const float4 *grel, const float4 *frame, const float4 *chg,
+                                                 const int64_t *perm, float wL, int n, const float *F, int use_far,
+                                                 int64_t N, double scale, double *y) {
+    __shared__ SrcTile tiles[NEAR_W][32];
+    int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int64_t g = (int64_t)blockIdx.x * NEAR_W + wid;
+    if (g >= ngroups) return;                      // whole warp exits together
+    SrcTile *tile = tiles[wid];
+    int64_t ti = 32 * g + lane;
+    bool act = ti < N;
+    int32_t myleaf = act ? elem_leaf[ti] : elem_leaf[N - 1];
+    int ix = cix[loff + myleaf], iy = ciy[loff + myleaf];
+    float mx = 0.f, my = 0.f;
+    if (act) {
+        float4 r = grel[ti];
+        mx = 0.5f * (r.x + r.z);
+        my = 0.5f * (r.y + r.w);
+    }
+    double accd[4] = {0, 0, 0, 0};
+    for (int q = goff[g]; q < goff[g + 1]; ++q) {
+        int64_t J = loff + gleaf[q];
+        int jx = cix[J], jy = ciy[J];
+        bool nb = act && abs(jx - ix) <= 1 && abs(jy - iy) <= 1;
+        float ox = wL * (float)(jx - ix), oy = wL * (float)(jy - iy);
+        int s0 = cstart[J], s1 = cend[J];
+        for (int sb = s0; sb < s1; sb += 32) {
+            int ns = min(32, s1 - sb);
+            __syncwarp();
+            if (lane < ns) {
+                int sj = sb + lane;
+                float4 r = grel[sj], f = frame[sj], c = chg[sj];
+                SrcTile st;
+                st.x0 = r.x; st.y0 = r.y; st.x1 = r.z; st.y1 = r.w;
+                st.Dx = c.x; st.Dy = c.y; st.q = c.z; st.a = f.z; st.tx = f.x; st.ty = f.y; st.idx = sj;
+                tile[lane] = st;
+            }
+            __syncwarp();
+            if (nb) {
+                float acc[4] = {0, 0, 0, 0};
+                for (int j = 0; j < ns; ++j) {
+                    SrcTile st = tile[j];
+                    if (st.idx == (int)ti) continue;
+                    st.x0 += ox; st.y0 += oy; st.x1 += ox; st.y1 += oy;
+                    pair_field<PRECISE>(k, kd, w, wd, mx, my, st, acc, accd);
                 }
-                __syncthreads();
-                int cnt = min(LEAF_T, s1 - sb);
-                if (act) {
-                    float acc[4] = {0, 0, 0, 0};      // one tile in FP32, tiles summed in FP64
-                    for (int j = 0; j < cnt; ++j) {
-                        if (tile[j].idx == ti) continue;
-                        pair_field<PRECISE>(k, kd, w, wd, mx, my, tile[j], acc, accd);
-                    }
-                    for (int c = 0; c < 4; ++c) accd[c] += (double)acc[c];
-                }
+                for (int c = 0; c < 4; ++c) accd[c] += (double)acc[c];
             }
         }
-        float acc[4] = {0, 0, 0, 0};
-        if (act && use_far) {
-            float cx_[DDM_MAX_CHEB], cy_[DDM_MAX_CHEB];
-            cardinal<DDM_MAX_CHEB>(mx / hL, n, cx_);
-            cardinal<DDM_MAX_CHEB>(my / hL, n, cy_);
-            for (int a = 0; a < n; ++a)
-                for (int b = 0; b < n; ++b) {
-                    float v = cx_[a] * cy_[b];
-                    int m = a * n + b;
-                    acc[0] += v * sf[m]; acc[1] += v * sf[n2 + m]; acc[2] += v * sf[2 * n2 + m]; acc[3] += v * sf[3 * n2 + m];
-                }
-        }
-        if (act) {
-            double g[4], ss, sn;
-            for (int c = 0; c < 4; ++c) g[c] = accd[c] + (double)acc[c];
-            to_local<double>((double)ttx, (double)tty, g, ss, sn);
-            int64_t e = perm[ti];
-            y[e] += scale * ss;
-            y[N + e] += scale * sn;
-            y[2 * N + e] += scale * g[3];
-        }
     }
+    if (!act) return;
+    if (use_far) {
+        float hL = 0.5f * wL;
+        float cx_[DDM_MAX_CHEB], cy_[DDM_MAX_CHEB];
+        cardinal<DDM_MAX_CHEB>(mx / hL, n, cx_);
+        cardinal<DDM_MAX_CHEB>(my / hL, n, cy_);
+        int n2 = n * n;
+        const float *Fc = F + (loff + myleaf) * 4 * n2;
+        float f4[4] = {0, 0, 0, 0};
+        for (int a = 0; a < n; ++a) {
+            float s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+            for (int b = 0; b < n; ++b) {
+                int m = a * n + b;
+                s0 += cy_[b] * Fc[m]; s1 += cy_[b] * Fc[n2 + m];
+                s2 += cy_[b] * Fc[2 * n2 + m]; s3 += cy_[b] * Fc[3 * n2 + m];
+            }
+            f4[0] += cx_[a] * s0; f4[1] += cx_[a] * s1; f4[2] += cx_[a] * s2; f4[3] += cx_[a] * s3;
+        }
+        for (int c = 0; c < 4; ++c) accd[c] += (double)f4[c];
+    }
+    float4 f = frame[ti];
+    double ss, sn;
+    to_local<double>((double)f.x, (double)f.y, accd, ss, sn);
+    int64_t e = perm[ti];
+    y[e] += scale * ss;
+    y[N + e] += scale * sn;
+    y[2 * N + e] += scale * accd[3];
 }
 
 // -------------------------------------------------------------------- dense
@@ -536,6 +587,8 @@ static Win<T> make_win(const ddm_ctx *ctx, double lo, double hi) {
     double c = ctx->kd.c;
     w.ct_hi = (T)(c * hi);
     w.ct_lo = (T)(lo > 0.0 ? c * lo : 0.0);
+    w.g_hi = (T)(1.0 / (4.0 * c * hi));
+    w.g_lo = (T)(lo > 0.0 ? 1.0 / (4.0 * c * lo) : 0.0);
     w.elastic = lo > 0.0 ? 0 : 1;
     return w;
 }
@@ -571,7 +624,21 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
     prof_end(ctx, 0, 1);
     // own elements (FP64 closed form), caller order
     prof_begin(ctx, 1);
-    k_self<<<(N + TB - 1) / TB, TB, 0, s>>>(ctx->kd, wd, x, t->xy_caller, N, scale, accumulate ? 0 : 1, y);
+    {
+        // own-element blocks of this time window, computed once and cached
+        int slot = -1;
+        for (int k = 0; k < 4; ++k)
+            if (t->win_blk[k] && t->win_lo[k] == lo && t->win_hi[k] == hi) slot = k;
+        if (slot < 0) {
+            slot = t->win_next;
+            t->win_next = (t->win_next + 1) % 4;
+            if (!t->win_blk[slot]) DDM_CUDA_TRY(ctx, cudaMalloc(&t->win_blk[slot], 9 * N * sizeof(double)));
+            k_self_blocks<<<(N + TB - 1) / TB, TB, 0, s>>>(ctx->kd, wd, t->xy_caller, N, t->win_blk[slot]);
+            t->win_lo[slot] = lo;
+            t->win_hi[slot] = hi;
+        }
+        k_self_apply<<<(N + TB - 1) / TB, TB, 0, s>>>(t->win_blk[slot], x, N, scale, accumulate ? 0 : 1, y);
+    }
     prof_end(ctx, 1, 1);
     int L = t->depth;
     int64_t loff = t->lvl_off[L], nleaf = t->lvl_off[L + 1] - loff;
@@ -611,10 +678,18 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
         for (int l = 0; l <= L + 1 && l < DDM_MAX_LEVELS + 2; ++l) lt.off[l] = t->lvl_off[l];
         lt.L = L;
         int64_t first = t->lvl_off[2], ncm = t->lvl_off[L + 1] - first;
-        int thr = ((n2 + 31) / 32) * 32;
+        int npl = (n2 + 31) / 32;
+        size_t smb = (size_t)M2L_W * 4 * n2 * sizeof(float);
         prof_begin(ctx, 4);
-        k_m2l<<<(unsigned)ncm, thr, 4 * n2 * sizeof(float), s>>>(kf, wf, lt, first, t->il_off, t->il_idx, t->cell_ix,
-                                                                t->cell_iy, t->h0, n, t->W, t->Fl);
+#define M2L_LAUNCH(NPL)                                                                                       \
+    k_m2l<NPL><<<(unsigned)ncm, 32 * M2L_W, smb, s>>>(kf, wf, lt, first, t->il_off, t->il_idx, t->cell_ix,    \
+                                                      t->cell_iy, t->h0, n, t->W, t->Fl)
+        if (npl <= 1) M2L_LAUNCH(1);
+        else if (npl <= 2) M2L_LAUNCH(2);
+        else if (npl <= 3) M2L_LAUNCH(3);
+        else if (npl <= 5) M2L_LAUNCH(5);
+        else M2L_LAUNCH(8);
+#undef M2L_LAUNCH
         prof_end(ctx, 4, 1);
         // downward pass
         prof_begin(ctx, 5);
@@ -625,10 +700,10 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
         prof_end(ctx, 5, L - 2);
     }
     prof_begin(ctx, 6);
-    auto klf = precise ? k_leaf<true> : k_leaf<false>;
-    klf<<<(unsigned)nleaf, LEAF_T, 0, s>>>(kf, ctx->kd, wf, wd, loff, t->cell_start, t->cell_end, t->cell_ix, t->cell_iy, t->nb_off,
-                                             t->nb_idx, t->g_rel, t->g_frame, t->chg, t->perm, wL, n, t->Fl, use_far, N,
-                                             scale, y);
+    auto knr = precise ? k_near<true> : k_near<false>;
+    knr<<<(unsigned)((t->n_groups + NEAR_W - 1) / NEAR_W), NEAR_T, 0, s>>>(
+        kf, ctx->kd, wf, wd, loff, t->n_groups, t->grp_off, t->grp_leaf, t->cell_start, t->cell_end, t->cell_ix,
+        t->cell_iy, t->elem_leaf, t->g_rel, t->g_frame, t->chg, t->perm, wL, n, t->Fl, use_far, N, scale, y);
     prof_end(ctx, 6, 1);
     DDM_CUDA_TRY(ctx, cudaGetLastError());
     return DDM_OK;

@@ -30,6 +30,7 @@ struct KConst {
 template <class T>
 struct Win {
     T ct_hi, ct_lo;
+    T g_hi, g_lo;      // 1/(4 ct_*) (0 when ct_* = 0)
     int elastic;
 };
 
@@ -49,6 +50,8 @@ struct ddm_tree {
     int32_t *il_off, *il_idx;  // interaction lists (CSR over cells)
     int32_t *nb_off, *nb_idx;  // neighbour lists of leaves incl. self (CSR over leaves, leaf-local)
     int32_t *elem_leaf;        // sorted element -> leaf index (leaf-local)
+    int64_t n_groups;          // groups of 32 consecutive sorted targets
+    int32_t *grp_off, *grp_leaf; // per group: union of the neighbour leaves of its targets (CSR, leaf-local)
     // sorted element geometry, FP32 relative to the element's leaf centre
     float4 *g_rel;             // (x0, y0, x1, y1) rel. to leaf centre
     float4 *g_frame;           // (tx, ty, half-length, 0)
@@ -56,6 +59,9 @@ struct ddm_tree {
     double *xy_caller;         // 4 x n FP64 end points, caller order (copy of the input)
     double *self_blk;          // 9 x n FP64 own-element blocks at the last dt (cache)
     double self_dt;            // dt of the cached self blocks (<0: none)
+    double *win_blk[4] = {nullptr, nullptr, nullptr, nullptr};   // own-element blocks per time window
+    double win_lo[4] = {-1, -1, -1, -1}, win_hi[4] = {-1, -1, -1, -1};
+    int win_next = 0;
     int64_t n_m2l, n_p2p;
     // per-tree workspaces
     float *W;                  // multipole weights, 4 n^2 per cell

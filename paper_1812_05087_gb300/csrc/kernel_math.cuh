@@ -44,8 +44,20 @@ template <> struct Prec<float> { static constexpr int NS = 11; static constexpr 
 template <> struct Prec<double> { static constexpr int NS = 22; static constexpr int NE = 40; static constexpr int NC = 60; };
 
 // e^-u, F, F', F'' with F(u) = (1 - e^-u)/u.
+// Above U_BIG e^-u is below the rounding of the algebraic tails (1/u)
+template <class T> struct Big;
+template <> struct Big<float> { static constexpr float U = 30.f; };
+template <> struct Big<double> { static constexpr double U = 70.0; };
+
 template <class T>
-DEV void f_funcs(T u, T &e, T &F0, T &F1, T &F2) {
+DEV void f_funcs(T u, T iu, T &e, T &F0, T &F1, T &F2) {
+    if (u > Big<T>::U) {
+        e = T(0);
+        F0 = iu;
+        F1 = -iu * iu;
+        F2 = T(2) * iu * iu * iu;
+        return;
+    }
     e = dexp<T>(-u);
     if (u < T(1)) {
         // F = sum (-u)^k/(k+1)!, F' = sum (k+1)(-1)^(k+1) u^k/(k+2)!,
@@ -65,7 +77,6 @@ DEV void f_funcs(T u, T &e, T &F0, T &F1, T &F2) {
         }
         F0 = a; F1 = b; F2 = c;
     } else {
-        T iu = T(1) / u;
         F0 = (T(1) - e) * iu;
         F1 = (e - F0) * iu;
         F2 = -(e + T(2) * F1) * iu;
@@ -74,7 +85,7 @@ DEV void f_funcs(T u, T &e, T &F0, T &F1, T &F2) {
 
 // ghat = (1 - F)/u and its two derivatives; P2h = P(2,u)/u^2.
 template <class T>
-DEV void g_funcs(T u, T e, T F0, T F1, T F2, T &g0, T &g1, T &g2, T &p2h) {
+DEV void g_funcs(T u, T iu, T e, T F0, T F1, T F2, T &g0, T &g1, T &g2, T &p2h) {
     if (u < T(1)) {
         // ghat = sum (-1)^k u^k/(k+2)!, ghat' = sum_{k>=1} (-1)^k k u^(k-1)/(k+2)!,
         // ghat'' = sum_{k>=2} (-1)^k k(k-1) u^(k-2)/(k+2)!,
@@ -94,7 +105,6 @@ DEV void g_funcs(T u, T e, T F0, T F1, T F2, T &g0, T &g1, T &g2, T &p2h) {
         }
         g0 = a; g1 = b; g2 = c; p2h = d;
     } else {
-        T iu = T(1) / u;
         g0 = (T(1) - F0) * iu;
         g1 = -(F1 + g0) * iu;
         g2 = -(F2 + T(2) * g1) * iu;
@@ -119,25 +129,59 @@ DEV T e1(T u) {
         s *= u;   // Ein(u)
         return s - dlog<T>(u) - T(0.57721566490153286061);
     }
-    if (u > T(700)) return T(0);
+    if (u > Big<T>::U) return T(0);
     T f = u + T(2 * Prec<T>::NC + 1);
 #pragma unroll
     for (int k = Prec<T>::NC; k >= 1; --k) f = u + T(2 * k - 1) - T(k * k) / f;
     return dexp<T>(-u) / f;
 }
 
+// FP32: Ein series below 1; for 1 <= u <= 30, E1 = e^-u/u * h(1/u) with
+// h(t) = u e^u E1(u) as a degree-12 Chebyshev series in
+// x = 2 (t - 1/30)/(1 - 1/30) - 1 (Clenshaw; coefficients from
+// csrc/fit_e1.py, relative error < 3e-7); 0 above 30.
+__constant__ float c_e1cheb[13] = {7.479364044e-01f, -1.782856521e-01f, 3.253978214e-02f, -7.307559064e-03f,
+                                   1.867943905e-03f, -5.230081780e-04f, 1.568588335e-04f, -4.967373770e-05f,
+                                   1.644605689e-05f, -5.651932686e-06f, 2.005327778e-06f, -7.314854142e-07f,
+                                   2.734071549e-07f};
+DEV float e1f(float u, float iu) {
+    if (u < 1.f) {
+        float s = 0.f;
+#pragma unroll
+        for (int k = 10; k >= 1; --k) {
+            float fk = 1.f;
+#pragma unroll
+            for (int j = 2; j <= k; ++j) fk *= (float)j;
+            s = s * u + ((k & 1) ? 1.f : -1.f) / ((float)k * fk);
+        }
+        return s * u - __logf(u) - 0.5772156649f;
+    }
+    if (u > 30.f) return 0.f;
+    float x = (iu - 1.f / 30.f) * (2.f / (1.f - 1.f / 30.f)) - 1.f;
+    float b1 = 0.f, b2 = 0.f;
+#pragma unroll
+    for (int k = 12; k >= 1; --k) {
+        float t = 2.f * x * b1 - b2 + c_e1cheb[k];
+        b2 = b1;
+        b1 = t;
+    }
+    return __expf(-u) * iu * (x * b1 - b2 + c_e1cheb[0]);
+}
+template <class T> DEV T e1x(T u, T iu) { return e1<T>(u); }
+template <> DEV float e1x<float>(float u, float iu) { return e1f(u, iu); }
+
 // ---------------------------------------------------------------------------
 // point kernel, potency form
 // ---------------------------------------------------------------------------
+// g0c = 1/(4ct), ct4 = 4ct, ir2 = 1/r^2 (precomputed by the caller)
 template <class T>
-DEV void pot_transient(const KConst<T> &k, T x, T y, T Pxx, T Pyy, T Pxy, T q, T ct, T s,
+DEV void pot_transient(const KConst<T> &k, T x, T y, T ir2, T Pxx, T Pyy, T Pxy, T q, T g0c, T ct4, T s,
                        T acc[4]) {
     T x2 = x * x, y2 = y * y, xy = x * y, r2 = x2 + y2;
-    T g0c = T(1) / (T(4) * ct);                // gamma0 = 1/(4ct)
-    T u = r2 * g0c;
+    T u = r2 * g0c, iu = ct4 * ir2;
     T e, F0, F1, F2, gh0, gh1, gh2, p2h;
-    f_funcs<T>(u, e, F0, F1, F2);
-    g_funcs<T>(u, e, F0, F1, F2, gh0, gh1, gh2, p2h);
+    f_funcs<T>(u, iu, e, F0, F1, F2);
+    g_funcs<T>(u, iu, e, F0, F1, F2, gh0, gh1, gh2, p2h);
     T dP = Pyy - Pxx, trP = Pxx + Pyy;
     T a = dP * (x2 - y2) - T(4) * Pxy * xy;
     T ax = T(2) * dP * x - T(4) * Pxy * y;
@@ -154,9 +198,9 @@ DEV void pot_transient(const KConst<T> &k, T x, T y, T Pxx, T Pyy, T Pxy, T q, T
     acc[2] += sk * pxy;
     acc[3] -= s * k.aS * k.Ce * (a * g0c * g0c * p2h - trP * g0c * e);
     if (q != T(0)) {
-        T E1 = e1<T>(u);
+        T E1 = e1x<T>(u, iu);
         T pre = s * q * k.i4pk;
-        T nn = T(2) * F0 / r2;
+        T nn = T(2) * F0 * ir2;
         acc[0] -= pre * k.eta * (nn * x2 + E1 - F0);
         acc[1] -= pre * k.eta * (nn * y2 + E1 - F0);
         acc[2] -= pre * k.eta * (nn * xy);
@@ -167,9 +211,9 @@ DEV void pot_transient(const KConst<T> &k, T x, T y, T Pxx, T Pyy, T Pxy, T q, T
 template <class T>
 DEV void pot_kernel(const KConst<T> &k, T x, T y, T Pxx, T Pyy, T Pxy, T q, const Win<T> &w,
                     T acc[4]) {
+    T ir2 = T(1) / (x * x + y * y);
     if (w.elastic) {
-        T x2 = x * x, y2 = y * y, xy = x * y, r2 = x2 + y2;
-        T ir2 = T(1) / r2;
+        T x2 = x * x, y2 = y * y, xy = x * y;
         T C = k.Cel * ir2 * ir2 * ir2;
         T A1 = x2 * x2, B1 = y2 * y2, Cm = x2 * y2;
         acc[0] -= C * (Pxx * (T(3) * A1 - T(6) * Cm - B1) + Pyy * (-A1 + T(6) * Cm - B1) +
@@ -179,20 +223,20 @@ DEV void pot_kernel(const KConst<T> &k, T x, T y, T Pxx, T Pyy, T Pxy, T q, cons
         acc[2] += C * (Pxx * xy * (-T(6) * x2 + T(2) * y2) + T(2) * Pxy * (A1 - T(6) * Cm + B1) +
                        Pyy * xy * (T(2) * x2 - T(6) * y2));
     }
-    pot_transient<T>(k, x, y, Pxx, Pyy, Pxy, q, w.ct_hi, T(1), acc);
-    if (w.ct_lo > T(0)) pot_transient<T>(k, x, y, Pxx, Pyy, Pxy, q, w.ct_lo, T(-1), acc);
+    pot_transient<T>(k, x, y, ir2, Pxx, Pyy, Pxy, q, w.g_hi, T(4) * w.ct_hi, T(1), acc);
+    if (w.ct_lo > T(0)) pot_transient<T>(k, x, y, ir2, Pxx, Pyy, Pxy, q, w.g_lo, T(4) * w.ct_lo, T(-1), acc);
 }
 
 // ---------------------------------------------------------------------------
 // half-line DD (edge dislocation), DD vector (Dx, Dy)
 // ---------------------------------------------------------------------------
 template <class T>
-DEV void disl_transient(const KConst<T> &k, T zx, T zy, T Dx, T Dy, T ct, T s, T acc[4]) {
+DEV void disl_transient(const KConst<T> &k, T zx, T zy, T ir2, T Dx, T Dy, T g0c, T ct4, T s, T acc[4]) {
     T r2 = zx * zx + zy * zy;
-    T beta = T(1) / (T(2) * ct);
-    T u = T(0.5) * r2 * beta;
+    T beta = T(2) * g0c;                        // 1/(2ct)
+    T u = r2 * g0c, iu = ct4 * ir2;
     T e, F0, F1, F2;
-    f_funcs<T>(u, e, F0, F1, F2);
+    f_funcs<T>(u, iu, e, F0, F1, F2);
     T V1 = F0 + F1, V2 = F1 + F2;
     T l = Dx * zy - Dy * zx, lx = -Dy, ly = Dx;
     T cm = -k.K2 * beta;
@@ -204,20 +248,21 @@ DEV void disl_transient(const KConst<T> &k, T zx, T zy, T Dx, T Dy, T ct, T s, T
     acc[0] -= sk * pyy;
     acc[1] -= sk * pxx;
     acc[2] += sk * pxy;
-    acc[3] -= s * k.aS * k.Ce * l / r2 * (u * F0);      // 1 - e^-u = u F(u)
+    acc[3] -= s * k.aS * k.Ce * l * ir2 * (u * F0);      // 1 - e^-u = u F(u)
 }
 
 template <class T>
 DEV void disl_field(const KConst<T> &k, T zx, T zy, T Dx, T Dy, const Win<T> &w, T s, T acc[4]) {
+    T ir2 = T(1) / (zx * zx + zy * zy);
     if (w.elastic) {
-        T x2 = zx * zx, y2 = zy * zy, r2 = x2 + y2;
-        T C = s * k.Cel / (r2 * r2);
+        T x2 = zx * zx, y2 = zy * zy;
+        T C = s * k.Cel * ir2 * ir2;
         acc[0] += C * (Dx * zy * (T(3) * x2 + y2) - Dy * zx * (x2 - y2));
         acc[1] -= C * (Dx * zy * (x2 - y2) + Dy * zx * (x2 + T(3) * y2));
         acc[2] -= C * (x2 - y2) * (Dx * zx + Dy * zy);
     }
-    disl_transient<T>(k, zx, zy, Dx, Dy, w.ct_hi, s, acc);
-    if (w.ct_lo > T(0)) disl_transient<T>(k, zx, zy, Dx, Dy, w.ct_lo, -s, acc);
+    disl_transient<T>(k, zx, zy, ir2, Dx, Dy, w.g_hi, T(4) * w.ct_hi, s, acc);
+    if (w.ct_lo > T(0)) disl_transient<T>(k, zx, zy, ir2, Dx, Dy, w.g_lo, T(4) * w.ct_lo, -s, acc);
 }
 
 // rotate a global (sxx, syy, sxy) into the target frame: (sigma_s, sigma_n)

@@ -316,6 +316,31 @@ __global__ void k_geom(const double *xy, int64_t n, const int32_t *idx, const in
     g_frame[i] = make_float4((float)((bx - ax) / L), (float)((by - ay) / L), (float)(0.5 * L), 0.f);
 }
 
+// union of the neighbour leaves of 32 consecutive sorted targets
+__global__ void k_groups(const int32_t *elem_leaf, int64_t n, int64_t ngroups, const int32_t *nboff,
+                         const int32_t *nbidx, const int32_t *goff, int32_t *gleaf, int32_t *cnt) {
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= ngroups) return;
+    int32_t set[32 * 9];
+    int m = 0, last = -1;
+    int64_t i1 = min(n, 32 * g + 32);
+    for (int64_t i = 32 * g; i < i1; ++i) {
+        int32_t lf = elem_leaf[i];
+        if (lf == last) continue;
+        last = lf;
+        for (int k = nboff[lf]; k < nboff[lf + 1]; ++k) {
+            int32_t j = nbidx[k];
+            bool seen = false;
+            for (int q = 0; q < m; ++q)
+                if (set[q] == j) { seen = true; break; }
+            if (!seen && m < 32 * 9) set[m++] = j;
+        }
+    }
+    if (cnt) cnt[g] = m;
+    if (gleaf)
+        for (int q = 0; q < m; ++q) gleaf[goff[g] + q] = set[q];
+}
+
 __global__ void k_p2p_count(const int32_t *cstart, const int32_t *cend, int64_t loff, int64_t nleaf,
                             const int32_t *nboff, const int32_t *nbidx, unsigned long long *tot) {
     int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -339,10 +364,12 @@ __global__ void k_p2p_count(const int32_t *cstart, const int32_t *cend, int64_t 
 
 void tree_free(ddm_tree *t) {
     if (!t) return;
-    void *ps[] = {t->perm, t->cell_key, t->cell_ix, t->cell_iy, t->cell_start, t->cell_end, t->cell_parent,
+    void *ps[] = {t->grp_off, t->grp_leaf, t->perm, t->cell_key, t->cell_ix, t->cell_iy, t->cell_start, t->cell_end, t->cell_parent,
                   t->il_off, t->il_idx, t->nb_off, t->nb_idx, t->elem_leaf, t->g_rel, t->g_frame,
                   t->xy_sorted, t->xy_caller, t->self_blk, t->W, t->Fl, t->chg};
     for (void *p : ps)
+        if (p) cudaFree(p);
+    for (double *p : t->win_blk)
         if (p) cudaFree(p);
     delete t;
 }
@@ -499,6 +526,20 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
     double wl = 2.0 * h0 / (double)side;
     k_geom<<<nbk, TB, 0, st>>>(d_xy, n, idx, t->elem_leaf, t->cell_ix, t->cell_iy, loff, X0, Y0, wl, t->perm,
                               t->g_rel, t->g_frame, t->xy_sorted); ++tl_launches;
+    // target groups for the near field
+    {
+        int64_t ng = (n + 31) / 32;
+        t->n_groups = ng;
+        int32_t *gc = S.get<int32_t>(ng + 1);
+        TRY(S.err);
+        TRY(cudaMalloc(&t->grp_off, (ng + 1) * sizeof(int32_t)));
+        k_groups<<<(ng + 127) / 128, 128, 0, st>>>(t->elem_leaf, n, ng, t->nb_off, t->nb_idx, nullptr, nullptr, gc); ++tl_launches;
+        int32_t gtot;
+        TRY(scan_excl(S, st, gc, t->grp_off, ng, &gtot));
+        TRY(cudaMemcpyAsync(t->grp_off + ng, &gtot, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        TRY(cudaMalloc(&t->grp_leaf, std::max(gtot, 1) * sizeof(int32_t)));
+        k_groups<<<(ng + 127) / 128, 128, 0, st>>>(t->elem_leaf, n, ng, t->nb_off, t->nb_idx, t->grp_off, t->grp_leaf, nullptr); ++tl_launches;
+    }
     unsigned long long *ptot = S.get<unsigned long long>(1);
     TRY(S.err);
     TRY(cudaMemsetAsync(ptot, 0, sizeof(unsigned long long), st));
