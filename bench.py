@@ -39,12 +39,7 @@ METRIC = "FMM matvec Melem/s & solves/s vs dense GPU DDM at <=1e-3 rel err; p50/
 WORKLOAD = "random pressurised fractures: 200 cracks x 100 elements (N=20000), dt=10 s"
 DT = 10.0
 LOADS = dict(sigma_H=30e6, sigma_h=25e6, p_f=10e6, p0=0.0)
-# FP32 operations of one point-kernel evaluation between two Chebyshev
-# nodes in M2L (elastic potency kernel, poroelastic transient with both
-# series branches' common path, fluid source, 4x4 accumulation), counted from
-# kernel_math.cuh; see DESIGN.md "roofline".
-M2L_FLOP_PER_NODE_PAIR = 220
-P2P_FLOP_PER_PAIR = 520
+STAGE_KERNEL = {"leaf": "k_near", "m2l": "k_m2l_gemm"}
 
 
 def parse():
@@ -126,6 +121,20 @@ def peaks():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         return {}
+
+
+def ncu_record():
+    """DRAM traffic / flop counts from the committed ncu capture, valid only
+    while the kernel sources are unchanged."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+    except Exception:
+        return None, False
+    csrc = os.path.join(ROOT, "paper_1812_05087_gb300", "csrc")
+    ok = all(hashlib.sha1(open(os.path.join(csrc, f), "rb").read()).hexdigest() == h
+             for f, h in rec["sources_sha1"].items())
+    return rec, ok
 
 
 def alu_peak_tflops(sm_mhz):
@@ -283,23 +292,27 @@ def main():
     ms_e2e = float(np.mean(t_e2e))
 
     # ---------------- roofline of the dominant kernel
-    st = {k: v for k, v in stages.items() if v[1] > 0}
+    st = {k: v for k, v in stages.items() if v[1] > 0 and k in STAGE_KERNEL}
     dom = max(st, key=lambda k: st[k][0])
     dom_ms = st[dom][0] / max(1, st[dom][1])
     n = args.n_cheb
     clocks = clk.summary()
     sm_mhz = clocks["sm_mhz"] or peaks().get("sm_max_mhz", 2070.0)
+    rec, rec_ok = ncu_record()
+    kname = STAGE_KERNEL[dom]
     if dom == "m2l":
-        flop = info["n_m2l_pairs"] * n ** 4 * M2L_FLOP_PER_NODE_PAIR
-    elif dom == "leaf":
-        flop = info["n_p2p_pairs"] * P2P_FLOP_PER_PAIR
+        flop = 2.0 * (4 * n * n) ** 2 * info["n_m2l_pairs"]
+        flop_note = "2 (4n^2)^2 flops per interaction pair"
     else:
-        flop = None
-    achieved = flop / (dom_ms * 1e-3) / 1e12 if flop else None
+        fpp = rec[kname]["fp32_flops_per_pair"] if rec else 604
+        flop = float(info["n_p2p_pairs"]) * fpp
+        flop_note = f"{fpp} FP32 flops per near pair (ncu-measured thread-level FP32 ops of k_near)"
+    achieved = flop / (dom_ms * 1e-3) / 1e12
     peak = alu_peak_tflops(sm_mhz)
-    roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak if achieved else None, "traffic": None,
-            "peak_note": f"FP32 FMA peak 152 SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz (median SM clock under load)",
+    roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": (rec[kname]["dram_bytes"] if (rec and rec_ok) else None),
+            "flops_per_launch": flop, "flop_note": flop_note,
+            "peak_note": f"FP32 peak 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (median SM clock sampled under load)",
             "ms_per_launch": dom_ms}
 
     # ---------------- accuracy + CPU baseline (oracle on sampled rows)

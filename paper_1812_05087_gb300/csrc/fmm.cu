@@ -323,6 +323,94 @@ __global__ void __launch_bounds__(32 * M2L_W) k_m2l(KConst<float> k, Win<float> 
     }
 }
 
+// Batched M2L (paper Sec. 3.3 M2L over interaction lists).  The kernel
+// between the Chebyshev nodes of two cells depends only on the level, the
+// cell offset and the time window, so one (4n^2 x 4n^2) operator per
+// (level, offset) is built once per window; the interaction pairs of one
+// (level, offset) group then form a GEMM  G = K_{l,o} [W_J1 ... W_JP],
+// whose columns are added to the targets' local expansions.
+// Operator layout: row (c_out * n^2 + m), column (c_in * n^2 + m').
+__global__ void k_m2l_ops(KConst<float> k, Win<float> w, int L, double h0, int n, const int32_t *koff, float *ops) {
+    int key = blockIdx.y;
+    int lvl = key / 49, o = key % 49, dx = o / 7 - 3, dy = o % 7 - 3;
+    if (lvl < 2 || (abs(dx) <= 1 && abs(dy) <= 1) || koff[key + 1] == koff[key]) return;
+    int n2 = n * n;
+    int np = blockIdx.x * blockDim.x + threadIdx.x;      // node pair (m, m')
+    if (np >= n2 * n2) return;
+    int m = np / n2, mp = np % n2;
+    float h = (float)(h0 / (double)(1 << lvl));
+    float zx = 2.f * h * dx + h * (c_gl.cheb[m / n] - c_gl.cheb[mp / n]);
+    float zy = 2.f * h * dy + h * (c_gl.cheb[m % n] - c_gl.cheb[mp % n]);
+    float *K = ops + (int64_t)key * 16 * n2 * n2;
+    int ld = 4 * n2;
+    for (int ci = 0; ci < 4; ++ci) {
+        float a[4] = {0, 0, 0, 0};
+        pot_kernel<float>(k, zx, zy, ci == 0, ci == 1, ci == 2, ci == 3, w, a);
+        for (int co = 0; co < 4; ++co) K[(int64_t)(co * n2 + m) * ld + ci * n2 + mp] = a[co];
+    }
+}
+
+// C[BM x BN] tile of K (rows) x W columns of one key group; BK-deep steps.
+constexpr int GM_BM = 64, GM_BN = 64, GM_BK = 16;
+__global__ void __launch_bounds__(256) k_m2l_gemm(const int32_t *koff, const int2 *pairs, int n, const float *ops,
+                                                  const float *W, float *F, int keys_first) {
+    __shared__ float sK[GM_BK][GM_BM + 4];
+    __shared__ float sB[GM_BK][GM_BN + 4];
+    __shared__ int sI[GM_BN], sJ[GM_BN];
+    int key = keys_first + blockIdx.z;
+    int p0 = koff[key] + blockIdx.y * GM_BN, p1 = koff[key + 1];
+    if (p0 >= p1) return;
+    int n2 = n * n, ld = 4 * n2;
+    int r0 = blockIdx.x * GM_BM;
+    if (r0 >= ld) return;
+    const float *K = ops + (int64_t)key * 16 * n2 * n2;
+    int tid = threadIdx.x;
+    if (tid < GM_BN) {
+        int p = p0 + tid;
+        sI[tid] = p < p1 ? pairs[p].x : -1;
+        sJ[tid] = p < p1 ? pairs[p].y : -1;
+    }
+    __syncthreads();
+    int tr = (tid / 16) * 4, tc = (tid % 16) * 4;    // 4x4 micro tile
+    float acc[4][4] = {{0}};
+    for (int k0 = 0; k0 < ld; k0 += GM_BK) {
+        // K tile: BM rows x BK cols  (coalesced along k)
+        for (int i = tid; i < GM_BM * GM_BK; i += 256) {
+            int rr = i / GM_BK, kk = i % GM_BK;
+            int row = r0 + rr, col = k0 + kk;
+            sK[kk][rr] = (row < ld && col < ld) ? K[(int64_t)row * ld + col] : 0.f;
+        }
+        // B tile: BK rows x BN pairs (column j = W of source J)
+        for (int i = tid; i < GM_BK * GM_BN; i += 256) {
+            int kk = i / GM_BN, jj = i % GM_BN;
+            int J = sJ[jj], col = k0 + kk;
+            sB[kk][jj] = (J >= 0 && col < ld) ? W[(int64_t)J * ld + col] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GM_BK; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) { a[i] = sK[kk][tr + i]; b[i] = sB[kk][tc + i]; }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        int I = sI[tc + j];
+        if (I < 0) continue;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            int row = r0 + tr + i;
+            if (row < ld) atomicAdd(&F[(int64_t)I * ld + row], acc[i][j]);
+        }
+    }
+}
+
 // ----------------------------------------------------------- leaf L2P + P2P
 struct SrcTile {
     float x0, y0, x1, y1;      // end points in the target leaf frame
@@ -389,13 +477,14 @@ __device__ __forceinline__ void pair_field(const KConst<float> &k, const KConst<
     }
 }
 
-// Near field + L2P.  One warp per group of 32 consecutive (Morton-sorted)
-// targets; the warp streams the union of the neighbour leaves of its
-// targets through shared memory and every lane evaluates the same source
-// against its own target (skipping sources whose leaf is not adjacent to the
-// target's leaf, and its own element).  FP32 within a 32-source tile, FP64
-// across tiles.  Then L2P from the target's leaf expansion.
-constexpr int NEAR_W = 4;
+// Near field + L2P.  One block per group of 32 consecutive (Morton-sorted)
+// targets; the block's NEAR_W warps split the union of the neighbour leaves
+// of those targets, stream each leaf through shared memory, and every lane
+// evaluates the same source against its own target (skipping sources whose
+// leaf is not adjacent to the target's leaf, and its own element).  FP32
+// within a 32-source tile, FP64 across tiles; the warps' sums are reduced in
+// shared memory, then warp 0 adds L2P from the target leaf's expansion.
+constexpr int NEAR_W = 8;
 constexpr int NEAR_T = 32 * NEAR_W;
 template <bool PRECISE>
 __global__ void __launch_bounds__(NEAR_T) k_near(KConst<float> k, KConst<double> kd, Win<float> w, Win<double> wd,
@@ -406,9 +495,9 @@ __global__ void __launch_bounds__(NEAR_T) k_near(KConst<float> k, KConst<double>
                                                  const int64_t *perm, float wL, int n, const float *F, int use_far,
                                                  int64_t N, double scale, double *y) {
     __shared__ SrcTile tiles[NEAR_W][32];
+    __shared__ double red[NEAR_W][4][32];
     int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int64_t g = (int64_t)blockIdx.x * NEAR_W + wid;
-    if (g >= ngroups) return;                      // whole warp exits together
+    int64_t g = blockIdx.x;
     SrcTile *tile = tiles[wid];
     int64_t ti = 32 * g + lane;
     bool act = ti < N;
@@ -421,7 +510,7 @@ __global__ void __launch_bounds__(NEAR_T) k_near(KConst<float> k, KConst<double>
         my = 0.5f * (r.y + r.w);
     }
     double accd[4] = {0, 0, 0, 0};
-    for (int q = goff[g]; q < goff[g + 1]; ++q) {
+    for (int q = goff[g] + wid; q < goff[g + 1]; q += NEAR_W) {
         int64_t J = loff + gleaf[q];
         int jx = cix[J], jy = ciy[J];
         bool nb = act && abs(jx - ix) <= 1 && abs(jy - iy) <= 1;
@@ -451,7 +540,14 @@ __global__ void __launch_bounds__(NEAR_T) k_near(KConst<float> k, KConst<double>
             }
         }
     }
-    if (!act) return;
+    for (int c = 0; c < 4; ++c) red[wid][c][lane] = accd[c];
+    __syncthreads();
+    if (wid != 0 || !act) return;
+    for (int c = 0; c < 4; ++c) {
+        double v = 0.0;
+        for (int ww = 0; ww < NEAR_W; ++ww) v += red[ww][c][lane];
+        accd[c] = v;
+    }
     if (use_far) {
         float hL = 0.5f * wL;
         float cx_[DDM_MAX_CHEB], cy_[DDM_MAX_CHEB];
@@ -678,18 +774,34 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
         for (int l = 0; l <= L + 1 && l < DDM_MAX_LEVELS + 2; ++l) lt.off[l] = t->lvl_off[l];
         lt.L = L;
         int64_t first = t->lvl_off[2], ncm = t->lvl_off[L + 1] - first;
-        int npl = (n2 + 31) / 32;
-        size_t smb = (size_t)M2L_W * 4 * n2 * sizeof(float);
         prof_begin(ctx, 4);
-#define M2L_LAUNCH(NPL)                                                                                       \
-    k_m2l<NPL><<<(unsigned)ncm, 32 * M2L_W, smb, s>>>(kf, wf, lt, first, t->il_off, t->il_idx, t->cell_ix,    \
-                                                      t->cell_iy, t->h0, n, t->W, t->Fl)
-        if (npl <= 1) M2L_LAUNCH(1);
-        else if (npl <= 2) M2L_LAUNCH(2);
-        else if (npl <= 3) M2L_LAUNCH(3);
-        else if (npl <= 5) M2L_LAUNCH(5);
-        else M2L_LAUNCH(8);
-#undef M2L_LAUNCH
+        {
+            int nk = t->n_keys;
+            size_t opsz = (size_t)nk * 16 * n2 * n2;
+            if (t->ops_n != n || !t->m2l_ops) {
+                if (t->m2l_ops) cudaFree(t->m2l_ops);
+                t->m2l_ops = nullptr;
+                DDM_CUDA_TRY(ctx, cudaMalloc(&t->m2l_ops, opsz * sizeof(float)));
+                t->ops_n = n;
+                t->ops_lo = t->ops_hi = -1.0;
+            }
+            if (t->ops_lo != lo || t->ops_hi != hi) {
+                dim3 g((unsigned)((n2 * n2 + 127) / 128), (unsigned)nk);
+                k_m2l_ops<<<g, 128, 0, s>>>(kf, wf, L, t->h0, n, t->mk_off, t->m2l_ops);
+                t->ops_lo = lo;
+                t->ops_hi = hi;
+                prof_end(ctx, 4, 1);
+                prof_begin(ctx, 4);
+            }
+            DDM_CUDA_TRY(ctx, cudaMemsetAsync(t->Fl, 0, (size_t)t->n_cells * 4 * n2 * sizeof(float), s));
+            // largest group bounds the column tiles
+            int kf0 = 2 * 49, nkeys = nk - kf0;
+            if (nkeys > 0) {
+                dim3 g((unsigned)((4 * n2 + GM_BM - 1) / GM_BM), (unsigned)((t->max_group + GM_BN - 1) / GM_BN),
+                       (unsigned)nkeys);
+                k_m2l_gemm<<<g, 256, 0, s>>>(t->mk_off, t->mk_pair, n, t->m2l_ops, t->W, t->Fl, kf0);
+            }
+        }
         prof_end(ctx, 4, 1);
         // downward pass
         prof_begin(ctx, 5);
@@ -701,7 +813,7 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
     }
     prof_begin(ctx, 6);
     auto knr = precise ? k_near<true> : k_near<false>;
-    knr<<<(unsigned)((t->n_groups + NEAR_W - 1) / NEAR_W), NEAR_T, 0, s>>>(
+    knr<<<(unsigned)t->n_groups, NEAR_T, 0, s>>>(
         kf, ctx->kd, wf, wd, loff, t->n_groups, t->grp_off, t->grp_leaf, t->cell_start, t->cell_end, t->cell_ix,
         t->cell_iy, t->elem_leaf, t->g_rel, t->g_frame, t->chg, t->perm, wL, n, t->Fl, use_far, N, scale, y);
     prof_end(ctx, 6, 1);

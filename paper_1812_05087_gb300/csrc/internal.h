@@ -63,6 +63,15 @@ struct ddm_tree {
     double win_lo[4] = {-1, -1, -1, -1}, win_hi[4] = {-1, -1, -1, -1};
     int win_next = 0;
     int64_t n_m2l, n_p2p;
+    // M2L pairs grouped by (level, cell offset): key = level * 49 + (dx+3)*7 + (dy+3)
+    int n_keys;                // (L + 1) * 49
+    int32_t *mk_off;           // CSR over keys
+    int2 *mk_pair;             // (target cell, source cell), global cell indices
+    int max_group;             // largest (level, offset) group
+    // M2L operators of the current time window, one (4n^2 x 4n^2) matrix per key
+    float *m2l_ops;
+    double ops_lo, ops_hi;
+    int ops_n;
     // per-tree workspaces
     float *W;                  // multipole weights, 4 n^2 per cell
     float *Fl;                 // local expansions, 4 n^2 per cell

@@ -341,6 +341,25 @@ __global__ void k_groups(const int32_t *elem_leaf, int64_t n, int64_t ngroups, c
         for (int q = 0; q < m; ++q) gleaf[goff[g] + q] = set[q];
 }
 
+// group interaction-list entries by (level, offset)
+__global__ void k_mkeys(const int32_t *iloff, const int32_t *ilidx, const int32_t *cix, const int32_t *ciy,
+                        const int64_t *lvloff, int L, int64_t first, int64_t ncell, const int32_t *koff,
+                        int32_t *kcur, int2 *pairs, int32_t *kcnt) {
+    int64_t c = first + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= first + ncell) return;
+    int lvl = 0;
+    while (lvl < L && c >= lvloff[lvl + 1]) ++lvl;
+    for (int q = iloff[c]; q < iloff[c + 1]; ++q) {
+        int32_t J = ilidx[q];
+        int key = lvl * 49 + (cix[c] - cix[J] + 3) * 7 + (ciy[c] - ciy[J] + 3);
+        if (kcnt) atomicAdd(&kcnt[key], 1);
+        else {
+            int pos = koff[key] + atomicAdd(&kcur[key], 1);
+            pairs[pos] = make_int2((int)c, J);
+        }
+    }
+}
+
 __global__ void k_p2p_count(const int32_t *cstart, const int32_t *cend, int64_t loff, int64_t nleaf,
                             const int32_t *nboff, const int32_t *nbidx, unsigned long long *tot) {
     int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -364,7 +383,7 @@ __global__ void k_p2p_count(const int32_t *cstart, const int32_t *cend, int64_t 
 
 void tree_free(ddm_tree *t) {
     if (!t) return;
-    void *ps[] = {t->grp_off, t->grp_leaf, t->perm, t->cell_key, t->cell_ix, t->cell_iy, t->cell_start, t->cell_end, t->cell_parent,
+    void *ps[] = {t->mk_off, t->mk_pair, t->m2l_ops, t->grp_off, t->grp_leaf, t->perm, t->cell_key, t->cell_ix, t->cell_iy, t->cell_start, t->cell_end, t->cell_parent,
                   t->il_off, t->il_idx, t->nb_off, t->nb_idx, t->elem_leaf, t->g_rel, t->g_frame,
                   t->xy_sorted, t->xy_caller, t->self_blk, t->W, t->Fl, t->chg};
     for (void *p : ps)
@@ -511,6 +530,38 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
                                                   1 << l, t->il_off, t->il_idx, nullptr); ++tl_launches;
     }
     t->n_m2l = iltot;
+    // M2L pairs grouped by (level, offset)
+    {
+        int nk = (L + 1) * 49;
+        t->n_keys = nk;
+        int32_t *kc = S.get<int32_t>(nk + 1), *kcur = S.get<int32_t>(nk);
+        int64_t *lo = S.get<int64_t>(L + 2);
+        TRY(S.err);
+        TRY(cudaMemcpyAsync(lo, t->lvl_off.data(), (L + 2) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+        TRY(cudaMemsetAsync(kc, 0, (nk + 1) * sizeof(int32_t), st));
+        TRY(cudaMemsetAsync(kcur, 0, nk * sizeof(int32_t), st));
+        TRY(cudaMalloc(&t->mk_off, (nk + 1) * sizeof(int32_t)));
+        TRY(cudaMalloc(&t->mk_pair, std::max(iltot, 1) * sizeof(int2)));
+        int64_t first = L >= 2 ? t->lvl_off[2] : NC, ncm = NC - first;
+        if (ncm > 0) {
+            k_mkeys<<<(ncm + 255) / 256, 256, 0, st>>>(t->il_off, t->il_idx, t->cell_ix, t->cell_iy, lo, L, first, ncm,
+                                                       nullptr, nullptr, nullptr, kc); ++tl_launches;
+        }
+        int32_t ktot;
+        TRY(scan_excl(S, st, kc, t->mk_off, nk, &ktot));
+        TRY(cudaMemcpyAsync(t->mk_off + nk, &ktot, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        if (ncm > 0) {
+            k_mkeys<<<(ncm + 255) / 256, 256, 0, st>>>(t->il_off, t->il_idx, t->cell_ix, t->cell_iy, lo, L, first, ncm,
+                                                       t->mk_off, kcur, t->mk_pair, nullptr); ++tl_launches;
+        }
+        t->ops_lo = t->ops_hi = -1.0;
+        t->ops_n = 0;
+        std::vector<int32_t> hk(nk + 1);
+        TRY(cudaMemcpyAsync(hk.data(), t->mk_off, (nk + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        TRY(cudaStreamSynchronize(st));
+        t->max_group = 0;
+        for (int k = 0; k < nk; ++k) t->max_group = std::max(t->max_group, hk[k + 1] - hk[k]);
+    }
 
     // sorted geometry
     TRY(cudaMalloc(&t->perm, n * sizeof(int64_t)));
