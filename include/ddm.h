@@ -183,6 +183,65 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
 ddm_status ddm_sif(ddm_ctx *ctx, const ddm_tree *tree, const double *d_x, const int64_t *d_tip,
                    int n, double *d_KI, double *d_KII);
 
+/* Batches of independent problems (no counterpart in the paper; many
+ * uneven fracture sets solved together).  A batch refers to P trees (which
+ * must outlive it); vectors of a batch are the problems' 3N vectors
+ * concatenated in the order of `trees`.  Products of all problems are one
+ * CUDA graph launch on the context stream (captured on the first call and
+ * again whenever dt, mode or the buffers change).  All problems share dt,
+ * system and GMRES parameters. */
+typedef struct ddm_batch ddm_batch;
+ddm_status ddm_batch_create(ddm_ctx *ctx, ddm_tree *const *trees, int n, ddm_batch **out);
+void ddm_batch_destroy(ddm_batch *batch);
+/* d_y_p = [K(dt)] d_x_p for every problem p. */
+ddm_status ddm_batch_matvec(ddm_ctx *ctx, ddm_batch *batch, double dt, const double *d_x, double *d_y,
+                            int mode);
+/* Lockstep restarted GMRES of every problem (FP64 Arnoldi with per-problem
+ * reductions; preconditioner, precision and stopping as ddm_gmres_solve).
+ * infos: n entries.  Returns DDM_ENOTCONV if any problem did not converge
+ * (its x and info are still written).  Synchronises the stream. */
+ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *batch, double dt, const double *d_rhs,
+                                 double *d_x, const ddm_gmres_params *prm, ddm_gmres_info *infos);
+
+/* Request loop with continuous batching (no counterpart in the paper; a
+ * serving front end for many fracture-set solves).  ddm_server_create
+ * starts a server thread with its own context and CUDA stream on the
+ * context's device, material and FMM parameters.  Requests queue in
+ * arrival order; the server admits them while the estimated device
+ * footprint of the admitted ones (tree, M2L operators, solution history,
+ * Krylov arena) stays within hbm_budget_bytes (0 = 64 GiB) and at most
+ * max_active run.  Each round advances every admitted request by one time
+ * step (history sum of its past steps, right-hand side from its loads, one
+ * lockstep batched GMRES of all admitted requests with the same dt and
+ * system, tolerance tol); finished requests leave and queued ones join the
+ * next round.  A request's d_xy and d_x must stay valid until ddm_poll
+ * reports completion; the solution of the last step is written to d_x
+ * (3N doubles).  ddm_submit does not block (DDM_ENOMEM if the request alone
+ * exceeds the budget); ddm_poll returns DDM_PENDING until the request is
+ * done, then its final status. */
+typedef struct ddm_server ddm_server;
+typedef struct {
+    int64_t n;              /* elements */
+    const double *d_xy;     /* 4N geometry (device) */
+    ddm_loads loads;        /* loads and system */
+    double dt;              /* time step */
+    int steps;              /* number of time steps */
+    double *d_x;            /* out: 3N solution of the last step (device) */
+} ddm_request;
+typedef struct {
+    int status;             /* DDM_PENDING, DDM_OK or the failure */
+    int iterations;         /* GMRES iterations over all steps */
+    int steps_done;
+    double rel_residual;    /* last step */
+    double queue_ms;        /* submit -> admission (host clock), -1 before */
+    double latency_ms;      /* submit -> completion, -1 before */
+} ddm_result;
+ddm_status ddm_server_create(ddm_ctx *ctx, size_t hbm_budget_bytes, int max_active, double tol,
+                             ddm_server **out);
+ddm_status ddm_submit(ddm_server *server, const ddm_request *req, uint64_t *ticket);
+ddm_status ddm_poll(ddm_server *server, uint64_t ticket, ddm_result *result);
+void ddm_server_destroy(ddm_server *server);
+
 /* Stage timing for profiling (no counterpart in the paper): when enabled,
  * CUDA events bracket each stage on the context stream.  ddm_profile_read
  * synchronises the stream and returns, per stage, the summed milliseconds

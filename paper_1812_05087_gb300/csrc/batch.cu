@@ -1,0 +1,542 @@
+// Batched products and solves of many independent (uneven) problems.
+//
+// A batch holds the trees of P problems.  The influence product of every
+// problem is captured once into one CUDA graph (the problems' FMM kernels on
+// forked streams, so that small problems overlap on the device) and the
+// whole batch is advanced by one graph launch.  GMRES runs in lockstep over
+// an arena that concatenates the problems' vectors: Arnoldi in FP64 with
+// segmented (per-problem) reductions, one Hessenberg column per problem read
+// back per iteration, Givens rotations and convergence per problem.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+constexpr int BT = 256;
+constexpr int SEG_CHUNK = 2048;     // elements per reduction block
+constexpr int NSTREAMS = 8;
+
+// per reduction block: problem and element range
+struct SegBlk {
+    int p;
+    int64_t a, b;
+};
+
+__global__ void k_dots_seg(const double *V, int64_t ld, const double *w, const SegBlk *blk, int ncols,
+                           double *h /* P x ncols_stride */, int hstride) {
+    __shared__ double s[BT];
+    SegBlk B = blk[blockIdx.x];
+    int v = blockIdx.y;
+    double acc = 0.0;
+    for (int64_t i = B.a + threadIdx.x; i < B.b; i += BT) acc += V[v * ld + i] * w[i];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = BT / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(&h[B.p * hstride + v], s[0]);
+}
+// w -= V h (per problem), hacc += h
+__global__ void k_sub_seg(const double *V, int64_t ld, int nv, const double *h, int hstride, const int32_t *prob,
+                          double *w, int64_t L) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= L) return;
+    const double *hp = h + prob[i] * hstride;
+    double s = 0.0;
+    for (int v = 0; v < nv; ++v) s += hp[v] * V[v * ld + i];
+    w[i] -= s;
+}
+__global__ void k_hacc(const double *h, double *hcol, int P, int hstride, int nv) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P * nv) return;
+    int p = i / nv, v = i % nv;
+    hcol[p * hstride + v] += h[p * hstride + v];
+}
+// out = w / sqrt(nrm2[p]) (0 for a zero norm); hcol[p][j1] = norm
+__global__ void k_scale_seg(const double *w, const double *nrm2, const int32_t *prob, int64_t L, double *out,
+                            double *hcol, int hstride, int j1, int P) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < P) hcol[i * hstride + j1] = sqrt(nrm2[i]);
+    if (i >= L) return;
+    double nr = sqrt(nrm2[prob[i]]);
+    out[i] = nr > 0.0 ? w[i] / nr : 0.0;
+}
+// v0 = -w / beta[p] (0 for inactive problems: coef = 0)
+__global__ void k_v0_seg(const double *w, const double *coef, const int32_t *prob, int64_t L, double *out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= L) return;
+    out[i] = coef[prob[i]] * w[i];
+}
+__global__ void k_axpy_b(double a, const double *x, double *y, int64_t L) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < L) y[i] += a * x[i];
+}
+// out_i = sum_v Y[p][v] V[v][i]
+__global__ void k_comb_seg(const double *V, int64_t ld, int nv, const double *Y, int ystride, const int32_t *prob,
+                           int64_t L, double *out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= L) return;
+    const double *yp = Y + prob[i] * ystride;
+    double s = 0.0;
+    for (int v = 0; v < nv; ++v) s += yp[v] * V[v * ld + i];
+    out[i] = s;
+}
+
+// arena (nc blocks of N per problem) <-> 3N layout helpers, one problem
+__global__ void k_precond_to3(const double *Minv, int64_t n, int nc, const double *v, double *z3) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    double in[3] = {0, 0, 0};
+    for (int c = 0; c < nc; ++c) in[c] = v[c * n + e];
+    for (int r = 0; r < 3; ++r) {
+        double s = 0;
+        if (r < nc)
+            for (int c = 0; c < nc; ++c) s += Minv[9 * e + 3 * r + c] * in[c];
+        z3[r * n + e] = s;
+    }
+}
+__global__ void k_copy_to3(const double *v, int64_t n, int nc, double *z3) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    for (int r = 0; r < 3; ++r) z3[r * n + e] = r < nc ? v[r * n + e] : 0.0;
+}
+__global__ void k_restrict_b(const double *y, int64_t n, int sys, int combine, double *out) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    out[e] = y[e];
+    out[n + e] = y[n + e] + (combine && sys == DDM_SYS_RATE ? y[2 * n + e] : 0.0);
+    if (sys == DDM_SYS_PRESSURE) out[2 * n + e] = y[2 * n + e];
+}
+__global__ void k_add_precond(const double *Minv, int64_t n, int nc, const double *v, double *x3) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    double in[3] = {0, 0, 0};
+    for (int c = 0; c < nc; ++c) in[c] = v[c * n + e];
+    for (int r = 0; r < nc; ++r) {
+        double s = 0;
+        for (int c = 0; c < nc; ++c) s += Minv[9 * e + 3 * r + c] * in[c];
+        x3[r * n + e] += s;
+    }
+}
+__global__ void k_invert_b(const double *blk, int64_t n, int sys, double *Minv) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const double *B = blk + 9 * e;
+    double *O = Minv + 9 * e;
+    for (int k = 0; k < 9; ++k) O[k] = 0;
+    if (sys == DDM_SYS_PRESSURE) {
+        double a = B[0], b = B[1], c = B[2], d = B[3], f = B[4], g = B[5], h = B[6], i = B[7], j = B[8];
+        double A = f * j - g * i, Bc = -(d * j - g * h), C = d * i - f * h;
+        double id = 1.0 / (a * A + b * Bc + c * C);
+        O[0] = A * id; O[1] = -(b * j - c * i) * id; O[2] = (b * g - c * f) * id;
+        O[3] = Bc * id; O[4] = (a * j - c * h) * id; O[5] = -(a * g - c * d) * id;
+        O[6] = C * id; O[7] = -(a * i - b * h) * id; O[8] = (a * f - b * d) * id;
+    } else {
+        double a = B[0], b = B[1], c = B[3], d = B[4];
+        if (sys == DDM_SYS_RATE) { c += B[6]; d += B[7]; }
+        double id = 1.0 / (a * d - b * c);
+        O[0] = d * id; O[1] = -b * id; O[3] = -c * id; O[4] = a * id;
+    }
+}
+
+inline unsigned nb(int64_t n) { return (unsigned)((n + BT - 1) / BT); }
+
+}  // namespace
+
+struct ddm_batch {
+    int P = 0;
+    std::vector<ddm_tree *> trees;
+    std::vector<int64_t> N, off3;         // elements, offset of each problem in 3N-layout arenas
+    int64_t tot3 = 0;
+    // solver arena (system rows)
+    int nc = 3, sys = -1, m = 0;
+    std::vector<int64_t> offs;            // offset of each problem in the system arena
+    int64_t L = 0;
+    int32_t *prob = nullptr;              // arena index -> problem
+    SegBlk *blk = nullptr;
+    int nblk = 0;
+    double *V = nullptr, *w = nullptr, *vin = nullptr, *b = nullptr, *tmp = nullptr;
+    double *full = nullptr, *y3 = nullptr, *Minv = nullptr;
+    double *h = nullptr, *hcol = nullptr, *nrm = nullptr, *coef = nullptr, *Y = nullptr;
+    std::vector<int64_t> minv_off;
+    // graphs
+    cudaGraphExec_t g_op = nullptr, g_prod = nullptr, g_res = nullptr;
+    double g_op_dt = -1, g_prod_dt = -1, g_res_dt = -1;
+    int g_op_mode = -1, g_prod_mode = -1, g_res_mode = -1, g_op_sys = -1, g_res_sys = -1;
+    const double *g_prod_x = nullptr, *g_res_x = nullptr;
+    long long k_op = 0, k_prod = 0, k_res = 0;   // kernels per graph launch
+    double *g_prod_y = nullptr;
+    cudaStream_t fork[NSTREAMS] = {};
+    cudaStream_t cap = nullptr;
+    cudaEvent_t ev_fork[NSTREAMS] = {}, ev_join[NSTREAMS] = {};
+    void free_solver() {
+        void *ps[] = {prob, blk, V, w, vin, b, tmp, Minv, h, hcol, nrm, coef, Y};
+        for (void *p : ps)
+            if (p) cudaFree(p);
+        prob = nullptr; blk = nullptr; V = w = vin = b = tmp = Minv = h = hcol = nrm = coef = Y = nullptr;
+        sys = -1; m = 0;
+    }
+    void free_graphs() {
+        if (g_op) cudaGraphExecDestroy(g_op);
+        if (g_prod) cudaGraphExecDestroy(g_prod);
+        if (g_res) cudaGraphExecDestroy(g_res);
+        g_op = g_prod = g_res = nullptr;
+    }
+};
+
+namespace {
+
+// capture fn(p, stream) for every problem into one graph on ctx->stream
+template <class Fn>
+ddm_status capture(ddm_ctx *ctx, ddm_batch *B, cudaGraphExec_t *out, long long *kernels, Fn fn) {
+    // capture on the batch's own stream; the graph is launched on the context stream
+    cudaStream_t s = B->cap;
+    DDM_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    if (*out) { cudaGraphExecDestroy(*out); *out = nullptr; }
+    cudaGraph_t g;
+    long long before[DDM_NSTAGES];
+    for (int k = 0; k < DDM_NSTAGES; ++k) before[k] = ctx->prof.launches[k];
+    DDM_CUDA_TRY(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    cudaEvent_t e0;
+    cudaEventCreateWithFlags(&e0, cudaEventDisableTiming);
+    cudaEventRecord(e0, s);
+    int ns = std::min(NSTREAMS, B->P);
+    for (int k = 0; k < ns; ++k) cudaStreamWaitEvent(B->fork[k], e0, 0);
+    ddm_status st = DDM_OK;
+    for (int p = 0; p < B->P && st == DDM_OK; ++p) st = fn(p, B->fork[p % ns]);
+    for (int k = 0; k < ns; ++k) {
+        cudaEventRecord(B->ev_join[k], B->fork[k]);
+        cudaStreamWaitEvent(s, B->ev_join[k], 0);
+    }
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    cudaEventDestroy(e0);
+    long long kern = 0;
+    for (int k = 0; k < DDM_NSTAGES; ++k) { kern += ctx->prof.launches[k] - before[k]; ctx->prof.launches[k] = before[k]; }
+    *kernels = kern;
+    if (st) { if (e == cudaSuccess) cudaGraphDestroy(g); return st; }
+    if (e != cudaSuccess) return ctx_fail(ctx, DDM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return ctx_fail(ctx, DDM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    return DDM_OK;
+}
+
+// run every problem's product once outside capture so that per-tree caches
+// (workspaces, M2L operators, own-element blocks) exist before capture
+ddm_status warm(ddm_ctx *ctx, ddm_batch *B, double dt, int mode) {
+    for (int p = 0; p < B->P; ++p) {
+        ddm_status st = op_apply(ctx, B->trees[p], 0.0, dt, B->full + B->off3[p], B->y3 + B->off3[p], mode, 0, 1.0);
+        if (st) return st;
+    }
+    return DDM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ddm_status ddm_batch_create(ddm_ctx *ctx, ddm_tree *const *trees, int n, ddm_batch **out) {
+    if (!ctx || !trees || n <= 0 || !out) return ctx_fail(ctx, DDM_EINVAL, "ddm_batch_create: bad arguments");
+    ddm_batch *B = new ddm_batch();
+    B->P = n;
+    int64_t o = 0;
+    for (int p = 0; p < n; ++p) {
+        if (!trees[p]) { delete B; return ctx_fail(ctx, DDM_EINVAL, "ddm_batch_create: null tree"); }
+        B->trees.push_back(trees[p]);
+        B->N.push_back(trees[p]->n);
+        B->off3.push_back(o);
+        o += 3 * trees[p]->n;
+    }
+    B->tot3 = o;
+    if (cudaMalloc(&B->full, o * sizeof(double)) != cudaSuccess || cudaMalloc(&B->y3, o * sizeof(double)) != cudaSuccess) {
+        delete B;
+        return ctx_fail(ctx, DDM_ENOMEM, "batch arena allocation failed");
+    }
+    cudaMemset(B->full, 0, o * sizeof(double));
+    cudaMemset(B->y3, 0, o * sizeof(double));
+    cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking);
+    for (int k = 0; k < NSTREAMS; ++k) {
+        cudaStreamCreateWithFlags(&B->fork[k], cudaStreamNonBlocking);
+        cudaEventCreateWithFlags(&B->ev_join[k], cudaEventDisableTiming);
+    }
+    *out = B;
+    return DDM_OK;
+}
+
+void ddm_batch_destroy(ddm_batch *B) {
+    if (!B) return;
+    B->free_graphs();
+    B->free_solver();
+    if (B->full) cudaFree(B->full);
+    if (B->y3) cudaFree(B->y3);
+    if (B->cap) cudaStreamDestroy(B->cap);
+    for (int k = 0; k < NSTREAMS; ++k) {
+        if (B->fork[k]) cudaStreamDestroy(B->fork[k]);
+        if (B->ev_join[k]) cudaEventDestroy(B->ev_join[k]);
+    }
+    delete B;
+}
+
+ddm_status ddm_batch_matvec(ddm_ctx *ctx, ddm_batch *B, double dt, const double *d_x, double *d_y, int mode) {
+    if (!ctx || !B || !d_x || !d_y || !(dt > 0)) return ctx_fail(ctx, DDM_EINVAL, "ddm_batch_matvec: bad arguments");
+    ddm_status st = upload_tables(ctx);
+    if (st) return st;
+    if (!B->g_prod || B->g_prod_dt != dt || B->g_prod_mode != mode || B->g_prod_x != d_x || B->g_prod_y != d_y) {
+        if ((st = warm(ctx, B, dt, mode))) return st;
+        DDM_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        int saved = ctx->prof.on;
+        ctx->prof.on = 0;
+        st = capture(ctx, B, &B->g_prod, &B->k_prod, [&](int p, cudaStream_t s) {
+            return op_apply(ctx, B->trees[p], 0.0, dt, d_x + B->off3[p], d_y + B->off3[p], mode, 0, 1.0, s);
+        });
+        ctx->prof.on = saved;
+        if (st) return st;
+        B->g_prod_dt = dt; B->g_prod_mode = mode; B->g_prod_x = d_x; B->g_prod_y = d_y;
+    }
+    DDM_CUDA_TRY(ctx, cudaGraphLaunch(B->g_prod, ctx->stream));
+    prof_end(ctx, 6, (int)B->k_prod);
+    return DDM_OK;
+}
+
+ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const double *d_rhs, double *d_x,
+                                 const ddm_gmres_params *prm, ddm_gmres_info *infos) {
+    if (!ctx || !B || !d_rhs || !d_x || !(dt > 0)) return ctx_fail(ctx, DDM_EINVAL, "ddm_batch_gmres_solve: bad arguments");
+    ddm_gmres_params Pm = prm ? *prm : ddm_gmres_params{DDM_SYS_PRESSURE, 50, 1000, 1e-6, DDM_MODE_FMM};
+    if (Pm.restart <= 0) Pm.restart = 50;
+    if (Pm.max_iters <= 0) Pm.max_iters = 1000;
+    if (!(Pm.tol > 0)) Pm.tol = 1e-6;
+    if (Pm.system < 0 || Pm.system > 2 || Pm.restart > 500) return ctx_fail(ctx, DDM_EINVAL, "bad GMRES params");
+    ddm_status st = upload_tables(ctx);
+    if (st) return st;
+    cudaStream_t s = ctx->stream;
+    const int P = B->P, m = Pm.restart, sys = Pm.system, mode = Pm.mode;
+    const int nc = sys == DDM_SYS_PRESSURE ? 3 : 2;
+    const int hs = m + 2;
+    // (re)allocate the solver arena
+    if (B->sys != sys || B->m < m) {
+        B->free_solver();
+        B->free_graphs();
+        B->nc = nc;
+        B->offs.assign(P + 1, 0);
+        B->minv_off.assign(P + 1, 0);
+        for (int p = 0; p < P; ++p) {
+            B->offs[p + 1] = B->offs[p] + nc * B->N[p];
+            B->minv_off[p + 1] = B->minv_off[p] + 9 * B->N[p];
+        }
+        int64_t L = B->offs[P];
+        B->L = L;
+        std::vector<int32_t> hp(L);
+        std::vector<SegBlk> hb;
+        for (int p = 0; p < P; ++p) {
+            for (int64_t i = B->offs[p]; i < B->offs[p + 1]; ++i) hp[i] = p;
+            for (int64_t a = B->offs[p]; a < B->offs[p + 1]; a += SEG_CHUNK)
+                hb.push_back(SegBlk{p, a, std::min(a + SEG_CHUNK, B->offs[p + 1])});
+        }
+        B->nblk = (int)hb.size();
+        bool ok = cudaMalloc(&B->prob, L * sizeof(int32_t)) == cudaSuccess &&
+                  cudaMalloc(&B->blk, hb.size() * sizeof(SegBlk)) == cudaSuccess &&
+                  cudaMalloc(&B->V, (size_t)(m + 1) * L * sizeof(double)) == cudaSuccess &&
+                  cudaMalloc(&B->w, L * sizeof(double)) == cudaSuccess &&
+                  cudaMalloc(&B->vin, L * sizeof(double)) == cudaSuccess &&
+                  cudaMalloc(&B->b, L * sizeof(double)) == cudaSuccess &&
+                  cudaMalloc(&B->tmp, L * sizeof(double)) == cudaSuccess &&
+                  cudaMalloc(&B->Minv, B->minv_off[P] * sizeof(double)) == cudaSuccess &&
+                  cudaMalloc(&B->h, (size_t)P * hs * sizeof(double)) == cudaSuccess &&
+                  cudaMalloc(&B->hcol, (size_t)P * hs * sizeof(double)) == cudaSuccess &&
+                  cudaMalloc(&B->nrm, (size_t)P * hs * sizeof(double)) == cudaSuccess &&
+                  cudaMalloc(&B->coef, P * sizeof(double)) == cudaSuccess &&
+                  cudaMalloc(&B->Y, (size_t)P * hs * sizeof(double)) == cudaSuccess;
+        if (!ok) { B->free_solver(); return ctx_fail(ctx, DDM_ENOMEM, "batch GMRES arena allocation failed"); }
+        cudaMemcpyAsync(B->prob, hp.data(), L * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(B->blk, hb.data(), hb.size() * sizeof(SegBlk), cudaMemcpyHostToDevice, s);
+        B->sys = sys;
+        B->m = m;
+        DDM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    }
+    const int64_t L = B->L;
+    // preconditioner blocks per problem
+    for (int p = 0; p < P; ++p) {
+        if ((st = self_blocks(ctx, B->trees[p], dt))) return st;
+        k_invert_b<<<nb(B->N[p]), BT, 0, s>>>(B->trees[p]->self_blk, B->N[p], sys, B->Minv + B->minv_off[p]);
+    }
+    // graphs: preconditioned operator vin -> w, residual operator (precise) x -> tmp
+    int saved = ctx->prof.on;
+    ctx->prof.on = 0;
+    if (!B->g_op || B->g_op_dt != dt || B->g_op_mode != mode || B->g_op_sys != sys) {
+        if ((st = warm(ctx, B, dt, mode))) { ctx->prof.on = saved; return st; }
+        DDM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        st = capture(ctx, B, &B->g_op, &B->k_op, [&](int p, cudaStream_t ps) -> ddm_status {
+            int64_t n = B->N[p];
+            k_precond_to3<<<nb(n), BT, 0, ps>>>(B->Minv + B->minv_off[p], n, nc, B->vin + B->offs[p], B->full + B->off3[p]);
+            ddm_status e = op_apply(ctx, B->trees[p], 0.0, dt, B->full + B->off3[p], B->y3 + B->off3[p], mode, 0, 1.0, ps);
+            if (e) return e;
+            k_restrict_b<<<nb(n), BT, 0, ps>>>(B->y3 + B->off3[p], n, sys, 1, B->w + B->offs[p]);
+            return DDM_OK;
+        });
+        if (st) { ctx->prof.on = saved; return st; }
+        B->g_op_dt = dt; B->g_op_mode = mode; B->g_op_sys = sys;
+    }
+    if (!B->g_res || B->g_res_dt != dt || B->g_res_mode != mode || B->g_res_sys != sys || B->g_res_x != d_x) {
+        if ((st = warm(ctx, B, dt, mode | DDM_MODE_PRECISE))) { ctx->prof.on = saved; return st; }
+        DDM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        st = capture(ctx, B, &B->g_res, &B->k_res, [&](int p, cudaStream_t ps) -> ddm_status {
+            int64_t n = B->N[p];
+            k_copy_to3<<<nb(n), BT, 0, ps>>>(d_x + B->off3[p], n, nc, B->full + B->off3[p]);
+            ddm_status e = op_apply(ctx, B->trees[p], 0.0, dt, B->full + B->off3[p], B->y3 + B->off3[p],
+                                    mode | DDM_MODE_PRECISE, 0, 1.0, ps);
+            if (e) return e;
+            k_restrict_b<<<nb(n), BT, 0, ps>>>(B->y3 + B->off3[p], n, sys, 1, B->tmp + B->offs[p]);
+            return DDM_OK;
+        });
+        if (st) { ctx->prof.on = saved; return st; }
+        B->g_res_dt = dt; B->g_res_mode = mode; B->g_res_sys = sys; B->g_res_x = d_x;
+    }
+    ctx->prof.on = saved;
+    // b = restrict(rhs) (- restrict(A [0; 0; Dq]) for the 2N systems)
+    for (int p = 0; p < P; ++p) {
+        int64_t n = B->N[p];
+        k_restrict_b<<<nb(n), BT, 0, s>>>(d_rhs + B->off3[p], n, sys, 0, B->b + B->offs[p]);
+        if (sys != DDM_SYS_PRESSURE) {
+            DDM_CUDA_TRY(ctx, cudaMemsetAsync(B->full + B->off3[p], 0, 2 * n * sizeof(double), s));
+            DDM_CUDA_TRY(ctx, cudaMemcpyAsync(B->full + B->off3[p] + 2 * n, d_x + B->off3[p] + 2 * n, n * sizeof(double),
+                                              cudaMemcpyDeviceToDevice, s));
+            if ((st = op_apply(ctx, B->trees[p], 0.0, dt, B->full + B->off3[p], B->y3 + B->off3[p],
+                               mode | DDM_MODE_PRECISE, 0, 1.0)))
+                return st;
+            k_restrict_b<<<nb(n), BT, 0, s>>>(B->y3 + B->off3[p], n, sys, 1, B->tmp + B->offs[p]);
+            k_axpy_b<<<nb(nc * n), BT, 0, s>>>(-1.0, B->tmp + B->offs[p], B->b + B->offs[p], nc * n);
+        }
+    }
+    auto seg_norms = [&](const double *v, std::vector<double> &out) -> ddm_status {
+        DDM_CUDA_TRY(ctx, cudaMemsetAsync(B->nrm, 0, P * sizeof(double), s));
+        k_dots_seg<<<dim3(B->nblk, 1), BT, 0, s>>>(v, 0, v, B->blk, 1, B->nrm, 1);
+        out.resize(P);
+        DDM_CUDA_TRY(ctx, cudaMemcpyAsync(out.data(), B->nrm, P * sizeof(double), cudaMemcpyDeviceToHost, s));
+        DDM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        for (double &x : out) x = sqrt(x);
+        return DDM_OK;
+    };
+    std::vector<double> bn, beta;
+    if ((st = seg_norms(B->b, bn))) return st;
+    for (double &x : bn)
+        if (x == 0) x = 1;
+    std::vector<int> iters(P, 0), restarts(P, 0), conv(P, 0), stall(P, 0), active(P, 1);
+    std::vector<double> rel(P, 1e300), best(P, 1e300);
+    std::vector<double> H((size_t)P * (m + 1) * m), cs((size_t)P * m), sn((size_t)P * m), gv((size_t)P * (m + 1));
+    std::vector<double> hc((size_t)P * hs), coef(P), Yh((size_t)P * hs);
+    std::vector<int> jend(P);
+    int total = 0;
+    while (true) {
+        // true residuals (precise operator): tmp = A x, w = A x - b
+        DDM_CUDA_TRY(ctx, cudaGraphLaunch(B->g_res, s));
+        prof_end(ctx, 6, (int)B->k_res);
+        DDM_CUDA_TRY(ctx, cudaMemcpyAsync(B->w, B->tmp, L * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        k_axpy_b<<<nb(L), BT, 0, s>>>(-1.0, B->b, B->w, L);
+        if ((st = seg_norms(B->w, beta))) return st;
+        int nact = 0;
+        for (int p = 0; p < P; ++p) {
+            rel[p] = beta[p] / bn[p];
+            if (!active[p]) continue;
+            if (rel[p] < Pm.tol) { conv[p] = 1; active[p] = 0; continue; }
+            if (rel[p] < 0.9 * best[p]) { best[p] = rel[p]; stall[p] = 0; }
+            else if (++stall[p] >= 3) { active[p] = 0; continue; }
+            if (iters[p] >= Pm.max_iters) { active[p] = 0; continue; }
+            ++nact;
+        }
+        if (nact == 0 || total >= Pm.max_iters) break;
+        for (int p = 0; p < P; ++p) coef[p] = active[p] && beta[p] > 0 ? -1.0 / beta[p] : 0.0;
+        DDM_CUDA_TRY(ctx, cudaMemcpyAsync(B->coef, coef.data(), P * sizeof(double), cudaMemcpyHostToDevice, s));
+        k_v0_seg<<<nb(L), BT, 0, s>>>(B->w, B->coef, B->prob, L, B->V);
+        std::fill(gv.begin(), gv.end(), 0.0);
+        for (int p = 0; p < P; ++p) { gv[(size_t)p * (m + 1)] = active[p] ? beta[p] : 0.0; jend[p] = 0; }
+        std::vector<int> live = active;
+        int j = 0;
+        for (; j < m; ++j) {
+            DDM_CUDA_TRY(ctx, cudaMemcpyAsync(B->vin, B->V + (int64_t)j * L, L * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            DDM_CUDA_TRY(ctx, cudaGraphLaunch(B->g_op, s));
+            prof_end(ctx, 6, (int)B->k_op);
+            prof_end(ctx, 8, 9);
+            DDM_CUDA_TRY(ctx, cudaMemsetAsync(B->hcol, 0, (size_t)P * hs * sizeof(double), s));
+            for (int pass = 0; pass < 2; ++pass) {
+                DDM_CUDA_TRY(ctx, cudaMemsetAsync(B->h, 0, (size_t)P * hs * sizeof(double), s));
+                k_dots_seg<<<dim3(B->nblk, j + 1), BT, 0, s>>>(B->V, L, B->w, B->blk, j + 1, B->h, hs);
+                k_sub_seg<<<nb(L), BT, 0, s>>>(B->V, L, j + 1, B->h, hs, B->prob, B->w, L);
+                k_hacc<<<nb((int64_t)P * (j + 1)), BT, 0, s>>>(B->h, B->hcol, P, hs, j + 1);
+            }
+            DDM_CUDA_TRY(ctx, cudaMemsetAsync(B->nrm, 0, P * sizeof(double), s));
+            k_dots_seg<<<dim3(B->nblk, 1), BT, 0, s>>>(B->w, 0, B->w, B->blk, 1, B->nrm, 1);
+            k_scale_seg<<<nb(std::max<int64_t>(L, P)), BT, 0, s>>>(B->w, B->nrm, B->prob, L, B->V + (int64_t)(j + 1) * L,
+                                                                   B->hcol, hs, j + 1, P);
+            DDM_CUDA_TRY(ctx, cudaMemcpyAsync(hc.data(), B->hcol, (size_t)P * hs * sizeof(double), cudaMemcpyDeviceToHost, s));
+            DDM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+            ++total;
+            int still = 0;
+            for (int p = 0; p < P; ++p) {
+                if (!live[p]) continue;
+                double *c = &hc[(size_t)p * hs];
+                double *csp = &cs[(size_t)p * m], *snp = &sn[(size_t)p * m], *g = &gv[(size_t)p * (m + 1)];
+                for (int i = 0; i < j; ++i) {
+                    double a = csp[i] * c[i] + snp[i] * c[i + 1];
+                    c[i + 1] = -snp[i] * c[i] + csp[i] * c[i + 1];
+                    c[i] = a;
+                }
+                double r = hypot(c[j], c[j + 1]);
+                csp[j] = r > 0 ? c[j] / r : 1.0;
+                snp[j] = r > 0 ? c[j + 1] / r : 0.0;
+                c[j] = r;
+                g[j + 1] = -snp[j] * g[j];
+                g[j] = csp[j] * g[j];
+                for (int i = 0; i <= j; ++i) H[((size_t)p * (m + 1) + i) * m + j] = c[i];
+                ++iters[p];
+                jend[p] = j + 1;
+                if (fabs(g[j + 1]) / bn[p] < Pm.tol || r == 0 || iters[p] >= Pm.max_iters) live[p] = 0;
+                else ++still;
+            }
+            if (still == 0) { ++j; break; }
+        }
+        // per-problem least squares and update x += M^-1 V y
+        std::fill(Yh.begin(), Yh.end(), 0.0);
+        for (int p = 0; p < P; ++p) {
+            if (!active[p]) continue;
+            int jp = jend[p];
+            double *y = &Yh[(size_t)p * hs];
+            for (int i = jp - 1; i >= 0; --i) {
+                double sum = gv[(size_t)p * (m + 1) + i];
+                for (int k = i + 1; k < jp; ++k) sum -= H[((size_t)p * (m + 1) + i) * m + k] * y[k];
+                double d = H[((size_t)p * (m + 1) + i) * m + i];
+                y[i] = d != 0 ? sum / d : 0.0;
+            }
+            ++restarts[p];
+        }
+        int jm = 0;
+        for (int p = 0; p < P; ++p) jm = std::max(jm, active[p] ? jend[p] : 0);
+        if (jm > 0) {
+            DDM_CUDA_TRY(ctx, cudaMemcpyAsync(B->Y, Yh.data(), (size_t)P * hs * sizeof(double), cudaMemcpyHostToDevice, s));
+            k_comb_seg<<<nb(L), BT, 0, s>>>(B->V, L, jm, B->Y, hs, B->prob, L, B->tmp);
+            for (int p = 0; p < P; ++p)
+                if (active[p])
+                    k_add_precond<<<nb(B->N[p]), BT, 0, s>>>(B->Minv + B->minv_off[p], B->N[p], nc, B->tmp + B->offs[p],
+                                                             d_x + B->off3[p]);
+            DDM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        }
+    }
+    bool all = true;
+    for (int p = 0; p < P; ++p) {
+        if (infos) {
+            infos[p].iterations = iters[p];
+            infos[p].restarts = restarts[p];
+            infos[p].rel_residual = rel[p];
+            infos[p].converged = conv[p];
+        }
+        all = all && conv[p];
+    }
+    DDM_CUDA_TRY(ctx, cudaGetLastError());
+    return all ? DDM_OK : ctx_fail(ctx, DDM_ENOTCONV, "batched GMRES: some problems did not converge");
+}
+
+}  // extern "C"

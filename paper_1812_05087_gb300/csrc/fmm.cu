@@ -16,6 +16,8 @@
 // the target element frame at the end.
 #include <cmath>
 #include <cstdio>
+#include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -639,10 +641,21 @@ __global__ void __launch_bounds__(DN_T) k_dense(KConst<float> k, KConst<double> 
 }  // namespace
 
 // ------------------------------------------------------------------- host
-static ddm_status upload_tables(ddm_ctx *ctx) {
-    static thread_local int last_n = -1, last_q = -1, last_dev = -1;
-    int n = ctx->prm.n_cheb, nq = ctx->prm.quad_near;
-    if (n == last_n && nq == last_q && ctx->device == last_dev) return DDM_OK;
+// The Gauss / Chebyshev tables live in __constant__ memory, which is global
+// to the device: the last uploaded (n_cheb, quad_near) is tracked process
+// wide, and contexts that use different values on one device must not run
+// concurrently.
+static std::mutex g_tab_mu;
+static int g_last_n[64], g_last_q[64];
+static bool g_tab_init = false;
+ddm_status upload_tables(ddm_ctx *ctx) {
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    if (!g_tab_init) {
+        for (int i = 0; i < 64; ++i) g_last_n[i] = g_last_q[i] = -1;
+        g_tab_init = true;
+    }
+    int n = ctx->prm.n_cheb, nq = ctx->prm.quad_near, dv = ctx->device & 63;
+    if (n == g_last_n[dv] && nq == g_last_q[dv]) return DDM_OK;
     GLTab h;
     memset(&h, 0, sizeof(h));
     double x[MAXGL], wt[MAXGL];
@@ -660,7 +673,8 @@ static ddm_status upload_tables(ddm_ctx *ctx) {
         h.bw[j] = (float)(((j & 1) ? -1.0 : 1.0) * sin(th));
     }
     DDM_CUDA_TRY(ctx, cudaMemcpyToSymbolAsync(c_gl, &h, sizeof(h), 0, cudaMemcpyHostToDevice, ctx->stream));
-    last_n = n; last_q = nq; last_dev = ctx->device;
+    DDM_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    g_last_n[dv] = n; g_last_q[dv] = nq;
     return DDM_OK;
 }
 
@@ -700,7 +714,7 @@ ddm_status self_blocks(ddm_ctx *ctx, ddm_tree *t, double dt) {
 }
 
 ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const double *x, double *y, int mode,
-                    int accumulate, double scale) {
+                    int accumulate, double scale, cudaStream_t stream_override) {
     const bool precise = (mode & DDM_MODE_PRECISE) != 0;
     mode &= ~DDM_MODE_PRECISE;
     if (!(hi > lo) || lo < 0.0) return ctx_fail(ctx, DDM_EINVAL, "matvec: need 0 <= tau_lo < tau_hi");
@@ -708,7 +722,7 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
     if (st) return st;
     st = ensure_workspace(ctx, t);
     if (st) return st;
-    cudaStream_t s = ctx->stream;
+    cudaStream_t s = stream_override ? stream_override : ctx->stream;
     int64_t N = t->n;
     int n = ctx->prm.n_cheb, n2 = n * n;
     const int TB = 256;

@@ -1,0 +1,275 @@
+// Continuous-batching request loop for fracture-set solves.
+//
+// Requests (geometry, loads, time step, number of steps) are queued by
+// ddm_submit.  A server thread with its own context and stream admits them
+// while the estimated device footprint fits the budget, keeps their trees,
+// solution history and Krylov arena resident, and advances all admitted
+// requests together: one round = one time step of every active request
+// (history sum, right-hand side, lockstep batched GMRES of all of them).
+// Finished requests leave after a round and queued ones join the next, so
+// requests that arrive while others run are admitted as slots and memory
+// free up.  ddm_poll reports completion.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "internal.h"
+
+extern "C" {
+ddm_status ddm_batch_create(ddm_ctx *ctx, ddm_tree *const *trees, int n, ddm_batch **out);
+void ddm_batch_destroy(ddm_batch *batch);
+ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *batch, double dt, const double *d_rhs, double *d_x,
+                                 const ddm_gmres_params *prm, ddm_gmres_info *infos);
+}
+
+namespace {
+using Clock = std::chrono::steady_clock;
+double ms_since(Clock::time_point a, Clock::time_point b) {
+    return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+struct Req {
+    uint64_t id;
+    ddm_request r;
+    Clock::time_point t_submit, t_admit, t_done;
+    ddm_tree *tree = nullptr;
+    double *hist = nullptr;      // steps x 3N solutions
+    double *rhs = nullptr;       // 3N
+    int step = 0;                // completed steps
+    int iters = 0;
+    double rel = 0.0;
+    size_t footprint = 0;
+    ddm_status status = DDM_PENDING;
+};
+}  // namespace
+
+struct ddm_server {
+    ddm_ctx *ctx = nullptr;              // server-owned context (own stream)
+    size_t budget = 0, used = 0;
+    int max_active = 0;
+    double tol = 1e-5;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<Req *> queue;
+    std::map<uint64_t, Req *> all;
+    uint64_t next_id = 1;
+    bool stop = false;
+    std::thread th;
+    long long rounds = 0;
+};
+
+namespace {
+
+size_t footprint(const ddm_request &r, int ncheb) {
+    size_t N = (size_t)r.n;
+    size_t per_tree = N * 400 + (size_t)16 * 49 * 16 * ncheb * ncheb * ncheb * ncheb * 4 / 2;
+    size_t vectors = N * 3 * 8 * (size_t)(r.steps + 1 + 60);
+    return per_tree + vectors;
+}
+
+void release(Req *q) {
+    if (q->tree) tree_free(q->tree);
+    if (q->hist) cudaFree(q->hist);
+    if (q->rhs) cudaFree(q->rhs);
+    q->tree = nullptr;
+    q->hist = q->rhs = nullptr;
+}
+
+void serve_loop(ddm_server *S) {
+    cudaSetDevice(S->ctx->device);
+    cudaStream_t s = S->ctx->stream;
+    std::vector<Req *> active;
+    while (true) {
+        // admission
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            if (active.empty())
+                S->cv.wait_for(lk, std::chrono::milliseconds(20), [&] { return S->stop || !S->queue.empty(); });
+            if (S->stop && S->queue.empty() && active.empty()) break;
+            while (!S->queue.empty() && (int)active.size() < S->max_active) {
+                Req *q = S->queue.front();
+                if (S->used + q->footprint > S->budget && !active.empty()) break;
+                S->queue.pop_front();
+                S->used += q->footprint;
+                q->t_admit = Clock::now();
+                lk.unlock();
+                ddm_status st = ddm_build_tree(S->ctx, q->r.d_xy, q->r.n, &q->tree);
+                if (!st && cudaMalloc(&q->hist, (size_t)q->r.steps * 3 * q->r.n * sizeof(double)) != cudaSuccess)
+                    st = DDM_ENOMEM;
+                if (!st && cudaMalloc(&q->rhs, (size_t)3 * q->r.n * sizeof(double)) != cudaSuccess) st = DDM_ENOMEM;
+                if (!st) cudaMemsetAsync(q->hist, 0, (size_t)q->r.steps * 3 * q->r.n * sizeof(double), s);
+                lk.lock();
+                if (st) {
+                    release(q);
+                    S->used -= q->footprint;
+                    q->status = st;
+                    q->t_done = Clock::now();
+                } else {
+                    active.push_back(q);
+                }
+            }
+        }
+        if (active.empty()) continue;
+        // one round: one time step of every active request (same dt per round
+        // group; requests are grouped by dt and system)
+        std::map<std::pair<double, int>, std::vector<Req *>> groups;
+        for (Req *q : active) groups[{q->r.dt, q->r.loads.system}].push_back(q);
+        for (auto &g : groups) {
+            std::vector<Req *> &rs = g.second;
+            double dt = g.first.first;
+            int sys = g.first.second;
+            ddm_status st = DDM_OK;
+            std::vector<ddm_tree *> trees;
+            int64_t tot = 0;
+            for (Req *q : rs) { trees.push_back(q->tree); tot += 3 * q->r.n; }
+            double *rhs = nullptr, *x = nullptr;
+            if (cudaMalloc(&rhs, tot * sizeof(double)) != cudaSuccess || cudaMalloc(&x, tot * sizeof(double)) != cudaSuccess)
+                st = DDM_ENOMEM;
+            int64_t o = 0;
+            for (Req *q : rs) {
+                if (st) break;
+                int64_t n3 = 3 * q->r.n;
+                st = ddm_rhs(S->ctx, q->tree, &q->r.loads, nullptr, q->rhs);
+                if (!st && q->step > 0) {
+                    std::vector<double> times(q->step + 2);
+                    for (int k = 0; k <= q->step + 1; ++k) times[k] = k * dt;
+                    st = ddm_history_apply(S->ctx, q->tree, q->hist, times.data(), q->step, q->rhs, DDM_MODE_FMM);
+                }
+                if (!st) cudaMemcpyAsync(rhs + o, q->rhs, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+                // initial guess: previous step (Dq of the 2N systems: 0)
+                if (q->step > 0)
+                    cudaMemcpyAsync(x + o, q->hist + (int64_t)(q->step - 1) * n3, n3 * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, s);
+                else
+                    cudaMemsetAsync(x + o, 0, n3 * sizeof(double), s);
+                if (!st && sys != DDM_SYS_PRESSURE) cudaMemsetAsync(x + o + 2 * q->r.n, 0, q->r.n * sizeof(double), s);
+                o += n3;
+            }
+            ddm_batch *B = nullptr;
+            std::vector<ddm_gmres_info> infos(rs.size());
+            if (!st) st = ddm_batch_create(S->ctx, trees.data(), (int)trees.size(), &B);
+            if (!st) {
+                ddm_gmres_params prm{sys, 50, 2000, S->tol, DDM_MODE_FMM};
+                st = ddm_batch_gmres_solve(S->ctx, B, dt, rhs, x, &prm, infos.data());
+                if (st == DDM_ENOTCONV) st = DDM_OK;      // per-request status below
+            }
+            o = 0;
+            for (size_t i = 0; i < rs.size(); ++i) {
+                Req *q = rs[i];
+                int64_t n3 = 3 * q->r.n;
+                if (!st) {
+                    cudaMemcpyAsync(q->hist + (int64_t)q->step * n3, x + o, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+                    q->iters += infos[i].iterations;
+                    q->rel = infos[i].rel_residual;
+                    if (!infos[i].converged) q->status = DDM_ENOTCONV;
+                    q->step += 1;
+                    if (q->step == q->r.steps)
+                        cudaMemcpyAsync(q->r.d_x, x + o, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+                } else {
+                    q->status = st;
+                    q->step = q->r.steps;
+                }
+                o += n3;
+            }
+            cudaStreamSynchronize(s);
+            if (B) ddm_batch_destroy(B);
+            if (rhs) cudaFree(rhs);
+            if (x) cudaFree(x);
+        }
+        // retire finished requests
+        std::lock_guard<std::mutex> lk(S->mu);
+        ++S->rounds;
+        std::vector<Req *> keep;
+        for (Req *q : active) {
+            if (q->step >= q->r.steps) {
+                release(q);
+                S->used -= q->footprint;
+                if (q->status == DDM_PENDING) q->status = DDM_OK;
+                q->t_done = Clock::now();
+            } else {
+                keep.push_back(q);
+            }
+        }
+        active.swap(keep);
+        S->cv.notify_all();
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+ddm_status ddm_server_create(ddm_ctx *ctx, size_t hbm_budget_bytes, int max_active, double tol, ddm_server **out) {
+    if (!ctx || !out || max_active <= 0 || !(tol > 0)) return ctx_fail(ctx, DDM_EINVAL, "ddm_server_create: bad arguments");
+    ddm_server *S = new ddm_server();
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) { delete S; return DDM_ECUDA; }
+    ddm_status r = ddm_create(&S->ctx, &ctx->mat, &ctx->prm, st);
+    if (r) { cudaStreamDestroy(st); delete S; return r; }
+    S->budget = hbm_budget_bytes ? hbm_budget_bytes : ((size_t)64 << 30);
+    S->max_active = max_active;
+    S->tol = tol;
+    S->th = std::thread(serve_loop, S);
+    *out = S;
+    return DDM_OK;
+}
+
+ddm_status ddm_submit(ddm_server *S, const ddm_request *req, uint64_t *ticket) {
+    if (!S || !req || !ticket || req->n <= 0 || !req->d_xy || !req->d_x || req->steps <= 0 || !(req->dt > 0) ||
+        req->loads.system < 0 || req->loads.system > 2)
+        return DDM_EINVAL;
+    Req *q = new Req();
+    q->r = *req;
+    q->t_submit = Clock::now();
+    q->footprint = footprint(*req, S->ctx->prm.n_cheb);
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (q->footprint > S->budget) { delete q; return DDM_ENOMEM; }
+    q->id = S->next_id++;
+    S->all[q->id] = q;
+    S->queue.push_back(q);
+    *ticket = q->id;
+    S->cv.notify_all();
+    return DDM_OK;
+}
+
+ddm_status ddm_poll(ddm_server *S, uint64_t ticket, ddm_result *res) {
+    if (!S || !res) return DDM_EINVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->all.find(ticket);
+    if (it == S->all.end()) return DDM_EINVAL;
+    Req *q = it->second;
+    res->status = q->status;
+    res->iterations = q->iters;
+    res->rel_residual = q->rel;
+    res->steps_done = q->step;
+    bool done = q->status != DDM_PENDING && q->t_done != Clock::time_point();
+    res->queue_ms = q->t_admit != Clock::time_point() ? ms_since(q->t_submit, q->t_admit) : -1.0;
+    res->latency_ms = done ? ms_since(q->t_submit, q->t_done) : -1.0;
+    if (!done) return DDM_PENDING;
+    return q->status;
+}
+
+void ddm_server_destroy(ddm_server *S) {
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv.notify_all();
+    if (S->th.joinable()) S->th.join();
+    for (auto &kv : S->all) {
+        release(kv.second);
+        delete kv.second;
+    }
+    cudaStream_t st = S->ctx->stream;
+    ddm_destroy(S->ctx);
+    cudaStreamDestroy(st);
+    delete S;
+}
+
+}  // extern "C"

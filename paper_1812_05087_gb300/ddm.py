@@ -27,7 +27,8 @@ _MODES = {"fmm": MODE_FMM, "dense": MODE_DENSE, "fmm+precise": MODE_FMM | MODE_P
 _SYSTEMS = {"pressure": SYS_PRESSURE, "impermeable": SYS_IMPERMEABLE, "rate": SYS_RATE}
 EXPORTS = ("ddm_create", "ddm_destroy", "ddm_last_error", "ddm_build_tree", "ddm_tree_destroy",
            "ddm_tree_get_info", "ddm_matvec", "ddm_history_apply", "ddm_rhs", "ddm_gmres_solve", "ddm_sif",
-           "ddm_profile", "ddm_profile_read")
+           "ddm_profile", "ddm_profile_read", "ddm_batch_create", "ddm_batch_destroy", "ddm_batch_matvec",
+           "ddm_batch_gmres_solve", "ddm_server_create", "ddm_submit", "ddm_poll", "ddm_server_destroy")
 NSTAGES = 10
 STAGES = ("charges", "self", "p2m", "m2m", "m2l", "l2l", "leaf", "dense", "krylov", "tree")
 
@@ -55,6 +56,16 @@ class ddm_loads(ctypes.Structure):
 class ddm_gmres_params(ctypes.Structure):
     _fields_ = [("system", ctypes.c_int), ("restart", ctypes.c_int), ("max_iters", ctypes.c_int),
                 ("tol", ctypes.c_double), ("mode", ctypes.c_int)]
+
+
+class ddm_request(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("d_xy", ctypes.c_void_p), ("loads", ddm_loads), ("dt", ctypes.c_double),
+                ("steps", ctypes.c_int), ("d_x", ctypes.c_void_p)]
+
+
+class ddm_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("steps_done", ctypes.c_int),
+                ("rel_residual", ctypes.c_double), ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
 
 
 class ddm_gmres_info(ctypes.Structure):
@@ -99,13 +110,25 @@ def load(build_if_missing: bool = True):
                                       ctypes.POINTER(ddm_gmres_info)]
         L.ddm_sif.argtypes = [_VP, _VP, _VP, _VP, ctypes.c_int, _VP, _VP]
         L.ddm_profile.argtypes = [_VP, ctypes.c_int]
+        L.ddm_server_create.argtypes = [_VP, ctypes.c_size_t, ctypes.c_int, ctypes.c_double, ctypes.POINTER(_VP)]
+        L.ddm_submit.argtypes = [_VP, ctypes.POINTER(ddm_request), ctypes.POINTER(ctypes.c_uint64)]
+        L.ddm_poll.argtypes = [_VP, ctypes.c_uint64, ctypes.POINTER(ddm_result)]
+        L.ddm_server_destroy.argtypes = [_VP]
+        L.ddm_server_destroy.restype = None
+        L.ddm_batch_create.argtypes = [_VP, ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP)]
+        L.ddm_batch_destroy.argtypes = [_VP]
+        L.ddm_batch_destroy.restype = None
+        L.ddm_batch_matvec.argtypes = [_VP, _VP, ctypes.c_double, _VP, _VP, ctypes.c_int]
+        L.ddm_batch_gmres_solve.argtypes = [_VP, _VP, ctypes.c_double, _VP, _VP, ctypes.POINTER(ddm_gmres_params),
+                                            ctypes.POINTER(ddm_gmres_info)]
         L.ddm_profile_read.argtypes = [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
         for name in EXPORTS:
             fn = getattr(L, name)
             if fn.restype is ctypes.c_int or name in ("ddm_create", "ddm_build_tree", "ddm_tree_get_info",
                                                       "ddm_matvec", "ddm_history_apply", "ddm_rhs",
                                                       "ddm_gmres_solve", "ddm_sif", "ddm_profile",
-                                                      "ddm_profile_read"):
+                                                      "ddm_profile_read", "ddm_batch_create", "ddm_batch_matvec",
+                                                      "ddm_batch_gmres_solve", "ddm_server_create", "ddm_submit", "ddm_poll", "ddm_server_destroy"):
                 fn.restype = ctypes.c_int
         _lib = L
         return L
@@ -220,6 +243,93 @@ def ddm_profile_read(ctx) -> dict:
     return {STAGES[k]: (ms[k], n[k]) for k in range(NSTAGES)}
 
 
+def ddm_batch_create(ctx, trees):
+    arr = (_VP * len(trees))(*[t for t in trees])
+    out = _VP()
+    _check(ctx, load().ddm_batch_create(ctx, arr, len(trees), ctypes.byref(out)), "ddm_batch_create")
+    return out
+
+
+def ddm_batch_destroy(batch):
+    load().ddm_batch_destroy(batch)
+
+
+def ddm_batch_matvec(ctx, batch, dt, x, y, mode=MODE_FMM):
+    _check(ctx, load().ddm_batch_matvec(ctx, batch, float(dt), _VP(_dev(x, None, "x")), _VP(_dev(y, None, "y")),
+                                        int(mode)), "ddm_batch_matvec")
+
+
+def ddm_batch_gmres_solve(ctx, batch, n, dt, rhs, x, system=SYS_PRESSURE, restart=50, max_iters=1000, tol=1e-6,
+                          mode=MODE_FMM, raise_on_notconv=True):
+    prm = ddm_gmres_params(int(system), int(restart), int(max_iters), float(tol), int(mode))
+    infos = (ddm_gmres_info * n)()
+    st = load().ddm_batch_gmres_solve(ctx, batch, float(dt), _VP(_dev(rhs, None, "rhs")), _VP(_dev(x, None, "x")),
+                                      ctypes.byref(prm), infos)
+    res = [{k: getattr(i, k) for k, _ in ddm_gmres_info._fields_} for i in infos]
+    if st == DDM_ENOTCONV and not raise_on_notconv:
+        return res
+    _check(ctx, st, "ddm_batch_gmres_solve")
+    return res
+
+
+def ddm_server_create(ctx, budget_bytes=0, max_active=64, tol=1e-5):
+    out = _VP()
+    _check(ctx, load().ddm_server_create(ctx, int(budget_bytes), int(max_active), float(tol), ctypes.byref(out)),
+           "ddm_server_create")
+    return out
+
+
+def ddm_submit(server, xy: torch.Tensor, x_out: torch.Tensor, dt, steps, sigma_H=0.0, sigma_h=0.0, p_f=0.0, p0=0.0,
+               system=SYS_PRESSURE) -> int:
+    n = xy.numel() // 4
+    req = ddm_request(n, _dev(xy, 4 * n, "xy"), ddm_loads(float(sigma_H), float(sigma_h), float(p_f), float(p0),
+                                                          int(system)), float(dt), int(steps), _dev(x_out, 3 * n, "x"))
+    t = ctypes.c_uint64()
+    st = load().ddm_submit(server, ctypes.byref(req), ctypes.byref(t))
+    if st != DDM_OK:
+        raise DDMError(st, "ddm_submit")
+    return t.value
+
+
+def ddm_poll(server, ticket) -> dict:
+    r = ddm_result()
+    st = load().ddm_poll(server, int(ticket), ctypes.byref(r))
+    d = {k: getattr(r, k) for k, _ in ddm_result._fields_}
+    d["poll"] = st
+    return d
+
+
+def ddm_server_destroy(server):
+    load().ddm_server_destroy(server)
+
+
+class Server:
+    """Continuous-batching request loop (see include/ddm.h)."""
+
+    def __init__(self, ctx: "Context", budget_bytes=0, max_active=64, tol=1e-5):
+        self.ptr = ddm_server_create(ctx.ptr, budget_bytes, max_active, tol)
+        self._keep = {}
+
+    def submit(self, xy, x_out, dt, steps, system="pressure", **loads) -> int:
+        t = ddm_submit(self.ptr, xy, x_out, dt, steps, system=_SYSTEMS[system], **loads)
+        self._keep[t] = (xy, x_out)
+        return t
+
+    def poll(self, ticket) -> dict:
+        return ddm_poll(self.ptr, ticket)
+
+    def close(self):
+        if self.ptr:
+            ddm_server_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ---------------------------------------------------------------- wrappers
 class Tree:
     def __init__(self, ctx: "Context", xy: torch.Tensor):
@@ -233,6 +343,42 @@ class Tree:
     def close(self):
         if self.ptr:
             ddm_tree_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent problems solved together (one graph launch per product)."""
+
+    def __init__(self, ctx: "Context", trees):
+        self.ctx = ctx
+        self.trees = list(trees)
+        self.sizes = [t.n for t in self.trees]
+        self.offsets = [0]
+        for n in self.sizes:
+            self.offsets.append(self.offsets[-1] + 3 * n)
+        self.ptr = ddm_batch_create(ctx.ptr, [t.ptr for t in self.trees])
+
+    def matvec(self, x, dt, mode="fmm", out=None):
+        out = torch.empty_like(x) if out is None else out
+        ddm_batch_matvec(self.ctx.ptr, self.ptr, dt, x, out, _MODES[mode])
+        return out
+
+    def gmres_solve(self, dt, rhs, x=None, system="pressure", restart=50, max_iters=1000, tol=1e-6, mode="fmm",
+                    raise_on_notconv=True):
+        x = torch.zeros(self.offsets[-1], dtype=torch.float64, device="cuda") if x is None else x
+        infos = ddm_batch_gmres_solve(self.ctx.ptr, self.ptr, len(self.trees), dt, rhs, x, _SYSTEMS[system], restart,
+                                      max_iters, tol, _MODES[mode], raise_on_notconv)
+        return x, infos
+
+    def close(self):
+        if self.ptr:
+            ddm_batch_destroy(self.ptr)
             self.ptr = None
 
     def __del__(self):
@@ -279,6 +425,9 @@ class Context:
         KII = torch.empty_like(KI)
         ddm_sif(self.ptr, tree.ptr, x, tips, KI, KII)
         return KI, KII
+
+    def batch(self, trees) -> Batch:
+        return Batch(self, trees)
 
     def profile(self, enable=True):
         ddm_profile(self.ptr, enable)
