@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--solves", type=int, default=10)
     ap.add_argument("--oracle-rows", type=int, default=12)
     ap.add_argument("--no-oracle", action="store_true")
+    ap.add_argument("--hist-lags", type=int, default=10)
+    ap.add_argument("--batch-problems", type=int, default=512)
+    ap.add_argument("--serve-seconds", type=float, default=4.0)
+    ap.add_argument("--serve-rate", type=float, default=50.0)
     return ap.parse_args()
 
 
@@ -291,6 +295,87 @@ def main():
     t_e2e = timed(e2e, args.steps, args.warmup)
     ms_e2e = float(np.mean(t_e2e))
 
+    # ---------------- history sum (time marching): H past steps of dt
+    H = args.hist_lags
+    hist = torch.as_tensor(np.stack([inputs.unknowns(N, seed=300 + k) for k in range(H)]), device="cuda")
+    times = [DT * k for k in range(H + 2)]
+    rhs_h = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
+    t_hist = timed(lambda: ctx.history_apply(tree, hist, times, rhs_h), 3, 1)
+    ms_hist = float(np.mean(t_hist))
+
+    # ---------------- batched uneven problems (one graph launch per product)
+    batch_res = None
+    if args.batch_problems > 0:
+        probs = inputs.batch_problems(args.batch_problems)
+        bctx = Context(inputs.MATERIAL, n_cheb=args.n_cheb, leaf_size=args.leaf)
+        t0 = time.perf_counter()
+        btrees = [bctx.build_tree(torch.as_tensor(pr["xy"], device="cuda")) for pr in probs]
+        torch.cuda.synchronize()
+        t_trees = time.perf_counter() - t0
+        brhs = torch.cat([bctx.rhs(t, system="pressure", **LOADS) for t in btrees])
+        batch = bctx.batch(btrees)
+        bx = torch.zeros_like(brhs)
+        batch.gmres_solve(DT, brhs, bx.zero_(), tol=1e-5, raise_on_notconv=False)      # capture + warm
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        binfos = batch.gmres_solve(DT, brhs, bx.zero_(), tol=1e-5, raise_on_notconv=False)[1]
+        torch.cuda.synchronize()
+        t_batch = time.perf_counter() - t0
+        # the same problems one at a time (a sample, extrapolated per problem)
+        ks = list(range(0, len(btrees), max(1, len(btrees) // 24)))
+        t0 = time.perf_counter()
+        for k in ks:
+            lo, hi = batch.offsets[k], batch.offsets[k + 1]
+            bctx.gmres_solve(btrees[k], DT, brhs[lo:hi].contiguous(), tol=1e-5, raise_on_notconv=False)
+        torch.cuda.synchronize()
+        t_seq = (time.perf_counter() - t0) / len(ks) * len(btrees)
+        batch_res = {"problems": len(btrees), "elements": int(sum(t.n for t in btrees)),
+                     "batched_solve_s": t_batch, "batched_solves_per_s": len(btrees) / t_batch,
+                     "sequential_solves_per_s": len(btrees) / t_seq, "speedup": t_seq / t_batch,
+                     "converged": int(sum(i["converged"] for i in binfos)),
+                     "max_iterations": int(max(i["iterations"] for i in binfos)), "tree_build_s": t_trees}
+        batch.close()
+        for t in btrees:
+            t.close()
+
+    # ---------------- serving: Poisson arrivals, continuous batching
+    serve_res = None
+    if args.serve_seconds > 0:
+        from paper_1812_05087_gb300.ddm import Server
+        trace = inputs.serving_trace(duration=args.serve_seconds, rate=args.serve_rate, nmin=1000, nmax=20000)
+        geos = []
+        for rq in trace:
+            nf = max(1, min(100, rq["N"] // 100))
+            box = 200.0 * (rq["N"] / 20000.0) ** 0.5 + 12.0
+            segs = inputs.random_fracture_segments(nf, box, 2.0, min(10.0, box / 2), max(10, rq["N"] // nf),
+                                                   seed=rq["seed"])
+            geos.append(torch.as_tensor(inputs.assemble(segs), device="cuda"))
+        steps = [1 + rq["steps"] % 5 for rq in trace]       # 1..5 steps per request
+        srv = Server(ctx, max_active=32, tol=1e-5)
+        outs = [torch.zeros(3 * (g.numel() // 4), dtype=torch.float64, device="cuda") for g in geos]
+        tickets = []
+        t0 = time.perf_counter()
+        for rq, g, o, st_ in zip(trace, geos, outs, steps):
+            while time.perf_counter() - t0 < rq["t"]:
+                time.sleep(0.0005)
+            tickets.append(srv.submit(g, o, DT, st_, **LOADS))
+        done = {}
+        while len(done) < len(tickets) and time.perf_counter() - t0 < args.serve_seconds + 120:
+            for tk in tickets:
+                if tk not in done:
+                    r = srv.poll(tk)
+                    if r["poll"] != 6:
+                        done[tk] = r
+            time.sleep(0.002)
+        t_all = time.perf_counter() - t0
+        srv.close()
+        lats = sorted(r["latency_ms"] for r in done.values() if r["status"] == 0)
+        serve_res = {"requests": len(tickets), "completed": len(lats), "time_step_solves": int(sum(steps)),
+                     "wall_s": t_all, "solves_per_s": sum(steps) / t_all, "requests_per_s": len(lats) / t_all,
+                     "p50_ms": lats[len(lats) // 2] if lats else None,
+                     "p99_ms": lats[min(len(lats) - 1, int(0.99 * len(lats)))] if lats else None,
+                     "trace": f"Poisson {args.serve_rate}/s for {args.serve_seconds} s, N log-uniform [1e3, 2e4], 1-5 steps"}
+
     # ---------------- roofline of the dominant kernel
     st = {k: v for k, v in stages.items() if v[1] > 0 and k in STAGE_KERNEL}
     dom = max(st, key=lambda k: st[k][0])
@@ -355,6 +440,8 @@ def main():
         "dense_melem_s": world * N / (ms_dense * 1e-3) / 1e6, "dense_ms_per_matvec": ms_dense,
         "dense_solve_ms": dense_solve_ms, "dense_gmres_iterations": dinfo["iterations"],
         "fmm_speedup_vs_dense": ms_dense / ms_fmm,
+        "history": {"lags": H, "ms": ms_hist, "melem_lags_per_s": N * H / (ms_hist * 1e-3) / 1e6},
+        "batched": batch_res, "serving": serve_res,
         "error": err,
         "stages_ms_per_matvec": {k: v[0] / 3 for k, v in stages.items() if v[1] > 0},
         "roofline": roof, "cpu_baseline": cpu,

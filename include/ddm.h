@@ -165,7 +165,10 @@ typedef struct {
 
 /* Solve [K(dt)] x = rhs restricted to the chosen system with restarted GMRES
  * (paper Sec. 4, "modified GMRES with FMM products") in FP64, right
- * block-Jacobi preconditioned by each element's own 3x3 (2x2) block.
+ * preconditioned by block Jacobi over fracture chains: elements that share
+ * end points are cut into blocks of <= 64 elements whose own influence
+ * matrices are inverted on the device (FP32) once per (dt, system); an
+ * element on no chain is a block of its own.
  * d_rhs: 3N doubles (rows not in the system are ignored).  d_x: 3N doubles,
  * in: initial guess (and the prescribed Dq for 2N systems), out: solution.
  * Mixed precision: Arnoldi steps use the FP32-pair operator; the true

@@ -174,13 +174,15 @@ inline unsigned nblk(int64_t len, int t = 256) { return (unsigned)((len + t - 1)
 struct GmresWork {
     int64_t cap_len = 0;
     int cap_m = 0;
+    cudaStream_t st = nullptr;
     double *V = nullptr, *w = nullptr, *z = nullptr, *full = nullptr, *y3 = nullptr, *b = nullptr;
     double *h = nullptr, *hcol = nullptr, *nrm = nullptr, *Minv = nullptr, *yv = nullptr;
     void release() {
         double *ps[] = {V, w, z, full, y3, b, h, hcol, nrm, Minv, yv};
-        for (double *p : ps)
-            if (p) cudaFree(p);
+        cudaStream_t s = st;
+        for (double *p : ps) dfree(p, s);
         *this = GmresWork();
+        st = s;
     }
 };
 
@@ -201,6 +203,13 @@ ddm_status ddm_create(ddm_ctx **out, const ddm_material *mat, const ddm_fmm_para
     c->prm = p;
     c->stream = (cudaStream_t)cuda_stream;
     if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return DDM_ECUDA; }
+    {   // keep freed pool memory inside the process (stream-ordered reuse)
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, c->device) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+    }
     const ddm_material &m = *mat;
     double G = m.G, nu = m.nu, nuu = m.nu_u, B = m.B;
     double alpha = 3 * (nuu - nu) / (B * (1 - 2 * nu) * (1 + nuu));
@@ -349,14 +358,15 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
     if (g.cap_len < len || g.cap_m < m) {
         g.release();
         size_t v3 = 3 * N * sizeof(double);
-        bool ok = cudaMalloc(&g.V, (size_t)(m + 1) * len * sizeof(double)) == cudaSuccess &&
-                  cudaMalloc(&g.w, v3) == cudaSuccess && cudaMalloc(&g.z, v3) == cudaSuccess &&
-                  cudaMalloc(&g.full, v3) == cudaSuccess && cudaMalloc(&g.y3, v3) == cudaSuccess &&
-                  cudaMalloc(&g.b, v3) == cudaSuccess && cudaMalloc(&g.h, (m + 2) * sizeof(double)) == cudaSuccess &&
-                  cudaMalloc(&g.hcol, (m + 2) * sizeof(double)) == cudaSuccess &&
-                  cudaMalloc(&g.nrm, sizeof(double)) == cudaSuccess &&
-                  cudaMalloc(&g.Minv, 9 * N * sizeof(double)) == cudaSuccess &&
-                  cudaMalloc(&g.yv, (m + 1) * sizeof(double)) == cudaSuccess;
+        g.st = s;
+        bool ok = dalloc(&g.V, (size_t)(m + 1) * len * sizeof(double), s) == cudaSuccess &&
+                  dalloc(&g.w, v3, s) == cudaSuccess && dalloc(&g.z, v3, s) == cudaSuccess &&
+                  dalloc(&g.full, v3, s) == cudaSuccess && dalloc(&g.y3, v3, s) == cudaSuccess &&
+                  dalloc(&g.b, v3, s) == cudaSuccess && dalloc(&g.h, (m + 2) * sizeof(double), s) == cudaSuccess &&
+                  dalloc(&g.hcol, (m + 2) * sizeof(double), s) == cudaSuccess &&
+                  dalloc(&g.nrm, sizeof(double), s) == cudaSuccess &&
+                  dalloc(&g.Minv, 9 * N * sizeof(double), s) == cudaSuccess &&
+                  dalloc(&g.yv, (m + 1) * sizeof(double), s) == cudaSuccess;
         if (!ok) { g.release(); return ctx_fail(ctx, DDM_ENOMEM, "GMRES workspace allocation failed"); }
         g.cap_len = len; g.cap_m = m;
     }
@@ -379,9 +389,8 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
         out = sqrt(out);
         return DDM_OK;
     };
-    // preconditioner
-    if ((st = self_blocks(ctx, t, dt))) return st;
-    k_invert<<<nblk(N), 256, 0, s>>>(t->self_blk, N, sys, g.Minv);
+    // preconditioner: inverted chain blocks of this (dt, system)
+    if ((st = pb_prepare(ctx, t, dt, sys, s))) return st;
     // b = restrict(rhs) - restrict(A [0; 0; Dq]) for the 2N systems
     k_restrict<<<nblk(N), 256, 0, s>>>(d_rhs, N, sys, 0, g.b);
     if (sys != DDM_SYS_PRESSURE) {
@@ -419,8 +428,9 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
         int j = 0;
         for (; j < m && iters < P.max_iters; ++j, ++iters) {
             double *vj = g.V + (int64_t)j * len;
-            k_precond<<<nblk(N), 256, 0, s>>>(g.Minv, N, nc, vj, g.z);
-            if ((st = apply(g.z, g.w, mode))) return st;
+            if ((st = pb_apply(ctx, t, sys, vj, g.full, s))) return st;
+            if ((st = op_apply(ctx, t, 0.0, dt, g.full, g.y3, mode, 0, 1.0))) return st;
+            k_restrict<<<nblk(N), 256, 0, s>>>(g.y3, N, sys, 1, g.w);
             prof_end(ctx, 8, 8);      // precond, restrict, 2x(dots, sub), norm, scale
             // CGS2 against V[0..j]
             DDM_CUDA_TRY(ctx, cudaMemsetAsync(g.hcol, 0, (m + 2) * sizeof(double), s));
@@ -461,8 +471,8 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
         if (j > 0) {
             DDM_CUDA_TRY(ctx, cudaMemcpyAsync(g.yv, yv.data(), j * sizeof(double), cudaMemcpyHostToDevice, s));
             k_comb<<<nblk(len), 256, 0, s>>>(g.V, len, j, g.yv, g.w, len);
-            k_precond<<<nblk(N), 256, 0, s>>>(g.Minv, N, nc, g.w, g.z);
-            k_axpy<<<nblk(len), 256, 0, s>>>(1.0, g.z, d_x, len);
+            if ((st = pb_apply(ctx, t, sys, g.w, g.full, s))) return st;
+            k_axpy<<<nblk(len), 256, 0, s>>>(1.0, g.full, d_x, len);
             DDM_CUDA_TRY(ctx, cudaStreamSynchronize(s));    // yv host buffer goes out of scope
         }
         ++restarts;

@@ -170,14 +170,15 @@ struct ddm_batch {
     int g_op_mode = -1, g_prod_mode = -1, g_res_mode = -1, g_op_sys = -1, g_res_sys = -1;
     const double *g_prod_x = nullptr, *g_res_x = nullptr;
     long long k_op = 0, k_prod = 0, k_res = 0;   // kernels per graph launch
+    std::vector<int> op_set;                     // problems in g_op / g_res
     double *g_prod_y = nullptr;
     cudaStream_t fork[NSTREAMS] = {};
     cudaStream_t cap = nullptr;
+    cudaStream_t ast = nullptr;            // stream of the arena allocations
     cudaEvent_t ev_fork[NSTREAMS] = {}, ev_join[NSTREAMS] = {};
     void free_solver() {
         void *ps[] = {prob, blk, V, w, vin, b, tmp, Minv, h, hcol, nrm, coef, Y};
-        for (void *p : ps)
-            if (p) cudaFree(p);
+        for (void *p : ps) dfree(p, ast);
         prob = nullptr; blk = nullptr; V = w = vin = b = tmp = Minv = h = hcol = nrm = coef = Y = nullptr;
         sys = -1; m = 0;
     }
@@ -193,7 +194,8 @@ namespace {
 
 // capture fn(p, stream) for every problem into one graph on ctx->stream
 template <class Fn>
-ddm_status capture(ddm_ctx *ctx, ddm_batch *B, cudaGraphExec_t *out, long long *kernels, Fn fn) {
+ddm_status capture(ddm_ctx *ctx, ddm_batch *B, cudaGraphExec_t *out, long long *kernels, const std::vector<int> &idx,
+                   Fn fn) {
     // capture on the batch's own stream; the graph is launched on the context stream
     cudaStream_t s = B->cap;
     DDM_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
@@ -205,10 +207,10 @@ ddm_status capture(ddm_ctx *ctx, ddm_batch *B, cudaGraphExec_t *out, long long *
     cudaEvent_t e0;
     cudaEventCreateWithFlags(&e0, cudaEventDisableTiming);
     cudaEventRecord(e0, s);
-    int ns = std::min(NSTREAMS, B->P);
+    int ns = std::max(1, std::min<int>(NSTREAMS, (int)idx.size()));
     for (int k = 0; k < ns; ++k) cudaStreamWaitEvent(B->fork[k], e0, 0);
     ddm_status st = DDM_OK;
-    for (int p = 0; p < B->P && st == DDM_OK; ++p) st = fn(p, B->fork[p % ns]);
+    for (size_t q = 0; q < idx.size() && st == DDM_OK; ++q) st = fn(idx[q], B->fork[q % ns]);
     for (int k = 0; k < ns; ++k) {
         cudaEventRecord(B->ev_join[k], B->fork[k]);
         cudaStreamWaitEvent(s, B->ev_join[k], 0);
@@ -253,12 +255,13 @@ ddm_status ddm_batch_create(ddm_ctx *ctx, ddm_tree *const *trees, int n, ddm_bat
         o += 3 * trees[p]->n;
     }
     B->tot3 = o;
-    if (cudaMalloc(&B->full, o * sizeof(double)) != cudaSuccess || cudaMalloc(&B->y3, o * sizeof(double)) != cudaSuccess) {
+    B->ast = ctx->stream;
+    if (dalloc(&B->full, o * sizeof(double), B->ast) != cudaSuccess || dalloc(&B->y3, o * sizeof(double), B->ast) != cudaSuccess) {
         delete B;
         return ctx_fail(ctx, DDM_ENOMEM, "batch arena allocation failed");
     }
-    cudaMemset(B->full, 0, o * sizeof(double));
-    cudaMemset(B->y3, 0, o * sizeof(double));
+    cudaMemsetAsync(B->full, 0, o * sizeof(double), B->ast);
+    cudaMemsetAsync(B->y3, 0, o * sizeof(double), B->ast);
     cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking);
     for (int k = 0; k < NSTREAMS; ++k) {
         cudaStreamCreateWithFlags(&B->fork[k], cudaStreamNonBlocking);
@@ -272,8 +275,8 @@ void ddm_batch_destroy(ddm_batch *B) {
     if (!B) return;
     B->free_graphs();
     B->free_solver();
-    if (B->full) cudaFree(B->full);
-    if (B->y3) cudaFree(B->y3);
+    dfree(B->full, B->ast);
+    dfree(B->y3, B->ast);
     if (B->cap) cudaStreamDestroy(B->cap);
     for (int k = 0; k < NSTREAMS; ++k) {
         if (B->fork[k]) cudaStreamDestroy(B->fork[k]);
@@ -291,7 +294,9 @@ ddm_status ddm_batch_matvec(ddm_ctx *ctx, ddm_batch *B, double dt, const double 
         DDM_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
         int saved = ctx->prof.on;
         ctx->prof.on = 0;
-        st = capture(ctx, B, &B->g_prod, &B->k_prod, [&](int p, cudaStream_t s) {
+        std::vector<int> all(B->P);
+        for (int p = 0; p < B->P; ++p) all[p] = p;
+        st = capture(ctx, B, &B->g_prod, &B->k_prod, all, [&](int p, cudaStream_t s) {
             return op_apply(ctx, B->trees[p], 0.0, dt, d_x + B->off3[p], d_y + B->off3[p], mode, 0, 1.0, s);
         });
         ctx->prof.on = saved;
@@ -338,19 +343,19 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
                 hb.push_back(SegBlk{p, a, std::min(a + SEG_CHUNK, B->offs[p + 1])});
         }
         B->nblk = (int)hb.size();
-        bool ok = cudaMalloc(&B->prob, L * sizeof(int32_t)) == cudaSuccess &&
-                  cudaMalloc(&B->blk, hb.size() * sizeof(SegBlk)) == cudaSuccess &&
-                  cudaMalloc(&B->V, (size_t)(m + 1) * L * sizeof(double)) == cudaSuccess &&
-                  cudaMalloc(&B->w, L * sizeof(double)) == cudaSuccess &&
-                  cudaMalloc(&B->vin, L * sizeof(double)) == cudaSuccess &&
-                  cudaMalloc(&B->b, L * sizeof(double)) == cudaSuccess &&
-                  cudaMalloc(&B->tmp, L * sizeof(double)) == cudaSuccess &&
-                  cudaMalloc(&B->Minv, B->minv_off[P] * sizeof(double)) == cudaSuccess &&
-                  cudaMalloc(&B->h, (size_t)P * hs * sizeof(double)) == cudaSuccess &&
-                  cudaMalloc(&B->hcol, (size_t)P * hs * sizeof(double)) == cudaSuccess &&
-                  cudaMalloc(&B->nrm, (size_t)P * hs * sizeof(double)) == cudaSuccess &&
-                  cudaMalloc(&B->coef, P * sizeof(double)) == cudaSuccess &&
-                  cudaMalloc(&B->Y, (size_t)P * hs * sizeof(double)) == cudaSuccess;
+        bool ok = dalloc(&B->prob, L * sizeof(int32_t), s) == cudaSuccess &&
+                  dalloc(&B->blk, hb.size() * sizeof(SegBlk), s) == cudaSuccess &&
+                  dalloc(&B->V, (size_t)(m + 1) * L * sizeof(double), s) == cudaSuccess &&
+                  dalloc(&B->w, L * sizeof(double), s) == cudaSuccess &&
+                  dalloc(&B->vin, L * sizeof(double), s) == cudaSuccess &&
+                  dalloc(&B->b, L * sizeof(double), s) == cudaSuccess &&
+                  dalloc(&B->tmp, L * sizeof(double), s) == cudaSuccess &&
+                  dalloc(&B->Minv, B->minv_off[P] * sizeof(double), s) == cudaSuccess &&
+                  dalloc(&B->h, (size_t)P * hs * sizeof(double), s) == cudaSuccess &&
+                  dalloc(&B->hcol, (size_t)P * hs * sizeof(double), s) == cudaSuccess &&
+                  dalloc(&B->nrm, (size_t)P * hs * sizeof(double), s) == cudaSuccess &&
+                  dalloc(&B->coef, P * sizeof(double), s) == cudaSuccess &&
+                  dalloc(&B->Y, (size_t)P * hs * sizeof(double), s) == cudaSuccess;
         if (!ok) { B->free_solver(); return ctx_fail(ctx, DDM_ENOMEM, "batch GMRES arena allocation failed"); }
         cudaMemcpyAsync(B->prob, hp.data(), L * sizeof(int32_t), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(B->blk, hb.data(), hb.size() * sizeof(SegBlk), cudaMemcpyHostToDevice, s);
@@ -359,32 +364,25 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
         DDM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     }
     const int64_t L = B->L;
-    // preconditioner blocks per problem
-    for (int p = 0; p < P; ++p) {
-        if ((st = self_blocks(ctx, B->trees[p], dt))) return st;
-        k_invert_b<<<nb(B->N[p]), BT, 0, s>>>(B->trees[p]->self_blk, B->N[p], sys, B->Minv + B->minv_off[p]);
-    }
+    // preconditioner blocks per problem (inverted fracture-chain blocks)
+    for (int p = 0; p < P; ++p)
+        if ((st = pb_prepare(ctx, B->trees[p], dt, sys, s))) return st;
     // graphs: preconditioned operator vin -> w, residual operator (precise) x -> tmp
     int saved = ctx->prof.on;
     ctx->prof.on = 0;
-    if (!B->g_op || B->g_op_dt != dt || B->g_op_mode != mode || B->g_op_sys != sys) {
-        if ((st = warm(ctx, B, dt, mode))) { ctx->prof.on = saved; return st; }
-        DDM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-        st = capture(ctx, B, &B->g_op, &B->k_op, [&](int p, cudaStream_t ps) -> ddm_status {
+    auto capture_op = [&](const std::vector<int> &idx) -> ddm_status {
+        return capture(ctx, B, &B->g_op, &B->k_op, idx, [&](int p, cudaStream_t ps) -> ddm_status {
             int64_t n = B->N[p];
-            k_precond_to3<<<nb(n), BT, 0, ps>>>(B->Minv + B->minv_off[p], n, nc, B->vin + B->offs[p], B->full + B->off3[p]);
-            ddm_status e = op_apply(ctx, B->trees[p], 0.0, dt, B->full + B->off3[p], B->y3 + B->off3[p], mode, 0, 1.0, ps);
+            ddm_status e = pb_apply(ctx, B->trees[p], sys, B->vin + B->offs[p], B->full + B->off3[p], ps);
+            if (e) return e;
+            e = op_apply(ctx, B->trees[p], 0.0, dt, B->full + B->off3[p], B->y3 + B->off3[p], mode, 0, 1.0, ps);
             if (e) return e;
             k_restrict_b<<<nb(n), BT, 0, ps>>>(B->y3 + B->off3[p], n, sys, 1, B->w + B->offs[p]);
             return DDM_OK;
         });
-        if (st) { ctx->prof.on = saved; return st; }
-        B->g_op_dt = dt; B->g_op_mode = mode; B->g_op_sys = sys;
-    }
-    if (!B->g_res || B->g_res_dt != dt || B->g_res_mode != mode || B->g_res_sys != sys || B->g_res_x != d_x) {
-        if ((st = warm(ctx, B, dt, mode | DDM_MODE_PRECISE))) { ctx->prof.on = saved; return st; }
-        DDM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-        st = capture(ctx, B, &B->g_res, &B->k_res, [&](int p, cudaStream_t ps) -> ddm_status {
+    };
+    auto capture_res = [&](const std::vector<int> &idx) -> ddm_status {
+        return capture(ctx, B, &B->g_res, &B->k_res, idx, [&](int p, cudaStream_t ps) -> ddm_status {
             int64_t n = B->N[p];
             k_copy_to3<<<nb(n), BT, 0, ps>>>(d_x + B->off3[p], n, nc, B->full + B->off3[p]);
             ddm_status e = op_apply(ctx, B->trees[p], 0.0, dt, B->full + B->off3[p], B->y3 + B->off3[p],
@@ -393,9 +391,13 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
             k_restrict_b<<<nb(n), BT, 0, ps>>>(B->y3 + B->off3[p], n, sys, 1, B->tmp + B->offs[p]);
             return DDM_OK;
         });
-        if (st) { ctx->prof.on = saved; return st; }
-        B->g_res_dt = dt; B->g_res_mode = mode; B->g_res_sys = sys; B->g_res_x = d_x;
-    }
+    };
+    std::vector<int> every(P);
+    for (int p = 0; p < P; ++p) every[p] = p;
+    if ((st = warm(ctx, B, dt, mode)) || (st = warm(ctx, B, dt, mode | DDM_MODE_PRECISE))) { ctx->prof.on = saved; return st; }
+    DDM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    if ((st = capture_op(every)) || (st = capture_res(every))) { ctx->prof.on = saved; return st; }
+    B->op_set = every;
     ctx->prof.on = saved;
     // b = restrict(rhs) (- restrict(A [0; 0; Dq]) for the 2N systems)
     for (int p = 0; p < P; ++p) {
@@ -440,8 +442,8 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
         if ((st = seg_norms(B->w, beta))) return st;
         int nact = 0;
         for (int p = 0; p < P; ++p) {
-            rel[p] = beta[p] / bn[p];
             if (!active[p]) continue;
+            rel[p] = beta[p] / bn[p];
             if (rel[p] < Pm.tol) { conv[p] = 1; active[p] = 0; continue; }
             if (rel[p] < 0.9 * best[p]) { best[p] = rel[p]; stall[p] = 0; }
             else if (++stall[p] >= 3) { active[p] = 0; continue; }
@@ -449,6 +451,17 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
             ++nact;
         }
         if (nact == 0 || total >= Pm.max_iters) break;
+        // drop converged problems from the graphs once a quarter of them left
+        if (nact < 0.75 * (double)B->op_set.size()) {
+            std::vector<int> act;
+            for (int p = 0; p < P; ++p)
+                if (active[p]) act.push_back(p);
+            int sv2 = ctx->prof.on;
+            ctx->prof.on = 0;
+            if ((st = capture_op(act)) || (st = capture_res(act))) { ctx->prof.on = sv2; return st; }
+            ctx->prof.on = sv2;
+            B->op_set = act;
+        }
         for (int p = 0; p < P; ++p) coef[p] = active[p] && beta[p] > 0 ? -1.0 / beta[p] : 0.0;
         DDM_CUDA_TRY(ctx, cudaMemcpyAsync(B->coef, coef.data(), P * sizeof(double), cudaMemcpyHostToDevice, s));
         k_v0_seg<<<nb(L), BT, 0, s>>>(B->w, B->coef, B->prob, L, B->V);
@@ -519,9 +532,10 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
             DDM_CUDA_TRY(ctx, cudaMemcpyAsync(B->Y, Yh.data(), (size_t)P * hs * sizeof(double), cudaMemcpyHostToDevice, s));
             k_comb_seg<<<nb(L), BT, 0, s>>>(B->V, L, jm, B->Y, hs, B->prob, L, B->tmp);
             for (int p = 0; p < P; ++p)
-                if (active[p])
-                    k_add_precond<<<nb(B->N[p]), BT, 0, s>>>(B->Minv + B->minv_off[p], B->N[p], nc, B->tmp + B->offs[p],
-                                                             d_x + B->off3[p]);
+                if (active[p]) {
+                    if ((st = pb_apply(ctx, B->trees[p], sys, B->tmp + B->offs[p], B->full + B->off3[p], s))) return st;
+                    k_axpy_b<<<nb(nc * B->N[p]), BT, 0, s>>>(1.0, B->full + B->off3[p], d_x + B->off3[p], nc * B->N[p]);
+                }
             DDM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
         }
     }

@@ -85,34 +85,6 @@ __global__ void k_charges(const double *x, const int64_t *perm, const float4 *fr
 }
 
 // --------------------------------------------------------- own element (FP64)
-__device__ void self_field(const KConst<double> &k, const Win<double> &w, double a, double tx, double ty,
-                           double Ds, double Dn, double Dq, double out[3]) {
-    double nx = -ty, ny = tx;
-    double Dx = Ds * tx + Dn * nx, Dy = Ds * ty + Dn * ny;
-    double g[4] = {0, 0, 0, 0};
-    disl_field<double>(k, a * tx, a * ty, Dx, Dy, w, 1.0, g);      // target - start = a t
-    disl_field<double>(k, -a * tx, -a * ty, Dx, Dy, w, -1.0, g);   // target - end   = -a t
-    double ss, sn;
-    to_local<double>(tx, ty, g, ss, sn);
-    double p = g[3];
-    // fluid source on its own element: closed forms along the line,
-    // int E1(s^2/4ct) ds and int F(s^2/4ct) ds over [-a, a]
-    if (Dq != 0.0) {
-        for (int side = 0; side < 2; ++side) {
-            double ct = side == 0 ? w.ct_hi : w.ct_lo;
-            if (ct <= 0.0) continue;
-            double sg = side == 0 ? 1.0 : -1.0;
-            double s4 = sqrt(4.0 * ct), A = a / s4;
-            double sp = 1.7724538509055160273 * erf(A);
-            double IE1 = 2.0 * s4 * (A * e1<double>(A * A) + sp);
-            double IF = 2.0 * s4 * (sp - (-expm1(-A * A)) / A);
-            sn += sg * (-k.eta * k.i4pk * Dq * (IE1 - IF));
-            p += sg * k.i4pk * Dq * IE1;
-        }
-    }
-    out[0] = ss; out[1] = sn; out[2] = p;
-}
-
 __global__ void k_self(KConst<double> k, Win<double> w, const double *x, const double *xy, int64_t n, double scale,
                        int overwrite, double *y) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -681,11 +653,11 @@ ddm_status upload_tables(ddm_ctx *ctx) {
 ddm_status ensure_workspace(ddm_ctx *ctx, ddm_tree *t) {
     int n = ctx->prm.n_cheb;
     if (t->ncheb_alloc == n && t->W) return DDM_OK;
-    if (t->W) cudaFree(t->W);
-    if (t->Fl) cudaFree(t->Fl);
+    dfree(t->W, t->stream);
+    dfree(t->Fl, t->stream);
     t->W = t->Fl = nullptr;
     size_t sz = (size_t)t->n_cells * 4 * n * n * sizeof(float);
-    if (cudaMalloc(&t->W, sz) != cudaSuccess || cudaMalloc(&t->Fl, sz) != cudaSuccess)
+    if (dalloc(&t->W, sz, t->stream) != cudaSuccess || dalloc(&t->Fl, sz, t->stream) != cudaSuccess)
         return ctx_fail(ctx, DDM_ENOMEM, "FMM workspace allocation failed");
     t->ncheb_alloc = n;
     return DDM_OK;
@@ -742,7 +714,7 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
         if (slot < 0) {
             slot = t->win_next;
             t->win_next = (t->win_next + 1) % 4;
-            if (!t->win_blk[slot]) DDM_CUDA_TRY(ctx, cudaMalloc(&t->win_blk[slot], 9 * N * sizeof(double)));
+            if (!t->win_blk[slot]) DDM_CUDA_TRY(ctx, dalloc(&t->win_blk[slot], 9 * N * sizeof(double), t->stream));
             k_self_blocks<<<(N + TB - 1) / TB, TB, 0, s>>>(ctx->kd, wd, t->xy_caller, N, t->win_blk[slot]);
             t->win_lo[slot] = lo;
             t->win_hi[slot] = hi;
@@ -793,9 +765,9 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
             int nk = t->n_keys;
             size_t opsz = (size_t)nk * 16 * n2 * n2;
             if (t->ops_n != n || !t->m2l_ops) {
-                if (t->m2l_ops) cudaFree(t->m2l_ops);
+                dfree(t->m2l_ops, t->stream);
                 t->m2l_ops = nullptr;
-                DDM_CUDA_TRY(ctx, cudaMalloc(&t->m2l_ops, opsz * sizeof(float)));
+                DDM_CUDA_TRY(ctx, dalloc(&t->m2l_ops, opsz * sizeof(float), t->stream));
                 t->ops_n = n;
                 t->ops_lo = t->ops_hi = -1.0;
             }

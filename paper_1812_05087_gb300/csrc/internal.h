@@ -35,6 +35,7 @@ struct Win {
 };
 
 struct ddm_tree {
+    cudaStream_t stream;       // stream of the build; frees are ordered on it
     int64_t n;                 // elements
     int depth;                 // leaf level L
     double cx, cy, h0;         // root square centre and half-width
@@ -63,6 +64,17 @@ struct ddm_tree {
     double win_lo[4] = {-1, -1, -1, -1}, win_hi[4] = {-1, -1, -1, -1};
     int win_next = 0;
     int64_t n_m2l, n_p2p;
+    // preconditioner blocks: runs of <= 64 elements along chains of elements
+    // that share end points (one fracture), caller element indices
+    int64_t n_pblk;
+    int32_t *pb_off;           // CSR over blocks (elements)
+    int64_t *pb_elem;          // caller element index, chain order
+    int64_t *pb_moff;          // offset of each block's (3m x 3m) matrix
+    int64_t pb_msize;          // total matrix entries
+    int pb_max;                // largest block (elements)
+    float *pb_inv;             // inverted system blocks of the cached (dt, system), FP32
+    double pb_dt;
+    int pb_sys;
     // M2L pairs grouped by (level, cell offset): key = level * 49 + (dx+3)*7 + (dy+3)
     int n_keys;                // (L + 1) * 49
     int32_t *mk_off;           // CSR over keys
@@ -113,6 +125,13 @@ struct ddm_ctx {
 void prof_begin(ddm_ctx *ctx, int stage);
 void prof_end(ddm_ctx *ctx, int stage, int launches);
 
+// Device memory comes from the stream-ordered allocator (the device's
+// default pool, kept by the process after frees), so that tree builds,
+// workspaces and per-request buffers do not synchronise the device.
+inline cudaError_t dalloc(void **p, size_t bytes, cudaStream_t s) { return cudaMallocAsync(p, bytes ? bytes : 1, s); }
+template <class T> inline cudaError_t dalloc(T **p, size_t bytes, cudaStream_t s) { return dalloc((void **)p, bytes, s); }
+inline void dfree(void *p, cudaStream_t s) { if (p) cudaFreeAsync(p, s); }
+
 // error helpers
 ddm_status ctx_fail(ddm_ctx *ctx, ddm_status st, const std::string &msg);
 #define DDM_CUDA_TRY(ctx, call)                                                        \
@@ -132,3 +151,6 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double tau_lo, double tau_hi, con
 ddm_status self_blocks(ddm_ctx *ctx, ddm_tree *t, double dt);   // fills t->self_blk (caller order)
 ddm_status ensure_workspace(ddm_ctx *ctx, ddm_tree *t);
 ddm_status upload_tables(ddm_ctx *ctx);
+// precond.cu: chain-block Jacobi preconditioner (cached per dt and system)
+ddm_status pb_prepare(ddm_ctx *ctx, ddm_tree *t, double dt, int sys, cudaStream_t s);
+ddm_status pb_apply(ddm_ctx *ctx, ddm_tree *t, int sys, const double *v, double *z3, cudaStream_t s);

@@ -272,3 +272,36 @@ DEV void to_local(T tx, T ty, const T g[4], T &ss, T &sn) {
     sn = g[0] * nx * nx + T(2) * g[2] * nx * ny + g[1] * ny * ny;
     ss = g[0] * tx * nx + g[2] * (tx * ny + ty * nx) + g[1] * ty * ny;
 }
+
+// ---------------------------------------------------------------------------
+// an element on its own midpoint (FP64): dislocation pair at +-a t plus the
+// closed-form fluid-source integrals along the line
+// ---------------------------------------------------------------------------
+__device__ inline void self_field(const KConst<double> &k, const Win<double> &w, double a, double tx, double ty,
+                           double Ds, double Dn, double Dq, double out[3]) {
+    double nx = -ty, ny = tx;
+    double Dx = Ds * tx + Dn * nx, Dy = Ds * ty + Dn * ny;
+    double g[4] = {0, 0, 0, 0};
+    disl_field<double>(k, a * tx, a * ty, Dx, Dy, w, 1.0, g);      // target - start = a t
+    disl_field<double>(k, -a * tx, -a * ty, Dx, Dy, w, -1.0, g);   // target - end   = -a t
+    double ss, sn;
+    to_local<double>(tx, ty, g, ss, sn);
+    double p = g[3];
+    // fluid source on its own element: closed forms along the line,
+    // int E1(s^2/4ct) ds and int F(s^2/4ct) ds over [-a, a]
+    if (Dq != 0.0) {
+        for (int side = 0; side < 2; ++side) {
+            double ct = side == 0 ? w.ct_hi : w.ct_lo;
+            if (ct <= 0.0) continue;
+            double sg = side == 0 ? 1.0 : -1.0;
+            double s4 = sqrt(4.0 * ct), A = a / s4;
+            double sp = 1.7724538509055160273 * erf(A);
+            double IE1 = 2.0 * s4 * (A * e1<double>(A * A) + sp);
+            double IF = 2.0 * s4 * (sp - (-expm1(-A * A)) / A);
+            sn += sg * (-k.eta * k.i4pk * Dq * (IE1 - IF));
+            p += sg * k.i4pk * Dq * IE1;
+        }
+    }
+    out[0] = ss; out[1] = sn; out[2] = p;
+}
+

@@ -72,10 +72,10 @@ size_t footprint(const ddm_request &r, int ncheb) {
     return per_tree + vectors;
 }
 
-void release(Req *q) {
+void release(Req *q, cudaStream_t s) {
     if (q->tree) tree_free(q->tree);
-    if (q->hist) cudaFree(q->hist);
-    if (q->rhs) cudaFree(q->rhs);
+    dfree(q->hist, s);
+    dfree(q->rhs, s);
     q->tree = nullptr;
     q->hist = q->rhs = nullptr;
 }
@@ -99,13 +99,13 @@ void serve_loop(ddm_server *S) {
                 q->t_admit = Clock::now();
                 lk.unlock();
                 ddm_status st = ddm_build_tree(S->ctx, q->r.d_xy, q->r.n, &q->tree);
-                if (!st && cudaMalloc(&q->hist, (size_t)q->r.steps * 3 * q->r.n * sizeof(double)) != cudaSuccess)
+                if (!st && dalloc(&q->hist, (size_t)q->r.steps * 3 * q->r.n * sizeof(double), s) != cudaSuccess)
                     st = DDM_ENOMEM;
-                if (!st && cudaMalloc(&q->rhs, (size_t)3 * q->r.n * sizeof(double)) != cudaSuccess) st = DDM_ENOMEM;
+                if (!st && dalloc(&q->rhs, (size_t)3 * q->r.n * sizeof(double), s) != cudaSuccess) st = DDM_ENOMEM;
                 if (!st) cudaMemsetAsync(q->hist, 0, (size_t)q->r.steps * 3 * q->r.n * sizeof(double), s);
                 lk.lock();
                 if (st) {
-                    release(q);
+                    release(q, s);
                     S->used -= q->footprint;
                     q->status = st;
                     q->t_done = Clock::now();
@@ -128,7 +128,7 @@ void serve_loop(ddm_server *S) {
             int64_t tot = 0;
             for (Req *q : rs) { trees.push_back(q->tree); tot += 3 * q->r.n; }
             double *rhs = nullptr, *x = nullptr;
-            if (cudaMalloc(&rhs, tot * sizeof(double)) != cudaSuccess || cudaMalloc(&x, tot * sizeof(double)) != cudaSuccess)
+            if (dalloc(&rhs, tot * sizeof(double), s) != cudaSuccess || dalloc(&x, tot * sizeof(double), s) != cudaSuccess)
                 st = DDM_ENOMEM;
             int64_t o = 0;
             for (Req *q : rs) {
@@ -178,8 +178,8 @@ void serve_loop(ddm_server *S) {
             }
             cudaStreamSynchronize(s);
             if (B) ddm_batch_destroy(B);
-            if (rhs) cudaFree(rhs);
-            if (x) cudaFree(x);
+            dfree(rhs, s);
+            dfree(x, s);
         }
         // retire finished requests
         std::lock_guard<std::mutex> lk(S->mu);
@@ -187,7 +187,7 @@ void serve_loop(ddm_server *S) {
         std::vector<Req *> keep;
         for (Req *q : active) {
             if (q->step >= q->r.steps) {
-                release(q);
+                release(q, s);
                 S->used -= q->footprint;
                 if (q->status == DDM_PENDING) q->status = DDM_OK;
                 q->t_done = Clock::now();
@@ -263,7 +263,7 @@ void ddm_server_destroy(ddm_server *S) {
     S->cv.notify_all();
     if (S->th.joinable()) S->th.join();
     for (auto &kv : S->all) {
-        release(kv.second);
+        release(kv.second, S->ctx->stream);
         delete kv.second;
     }
     cudaStream_t st = S->ctx->stream;

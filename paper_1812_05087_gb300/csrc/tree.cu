@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 
 #include "internal.h"
 
@@ -94,17 +95,18 @@ __global__ void k_scan_add(int32_t *out, int64_t n, const int32_t *offs) {
     if (i < n) out[i] += offs[blockIdx.x];
 }
 
-struct Scratch {      // simple bump allocations freed at the end of the build
+struct Scratch {      // build-time buffers, freed (stream-ordered) at the end of the build
     std::vector<void *> ptrs;
+    cudaStream_t st = nullptr;
     cudaError_t err = cudaSuccess;
     template <class T> T *get(size_t count) {
         void *p = nullptr;
-        cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+        cudaError_t e = dalloc(&p, std::max<size_t>(count, 1) * sizeof(T), st);
         if (e != cudaSuccess) { err = e; return nullptr; }
         ptrs.push_back(p);
         return (T *)p;
     }
-    ~Scratch() { for (void *p : ptrs) cudaFree(p); }
+    ~Scratch() { for (void *p : ptrs) dfree(p, st); }
 };
 
 // exclusive scan, returns the total (synchronises)
@@ -383,13 +385,11 @@ __global__ void k_p2p_count(const int32_t *cstart, const int32_t *cend, int64_t 
 
 void tree_free(ddm_tree *t) {
     if (!t) return;
-    void *ps[] = {t->mk_off, t->mk_pair, t->m2l_ops, t->grp_off, t->grp_leaf, t->perm, t->cell_key, t->cell_ix, t->cell_iy, t->cell_start, t->cell_end, t->cell_parent,
+    void *ps[] = {t->pb_off, t->pb_elem, t->pb_moff, t->pb_inv, t->mk_off, t->mk_pair, t->m2l_ops, t->grp_off, t->grp_leaf, t->perm, t->cell_key, t->cell_ix, t->cell_iy, t->cell_start, t->cell_end, t->cell_parent,
                   t->il_off, t->il_idx, t->nb_off, t->nb_idx, t->elem_leaf, t->g_rel, t->g_frame,
                   t->xy_sorted, t->xy_caller, t->self_blk, t->W, t->Fl, t->chg};
-    for (void *p : ps)
-        if (p) cudaFree(p);
-    for (double *p : t->win_blk)
-        if (p) cudaFree(p);
+    for (void *p : ps) dfree(p, t->stream);
+    for (double *p : t->win_blk) dfree(p, t->stream);
     delete t;
 }
 
@@ -401,6 +401,8 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
     t->n = n;
     t->self_dt = -1.0;
     Scratch S;
+    S.st = st;
+    t->stream = st;
     tl_launches = 0;
     prof_begin(ctx, 9);
     const int TB = 256;
@@ -474,12 +476,12 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
     }
     int64_t NC = t->lvl_off[L + 1];
     t->n_cells = NC;
-    TRY(cudaMalloc(&t->cell_key, NC * sizeof(uint32_t)));
-    TRY(cudaMalloc(&t->cell_ix, NC * sizeof(int32_t)));
-    TRY(cudaMalloc(&t->cell_iy, NC * sizeof(int32_t)));
-    TRY(cudaMalloc(&t->cell_start, NC * sizeof(int32_t)));
-    TRY(cudaMalloc(&t->cell_end, NC * sizeof(int32_t)));
-    TRY(cudaMalloc(&t->cell_parent, NC * sizeof(int32_t)));
+    TRY(dalloc(&t->cell_key, NC * sizeof(uint32_t), st));
+    TRY(dalloc(&t->cell_ix, NC * sizeof(int32_t), st));
+    TRY(dalloc(&t->cell_iy, NC * sizeof(int32_t), st));
+    TRY(dalloc(&t->cell_start, NC * sizeof(int32_t), st));
+    TRY(dalloc(&t->cell_end, NC * sizeof(int32_t), st));
+    TRY(dalloc(&t->cell_parent, NC * sizeof(int32_t), st));
     for (int l = 0; l <= L; ++l) {
         int32_t *fl = ecell[L + 1 + l];
         int32_t *exl = ecell[l];
@@ -503,13 +505,13 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
     int side = 1 << L;
     int32_t *cnt = S.get<int32_t>(std::max<int64_t>(NC, nleaf) + 1);
     TRY(S.err);
-    TRY(cudaMalloc(&t->nb_off, (nleaf + 1) * sizeof(int32_t)));
+    TRY(dalloc(&t->nb_off, (nleaf + 1) * sizeof(int32_t), st));
     int64_t lb = (nleaf + TB - 1) / TB;
     k_neigh<<<lb, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, loff, nleaf, side, nullptr, nullptr, cnt); ++tl_launches;
     int32_t nbtot;
     TRY(scan_excl(S, st, cnt, t->nb_off, nleaf, &nbtot));
     TRY(cudaMemcpyAsync(t->nb_off + nleaf, &nbtot, sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    TRY(cudaMalloc(&t->nb_idx, std::max(nbtot, 1) * sizeof(int32_t)));
+    TRY(dalloc(&t->nb_idx, std::max(nbtot, 1) * sizeof(int32_t), st));
     k_neigh<<<lb, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, loff, nleaf, side, t->nb_off, t->nb_idx, nullptr); ++tl_launches;
 
     // interaction lists, levels >= 2
@@ -519,11 +521,11 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
         k_ilist<<<(nc + TB - 1) / TB, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, t->lvl_off[l], nc,
                                                   1 << l, nullptr, nullptr, cnt); ++tl_launches;
     }
-    TRY(cudaMalloc(&t->il_off, (NC + 1) * sizeof(int32_t)));
+    TRY(dalloc(&t->il_off, (NC + 1) * sizeof(int32_t), st));
     int32_t iltot;
     TRY(scan_excl(S, st, cnt, t->il_off, NC, &iltot));
     TRY(cudaMemcpyAsync(t->il_off + NC, &iltot, sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    TRY(cudaMalloc(&t->il_idx, std::max(iltot, 1) * sizeof(int32_t)));
+    TRY(dalloc(&t->il_idx, std::max(iltot, 1) * sizeof(int32_t), st));
     for (int l = 2; l <= L; ++l) {
         int64_t nc = ncl[l];
         k_ilist<<<(nc + TB - 1) / TB, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, t->lvl_off[l], nc,
@@ -540,8 +542,8 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
         TRY(cudaMemcpyAsync(lo, t->lvl_off.data(), (L + 2) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
         TRY(cudaMemsetAsync(kc, 0, (nk + 1) * sizeof(int32_t), st));
         TRY(cudaMemsetAsync(kcur, 0, nk * sizeof(int32_t), st));
-        TRY(cudaMalloc(&t->mk_off, (nk + 1) * sizeof(int32_t)));
-        TRY(cudaMalloc(&t->mk_pair, std::max(iltot, 1) * sizeof(int2)));
+        TRY(dalloc(&t->mk_off, (nk + 1) * sizeof(int32_t), st));
+        TRY(dalloc(&t->mk_pair, std::max(iltot, 1) * sizeof(int2), st));
         int64_t first = L >= 2 ? t->lvl_off[2] : NC, ncm = NC - first;
         if (ncm > 0) {
             k_mkeys<<<(ncm + 255) / 256, 256, 0, st>>>(t->il_off, t->il_idx, t->cell_ix, t->cell_iy, lo, L, first, ncm,
@@ -564,15 +566,15 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
     }
 
     // sorted geometry
-    TRY(cudaMalloc(&t->perm, n * sizeof(int64_t)));
-    TRY(cudaMalloc(&t->elem_leaf, n * sizeof(int32_t)));
-    TRY(cudaMalloc(&t->g_rel, n * sizeof(float4)));
-    TRY(cudaMalloc(&t->g_frame, n * sizeof(float4)));
-    TRY(cudaMalloc(&t->xy_sorted, 4 * n * sizeof(double)));
-    TRY(cudaMalloc(&t->self_blk, 9 * n * sizeof(double)));
-    TRY(cudaMalloc(&t->xy_caller, 4 * n * sizeof(double)));
+    TRY(dalloc(&t->perm, n * sizeof(int64_t), st));
+    TRY(dalloc(&t->elem_leaf, n * sizeof(int32_t), st));
+    TRY(dalloc(&t->g_rel, n * sizeof(float4), st));
+    TRY(dalloc(&t->g_frame, n * sizeof(float4), st));
+    TRY(dalloc(&t->xy_sorted, 4 * n * sizeof(double), st));
+    TRY(dalloc(&t->self_blk, 9 * n * sizeof(double), st));
+    TRY(dalloc(&t->xy_caller, 4 * n * sizeof(double), st));
     TRY(cudaMemcpyAsync(t->xy_caller, d_xy, 4 * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    TRY(cudaMalloc(&t->chg, n * sizeof(float4)));
+    TRY(dalloc(&t->chg, n * sizeof(float4), st));
     TRY(cudaMemcpyAsync(t->elem_leaf, ecell[L], n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
     double wl = 2.0 * h0 / (double)side;
     k_geom<<<nbk, TB, 0, st>>>(d_xy, n, idx, t->elem_leaf, t->cell_ix, t->cell_iy, loff, X0, Y0, wl, t->perm,
@@ -583,13 +585,73 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
         t->n_groups = ng;
         int32_t *gc = S.get<int32_t>(ng + 1);
         TRY(S.err);
-        TRY(cudaMalloc(&t->grp_off, (ng + 1) * sizeof(int32_t)));
+        TRY(dalloc(&t->grp_off, (ng + 1) * sizeof(int32_t), st));
         k_groups<<<(ng + 127) / 128, 128, 0, st>>>(t->elem_leaf, n, ng, t->nb_off, t->nb_idx, nullptr, nullptr, gc); ++tl_launches;
         int32_t gtot;
         TRY(scan_excl(S, st, gc, t->grp_off, ng, &gtot));
         TRY(cudaMemcpyAsync(t->grp_off + ng, &gtot, sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        TRY(cudaMalloc(&t->grp_leaf, std::max(gtot, 1) * sizeof(int32_t)));
+        TRY(dalloc(&t->grp_leaf, std::max(gtot, 1) * sizeof(int32_t), st));
         k_groups<<<(ng + 127) / 128, 128, 0, st>>>(t->elem_leaf, n, ng, t->nb_off, t->nb_idx, t->grp_off, t->grp_leaf, nullptr); ++tl_launches;
+    }
+    // preconditioner blocks: chains of elements sharing end points (host)
+    {
+        std::vector<double> hxy(4 * n);
+        TRY(cudaMemcpyAsync(hxy.data(), d_xy, 4 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+        TRY(cudaStreamSynchronize(st));
+        // end points are matched on a grid of 1e-6 of the shortest element
+        double lmin = 1e300;
+        for (int64_t e = 0; e < n; ++e)
+            lmin = std::min(lmin, hypot(hxy[2 * n + e] - hxy[e], hxy[3 * n + e] - hxy[n + e]));
+        double q = 1e-6 * lmin;
+        auto key = [&](double x, double y) { return std::make_pair((long long)llround(x / q), (long long)llround(y / q)); };
+        std::map<std::pair<long long, long long>, int64_t> starts;
+        for (int64_t e = 0; e < n; ++e) starts[key(hxy[e], hxy[n + e])] = e;
+        std::vector<int64_t> next(n, -1), prevc(n, 0);
+        for (int64_t e = 0; e < n; ++e) {
+            auto it = starts.find(key(hxy[2 * n + e], hxy[3 * n + e]));
+            if (it != starts.end() && it->second != e && prevc[it->second] == 0) {
+                next[e] = it->second;
+                prevc[it->second] = 1;
+            }
+        }
+        std::vector<int32_t> boff{0};
+        std::vector<int64_t> belem, moff{0};
+        std::vector<char> seen(n, 0);
+        const int BMAX = 64;
+        auto emit_chain = [&](int64_t head) {
+            int cnt = 0;
+            for (int64_t e = head; e >= 0 && !seen[e]; e = next[e]) {
+                seen[e] = 1;
+                belem.push_back(e);
+                if (++cnt == BMAX) {
+                    boff.push_back((int32_t)belem.size());
+                    cnt = 0;
+                }
+            }
+            if (cnt) boff.push_back((int32_t)belem.size());
+        };
+        for (int64_t e = 0; e < n; ++e)
+            if (!prevc[e]) emit_chain(e);
+        for (int64_t e = 0; e < n; ++e)      // closed loops
+            if (!seen[e]) emit_chain(e);
+        t->n_pblk = (int64_t)boff.size() - 1;
+        t->pb_max = 0;
+        for (int64_t b = 0; b < t->n_pblk; ++b) {
+            int m = boff[b + 1] - boff[b];
+            t->pb_max = std::max(t->pb_max, m);
+            moff.push_back(moff.back() + (int64_t)9 * m * m);
+        }
+        t->pb_msize = moff.back();
+        TRY(dalloc(&t->pb_off, boff.size() * sizeof(int32_t), st));
+        TRY(dalloc(&t->pb_elem, std::max<size_t>(belem.size(), 1) * sizeof(int64_t), st));
+        TRY(dalloc(&t->pb_moff, moff.size() * sizeof(int64_t), st));
+        TRY(cudaMemcpyAsync(t->pb_off, boff.data(), boff.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        TRY(cudaMemcpyAsync(t->pb_elem, belem.data(), belem.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+        TRY(cudaMemcpyAsync(t->pb_moff, moff.data(), moff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+        TRY(cudaStreamSynchronize(st));
+        t->pb_inv = nullptr;
+        t->pb_dt = -1.0;
+        t->pb_sys = -1;
     }
     unsigned long long *ptot = S.get<unsigned long long>(1);
     TRY(S.err);
