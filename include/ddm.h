@@ -112,8 +112,8 @@ ddm_status ddm_tree_get_info(const ddm_tree *tree, ddm_tree_info *info);
 
 #define DDM_MODE_FMM 0     /* Chebyshev FMM (paper Sec. 3) */
 #define DDM_MODE_DENSE 1   /* every pair evaluated on the fly (conventional PDDM) */
-#define DDM_MODE_PRECISE 16 /* OR-ed flag: DD kernels of close pairs (< 2 element
-                               lengths) in FP64, for accurate residuals */
+#define DDM_MODE_PRECISE 16 /* OR-ed flag: DD part of every directly summed pair
+                               in FP64, for accurate residuals */
 
 /* d_y = [K(tau_hi) - K(tau_lo)] d_x  (paper Eqs. 2.3-2.5, left-hand sums for
  * tau_lo = 0, tau_hi = dt; one history term otherwise).  0 <= tau_lo < tau_hi.
@@ -173,9 +173,12 @@ typedef struct {
  * in: initial guess (and the prescribed Dq for 2N systems), out: solution.
  * Mixed precision: Arnoldi steps use the FP32-pair operator; the true
  * residual at every restart (and the convergence test) uses the operator
- * with DDM_MODE_PRECISE.  Returns DDM_ENOTCONV (x and info still written)
- * when max_iters is reached or three restarts in a row fail to reduce the
- * true residual by 10%.
+ * with DDM_MODE_PRECISE; each restart's inner solve runs until its
+ * estimated residual is below max(0.3 tol ||b||, 1e-4 of the restart's
+ * residual).  A restart that fails to reduce the true residual by 10%
+ * switches the inner products to the precise operator as well.  Returns
+ * DDM_ENOTCONV (x and info still written) when max_iters is reached or three
+ * further restarts in a row fail to reduce the true residual by 10%.
  * Synchronises the stream (reads the Hessenberg columns back). */
 ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const double *d_rhs,
                            double *d_x, const ddm_gmres_params *prm, ddm_gmres_info *info);

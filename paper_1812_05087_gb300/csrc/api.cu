@@ -370,7 +370,7 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
         if (!ok) { g.release(); return ctx_fail(ctx, DDM_ENOMEM, "GMRES workspace allocation failed"); }
         g.cap_len = len; g.cap_m = m;
     }
-    int mode = P.mode, sys = P.system;
+    int mode = P.mode & ~DDM_MODE_PRECISE, sys = P.system;
     ddm_status st;
     // operator y(len) = restrict(A(dt) [v; 0]) ; the 3N layout keeps blocks of N
     auto apply = [&](const double *v, double *out, int md) -> ddm_status {
@@ -417,9 +417,14 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
         if ((st = norm(g.w, beta))) return st;
         rel = beta / bnorm;
         if (rel < P.tol) { conv = true; break; }
-        // stop after three restarts in a row without a 10% decrease
+        // no 10% decrease over a restart: first switch the inner products to
+        // the precise operator (refinement with consistent operators), then
+        // stop after three such restarts
         if (rel < 0.9 * best) { best = rel; stall = 0; }
+        else if (!(mode & DDM_MODE_PRECISE)) { mode |= DDM_MODE_PRECISE; stall = 0; }
         else if (++stall >= 3) break;
+        // inner target: two decades below beta, or below the tolerance
+        double inner = std::max(0.3 * P.tol * bnorm, 1e-4 * beta);
         // v0 = -w / beta
         DDM_CUDA_TRY(ctx, cudaMemsetAsync(g.V, 0, len * sizeof(double), s));
         k_axpy<<<nblk(len), 256, 0, s>>>(-1.0 / beta, g.w, g.V, len);
@@ -459,7 +464,7 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
             gv[j] = cs[j] * gv[j];
             for (int i = 0; i <= j; ++i) H[i * m + j] = hc[i];
             rel = fabs(gv[j + 1]) / bnorm;
-            if (rel < P.tol || r == 0) { ++j; ++iters; break; }
+            if (fabs(gv[j + 1]) < inner || r == 0) { ++j; ++iters; break; }
         }
         // least squares: upper triangular solve, x += M^-1 V y
         std::vector<double> yv(j, 0.0);

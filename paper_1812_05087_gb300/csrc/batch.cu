@@ -319,7 +319,7 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
     ddm_status st = upload_tables(ctx);
     if (st) return st;
     cudaStream_t s = ctx->stream;
-    const int P = B->P, m = Pm.restart, sys = Pm.system, mode = Pm.mode;
+    const int P = B->P, m = Pm.restart, sys = Pm.system, mode = Pm.mode & ~DDM_MODE_PRECISE;
     const int nc = sys == DDM_SYS_PRESSURE ? 3 : 2;
     const int hs = m + 2;
     // (re)allocate the solver arena
@@ -370,12 +370,14 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
     // graphs: preconditioned operator vin -> w, residual operator (precise) x -> tmp
     int saved = ctx->prof.on;
     ctx->prof.on = 0;
+    std::vector<int> prec(P, 0);      // per problem: inner products with the precise operator
     auto capture_op = [&](const std::vector<int> &idx) -> ddm_status {
         return capture(ctx, B, &B->g_op, &B->k_op, idx, [&](int p, cudaStream_t ps) -> ddm_status {
             int64_t n = B->N[p];
             ddm_status e = pb_apply(ctx, B->trees[p], sys, B->vin + B->offs[p], B->full + B->off3[p], ps);
             if (e) return e;
-            e = op_apply(ctx, B->trees[p], 0.0, dt, B->full + B->off3[p], B->y3 + B->off3[p], mode, 0, 1.0, ps);
+            e = op_apply(ctx, B->trees[p], 0.0, dt, B->full + B->off3[p], B->y3 + B->off3[p],
+                         mode | (prec[p] ? DDM_MODE_PRECISE : 0), 0, 1.0, ps);
             if (e) return e;
             k_restrict_b<<<nb(n), BT, 0, ps>>>(B->y3 + B->off3[p], n, sys, 1, B->w + B->offs[p]);
             return DDM_OK;
@@ -441,18 +443,21 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
         k_axpy_b<<<nb(L), BT, 0, s>>>(-1.0, B->b, B->w, L);
         if ((st = seg_norms(B->w, beta))) return st;
         int nact = 0;
+        bool reprec = false;
         for (int p = 0; p < P; ++p) {
             if (!active[p]) continue;
             rel[p] = beta[p] / bn[p];
             if (rel[p] < Pm.tol) { conv[p] = 1; active[p] = 0; continue; }
             if (rel[p] < 0.9 * best[p]) { best[p] = rel[p]; stall[p] = 0; }
+            else if (!prec[p]) { prec[p] = 1; stall[p] = 0; reprec = true; }
             else if (++stall[p] >= 3) { active[p] = 0; continue; }
             if (iters[p] >= Pm.max_iters) { active[p] = 0; continue; }
             ++nact;
         }
         if (nact == 0 || total >= Pm.max_iters) break;
         // drop converged problems from the graphs once a quarter of them left
-        if (nact < 0.75 * (double)B->op_set.size()) {
+        // (and re-capture when a problem switched to precise inner products)
+        if (reprec || nact < 0.75 * (double)B->op_set.size()) {
             std::vector<int> act;
             for (int p = 0; p < P; ++p)
                 if (active[p]) act.push_back(p);
@@ -466,7 +471,12 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
         DDM_CUDA_TRY(ctx, cudaMemcpyAsync(B->coef, coef.data(), P * sizeof(double), cudaMemcpyHostToDevice, s));
         k_v0_seg<<<nb(L), BT, 0, s>>>(B->w, B->coef, B->prob, L, B->V);
         std::fill(gv.begin(), gv.end(), 0.0);
-        for (int p = 0; p < P; ++p) { gv[(size_t)p * (m + 1)] = active[p] ? beta[p] : 0.0; jend[p] = 0; }
+        std::vector<double> inner(P);
+        for (int p = 0; p < P; ++p) {
+            gv[(size_t)p * (m + 1)] = active[p] ? beta[p] : 0.0;
+            jend[p] = 0;
+            inner[p] = std::max(0.3 * Pm.tol * bn[p], 1e-4 * beta[p]);
+        }
         std::vector<int> live = active;
         int j = 0;
         for (; j < m; ++j) {
@@ -507,7 +517,7 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
                 for (int i = 0; i <= j; ++i) H[((size_t)p * (m + 1) + i) * m + j] = c[i];
                 ++iters[p];
                 jend[p] = j + 1;
-                if (fabs(g[j + 1]) / bn[p] < Pm.tol || r == 0 || iters[p] >= Pm.max_iters) live[p] = 0;
+                if (fabs(g[j + 1]) < inner[p] || r == 0 || iters[p] >= Pm.max_iters) live[p] = 0;
                 else ++still;
             }
             if (still == 0) { ++j; break; }

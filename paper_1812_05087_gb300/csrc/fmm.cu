@@ -416,8 +416,10 @@ __device__ __forceinline__ void q_point(const KConst<float> &k, float zx, float 
 
 // near/far element integral of one source element at target m (target
 // frame coordinates); self pairs are excluded by the caller.  PRECISE: the
-// DD part of close pairs (centre distance < 2 element lengths), whose
-// contributions nearly cancel for smooth openings, in FP64.
+// DD part of every pair in FP64 (closed form near, Gauss rule far) - the
+// element contributions along a fracture nearly cancel for smooth openings,
+// by a factor that grows with the elements per fracture, so residuals need
+// FP64 here; the fluid-source part stays FP32.
 template <bool PRECISE>
 __device__ __forceinline__ void pair_field(const KConst<float> &k, const KConst<double> &kd, const Win<float> &w,
                                            const Win<double> &wd, float mx, float my, const SrcTile &s,
@@ -425,7 +427,37 @@ __device__ __forceinline__ void pair_field(const KConst<float> &k, const KConst<
     float cxs = 0.5f * (s.x0 + s.x1), cys = 0.5f * (s.y0 + s.y1);
     float dx = mx - cxs, dy = my - cys;
     float r2 = dx * dx + dy * dy;
-    if (r2 > 64.f * s.a * s.a) {
+    bool far = r2 > 64.f * s.a * s.a;
+    if (PRECISE) {
+        if (far) {
+            double nx = -(double)s.ty, ny = (double)s.tx;
+            double Pxx = s.Dx * nx, Pyy = s.Dy * ny, Pxy = 0.5 * (s.Dx * ny + s.Dy * nx);
+#pragma unroll
+            for (int g = 0; g < 3; ++g) {
+                double sg = (double)c_gl.xf[g] * s.a, wt = (double)c_gl.wf[g] * s.a;
+                pot_kernel<double>(kd, dx - sg * s.tx, dy - sg * s.ty, wt * Pxx, wt * Pyy, wt * Pxy, 0.0, wd, accd);
+            }
+        } else {
+            disl_field<double>(kd, (double)(mx - s.x0), (double)(my - s.y0), (double)s.Dx, (double)s.Dy, wd, 1.0, accd);
+            disl_field<double>(kd, (double)(mx - s.x1), (double)(my - s.y1), (double)s.Dx, (double)s.Dy, wd, -1.0, accd);
+        }
+        if (s.q != 0.f) {
+            if (far) {
+#pragma unroll
+                for (int g = 0; g < 3; ++g) {
+                    float sg = c_gl.xf[g] * s.a, wt = c_gl.wf[g] * s.a;
+                    q_point(k, dx - sg * s.tx, dy - sg * s.ty, wt * s.q, w, acc);
+                }
+            } else {
+                for (int g = 0; g < c_gl.nn; ++g) {
+                    float sg = c_gl.xn[g] * s.a, wt = c_gl.wn[g] * s.a;
+                    q_point(k, dx - sg * s.tx, dy - sg * s.ty, wt * s.q, w, acc);
+                }
+            }
+        }
+        return;
+    }
+    if (far) {
         // far: 3-point Gauss rule of the point kernel
         float nx = -s.ty, ny = s.tx;
         float Pxx = s.Dx * nx, Pyy = s.Dy * ny, Pxy = 0.5f * (s.Dx * ny + s.Dy * nx);
@@ -435,13 +467,8 @@ __device__ __forceinline__ void pair_field(const KConst<float> &k, const KConst<
             pot_kernel<float>(k, dx - sg * s.tx, dy - sg * s.ty, wt * Pxx, wt * Pyy, wt * Pxy, wt * s.q, w, acc);
         }
     } else {
-        if (PRECISE && r2 < 16.f * s.a * s.a) {
-            disl_field<double>(kd, (double)(mx - s.x0), (double)(my - s.y0), (double)s.Dx, (double)s.Dy, wd, 1.0, accd);
-            disl_field<double>(kd, (double)(mx - s.x1), (double)(my - s.y1), (double)s.Dx, (double)s.Dy, wd, -1.0, accd);
-        } else {
-            disl_field<float>(k, mx - s.x0, my - s.y0, s.Dx, s.Dy, w, 1.f, acc);
-            disl_field<float>(k, mx - s.x1, my - s.y1, s.Dx, s.Dy, w, -1.f, acc);
-        }
+        disl_field<float>(k, mx - s.x0, my - s.y0, s.Dx, s.Dy, w, 1.f, acc);
+        disl_field<float>(k, mx - s.x1, my - s.y1, s.Dx, s.Dy, w, -1.f, acc);
         if (s.q != 0.f) {
             for (int g = 0; g < c_gl.nn; ++g) {
                 float sg = c_gl.xn[g] * s.a, wt = c_gl.wn[g] * s.a;
