@@ -248,6 +248,27 @@ ddm_status ddm_submit(ddm_server *server, const ddm_request *req, uint64_t *tick
 ddm_status ddm_poll(ddm_server *server, uint64_t ticket, ddm_result *result);
 void ddm_server_destroy(ddm_server *server);
 
+/* Dense influence product that allocates nothing (no counterpart in the
+ * paper).  For callers that cannot allocate device memory where they need a
+ * product - e.g. a real-time loop that forbids allocation after start-up,
+ * or code running inside another framework's fixed memory budget or while
+ * that framework holds its allocator.  Same result as ddm_matvec with
+ * DDM_MODE_DENSE, but needs no tree: d_xy is the 4N geometry
+ * [x0, y0, x1, y1] (device, caller order), d_x / d_y 3N vectors (device,
+ * must not overlap); d_y is overwritten.
+ * Scratch: a device array inside the library for DDM_STATIC_MAX_ELEMENTS
+ * elements (about 3 MB, held by every GPU that loads the library until the
+ * process exits); n outside [1, DDM_STATIC_MAX_ELEMENTS] gives DDM_EINVAL.
+ * The call uses no cudaMalloc/cudaFree or other allocating routine.  The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the array: calls whose work
+ * overlaps on the GPU (other streams, other threads) race, so serialise
+ * them.  Each call rewrites the entries it reads; nothing needs clearing. */
+#define DDM_STATIC_MAX_ELEMENTS 65536
+ddm_status ddm_matvec_dense_static(ddm_ctx *ctx, const double *d_xy, int64_t n, double tau_lo,
+                                   double tau_hi, const double *d_x, double *d_y);
+
 /* Stage timing for profiling (no counterpart in the paper): when enabled,
  * CUDA events bracket each stage on the context stream.  ddm_profile_read
  * synchronises the stream and returns, per stage, the summed milliseconds

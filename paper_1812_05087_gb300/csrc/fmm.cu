@@ -18,6 +18,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "internal.h"
@@ -830,6 +831,127 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
         kf, ctx->kd, wf, wd, loff, t->n_groups, t->grp_off, t->grp_leaf, t->cell_start, t->cell_end, t->cell_ix,
         t->cell_iy, t->elem_leaf, t->g_rel, t->g_frame, t->chg, t->perm, wL, n, t->Fl, use_far, N, scale, y);
     prof_end(ctx, 6, 1);
+    DDM_CUDA_TRY(ctx, cudaGetLastError());
+    return DDM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free dense product.
+//
+// Some callers cannot allocate device memory at the point where they need a
+// product: a real-time loop that forbids allocation after start-up, code
+// running inside another framework's fixed memory budget, or code called
+// while that framework holds its allocator.  ddm_matvec_dense_static serves
+// them: it needs no tree, no workspace and no allocation.  Its only scratch
+// (per element: FP64 midpoint, FP32 frame and DD charges) is this file-scope
+// device array, sized for DDM_STATIC_MAX_ELEMENTS elements (48 B each,
+// 3 MB), which every GPU that loads the library holds until the process
+// exits.  All calls share the array, so calls whose work overlaps on the GPU
+// race; each call rewrites the entries of its n elements before reading them,
+// and nothing in the array needs to start at zero.
+// ---------------------------------------------------------------------------
+namespace {
+struct StaticElem {
+    double2 mid;     // midpoint (FP64)
+    float4 frame;    // tangent (x, y), half-length, unused
+    float4 chg;      // global DD vector (x, y), fluid source, unused
+};
+static __device__ __align__(256) StaticElem g_static_scratch[DDM_STATIC_MAX_ELEMENTS];
+
+std::mutex g_static_mu;
+StaticElem *g_static_ptr[256] = {nullptr};   // device address of the array, per device
+
+__global__ void k_static_prep(const double *xy, const double *x, int64_t n, StaticElem *sc) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    double ax = xy[e], ay = xy[n + e], bx = xy[2 * n + e], by = xy[3 * n + e];
+    double L = hypot(bx - ax, by - ay), tx = (bx - ax) / L, ty = (by - ay) / L;
+    float Ds = (float)x[e], Dn = (float)x[n + e], Dq = (float)x[2 * n + e];
+    float ftx = (float)tx, fty = (float)ty;
+    StaticElem s;
+    s.mid = make_double2(0.5 * (ax + bx), 0.5 * (ay + by));
+    s.frame = make_float4(ftx, fty, (float)(0.5 * L), 0.f);
+    s.chg = make_float4(Ds * ftx - Dn * fty, Ds * fty + Dn * ftx, Dq, 0.f);
+    sc[e] = s;
+}
+
+// one thread per target, all sources through shared memory tiles; pair
+// offsets from FP64 midpoints, own element in FP64 closed form
+constexpr int ST_T = 128;
+__global__ void __launch_bounds__(ST_T) k_static_dense(KConst<float> k, KConst<double> kd, Win<float> w,
+                                                       Win<double> wd, const StaticElem *sc, const double *x,
+                                                       int64_t n, double *y) {
+    __shared__ StaticElem tile[ST_T];
+    int64_t ti = blockIdx.x * (int64_t)ST_T + threadIdx.x;
+    bool act = ti < n;
+    StaticElem me = act ? sc[ti] : sc[0];
+    double accd[4] = {0, 0, 0, 0};
+    for (int64_t sb = 0; sb < n; sb += ST_T) {
+        __syncthreads();
+        if (sb + threadIdx.x < n) tile[threadIdx.x] = sc[sb + threadIdx.x];
+        __syncthreads();
+        int cnt = (int)(n - sb < ST_T ? n - sb : ST_T);
+        if (act) {
+            float acc[4] = {0, 0, 0, 0};
+            for (int j = 0; j < cnt; ++j) {
+                if (sb + j == ti) continue;
+                const StaticElem &o = tile[j];
+                float cx = (float)(o.mid.x - me.mid.x), cy = (float)(o.mid.y - me.mid.y);
+                SrcTile st;
+                st.x0 = cx - o.frame.z * o.frame.x; st.y0 = cy - o.frame.z * o.frame.y;
+                st.x1 = cx + o.frame.z * o.frame.x; st.y1 = cy + o.frame.z * o.frame.y;
+                st.Dx = o.chg.x; st.Dy = o.chg.y; st.q = o.chg.z; st.a = o.frame.z;
+                st.tx = o.frame.x; st.ty = o.frame.y; st.idx = (int)(sb + j);
+                pair_field<false>(k, kd, w, wd, 0.f, 0.f, st, acc, accd);
+            }
+            for (int c = 0; c < 4; ++c) accd[c] += (double)acc[c];
+        }
+    }
+    if (!act) return;
+    double tx = (double)me.frame.x, ty = (double)me.frame.y, ss, sn;
+    to_local<double>(tx, ty, accd, ss, sn);
+    double o[3];
+    self_field(kd, wd, (double)me.frame.z, tx, ty, x[ti], x[n + ti], x[2 * n + ti], o);
+    y[ti] = ss + o[0];
+    y[n + ti] = sn + o[1];
+    y[2 * n + ti] = accd[3] + o[2];
+}
+}  // namespace
+
+extern "C" ddm_status ddm_matvec_dense_static(ddm_ctx *ctx, const double *d_xy, int64_t n, double tau_lo,
+                                              double tau_hi, const double *d_x, double *d_y) {
+    if (!ctx || !d_xy || !d_x || !d_y || d_x == d_y)
+        return ctx_fail(ctx, DDM_EINVAL, "ddm_matvec_dense_static: bad arguments");
+    if (n <= 0 || n > DDM_STATIC_MAX_ELEMENTS)
+        return ctx_fail(ctx, DDM_EINVAL, "ddm_matvec_dense_static: n must be in [1, " +
+                                             std::to_string(DDM_STATIC_MAX_ELEMENTS) + "], got " + std::to_string(n));
+    if (!(tau_hi > tau_lo) || tau_lo < 0.0)
+        return ctx_fail(ctx, DDM_EINVAL, "ddm_matvec_dense_static: need 0 <= tau_lo < tau_hi");
+    int dev = 0;
+    DDM_CUDA_TRY(ctx, cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return ctx_fail(ctx, DDM_EINVAL, "ddm_matvec_dense_static: device index out of range");
+    StaticElem *sc = nullptr;
+    {
+        // set-up, once per device, with that device current: the host-side
+        // name of the array is not a device address; ask the runtime for it
+        std::lock_guard<std::mutex> lk(g_static_mu);
+        if (!g_static_ptr[dev]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+            if (e != cudaSuccess)
+                return ctx_fail(ctx, DDM_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            g_static_ptr[dev] = (StaticElem *)p;
+        }
+        sc = g_static_ptr[dev];
+    }
+    ddm_status st = upload_tables(ctx);
+    if (st) return st;
+    cudaStream_t s = ctx->stream;
+    Win<float> wf = make_win<float>(ctx, tau_lo, tau_hi);
+    Win<double> wd = make_win<double>(ctx, tau_lo, tau_hi);
+    k_static_prep<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_xy, d_x, n, sc);
+    k_static_dense<<<(unsigned)((n + ST_T - 1) / ST_T), ST_T, 0, s>>>(ctx->kf, ctx->kd, wf, wd, sc, d_x, n, d_y);
+    prof_end(ctx, 7, 2);
     DDM_CUDA_TRY(ctx, cudaGetLastError());
     return DDM_OK;
 }

@@ -28,7 +28,9 @@ _SYSTEMS = {"pressure": SYS_PRESSURE, "impermeable": SYS_IMPERMEABLE, "rate": SY
 EXPORTS = ("ddm_create", "ddm_destroy", "ddm_last_error", "ddm_build_tree", "ddm_tree_destroy",
            "ddm_tree_get_info", "ddm_matvec", "ddm_history_apply", "ddm_rhs", "ddm_gmres_solve", "ddm_sif",
            "ddm_profile", "ddm_profile_read", "ddm_batch_create", "ddm_batch_destroy", "ddm_batch_matvec",
-           "ddm_batch_gmres_solve", "ddm_server_create", "ddm_submit", "ddm_poll", "ddm_server_destroy")
+           "ddm_batch_gmres_solve", "ddm_server_create", "ddm_submit", "ddm_poll", "ddm_server_destroy",
+           "ddm_matvec_dense_static")
+STATIC_MAX_ELEMENTS = 65536
 NSTAGES = 10
 STAGES = ("charges", "self", "p2m", "m2m", "m2l", "l2l", "leaf", "dense", "krylov", "tree")
 
@@ -110,6 +112,7 @@ def load(build_if_missing: bool = True):
                                       ctypes.POINTER(ddm_gmres_info)]
         L.ddm_sif.argtypes = [_VP, _VP, _VP, _VP, ctypes.c_int, _VP, _VP]
         L.ddm_profile.argtypes = [_VP, ctypes.c_int]
+        L.ddm_matvec_dense_static.argtypes = [_VP, _VP, ctypes.c_int64, ctypes.c_double, ctypes.c_double, _VP, _VP]
         L.ddm_server_create.argtypes = [_VP, ctypes.c_size_t, ctypes.c_int, ctypes.c_double, ctypes.POINTER(_VP)]
         L.ddm_submit.argtypes = [_VP, ctypes.POINTER(ddm_request), ctypes.POINTER(ctypes.c_uint64)]
         L.ddm_poll.argtypes = [_VP, ctypes.c_uint64, ctypes.POINTER(ddm_result)]
@@ -122,13 +125,10 @@ def load(build_if_missing: bool = True):
         L.ddm_batch_gmres_solve.argtypes = [_VP, _VP, ctypes.c_double, _VP, _VP, ctypes.POINTER(ddm_gmres_params),
                                             ctypes.POINTER(ddm_gmres_info)]
         L.ddm_profile_read.argtypes = [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
-        for name in EXPORTS:
+        for name in EXPORTS:      # every entry point returns ddm_status unless set above
             fn = getattr(L, name)
-            if fn.restype is ctypes.c_int or name in ("ddm_create", "ddm_build_tree", "ddm_tree_get_info",
-                                                      "ddm_matvec", "ddm_history_apply", "ddm_rhs",
-                                                      "ddm_gmres_solve", "ddm_sif", "ddm_profile",
-                                                      "ddm_profile_read", "ddm_batch_create", "ddm_batch_matvec",
-                                                      "ddm_batch_gmres_solve", "ddm_server_create", "ddm_submit", "ddm_poll", "ddm_server_destroy"):
+            if name not in ("ddm_destroy", "ddm_tree_destroy", "ddm_batch_destroy", "ddm_server_destroy",
+                            "ddm_last_error"):
                 fn.restype = ctypes.c_int
         _lib = L
         return L
@@ -241,6 +241,15 @@ def ddm_profile_read(ctx) -> dict:
     n = (ctypes.c_int64 * NSTAGES)()
     _check(ctx, load().ddm_profile_read(ctx, ms, n), "ddm_profile_read")
     return {STAGES[k]: (ms[k], n[k]) for k in range(NSTAGES)}
+
+
+def ddm_matvec_dense_static(ctx, xy, tau_lo, tau_hi, x, y):
+    """Allocation-free dense product (see include/ddm.h): y = [K(hi) - K(lo)] x
+    for the elements xy (4N), using the library's fixed scratch array."""
+    n = xy.numel() // 4
+    _check(ctx, load().ddm_matvec_dense_static(ctx, _VP(_dev(xy, 4 * n, "xy")), n, float(tau_lo), float(tau_hi),
+                                               _VP(_dev(x, 3 * n, "x")), _VP(_dev(y, 3 * n, "y"))),
+           "ddm_matvec_dense_static")
 
 
 def ddm_batch_create(ctx, trees):
