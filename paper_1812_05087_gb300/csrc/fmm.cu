@@ -479,96 +479,94 @@ __device__ __forceinline__ void pair_field(const KConst<float> &k, const KConst<
     }
 }
 
-// Near field + L2P.  One block per group of 32 consecutive (Morton-sorted)
-// targets; the block's NEAR_W warps split the union of the neighbour leaves
-// of those targets, stream each leaf through shared memory, and every lane
-// evaluates the same source against its own target (skipping sources whose
-// leaf is not adjacent to the target's leaf, and its own element).  FP32
-// within a 32-source tile, FP64 across tiles; the warps' sums are reduced in
-// shared memory, then warp 0 adds L2P from the target leaf's expansion.
+// Near field + L2P.  One warp per target: the lanes take the sources of the
+// target leaf's neighbour leaves (self + up to 8; about 50 sources at the
+// usual depths) in a strided loop, so nearly every lane has a pair and there
+// are as many warps as targets.  Each lane sums its pairs in FP32, the warp
+// then reduces in FP64; L2P is split over the lanes by Chebyshev node and
+// reduced the same way.
 constexpr int NEAR_W = 8;
 constexpr int NEAR_T = 32 * NEAR_W;
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
 template <bool PRECISE>
 __global__ void __launch_bounds__(NEAR_T) k_near(KConst<float> k, KConst<double> kd, Win<float> w, Win<double> wd,
-                                                 int64_t loff, int64_t ngroups, const int32_t *goff,
-                                                 const int32_t *gleaf, const int32_t *cstart, const int32_t *cend,
-                                                 const int32_t *cix, const int32_t *ciy, const int32_t *elem_leaf,
-                                                 const float4 *grel, const float4 *frame, const float4 *chg,
-                                                 const int64_t *perm, float wL, int n, const float *F, int use_far,
-                                                 int64_t N, double scale, double *y) {
-    __shared__ SrcTile tiles[NEAR_W][32];
-    __shared__ double red[NEAR_W][4][32];
+                                                 int64_t loff, const int32_t *cstart, const int32_t *cend,
+                                                 const int32_t *cix, const int32_t *ciy, const int32_t *nboff,
+                                                 const int32_t *nbidx, const int32_t *elem_leaf, const float4 *grel,
+                                                 const float4 *frame, const float4 *chg, const int64_t *perm,
+                                                 float wL, int n, const float *F, int use_far, int64_t N,
+                                                 double scale, double *y) {
+    __shared__ int sst[NEAR_W][9], spre[NEAR_W][10];
+    __shared__ float sox[NEAR_W][9], soy[NEAR_W][9];
     int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int64_t g = blockIdx.x;
-    SrcTile *tile = tiles[wid];
-    int64_t ti = 32 * g + lane;
-    bool act = ti < N;
-    int32_t myleaf = act ? elem_leaf[ti] : elem_leaf[N - 1];
-    int ix = cix[loff + myleaf], iy = ciy[loff + myleaf];
-    float mx = 0.f, my = 0.f;
-    if (act) {
-        float4 r = grel[ti];
-        mx = 0.5f * (r.x + r.z);
-        my = 0.5f * (r.y + r.w);
-    }
-    double accd[4] = {0, 0, 0, 0};
-    for (int q = goff[g] + wid; q < goff[g + 1]; q += NEAR_W) {
-        int64_t J = loff + gleaf[q];
-        int jx = cix[J], jy = ciy[J];
-        bool nb = act && abs(jx - ix) <= 1 && abs(jy - iy) <= 1;
-        float ox = wL * (float)(jx - ix), oy = wL * (float)(jy - iy);
-        int s0 = cstart[J], s1 = cend[J];
-        for (int sb = s0; sb < s1; sb += 32) {
-            int ns = min(32, s1 - sb);
-            __syncwarp();
-            if (lane < ns) {
-                int sj = sb + lane;
-                float4 r = grel[sj], f = frame[sj], c = chg[sj];
-                SrcTile st;
-                st.x0 = r.x; st.y0 = r.y; st.x1 = r.z; st.y1 = r.w;
-                st.Dx = c.x; st.Dy = c.y; st.q = c.z; st.a = f.z; st.tx = f.x; st.ty = f.y; st.idx = sj;
-                tile[lane] = st;
-            }
-            __syncwarp();
-            if (nb) {
-                float acc[4] = {0, 0, 0, 0};
-                for (int j = 0; j < ns; ++j) {
-                    SrcTile st = tile[j];
-                    if (st.idx == (int)ti) continue;
-                    st.x0 += ox; st.y0 += oy; st.x1 += ox; st.y1 += oy;
-                    pair_field<PRECISE>(k, kd, w, wd, mx, my, st, acc, accd);
-                }
-                for (int c = 0; c < 4; ++c) accd[c] += (double)acc[c];
-            }
+    int64_t ti = (int64_t)blockIdx.x * NEAR_W + wid;
+    if (ti >= N) return;                      // whole warp leaves together
+    int32_t leaf = elem_leaf[ti];
+    int64_t cell = loff + leaf;
+    int ix = cix[cell], iy = ciy[cell];
+    int q0 = nboff[leaf], nq = nboff[leaf + 1] - q0;
+    if (lane == 0) {
+        int run = 0;
+        for (int q = 0; q < nq; ++q) {
+            int64_t J = loff + nbidx[q0 + q];
+            sst[wid][q] = cstart[J];
+            spre[wid][q] = run;
+            run += cend[J] - cstart[J];
+            sox[wid][q] = wL * (float)(cix[J] - ix);
+            soy[wid][q] = wL * (float)(ciy[J] - iy);
         }
+        spre[wid][nq] = run;
     }
-    for (int c = 0; c < 4; ++c) red[wid][c][lane] = accd[c];
-    __syncthreads();
-    if (wid != 0 || !act) return;
-    for (int c = 0; c < 4; ++c) {
-        double v = 0.0;
-        for (int ww = 0; ww < NEAR_W; ++ww) v += red[ww][c][lane];
-        accd[c] = v;
+    __syncwarp();
+    float4 rt = grel[ti];
+    float mx = 0.5f * (rt.x + rt.z), my = 0.5f * (rt.y + rt.w);
+    int S = spre[wid][nq];
+    float acc[4] = {0, 0, 0, 0};
+    double accd[4] = {0, 0, 0, 0};
+    int q = 0;
+    for (int c = lane; c < S; c += 32) {
+        while (c >= spre[wid][q + 1]) ++q;
+        int sj = sst[wid][q] + (c - spre[wid][q]);
+        if (sj == (int)ti) continue;
+        float4 r = grel[sj], f = frame[sj], cg = chg[sj];
+        float ox = sox[wid][q], oy = soy[wid][q];
+        SrcTile st;
+        st.x0 = r.x + ox; st.y0 = r.y + oy; st.x1 = r.z + ox; st.y1 = r.w + oy;
+        st.Dx = cg.x; st.Dy = cg.y; st.q = cg.z; st.a = f.z; st.tx = f.x; st.ty = f.y; st.idx = sj;
+        pair_field<PRECISE>(k, kd, w, wd, mx, my, st, acc, accd);
     }
+    for (int c = 0; c < 4; ++c) accd[c] += (double)acc[c];
     if (use_far) {
+        // L2P: lane handles nodes m = lane, lane + 32, ...
         float hL = 0.5f * wL;
-        float cx_[DDM_MAX_CHEB], cy_[DDM_MAX_CHEB];
-        cardinal<DDM_MAX_CHEB>(mx / hL, n, cx_);
-        cardinal<DDM_MAX_CHEB>(my / hL, n, cy_);
+        float xh = mx / hL, yh = my / hL;
         int n2 = n * n;
-        const float *Fc = F + (loff + myleaf) * 4 * n2;
+        float sx = 0.f, sy = 0.f;
+        int hx = -1, hy = -1;
+        for (int j = 0; j < n; ++j) {             // barycentric denominators
+            float dxj = xh - c_gl.cheb[j], dyj = yh - c_gl.cheb[j];
+            if (fabsf(dxj) < 1e-7f) hx = j;
+            if (fabsf(dyj) < 1e-7f) hy = j;
+            sx += c_gl.bw[j] / dxj;
+            sy += c_gl.bw[j] / dyj;
+        }
+        const float *Fc = F + cell * 4 * n2;
         float f4[4] = {0, 0, 0, 0};
-        for (int a = 0; a < n; ++a) {
-            float s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-            for (int b = 0; b < n; ++b) {
-                int m = a * n + b;
-                s0 += cy_[b] * Fc[m]; s1 += cy_[b] * Fc[n2 + m];
-                s2 += cy_[b] * Fc[2 * n2 + m]; s3 += cy_[b] * Fc[3 * n2 + m];
-            }
-            f4[0] += cx_[a] * s0; f4[1] += cx_[a] * s1; f4[2] += cx_[a] * s2; f4[3] += cx_[a] * s3;
+        for (int m = lane; m < n2; m += 32) {
+            int a = m / n, bb = m % n;
+            float la = hx >= 0 ? (a == hx ? 1.f : 0.f) : c_gl.bw[a] / (xh - c_gl.cheb[a]) / sx;
+            float lb = hy >= 0 ? (bb == hy ? 1.f : 0.f) : c_gl.bw[bb] / (yh - c_gl.cheb[bb]) / sy;
+            float v = la * lb;
+            f4[0] += v * Fc[m]; f4[1] += v * Fc[n2 + m]; f4[2] += v * Fc[2 * n2 + m]; f4[3] += v * Fc[3 * n2 + m];
         }
         for (int c = 0; c < 4; ++c) accd[c] += (double)f4[c];
     }
+    for (int c = 0; c < 4; ++c) accd[c] = warp_sum(accd[c]);
+    if (lane != 0) return;
     float4 f = frame[ti];
     double ss, sn;
     to_local<double>((double)f.x, (double)f.y, accd, ss, sn);
@@ -827,9 +825,9 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
     }
     prof_begin(ctx, 6);
     auto knr = precise ? k_near<true> : k_near<false>;
-    knr<<<(unsigned)t->n_groups, NEAR_T, 0, s>>>(
-        kf, ctx->kd, wf, wd, loff, t->n_groups, t->grp_off, t->grp_leaf, t->cell_start, t->cell_end, t->cell_ix,
-        t->cell_iy, t->elem_leaf, t->g_rel, t->g_frame, t->chg, t->perm, wL, n, t->Fl, use_far, N, scale, y);
+    knr<<<(unsigned)((N + NEAR_W - 1) / NEAR_W), NEAR_T, 0, s>>>(
+        kf, ctx->kd, wf, wd, loff, t->cell_start, t->cell_end, t->cell_ix, t->cell_iy, t->nb_off, t->nb_idx,
+        t->elem_leaf, t->g_rel, t->g_frame, t->chg, t->perm, wL, n, t->Fl, use_far, N, scale, y);
     prof_end(ctx, 6, 1);
     DDM_CUDA_TRY(ctx, cudaGetLastError());
     return DDM_OK;

@@ -500,6 +500,58 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
                                                    t->lvl_off[l - 1], t->cell_parent); ++tl_launches;
     }
 
+    // depth by cost model: the occupancy rule gives the deepest useful
+    // depth; shallower depths trade M2L and tree passes for more direct
+    // pairs.  Costs per unit measured on GB300 for n = 8 (near pair 19.4 ps,
+    // interaction pair 8.1 ns scaling with n^4, cell 25 ns).
+    if (L >= 3 && ctx->prm.max_depth == 0) {
+        int32_t *ccnt = S.get<int32_t>(NC + 1), *coff = S.get<int32_t>(NC + 1);
+        unsigned long long *pp = S.get<unsigned long long>(1);
+        TRY(S.err);
+        std::vector<long long> il_lvl(L + 1, 0);
+        TRY(cudaMemsetAsync(ccnt, 0, (NC + 1) * sizeof(int32_t), st));
+        for (int l = 2; l <= L; ++l) {
+            int64_t nc = ncl[l];
+            k_ilist<<<(nc + TB - 1) / TB, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, t->lvl_off[l], nc, 1 << l,
+                                                      nullptr, nullptr, ccnt); ++tl_launches;
+        }
+        std::vector<int32_t> hc(NC);
+        TRY(cudaMemcpyAsync(hc.data(), ccnt, NC * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        TRY(cudaStreamSynchronize(st));
+        for (int l = 2; l <= L; ++l)
+            for (int64_t c = t->lvl_off[l]; c < t->lvl_off[l + 1]; ++c) il_lvl[l] += hc[c];
+        double nfac = std::pow(ctx->prm.n_cheb / 8.0, 4.0);
+        double best = 1e300;
+        int bestL = L;
+        for (int Lc = std::max(2, L - 4); Lc <= L; ++Lc) {
+            int64_t nc = ncl[Lc], off = t->lvl_off[Lc];
+            k_neigh<<<(nc + TB - 1) / TB, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, off, nc, 1 << Lc, nullptr,
+                                                      nullptr, ccnt); ++tl_launches;
+            int32_t tot;
+            TRY(scan_excl(S, st, ccnt, coff, nc, &tot));
+            TRY(cudaMemcpyAsync(coff + nc, &tot, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+            int32_t *nbi = S.get<int32_t>(std::max(tot, 1));
+            TRY(S.err);
+            k_neigh<<<(nc + TB - 1) / TB, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, off, nc, 1 << Lc, coff,
+                                                      nbi, nullptr); ++tl_launches;
+            TRY(cudaMemsetAsync(pp, 0, sizeof(unsigned long long), st));
+            k_p2p_count<<<(nc + TB - 1) / TB, TB, 0, st>>>(t->cell_start, t->cell_end, off, nc, coff, nbi, pp); ++tl_launches;
+            unsigned long long hp = 0;
+            TRY(cudaMemcpyAsync(&hp, pp, sizeof(hp), cudaMemcpyDeviceToHost, st));
+            TRY(cudaStreamSynchronize(st));
+            long long m2l = 0, cells = 0;
+            for (int l = 2; l <= Lc; ++l) m2l += il_lvl[l];
+            for (int l = 0; l <= Lc; ++l) cells += ncl[l];
+            double cost = 19.4e-12 * (double)hp + 8.1e-9 * nfac * (double)m2l + 25e-9 * (double)cells;
+            if (cost < best) { best = cost; bestL = Lc; }
+        }
+        L = bestL;
+        t->depth = L;
+        t->lvl_off.resize(L + 2);
+        NC = t->lvl_off[L + 1];      // cells of the levels kept
+        t->n_cells = NC;
+    }
+
     // neighbours of leaves
     int64_t nleaf = ncl[L], loff = t->lvl_off[L];
     int side = 1 << L;
