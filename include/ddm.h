@@ -68,8 +68,10 @@ typedef struct {
 } ddm_material;
 
 /* FMM controls (paper Sec. 3): n_cheb = Chebyshev nodes per dimension
- * (n^2 per cell), leaf_size = the "prescribed number" of elements above
- * which a cell is split, max_depth caps the quadtree depth (0 = automatic).
+ * (n^2 per cell; even, 2..16), leaf_size = the "prescribed number" of elements above
+ * which a cell is split, max_depth fixes the quadtree depth cap (0 =
+ * automatic: the deepest depth allowed by leaf_size, then the depth that
+ * minimises a cost model of the product measured on GB300).
  * quad_near = Gauss points per element for the fluid-source near field
  * (0 = 6). */
 typedef struct {

@@ -196,7 +196,8 @@ ddm_status ddm_create(ddm_ctx **out, const ddm_material *mat, const ddm_fmm_para
     if (p.n_cheb <= 0) p.n_cheb = 8;
     if (p.leaf_size <= 0) p.leaf_size = 32;
     if (p.quad_near <= 0) p.quad_near = 6;
-    if (p.n_cheb < 2 || p.n_cheb > DDM_MAX_CHEB || p.quad_near > 16 || p.max_depth < 0) return DDM_EINVAL;
+    if (p.n_cheb < 2 || p.n_cheb > DDM_MAX_CHEB || (p.n_cheb & 1) || p.quad_near > 16 || p.max_depth < 0)
+        return DDM_EINVAL;
     ddm_ctx *c = new (std::nothrow) ddm_ctx();
     if (!c) return DDM_ENOMEM;
     c->mat = *mat;

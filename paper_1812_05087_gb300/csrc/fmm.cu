@@ -325,19 +325,20 @@ __global__ void k_m2l_ops(KConst<float> k, Win<float> w, int L, double h0, int n
     }
 }
 
-// C[BM x BN] tile of K (rows) x W columns of one key group; BK-deep steps.
-constexpr int GM_BM = 64, GM_BN = 64, GM_BK = 16;
-__global__ void __launch_bounds__(256) k_m2l_gemm(const int32_t *koff, const int2 *pairs, int n, const float *ops,
-                                                  const float *W, float *F, int keys_first) {
-    __shared__ float sK[GM_BK][GM_BM + 4];
-    __shared__ float sB[GM_BK][GM_BN + 4];
+// One work item = one (level, offset) group's column tile of up to 64
+// interaction pairs; blockIdx.y picks a 128-row slice of the 4n^2 operator
+// rows.  256 threads, 8 x 4 register tile each, BK = 16, double-buffered
+// shared memory; results are added to the targets' local expansions.
+constexpr int GM_BM = 128, GM_BN = 64, GM_BK = 16;
+__global__ void __launch_bounds__(256) k_m2l_gemm(const int2 *work, const int32_t *koff, const int2 *pairs, int n,
+                                                  const float *ops, const float *W, float *F) {
+    __shared__ __align__(16) float sK[2][GM_BK][GM_BM];
+    __shared__ __align__(16) float sB[2][GM_BK][GM_BN];
     __shared__ int sI[GM_BN], sJ[GM_BN];
-    int key = keys_first + blockIdx.z;
-    int p0 = koff[key] + blockIdx.y * GM_BN, p1 = koff[key + 1];
-    if (p0 >= p1) return;
+    int2 wk = work[blockIdx.x];
+    int key = wk.x, p0 = wk.y, p1 = min(koff[key + 1], p0 + GM_BN);
     int n2 = n * n, ld = 4 * n2;
-    int r0 = blockIdx.x * GM_BM;
-    if (r0 >= ld) return;
+    int r0 = blockIdx.y * GM_BM;
     const float *K = ops + (int64_t)key * 16 * n2 * n2;
     int tid = threadIdx.x;
     if (tid < GM_BN) {
@@ -346,31 +347,53 @@ __global__ void __launch_bounds__(256) k_m2l_gemm(const int32_t *koff, const int
         sJ[tid] = p < p1 ? pairs[p].y : -1;
     }
     __syncthreads();
-    int tr = (tid / 16) * 4, tc = (tid % 16) * 4;    // 4x4 micro tile
-    float acc[4][4] = {{0}};
-    for (int k0 = 0; k0 < ld; k0 += GM_BK) {
-        // K tile: BM rows x BK cols  (coalesced along k)
-        for (int i = tid; i < GM_BM * GM_BK; i += 256) {
-            int rr = i / GM_BK, kk = i % GM_BK;
-            int row = r0 + rr, col = k0 + kk;
-            sK[kk][rr] = (row < ld && col < ld) ? K[(int64_t)row * ld + col] : 0.f;
+    // loaders: K tile 128 x 16 -> each thread 8 consecutive k of one row;
+    // B tile 16 x 64 -> each thread 4 consecutive k of one column
+    int kr = tid >> 1, kk0 = (tid & 1) * 8;
+    int bj = tid >> 2, bk0 = (tid & 3) * 4;
+    int Jb = sJ[bj];
+    int tr = (tid >> 4) * 8, tc = (tid & 15) * 4;
+    float acc[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    int nsteps = ld / GM_BK;
+    for (int st = 0; st <= nsteps; ++st) {
+        int buf = st & 1;
+        if (st < nsteps) {       // stage step st into buffer buf
+            int k0 = st * GM_BK, row = r0 + kr;
+            if (row < ld) {
+                const float *src = K + (int64_t)row * ld + k0 + kk0;
+                float4 v0 = *(const float4 *)src, v1 = *(const float4 *)(src + 4);
+                sK[buf][kk0 + 0][kr] = v0.x; sK[buf][kk0 + 1][kr] = v0.y;
+                sK[buf][kk0 + 2][kr] = v0.z; sK[buf][kk0 + 3][kr] = v0.w;
+                sK[buf][kk0 + 4][kr] = v1.x; sK[buf][kk0 + 5][kr] = v1.y;
+                sK[buf][kk0 + 6][kr] = v1.z; sK[buf][kk0 + 7][kr] = v1.w;
+            } else {
+                for (int q = 0; q < 8; ++q) sK[buf][kk0 + q][kr] = 0.f;
+            }
+            if (Jb >= 0) {
+                float4 v = *(const float4 *)(W + (int64_t)Jb * ld + k0 + bk0);
+                sB[buf][bk0 + 0][bj] = v.x; sB[buf][bk0 + 1][bj] = v.y;
+                sB[buf][bk0 + 2][bj] = v.z; sB[buf][bk0 + 3][bj] = v.w;
+            } else {
+                for (int q = 0; q < 4; ++q) sB[buf][bk0 + q][bj] = 0.f;
+            }
         }
-        // B tile: BK rows x BN pairs (column j = W of source J)
-        for (int i = tid; i < GM_BK * GM_BN; i += 256) {
-            int kk = i / GM_BN, jj = i % GM_BN;
-            int J = sJ[jj], col = k0 + kk;
-            sB[kk][jj] = (J >= 0 && col < ld) ? W[(int64_t)J * ld + col] : 0.f;
-        }
-        __syncthreads();
+        if (st > 0) {            // compute step st - 1 from the other buffer
+            int cur = buf ^ 1;
 #pragma unroll
-        for (int kk = 0; kk < GM_BK; ++kk) {
-            float a[4], b[4];
+            for (int kk = 0; kk < GM_BK; ++kk) {
+                float4 a0 = *(const float4 *)&sK[cur][kk][tr], a1 = *(const float4 *)&sK[cur][kk][tr + 4];
+                float4 b0 = *(const float4 *)&sB[cur][kk][tc];
+                float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                float bb[4] = {b0.x, b0.y, b0.z, b0.w};
 #pragma unroll
-            for (int i = 0; i < 4; ++i) { a[i] = sK[kk][tr + i]; b[i] = sB[kk][tc + i]; }
+                for (int i = 0; i < 8; ++i)
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], bb[j], acc[i][j]);
+            }
         }
         __syncthreads();
     }
@@ -379,7 +402,7 @@ __global__ void __launch_bounds__(256) k_m2l_gemm(const int32_t *koff, const int
         int I = sI[tc + j];
         if (I < 0) continue;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < 8; ++i) {
             int row = r0 + tr + i;
             if (row < ld) atomicAdd(&F[(int64_t)I * ld + row], acc[i][j]);
         }
@@ -806,12 +829,9 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
                 prof_begin(ctx, 4);
             }
             DDM_CUDA_TRY(ctx, cudaMemsetAsync(t->Fl, 0, (size_t)t->n_cells * 4 * n2 * sizeof(float), s));
-            // largest group bounds the column tiles
-            int kf0 = 2 * 49, nkeys = nk - kf0;
-            if (nkeys > 0) {
-                dim3 g((unsigned)((4 * n2 + GM_BM - 1) / GM_BM), (unsigned)((t->max_group + GM_BN - 1) / GM_BN),
-                       (unsigned)nkeys);
-                k_m2l_gemm<<<g, 256, 0, s>>>(t->mk_off, t->mk_pair, n, t->m2l_ops, t->W, t->Fl, kf0);
+            if (t->n_work > 0) {
+                dim3 g((unsigned)t->n_work, (unsigned)((4 * n2 + GM_BM - 1) / GM_BM));
+                k_m2l_gemm<<<g, 256, 0, s>>>(t->mk_work, t->mk_off, t->mk_pair, n, t->m2l_ops, t->W, t->Fl);
             }
         }
         prof_end(ctx, 4, 1);

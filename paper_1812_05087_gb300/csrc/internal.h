@@ -80,6 +80,8 @@ struct ddm_tree {
     int32_t *mk_off;           // CSR over keys
     int2 *mk_pair;             // (target cell, source cell), global cell indices
     int max_group;             // largest (level, offset) group
+    int2 *mk_work;             // (key, first pair) of every 64-pair column tile
+    int n_work;
     // M2L operators of the current time window, one (4n^2 x 4n^2) matrix per key
     float *m2l_ops;
     double ops_lo, ops_hi;

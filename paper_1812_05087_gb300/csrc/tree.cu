@@ -385,7 +385,7 @@ __global__ void k_p2p_count(const int32_t *cstart, const int32_t *cend, int64_t 
 
 void tree_free(ddm_tree *t) {
     if (!t) return;
-    void *ps[] = {t->pb_off, t->pb_elem, t->pb_moff, t->pb_inv, t->mk_off, t->mk_pair, t->m2l_ops, t->grp_off, t->grp_leaf, t->perm, t->cell_key, t->cell_ix, t->cell_iy, t->cell_start, t->cell_end, t->cell_parent,
+    void *ps[] = {t->mk_work, t->pb_off, t->pb_elem, t->pb_moff, t->pb_inv, t->mk_off, t->mk_pair, t->m2l_ops, t->grp_off, t->grp_leaf, t->perm, t->cell_key, t->cell_ix, t->cell_iy, t->cell_start, t->cell_end, t->cell_parent,
                   t->il_off, t->il_idx, t->nb_off, t->nb_idx, t->elem_leaf, t->g_rel, t->g_frame,
                   t->xy_sorted, t->xy_caller, t->self_blk, t->W, t->Fl, t->chg};
     for (void *p : ps) dfree(p, t->stream);
@@ -503,7 +503,7 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
     // depth by cost model: the occupancy rule gives the deepest useful
     // depth; shallower depths trade M2L and tree passes for more direct
     // pairs.  Costs per unit measured on GB300 for n = 8 (near pair 19.4 ps,
-    // interaction pair 8.1 ns scaling with n^4, cell 25 ns).
+    // interaction pair 3.5 ns scaling with n^4, cell 25 ns).
     if (L >= 3 && ctx->prm.max_depth == 0) {
         int32_t *ccnt = S.get<int32_t>(NC + 1), *coff = S.get<int32_t>(NC + 1);
         unsigned long long *pp = S.get<unsigned long long>(1);
@@ -542,7 +542,7 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
             long long m2l = 0, cells = 0;
             for (int l = 2; l <= Lc; ++l) m2l += il_lvl[l];
             for (int l = 0; l <= Lc; ++l) cells += ncl[l];
-            double cost = 19.4e-12 * (double)hp + 8.1e-9 * nfac * (double)m2l + 25e-9 * (double)cells;
+            double cost = 21.5e-12 * (double)hp + 3.5e-9 * nfac * (double)m2l + 25e-9 * (double)cells;
             if (cost < best) { best = cost; bestL = Lc; }
         }
         L = bestL;
@@ -614,7 +614,16 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
         TRY(cudaMemcpyAsync(hk.data(), t->mk_off, (nk + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         TRY(cudaStreamSynchronize(st));
         t->max_group = 0;
-        for (int k = 0; k < nk; ++k) t->max_group = std::max(t->max_group, hk[k + 1] - hk[k]);
+        std::vector<int2> work;
+        for (int k = 0; k < nk; ++k) {
+            t->max_group = std::max(t->max_group, hk[k + 1] - hk[k]);
+            for (int p0 = hk[k]; p0 < hk[k + 1]; p0 += 64) work.push_back(make_int2(k, p0));
+        }
+        t->n_work = (int)work.size();
+        TRY(dalloc(&t->mk_work, std::max<size_t>(work.size(), 1) * sizeof(int2), st));
+        if (!work.empty())
+            TRY(cudaMemcpyAsync(t->mk_work, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+        TRY(cudaStreamSynchronize(st));
     }
 
     // sorted geometry
