@@ -276,8 +276,11 @@ ddm_status ddm_matvec_dense_static(ddm_ctx *ctx, const double *d_xy, int64_t n, 
  * synchronises the stream and returns, per stage, the summed milliseconds
  * (ms[DDM_NSTAGES]) and the number of kernel launches (counted whether or
  * not timing is enabled) since the last read, then resets both.
- * Stages: 0 charges, 1 own element, 2 P2M, 3 M2M, 4 M2L, 5 L2L, 6 leaf
- * (L2P + P2P), 7 dense product, 8 GMRES vector kernels, 9 tree build. */
+ * Stages: 0 charges + own elements (dense path, trees below depth 2),
+ * 1 own-element blocks of a new time window, 2 upward pass (charges, own
+ * elements, P2M, M2M), 3 M2L operators of a new time window, 4 M2L,
+ * 5 downward pass (L2L), 6 leaf (L2P + P2P), 7 dense product, 8 GMRES
+ * vector kernels, 9 tree build. */
 #define DDM_NSTAGES 10
 ddm_status ddm_profile(ddm_ctx *ctx, int enable);
 ddm_status ddm_profile_read(ddm_ctx *ctx, double *ms, int64_t *launches);

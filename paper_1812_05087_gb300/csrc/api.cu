@@ -111,40 +111,6 @@ __global__ void k_scale_to(const double *w, int64_t len, const double *nrm2, dou
     if (i >= len) return;
     out[i] = nrm > 0 ? w[i] / nrm : 0.0;
 }
-// z = M^-1 v (block Jacobi with the own-element blocks, inverted per element)
-__global__ void k_precond(const double *Minv, int64_t n, int nc, const double *v, double *z) {
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= n) return;
-    double in[3] = {0, 0, 0};
-    for (int c = 0; c < nc; ++c) in[c] = v[c * n + e];
-    for (int r = 0; r < nc; ++r) {
-        double s = 0;
-        for (int c = 0; c < nc; ++c) s += Minv[9 * e + 3 * r + c] * in[c];
-        z[r * n + e] = s;
-    }
-}
-// inverse of the system's own-element block (3x3, or the 2x2 of the 2N systems)
-__global__ void k_invert(const double *blk, int64_t n, int sys, double *Minv) {
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= n) return;
-    const double *B = blk + 9 * e;
-    double *O = Minv + 9 * e;
-    for (int k = 0; k < 9; ++k) O[k] = 0;
-    if (sys == DDM_SYS_PRESSURE) {
-        double a = B[0], b = B[1], c = B[2], d = B[3], f = B[4], g = B[5], h = B[6], i = B[7], j = B[8];
-        double A = f * j - g * i, Bc = -(d * j - g * h), C = d * i - f * h;
-        double det = a * A + b * Bc + c * C;
-        double id = 1.0 / det;
-        O[0] = A * id; O[1] = -(b * j - c * i) * id; O[2] = (b * g - c * f) * id;
-        O[3] = Bc * id; O[4] = (a * j - c * h) * id; O[5] = -(a * g - c * d) * id;
-        O[6] = C * id; O[7] = -(a * i - b * h) * id; O[8] = (a * f - b * d) * id;
-    } else {
-        double a = B[0], b = B[1], c = B[3], d = B[4];
-        if (sys == DDM_SYS_RATE) { c += B[6]; d += B[7]; }
-        double id = 1.0 / (a * d - b * c);
-        O[0] = d * id; O[1] = -b * id; O[3] = -c * id; O[4] = a * id;
-    }
-}
 // restrict a 3N product to the system rows (RATE: sigma_n + p)
 // (combine = 1 for products, 0 for a right-hand side, whose rows are already
 // the system's)

@@ -88,18 +88,6 @@ __global__ void k_comb_seg(const double *V, int64_t ld, int nv, const double *Y,
 }
 
 // arena (nc blocks of N per problem) <-> 3N layout helpers, one problem
-__global__ void k_precond_to3(const double *Minv, int64_t n, int nc, const double *v, double *z3) {
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= n) return;
-    double in[3] = {0, 0, 0};
-    for (int c = 0; c < nc; ++c) in[c] = v[c * n + e];
-    for (int r = 0; r < 3; ++r) {
-        double s = 0;
-        if (r < nc)
-            for (int c = 0; c < nc; ++c) s += Minv[9 * e + 3 * r + c] * in[c];
-        z3[r * n + e] = s;
-    }
-}
 __global__ void k_copy_to3(const double *v, int64_t n, int nc, double *z3) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= n) return;
@@ -112,38 +100,6 @@ __global__ void k_restrict_b(const double *y, int64_t n, int sys, int combine, d
     out[n + e] = y[n + e] + (combine && sys == DDM_SYS_RATE ? y[2 * n + e] : 0.0);
     if (sys == DDM_SYS_PRESSURE) out[2 * n + e] = y[2 * n + e];
 }
-__global__ void k_add_precond(const double *Minv, int64_t n, int nc, const double *v, double *x3) {
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= n) return;
-    double in[3] = {0, 0, 0};
-    for (int c = 0; c < nc; ++c) in[c] = v[c * n + e];
-    for (int r = 0; r < nc; ++r) {
-        double s = 0;
-        for (int c = 0; c < nc; ++c) s += Minv[9 * e + 3 * r + c] * in[c];
-        x3[r * n + e] += s;
-    }
-}
-__global__ void k_invert_b(const double *blk, int64_t n, int sys, double *Minv) {
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= n) return;
-    const double *B = blk + 9 * e;
-    double *O = Minv + 9 * e;
-    for (int k = 0; k < 9; ++k) O[k] = 0;
-    if (sys == DDM_SYS_PRESSURE) {
-        double a = B[0], b = B[1], c = B[2], d = B[3], f = B[4], g = B[5], h = B[6], i = B[7], j = B[8];
-        double A = f * j - g * i, Bc = -(d * j - g * h), C = d * i - f * h;
-        double id = 1.0 / (a * A + b * Bc + c * C);
-        O[0] = A * id; O[1] = -(b * j - c * i) * id; O[2] = (b * g - c * f) * id;
-        O[3] = Bc * id; O[4] = (a * j - c * h) * id; O[5] = -(a * g - c * d) * id;
-        O[6] = C * id; O[7] = -(a * i - b * h) * id; O[8] = (a * f - b * d) * id;
-    } else {
-        double a = B[0], b = B[1], c = B[3], d = B[4];
-        if (sys == DDM_SYS_RATE) { c += B[6]; d += B[7]; }
-        double id = 1.0 / (a * d - b * c);
-        O[0] = d * id; O[1] = -b * id; O[3] = -c * id; O[4] = a * id;
-    }
-}
-
 inline unsigned nb(int64_t n) { return (unsigned)((n + BT - 1) / BT); }
 
 }  // namespace

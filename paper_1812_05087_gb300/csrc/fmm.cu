@@ -36,6 +36,19 @@ struct GLTab {
 };
 __constant__ GLTab c_gl;
 
+// dispatch on the (even) number of Chebyshev nodes per dimension
+#define DDM_CHEB_SWITCH(n, M)              \
+    switch (n) {                           \
+        case 2: M(2); break;               \
+        case 4: M(4); break;               \
+        case 6: M(6); break;               \
+        case 8: M(8); break;               \
+        case 10: M(10); break;             \
+        case 12: M(12); break;             \
+        case 14: M(14); break;             \
+        default: M(16); break;             \
+    }
+
 // Gauss-Legendre nodes/weights on [-1, 1] (Newton on P_n), FP64 on the host.
 void gauss_legendre(int n, double *x, double *w) {
     for (int i = 0; i < n; ++i) {
@@ -74,32 +87,34 @@ __device__ __forceinline__ void cardinal(float x, int n, float *out) {
     for (int j = 0; j < n; ++j) out[j] *= is;
 }
 
-// ----------------------------------------------------------------- charges
-__global__ void k_charges(const double *x, const int64_t *perm, const float4 *frame, int64_t n, float4 *chg) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
+// ------------------------------------------------ charges + own element
+// Element i (sorted order): its DD vector in the global frame for the
+// expansions and the near field, and its own-element term through the
+// cached FP64 3x3 block of the time window (caller order).
+__device__ __forceinline__ void prep_elem(int64_t i, const double *x, const int64_t *perm, const float4 *frame,
+                                          const double *blk, int64_t n, double scale, int overwrite, float4 *chg,
+                                          double *y) {
     int64_t e = perm[i];
     float4 f = frame[i];
-    float Ds = (float)x[e], Dn = (float)x[n + e], Dq = (float)x[2 * n + e];
+    double a = x[e], b = x[n + e], c = x[2 * n + e];
+    float Ds = (float)a, Dn = (float)b;
     // D = Ds t + Dn n, n = (-ty, tx)
-    chg[i] = make_float4(Ds * f.x - Dn * f.y, Ds * f.y + Dn * f.x, Dq, 0.f);
-}
-
-// --------------------------------------------------------- own element (FP64)
-__global__ void k_self(KConst<double> k, Win<double> w, const double *x, const double *xy, int64_t n, double scale,
-                       int overwrite, double *y) {
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= n) return;
-    double dx = xy[2 * n + e] - xy[e], dy = xy[3 * n + e] - xy[n + e];
-    double L = hypot(dx, dy);
-    double o[3];
-    self_field(k, w, 0.5 * L, dx / L, dy / L, x[e], x[n + e], x[2 * n + e], o);
+    chg[i] = make_float4(Ds * f.x - Dn * f.y, Ds * f.y + Dn * f.x, (float)c, 0.f);
+    const double *B = blk + 9 * e;
+#pragma unroll
     for (int r = 0; r < 3; ++r) {
-        double v = scale * o[r];
+        double v = scale * (B[3 * r] * a + B[3 * r + 1] * b + B[3 * r + 2] * c);
         if (overwrite) y[r * n + e] = v; else y[r * n + e] += v;
     }
 }
 
+__global__ void k_prep(const double *x, const int64_t *perm, const float4 *frame, const double *blk, int64_t n,
+                       double scale, int overwrite, float4 *chg, double *y) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) prep_elem(i, x, perm, frame, blk, n, scale, overwrite, chg, y);
+}
+
+// --------------------------------------------------------- own element (FP64)
 // own 3x3 blocks (rows sigma_s, sigma_n, p; columns Ds, Dn, Dq), caller order
 __global__ void k_self_blocks(KConst<double> k, Win<double> w, const double *xy, int64_t n, double *blk) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -113,191 +128,239 @@ __global__ void k_self_blocks(KConst<double> k, Win<double> w, const double *xy,
     }
 }
 
-// own element through cached 3x3 blocks (caller order)
-__global__ void k_self_apply(const double *blk, const double *x, int64_t n, double scale, int overwrite, double *y) {
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= n) return;
-    const double *B = blk + 9 * e;
-    double a = x[e], b = x[n + e], c = x[2 * n + e];
-    for (int r = 0; r < 3; ++r) {
-        double v = scale * (B[3 * r] * a + B[3 * r + 1] * b + B[3 * r + 2] * c);
-        if (overwrite) y[r * n + e] = v; else y[r * n + e] += v;
+// ------------------------------------------------------- upward pass (fused)
+// Chebyshev cardinal functions of one point into a strided shared-memory
+// column (the approximate divide is well inside the expansion error).
+template <int N>
+__device__ __forceinline__ void cardinal_col(float x, float *col, int stride) {
+    float v[N], s = 0.f;
+    int hit = -1;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        float d = x - c_gl.cheb[j];
+        if (fabsf(d) < 1e-7f) hit = j;
+        v[j] = __fdividef(c_gl.bw[j], d);
+        s += v[j];
     }
+    float is = __fdividef(1.f, s);
+#pragma unroll
+    for (int j = 0; j < N; ++j) col[j * stride] = hit >= 0 ? (j == hit ? 1.f : 0.f) : v[j] * is;
 }
 
-// ---------------------------------------------------------------------- P2M
-constexpr int P2M_T = 128;
-__global__ void __launch_bounds__(P2M_T) k_p2m(const int32_t *cstart, const int32_t *cend, int64_t loff,
-                                               const float4 *grel, const float4 *frame, const float4 *chg,
-                                               float hL, int n, float *W) {
-    __shared__ float sx[P2M_T][DDM_MAX_CHEB], sy[P2M_T][DDM_MAX_CHEB], wd[P2M_T][4];
-    int64_t cell = loff + blockIdx.x;
-    int s0 = cstart[cell], s1 = cend[cell];
-    int nq = c_gl.nc, n2 = n * n;
-    int npts = (s1 - s0) * nq;
-    float acc[8];
-    for (int k = 0; k < 8; ++k) acc[k] = 0.f;
-    float ih = 1.f / hL;
-    for (int base = 0; base < npts; base += P2M_T) {
-        int p = base + threadIdx.x;
+constexpr int UP_T = 128;
+// shared-memory floats of the fused passes: the P2M staging (cardinals of
+// 128 points in x and y, 128 point weights) and the M2M staging (weights of
+// up to 4 children and their half-transferred copies) share one buffer
+template <int N>
+struct UpSmem {
+    static constexpr int N2 = N * N, NOUT = 4 * N2, SXS = UP_T + 1;
+    static constexpr int P2M = 2 * N * SXS + 4 * UP_T;
+    static constexpr int M2M = 8 * NOUT;
+    static constexpr int SIZE = P2M > M2M ? P2M : M2M;
+};
+
+// One block per leaf: charges and own-element terms of the leaf's elements,
+// P2M of the leaf (paper Sec. 3.3: W_m = sum_j int S_n(ybar_m, y) b_j ds,
+// Gauss rule with n points per element, exact for the polynomial
+// cardinals), then M2M towards level 2.  The block that completes the
+// last child of a parent (counted with a device-scope atomic after a
+// fence) computes the parent's weights from all its children in a fixed
+// order, so the whole upward pass is one launch, needs no zeroed buffer
+// and sums in the same order every time.  Nothing waits: the other blocks
+// simply finish.  The last block resets the parent's counter for the next
+// pass.
+//
+// P2M: lane owns node entries (a, b) = lane + 32 j and all 4 components;
+// the 4 warps take every 4th point and are summed at the end.
+template <int N>
+__global__ void __launch_bounds__(UP_T) k_up(const int32_t *cstart, const int32_t *cend, int64_t loff, int64_t off3,
+                                             const int32_t *cix, const int32_t *ciy, const int32_t *parent,
+                                             const int32_t *child0, const int32_t *nchild, int32_t *cnt,
+                                             const float *T, const double *x, const int64_t *perm,
+                                             const float4 *grel, const float4 *frame, const double *blk,
+                                             int64_t n_elem, double scale, int overwrite, double *y, float4 *chg,
+                                             float hL, float *W) {
+    using S = UpSmem<N>;
+    constexpr int N2 = S::N2, NOUT = S::NOUT, SXS = S::SXS, NE = (N2 + 31) / 32, KO = (NOUT + UP_T - 1) / UP_T;
+    __shared__ __align__(16) float sm[S::SIZE];
+    __shared__ float sT[2 * N2];
+    __shared__ int s_last, s_q[4];
+    float *sx = sm, *sy = sm + N * SXS;
+    float4 *wd = reinterpret_cast<float4 *>(sm + 2 * N * SXS);   // 16-byte aligned: 2 N SXS is a multiple of 4
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t leaf = loff + blockIdx.x;
+    const int s0 = cstart[leaf], s1 = cend[leaf];
+    for (int i = s0 + tid; i < s1; i += UP_T) prep_elem(i, x, perm, frame, blk, n_elem, scale, overwrite, chg, y);
+    for (int i = tid; i < 2 * N2; i += UP_T) sT[i] = T[i];
+    const int nq = c_gl.nc;
+    float acc[NE][4];
+#pragma unroll
+    for (int j = 0; j < NE; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    const float ih = 1.f / hL;
+    const int npts = (s1 - s0) * nq;
+    __syncthreads();                          // charges of the leaf written
+    for (int base = 0; base < npts; base += UP_T) {
+        int p = base + tid;
         if (p < npts) {
             int e = s0 + p / nq, g = p % nq;
             float4 r = grel[e], f = frame[e], c = chg[e];
             float xi = c_gl.xc[g];
             float px = 0.5f * (r.x + r.z) + xi * f.z * f.x, py = 0.5f * (r.y + r.w) + xi * f.z * f.y;
-            cardinal<DDM_MAX_CHEB>(px * ih, n, sx[threadIdx.x]);
-            cardinal<DDM_MAX_CHEB>(py * ih, n, sy[threadIdx.x]);
-            float wt = c_gl.wc[g] * f.z;           // ds = a dxi
+            cardinal_col<N>(px * ih, sx + tid, SXS);
+            cardinal_col<N>(py * ih, sy + tid, SXS);
+            float wt = c_gl.wc[g] * f.z;      // ds = a dxi
             float nx = -f.y, ny = f.x;
-            wd[threadIdx.x][0] = wt * c.x * nx;
-            wd[threadIdx.x][1] = wt * c.y * ny;
-            wd[threadIdx.x][2] = wt * 0.5f * (c.x * ny + c.y * nx);
-            wd[threadIdx.x][3] = wt * c.z;
+            wd[tid] = make_float4(wt * c.x * nx, wt * c.y * ny, wt * 0.5f * (c.x * ny + c.y * nx), wt * c.z);
         }
         __syncthreads();
-        int cnt = min(P2M_T, npts - base);
-        for (int ent = threadIdx.x, slot = 0; ent < n2 && slot < 2; ent += P2M_T, ++slot) {
-            int a = ent / n, b = ent % n;
-            float s0_ = 0, s1_ = 0, s2_ = 0, s3_ = 0;
-            for (int q = 0; q < cnt; ++q) {
-                float v = sx[q][a] * sy[q][b];
-                s0_ += v * wd[q][0]; s1_ += v * wd[q][1]; s2_ += v * wd[q][2]; s3_ += v * wd[q][3];
+        int np = min(UP_T, npts - base);
+        for (int q = warp; q < np; q += 4) {
+            float4 w4 = wd[q];
+#pragma unroll
+            for (int j = 0; j < NE; ++j) {
+                int ent = lane + 32 * j;
+                if (ent < N2) {
+                    float v = sx[(ent / N) * SXS + q] * sy[(ent % N) * SXS + q];
+                    acc[j][0] = fmaf(v, w4.x, acc[j][0]);
+                    acc[j][1] = fmaf(v, w4.y, acc[j][1]);
+                    acc[j][2] = fmaf(v, w4.z, acc[j][2]);
+                    acc[j][3] = fmaf(v, w4.w, acc[j][3]);
+                }
             }
-            acc[4 * slot] += s0_; acc[4 * slot + 1] += s1_; acc[4 * slot + 2] += s2_; acc[4 * slot + 3] += s3_;
         }
         __syncthreads();
     }
-    float *Wc = W + cell * 4 * n2;
-    for (int ent = threadIdx.x, slot = 0; ent < n2 && slot < 2; ent += P2M_T, ++slot)
-        for (int c = 0; c < 4; ++c) Wc[c * n2 + ent] = acc[4 * slot + c];
+    // sum the 4 warps' partial weights (staging reused)
+    float *red = sm;
+#pragma unroll
+    for (int j = 0; j < NE; ++j) {
+        int ent = lane + 32 * j;
+        if (ent < N2)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) red[warp * NOUT + c * N2 + ent] = acc[j][c];
+    }
+    __syncthreads();
+    float *Wc = W + leaf * NOUT;
+#pragma unroll
+    for (int k = 0; k < KO; ++k) {
+        int o = tid + k * UP_T;
+        if (o < NOUT) Wc[o] = red[o] + red[NOUT + o] + red[2 * NOUT + o] + red[3 * NOUT + o];
+    }
+    float *sw = sm, *tmp = sm + 4 * NOUT;
+    int64_t cur = leaf;
+    while (cur >= off3) {                     // cur at level >= 3: its parent needs weights
+        __threadfence();                      // this thread's weights visible device-wide
+        __syncthreads();
+        if (tid == 0) {
+            int p = parent[cur];
+            int last = atomicAdd(&cnt[p], 1) == nchild[p] - 1;
+            if (last) cnt[p] = 0;
+            s_last = last;
+        }
+        __syncthreads();
+        if (!s_last) return;
+        __threadfence();
+        const int p = parent[cur], c0 = child0[p], nc = nchild[p];
+        // the children's weights are contiguous; written by other blocks: via L2
+        const float *Wch = W + (int64_t)c0 * NOUT;
+        for (int i = tid; i < nc * NOUT; i += UP_T) sw[i] = __ldcg(Wch + i);
+        if (tid < nc) s_q[tid] = ((cix[c0 + tid] & 1) ? 1 : 0) | ((ciy[c0 + tid] & 1) ? 2 : 0);
+        __syncthreads();
+        // tmp[ch][c][a][b'] = sum_a' Tx[a][a'] W^ch[c][a'][b']
+        for (int i = tid; i < nc * NOUT; i += UP_T) {
+            int ch = i / NOUT, r = i % NOUT, c = r / N2, a = (r / N) % N, b = r % N;
+            const float *Tx = sT + ((s_q[ch] & 1) ? N2 : 0) + a * N;
+            const float *src = sw + ch * NOUT + c * N2 + b;
+            float s = 0.f;
+#pragma unroll
+            for (int k = 0; k < N; ++k) s = fmaf(Tx[k], src[k * N], s);
+            tmp[i] = s;
+        }
+        __syncthreads();
+        // W^p[c][a][b] = sum_ch sum_b' Ty[b][b'] tmp[ch][c][a][b']
+        float *Wp = W + (int64_t)p * NOUT;
+#pragma unroll
+        for (int k = 0; k < KO; ++k) {
+            int o = tid + k * UP_T;
+            if (o < NOUT) {
+                int c = o / N2, a = (o / N) % N, b = o % N;
+                float s = 0.f;
+                for (int ch = 0; ch < nc; ++ch) {
+                    const float *Ty = sT + ((s_q[ch] & 2) ? N2 : 0) + b * N;
+                    const float *tc = tmp + ch * NOUT + c * N2 + a * N;
+#pragma unroll
+                    for (int j = 0; j < N; ++j) s = fmaf(Ty[j], tc[j], s);
+                }
+                Wp[o] = s;
+            }
+        }
+        cur = p;
+    }
 }
 
-// ---------------------------------------------------------------------- M2M
-// one block per child cell; adds S_n(ybar^parent, ybar^child) W^child to the parent
-__global__ void k_m2m(int64_t off, const int32_t *cix, const int32_t *ciy, const int32_t *parent,
-                      const float *T, int n, float *W) {
-    extern __shared__ float sm[];
-    float *wc = sm, *tmp = sm + 4 * n * n;
-    int64_t cell = off + blockIdx.x;
-    int n2 = n * n;
-    const float *Wc = W + cell * 4 * n2;
-    for (int i = threadIdx.x; i < 4 * n2; i += blockDim.x) wc[i] = Wc[i];
-    __syncthreads();
-    const float *Tx = T + ((cix[cell] & 1) ? n2 : 0), *Ty = T + ((ciy[cell] & 1) ? n2 : 0);
-    // tmp[c][a][b'] = sum_a' Tx[a][a'] wc[c][a'][b']
-    for (int i = threadIdx.x; i < 4 * n2; i += blockDim.x) {
-        int c = i / n2, a = (i / n) % n, b = i % n;
-        float s = 0;
-        for (int ap = 0; ap < n; ++ap) s += Tx[a * n + ap] * wc[c * n2 + ap * n + b];
-        tmp[i] = s;
+// ----------------------------------------------------- downward pass (fused)
+// One block per leaf: f = g at the level-2 ancestor, then down the chain
+// f <- S_n(xbar^child, xbar^parent) f + g^child (paper Sec. 3.3 L2L), and
+// the leaf's complete local expansion replaces its own M2L sum.  The
+// ancestors' values are only read, so leaves sharing them need no order.
+template <int N>
+__global__ void __launch_bounds__(UP_T) k_down(int64_t loff, int L, const int32_t *cix, const int32_t *ciy,
+                                               const int32_t *parent, const float *T, float *F) {
+    constexpr int N2 = N * N, NOUT = 4 * N2, KO = (NOUT + UP_T - 1) / UP_T;
+    __shared__ float sT[2 * N2], sf[NOUT], tmp[NOUT];
+    __shared__ int64_t anc[DDM_MAX_LEVELS + 1];
+    __shared__ int squad[DDM_MAX_LEVELS + 1];
+    const int tid = threadIdx.x;
+    const int64_t leaf = loff + blockIdx.x;
+    if (tid == 0) {
+        int64_t c = leaf;
+        for (int l = L; l >= 2; --l) {
+            anc[l] = c;
+            squad[l] = ((cix[c] & 1) ? 1 : 0) | ((ciy[c] & 1) ? 2 : 0);
+            c = parent[c];
+        }
     }
+    for (int i = tid; i < 2 * N2; i += UP_T) sT[i] = T[i];
     __syncthreads();
-    float *Wp = W + (int64_t)parent[cell] * 4 * n2;
-    for (int i = threadIdx.x; i < 4 * n2; i += blockDim.x) {
-        int c = i / n2, a = (i / n) % n, b = i % n;
-        float s = 0;
-        for (int bp = 0; bp < n; ++bp) s += Ty[b * n + bp] * tmp[c * n2 + a * n + bp];
-        atomicAdd(&Wp[i], s);
-    }
-}
-
-// ---------------------------------------------------------------------- L2L
-// one block per child cell: f^child += S_n(xbar^child in parent) f^parent
-__global__ void k_l2l(int64_t off, const int32_t *cix, const int32_t *ciy, const int32_t *parent,
-                      const float *T, int n, float *F) {
-    extern __shared__ float sm[];
-    float *fp = sm, *tmp = sm + 4 * n * n;
-    int64_t cell = off + blockIdx.x;
-    int n2 = n * n;
-    const float *Fp = F + (int64_t)parent[cell] * 4 * n2;
-    for (int i = threadIdx.x; i < 4 * n2; i += blockDim.x) fp[i] = Fp[i];
+    const float *F2 = F + anc[2] * NOUT;
+    for (int i = tid; i < NOUT; i += UP_T) sf[i] = F2[i];
     __syncthreads();
-    const float *Tx = T + ((cix[cell] & 1) ? n2 : 0), *Ty = T + ((ciy[cell] & 1) ? n2 : 0);
-    // child node a' takes sum_a T[a][a'] (transpose of M2M)
-    for (int i = threadIdx.x; i < 4 * n2; i += blockDim.x) {
-        int c = i / n2, ap = (i / n) % n, b = i % n;
-        float s = 0;
-        for (int a = 0; a < n; ++a) s += Tx[a * n + ap] * fp[c * n2 + a * n + b];
-        tmp[i] = s;
+    for (int l = 3; l <= L; ++l) {
+        const float *Fc = F + anc[l] * NOUT;
+        float g[KO];                          // this level's M2L sums, fetched early
+#pragma unroll
+        for (int k = 0; k < KO; ++k) g[k] = (tid + k * UP_T < NOUT) ? Fc[tid + k * UP_T] : 0.f;
+        const float *Tx = sT + ((squad[l] & 1) ? N2 : 0), *Ty = sT + ((squad[l] & 2) ? N2 : 0);
+        // tmp[c][a'][b] = sum_a Tx[a][a'] f[c][a][b]
+        for (int i = tid; i < NOUT; i += UP_T) {
+            int c = i / N2, a = (i / N) % N, b = i % N;
+            const float *src = sf + c * N2 + b;
+            float s = 0.f;
+#pragma unroll
+            for (int k = 0; k < N; ++k) s = fmaf(Tx[k * N + a], src[k * N], s);
+            tmp[i] = s;
+        }
+        __syncthreads();
+        // f[c][a'][b'] = sum_b Ty[b][b'] tmp[c][a'][b] + g
+#pragma unroll
+        for (int k = 0; k < KO; ++k) {
+            int o = tid + k * UP_T;
+            if (o < NOUT) {
+                int c = o / N2, a = (o / N) % N, b = o % N;
+                const float *tc = tmp + c * N2 + a * N;
+                float s = g[k];
+#pragma unroll
+                for (int j = 0; j < N; ++j) s = fmaf(Ty[j * N + b], tc[j], s);
+                sf[o] = s;
+            }
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    float *Fc = F + cell * 4 * n2;
-    for (int i = threadIdx.x; i < 4 * n2; i += blockDim.x) {
-        int c = i / n2, ap = (i / n) % n, bp = i % n;
-        float s = 0;
-        for (int b = 0; b < n; ++b) s += Ty[b * n + bp] * tmp[c * n2 + ap * n + b];
-        Fc[i] += s;
-    }
+    float *Fl = F + leaf * NOUT;
+    for (int i = tid; i < NOUT; i += UP_T) Fl[i] = sf[i];
 }
 
 // ---------------------------------------------------------------------- M2L
-// One block (4 warps) per target cell at levels >= 2; the warps take
-// interleaved entries of the interaction list, each lane owns NPL target
-// nodes and evaluates the kernel against all n^2 source nodes of the entry
-// (weights staged in shared memory); the four warps' sums are reduced in
-// shared memory at the end.
-struct LevelTab {
-    int64_t off[DDM_MAX_LEVELS + 2];
-    int L;
-};
-constexpr int M2L_W = 4;
-template <int NPL>
-__global__ void __launch_bounds__(32 * M2L_W) k_m2l(KConst<float> k, Win<float> w, LevelTab lt, int64_t first,
-                                                   const int32_t *iloff, const int32_t *ilidx, const int32_t *cix,
-                                                   const int32_t *ciy, double h0, int n, const float *W, float *F) {
-    extern __shared__ float sm[];            // M2L_W x 4 n^2 (weights, then partial sums)
-    int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int n2 = n * n;
-    float *sw = sm + wid * 4 * n2;
-    int64_t cell = first + blockIdx.x;
-    int lvl = 0;
-    while (lvl < lt.L && cell >= lt.off[lvl + 1]) ++lvl;
-    float h = (float)(h0 / (double)(1 << lvl)), wl = 2.f * h;
-    int ixI = cix[cell], iyI = ciy[cell];
-    float acc[NPL][4];
-    float tx[NPL], ty[NPL];
-#pragma unroll
-    for (int r = 0; r < NPL; ++r) {
-        int m = lane + 32 * r;
-        acc[r][0] = acc[r][1] = acc[r][2] = acc[r][3] = 0.f;
-        tx[r] = m < n2 ? h * c_gl.cheb[m / n] : 0.f;
-        ty[r] = m < n2 ? h * c_gl.cheb[m % n] : 0.f;
-    }
-    for (int q = iloff[cell] + wid; q < iloff[cell + 1]; q += M2L_W) {
-        int32_t J = ilidx[q];
-        const float *WJ = W + (int64_t)J * 4 * n2;
-        __syncwarp();
-        for (int i = lane; i < 4 * n2; i += 32) sw[i] = WJ[i];
-        __syncwarp();
-        float ox = wl * (float)(ixI - cix[J]), oy = wl * (float)(iyI - ciy[J]);
-        for (int ap = 0; ap < n; ++ap) {
-            float sx = ox - h * c_gl.cheb[ap];
-            for (int bp = 0; bp < n; ++bp) {
-                int mp = ap * n + bp;
-                float sy = oy - h * c_gl.cheb[bp];
-                float w0 = sw[mp], w1 = sw[n2 + mp], w2 = sw[2 * n2 + mp], w3 = sw[3 * n2 + mp];
-#pragma unroll
-                for (int r = 0; r < NPL; ++r)
-                    if (lane + 32 * r < n2) pot_kernel<float>(k, tx[r] + sx, ty[r] + sy, w0, w1, w2, w3, w, acc[r]);
-            }
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < NPL; ++r) {
-        int m = lane + 32 * r;
-        if (m < n2)
-            for (int c = 0; c < 4; ++c) sm[wid * 4 * n2 + c * n2 + m] = acc[r][c];
-    }
-    __syncthreads();
-    float *Fc = F + cell * 4 * n2;
-    for (int i = threadIdx.x; i < 4 * n2; i += 32 * M2L_W) {
-        float v = 0.f;
-        for (int ww = 0; ww < M2L_W; ++ww) v += sm[ww * 4 * n2 + i];
-        Fc[i] = v;
-    }
-}
-
 // Batched M2L (paper Sec. 3.3 M2L over interaction lists).  The kernel
 // between the Chebyshev nodes of two cells depends only on the level, the
 // cell offset and the time window, so one (4n^2 x 4n^2) operator per
@@ -750,30 +813,32 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
     KConst<float> kf = ctx->kf;
     Win<float> wf = make_win<float>(ctx, lo, hi);
     Win<double> wd = make_win<double>(ctx, lo, hi);
-    prof_begin(ctx, 0);
-    k_charges<<<(N + TB - 1) / TB, TB, 0, s>>>(x, t->perm, t->g_frame, N, t->chg);
-    prof_end(ctx, 0, 1);
-    // own elements (FP64 closed form), caller order
-    prof_begin(ctx, 1);
-    {
-        // own-element blocks of this time window, computed once and cached
-        int slot = -1;
-        for (int k = 0; k < 4; ++k)
-            if (t->win_blk[k] && t->win_lo[k] == lo && t->win_hi[k] == hi) slot = k;
-        if (slot < 0) {
-            slot = t->win_next;
-            t->win_next = (t->win_next + 1) % 4;
-            if (!t->win_blk[slot]) DDM_CUDA_TRY(ctx, dalloc(&t->win_blk[slot], 9 * N * sizeof(double), t->stream));
-            k_self_blocks<<<(N + TB - 1) / TB, TB, 0, s>>>(ctx->kd, wd, t->xy_caller, N, t->win_blk[slot]);
-            t->win_lo[slot] = lo;
-            t->win_hi[slot] = hi;
-        }
-        k_self_apply<<<(N + TB - 1) / TB, TB, 0, s>>>(t->win_blk[slot], x, N, scale, accumulate ? 0 : 1, y);
+    // own-element blocks of this time window (FP64 closed form), computed
+    // once per window and cached
+    int slot = -1;
+    for (int k = 0; k < 4; ++k)
+        if (t->win_blk[k] && t->win_lo[k] == lo && t->win_hi[k] == hi) slot = k;
+    if (slot < 0) {
+        prof_begin(ctx, 1);
+        slot = t->win_next;
+        t->win_next = (t->win_next + 1) % 4;
+        if (!t->win_blk[slot]) DDM_CUDA_TRY(ctx, dalloc(&t->win_blk[slot], 9 * N * sizeof(double), t->stream));
+        k_self_blocks<<<(N + TB - 1) / TB, TB, 0, s>>>(ctx->kd, wd, t->xy_caller, N, t->win_blk[slot]);
+        t->win_lo[slot] = lo;
+        t->win_hi[slot] = hi;
+        prof_end(ctx, 1, 1);
     }
-    prof_end(ctx, 1, 1);
+    const double *blk = t->win_blk[slot];
+    const int overwrite = accumulate ? 0 : 1;
     int L = t->depth;
     int64_t loff = t->lvl_off[L], nleaf = t->lvl_off[L + 1] - loff;
     float wL = (float)(2.0 * t->h0 / (double)(1 << L));
+    int use_far = mode != DDM_MODE_DENSE && L >= 2;
+    if (!use_far) {
+        prof_begin(ctx, 0);
+        k_prep<<<(N + TB - 1) / TB, TB, 0, s>>>(x, t->perm, t->g_frame, blk, N, scale, overwrite, t->chg, y);
+        prof_end(ctx, 0, 1);
+    }
     if (mode == DDM_MODE_DENSE) {
         int64_t tiles = (N + DN_T - 1) / DN_T;
         int64_t chunks = std::max<int64_t>(1, std::min<int64_t>((4 * 152 + tiles - 1) / tiles, (N + DN_T - 1) / DN_T));
@@ -788,60 +853,53 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
         DDM_CUDA_TRY(ctx, cudaGetLastError());
         return DDM_OK;
     }
-    int use_far = L >= 2;
     if (use_far) {
+        // upward pass: charges, own elements, P2M and M2M in one launch
         float hL = 0.5f * wL;
-        // upward pass
-        DDM_CUDA_TRY(ctx, cudaMemsetAsync(t->W, 0, (size_t)t->n_cells * 4 * n2 * sizeof(float), s));
+        int64_t off3 = L >= 3 ? t->lvl_off[3] : t->n_cells;
         prof_begin(ctx, 2);
-        k_p2m<<<(unsigned)nleaf, P2M_T, 0, s>>>(t->cell_start, t->cell_end, loff, t->g_rel, t->g_frame, t->chg, hL, n,
-                                                t->W);
+#define DDM_UP(NN)                                                                                          \
+    k_up<NN><<<(unsigned)nleaf, UP_T, 0, s>>>(t->cell_start, t->cell_end, loff, off3, t->cell_ix, t->cell_iy,       \
+                                              t->cell_parent, t->cell_child0, t->cell_nchild, t->up_cnt,          \
+                                              ctx->cheb_T, x, t->perm, t->g_rel, t->g_frame, blk, N, scale,       \
+                                              overwrite, y, t->chg, hL, t->W)
+        DDM_CHEB_SWITCH(n, DDM_UP);
+#undef DDM_UP
         prof_end(ctx, 2, 1);
-        size_t sm2 = 8 * n2 * sizeof(float);
-        prof_begin(ctx, 3);
-        for (int l = L; l >= 3; --l) {
-            int64_t off = t->lvl_off[l], nc = t->lvl_off[l + 1] - off;
-            k_m2m<<<(unsigned)nc, 128, sm2, s>>>(off, t->cell_ix, t->cell_iy, t->cell_parent, ctx->cheb_T, n, t->W);
+        // M2L on every level >= 2: operators of this window, then one GEMM launch
+        int nk = t->n_keys;
+        size_t opsz = (size_t)nk * 16 * n2 * n2;
+        if (t->ops_n != n || !t->m2l_ops) {
+            dfree(t->m2l_ops, t->stream);
+            t->m2l_ops = nullptr;
+            DDM_CUDA_TRY(ctx, dalloc(&t->m2l_ops, opsz * sizeof(float), t->stream));
+            t->ops_n = n;
+            t->ops_lo = t->ops_hi = -1.0;
         }
-        prof_end(ctx, 3, L - 2);
-        // M2L on every level >= 2 in one launch
-        LevelTab lt;
-        for (int l = 0; l <= L + 1 && l < DDM_MAX_LEVELS + 2; ++l) lt.off[l] = t->lvl_off[l];
-        lt.L = L;
-        int64_t first = t->lvl_off[2], ncm = t->lvl_off[L + 1] - first;
+        if (t->ops_lo != lo || t->ops_hi != hi) {
+            prof_begin(ctx, 3);
+            dim3 g((unsigned)((n2 * n2 + 127) / 128), (unsigned)nk);
+            k_m2l_ops<<<g, 128, 0, s>>>(kf, wf, L, t->h0, n, t->mk_off, t->m2l_ops);
+            t->ops_lo = lo;
+            t->ops_hi = hi;
+            prof_end(ctx, 3, 1);
+        }
         prof_begin(ctx, 4);
-        {
-            int nk = t->n_keys;
-            size_t opsz = (size_t)nk * 16 * n2 * n2;
-            if (t->ops_n != n || !t->m2l_ops) {
-                dfree(t->m2l_ops, t->stream);
-                t->m2l_ops = nullptr;
-                DDM_CUDA_TRY(ctx, dalloc(&t->m2l_ops, opsz * sizeof(float), t->stream));
-                t->ops_n = n;
-                t->ops_lo = t->ops_hi = -1.0;
-            }
-            if (t->ops_lo != lo || t->ops_hi != hi) {
-                dim3 g((unsigned)((n2 * n2 + 127) / 128), (unsigned)nk);
-                k_m2l_ops<<<g, 128, 0, s>>>(kf, wf, L, t->h0, n, t->mk_off, t->m2l_ops);
-                t->ops_lo = lo;
-                t->ops_hi = hi;
-                prof_end(ctx, 4, 1);
-                prof_begin(ctx, 4);
-            }
-            DDM_CUDA_TRY(ctx, cudaMemsetAsync(t->Fl, 0, (size_t)t->n_cells * 4 * n2 * sizeof(float), s));
-            if (t->n_work > 0) {
-                dim3 g((unsigned)t->n_work, (unsigned)((4 * n2 + GM_BM - 1) / GM_BM));
-                k_m2l_gemm<<<g, 256, 0, s>>>(t->mk_work, t->mk_off, t->mk_pair, n, t->m2l_ops, t->W, t->Fl);
-            }
+        DDM_CUDA_TRY(ctx, cudaMemsetAsync(t->Fl, 0, (size_t)t->n_cells * 4 * n2 * sizeof(float), s));
+        if (t->n_work > 0) {
+            dim3 g((unsigned)t->n_work, (unsigned)((4 * n2 + GM_BM - 1) / GM_BM));
+            k_m2l_gemm<<<g, 256, 0, s>>>(t->mk_work, t->mk_off, t->mk_pair, n, t->m2l_ops, t->W, t->Fl);
         }
-        prof_end(ctx, 4, 1);
-        // downward pass
-        prof_begin(ctx, 5);
-        for (int l = 3; l <= L; ++l) {
-            int64_t off = t->lvl_off[l], nc = t->lvl_off[l + 1] - off;
-            k_l2l<<<(unsigned)nc, 128, sm2, s>>>(off, t->cell_ix, t->cell_iy, t->cell_parent, ctx->cheb_T, n, t->Fl);
+        prof_end(ctx, 4, 2);
+        // downward pass: L2L chains to the leaves in one launch
+        if (L >= 3) {
+            prof_begin(ctx, 5);
+#define DDM_DOWN(NN)                                                                                        \
+    k_down<NN><<<(unsigned)nleaf, UP_T, 0, s>>>(loff, L, t->cell_ix, t->cell_iy, t->cell_parent, ctx->cheb_T, t->Fl)
+            DDM_CHEB_SWITCH(n, DDM_DOWN);
+#undef DDM_DOWN
+            prof_end(ctx, 5, 1);
         }
-        prof_end(ctx, 5, L - 2);
     }
     prof_begin(ctx, 6);
     auto knr = precise ? k_near<true> : k_near<false>;

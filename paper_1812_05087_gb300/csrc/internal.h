@@ -48,6 +48,9 @@ struct ddm_tree {
     int32_t *cell_ix, *cell_iy;// integer cell coordinates at the cell's level
     int32_t *cell_start, *cell_end;   // sorted element range
     int32_t *cell_parent;      // global cell index of the parent (-1 at level 0)
+    int32_t *cell_child0;      // global index of the first child (cells of one parent are contiguous)
+    int32_t *cell_nchild;      // number of non-empty children
+    int32_t *up_cnt;           // per cell: children done in the running upward pass (0 between passes)
     int32_t *il_off, *il_idx;  // interaction lists (CSR over cells)
     int32_t *nb_off, *nb_idx;  // neighbour lists of leaves incl. self (CSR over leaves, leaf-local)
     int32_t *elem_leaf;        // sorted element -> leaf index (leaf-local)
@@ -96,7 +99,8 @@ struct ddm_tree {
 struct GmresWork;
 
 // Optional stage timing (CUDA events on the context stream) and launch
-// counting.  Stages: 0 charges, 1 self, 2 p2m, 3 m2m, 4 m2l, 5 l2l, 6 leaf,
+// counting.  Stages: 0 prep (charges + own elements), 1 own-element blocks,
+// 2 up (fused with prep, P2M, M2M), 3 M2L operators, 4 m2l, 5 down, 6 leaf,
 // 7 dense, 8 krylov vector kernels, 9 tree build.
 #define DDM_NSTAGES 10
 struct Prof {

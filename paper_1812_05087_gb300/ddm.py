@@ -32,7 +32,7 @@ EXPORTS = ("ddm_create", "ddm_destroy", "ddm_last_error", "ddm_build_tree", "ddm
            "ddm_matvec_dense_static")
 STATIC_MAX_ELEMENTS = 65536
 NSTAGES = 10
-STAGES = ("charges", "self", "p2m", "m2m", "m2l", "l2l", "leaf", "dense", "krylov", "tree")
+STAGES = ("prep", "self_blocks", "up", "m2l_ops", "m2l", "down", "leaf", "dense", "krylov", "tree")
 
 
 class ddm_material(ctypes.Structure):
