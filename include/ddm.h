@@ -91,6 +91,13 @@ ddm_status ddm_create(ddm_ctx **out, const ddm_material *mat, const ddm_fmm_para
 void ddm_destroy(ddm_ctx *ctx);
 const char *ddm_last_error(const ddm_ctx *ctx);
 
+/* Kernels that wait on the GPU (tensor-core pipelines) give up after a
+ * bounded number of polls and raise a device word on the context instead of
+ * hanging.  ddm_device_check synchronises the context stream, returns
+ * DDM_ETIMEOUT (and clears the word) if any such wait expired since the last
+ * check, else DDM_OK.  No counterpart in the paper. */
+ddm_status ddm_device_check(ddm_ctx *ctx);
+
 /* Build the quadtree of paper Sec. 3.1 over the element midpoints: level-0
  * square covering all midpoints, uniform depth (smallest depth whose leaves
  * hold <= leaf_size elements, capped so that no element is longer than a

@@ -208,6 +208,11 @@ ddm_status ddm_create(ddm_ctx **out, const ddm_material *mat, const ddm_fmm_para
                 T[q * n * n + a * n + ap] = (float)cheb_S(n, xi[a], 0.5 * (xi[ap] + (q ? 1.0 : -1.0)));
     if (cudaMalloc(&c->cheb_T, T.size() * sizeof(float)) != cudaSuccess) { delete c; return DDM_ENOMEM; }
     cudaMemcpy(c->cheb_T, T.data(), T.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess || cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess) {
+        cudaFree(c->cheb_T);
+        delete c;
+        return DDM_ENOMEM;
+    }
     c->gm = new GmresWork();
     *out = c;
     return DDM_OK;
@@ -216,11 +221,22 @@ ddm_status ddm_create(ddm_ctx **out, const ddm_material *mat, const ddm_fmm_para
 void ddm_destroy(ddm_ctx *ctx) {
     if (!ctx) return;
     if (ctx->cheb_T) cudaFree(ctx->cheb_T);
+    if (ctx->d_err) cudaFree(ctx->d_err);
     if (ctx->gm) { ctx->gm->release(); delete ctx->gm; }
     delete ctx;
 }
 
 const char *ddm_last_error(const ddm_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+ddm_status ddm_device_check(ddm_ctx *ctx) {
+    if (!ctx) return DDM_EINVAL;
+    int h = 0;
+    DDM_CUDA_TRY(ctx, cudaMemcpyAsync(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    DDM_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    if (!h) return DDM_OK;
+    DDM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+    return ctx_fail(ctx, DDM_ETIMEOUT, "a bounded device wait expired (results of the affected calls are invalid)");
+}
 
 ddm_status ddm_profile(ddm_ctx *ctx, int enable) {
     if (!ctx) return DDM_EINVAL;

@@ -388,88 +388,226 @@ __global__ void k_m2l_ops(KConst<float> k, Win<float> w, int L, double h0, int n
     }
 }
 
-// One work item = one (level, offset) group's column tile of up to 64
-// interaction pairs; blockIdx.y picks a 128-row slice of the 4n^2 operator
-// rows.  256 threads, 8 x 4 register tile each, BK = 16, double-buffered
-// shared memory; results are added to the targets' local expansions.
-constexpr int GM_BM = 128, GM_BN = 64, GM_BK = 16;
-__global__ void __launch_bounds__(256) k_m2l_gemm(const int2 *work, const int32_t *koff, const int2 *pairs, int n,
-                                                  const float *ops, const float *W, float *F) {
-    __shared__ __align__(16) float sK[2][GM_BK][GM_BM];
-    __shared__ __align__(16) float sB[2][GM_BK][GM_BN];
-    __shared__ int sI[GM_BN], sJ[GM_BN];
-    int2 wk = work[blockIdx.x];
-    int key = wk.x, p0 = wk.y, p1 = min(koff[key + 1], p0 + GM_BN);
-    int n2 = n * n, ld = 4 * n2;
-    int r0 = blockIdx.y * GM_BM;
+// ------------------------------------------------------ M2L on tcgen05 (TF32)
+// The same grouped product G = K_{l,o} [W_J1 ... W_JP] on the fifth-
+// generation tensor cores.  One CTA = one work item (column tile of up to
+// 64 interaction pairs of one (level, offset) group) x one 128-row slice of
+// the 4n^2 operator rows; the 128 x 64 FP32 accumulator lives in tensor
+// memory (64 columns).  Operands are split on the way into shared memory,
+// x = hi + lo with hi = x with the low 13 mantissa bits cleared (exact in
+// TF32) and lo = x - hi (exact in FP32), and each K step issues
+// hi*hi + hi*lo + lo*hi (the "3xTF32" product; the dropped lo*lo term is
+// ~2^-22 relative), so the result keeps FP32 accuracy.  The four 128-thread
+// warps stage K chunks of 32 (one 128-byte row of FP32 per matrix row) into
+// a 128-byte-swizzled K-major layout, two stages deep: while the tensor
+// core works on one stage, the threads fill the other.  One thread issues
+// the MMAs and commits them to the stage's mbarrier.  Every wait is bounded;
+// on expiry the CTA raises the context's error word, skips its output and
+// still releases its tensor memory.
+namespace tc {
+constexpr int BM = 128, BN = 64, BK = 32, THREADS = 128, NSTAGE = 2;
+constexpr int A_BYTES = BM * BK * 4, B_BYTES = BN * BK * 4;
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;     // hi and lo of both operands
+constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024;    // + room to align to 1024 B
+constexpr uint32_t TMEM_COLS = 64;
+constexpr int WAIT_POLLS = 1 << 20;
+// instruction descriptor (kind::tf32): D F32 (bits 4-5 = 1), A and B TF32
+// (bits 7-9, 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bit 17,
+// M >> 4 at bit 24
+constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start address >> 4 (bits 0-13), leading
+// byte offset (unused for swizzled K-major, 16 B), stride byte offset 1024 B
+// between 8-row groups (bits 32-45), descriptor version 1 (bit 46),
+// 128-byte swizzle (bits 61-63 = 2)
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// byte offset of 16-byte chunk c of row r in a 128-byte-swizzled tile
+__device__ __forceinline__ uint32_t sw128_off(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
+
+__device__ __forceinline__ void split4(float4 v, float4 &h, float4 &l) {
+    h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
+    h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
+    h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
+    h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
+    l = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait for the phase with this parity; on expiry set *err (every
+// thread keeps the same control flow, so barriers still match)
+__device__ __forceinline__ void mbar_wait(uint64_t *bar, uint32_t parity, volatile int *err) {
+    if (*err) return;
+    for (int i = 0; i < WAIT_POLLS; ++i)
+        if (mbar_try(bar, parity)) return;
+    *err = 1;
+}
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(IDESC), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// 32 TMEM lanes (one per thread of the warp) x 16 consecutive columns
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15])
+                 :
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+}  // namespace tc
+
+__global__ void __launch_bounds__(tc::THREADS) k_m2l_tc(const int2 *work, const int32_t *koff, const int2 *pairs,
+                                                        int n, const float *ops, const float *W, float *F,
+                                                        int *err) {
+    using namespace tc;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t bar[NSTAGE];
+    __shared__ uint32_t s_tmem;
+    __shared__ int sI[BN], sJ[BN];
+    __shared__ int s_err;
+    volatile int *verr = &s_err;
+    const uint32_t raw = smem_u32(smem_raw);
+    uint8_t *base = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int2 wk = work[blockIdx.x];
+    const int key = wk.x, p0 = wk.y, p1 = min(koff[key + 1], p0 + BN);
+    const int n2 = n * n, ld = 4 * n2;
+    const int r0 = blockIdx.y * BM;
     const float *K = ops + (int64_t)key * 16 * n2 * n2;
-    int tid = threadIdx.x;
-    if (tid < GM_BN) {
+    if (tid < BN) {
         int p = p0 + tid;
         sI[tid] = p < p1 ? pairs[p].x : -1;
         sJ[tid] = p < p1 ? pairs[p].y : -1;
     }
-    __syncthreads();
-    // loaders: K tile 128 x 16 -> each thread 8 consecutive k of one row;
-    // B tile 16 x 64 -> each thread 4 consecutive k of one column
-    int kr = tid >> 1, kk0 = (tid & 1) * 8;
-    int bj = tid >> 2, bk0 = (tid & 3) * 4;
-    int Jb = sJ[bj];
-    int tr = (tid >> 4) * 8, tc = (tid & 15) * 4;
-    float acc[8][4];
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-    int nsteps = ld / GM_BK;
-    for (int st = 0; st <= nsteps; ++st) {
-        int buf = st & 1;
-        if (st < nsteps) {       // stage step st into buffer buf
-            int k0 = st * GM_BK, row = r0 + kr;
-            if (row < ld) {
-                const float *src = K + (int64_t)row * ld + k0 + kk0;
-                float4 v0 = *(const float4 *)src, v1 = *(const float4 *)(src + 4);
-                sK[buf][kk0 + 0][kr] = v0.x; sK[buf][kk0 + 1][kr] = v0.y;
-                sK[buf][kk0 + 2][kr] = v0.z; sK[buf][kk0 + 3][kr] = v0.w;
-                sK[buf][kk0 + 4][kr] = v1.x; sK[buf][kk0 + 5][kr] = v1.y;
-                sK[buf][kk0 + 6][kr] = v1.z; sK[buf][kk0 + 7][kr] = v1.w;
-            } else {
-                for (int q = 0; q < 8; ++q) sK[buf][kk0 + q][kr] = 0.f;
-            }
-            if (Jb >= 0) {
-                float4 v = *(const float4 *)(W + (int64_t)Jb * ld + k0 + bk0);
-                sB[buf][bk0 + 0][bj] = v.x; sB[buf][bk0 + 1][bj] = v.y;
-                sB[buf][bk0 + 2][bj] = v.z; sB[buf][bk0 + 3][bj] = v.w;
-            } else {
-                for (int q = 0; q < 4; ++q) sB[buf][bk0 + q][bj] = 0.f;
-            }
-        }
-        if (st > 0) {            // compute step st - 1 from the other buffer
-            int cur = buf ^ 1;
-#pragma unroll
-            for (int kk = 0; kk < GM_BK; ++kk) {
-                float4 a0 = *(const float4 *)&sK[cur][kk][tr], a1 = *(const float4 *)&sK[cur][kk][tr + 4];
-                float4 b0 = *(const float4 *)&sB[cur][kk][tc];
-                float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-                float bb[4] = {b0.x, b0.y, b0.z, b0.w};
-#pragma unroll
-                for (int i = 0; i < 8; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], bb[j], acc[i][j]);
-            }
-        }
-        __syncthreads();
+    if (tid == 0) {
+        s_err = 0;
+        for (int s = 0; s < NSTAGE; ++s) mbar_init(&bar[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = s_tmem;
+    const int nkb = (ld + BK - 1) / BK;
+    for (int kb = 0; kb < nkb; ++kb) {
+        const int st = kb % NSTAGE;
+        uint8_t *a_hi = base + st * STAGE_BYTES, *a_lo = a_hi + A_BYTES, *b_hi = a_lo + A_BYTES,
+                *b_lo = b_hi + B_BYTES;
+        const int k0 = kb * BK;
+        float4 va[8], vb[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        int I = sI[tc + j];
-        if (I < 0) continue;
+        for (int i = 0; i < 8; ++i) {        // operator rows r0.., 8 float4 per 32-wide K chunk
+            int idx = tid + i * THREADS, row = idx >> 3, c = idx & 7, gr = r0 + row, gk = k0 + 4 * c;
+            va[i] = (gr < ld && gk < ld) ? __ldg(reinterpret_cast<const float4 *>(K + (int64_t)gr * ld + gk))
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {        // source weights, one column per pair
+            int idx = tid + i * THREADS, col = idx >> 3, c = idx & 7, J = sJ[col], gk = k0 + 4 * c;
+            vb[i] = (J >= 0 && gk < ld) ? __ldg(reinterpret_cast<const float4 *>(W + (int64_t)J * ld + gk))
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        // the MMAs that last read this stage (issued NSTAGE chunks ago) must be done
+        if (kb >= NSTAGE) mbar_wait(&bar[st], (uint32_t)((kb / NSTAGE - 1) & 1), verr);
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            int row = r0 + tr + i;
-            if (row < ld) atomicAdd(&F[(int64_t)I * ld + row], acc[i][j]);
+            int idx = tid + i * THREADS, row = idx >> 3, c = idx & 7;
+            float4 h, l;
+            split4(va[i], h, l);
+            uint32_t off = sw128_off(row, c);
+            *reinterpret_cast<float4 *>(a_hi + off) = h;
+            *reinterpret_cast<float4 *>(a_lo + off) = l;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            int idx = tid + i * THREADS, col = idx >> 3, c = idx & 7;
+            float4 h, l;
+            split4(vb[i], h, l);
+            uint32_t off = sw128_off(col, c);
+            *reinterpret_cast<float4 *>(b_hi + off) = h;
+            *reinterpret_cast<float4 *>(b_lo + off) = l;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // stores visible to the tensor core
+        __syncthreads();
+        if (tid == 0) {
+            fence_after_sync();
+            const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), bh = smem_u32(b_hi), bl = smem_u32(b_lo);
+#pragma unroll
+            for (int kk = 0; kk < BK / 8; ++kk) {   // K = 8 per MMA: 32 bytes along the swizzled row
+                const uint32_t o = 32u * kk;
+                mma_tf32(tmem, sw128_desc(al + o), sw128_desc(bh + o), (kb | kk) != 0);
+                mma_tf32(tmem, sw128_desc(ah + o), sw128_desc(bl + o), 1u);
+                mma_tf32(tmem, sw128_desc(ah + o), sw128_desc(bh + o), 1u);
+            }
+            mma_commit(&bar[st]);
         }
     }
+    // all MMAs done (the last commit covers every earlier one of the thread)
+    mbar_wait(&bar[(nkb - 1) % NSTAGE], (uint32_t)(((nkb - 1) / NSTAGE) & 1), verr);
+    fence_after_sync();
+    const int row = r0 + warp * 32 + lane;
+    const bool ok = *verr == 0;
+#pragma unroll
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        if (ok && row < ld) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                int I = sI[c0 + j];
+                if (I >= 0) atomicAdd(&F[(int64_t)I * ld + row], v[j]);
+            }
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    if (tid == 0 && !ok) atomicExch(err, 1);
 }
 
 // ----------------------------------------------------------- leaf L2P + P2P
@@ -887,8 +1025,15 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
         prof_begin(ctx, 4);
         DDM_CUDA_TRY(ctx, cudaMemsetAsync(t->Fl, 0, (size_t)t->n_cells * 4 * n2 * sizeof(float), s));
         if (t->n_work > 0) {
-            dim3 g((unsigned)t->n_work, (unsigned)((4 * n2 + GM_BM - 1) / GM_BM));
-            k_m2l_gemm<<<g, 256, 0, s>>>(t->mk_work, t->mk_off, t->mk_pair, n, t->m2l_ops, t->W, t->Fl);
+            static bool attr[64] = {false};
+            if (!attr[ctx->device & 63]) {
+                DDM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       tc::SMEM_BYTES));
+                attr[ctx->device & 63] = true;
+            }
+            dim3 g((unsigned)t->n_work, (unsigned)((4 * n2 + tc::BM - 1) / tc::BM));
+            k_m2l_tc<<<g, tc::THREADS, tc::SMEM_BYTES, s>>>(t->mk_work, t->mk_off, t->mk_pair, n, t->m2l_ops, t->W,
+                                                            t->Fl, ctx->d_err);
         }
         prof_end(ctx, 4, 2);
         // downward pass: L2L chains to the leaves in one launch

@@ -125,6 +125,7 @@ struct ddm_ctx {
     float *cheb_T;             // 2 x n x n
     GmresWork *gm;
     Prof prof;
+    int *d_err;                // device word raised by a kernel whose bounded wait expired
 };
 
 // begin/end a profiled stage (no-ops unless profiling is on); count launches

@@ -25,7 +25,7 @@ SYS_PRESSURE, SYS_IMPERMEABLE, SYS_RATE = 0, 1, 2
 _MODES = {"fmm": MODE_FMM, "dense": MODE_DENSE, "fmm+precise": MODE_FMM | MODE_PRECISE,
           "dense+precise": MODE_DENSE | MODE_PRECISE}
 _SYSTEMS = {"pressure": SYS_PRESSURE, "impermeable": SYS_IMPERMEABLE, "rate": SYS_RATE}
-EXPORTS = ("ddm_create", "ddm_destroy", "ddm_last_error", "ddm_build_tree", "ddm_tree_destroy",
+EXPORTS = ("ddm_create", "ddm_destroy", "ddm_last_error", "ddm_device_check", "ddm_build_tree", "ddm_tree_destroy",
            "ddm_tree_get_info", "ddm_matvec", "ddm_history_apply", "ddm_rhs", "ddm_gmres_solve", "ddm_sif",
            "ddm_profile", "ddm_profile_read", "ddm_batch_create", "ddm_batch_destroy", "ddm_batch_matvec",
            "ddm_batch_gmres_solve", "ddm_server_create", "ddm_submit", "ddm_poll", "ddm_server_destroy",
@@ -236,6 +236,12 @@ def ddm_profile(ctx, enable=True):
     _check(ctx, load().ddm_profile(ctx, int(bool(enable))), "ddm_profile")
 
 
+def ddm_device_check(ctx):
+    """Synchronise the context stream; raise DDMError (DDM_ETIMEOUT) if a
+    bounded device wait expired since the last check."""
+    _check(ctx, load().ddm_device_check(ctx), "ddm_device_check")
+
+
 def ddm_profile_read(ctx) -> dict:
     ms = (ctypes.c_double * NSTAGES)()
     n = (ctypes.c_int64 * NSTAGES)()
@@ -443,6 +449,9 @@ class Context:
 
     def profile_read(self) -> dict:
         return ddm_profile_read(self.ptr)
+
+    def device_check(self):
+        ddm_device_check(self.ptr)
 
     def close(self):
         if self.ptr:
