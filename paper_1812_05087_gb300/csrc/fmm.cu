@@ -27,12 +27,12 @@
 namespace {
 
 constexpr int MAXGL = 16;
+// Quadrature and Chebyshev tables for every supported order, uploaded once
+// per device: contexts with different orders can run side by side.
 struct GLTab {
-    float xn[MAXGL], wn[MAXGL];   // near rule (fluid source), quad_near points
-    float xf[3], wf[3];           // far rule, 3 points
-    float xc[MAXGL], wc[MAXGL];   // P2M rule, n_cheb points
-    float cheb[DDM_MAX_CHEB], bw[DDM_MAX_CHEB];
-    int nn, nc;
+    float xn[MAXGL + 1][MAXGL], wn[MAXGL + 1][MAXGL];   // near rule (fluid source), [points][i]
+    float xc[DDM_MAX_CHEB / 2][DDM_MAX_CHEB], wc[DDM_MAX_CHEB / 2][DDM_MAX_CHEB];   // P2M rule, n points, [n/2-1]
+    float cheb[DDM_MAX_CHEB / 2][DDM_MAX_CHEB], bw[DDM_MAX_CHEB / 2][DDM_MAX_CHEB]; // roots of T_n, barycentric weights
 };
 __constant__ GLTab c_gl;
 
@@ -64,27 +64,6 @@ void gauss_legendre(int n, double *x, double *w) {
         x[i] = z;
         w[i] = 2 / ((1 - z * z) * dp * dp);
     }
-}
-
-// Chebyshev cardinal functions S_n(xi_a, x) = l_a(x) at the roots of T_n,
-// barycentric form (stable also slightly outside [-1, 1]).
-template <int NMAX>
-__device__ __forceinline__ void cardinal(float x, int n, float *out) {
-    float s = 0.f;
-    int hit = -1;
-    for (int j = 0; j < n; ++j) {
-        float d = x - c_gl.cheb[j];
-        if (fabsf(d) < 1e-7f) hit = j;
-        float v = c_gl.bw[j] / d;
-        out[j] = v;
-        s += v;
-    }
-    if (hit >= 0) {
-        for (int j = 0; j < n; ++j) out[j] = (j == hit) ? 1.f : 0.f;
-        return;
-    }
-    float is = 1.f / s;
-    for (int j = 0; j < n; ++j) out[j] *= is;
 }
 
 // ------------------------------------------------ charges + own element
@@ -137,9 +116,9 @@ __device__ __forceinline__ void cardinal_col(float x, float *col, int stride) {
     int hit = -1;
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-        float d = x - c_gl.cheb[j];
+        float d = x - c_gl.cheb[N / 2 - 1][j];
         if (fabsf(d) < 1e-7f) hit = j;
-        v[j] = __fdividef(c_gl.bw[j], d);
+        v[j] = __fdividef(c_gl.bw[N / 2 - 1][j], d);
         s += v[j];
     }
     float is = __fdividef(1.f, s);
@@ -192,7 +171,7 @@ __global__ void __launch_bounds__(UP_T) k_up(const int32_t *cstart, const int32_
     const int s0 = cstart[leaf], s1 = cend[leaf];
     for (int i = s0 + tid; i < s1; i += UP_T) prep_elem(i, x, perm, frame, blk, n_elem, scale, overwrite, chg, y);
     for (int i = tid; i < 2 * N2; i += UP_T) sT[i] = T[i];
-    const int nq = c_gl.nc;
+    constexpr int nq = N;                     // Gauss points per element
     float acc[NE][4];
 #pragma unroll
     for (int j = 0; j < NE; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
@@ -204,11 +183,11 @@ __global__ void __launch_bounds__(UP_T) k_up(const int32_t *cstart, const int32_
         if (p < npts) {
             int e = s0 + p / nq, g = p % nq;
             float4 r = grel[e], f = frame[e], c = chg[e];
-            float xi = c_gl.xc[g];
+            float xi = c_gl.xc[N / 2 - 1][g];
             float px = 0.5f * (r.x + r.z) + xi * f.z * f.x, py = 0.5f * (r.y + r.w) + xi * f.z * f.y;
             cardinal_col<N>(px * ih, sx + tid, SXS);
             cardinal_col<N>(py * ih, sy + tid, SXS);
-            float wt = c_gl.wc[g] * f.z;      // ds = a dxi
+            float wt = c_gl.wc[N / 2 - 1][g] * f.z;   // ds = a dxi
             float nx = -f.y, ny = f.x;
             wd[tid] = make_float4(wt * c.x * nx, wt * c.y * ny, wt * 0.5f * (c.x * ny + c.y * nx), wt * c.z);
         }
@@ -377,8 +356,9 @@ __global__ void k_m2l_ops(KConst<float> k, Win<float> w, int L, double h0, int n
     if (np >= n2 * n2) return;
     int m = np / n2, mp = np % n2;
     float h = (float)(h0 / (double)(1 << lvl));
-    float zx = 2.f * h * dx + h * (c_gl.cheb[m / n] - c_gl.cheb[mp / n]);
-    float zy = 2.f * h * dy + h * (c_gl.cheb[m % n] - c_gl.cheb[mp % n]);
+    const float *cheb = c_gl.cheb[(n >> 1) - 1];
+    float zx = 2.f * h * dx + h * (cheb[m / n] - cheb[mp / n]);
+    float zy = 2.f * h * dy + h * (cheb[m % n] - cheb[mp % n]);
     float *K = ops + (int64_t)key * 16 * n2 * n2;
     int ld = 4 * n2;
     for (int ci = 0; ci < 4; ++ci) {
@@ -625,7 +605,7 @@ __device__ __forceinline__ void q_point(const KConst<float> &k, float zx, float 
         if (ct <= 0.f) continue;
         float s = side == 0 ? 1.f : -1.f;
         float x2 = zx * zx, y2 = zy * zy, r2 = x2 + y2;
-        float ir2 = 1.f / r2;
+        float ir2 = __fdividef(1.f, r2);
         float g0c = side == 0 ? w.g_hi : w.g_lo;
         float u = r2 * g0c, iu = 4.f * ct * ir2;
         float e, F0, F1, F2;
@@ -639,171 +619,300 @@ __device__ __forceinline__ void q_point(const KConst<float> &k, float zx, float 
     }
 }
 
-// near/far element integral of one source element at target m (target
-// frame coordinates); self pairs are excluded by the caller.  PRECISE: the
-// DD part of every pair in FP64 (closed form near, Gauss rule far) - the
-// element contributions along a fracture nearly cancel for smooth openings,
-// by a factor that grows with the elements per fracture, so residuals need
-// FP64 here; the fluid-source part stays FP32.
+// Far pairs (centre distance r > 8 a): Gauss-Legendre rule of the point
+// kernel along the element.  The m-point rule's relative error for a kernel
+// decaying like r^-2 is about c_m (a/r)^(2m) (c_2 ~ 0.44, c_3 ~ 0.16): 3
+// points (nodes 0, +-sqrt(3/5), weights 8/9, 5/9) up to r = 24 a (<= 6e-7
+// at r = 8 a) and 2 points (+-1/sqrt(3), weights 1) beyond (<= 1.3e-6).
+// PRECISE: the DD part in FP64 with the 3-point rule at every distance.
+__device__ __forceinline__ void far_node(int ng, int g, float &xi, float &wt) {
+    if (ng == 3) {
+        xi = g == 0 ? -0.77459666924f : (g == 1 ? 0.f : 0.77459666924f);
+        wt = g == 1 ? 0.88888888889f : 0.55555555556f;
+    } else {
+        xi = g == 0 ? -0.57735026919f : 0.57735026919f;
+        wt = 1.f;
+    }
+}
 template <bool PRECISE>
-__device__ __forceinline__ void pair_field(const KConst<float> &k, const KConst<double> &kd, const Win<float> &w,
-                                           const Win<double> &wd, float mx, float my, const SrcTile &s,
-                                           float acc[4], double accd[4]) {
-    float cxs = 0.5f * (s.x0 + s.x1), cys = 0.5f * (s.y0 + s.y1);
-    float dx = mx - cxs, dy = my - cys;
-    float r2 = dx * dx + dy * dy;
-    bool far = r2 > 64.f * s.a * s.a;
+__device__ __forceinline__ void far_pair(const KConst<float> &k, const KConst<double> &kd, const Win<float> &w,
+                                         const Win<double> &wd, float dx, float dy, float r2, float a, float tx,
+                                         float ty, float Dx, float Dy, float q, float acc[4], double accd[4]) {
+    const int ng = (PRECISE || r2 <= 576.f * a * a) ? 3 : 2;
     if (PRECISE) {
-        if (far) {
-            double nx = -(double)s.ty, ny = (double)s.tx;
-            double Pxx = s.Dx * nx, Pyy = s.Dy * ny, Pxy = 0.5 * (s.Dx * ny + s.Dy * nx);
+        double nx = -(double)ty, ny = (double)tx;
+        double Pxx = Dx * nx, Pyy = Dy * ny, Pxy = 0.5 * (Dx * ny + Dy * nx);
 #pragma unroll
-            for (int g = 0; g < 3; ++g) {
-                double sg = (double)c_gl.xf[g] * s.a, wt = (double)c_gl.wf[g] * s.a;
-                pot_kernel<double>(kd, dx - sg * s.tx, dy - sg * s.ty, wt * Pxx, wt * Pyy, wt * Pxy, 0.0, wd, accd);
-            }
-        } else {
-            disl_field<double>(kd, (double)(mx - s.x0), (double)(my - s.y0), (double)s.Dx, (double)s.Dy, wd, 1.0, accd);
-            disl_field<double>(kd, (double)(mx - s.x1), (double)(my - s.y1), (double)s.Dx, (double)s.Dy, wd, -1.0, accd);
-        }
-        if (s.q != 0.f) {
-            if (far) {
-#pragma unroll
-                for (int g = 0; g < 3; ++g) {
-                    float sg = c_gl.xf[g] * s.a, wt = c_gl.wf[g] * s.a;
-                    q_point(k, dx - sg * s.tx, dy - sg * s.ty, wt * s.q, w, acc);
-                }
-            } else {
-                for (int g = 0; g < c_gl.nn; ++g) {
-                    float sg = c_gl.xn[g] * s.a, wt = c_gl.wn[g] * s.a;
-                    q_point(k, dx - sg * s.tx, dy - sg * s.ty, wt * s.q, w, acc);
-                }
-            }
+        for (int g = 0; g < 3; ++g) {
+            float xi, wt;
+            far_node(3, g, xi, wt);
+            double sg = (double)xi * a, wg = (double)wt * a;
+            pot_kernel<double>(kd, dx - sg * tx, dy - sg * ty, wg * Pxx, wg * Pyy, wg * Pxy, 0.0, wd, accd);
+            if (q != 0.f) q_point(k, dx - (float)sg * tx, dy - (float)sg * ty, (float)wg * q, w, acc);
         }
         return;
     }
-    if (far) {
-        // far: 3-point Gauss rule of the point kernel
-        float nx = -s.ty, ny = s.tx;
-        float Pxx = s.Dx * nx, Pyy = s.Dy * ny, Pxy = 0.5f * (s.Dx * ny + s.Dy * nx);
+    float nx = -ty, ny = tx;
+    float Pxx = Dx * nx, Pyy = Dy * ny, Pxy = 0.5f * (Dx * ny + Dy * nx);
 #pragma unroll
-        for (int g = 0; g < 3; ++g) {
-            float sg = c_gl.xf[g] * s.a, wt = c_gl.wf[g] * s.a;
-            pot_kernel<float>(k, dx - sg * s.tx, dy - sg * s.ty, wt * Pxx, wt * Pyy, wt * Pxy, wt * s.q, w, acc);
-        }
-    } else {
-        disl_field<float>(k, mx - s.x0, my - s.y0, s.Dx, s.Dy, w, 1.f, acc);
-        disl_field<float>(k, mx - s.x1, my - s.y1, s.Dx, s.Dy, w, -1.f, acc);
-        if (s.q != 0.f) {
-            for (int g = 0; g < c_gl.nn; ++g) {
-                float sg = c_gl.xn[g] * s.a, wt = c_gl.wn[g] * s.a;
-                q_point(k, dx - sg * s.tx, dy - sg * s.ty, wt * s.q, w, acc);
-            }
+    for (int g = 0; g < 3; ++g) {
+        if (g < ng) {
+            float xi, wt;
+            far_node(ng, g, xi, wt);
+            float sg = xi * a, wg = wt * a;
+            pot_kernel<float>(k, dx - sg * tx, dy - sg * ty, wg * Pxx, wg * Pyy, wg * Pxy, wg * q, w, acc);
         }
     }
 }
 
-// Near field + L2P.  One warp per target: the lanes take the sources of the
-// target leaf's neighbour leaves (self + up to 8; about 50 sources at the
-// usual depths) in a strided loop, so nearly every lane has a pair and there
-// are as many warps as targets.  Each lane sums its pairs in FP32, the warp
-// then reduces in FP64; L2P is split over the lanes by Chebyshev node and
-// reduced the same way.
+// Close pairs (r <= 8 a), split into units: unit 0 / 1 = the dislocation
+// at end point 0 (+) / 1 (-) (exact element integral of the DD part),
+// unit 2 + g = Gauss point g of the nq-point rule for the fluid source.
+// (x0, y0, x1, y1) are the source end points and (mx, my) the target in
+// the same frame.  PRECISE: the DD units in FP64.
+template <bool PRECISE>
+__device__ __forceinline__ void near_unit(int unit, int nq, const KConst<float> &k, const KConst<double> &kd,
+                                          const Win<float> &w, const Win<double> &wd, float mx, float my, float x0,
+                                          float y0, float x1, float y1, float a, float tx, float ty, float Dx,
+                                          float Dy, float q, float acc[4], double accd[4]) {
+    if (unit < 2) {
+        float ex = unit ? x1 : x0, ey = unit ? y1 : y0;
+        if (PRECISE)
+            disl_field<double>(kd, (double)(mx - ex), (double)(my - ey), (double)Dx, (double)Dy, wd,
+                               unit ? -1.0 : 1.0, accd);
+        else
+            disl_field<float>(k, mx - ex, my - ey, Dx, Dy, w, unit ? -1.f : 1.f, acc);
+    } else if (q != 0.f) {
+        int g = unit - 2;
+        float sg = c_gl.xn[nq][g] * a, wt = c_gl.wn[nq][g] * a;
+        float cx = 0.5f * (x0 + x1), cy = 0.5f * (y0 + y1);
+        q_point(k, mx - cx - sg * tx, my - cy - sg * ty, wt * q, w, acc);
+    }
+}
+
+// one (target, source) pair, self pairs excluded by the caller
+template <bool PRECISE>
+__device__ __forceinline__ void pair_field(const KConst<float> &k, const KConst<double> &kd, const Win<float> &w,
+                                           const Win<double> &wd, int nq, float mx, float my, const SrcTile &s,
+                                           float acc[4], double accd[4]) {
+    float dx = mx - 0.5f * (s.x0 + s.x1), dy = my - 0.5f * (s.y0 + s.y1);
+    float r2 = dx * dx + dy * dy;
+    if (r2 > 64.f * s.a * s.a) {
+        far_pair<PRECISE>(k, kd, w, wd, dx, dy, r2, s.a, s.tx, s.ty, s.Dx, s.Dy, s.q, acc, accd);
+    } else {
+        int nu = 2 + (s.q != 0.f ? nq : 0);
+        for (int u = 0; u < nu; ++u)
+            near_unit<PRECISE>(u, nq, k, kd, w, wd, mx, my, s.x0, s.y0, s.x1, s.y1, s.a, s.tx, s.ty, s.Dx, s.Dy,
+                               s.q, acc, accd);
+    }
+}
+
+// Near field + L2P.  One warp per target.  The lanes walk the sources of
+// the target leaf's neighbour leaves (self + up to 8; table precomputed per
+// leaf: start, count, cell offset) 32 at a time and evaluate the far pairs
+// at once; close pairs go to a per-warp queue and are evaluated afterwards
+// as independent units (2 dislocations + nq fluid-source points each), so
+// the costly close-pair arithmetic runs on full warps instead of on the few
+// lanes that meet a close pair in each step.  Each lane sums its pairs in
+// FP32, the warp then reduces in FP64; L2P is split over the lanes by
+// Chebyshev node and reduced the same way.
 constexpr int NEAR_W = 8;
 constexpr int NEAR_T = 32 * NEAR_W;
+constexpr int NEAR_Q = 64;     // close pairs queued per target; further ones are evaluated in place
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
     return v;
 }
+// FP64 runs at 1/64 of the FP32 rate on this GPU, so the per-target sums
+// are carried as unevaluated FP32 pairs (h + l, Knuth's two-sum), which
+// keeps ~44 bits through the warp reduction at FP32 cost.
+__device__ __forceinline__ void two_sum_add(float &h, float &l, float bh, float bl) {
+    float s = h + bh, v = s - h;
+    float e = (h - (s - v)) + (bh - v) + (l + bl);
+    h = s + e;
+    l = e - (h - s);
+}
+__device__ __forceinline__ void warp_sum_ds(float &h, float &l) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float bh = __shfl_xor_sync(0xFFFFFFFFu, h, o), bl = __shfl_xor_sync(0xFFFFFFFFu, l, o);
+        two_sum_add(h, l, bh, bl);
+    }
+}
 template <bool PRECISE>
 __global__ void __launch_bounds__(NEAR_T) k_near(KConst<float> k, KConst<double> kd, Win<float> w, Win<double> wd,
-                                                 int64_t loff, const int32_t *cstart, const int32_t *cend,
-                                                 const int32_t *cix, const int32_t *ciy, const int32_t *nboff,
-                                                 const int32_t *nbidx, const int32_t *elem_leaf, const float4 *grel,
-                                                 const float4 *frame, const float4 *chg, const int64_t *perm,
-                                                 float wL, int n, const float *F, int use_far, int64_t N,
-                                                 double scale, double *y) {
+                                                 const int32_t *nboff, const int4 *nbtab, const int32_t *elem_leaf,
+                                                 const float4 *grel, const float4 *frame, const float4 *chg,
+                                                 const int64_t *perm, int64_t loff, float wL, int n, int nq,
+                                                 const float *F, int use_far, int64_t N, double scale, double *y) {
+    constexpr unsigned FULL = 0xFFFFFFFFu;
     __shared__ int sst[NEAR_W][9], spre[NEAR_W][10];
     __shared__ float sox[NEAR_W][9], soy[NEAR_W][9];
-    int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int64_t ti = (int64_t)blockIdx.x * NEAR_W + wid;
+    __shared__ int2 sq[NEAR_W][NEAR_Q];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t ti = (int64_t)blockIdx.x * NEAR_W + wid;
     if (ti >= N) return;                      // whole warp leaves together
-    int32_t leaf = elem_leaf[ti];
-    int64_t cell = loff + leaf;
-    int ix = cix[cell], iy = ciy[cell];
-    int q0 = nboff[leaf], nq = nboff[leaf + 1] - q0;
-    if (lane == 0) {
-        int run = 0;
-        for (int q = 0; q < nq; ++q) {
-            int64_t J = loff + nbidx[q0 + q];
-            sst[wid][q] = cstart[J];
-            spre[wid][q] = run;
-            run += cend[J] - cstart[J];
-            sox[wid][q] = wL * (float)(cix[J] - ix);
-            soy[wid][q] = wL * (float)(ciy[J] - iy);
+    const int32_t leaf = elem_leaf[ti];
+    const int q0 = nboff[leaf], nb = nboff[leaf + 1] - q0;
+    {   // neighbour table: one lane per neighbour leaf, counts prefix-summed
+        int4 tb = lane < nb ? nbtab[q0 + lane] : make_int4(0, 0, 0, 0);
+        int incl = tb.y;
+#pragma unroll
+        for (int o = 1; o < 16; o <<= 1) {
+            int v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += v;
         }
-        spre[wid][nq] = run;
+        if (lane < nb) {
+            sst[wid][lane] = tb.x;
+            spre[wid][lane + 1] = incl;
+            sox[wid][lane] = wL * (float)tb.z;
+            soy[wid][lane] = wL * (float)tb.w;
+        }
+        if (lane == 0) spre[wid][0] = 0;
     }
     __syncwarp();
-    float4 rt = grel[ti];
-    float mx = 0.5f * (rt.x + rt.z), my = 0.5f * (rt.y + rt.w);
-    int S = spre[wid][nq];
+    const float4 rt = grel[ti];
+    const float mx = 0.5f * (rt.x + rt.z), my = 0.5f * (rt.y + rt.w);
+    const int S = spre[wid][nb];
     float acc[4] = {0, 0, 0, 0};
     double accd[4] = {0, 0, 0, 0};
-    int q = 0;
-    for (int c = lane; c < S; c += 32) {
-        while (c >= spre[wid][q + 1]) ++q;
-        int sj = sst[wid][q] + (c - spre[wid][q]);
-        if (sj == (int)ti) continue;
-        float4 r = grel[sj], f = frame[sj], cg = chg[sj];
-        float ox = sox[wid][q], oy = soy[wid][q];
-        SrcTile st;
-        st.x0 = r.x + ox; st.y0 = r.y + oy; st.x1 = r.z + ox; st.y1 = r.w + oy;
-        st.Dx = cg.x; st.Dy = cg.y; st.q = cg.z; st.a = f.z; st.tx = f.x; st.ty = f.y; st.idx = sj;
-        pair_field<PRECISE>(k, kd, w, wd, mx, my, st, acc, accd);
+    int qn = 0, slot = 0;
+    bool anyq = false;
+    for (int base = 0; base < S; base += 32) {
+        const int c = base + lane;
+        bool close = false, hasq = false;
+        int sj = -1;
+        float4 r = make_float4(0.f, 0.f, 0.f, 0.f), f = r, cg = r;
+        float ox = 0.f, oy = 0.f;
+        if (c < S) {
+            while (c >= spre[wid][slot + 1]) ++slot;
+            sj = sst[wid][slot] + (c - spre[wid][slot]);
+            if (sj != (int)ti) {
+                r = grel[sj];
+                f = frame[sj];
+                cg = chg[sj];
+                ox = sox[wid][slot];
+                oy = soy[wid][slot];
+                float dx = mx - 0.5f * (r.x + r.z) - ox, dy = my - 0.5f * (r.y + r.w) - oy;
+                float r2 = dx * dx + dy * dy;
+                if (r2 > 64.f * f.z * f.z)
+                    far_pair<PRECISE>(k, kd, w, wd, dx, dy, r2, f.z, f.x, f.y, cg.x, cg.y, cg.z, acc, accd);
+                else {
+                    close = true;
+                    hasq = cg.z != 0.f;
+                }
+            }
+        }
+        const unsigned m = __ballot_sync(FULL, close);
+        if (m) {
+            anyq = anyq || __ballot_sync(FULL, hasq) != 0u;
+            const int pos = qn + __popc(m & ((1u << lane) - 1u));
+            if (close) {
+                if (pos < NEAR_Q) {
+                    sq[wid][pos] = make_int2(sj, slot);
+                } else {                      // queue full: this pair in place
+                    int nu = 2 + (hasq ? nq : 0);
+                    for (int u = 0; u < nu; ++u)
+                        near_unit<PRECISE>(u, nq, k, kd, w, wd, mx, my, r.x + ox, r.y + oy, r.z + ox, r.w + oy, f.z,
+                                           f.x, f.y, cg.x, cg.y, cg.z, acc, accd);
+                }
+            }
+            qn += __popc(m);
+        }
     }
-    for (int c = 0; c < 4; ++c) accd[c] += (double)acc[c];
+    __syncwarp();
+    const int nqd = qn < NEAR_Q ? qn : NEAR_Q;
+    if (nqd > 0) {
+        // units: first the 2 dislocations of every queued pair, then the
+        // fluid-source points (only if some queued source carries q)
+        const int nf = anyq ? nq : 0, nd = 2 * nqd, U = nd + nf * nqd;
+        for (int base = 0; base < U; base += 32) {
+            const int u = base + lane;
+            if (u < U) {
+                int pi, unit;
+                if (u < nd) {
+                    pi = u >> 1;
+                    unit = u & 1;
+                } else {
+                    pi = (u - nd) / nf;
+                    unit = 2 + (u - nd) - pi * nf;
+                }
+                const int2 e = sq[wid][pi];
+                const float4 r = grel[e.x], f = frame[e.x], cg = chg[e.x];
+                const float ox = sox[wid][e.y], oy = soy[wid][e.y];
+                near_unit<PRECISE>(unit, nq, k, kd, w, wd, mx, my, r.x + ox, r.y + oy, r.z + ox, r.w + oy, f.z, f.x,
+                                   f.y, cg.x, cg.y, cg.z, acc, accd);
+            }
+        }
+    }
+    float hl[4][2];                           // per-lane sums as FP32 pairs
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        hl[c][0] = acc[c];
+        hl[c][1] = 0.f;
+    }
     if (use_far) {
         // L2P: lane handles nodes m = lane, lane + 32, ...
-        float hL = 0.5f * wL;
-        float xh = mx / hL, yh = my / hL;
-        int n2 = n * n;
+        const float *cheb = c_gl.cheb[(n >> 1) - 1], *bw = c_gl.bw[(n >> 1) - 1];
+        const float hL = 0.5f * wL;
+        const float xh = __fdividef(mx, hL), yh = __fdividef(my, hL);
+        const int n2 = n * n;
         float sx = 0.f, sy = 0.f;
         int hx = -1, hy = -1;
         for (int j = 0; j < n; ++j) {             // barycentric denominators
-            float dxj = xh - c_gl.cheb[j], dyj = yh - c_gl.cheb[j];
+            float dxj = xh - cheb[j], dyj = yh - cheb[j];
             if (fabsf(dxj) < 1e-7f) hx = j;
             if (fabsf(dyj) < 1e-7f) hy = j;
-            sx += c_gl.bw[j] / dxj;
-            sy += c_gl.bw[j] / dyj;
+            sx += __fdividef(bw[j], dxj);
+            sy += __fdividef(bw[j], dyj);
         }
-        const float *Fc = F + cell * 4 * n2;
+        const float isx = __fdividef(1.f, sx), isy = __fdividef(1.f, sy);
+        const float *Fc = F + (loff + leaf) * 4 * n2;
         float f4[4] = {0, 0, 0, 0};
         for (int m = lane; m < n2; m += 32) {
-            int a = m / n, bb = m % n;
-            float la = hx >= 0 ? (a == hx ? 1.f : 0.f) : c_gl.bw[a] / (xh - c_gl.cheb[a]) / sx;
-            float lb = hy >= 0 ? (bb == hy ? 1.f : 0.f) : c_gl.bw[bb] / (yh - c_gl.cheb[bb]) / sy;
+            int a = m / n, bb = m - a * n;
+            float la = hx >= 0 ? (a == hx ? 1.f : 0.f) : __fdividef(bw[a], xh - cheb[a]) * isx;
+            float lb = hy >= 0 ? (bb == hy ? 1.f : 0.f) : __fdividef(bw[bb], yh - cheb[bb]) * isy;
             float v = la * lb;
             f4[0] += v * Fc[m]; f4[1] += v * Fc[n2 + m]; f4[2] += v * Fc[2 * n2 + m]; f4[3] += v * Fc[3 * n2 + m];
         }
-        for (int c = 0; c < 4; ++c) accd[c] += (double)f4[c];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) two_sum_add(hl[c][0], hl[c][1], f4[c], 0.f);
     }
-    for (int c = 0; c < 4; ++c) accd[c] = warp_sum(accd[c]);
-    if (lane != 0) return;
-    float4 f = frame[ti];
-    double ss, sn;
-    to_local<double>((double)f.x, (double)f.y, accd, ss, sn);
-    int64_t e = perm[ti];
-    y[e] += scale * ss;
-    y[N + e] += scale * sn;
-    y[2 * N + e] += scale * accd[3];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) warp_sum_ds(hl[c][0], hl[c][1]);
+    if (PRECISE) {                            // the FP64 part of the DD units
+#pragma unroll
+        for (int c = 0; c < 4; ++c) accd[c] = warp_sum(accd[c]);
+    }
+    // lanes 0, 1, 2 write sigma_s, sigma_n, p; the rotation to the target
+    // frame is applied to both halves of each pair
+    if (lane >= 3) return;
+    const float4 f = frame[ti];
+    const float nx = -f.y, ny = f.x;
+    float vh, vl;
+    double vd = 0.0;
+    if (lane == 2) {
+        vh = hl[3][0];
+        vl = hl[3][1];
+        if (PRECISE) vd = accd[3];
+    } else {
+        // sigma_n = g . (n n), sigma_s = g . sym(t n)
+        const float cxx = lane ? nx * nx : f.x * nx, cyy = lane ? ny * ny : f.y * ny;
+        const float cxy = lane ? 2.f * nx * ny : f.x * ny + f.y * nx;
+        vh = cxx * hl[0][0] + cyy * hl[1][0] + cxy * hl[2][0];
+        vl = cxx * hl[0][1] + cyy * hl[1][1] + cxy * hl[2][1];
+        if (PRECISE) vd = (double)cxx * accd[0] + (double)cyy * accd[1] + (double)cxy * accd[2];
+    }
+    const int64_t e = perm[ti];
+    y[lane * N + e] += scale * (((double)vh + (double)vl) + vd);
 }
 
 // -------------------------------------------------------------------- dense
 constexpr int DN_T = 128;
 template <bool PRECISE>
-__global__ void __launch_bounds__(DN_T) k_dense(KConst<float> k, KConst<double> kd, Win<float> w, Win<double> wd, int64_t loff, const int32_t *elem_leaf,
+__global__ void __launch_bounds__(DN_T) k_dense(KConst<float> k, KConst<double> kd, Win<float> w, Win<double> wd, int nq, int64_t loff, const int32_t *elem_leaf,
                                                 const int32_t *cix, const int32_t *ciy, const float4 *grel,
                                                 const float4 *frame, const float4 *chg, const int64_t *perm,
                                                 float wL, int64_t N, int64_t chunk, double scale, double *y) {
@@ -845,7 +954,7 @@ __global__ void __launch_bounds__(DN_T) k_dense(KConst<float> k, KConst<double> 
                 SrcTile s = tile[j];
                 float ox = wL * (float)(sjx[j] - ixI), oy = wL * (float)(sjy[j] - iyI);
                 s.x0 += ox; s.y0 += oy; s.x1 += ox; s.y1 += oy;
-                pair_field<PRECISE>(k, kd, w, wd, mx, my, s, acc, accd);
+                pair_field<PRECISE>(k, kd, w, wd, nq, mx, my, s, acc, accd);
             }
             for (int c = 0; c < 4; ++c) accd[c] += (double)acc[c];
         }
@@ -868,35 +977,31 @@ __global__ void __launch_bounds__(DN_T) k_dense(KConst<float> k, KConst<double> 
 // wide, and contexts that use different values on one device must not run
 // concurrently.
 static std::mutex g_tab_mu;
-static int g_last_n[64], g_last_q[64];
-static bool g_tab_init = false;
+static bool g_tab_done[64];
 ddm_status upload_tables(ddm_ctx *ctx) {
     std::lock_guard<std::mutex> lk(g_tab_mu);
-    if (!g_tab_init) {
-        for (int i = 0; i < 64; ++i) g_last_n[i] = g_last_q[i] = -1;
-        g_tab_init = true;
-    }
-    int n = ctx->prm.n_cheb, nq = ctx->prm.quad_near, dv = ctx->device & 63;
-    if (n == g_last_n[dv] && nq == g_last_q[dv]) return DDM_OK;
+    int dv = ctx->device & 63;
+    if (g_tab_done[dv]) return DDM_OK;
     GLTab h;
     memset(&h, 0, sizeof(h));
     double x[MAXGL], wt[MAXGL];
-    gauss_legendre(nq, x, wt);
-    for (int i = 0; i < nq; ++i) { h.xn[i] = (float)x[i]; h.wn[i] = (float)wt[i]; }
-    h.nn = nq;
-    gauss_legendre(3, x, wt);
-    for (int i = 0; i < 3; ++i) { h.xf[i] = (float)x[i]; h.wf[i] = (float)wt[i]; }
-    gauss_legendre(n, x, wt);
-    for (int i = 0; i < n; ++i) { h.xc[i] = (float)x[i]; h.wc[i] = (float)wt[i]; }
-    h.nc = n;
-    for (int j = 0; j < n; ++j) {
-        double th = (2 * j + 1) * M_PI / (2.0 * n);
-        h.cheb[j] = (float)cos(th);
-        h.bw[j] = (float)(((j & 1) ? -1.0 : 1.0) * sin(th));
+    for (int m = 1; m <= MAXGL; ++m) {
+        gauss_legendre(m, x, wt);
+        for (int i = 0; i < m; ++i) { h.xn[m][i] = (float)x[i]; h.wn[m][i] = (float)wt[i]; }
+    }
+    for (int n = 2; n <= DDM_MAX_CHEB; n += 2) {
+        int o = n / 2 - 1;
+        gauss_legendre(n, x, wt);
+        for (int i = 0; i < n; ++i) { h.xc[o][i] = (float)x[i]; h.wc[o][i] = (float)wt[i]; }
+        for (int j = 0; j < n; ++j) {
+            double th = (2 * j + 1) * M_PI / (2.0 * n);
+            h.cheb[o][j] = (float)cos(th);
+            h.bw[o][j] = (float)(((j & 1) ? -1.0 : 1.0) * sin(th));
+        }
     }
     DDM_CUDA_TRY(ctx, cudaMemcpyToSymbolAsync(c_gl, &h, sizeof(h), 0, cudaMemcpyHostToDevice, ctx->stream));
     DDM_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-    g_last_n[dv] = n; g_last_q[dv] = nq;
+    g_tab_done[dv] = true;
     return DDM_OK;
 }
 
@@ -984,7 +1089,7 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
         chunks = (N + chunk - 1) / chunk;
         prof_begin(ctx, 7);
         auto kdn = precise ? k_dense<true> : k_dense<false>;
-        kdn<<<dim3((unsigned)tiles, (unsigned)chunks), DN_T, 0, s>>>(kf, ctx->kd, wf, wd, loff, t->elem_leaf, t->cell_ix, t->cell_iy,
+        kdn<<<dim3((unsigned)tiles, (unsigned)chunks), DN_T, 0, s>>>(kf, ctx->kd, wf, wd, ctx->prm.quad_near, loff, t->elem_leaf, t->cell_ix, t->cell_iy,
                                                                         t->g_rel, t->g_frame, t->chg, t->perm, wL, N,
                                                                         chunk, scale, y);
         prof_end(ctx, 7, 1);
@@ -1049,8 +1154,8 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
     prof_begin(ctx, 6);
     auto knr = precise ? k_near<true> : k_near<false>;
     knr<<<(unsigned)((N + NEAR_W - 1) / NEAR_W), NEAR_T, 0, s>>>(
-        kf, ctx->kd, wf, wd, loff, t->cell_start, t->cell_end, t->cell_ix, t->cell_iy, t->nb_off, t->nb_idx,
-        t->elem_leaf, t->g_rel, t->g_frame, t->chg, t->perm, wL, n, t->Fl, use_far, N, scale, y);
+        kf, ctx->kd, wf, wd, t->nb_off, t->nb_tab, t->elem_leaf, t->g_rel, t->g_frame, t->chg, t->perm, loff, wL, n,
+        ctx->prm.quad_near, t->Fl, use_far, N, scale, y);
     prof_end(ctx, 6, 1);
     DDM_CUDA_TRY(ctx, cudaGetLastError());
     return DDM_OK;
@@ -1100,7 +1205,7 @@ __global__ void k_static_prep(const double *xy, const double *x, int64_t n, Stat
 // offsets from FP64 midpoints, own element in FP64 closed form
 constexpr int ST_T = 128;
 __global__ void __launch_bounds__(ST_T) k_static_dense(KConst<float> k, KConst<double> kd, Win<float> w,
-                                                       Win<double> wd, const StaticElem *sc, const double *x,
+                                                       Win<double> wd, int nq, const StaticElem *sc, const double *x,
                                                        int64_t n, double *y) {
     __shared__ StaticElem tile[ST_T];
     int64_t ti = blockIdx.x * (int64_t)ST_T + threadIdx.x;
@@ -1123,7 +1228,7 @@ __global__ void __launch_bounds__(ST_T) k_static_dense(KConst<float> k, KConst<d
                 st.x1 = cx + o.frame.z * o.frame.x; st.y1 = cy + o.frame.z * o.frame.y;
                 st.Dx = o.chg.x; st.Dy = o.chg.y; st.q = o.chg.z; st.a = o.frame.z;
                 st.tx = o.frame.x; st.ty = o.frame.y; st.idx = (int)(sb + j);
-                pair_field<false>(k, kd, w, wd, 0.f, 0.f, st, acc, accd);
+                pair_field<false>(k, kd, w, wd, nq, 0.f, 0.f, st, acc, accd);
             }
             for (int c = 0; c < 4; ++c) accd[c] += (double)acc[c];
         }
@@ -1171,7 +1276,7 @@ extern "C" ddm_status ddm_matvec_dense_static(ddm_ctx *ctx, const double *d_xy, 
     Win<float> wf = make_win<float>(ctx, tau_lo, tau_hi);
     Win<double> wd = make_win<double>(ctx, tau_lo, tau_hi);
     k_static_prep<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_xy, d_x, n, sc);
-    k_static_dense<<<(unsigned)((n + ST_T - 1) / ST_T), ST_T, 0, s>>>(ctx->kf, ctx->kd, wf, wd, sc, d_x, n, d_y);
+    k_static_dense<<<(unsigned)((n + ST_T - 1) / ST_T), ST_T, 0, s>>>(ctx->kf, ctx->kd, wf, wd, ctx->prm.quad_near, sc, d_x, n, d_y);
     prof_end(ctx, 7, 2);
     DDM_CUDA_TRY(ctx, cudaGetLastError());
     return DDM_OK;

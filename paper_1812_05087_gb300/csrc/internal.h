@@ -53,6 +53,7 @@ struct ddm_tree {
     int32_t *up_cnt;           // per cell: children done in the running upward pass (0 between passes)
     int32_t *il_off, *il_idx;  // interaction lists (CSR over cells)
     int32_t *nb_off, *nb_idx;  // neighbour lists of leaves incl. self (CSR over leaves, leaf-local)
+    int4 *nb_tab;              // per neighbour entry: (element start, count, cell dx, cell dy)
     int32_t *elem_leaf;        // sorted element -> leaf index (leaf-local)
     int64_t n_groups;          // groups of 32 consecutive sorted targets
     int32_t *grp_off, *grp_leaf; // per group: union of the neighbour leaves of its targets (CSR, leaf-local)

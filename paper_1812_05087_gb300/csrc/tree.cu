@@ -263,6 +263,19 @@ __global__ void k_children(const int32_t *parent, int64_t first, int64_t ncell, 
     if (parent[c - 1] != p) child0[p] = (int32_t)c;
 }
 
+// per neighbour entry of every leaf: the neighbour's element range and its
+// cell offset from the leaf, so the near field reads one record per entry
+__global__ void k_nbtab(const int32_t *nboff, const int32_t *nbidx, const int32_t *cstart, const int32_t *cend,
+                        const int32_t *cix, const int32_t *ciy, int64_t loff, int64_t nleaf, int4 *tab) {
+    int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (L >= nleaf) return;
+    int64_t me = loff + L;
+    for (int e = nboff[L]; e < nboff[L + 1]; ++e) {
+        int64_t J = loff + nbidx[e];
+        tab[e] = make_int4(cstart[J], cend[J] - cstart[J], cix[J] - cix[me], ciy[J] - ciy[me]);
+    }
+}
+
 __device__ int32_t find_key(const uint32_t *ckey, int64_t off, int64_t ncell, uint32_t k) {
     int64_t lo = 0, hi = ncell;
     while (lo < hi) {
@@ -397,7 +410,7 @@ __global__ void k_p2p_count(const int32_t *cstart, const int32_t *cend, int64_t 
 void tree_free(ddm_tree *t) {
     if (!t) return;
     void *ps[] = {t->mk_work, t->pb_off, t->pb_elem, t->pb_moff, t->pb_inv, t->mk_off, t->mk_pair, t->m2l_ops, t->grp_off, t->grp_leaf, t->perm, t->cell_key, t->cell_ix, t->cell_iy, t->cell_start, t->cell_end, t->cell_parent, t->cell_child0, t->cell_nchild, t->up_cnt,
-                  t->il_off, t->il_idx, t->nb_off, t->nb_idx, t->elem_leaf, t->g_rel, t->g_frame,
+                  t->il_off, t->il_idx, t->nb_off, t->nb_idx, t->nb_tab, t->elem_leaf, t->g_rel, t->g_frame,
                   t->xy_sorted, t->xy_caller, t->self_blk, t->W, t->Fl, t->chg};
     for (void *p : ps) dfree(p, t->stream);
     for (double *p : t->win_blk) dfree(p, t->stream);
@@ -589,6 +602,9 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
     TRY(cudaMemcpyAsync(t->nb_off + nleaf, &nbtot, sizeof(int32_t), cudaMemcpyHostToDevice, st));
     TRY(dalloc(&t->nb_idx, std::max(nbtot, 1) * sizeof(int32_t), st));
     k_neigh<<<lb, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, loff, nleaf, side, t->nb_off, t->nb_idx, nullptr); ++tl_launches;
+    TRY(dalloc(&t->nb_tab, std::max(nbtot, 1) * sizeof(int4), st));
+    k_nbtab<<<lb, TB, 0, st>>>(t->nb_off, t->nb_idx, t->cell_start, t->cell_end, t->cell_ix, t->cell_iy, loff, nleaf,
+                               t->nb_tab); ++tl_launches;
 
     // interaction lists, levels >= 2
     TRY(cudaMemsetAsync(cnt, 0, NC * sizeof(int32_t), st));
