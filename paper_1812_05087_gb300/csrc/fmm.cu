@@ -600,6 +600,7 @@ struct SrcTile {
 
 __device__ __forceinline__ void q_point(const KConst<float> &k, float zx, float zy, float q, const Win<float> &w,
                                         float acc[4]) {
+#pragma unroll 1
     for (int side = 0; side < 2; ++side) {
         float ct = side == 0 ? w.ct_hi : w.ct_lo;
         if (ct <= 0.f) continue;
@@ -654,14 +655,12 @@ __device__ __forceinline__ void far_pair(const KConst<float> &k, const KConst<do
     }
     float nx = -ty, ny = tx;
     float Pxx = Dx * nx, Pyy = Dy * ny, Pxy = 0.5f * (Dx * ny + Dy * nx);
-#pragma unroll
-    for (int g = 0; g < 3; ++g) {
-        if (g < ng) {
-            float xi, wt;
-            far_node(ng, g, xi, wt);
-            float sg = xi * a, wg = wt * a;
-            pot_kernel<float>(k, dx - sg * tx, dy - sg * ty, wg * Pxx, wg * Pyy, wg * Pxy, wg * q, w, acc);
-        }
+#pragma unroll 1
+    for (int g = 0; g < ng; ++g) {
+        float xi, wt;
+        far_node(ng, g, xi, wt);
+        float sg = xi * a, wg = wt * a;
+        pot_kernel<float>(k, dx - sg * tx, dy - sg * ty, wg * Pxx, wg * Pyy, wg * Pxy, wg * q, w, acc);
     }
 }
 
@@ -741,7 +740,7 @@ __device__ __forceinline__ void warp_sum_ds(float &h, float &l) {
     }
 }
 template <bool PRECISE>
-__global__ void __launch_bounds__(NEAR_T) k_near(KConst<float> k, KConst<double> kd, Win<float> w, Win<double> wd,
+__global__ void __launch_bounds__(NEAR_T, 4) k_near(KConst<float> k, KConst<double> kd, Win<float> w, Win<double> wd,
                                                  const int32_t *nboff, const int4 *nbtab, const int32_t *elem_leaf,
                                                  const float4 *grel, const float4 *frame, const float4 *chg,
                                                  const int64_t *perm, int64_t loff, float wL, int n, int nq,

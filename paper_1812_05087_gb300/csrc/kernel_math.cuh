@@ -49,6 +49,32 @@ template <class T> struct Big;
 template <> struct Big<float> { static constexpr float U = 30.f; };
 template <> struct Big<double> { static constexpr double U = 70.0; };
 
+// The series branches (u < 1) are rare on the hot path (they serve pairs
+// closer than ~2 sqrt(ct)) and long once unrolled, so they live out of line
+// and the hot kernels keep a small instruction footprint.
+template <class T> struct Tri { T a, b, c; };
+template <class T> struct Quad { T a, b, c, d; };
+
+// F = sum (-u)^k/(k+1)!, F' = sum (k+1)(-1)^(k+1) u^k/(k+2)!,
+// F'' = sum (k+1)(k+2)(-1)^k u^k/(k+3)!   (Horner, highest term first)
+template <class T>
+__device__ __noinline__ Tri<T> f_series(T u) {
+    T a = 0, b = 0, c = 0;
+#pragma unroll
+    for (int k = Prec<T>::NS; k >= 0; --k) {
+        T f1 = 1, f2 = 1, f3 = 1;
+#pragma unroll
+        for (int j = 2; j <= k + 1; ++j) f1 *= T(j);
+        f2 = f1 * T(k + 2);
+        f3 = f2 * T(k + 3);
+        T sg = (k & 1) ? T(-1) : T(1);
+        a = a * u + sg / f1;
+        b = b * u - sg * T(k + 1) / f2;
+        c = c * u + sg * T((k + 1) * (k + 2)) / f3;
+    }
+    return Tri<T>{a, b, c};
+}
+
 template <class T>
 DEV void f_funcs(T u, T iu, T &e, T &F0, T &F1, T &F2) {
     if (u > Big<T>::U) {
@@ -60,22 +86,8 @@ DEV void f_funcs(T u, T iu, T &e, T &F0, T &F1, T &F2) {
     }
     e = dexp<T>(-u);
     if (u < T(1)) {
-        // F = sum (-u)^k/(k+1)!, F' = sum (k+1)(-1)^(k+1) u^k/(k+2)!,
-        // F'' = sum (k+1)(k+2)(-1)^k u^k/(k+3)!   (Horner, highest term first)
-        T a = 0, b = 0, c = 0;
-#pragma unroll
-        for (int k = Prec<T>::NS; k >= 0; --k) {
-            T f1 = 1, f2 = 1, f3 = 1;
-#pragma unroll
-            for (int j = 2; j <= k + 1; ++j) f1 *= T(j);
-            f2 = f1 * T(k + 2);
-            f3 = f2 * T(k + 3);
-            T sg = (k & 1) ? T(-1) : T(1);
-            a = a * u + sg / f1;
-            b = b * u - sg * T(k + 1) / f2;
-            c = c * u + sg * T((k + 1) * (k + 2)) / f3;
-        }
-        F0 = a; F1 = b; F2 = c;
+        Tri<T> r = f_series<T>(u);
+        F0 = r.a; F1 = r.b; F2 = r.c;
     } else {
         F0 = (T(1) - e) * iu;
         F1 = (e - F0) * iu;
@@ -84,26 +96,32 @@ DEV void f_funcs(T u, T iu, T &e, T &F0, T &F1, T &F2) {
 }
 
 // ghat = (1 - F)/u and its two derivatives; P2h = P(2,u)/u^2.
+// ghat = sum (-1)^k u^k/(k+2)!, ghat' = sum_{k>=1} (-1)^k k u^(k-1)/(k+2)!,
+// ghat'' = sum_{k>=2} (-1)^k k(k-1) u^(k-2)/(k+2)!,
+// P2h = sum_{k>=2} (-1)^k (k-1) u^(k-2)/k!
+template <class T>
+__device__ __noinline__ Quad<T> g_series(T u) {
+    T a = 0, b = 0, c = 0, d = 0;
+#pragma unroll
+    for (int k = Prec<T>::NS + 2; k >= 0; --k) {
+        T fk = 1;
+#pragma unroll
+        for (int j = 2; j <= k; ++j) fk *= T(j);
+        T fk2 = fk * T(k + 1) * T(k + 2);
+        T sg = (k & 1) ? T(-1) : T(1);
+        a = a * u + sg / fk2;
+        if (k >= 1) b = b * u + sg * T(k) / fk2;
+        if (k >= 2) c = c * u + sg * T(k * (k - 1)) / fk2;
+        if (k >= 2) d = d * u + sg * T(k - 1) / fk;
+    }
+    return Quad<T>{a, b, c, d};
+}
+
 template <class T>
 DEV void g_funcs(T u, T iu, T e, T F0, T F1, T F2, T &g0, T &g1, T &g2, T &p2h) {
     if (u < T(1)) {
-        // ghat = sum (-1)^k u^k/(k+2)!, ghat' = sum_{k>=1} (-1)^k k u^(k-1)/(k+2)!,
-        // ghat'' = sum_{k>=2} (-1)^k k(k-1) u^(k-2)/(k+2)!,
-        // P2h = sum_{k>=2} (-1)^k (k-1) u^(k-2)/k!
-        T a = 0, b = 0, c = 0, d = 0;
-#pragma unroll
-        for (int k = Prec<T>::NS + 2; k >= 0; --k) {
-            T fk = 1;
-#pragma unroll
-            for (int j = 2; j <= k; ++j) fk *= T(j);
-            T fk2 = fk * T(k + 1) * T(k + 2);
-            T sg = (k & 1) ? T(-1) : T(1);
-            a = a * u + sg / fk2;
-            if (k >= 1) b = b * u + sg * T(k) / fk2;
-            if (k >= 2) c = c * u + sg * T(k * (k - 1)) / fk2;
-            if (k >= 2) d = d * u + sg * T(k - 1) / fk;
-        }
-        g0 = a; g1 = b; g2 = c; p2h = d;
+        Quad<T> r = g_series<T>(u);
+        g0 = r.a; g1 = r.b; g2 = r.c; p2h = r.d;
     } else {
         g0 = (T(1) - F0) * iu;
         g1 = -(F1 + g0) * iu;
@@ -144,18 +162,19 @@ __constant__ float c_e1cheb[13] = {7.479364044e-01f, -1.782856521e-01f, 3.253978
                                    1.867943905e-03f, -5.230081780e-04f, 1.568588335e-04f, -4.967373770e-05f,
                                    1.644605689e-05f, -5.651932686e-06f, 2.005327778e-06f, -7.314854142e-07f,
                                    2.734071549e-07f};
-DEV float e1f(float u, float iu) {
-    if (u < 1.f) {
-        float s = 0.f;
+static __device__ __noinline__ float e1f_series(float u) {
+    float s = 0.f;
 #pragma unroll
-        for (int k = 10; k >= 1; --k) {
-            float fk = 1.f;
+    for (int k = 10; k >= 1; --k) {
+        float fk = 1.f;
 #pragma unroll
-            for (int j = 2; j <= k; ++j) fk *= (float)j;
-            s = s * u + ((k & 1) ? 1.f : -1.f) / ((float)k * fk);
-        }
-        return s * u - __logf(u) - 0.5772156649f;
+        for (int j = 2; j <= k; ++j) fk *= (float)j;
+        s = s * u + ((k & 1) ? 1.f : -1.f) / ((float)k * fk);
     }
+    return s * u - __logf(u) - 0.5772156649f;
+}
+DEV float e1f(float u, float iu) {
+    if (u < 1.f) return e1f_series(u);
     if (u > 30.f) return 0.f;
     float x = (iu - 1.f / 30.f) * (2.f / (1.f - 1.f / 30.f)) - 1.f;
     float b1 = 0.f, b2 = 0.f;
@@ -223,8 +242,11 @@ DEV void pot_kernel(const KConst<T> &k, T x, T y, T Pxx, T Pyy, T Pxy, T q, cons
         acc[2] += C * (Pxx * xy * (-T(6) * x2 + T(2) * y2) + T(2) * Pxy * (A1 - T(6) * Cm + B1) +
                        Pyy * xy * (T(2) * x2 - T(6) * y2));
     }
-    pot_transient<T>(k, x, y, ir2, Pxx, Pyy, Pxy, q, w.g_hi, T(4) * w.ct_hi, T(1), acc);
-    if (w.ct_lo > T(0)) pot_transient<T>(k, x, y, ir2, Pxx, Pyy, Pxy, q, w.g_lo, T(4) * w.ct_lo, T(-1), acc);
+    const int sides = w.ct_lo > T(0) ? 2 : 1;
+#pragma unroll 1
+    for (int sd = 0; sd < sides; ++sd)
+        pot_transient<T>(k, x, y, ir2, Pxx, Pyy, Pxy, q, sd ? w.g_lo : w.g_hi, T(4) * (sd ? w.ct_lo : w.ct_hi),
+                         sd ? T(-1) : T(1), acc);
 }
 
 // ---------------------------------------------------------------------------
@@ -261,8 +283,11 @@ DEV void disl_field(const KConst<T> &k, T zx, T zy, T Dx, T Dy, const Win<T> &w,
         acc[1] -= C * (Dx * zy * (x2 - y2) + Dy * zx * (x2 + T(3) * y2));
         acc[2] -= C * (x2 - y2) * (Dx * zx + Dy * zy);
     }
-    disl_transient<T>(k, zx, zy, ir2, Dx, Dy, w.g_hi, T(4) * w.ct_hi, s, acc);
-    if (w.ct_lo > T(0)) disl_transient<T>(k, zx, zy, ir2, Dx, Dy, w.g_lo, T(4) * w.ct_lo, -s, acc);
+    const int sides = w.ct_lo > T(0) ? 2 : 1;
+#pragma unroll 1
+    for (int sd = 0; sd < sides; ++sd)
+        disl_transient<T>(k, zx, zy, ir2, Dx, Dy, sd ? w.g_lo : w.g_hi, T(4) * (sd ? w.ct_lo : w.ct_hi),
+                          sd ? -s : s, acc);
 }
 
 // rotate a global (sxx, syy, sxy) into the target frame: (sigma_s, sigma_n)
