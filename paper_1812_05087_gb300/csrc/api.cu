@@ -383,9 +383,11 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
         k_restrict<<<nblk(N), 256, 0, s>>>(g.y3, N, sys, 1, g.w);
         k_axpy<<<nblk(len), 256, 0, s>>>(-1.0, g.w, g.b, len);
     }
-    double bnorm;
+    double bnorm, xnorm;
     if ((st = norm(g.b, bnorm))) return st;
     if (bnorm == 0) bnorm = 1;
+    if ((st = norm(d_x, xnorm))) return st;     // a zero initial guess needs no product
+    bool x_zero = xnorm == 0.0;
     int iters = 0, restarts = 0;
     double rel = 1e300;
     std::vector<double> H((m + 1) * m), cs(m), sn(m), gv(m + 1), hc(m + 2);
@@ -394,7 +396,12 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
     int stall = 0;
     while (iters < P.max_iters) {
         // r = b - A x
-        if ((st = apply(d_x, g.w, mode | DDM_MODE_PRECISE))) return st;
+        if (x_zero) {
+            DDM_CUDA_TRY(ctx, cudaMemsetAsync(g.w, 0, len * sizeof(double), s));
+            x_zero = false;
+        } else {
+            if ((st = apply(d_x, g.w, mode | DDM_MODE_PRECISE))) return st;
+        }
         k_axpy<<<nblk(len), 256, 0, s>>>(-1.0, g.b, g.w, len);          // w = A x - b
         double beta;
         if ((st = norm(g.w, beta))) return st;

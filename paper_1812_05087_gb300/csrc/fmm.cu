@@ -1029,11 +1029,10 @@ static Win<T> make_win(const ddm_ctx *ctx, double lo, double hi) {
     return w;
 }
 
-ddm_status self_blocks(ddm_ctx *ctx, ddm_tree *t, double dt) {
+ddm_status self_blocks(ddm_ctx *ctx, ddm_tree *t, double dt, cudaStream_t s) {
     if (t->self_dt == dt) return DDM_OK;
     int64_t n = t->n;
-    k_self_blocks<<<(n + 255) / 256, 256, 0, ctx->stream>>>(ctx->kd, make_win<double>(ctx, 0.0, dt), t->xy_caller, n,
-                                                            t->self_blk);
+    k_self_blocks<<<(n + 255) / 256, 256, 0, s>>>(ctx->kd, make_win<double>(ctx, 0.0, dt), t->xy_caller, n, t->self_blk);
     DDM_CUDA_TRY(ctx, cudaGetLastError());
     t->self_dt = dt;
     return DDM_OK;

@@ -156,7 +156,7 @@ void tree_free(ddm_tree *t);
 // fmm.cu: y = [K(hi) - K(lo)] x  (caller order), accumulate: y += s * (...)
 ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double tau_lo, double tau_hi, const double *d_x,
                     double *d_y, int mode, int accumulate, double scale, cudaStream_t stream = nullptr);
-ddm_status self_blocks(ddm_ctx *ctx, ddm_tree *t, double dt);   // fills t->self_blk (caller order)
+ddm_status self_blocks(ddm_ctx *ctx, ddm_tree *t, double dt, cudaStream_t s);   // fills t->self_blk (caller order)
 ddm_status ensure_workspace(ddm_ctx *ctx, ddm_tree *t);
 ddm_status upload_tables(ddm_ctx *ctx);
 // precond.cu: chain-block Jacobi preconditioner (cached per dt and system)

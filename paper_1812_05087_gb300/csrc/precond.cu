@@ -4,11 +4,11 @@
 // cut into blocks of at most 64 elements at tree build.  For a time step dt
 // each block's own influence matrix (all its element pairs: FP32 closed
 // forms for the DD part on FP64 offsets, Gauss rule for the fluid source,
-// the own element in FP64 closed form) is assembled for the rows and
-// unknowns of the system being solved and inverted on the device in FP32
-// (Gauss-Jordan with partial pivoting, one thread block per matrix); a
-// preconditioner needs no more precision, and FP32 runs at 64x the FP64
-// rate of this part.  Applying the preconditioner is
+// the own element from the cached FP64 closed form) is assembled for the
+// rows and unknowns of the system being solved and inverted on the device
+// in FP32 (Gauss-Jordan with partial pivoting, one CTA per matrix held in
+// shared memory); a preconditioner needs no more precision, and FP32 runs
+// at 64x the FP64 rate.  Applying the preconditioner is
 // one small dense product per block.  Elements that belong to no chain form
 // 1-element blocks, i.e. the own-element 3x3 block Jacobi.
 #include <cmath>
@@ -27,39 +27,40 @@ __constant__ double c_gl8x[8] = {-0.9602898564975363, -0.7966664774136267, -0.52
 __constant__ double c_gl8w[8] = {0.1012285362903763, 0.2223810344533745, 0.3137066458778873, 0.3626837833783620,
                                  0.3626837833783620, 0.3137066458778873, 0.2223810344533745, 0.1012285362903763};
 
+// per element (caller order): FP64 midpoint, FP32 tangent and half-length
+struct PbGeo {
+    double2 mid;
+    float4 t;        // tx, ty, a, 0
+};
+__global__ void k_pb_geom(const double *xy, int64_t N, PbGeo *g) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= N) return;
+    double ax = xy[e], ay = xy[N + e], bx = xy[2 * N + e], by = xy[3 * N + e];
+    double L = hypot(bx - ax, by - ay);
+    g[e].mid = make_double2(0.5 * (ax + bx), 0.5 * (ay + by));
+    g[e].t = make_float4((float)((bx - ax) / L), (float)((by - ay) / L), (float)(0.5 * L), 0.f);
+}
+
 // rows (sigma_s, sigma_n, p) at element i's midpoint from unit (Ds, Dn, Dq)
-// on element j: FP32 pair arithmetic on offsets taken in FP64 (the
-// preconditioner needs no more), own element in FP64 closed form
-__device__ void pair_block(const KConst<float> &kf, const Win<float> &wf, const KConst<double> &kd,
-                           const Win<double> &wd, const double *xy, int64_t N, int64_t i, int64_t j, float out[3][3]) {
-    double ax = xy[i], ay = xy[N + i], bx = xy[2 * N + i], by = xy[3 * N + i];
-    double Li = hypot(bx - ax, by - ay), tix = (bx - ax) / Li, tiy = (by - ay) / Li;
-    if (i == j) {
-        for (int c = 0; c < 3; ++c) {
-            double o[3];
-            self_field(kd, wd, 0.5 * Li, tix, tiy, c == 0, c == 1, c == 2, o);
-            for (int r = 0; r < 3; ++r) out[r][c] = (float)o[r];
-        }
-        return;
-    }
-    double mx = 0.5 * (ax + bx), my = 0.5 * (ay + by);
-    double cx = xy[j], cy = xy[N + j], dx = xy[2 * N + j], dy = xy[3 * N + j];
-    double Lj = hypot(dx - cx, dy - cy);
-    float tjx = (float)((dx - cx) / Lj), tjy = (float)((dy - cy) / Lj), njx = -tjy, njy = tjx;
-    float z1x = (float)(mx - cx), z1y = (float)(my - cy), z2x = (float)(mx - dx), z2y = (float)(my - dy);
-    float ftx = (float)tix, fty = (float)tiy;
+// on element j != i: FP32 pair arithmetic on the FP64 midpoint offset (the
+// preconditioner needs no more)
+__device__ void pair_block(const KConst<float> &kf, const Win<float> &wf, const PbGeo &gi, const PbGeo &gj,
+                           float out[3][3]) {
+    float ox = (float)(gi.mid.x - gj.mid.x), oy = (float)(gi.mid.y - gj.mid.y);
+    float tjx = gj.t.x, tjy = gj.t.y, a = gj.t.z, njx = -tjy, njy = tjx;
+    float z1x = ox + a * tjx, z1y = oy + a * tjy, z2x = ox - a * tjx, z2y = oy - a * tjy;
     for (int c = 0; c < 2; ++c) {
         float Dx = c == 0 ? tjx : njx, Dy = c == 0 ? tjy : njy;
         float g[4] = {0, 0, 0, 0};
         disl_field<float>(kf, z1x, z1y, Dx, Dy, wf, 1.f, g);
         disl_field<float>(kf, z2x, z2y, Dx, Dy, wf, -1.f, g);
         float ss, sn;
-        to_local<float>(ftx, fty, g, ss, sn);
+        to_local<float>(gi.t.x, gi.t.y, g, ss, sn);
         out[0][c] = ss; out[1][c] = sn; out[2][c] = g[3];
     }
     // fluid source: 8-point Gauss rule of the point kernel along element j
     float g[4] = {0, 0, 0, 0};
-    float a = (float)(0.5 * Lj), ox = (float)(mx - 0.5 * (cx + dx)), oy = (float)(my - 0.5 * (cy + dy));
+#pragma unroll 1
     for (int q = 0; q < 8; ++q) {
         float s = (float)c_gl8x[q] * a, wt = (float)c_gl8w[q] * a;
         float zx = ox - s * tjx, zy = oy - s * tjy;
@@ -67,22 +68,29 @@ __device__ void pair_block(const KConst<float> &kf, const Win<float> &wf, const 
         pot_transient<float>(kf, zx, zy, ir2, 0.f, 0.f, 0.f, wt, wf.g_hi, 4.f * wf.ct_hi, 1.f, g);
     }
     float ss, sn;
-    to_local<float>(ftx, fty, g, ss, sn);
+    to_local<float>(gi.t.x, gi.t.y, g, ss, sn);
     out[0][2] = ss; out[1][2] = sn; out[2][2] = g[3];
 }
 
 // assemble the system block of every preconditioner block:
-// row (rc * m + i), column (cc * m + j), rc, cc < nc; RATE: row 1 = sigma_n + p
-__global__ void k_pb_assemble(KConst<float> kf, Win<float> wf, KConst<double> kd, Win<double> wd, const double *xy,
-                              int64_t N, const int32_t *boff, const int64_t *belem, const int64_t *moff, int nc, int sys,
+// row (rc * m + i), column (cc * m + j), rc, cc < nc; RATE: row 1 = sigma_n + p;
+// the own element from the cached FP64 3x3 blocks of the step
+__global__ void k_pb_assemble(KConst<float> kf, Win<float> wf, const PbGeo *geo, const double *selfblk,
+                              const int32_t *boff, const int64_t *belem, const int64_t *moff, int nc, int sys,
                               float *M) {
     int b = blockIdx.y;
     int m = boff[b + 1] - boff[b];
     int64_t pair = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (pair >= (int64_t)m * m) return;
     int i = (int)(pair / m), j = (int)(pair % m);
+    int64_t ei = belem[boff[b] + i], ej = belem[boff[b] + j];
     float o[3][3];
-    pair_block(kf, wf, kd, wd, xy, N, belem[boff[b] + i], belem[boff[b] + j], o);
+    if (ei == ej) {
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) o[r][c] = (float)selfblk[9 * ei + 3 * r + c];
+    } else {
+        pair_block(kf, wf, geo[ei], geo[ej], o);
+    }
     if (sys == DDM_SYS_RATE)
         for (int c = 0; c < 3; ++c) o[1][c] += o[2][c];
     int n = nc * m;
@@ -91,94 +99,97 @@ __global__ void k_pb_assemble(KConst<float> kf, Win<float> wf, KConst<double> kd
         for (int cc = 0; cc < nc; ++cc) A[(int64_t)(rc * m + i) * n + cc * m + j] = o[rc][cc];
 }
 
-// in-place Gauss-Jordan inversion with partial pivoting, one block per matrix
-__global__ void k_pb_invert(const int32_t *boff, const int64_t *moff, int nc, float *M, int *piv_ws) {
-    __shared__ float sv[PT];
-    __shared__ int si[PT];
-    __shared__ float pivval;
-    __shared__ int pivrow;
-    int b = blockIdx.x;
-    int n = nc * (boff[b + 1] - boff[b]);
-    float *A = M + moff[b];
-    int *perm = piv_ws + (int64_t)boff[b] * 3;     // column swaps to undo (n entries)
+// In-place Gauss-Jordan inversion with partial pivoting, one CTA per
+// matrix held in shared memory (n <= 192: 147 KB).  32 x 32 threads: tx
+// walks the columns, ty the rows, 32 apart.  Row k is the pivot row after
+// the swap; the multipliers of column k are saved before the update.
+constexpr int INV_MAX = 3 * 64;
+__global__ void __launch_bounds__(1024) k_pb_invert(const int32_t *boff, const int64_t *moff, int nc, float *M) {
+    extern __shared__ float A[];
+    __shared__ float colk[INV_MAX];
+    __shared__ int piv[INV_MAX];
+    __shared__ float s_ip;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    const int b = blockIdx.x;
+    const int n = nc * (boff[b + 1] - boff[b]);
+    float *G = M + moff[b];
+    for (int i = tid; i < n * n; i += 1024) A[i] = G[i];
+    __syncthreads();
     for (int k = 0; k < n; ++k) {
-        // pivot search in column k, rows >= k
-        float best = -1.f;
-        int bi = k;
-        for (int r = k + threadIdx.x; r < n; r += PT) {
-            float v = fabsf(A[(int64_t)r * n + k]);
-            if (v > best) { best = v; bi = r; }
-        }
-        sv[threadIdx.x] = best;
-        si[threadIdx.x] = bi;
-        __syncthreads();
-        for (int o = PT / 2; o > 0; o >>= 1) {
-            if (threadIdx.x < o && sv[threadIdx.x + o] > sv[threadIdx.x]) {
-                sv[threadIdx.x] = sv[threadIdx.x + o];
-                si[threadIdx.x] = si[threadIdx.x + o];
+        if (ty == 0) {                        // pivot: largest |A[r][k]|, r >= k
+            float best = -1.f;
+            int bi = k;
+            for (int r = k + tx; r < n; r += 32) {
+                float v = fabsf(A[r * n + k]);
+                if (v > best) { best = v; bi = r; }
             }
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            pivrow = si[0];
-            perm[k] = pivrow;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                float ob = __shfl_xor_sync(0xFFFFFFFFu, best, o);
+                int oi = __shfl_xor_sync(0xFFFFFFFFu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (tx == 0) piv[k] = bi;
         }
         __syncthreads();
-        int pr = pivrow;
+        const int pr = piv[k];
         if (pr != k)
-            for (int c = threadIdx.x; c < n; c += PT) {
-                float t = A[(int64_t)k * n + c];
-                A[(int64_t)k * n + c] = A[(int64_t)pr * n + c];
-                A[(int64_t)pr * n + c] = t;
+            for (int c = tid; c < n; c += 1024) {
+                float t = A[k * n + c];
+                A[k * n + c] = A[pr * n + c];
+                A[pr * n + c] = t;
             }
         __syncthreads();
-        if (threadIdx.x == 0) pivval = A[(int64_t)k * n + k];
-        __syncthreads();
-        float ip = pivval != 0.f ? 1.f / pivval : 0.f;
-        // row k: scale, with the pivot position holding the inverse pivot
-        for (int c = threadIdx.x; c < n; c += PT)
-            A[(int64_t)k * n + c] = (c == k) ? ip : A[(int64_t)k * n + c] * ip;
-        __syncthreads();
-        // eliminate column k from the other rows
-        for (int64_t idx = threadIdx.x; idx < (int64_t)n * n; idx += PT) {
-            int r = (int)(idx / n), c = (int)(idx % n);
-            if (r == k || c == k) continue;
-            A[idx] -= A[(int64_t)r * n + k] * A[(int64_t)k * n + c];
+        if (tid == 0) {
+            float p = A[k * n + k];
+            s_ip = p != 0.f ? 1.f / p : 0.f;
         }
+        for (int r = tid; r < n; r += 1024) colk[r] = A[r * n + k];
         __syncthreads();
-        for (int r = threadIdx.x; r < n; r += PT)
-            if (r != k) A[(int64_t)r * n + k] = -A[(int64_t)r * n + k] * ip;
+        const float ip = s_ip;
+        for (int c = tid; c < n; c += 1024) A[k * n + c] = (c == k) ? ip : A[k * n + c] * ip;
+        __syncthreads();
+        for (int r = ty; r < n; r += 32) {
+            if (r == k) continue;
+            const float f = colk[r];
+            for (int c = tx; c < n; c += 32)
+                A[r * n + c] = (c == k) ? -f * ip : A[r * n + c] - f * A[k * n + c];
+        }
         __syncthreads();
     }
     // undo the row interchanges as column swaps, in reverse order
     for (int k = n - 1; k >= 0; --k) {
-        int pr = perm[k];
+        const int pr = piv[k];
         if (pr != k)
-            for (int r = threadIdx.x; r < n; r += PT) {
-                float t = A[(int64_t)r * n + k];
-                A[(int64_t)r * n + k] = A[(int64_t)r * n + pr];
-                A[(int64_t)r * n + pr] = t;
+            for (int r = tid; r < n; r += 1024) {
+                float t = A[r * n + k];
+                A[r * n + k] = A[r * n + pr];
+                A[r * n + pr] = t;
             }
         __syncthreads();
     }
+    for (int i = tid; i < n * n; i += 1024) G[i] = A[i];
 }
 
-// z (3N layout, caller order) = Minv v (v in the system layout nc x N);
-// the unknown blocks beyond nc are set to zero
+// z (3N layout, caller order) = Minv v (v in the system layout nc x N); one
+// warp per row, lanes along the row (coalesced); the unknown blocks beyond
+// nc are set to zero
 __global__ void k_pb_apply(const int32_t *boff, const int64_t *belem, const int64_t *moff, int nc, const float *Minv,
                            const double *v, int64_t N, double *z, int zero_rest) {
-    extern __shared__ float svf[];
-    float *sv = svf;
-    int b = blockIdx.x;
-    int m = boff[b + 1] - boff[b], n = nc * m;
+    __shared__ float sv[INV_MAX];
+    const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int m = boff[b + 1] - boff[b], n = nc * m;
     const int64_t *el = belem + boff[b];
     for (int c = threadIdx.x; c < n; c += blockDim.x) sv[c] = (float)v[(c / m) * N + el[c % m]];
     __syncthreads();
     const float *A = Minv + moff[b];
-    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    for (int r = warp; r < n; r += nw) {
+        const float *Ar = A + (int64_t)r * n;
         float s = 0.f;
-        for (int c = 0; c < n; ++c) s += A[(int64_t)r * n + c] * sv[c];
-        z[(r / m) * N + el[r % m]] = (double)s;
+        for (int c = lane; c < n; c += 32) s = fmaf(Ar[c], sv[c], s);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+        if (lane == 0) z[(r / m) * N + el[r % m]] = (double)s;
     }
     if (zero_rest && nc < 3)
         for (int e = threadIdx.x; e < m; e += blockDim.x) z[2 * N + el[e]] = 0.0;
@@ -199,15 +210,26 @@ ddm_status pb_prepare(ddm_ctx *ctx, ddm_tree *t, double dt, int sys, cudaStream_
     w.g_lo = 0.0;
     w.elastic = 1;
     Win<float> wf{(float)w.ct_hi, 0.f, (float)w.g_hi, 0.f, 1};
+    ddm_status st = self_blocks(ctx, t, dt, s);   // own elements, FP64, cached per dt
+    if (st) return st;
+    PbGeo *geo = nullptr;
+    DDM_CUDA_TRY(ctx, dalloc(&geo, (size_t)t->n * sizeof(PbGeo), s));
+    k_pb_geom<<<(unsigned)((t->n + 255) / 256), 256, 0, s>>>(t->xy_caller, t->n, geo);
     int64_t mm = (int64_t)t->pb_max * t->pb_max;
     dim3 g((unsigned)((mm + 127) / 128), (unsigned)t->n_pblk);
-    k_pb_assemble<<<g, 128, 0, s>>>(ctx->kf, wf, ctx->kd, w, t->xy_caller, t->n, t->pb_off, t->pb_elem, t->pb_moff,
-                                    nc, sys, t->pb_inv);
-    int *piv = nullptr;
-    DDM_CUDA_TRY(ctx, dalloc(&piv, (size_t)3 * t->n * sizeof(int), s));
-    k_pb_invert<<<(unsigned)t->n_pblk, PT, 0, s>>>(t->pb_off, t->pb_moff, nc, t->pb_inv, piv);
-    prof_end(ctx, 8, 2);
-    dfree(piv, s);
+    k_pb_assemble<<<g, 128, 0, s>>>(ctx->kf, wf, geo, t->self_blk, t->pb_off, t->pb_elem, t->pb_moff, nc, sys,
+                                    t->pb_inv);
+    const int nmax = nc * t->pb_max;
+    const size_t smem = (size_t)nmax * nmax * sizeof(float);
+    static bool attr[64] = {false};
+    if (!attr[ctx->device & 63]) {
+        DDM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_pb_invert, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)(INV_MAX * INV_MAX * sizeof(float))));
+        attr[ctx->device & 63] = true;
+    }
+    k_pb_invert<<<(unsigned)t->n_pblk, dim3(32, 32), smem, s>>>(t->pb_off, t->pb_moff, nc, t->pb_inv);
+    prof_end(ctx, 8, 4);
+    dfree(geo, s);
     DDM_CUDA_TRY(ctx, cudaGetLastError());
     t->pb_dt = dt;
     t->pb_sys = sys;
@@ -217,8 +239,7 @@ ddm_status pb_prepare(ddm_ctx *ctx, ddm_tree *t, double dt, int sys, cudaStream_
 // z = M^-1 v : v in the system layout (nc blocks of N), z in the 3N layout
 ddm_status pb_apply(ddm_ctx *ctx, ddm_tree *t, int sys, const double *v, double *z, cudaStream_t s) {
     int nc = sys == DDM_SYS_PRESSURE ? 3 : 2;
-    size_t sm = (size_t)nc * t->pb_max * sizeof(float);
-    k_pb_apply<<<(unsigned)t->n_pblk, 128, sm, s>>>(t->pb_off, t->pb_elem, t->pb_moff, nc, t->pb_inv, v, t->n, z, 1);
+    k_pb_apply<<<(unsigned)t->n_pblk, 256, 0, s>>>(t->pb_off, t->pb_elem, t->pb_moff, nc, t->pb_inv, v, t->n, z, 1);
     prof_end(ctx, 8, 1);
     DDM_CUDA_TRY(ctx, cudaGetLastError());
     return DDM_OK;
