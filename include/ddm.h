@@ -168,7 +168,7 @@ typedef struct {
 typedef struct {
     int iterations;
     int restarts;
-    double rel_residual;   /* true residual of the returned x (recomputed) */
+    double rel_residual;   /* residual of the returned x, recomputed with the last residual operator */
     int converged;
 } ddm_gmres_info;
 
@@ -180,14 +180,15 @@ typedef struct {
  * element on no chain is a block of its own.
  * d_rhs: 3N doubles (rows not in the system are ignored).  d_x: 3N doubles,
  * in: initial guess (and the prescribed Dq for 2N systems), out: solution.
- * Mixed precision: Arnoldi steps use the FP32-pair operator; the true
- * residual at every restart (and the convergence test) uses the operator
- * with DDM_MODE_PRECISE; each restart's inner solve runs until its
- * estimated residual is below max(0.3 tol ||b||, 1e-4 of the restart's
- * residual).  A restart that fails to reduce the true residual by 10%
- * switches the inner products to the precise operator as well.  Returns
+ * Precision escalates on stalls: at first every product (Arnoldi steps and
+ * the residual recomputed at each restart) uses the requested mode, and
+ * each restart's inner solve runs to 0.3 tol ||b||.  A restart that fails
+ * to reduce the recomputed residual by 10% switches the residuals (and the
+ * convergence test) to the operator with DDM_MODE_PRECISE, inner solves then
+ * running to max(0.3 tol ||b||, 1e-4 of the restart's residual); a further
+ * such restart makes the Arnoldi products precise as well.  Returns
  * DDM_ENOTCONV (x and info still written) when max_iters is reached or three
- * further restarts in a row fail to reduce the true residual by 10%.
+ * further restarts in a row fail to reduce the residual by 10%.
  * Synchronises the stream (reads the Hessenberg columns back). */
 ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const double *d_rhs,
                            double *d_x, const ddm_gmres_params *prm, ddm_gmres_info *info);

@@ -326,14 +326,16 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
     // graphs: preconditioned operator vin -> w, residual operator (precise) x -> tmp
     int saved = ctx->prof.on;
     ctx->prof.on = 0;
-    std::vector<int> prec(P, 0);      // per problem: inner products with the precise operator
+    // per problem precision level, as in ddm_gmres_solve: 0 requested
+    // products throughout, 1 precise residuals, 2 precise inner products too
+    std::vector<int> level(P, 0);
     auto capture_op = [&](const std::vector<int> &idx) -> ddm_status {
         return capture(ctx, B, &B->g_op, &B->k_op, idx, [&](int p, cudaStream_t ps) -> ddm_status {
             int64_t n = B->N[p];
             ddm_status e = pb_apply(ctx, B->trees[p], sys, B->vin + B->offs[p], B->full + B->off3[p], ps);
             if (e) return e;
             e = op_apply(ctx, B->trees[p], 0.0, dt, B->full + B->off3[p], B->y3 + B->off3[p],
-                         mode | (prec[p] ? DDM_MODE_PRECISE : 0), 0, 1.0, ps);
+                         mode | (level[p] >= 2 ? DDM_MODE_PRECISE : 0), 0, 1.0, ps);
             if (e) return e;
             k_restrict_b<<<nb(n), BT, 0, ps>>>(B->y3 + B->off3[p], n, sys, 1, B->w + B->offs[p]);
             return DDM_OK;
@@ -344,7 +346,7 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
             int64_t n = B->N[p];
             k_copy_to3<<<nb(n), BT, 0, ps>>>(d_x + B->off3[p], n, nc, B->full + B->off3[p]);
             ddm_status e = op_apply(ctx, B->trees[p], 0.0, dt, B->full + B->off3[p], B->y3 + B->off3[p],
-                                    mode | DDM_MODE_PRECISE, 0, 1.0, ps);
+                                    mode | (level[p] >= 1 ? DDM_MODE_PRECISE : 0), 0, 1.0, ps);
             if (e) return e;
             k_restrict_b<<<nb(n), BT, 0, ps>>>(B->y3 + B->off3[p], n, sys, 1, B->tmp + B->offs[p]);
             return DDM_OK;
@@ -392,7 +394,7 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
     std::vector<int> jend(P);
     int total = 0;
     while (true) {
-        // true residuals (precise operator): tmp = A x, w = A x - b
+        // residuals (operator of each problem's level): tmp = A x, w = A x - b
         DDM_CUDA_TRY(ctx, cudaGraphLaunch(B->g_res, s));
         prof_end(ctx, 6, (int)B->k_res);
         DDM_CUDA_TRY(ctx, cudaMemcpyAsync(B->w, B->tmp, L * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -400,12 +402,17 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
         if ((st = seg_norms(B->w, beta))) return st;
         int nact = 0;
         bool reprec = false;
+        std::vector<int> remeasure(P, 0);   // switched to precise residuals: no cycle until re-measured
         for (int p = 0; p < P; ++p) {
             if (!active[p]) continue;
             rel[p] = beta[p] / bn[p];
             if (rel[p] < Pm.tol) { conv[p] = 1; active[p] = 0; continue; }
             if (rel[p] < 0.9 * best[p]) { best[p] = rel[p]; stall[p] = 0; }
-            else if (!prec[p]) { prec[p] = 1; stall[p] = 0; reprec = true; }
+            else if (level[p] < 2) {
+                if (++level[p] == 1) { best[p] = 1e300; remeasure[p] = 1; }
+                stall[p] = 0;
+                reprec = true;
+            }
             else if (++stall[p] >= 3) { active[p] = 0; continue; }
             if (iters[p] >= Pm.max_iters) { active[p] = 0; continue; }
             ++nact;
@@ -431,9 +438,11 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
         for (int p = 0; p < P; ++p) {
             gv[(size_t)p * (m + 1)] = active[p] ? beta[p] : 0.0;
             jend[p] = 0;
-            inner[p] = std::max(0.3 * Pm.tol * bn[p], 1e-4 * beta[p]);
+            inner[p] = level[p] == 0 ? 0.3 * Pm.tol * bn[p] : std::max(0.3 * Pm.tol * bn[p], 1e-4 * beta[p]);
         }
         std::vector<int> live = active;
+        for (int p = 0; p < P; ++p)
+            if (remeasure[p]) live[p] = 0;
         int j = 0;
         for (; j < m; ++j) {
             DDM_CUDA_TRY(ctx, cudaMemcpyAsync(B->vin, B->V + (int64_t)j * L, L * sizeof(double), cudaMemcpyDeviceToDevice, s));
