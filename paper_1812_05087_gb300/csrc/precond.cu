@@ -183,13 +183,25 @@ __global__ void k_pb_apply(const int32_t *boff, const int64_t *belem, const int6
     for (int c = threadIdx.x; c < n; c += blockDim.x) sv[c] = (float)v[(c / m) * N + el[c % m]];
     __syncthreads();
     const float *A = Minv + moff[b];
-    for (int r = warp; r < n; r += nw) {
-        const float *Ar = A + (int64_t)r * n;
-        float s = 0.f;
-        for (int c = lane; c < n; c += 32) s = fmaf(Ar[c], sv[c], s);
+    // two rows per warp step, all loads of both rows issued up front
+    for (int r = 2 * warp; r < n; r += 2 * nw) {
+        const float *A0 = A + (int64_t)r * n;
+        const bool two = r + 1 < n;
+        const float *A1 = two ? A0 + n : A0;
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll 6
+        for (int c = lane; c < n; c += 32) {
+            const float v = sv[c];
+            s0 = fmaf(A0[c], v, s0);
+            s1 = fmaf(A1[c], v, s1);
+        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
-        if (lane == 0) z[(r / m) * N + el[r % m]] = (double)s;
+        for (int o = 16; o > 0; o >>= 1) {
+            s0 += __shfl_xor_sync(0xFFFFFFFFu, s0, o);
+            s1 += __shfl_xor_sync(0xFFFFFFFFu, s1, o);
+        }
+        if (lane == 0) z[(r / m) * N + el[r % m]] = (double)s0;
+        if (lane == 1 && two) z[((r + 1) / m) * N + el[(r + 1) % m]] = (double)s1;
     }
     if (zero_rest && nc < 3)
         for (int e = threadIdx.x; e < m; e += blockDim.x) z[2 * N + el[e]] = 0.0;
@@ -239,7 +251,7 @@ ddm_status pb_prepare(ddm_ctx *ctx, ddm_tree *t, double dt, int sys, cudaStream_
 // z = M^-1 v : v in the system layout (nc blocks of N), z in the 3N layout
 ddm_status pb_apply(ddm_ctx *ctx, ddm_tree *t, int sys, const double *v, double *z, cudaStream_t s) {
     int nc = sys == DDM_SYS_PRESSURE ? 3 : 2;
-    k_pb_apply<<<(unsigned)t->n_pblk, 256, 0, s>>>(t->pb_off, t->pb_elem, t->pb_moff, nc, t->pb_inv, v, t->n, z, 1);
+    k_pb_apply<<<(unsigned)t->n_pblk, 512, 0, s>>>(t->pb_off, t->pb_elem, t->pb_moff, nc, t->pb_inv, v, t->n, z, 1);
     prof_end(ctx, 8, 1);
     DDM_CUDA_TRY(ctx, cudaGetLastError());
     return DDM_OK;

@@ -8,7 +8,6 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <map>
 
 #include "internal.h"
 
@@ -704,15 +703,31 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
         for (int64_t e = 0; e < n; ++e)
             lmin = std::min(lmin, hypot(hxy[2 * n + e] - hxy[e], hxy[3 * n + e] - hxy[n + e]));
         double q = 1e-6 * lmin;
-        auto key = [&](double x, double y) { return std::make_pair((long long)llround(x / q), (long long)llround(y / q)); };
-        std::map<std::pair<long long, long long>, int64_t> starts;
-        for (int64_t e = 0; e < n; ++e) starts[key(hxy[e], hxy[n + e])] = e;
+        // start points in an open-addressing hash table (quantised coordinates)
+        size_t cap = 1;
+        while (cap < 2 * (size_t)n) cap <<= 1;
+        std::vector<int64_t> slot(cap, -1);
+        std::vector<long long> skx(cap), sky(cap);
+        auto hidx = [&](long long kx, long long ky) {
+            uint64_t h = (uint64_t)kx * 0x9E3779B97F4A7C15ull ^ ((uint64_t)ky + 0x632BE59BD9B4E019ull) * 0xC2B2AE3D27D4EB4Full;
+            return (size_t)((h ^ (h >> 29)) & (cap - 1));
+        };
+        auto qz = [&](double v) { return (long long)llround(v / q); };
+        for (int64_t e = 0; e < n; ++e) {          // a repeated start point keeps the last element
+            long long kx = qz(hxy[e]), ky = qz(hxy[n + e]);
+            size_t i = hidx(kx, ky);
+            while (slot[i] >= 0 && !(skx[i] == kx && sky[i] == ky)) i = (i + 1) & (cap - 1);
+            slot[i] = e; skx[i] = kx; sky[i] = ky;
+        }
         std::vector<int64_t> next(n, -1), prevc(n, 0);
         for (int64_t e = 0; e < n; ++e) {
-            auto it = starts.find(key(hxy[2 * n + e], hxy[3 * n + e]));
-            if (it != starts.end() && it->second != e && prevc[it->second] == 0) {
-                next[e] = it->second;
-                prevc[it->second] = 1;
+            long long kx = qz(hxy[2 * n + e]), ky = qz(hxy[3 * n + e]);
+            size_t i = hidx(kx, ky);
+            while (slot[i] >= 0 && !(skx[i] == kx && sky[i] == ky)) i = (i + 1) & (cap - 1);
+            int64_t f = slot[i];
+            if (f >= 0 && f != e && prevc[f] == 0) {
+                next[e] = f;
+                prevc[f] = 1;
             }
         }
         std::vector<int32_t> boff{0};
