@@ -655,6 +655,20 @@ __device__ __forceinline__ void far_pair(const KConst<float> &k, const KConst<do
     }
     float nx = -ty, ny = tx;
     float Pxx = Dx * nx, Pyy = Dy * ny, Pxy = 0.5f * (Dx * ny + Dy * nx);
+    // every Gauss point at u > 30 on both sides (the hi side has the smaller
+    // u): the rational form of the kernel (pot_bigu)
+    float rmin = sqrtf(r2) - a;
+    if (rmin * rmin * w.g_hi > Big<float>::U) {
+        const float d4ct = 4.f * (w.ct_hi - w.ct_lo);
+#pragma unroll 1
+        for (int g = 0; g < ng; ++g) {
+            float xi, wt;
+            far_node(ng, g, xi, wt);
+            float sg = xi * a, wg = wt * a;
+            pot_bigu(k, dx - sg * tx, dy - sg * ty, wg * Pxx, wg * Pyy, wg * Pxy, wg * q, w.elastic, d4ct, acc);
+        }
+        return;
+    }
 #pragma unroll 1
     for (int g = 0; g < ng; ++g) {
         float xi, wt;

@@ -249,6 +249,44 @@ DEV void pot_kernel(const KConst<T> &k, T x, T y, T Pxx, T Pyy, T Pxy, T q, cons
                          sd ? T(-1) : T(1), acc);
 }
 
+// Point kernel where u = r^2/(4ct) > Big<float>::U on every side of the
+// window, so that e^-u and E1(u) vanish in FP32 (the general path above
+// takes the same branches).  Expanding pot_kernel + pot_transient with
+// F = 1/u, F' = -1/u^2, F'' = 2/u^3, E1 = 0 gives exactly
+//   drained elastic + transient
+//     = [elastic window] * (undrained elastic: C_el -> C_el + 2 G2 K2,
+//                           pressure aS Ce ((Pxx-Pyy)(x^2-y^2) + 4 Pxy x y)/r^4)
+//       + d4ct * 6 G2 K2 / r^8 * ( Q, -Q, -2 R, 0 )
+//       + fluid source: -eta q/(4 pi kappa) d4ct / r^4 * (x^2-y^2, y^2-x^2, 2xy, 0)
+// with Q = (Pxx-Pyy)(x^4 - 6x^2y^2 + y^4) + 8 Pxy xy (x^2-y^2),
+//      R = Pxy (x^4 - 6x^2y^2 + y^4) - 2 (Pxx-Pyy) xy (x^2-y^2),
+// d4ct = 4c (t_hi - t_lo) (t_lo = 0 for the elastic window): the t-free
+// transient terms of the two sides cancel in a time element.
+DEV void pot_bigu(const KConst<float> &k, float x, float y, float Pxx, float Pyy, float Pxy, float q, int elastic,
+                  float d4ct, float acc[4]) {
+    float x2 = x * x, y2 = y * y, xy = x * y;
+    float ir2 = __fdividef(1.f, x2 + y2), ir4 = ir2 * ir2;
+    float d = x2 - y2, dPm = Pxx - Pyy;
+    if (elastic) {
+        float C = (k.Cel + 2.f * k.G2 * k.K2) * ir4 * ir2;
+        float A1 = x2 * x2, B1 = y2 * y2, Cm = x2 * y2;
+        acc[0] -= C * (Pxx * (3.f * A1 - 6.f * Cm - B1) + Pyy * (-A1 + 6.f * Cm - B1) +
+                       Pxy * xy * (12.f * x2 - 4.f * y2));
+        acc[1] += C * (Pxx * (A1 - 6.f * Cm + B1) + Pyy * (A1 + 6.f * Cm - 3.f * B1) +
+                       Pxy * xy * (4.f * x2 - 12.f * y2));
+        acc[2] += C * (Pxx * xy * (-6.f * x2 + 2.f * y2) + 2.f * Pxy * (A1 - 6.f * Cm + B1) +
+                       Pyy * xy * (2.f * x2 - 6.f * y2));
+        acc[3] += k.aS * k.Ce * (dPm * d + 4.f * Pxy * xy) * ir4;
+    }
+    float c4 = d * d - 4.f * x2 * y2, s4 = 4.f * xy * d;
+    float f = 6.f * k.G2 * k.K2 * d4ct * ir4 * ir4;
+    float Q = dPm * c4 + 2.f * Pxy * s4, R = Pxy * c4 - 0.5f * dPm * s4;
+    float fq = -k.eta * k.i4pk * q * d4ct * ir4;
+    acc[0] += f * Q + fq * d;
+    acc[1] -= f * Q + fq * d;
+    acc[2] += fq * 2.f * xy - 2.f * f * R;
+}
+
 // ---------------------------------------------------------------------------
 // half-line DD (edge dislocation), DD vector (Dx, Dy)
 // ---------------------------------------------------------------------------
