@@ -788,6 +788,15 @@ __global__ void __launch_bounds__(NEAR_T, 4) k_near(KConst<float> k, KConst<doub
     const float4 rt = grel[ti];
     const float mx = 0.5f * (rt.x + rt.z), my = 0.5f * (rt.y + rt.w);
     const int S = spre[wid][nb];
+    // lanes 0, 1, 2 write sigma_s, sigma_n, p at the end: fetch what they need now
+    int64_t eout = 0;
+    float4 fout = make_float4(0.f, 0.f, 0.f, 0.f);
+    double yold = 0.0;
+    if (lane < 3) {
+        eout = perm[ti];
+        fout = frame[ti];
+        yold = y[lane * N + eout];
+    }
     float acc[4] = {0, 0, 0, 0};
     double accd[4] = {0, 0, 0, 0};
     int qn = 0, slot = 0;
@@ -866,29 +875,37 @@ __global__ void __launch_bounds__(NEAR_T, 4) k_near(KConst<float> k, KConst<doub
         hl[c][1] = 0.f;
     }
     if (use_far) {
-        // L2P: lane handles nodes m = lane, lane + 32, ...
+        // L2P.  Barycentric terms: lane j < n takes x node j, lane 16 + j
+        // y node j; the sums are reduced within each half-warp, and every
+        // lane then fetches the two cardinals of its nodes m = lane,
+        // lane + 32, ... by shuffle.
         const float *cheb = c_gl.cheb[(n >> 1) - 1], *bw = c_gl.bw[(n >> 1) - 1];
         const float hL = 0.5f * wL;
-        const float xh = __fdividef(mx, hL), yh = __fdividef(my, hL);
-        const int n2 = n * n;
-        float sx = 0.f, sy = 0.f;
-        int hx = -1, hy = -1;
-        for (int j = 0; j < n; ++j) {             // barycentric denominators
-            float dxj = xh - cheb[j], dyj = yh - cheb[j];
-            if (fabsf(dxj) < 1e-7f) hx = j;
-            if (fabsf(dyj) < 1e-7f) hy = j;
-            sx += __fdividef(bw[j], dxj);
-            sy += __fdividef(bw[j], dyj);
+        const int j = lane & 15;
+        const bool isy = lane >= 16;
+        float tv = 0.f;
+        bool hit = false;
+        if (j < n) {
+            float d = __fdividef(isy ? my : mx, hL) - cheb[j];
+            hit = fabsf(d) < 1e-7f;
+            tv = hit ? 0.f : __fdividef(bw[j], d);
         }
-        const float isx = __fdividef(1.f, sx), isy = __fdividef(1.f, sy);
+        float sum = tv;
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
+        const unsigned hm = __ballot_sync(FULL, hit);
+        const bool half_hit = isy ? (hm >> 16) != 0u : (hm & 0xFFFFu) != 0u;
+        const float card = half_hit ? (hit ? 1.f : 0.f) : tv * __fdividef(1.f, sum);
+        const int n2 = n * n;
         const float *Fc = F + (loff + leaf) * 4 * n2;
         float f4[4] = {0, 0, 0, 0};
-        for (int m = lane; m < n2; m += 32) {
-            int a = m / n, bb = m - a * n;
-            float la = hx >= 0 ? (a == hx ? 1.f : 0.f) : __fdividef(bw[a], xh - cheb[a]) * isx;
-            float lb = hy >= 0 ? (bb == hy ? 1.f : 0.f) : __fdividef(bw[bb], yh - cheb[bb]) * isy;
-            float v = la * lb;
-            f4[0] += v * Fc[m]; f4[1] += v * Fc[n2 + m]; f4[2] += v * Fc[2 * n2 + m]; f4[3] += v * Fc[3 * n2 + m];
+        for (int base = 0; base < n2; base += 32) {
+            const int m = base + lane, mc = m < n2 ? m : n2 - 1;
+            const int a = mc / n, bb = mc - a * n;
+            const float v = __shfl_sync(FULL, card, a) * __shfl_sync(FULL, card, 16 + bb);
+            if (m < n2) {
+                f4[0] += v * Fc[m]; f4[1] += v * Fc[n2 + m]; f4[2] += v * Fc[2 * n2 + m]; f4[3] += v * Fc[3 * n2 + m];
+            }
         }
 #pragma unroll
         for (int c = 0; c < 4; ++c) two_sum_add(hl[c][0], hl[c][1], f4[c], 0.f);
@@ -902,7 +919,7 @@ __global__ void __launch_bounds__(NEAR_T, 4) k_near(KConst<float> k, KConst<doub
     // lanes 0, 1, 2 write sigma_s, sigma_n, p; the rotation to the target
     // frame is applied to both halves of each pair
     if (lane >= 3) return;
-    const float4 f = frame[ti];
+    const float4 f = fout;
     const float nx = -f.y, ny = f.x;
     float vh, vl;
     double vd = 0.0;
@@ -918,8 +935,7 @@ __global__ void __launch_bounds__(NEAR_T, 4) k_near(KConst<float> k, KConst<doub
         vl = cxx * hl[0][1] + cyy * hl[1][1] + cxy * hl[2][1];
         if (PRECISE) vd = (double)cxx * accd[0] + (double)cyy * accd[1] + (double)cxy * accd[2];
     }
-    const int64_t e = perm[ti];
-    y[lane * N + e] += scale * (((double)vh + (double)vl) + vd);
+    y[lane * N + eout] = yold + scale * (((double)vh + (double)vl) + vd);
 }
 
 // -------------------------------------------------------------------- dense
