@@ -126,7 +126,7 @@ __device__ __forceinline__ void cardinal_col(float x, float *col, int stride) {
     for (int j = 0; j < N; ++j) col[j * stride] = hit >= 0 ? (j == hit ? 1.f : 0.f) : v[j] * is;
 }
 
-constexpr int UP_T = 128;
+constexpr int UP_T = 256, UP_W = UP_T / 32;
 // shared-memory floats of the fused passes: the P2M staging (cardinals of
 // 128 points in x and y, 128 point weights) and the M2M staging (weights of
 // up to 4 children and their half-transferred copies) share one buffer
@@ -135,7 +135,8 @@ struct UpSmem {
     static constexpr int N2 = N * N, NOUT = 4 * N2, SXS = UP_T + 1;
     static constexpr int P2M = 2 * N * SXS + 4 * UP_T;
     static constexpr int M2M = 8 * NOUT;
-    static constexpr int SIZE = P2M > M2M ? P2M : M2M;
+    static constexpr int RED = UP_W * NOUT;
+    static constexpr int SIZE = (P2M > M2M ? P2M : M2M) > RED ? (P2M > M2M ? P2M : M2M) : RED;
 };
 
 // One block per leaf: charges and own-element terms of the leaf's elements,
@@ -150,7 +151,7 @@ struct UpSmem {
 // pass.
 //
 // P2M: lane owns node entries (a, b) = lane + 32 j and all 4 components;
-// the 4 warps take every 4th point and are summed at the end.
+// the UP_W warps take every UP_W-th point and are summed at the end.
 template <int N>
 __global__ void __launch_bounds__(UP_T) k_up(const int32_t *cstart, const int32_t *cend, int64_t loff, int64_t off3,
                                              const int32_t *cix, const int32_t *ciy, const int32_t *parent,
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(UP_T) k_up(const int32_t *cstart, const int32_
         }
         __syncthreads();
         int np = min(UP_T, npts - base);
-        for (int q = warp; q < np; q += 4) {
+        for (int q = warp; q < np; q += UP_W) {
             float4 w4 = wd[q];
 #pragma unroll
             for (int j = 0; j < NE; ++j) {
@@ -209,7 +210,7 @@ __global__ void __launch_bounds__(UP_T) k_up(const int32_t *cstart, const int32_
         }
         __syncthreads();
     }
-    // sum the 4 warps' partial weights (staging reused)
+    // sum the warps' partial weights (staging reused)
     float *red = sm;
 #pragma unroll
     for (int j = 0; j < NE; ++j) {
@@ -223,7 +224,12 @@ __global__ void __launch_bounds__(UP_T) k_up(const int32_t *cstart, const int32_
 #pragma unroll
     for (int k = 0; k < KO; ++k) {
         int o = tid + k * UP_T;
-        if (o < NOUT) Wc[o] = red[o] + red[NOUT + o] + red[2 * NOUT + o] + red[3 * NOUT + o];
+        if (o < NOUT) {
+            float v = 0.f;
+#pragma unroll
+            for (int w = 0; w < UP_W; ++w) v += red[w * NOUT + o];
+            Wc[o] = v;
+        }
     }
     float *sw = sm, *tmp = sm + 4 * NOUT;
     int64_t cur = leaf;
@@ -282,10 +288,11 @@ __global__ void __launch_bounds__(UP_T) k_up(const int32_t *cstart, const int32_
 // f <- S_n(xbar^child, xbar^parent) f + g^child (paper Sec. 3.3 L2L), and
 // the leaf's complete local expansion replaces its own M2L sum.  The
 // ancestors' values are only read, so leaves sharing them need no order.
+constexpr int L2L_T = 128;
 template <int N>
-__global__ void __launch_bounds__(UP_T) k_down(int64_t loff, int L, const int32_t *cix, const int32_t *ciy,
+__global__ void __launch_bounds__(L2L_T) k_down(int64_t loff, int L, const int32_t *cix, const int32_t *ciy,
                                                const int32_t *parent, const float *T, float *F) {
-    constexpr int N2 = N * N, NOUT = 4 * N2, KO = (NOUT + UP_T - 1) / UP_T;
+    constexpr int N2 = N * N, NOUT = 4 * N2, KO = (NOUT + L2L_T - 1) / L2L_T;
     __shared__ float sT[2 * N2], sf[NOUT], tmp[NOUT];
     __shared__ int64_t anc[DDM_MAX_LEVELS + 1];
     __shared__ int squad[DDM_MAX_LEVELS + 1];
@@ -299,19 +306,19 @@ __global__ void __launch_bounds__(UP_T) k_down(int64_t loff, int L, const int32_
             c = parent[c];
         }
     }
-    for (int i = tid; i < 2 * N2; i += UP_T) sT[i] = T[i];
+    for (int i = tid; i < 2 * N2; i += L2L_T) sT[i] = T[i];
     __syncthreads();
     const float *F2 = F + anc[2] * NOUT;
-    for (int i = tid; i < NOUT; i += UP_T) sf[i] = F2[i];
+    for (int i = tid; i < NOUT; i += L2L_T) sf[i] = F2[i];
     __syncthreads();
     for (int l = 3; l <= L; ++l) {
         const float *Fc = F + anc[l] * NOUT;
         float g[KO];                          // this level's M2L sums, fetched early
 #pragma unroll
-        for (int k = 0; k < KO; ++k) g[k] = (tid + k * UP_T < NOUT) ? Fc[tid + k * UP_T] : 0.f;
+        for (int k = 0; k < KO; ++k) g[k] = (tid + k * L2L_T < NOUT) ? Fc[tid + k * L2L_T] : 0.f;
         const float *Tx = sT + ((squad[l] & 1) ? N2 : 0), *Ty = sT + ((squad[l] & 2) ? N2 : 0);
         // tmp[c][a'][b] = sum_a Tx[a][a'] f[c][a][b]
-        for (int i = tid; i < NOUT; i += UP_T) {
+        for (int i = tid; i < NOUT; i += L2L_T) {
             int c = i / N2, a = (i / N) % N, b = i % N;
             const float *src = sf + c * N2 + b;
             float s = 0.f;
@@ -323,7 +330,7 @@ __global__ void __launch_bounds__(UP_T) k_down(int64_t loff, int L, const int32_
         // f[c][a'][b'] = sum_b Ty[b][b'] tmp[c][a'][b] + g
 #pragma unroll
         for (int k = 0; k < KO; ++k) {
-            int o = tid + k * UP_T;
+            int o = tid + k * L2L_T;
             if (o < NOUT) {
                 int c = o / N2, a = (o / N) % N, b = o % N;
                 const float *tc = tmp + c * N2 + a * N;
@@ -336,7 +343,7 @@ __global__ void __launch_bounds__(UP_T) k_down(int64_t loff, int L, const int32_
         __syncthreads();
     }
     float *Fl = F + leaf * NOUT;
-    for (int i = tid; i < NOUT; i += UP_T) Fl[i] = sf[i];
+    for (int i = tid; i < NOUT; i += L2L_T) Fl[i] = sf[i];
 }
 
 // ---------------------------------------------------------------------- M2L
@@ -1173,7 +1180,7 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
         if (L >= 3) {
             prof_begin(ctx, 5);
 #define DDM_DOWN(NN)                                                                                        \
-    k_down<NN><<<(unsigned)nleaf, UP_T, 0, s>>>(loff, L, t->cell_ix, t->cell_iy, t->cell_parent, ctx->cheb_T, t->Fl)
+    k_down<NN><<<(unsigned)nleaf, L2L_T, 0, s>>>(loff, L, t->cell_ix, t->cell_iy, t->cell_parent, ctx->cheb_T, t->Fl)
             DDM_CHEB_SWITCH(n, DDM_DOWN);
 #undef DDM_DOWN
             prof_end(ctx, 5, 1);
