@@ -222,6 +222,7 @@ void ddm_destroy(ddm_ctx *ctx) {
     if (!ctx) return;
     if (ctx->cheb_T) cudaFree(ctx->cheb_T);
     if (ctx->d_err) cudaFree(ctx->d_err);
+    if (ctx->h_pin) cudaFreeHost(ctx->h_pin);
     if (ctx->gm) { ctx->gm->release(); delete ctx->gm; }
     delete ctx;
 }

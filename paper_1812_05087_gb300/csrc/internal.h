@@ -127,6 +127,8 @@ struct ddm_ctx {
     GmresWork *gm;
     Prof prof;
     int *d_err;                // device word raised by a kernel whose bounded wait expired
+    double *h_pin = nullptr;   // pinned host staging (tree build: element end points)
+    int64_t h_pin_cap = 0;
 };
 
 // begin/end a profiled stage (no-ops unless profiling is on); count launches

@@ -9,6 +9,8 @@
 #include <cstdio>
 #include <cstring>
 
+#include <thread>
+
 #include "internal.h"
 
 namespace {
@@ -107,6 +109,30 @@ struct Scratch {      // build-time buffers, freed (stream-ordered) at the end o
     }
     ~Scratch() { for (void *p : ptrs) dfree(p, st); }
 };
+
+// total of an exclusive scan on the device: out[n-1] + in[n-1]
+__global__ void k_scan_total(const int32_t *in, const int32_t *out, int64_t n, int32_t *total) {
+    *total = n > 0 ? out[n - 1] + in[n - 1] : 0;
+}
+cudaError_t scan_excl(Scratch &S, cudaStream_t st, const int32_t *in, int32_t *out, int64_t n, int32_t *total);
+// exclusive scan whose total stays on the device (no synchronisation)
+cudaError_t scan_excl_dev(Scratch &S, cudaStream_t st, const int32_t *in, int32_t *out, int64_t n,
+                          int32_t *d_total) {
+    int64_t nb = (n + SCAN_BLOCK - 1) / SCAN_BLOCK;
+    if (nb == 0) return cudaMemsetAsync(d_total, 0, sizeof(int32_t), st);
+    int32_t *sums = S.get<int32_t>(nb), *soff = S.get<int32_t>(nb);
+    if (S.err) return S.err;
+    k_scan_tiles<<<nb, SCAN_BLOCK, 0, st>>>(in, out, n, sums); ++tl_launches;
+    if (nb > 1) {
+        int32_t *dummy = S.get<int32_t>(1);
+        if (S.err) return S.err;
+        cudaError_t e = scan_excl_dev(S, st, sums, soff, nb, dummy);
+        if (e) return e;
+        k_scan_add<<<nb, SCAN_BLOCK, 0, st>>>(out, n, soff); ++tl_launches;
+    }
+    k_scan_total<<<1, 1, 0, st>>>(in, out, n, d_total); ++tl_launches;
+    return cudaGetLastError();
+}
 
 // exclusive scan, returns the total (synchronises)
 cudaError_t scan_excl(Scratch &S, cudaStream_t st, const int32_t *in, int32_t *out, int64_t n,
@@ -284,6 +310,35 @@ __device__ int32_t find_key(const uint32_t *ckey, int64_t off, int64_t ncell, ui
     return (lo < ncell && ckey[off + lo] == k) ? (int32_t)lo : -1;
 }
 
+// sum of ncell counts (atomic, into one 64-bit total)
+__global__ void k_sum_range(const int32_t *cnt, int64_t ncell, unsigned long long *total) {
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int v = c < ncell ? cnt[c] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(total, (unsigned long long)v);
+}
+// direct pairs if the cells of this level were the leaves: own elements x
+// elements of the cells sharing a vertex (incl. itself)
+__global__ void k_p2p_estimate(const uint32_t *ckey, const int32_t *cix, const int32_t *ciy, const int32_t *cstart,
+                               const int32_t *cend, int64_t off, int64_t ncell, int side, unsigned long long *total) {
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    unsigned long long v = 0;
+    if (c < ncell) {
+        int ix = cix[off + c], iy = ciy[off + c];
+        long long nb = 0;
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                int jx = ix + dx, jy = iy + dy;
+                if (jx < 0 || jy < 0 || jx >= side || jy >= side) continue;
+                int32_t j = find_key(ckey, off, ncell, spread2(jx) | (spread2(jy) << 1));
+                if (j >= 0) nb += cend[off + j] - cstart[off + j];
+            }
+        v = (unsigned long long)(cend[off + c] - cstart[off + c]) * (unsigned long long)nb;
+    }
+    if (v) atomicAdd(total, v);
+}
+
 // neighbours of each leaf (incl. itself): pass 0 counts, pass 1 fills
 __global__ void k_neigh(const uint32_t *ckey, const int32_t *cix, const int32_t *ciy, int64_t off,
                         int64_t ncell, int side, const int32_t *nboff, int32_t *nbidx, int32_t *cnt) {
@@ -406,6 +461,69 @@ __global__ void k_p2p_count(const int32_t *cstart, const int32_t *cend, int64_t 
         }                                                                           \
     } while (0)
 
+// Preconditioner blocks (host): chains of elements sharing end points, cut
+// into runs of at most 64 elements; elements on no chain are blocks of one.
+struct Chains {
+    std::vector<int32_t> boff{0};
+    std::vector<int64_t> belem;
+};
+static void find_chains(const double *hxy, int64_t n, Chains &out) {
+    std::vector<int32_t> &boff = out.boff;
+    std::vector<int64_t> &belem = out.belem;
+    // end points are matched on a grid of 1e-6 of the shortest element
+    double lmin = 1e300;
+    for (int64_t e = 0; e < n; ++e)
+        lmin = std::min(lmin, hypot(hxy[2 * n + e] - hxy[e], hxy[3 * n + e] - hxy[n + e]));
+    const double q = 1e-6 * lmin;
+    // start points in an open-addressing hash table (quantised coordinates)
+    size_t cap = 1;
+    while (cap < 2 * (size_t)n) cap <<= 1;
+    std::vector<int64_t> slot(cap, -1);
+    std::vector<long long> skx(cap), sky(cap);
+    auto hidx = [&](long long kx, long long ky) {
+        uint64_t h = (uint64_t)kx * 0x9E3779B97F4A7C15ull ^ ((uint64_t)ky + 0x632BE59BD9B4E019ull) * 0xC2B2AE3D27D4EB4Full;
+        return (size_t)((h ^ (h >> 29)) & (cap - 1));
+    };
+    auto qz = [&](double v) { return (long long)llround(v / q); };
+    for (int64_t e = 0; e < n; ++e) {      // a repeated start point keeps the last element
+        long long kx = qz(hxy[e]), ky = qz(hxy[n + e]);
+        size_t i = hidx(kx, ky);
+        while (slot[i] >= 0 && !(skx[i] == kx && sky[i] == ky)) i = (i + 1) & (cap - 1);
+        slot[i] = e;
+        skx[i] = kx;
+        sky[i] = ky;
+    }
+    std::vector<int64_t> next(n, -1), prevc(n, 0);
+    for (int64_t e = 0; e < n; ++e) {
+        long long kx = qz(hxy[2 * n + e]), ky = qz(hxy[3 * n + e]);
+        size_t i = hidx(kx, ky);
+        while (slot[i] >= 0 && !(skx[i] == kx && sky[i] == ky)) i = (i + 1) & (cap - 1);
+        int64_t f = slot[i];
+        if (f >= 0 && f != e && prevc[f] == 0) {
+            next[e] = f;
+            prevc[f] = 1;
+        }
+    }
+    std::vector<char> seen(n, 0);
+    const int BMAX = 64;
+    auto emit_chain = [&](int64_t head) {
+        int cnt = 0;
+        for (int64_t e = head; e >= 0 && !seen[e]; e = next[e]) {
+            seen[e] = 1;
+            belem.push_back(e);
+            if (++cnt == BMAX) {
+                boff.push_back((int32_t)belem.size());
+                cnt = 0;
+            }
+        }
+        if (cnt) boff.push_back((int32_t)belem.size());
+    };
+    for (int64_t e = 0; e < n; ++e)
+        if (!prevc[e]) emit_chain(e);
+    for (int64_t e = 0; e < n; ++e)          // closed loops
+        if (!seen[e]) emit_chain(e);
+}
+
 void tree_free(ddm_tree *t) {
     if (!t) return;
     void *ps[] = {t->mk_work, t->pb_off, t->pb_elem, t->pb_moff, t->pb_inv, t->mk_off, t->mk_pair, t->m2l_ops, t->grp_off, t->grp_leaf, t->perm, t->cell_key, t->cell_ix, t->cell_iy, t->cell_start, t->cell_end, t->cell_parent, t->cell_child0, t->cell_nchild, t->up_cnt,
@@ -446,6 +564,37 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
         lmax = std::max(lmax, -hp[6 * b + 4]); bad = std::max(bad, -hp[6 * b + 5]);
     }
     if (bad > 0) { tree_free(t); return ctx_fail(ctx, DDM_EINVAL, "ddm_build_tree: zero-length or non-finite element"); }
+    // end points to the host (context's pinned buffer) for the chain search,
+    // which runs on a worker thread while the device builds the tree
+    if (ctx->h_pin_cap < 4 * n) {
+        if (ctx->h_pin) cudaFreeHost(ctx->h_pin);
+        ctx->h_pin = nullptr;
+        ctx->h_pin_cap = 0;
+        TRY(cudaMallocHost(&ctx->h_pin, 4 * n * sizeof(double)));
+        ctx->h_pin_cap = 4 * n;
+    }
+    cudaEvent_t xy_ev;
+    TRY(cudaEventCreateWithFlags(&xy_ev, cudaEventDisableTiming));
+    TRY(cudaMemcpyAsync(ctx->h_pin, d_xy, 4 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    TRY(cudaEventRecord(xy_ev, st));
+    Chains chains;
+    bool chain_ok = true;
+    const double *hxy_pin = ctx->h_pin;
+    std::thread chain_th([&chains, &chain_ok, xy_ev, hxy_pin, n]() {
+        if (cudaEventSynchronize(xy_ev) != cudaSuccess) { chain_ok = false; return; }
+        find_chains(hxy_pin, n, chains);
+    });
+    bool chain_th_live = true;
+    // a failing step below must not leave the worker running
+    struct Joiner {
+        std::thread &th;
+        bool &live;
+        cudaEvent_t ev;
+        ~Joiner() {
+            if (live && th.joinable()) th.join();
+            cudaEventDestroy(ev);
+        }
+    } joiner{chain_th, chain_th_live, xy_ev};
     double span = std::max(std::max(mxx - mnx, mxy - mny), 4.0 * lmax);
     double h0 = 0.5 * span * (1.0 + 1e-9) + 1e-300;
     t->cx = 0.5 * (mnx + mxx); t->cy = 0.5 * (mny + mxy); t->h0 = h0;
@@ -482,12 +631,11 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
     TRY(S.err);
     std::vector<int64_t> ncl(L + 1);
     t->lvl_off.assign(L + 2, 0);
-    for (int l = 0; l <= L; ++l) {
+    int32_t *d_ncl = S.get<int32_t>(L + 1);
+    TRY(S.err);
+    for (int l = 0; l <= L; ++l) {       // cell counts of all levels, read back once
         k_flags<<<nbk, TB, 0, st>>>(key, n, 2 * (KEY_LEVELS - l), flag); ++tl_launches;
-        int32_t tot;
-        TRY(scan_excl(S, st, flag, ex, n, &tot));
-        ncl[l] = tot;
-        t->lvl_off[l + 1] = t->lvl_off[l] + tot;
+        TRY(scan_excl_dev(S, st, flag, ex, n, d_ncl + l));
         ecell[l] = S.get<int32_t>(n);
         TRY(S.err);
         TRY(cudaMemcpyAsync(ecell[l], ex, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
@@ -496,6 +644,15 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
         TRY(S.err);
         TRY(cudaMemcpyAsync(fl, flag, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
         ecell.push_back(fl);   // keep alive; index L+1+l
+    }
+    {
+        std::vector<int32_t> h(L + 1);
+        TRY(cudaMemcpyAsync(h.data(), d_ncl, (L + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        TRY(cudaStreamSynchronize(st));
+        for (int l = 0; l <= L; ++l) {
+            ncl[l] = h[l];
+            t->lvl_off[l + 1] = t->lvl_off[l] + h[l];
+        }
     }
     int64_t NC = t->lvl_off[L + 1];
     t->n_cells = NC;
@@ -528,44 +685,36 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
     // pairs.  Costs per unit measured on GB300 for n = 8 (near pair 19.4 ps,
     // interaction pair 3.5 ns scaling with n^4, cell 25 ns).
     if (L >= 3 && ctx->prm.max_depth == 0) {
-        int32_t *ccnt = S.get<int32_t>(NC + 1), *coff = S.get<int32_t>(NC + 1);
-        unsigned long long *pp = S.get<unsigned long long>(1);
+        const int L0 = std::max(2, L - 4), NCAND = L - L0 + 1;
+        int32_t *ccnt = S.get<int32_t>(NC + 1);
+        unsigned long long *dsum = S.get<unsigned long long>(2 * (L + 1));   // M2L pairs per level, near pairs per depth
         TRY(S.err);
-        std::vector<long long> il_lvl(L + 1, 0);
+        TRY(cudaMemsetAsync(dsum, 0, 2 * (L + 1) * sizeof(unsigned long long), st));
         TRY(cudaMemsetAsync(ccnt, 0, (NC + 1) * sizeof(int32_t), st));
         for (int l = 2; l <= L; ++l) {
             int64_t nc = ncl[l];
             k_ilist<<<(nc + TB - 1) / TB, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, t->lvl_off[l], nc, 1 << l,
                                                       nullptr, nullptr, ccnt); ++tl_launches;
+            k_sum_range<<<(nc + TB - 1) / TB, TB, 0, st>>>(ccnt, nc, dsum + l); ++tl_launches;
         }
-        std::vector<int32_t> hc(NC);
-        TRY(cudaMemcpyAsync(hc.data(), ccnt, NC * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        for (int Lc = L0; Lc <= L; ++Lc) {
+            int64_t nc = ncl[Lc];
+            k_p2p_estimate<<<(nc + TB - 1) / TB, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, t->cell_start,
+                                                             t->cell_end, t->lvl_off[Lc], nc, 1 << Lc,
+                                                             dsum + (L + 1) + Lc); ++tl_launches;
+        }
+        std::vector<unsigned long long> hs(2 * (L + 1));
+        TRY(cudaMemcpyAsync(hs.data(), dsum, hs.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
         TRY(cudaStreamSynchronize(st));
-        for (int l = 2; l <= L; ++l)
-            for (int64_t c = t->lvl_off[l]; c < t->lvl_off[l + 1]; ++c) il_lvl[l] += hc[c];
         double nfac = std::pow(ctx->prm.n_cheb / 8.0, 4.0);
         double best = 1e300;
         int bestL = L;
-        for (int Lc = std::max(2, L - 4); Lc <= L; ++Lc) {
-            int64_t nc = ncl[Lc], off = t->lvl_off[Lc];
-            k_neigh<<<(nc + TB - 1) / TB, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, off, nc, 1 << Lc, nullptr,
-                                                      nullptr, ccnt); ++tl_launches;
-            int32_t tot;
-            TRY(scan_excl(S, st, ccnt, coff, nc, &tot));
-            TRY(cudaMemcpyAsync(coff + nc, &tot, sizeof(int32_t), cudaMemcpyHostToDevice, st));
-            int32_t *nbi = S.get<int32_t>(std::max(tot, 1));
-            TRY(S.err);
-            k_neigh<<<(nc + TB - 1) / TB, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, off, nc, 1 << Lc, coff,
-                                                      nbi, nullptr); ++tl_launches;
-            TRY(cudaMemsetAsync(pp, 0, sizeof(unsigned long long), st));
-            k_p2p_count<<<(nc + TB - 1) / TB, TB, 0, st>>>(t->cell_start, t->cell_end, off, nc, coff, nbi, pp); ++tl_launches;
-            unsigned long long hp = 0;
-            TRY(cudaMemcpyAsync(&hp, pp, sizeof(hp), cudaMemcpyDeviceToHost, st));
-            TRY(cudaStreamSynchronize(st));
+        (void)NCAND;
+        for (int Lc = L0; Lc <= L; ++Lc) {
             long long m2l = 0, cells = 0;
-            for (int l = 2; l <= Lc; ++l) m2l += il_lvl[l];
+            for (int l = 2; l <= Lc; ++l) m2l += (long long)hs[l];
             for (int l = 0; l <= Lc; ++l) cells += ncl[l];
-            double cost = 21.5e-12 * (double)hp + 3.5e-9 * nfac * (double)m2l + 25e-9 * (double)cells;
+            double cost = 21.5e-12 * (double)hs[L + 1 + Lc] + 3.5e-9 * nfac * (double)m2l + 25e-9 * (double)cells;
             if (cost < best) { best = cost; bestL = Lc; }
         }
         L = bestL;
@@ -693,63 +842,15 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
         TRY(dalloc(&t->grp_leaf, std::max(gtot, 1) * sizeof(int32_t), st));
         k_groups<<<(ng + 127) / 128, 128, 0, st>>>(t->elem_leaf, n, ng, t->nb_off, t->nb_idx, t->grp_off, t->grp_leaf, nullptr); ++tl_launches;
     }
-    // preconditioner blocks: chains of elements sharing end points (host)
+    // preconditioner blocks: the chain search (host worker thread, started
+    // after the bounding box) is joined here
     {
-        std::vector<double> hxy(4 * n);
-        TRY(cudaMemcpyAsync(hxy.data(), d_xy, 4 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
-        TRY(cudaStreamSynchronize(st));
-        // end points are matched on a grid of 1e-6 of the shortest element
-        double lmin = 1e300;
-        for (int64_t e = 0; e < n; ++e)
-            lmin = std::min(lmin, hypot(hxy[2 * n + e] - hxy[e], hxy[3 * n + e] - hxy[n + e]));
-        double q = 1e-6 * lmin;
-        // start points in an open-addressing hash table (quantised coordinates)
-        size_t cap = 1;
-        while (cap < 2 * (size_t)n) cap <<= 1;
-        std::vector<int64_t> slot(cap, -1);
-        std::vector<long long> skx(cap), sky(cap);
-        auto hidx = [&](long long kx, long long ky) {
-            uint64_t h = (uint64_t)kx * 0x9E3779B97F4A7C15ull ^ ((uint64_t)ky + 0x632BE59BD9B4E019ull) * 0xC2B2AE3D27D4EB4Full;
-            return (size_t)((h ^ (h >> 29)) & (cap - 1));
-        };
-        auto qz = [&](double v) { return (long long)llround(v / q); };
-        for (int64_t e = 0; e < n; ++e) {          // a repeated start point keeps the last element
-            long long kx = qz(hxy[e]), ky = qz(hxy[n + e]);
-            size_t i = hidx(kx, ky);
-            while (slot[i] >= 0 && !(skx[i] == kx && sky[i] == ky)) i = (i + 1) & (cap - 1);
-            slot[i] = e; skx[i] = kx; sky[i] = ky;
-        }
-        std::vector<int64_t> next(n, -1), prevc(n, 0);
-        for (int64_t e = 0; e < n; ++e) {
-            long long kx = qz(hxy[2 * n + e]), ky = qz(hxy[3 * n + e]);
-            size_t i = hidx(kx, ky);
-            while (slot[i] >= 0 && !(skx[i] == kx && sky[i] == ky)) i = (i + 1) & (cap - 1);
-            int64_t f = slot[i];
-            if (f >= 0 && f != e && prevc[f] == 0) {
-                next[e] = f;
-                prevc[f] = 1;
-            }
-        }
-        std::vector<int32_t> boff{0};
-        std::vector<int64_t> belem, moff{0};
-        std::vector<char> seen(n, 0);
-        const int BMAX = 64;
-        auto emit_chain = [&](int64_t head) {
-            int cnt = 0;
-            for (int64_t e = head; e >= 0 && !seen[e]; e = next[e]) {
-                seen[e] = 1;
-                belem.push_back(e);
-                if (++cnt == BMAX) {
-                    boff.push_back((int32_t)belem.size());
-                    cnt = 0;
-                }
-            }
-            if (cnt) boff.push_back((int32_t)belem.size());
-        };
-        for (int64_t e = 0; e < n; ++e)
-            if (!prevc[e]) emit_chain(e);
-        for (int64_t e = 0; e < n; ++e)      // closed loops
-            if (!seen[e]) emit_chain(e);
+        chain_th.join();
+        chain_th_live = false;
+        if (!chain_ok) { tree_free(t); return ctx_fail(ctx, DDM_ECUDA, "tree build: end point copy failed"); }
+        std::vector<int32_t> &boff = chains.boff;
+        std::vector<int64_t> &belem = chains.belem;
+        std::vector<int64_t> moff{0};
         t->n_pblk = (int64_t)boff.size() - 1;
         t->pb_max = 0;
         for (int64_t b = 0; b < t->n_pblk; ++b) {
