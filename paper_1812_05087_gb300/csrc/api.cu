@@ -81,35 +81,198 @@ __global__ void k_sif(const double *xy, int64_t n, const double *x, const int64_
 
 // --- GMRES helpers (FP64).  Reduced vectors (length nu) live in the first
 // ncomp blocks of N of a 3N vector layout.
-constexpr int RT = 256;
-__global__ void k_dots(const double *V, int64_t ld, int nv, const double *w, int64_t len, double *h) {
-    __shared__ double s[RT];
-    int v = blockIdx.y;
-    double acc = 0;
-    for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < len; i += (int64_t)gridDim.x * RT)
-        acc += V[v * ld + i] * w[i];
-    s[threadIdx.x] = acc;
-    __syncthreads();
-    for (int o = RT / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+// Dot products h[v] = V[v] . w for all v < nv in two steps without atomics:
+// every block covers one contiguous chunk of the vectors, each thread
+// carrying up to DP_V partial sums in registers, reduced across the warp by
+// shuffles and across the block in shared memory into part[block][v]; the
+// final kernel sums the blocks (one warp per vector) and maintains the
+// Hessenberg column (hcol = h on the first CGS pass, += h on the second).
+constexpr int DP_T = 128, DP_V = 8, DP_G = 304;
+__global__ void __launch_bounds__(DP_T) k_dots_part(const double *V, int64_t ld, int nv, const double *w, int64_t len,
+                                                    int64_t chunk, double *part, int pld) {
+    __shared__ double red[DP_T / 32][DP_V];
+    const int64_t i0 = blockIdx.x * chunk, i1 = i0 + chunk < len ? i0 + chunk : len;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int v0 = 0; v0 < nv; v0 += DP_V) {
+        double acc[DP_V];
+#pragma unroll
+        for (int q = 0; q < DP_V; ++q) acc[q] = 0.0;
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += DP_T) {
+            const double wi = w[i];
+#pragma unroll
+            for (int q = 0; q < DP_V; ++q)
+                if (v0 + q < nv) acc[q] = fma(V[(int64_t)(v0 + q) * ld + i], wi, acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < DP_V; ++q)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xFFFFFFFFu, acc[q], o);
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < DP_V; ++q) red[wid][q] = acc[q];
+        __syncthreads();
+        if (threadIdx.x < DP_V && v0 + threadIdx.x < nv) {
+            double sum = 0.0;
+#pragma unroll
+            for (int k = 0; k < DP_T / 32; ++k) sum += red[k][threadIdx.x];
+            part[(int64_t)blockIdx.x * pld + v0 + threadIdx.x] = sum;
+        }
         __syncthreads();
     }
-    if (threadIdx.x == 0) atomicAdd(&h[v], s[0]);
 }
-__global__ void k_sub(const double *V, int64_t ld, int nv, const double *h, double *w, int64_t len, double *hacc) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (blockIdx.x == 0 && threadIdx.x < nv && hacc) hacc[threadIdx.x] += h[threadIdx.x];
-    if (i >= len) return;
-    double s = 0;
-    for (int v = 0; v < nv; ++v) s += h[v] * V[v * ld + i];
-    w[i] -= s;
+__global__ void k_dots_final(const double *part, int G, int pld, int nv, double *h, double *hcol, int accumulate) {
+    const int v = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (v >= nv) return;
+    double sum = 0.0;
+    for (int b = lane; b < G; b += 32) sum += part[(int64_t)b * pld + v];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+    if (lane == 0) {
+        h[v] = sum;
+        if (hcol) hcol[v] = accumulate ? hcol[v] + sum : sum;
+    }
 }
-__global__ void k_scale_to(const double *w, int64_t len, const double *nrm2, double *out, double *hcol_j1) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    double nrm = sqrt(*nrm2);
-    if (i == 0) *hcol_j1 = nrm;
-    if (i >= len) return;
-    out[i] = nrm > 0 ? w[i] / nrm : 0.0;
+// One Arnoldi orthogonalisation step as a single cooperative kernel (its
+// blocks meet at grid barriers, so it is launched cooperatively, which
+// guarantees they are all resident):
+//   1. partial dot products of w with V[0..nv) per block chunk;
+//   2. block v sums vector v's partials: h[v], hcol[v] (= or += h[v]);
+//   3. w -= V h per chunk, partial ||w||^2;
+//   4. every block sums the norm partials and takes the same decision
+//      (Daniel-Gragg-Kaufman-Stewart): a second pass (1-3 again, hcol
+//      accumulating) when ||w_new||^2 < (||w_new||^2 + |h|^2) / 2;
+//   5. V[nv] = w / ||w||, hcol[nv] = ||w||.
+// The barriers give up after a bounded number of polls and raise the error
+// word (the results are then invalid, nothing hangs).
+constexpr long long GB_POLLS = 1ll << 22;
+__device__ __forceinline__ void grid_barrier(unsigned *bar, int *err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vb = bar;
+        const unsigned gen = vb[1];
+        __threadfence();
+        if (atomicAdd(&bar[0], 1u) == gridDim.x - 1) {
+            bar[0] = 0u;
+            __threadfence();
+            atomicAdd(&bar[1], 1u);
+        } else {
+            long long polls = 0;
+            while (vb[1] == gen) {
+                if (++polls > GB_POLLS) { atomicExch(err, 1); break; }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+__global__ void __launch_bounds__(DP_T) k_arnoldi_orth(double *V, int64_t len, int nv, double *w, int64_t chunk,
+                                                       double *part, int pld, double *h, double *hcol,
+                                                       unsigned *bar, int *err) {
+    __shared__ double red[DP_T / 32][DP_V];
+    __shared__ double sh[512];
+    __shared__ double s_nrm, s_hh;
+    const int64_t i0 = blockIdx.x * chunk, i1 = i0 + chunk < len ? i0 + chunk : len;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int G = gridDim.x;
+    double nrm2 = 0.0;
+    for (int pass = 0; pass < 2; ++pass) {
+        // 1. partial dots
+        for (int v0 = 0; v0 < nv; v0 += DP_V) {
+            double acc[DP_V];
+#pragma unroll
+            for (int q = 0; q < DP_V; ++q) acc[q] = 0.0;
+            for (int64_t i = i0 + threadIdx.x; i < i1; i += DP_T) {
+                const double wi = w[i];
+#pragma unroll
+                for (int q = 0; q < DP_V; ++q)
+                    if (v0 + q < nv) acc[q] = fma(V[(int64_t)(v0 + q) * len + i], wi, acc[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < DP_V; ++q)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xFFFFFFFFu, acc[q], o);
+            if (lane == 0)
+#pragma unroll
+                for (int q = 0; q < DP_V; ++q) red[wid][q] = acc[q];
+            __syncthreads();
+            if (threadIdx.x < DP_V && v0 + threadIdx.x < nv) {
+                double sum = 0.0;
+#pragma unroll
+                for (int k = 0; k < DP_T / 32; ++k) sum += red[k][threadIdx.x];
+                part[(int64_t)blockIdx.x * pld + v0 + threadIdx.x] = sum;
+            }
+            __syncthreads();
+        }
+        grid_barrier(bar, err);
+        // 2. block v reduces vector v
+        for (int v = blockIdx.x; v < nv; v += G) {
+            double sum = 0.0;
+            for (int b = threadIdx.x; b < G; b += DP_T) sum += __ldcg(part + (int64_t)b * pld + v);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+            if (lane == 0) red[wid][0] = sum;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double tot = 0.0;
+#pragma unroll
+                for (int k = 0; k < DP_T / 32; ++k) tot += red[k][0];
+                h[v] = tot;
+                hcol[v] = pass ? hcol[v] + tot : tot;
+            }
+            __syncthreads();
+        }
+        grid_barrier(bar, err);
+        // 3. w -= V h, partial norms
+        for (int v = threadIdx.x; v < nv; v += DP_T) sh[v] = __ldcg(h + v);
+        __syncthreads();
+        double acc = 0.0;
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += DP_T) {
+            double sum = 0.0;
+            for (int v = 0; v < nv; ++v) sum = fma(sh[v], V[(int64_t)v * len + i], sum);
+            const double wi = w[i] - sum;
+            w[i] = wi;
+            acc = fma(wi, wi, acc);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+        if (lane == 0) red[wid][0] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tot = 0.0;
+#pragma unroll
+            for (int k = 0; k < DP_T / 32; ++k) tot += red[k][0];
+            part[(int64_t)blockIdx.x * pld] = tot;
+        }
+        grid_barrier(bar, err);
+        // 4. norm and the second-pass decision, the same in every block
+        if (wid == 0) {
+            double sum = 0.0, hh = 0.0;
+            for (int b = lane; b < G; b += 32) sum += __ldcg(part + (int64_t)b * pld);
+            for (int v = lane; v < nv; v += 32) hh += sh[v] * sh[v];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+                hh += __shfl_xor_sync(0xFFFFFFFFu, hh, o);
+            }
+            if (lane == 0) {
+                s_nrm = sum;
+                s_hh = hh;
+            }
+        }
+        __syncthreads();
+        nrm2 = s_nrm;
+        const bool again = pass == 0 && nrm2 < 0.5 * (nrm2 + s_hh);
+        // the norm partials in part[] are read by every block before any
+        // block overwrites part[] in the next pass
+        grid_barrier(bar, err);
+        if (!again) break;
+    }
+    // 5. next basis vector
+    const double nrm = sqrt(nrm2);
+    if (blockIdx.x == 0 && threadIdx.x == 0) hcol[nv] = nrm;
+    double *out = V + (int64_t)nv * len;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += DP_T) out[i] = nrm > 0.0 ? w[i] / nrm : 0.0;
 }
 // restrict a 3N product to the system rows (RATE: sigma_n + p)
 // (combine = 1 for products, 0 for a right-hand side, whose rows are already
@@ -142,11 +305,13 @@ struct GmresWork {
     int cap_m = 0;
     cudaStream_t st = nullptr;
     double *V = nullptr, *w = nullptr, *z = nullptr, *full = nullptr, *y3 = nullptr, *b = nullptr;
-    double *h = nullptr, *hcol = nullptr, *nrm = nullptr, *Minv = nullptr, *yv = nullptr;
+    double *h = nullptr, *hcol = nullptr, *nrm = nullptr, *Minv = nullptr, *yv = nullptr, *part = nullptr;
+    unsigned *cnt = nullptr;   // 2 last-block counters (zero between launches), then the DGKS flag
     void release() {
-        double *ps[] = {V, w, z, full, y3, b, h, hcol, nrm, Minv, yv};
+        double *ps[] = {V, w, z, full, y3, b, h, hcol, nrm, Minv, yv, part};
         cudaStream_t s = st;
         for (double *p : ps) dfree(p, s);
+        dfree(cnt, s);
         *this = GmresWork();
         st = s;
     }
@@ -350,7 +515,10 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
                   dalloc(&g.hcol, (m + 2) * sizeof(double), s) == cudaSuccess &&
                   dalloc(&g.nrm, sizeof(double), s) == cudaSuccess &&
                   dalloc(&g.Minv, 9 * N * sizeof(double), s) == cudaSuccess &&
-                  dalloc(&g.yv, (m + 1) * sizeof(double), s) == cudaSuccess;
+                  dalloc(&g.yv, (m + 1) * sizeof(double), s) == cudaSuccess &&
+                  dalloc(&g.part, (size_t)DP_G * (m + 2) * sizeof(double), s) == cudaSuccess &&
+                  dalloc(&g.cnt, 4 * sizeof(unsigned), s) == cudaSuccess &&
+                  cudaMemsetAsync(g.cnt, 0, 4 * sizeof(unsigned), s) == cudaSuccess;
         if (!ok) { g.release(); return ctx_fail(ctx, DDM_ENOMEM, "GMRES workspace allocation failed"); }
         g.cap_len = len; g.cap_m = m;
     }
@@ -365,9 +533,24 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
         k_restrict<<<nblk(N), 256, 0, s>>>(g.y3, N, sys, 1, out);
         return DDM_OK;
     };
+    const int pld = m + 2;
+    const int64_t chunk = (len + DP_G - 1) / DP_G;
+    // cooperative orthogonalisation grid: every block resident at once
+    int orth_grid = DP_G;
+    {
+        int per_sm = 0, nsm = 0;
+        DDM_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi_orth, DP_T, 0));
+        DDM_CUDA_TRY(ctx, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+        orth_grid = std::max(1, std::min(DP_G, per_sm * nsm));
+    }
+    const int64_t orth_chunk = (len + orth_grid - 1) / orth_grid;
+    // h[v] = V[v] . w, v < nv (hcol: see k_dots_final)
+    auto dots = [&](const double *Vb, int nv, const double *w, double *h, double *hcol, int accumulate) {
+        k_dots_part<<<DP_G, DP_T, 0, s>>>(Vb, len, nv, w, len, chunk, g.part, pld);
+        k_dots_final<<<(nv + 3) / 4, 128, 0, s>>>(g.part, DP_G, pld, nv, h, hcol, accumulate);
+    };
     auto norm = [&](const double *v, double &out) -> ddm_status {
-        DDM_CUDA_TRY(ctx, cudaMemsetAsync(g.nrm, 0, sizeof(double), s));
-        k_dots<<<dim3(std::min<unsigned>(nblk(len), 1024), 1), RT, 0, s>>>(v, len, 1, v, len, g.nrm);
+        dots(v, 1, v, g.nrm, nullptr, 0);
         DDM_CUDA_TRY(ctx, cudaMemcpyAsync(&out, g.nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
         DDM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
         out = sqrt(out);
@@ -437,19 +620,24 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
         for (; j < m && iters < P.max_iters; ++j, ++iters) {
             double *vj = g.V + (int64_t)j * len;
             if ((st = pb_apply(ctx, t, sys, vj, g.full, s))) return st;
-            if ((st = op_apply(ctx, t, 0.0, dt, g.full, g.y3, mode, 0, 1.0))) return st;
-            k_restrict<<<nblk(N), 256, 0, s>>>(g.y3, N, sys, 1, g.w);
-            prof_end(ctx, 8, 8);      // precond, restrict, 2x(dots, sub), norm, scale
-            // CGS2 against V[0..j]
-            DDM_CUDA_TRY(ctx, cudaMemsetAsync(g.hcol, 0, (m + 2) * sizeof(double), s));
-            for (int pass = 0; pass < 2; ++pass) {
-                DDM_CUDA_TRY(ctx, cudaMemsetAsync(g.h, 0, (m + 2) * sizeof(double), s));
-                k_dots<<<dim3(std::min<unsigned>(nblk(len), 256), j + 1), RT, 0, s>>>(g.V, len, j + 1, g.w, len, g.h);
-                k_sub<<<nblk(len), 256, 0, s>>>(g.V, len, j + 1, g.h, g.w, len, g.hcol);
+            if (sys == DDM_SYS_PRESSURE) {        // the 3N product is already the system's rows
+                if ((st = op_apply(ctx, t, 0.0, dt, g.full, g.w, mode, 0, 1.0))) return st;
+            } else {
+                if ((st = op_apply(ctx, t, 0.0, dt, g.full, g.y3, mode, 0, 1.0))) return st;
+                k_restrict<<<nblk(N), 256, 0, s>>>(g.y3, N, sys, 1, g.w);
             }
-            DDM_CUDA_TRY(ctx, cudaMemsetAsync(g.nrm, 0, sizeof(double), s));
-            k_dots<<<dim3(std::min<unsigned>(nblk(len), 1024), 1), RT, 0, s>>>(g.w, len, 1, g.w, len, g.nrm);
-            k_scale_to<<<nblk(len), 256, 0, s>>>(g.w, len, g.nrm, g.V + (int64_t)(j + 1) * len, g.hcol + j + 1);
+            // orthogonalise against V[0..j] and normalise (one cooperative kernel)
+            {
+                double *Vp = g.V, *wp = g.w, *pp = g.part, *hp = g.h, *hcp = g.hcol;
+                int nvj = j + 1, pl = pld;
+                int64_t ln = len, ch = orth_chunk;
+                unsigned *bp = g.cnt;
+                int *ep = ctx->d_err;
+                void *args[] = {&Vp, &ln, &nvj, &wp, &ch, &pp, &pl, &hp, &hcp, &bp, &ep};
+                DDM_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void *)k_arnoldi_orth, dim3(orth_grid), dim3(DP_T),
+                                                              args, 0, s));
+            }
+            prof_end(ctx, 8, 2);      // precond, orthogonalisation
             DDM_CUDA_TRY(ctx, cudaMemcpyAsync(hc.data(), g.hcol, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
             DDM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
             // Givens rotations on the new column

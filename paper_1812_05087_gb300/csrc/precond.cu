@@ -7,7 +7,7 @@
 // the own element from the cached FP64 closed form) is assembled for the
 // rows and unknowns of the system being solved and inverted on the device
 // in FP32 (Gauss-Jordan with partial pivoting, one CTA per matrix held in
-// shared memory); a preconditioner needs no more precision, and FP32 runs
+// registers); a preconditioner needs no more precision, and FP32 runs
 // at 64x the FP64 rate.  Applying the preconditioner is
 // one small dense product per block.  Elements that belong to no chain form
 // 1-element blocks, i.e. the own-element 3x3 block Jacobi.
@@ -18,8 +18,6 @@
 #include "kernel_math.cuh"
 
 namespace {
-
-constexpr int PT = 256;
 
 // Gauss-Legendre, 8 points on [-1, 1] (fluid source between elements)
 __constant__ double c_gl8x[8] = {-0.9602898564975363, -0.7966664774136267, -0.5255324099163290, -0.1834346424956498,
@@ -100,75 +98,148 @@ __global__ void k_pb_assemble(KConst<float> kf, Win<float> wf, const PbGeo *geo,
 }
 
 // In-place Gauss-Jordan inversion with partial pivoting, one CTA per
-// matrix held in shared memory (n <= 192: 147 KB).  32 x 32 threads: tx
-// walks the columns, ty the rows, 32 apart.  Row k is the pivot row after
-// the swap; the multipliers of column k are saved before the update.
-constexpr int INV_MAX = 3 * 64;
-__global__ void __launch_bounds__(1024) k_pb_invert(const int32_t *boff, const int64_t *moff, int nc, float *M) {
-    extern __shared__ float A[];
-    __shared__ float colk[INV_MAX];
-    __shared__ int piv[INV_MAX];
-    __shared__ float s_ip;
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+// matrix (n <= 192) held in registers: 32 x 32 threads, thread (tx, ty)
+// owns rows ty + 32 i and columns tx + 32 j (i, j < 6).  Each step
+// broadcasts the pivot row and column through shared memory; row swaps go
+// through shared memory, the final column swaps through warp shuffles.
+constexpr int INV_MAX = 3 * 64, GJ_R = INV_MAX / 32;
+__global__ void __launch_bounds__(1024, 1) k_pb_invert(const int32_t *boff, const int64_t *moff, int nc, float *M) {
+    __shared__ float prow[INV_MAX], colk[INV_MAX], cand_v[32];
+    __shared__ int piv[INV_MAX], cand_r[32];
+    const int tx = threadIdx.x, ty = threadIdx.y;
     const int b = blockIdx.x;
     const int n = nc * (boff[b + 1] - boff[b]);
     float *G = M + moff[b];
-    for (int i = tid; i < n * n; i += 1024) A[i] = G[i];
-    __syncthreads();
+    float a[GJ_R][GJ_R];
+#pragma unroll
+    for (int i = 0; i < GJ_R; ++i)
+#pragma unroll
+        for (int j = 0; j < GJ_R; ++j) {
+            const int r = ty + 32 * i, c = tx + 32 * j;
+            a[i][j] = (r < n && c < n) ? G[r * n + c] : 0.f;
+        }
     for (int k = 0; k < n; ++k) {
-        if (ty == 0) {                        // pivot: largest |A[r][k]|, r >= k
+        const int ki = k >> 5, kt = k & 31;
+        // pivot: largest |A[r][k]|, r >= k; candidates from the owners of column k
+        if (tx == kt) {
             float best = -1.f;
             int bi = k;
-            for (int r = k + tx; r < n; r += 32) {
-                float v = fabsf(A[r * n + k]);
-                if (v > best) { best = v; bi = r; }
+#pragma unroll
+            for (int i = 0; i < GJ_R; ++i) {
+                float v = 0.f;
+#pragma unroll
+                for (int j = 0; j < GJ_R; ++j)
+                    if (j == ki) v = a[i][j];
+                const int r = ty + 32 * i;
+                if (r >= k && r < n && fabsf(v) > best) { best = fabsf(v); bi = r; }
             }
+            cand_v[ty] = best;
+            cand_r[ty] = bi;
+        }
+        __syncthreads();
+        if (ty == 0) {
+            float v = cand_v[tx];
+            int r = cand_r[tx];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                float ob = __shfl_xor_sync(0xFFFFFFFFu, best, o);
-                int oi = __shfl_xor_sync(0xFFFFFFFFu, bi, o);
-                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+                const float ov = __shfl_xor_sync(0xFFFFFFFFu, v, o);
+                const int orr = __shfl_xor_sync(0xFFFFFFFFu, r, o);
+                if (ov > v || (ov == v && orr < r)) { v = ov; r = orr; }
             }
-            if (tx == 0) piv[k] = bi;
+            if (tx == 0) piv[k] = r;
         }
         __syncthreads();
-        const int pr = piv[k];
-        if (pr != k)
-            for (int c = tid; c < n; c += 1024) {
-                float t = A[k * n + c];
-                A[k * n + c] = A[pr * n + c];
-                A[pr * n + c] = t;
+        const int pr = piv[k], pi = pr >> 5, pt = pr & 31;
+        if (pr != k) {                        // swap rows k and pr through shared memory
+            if (ty == kt)
+#pragma unroll
+                for (int i = 0; i < GJ_R; ++i)
+                    if (i == ki)
+#pragma unroll
+                        for (int j = 0; j < GJ_R; ++j) prow[tx + 32 * j] = a[i][j];
+            if (ty == pt)
+#pragma unroll
+                for (int i = 0; i < GJ_R; ++i)
+                    if (i == pi)
+#pragma unroll
+                        for (int j = 0; j < GJ_R; ++j) colk[tx + 32 * j] = a[i][j];
+            __syncthreads();
+            if (ty == kt)
+#pragma unroll
+                for (int i = 0; i < GJ_R; ++i)
+                    if (i == ki)
+#pragma unroll
+                        for (int j = 0; j < GJ_R; ++j) a[i][j] = colk[tx + 32 * j];
+            if (ty == pt)
+#pragma unroll
+                for (int i = 0; i < GJ_R; ++i)
+                    if (i == pi)
+#pragma unroll
+                        for (int j = 0; j < GJ_R; ++j) a[i][j] = prow[tx + 32 * j];
+            __syncthreads();
+        }
+        // pivot row and column to shared memory
+        if (ty == kt)
+#pragma unroll
+            for (int i = 0; i < GJ_R; ++i)
+                if (i == ki)
+#pragma unroll
+                    for (int j = 0; j < GJ_R; ++j) prow[tx + 32 * j] = a[i][j];
+        if (tx == kt)
+#pragma unroll
+            for (int i = 0; i < GJ_R; ++i)
+#pragma unroll
+                for (int j = 0; j < GJ_R; ++j)
+                    if (j == ki) colk[ty + 32 * i] = a[i][j];
+        __syncthreads();
+        const float p = prow[k];
+        const float ip = p != 0.f ? 1.f / p : 0.f;
+        float pc[GJ_R], cr[GJ_R];
+#pragma unroll
+        for (int j = 0; j < GJ_R; ++j) pc[j] = prow[tx + 32 * j] * ip;
+#pragma unroll
+        for (int i = 0; i < GJ_R; ++i) cr[i] = colk[ty + 32 * i];
+#pragma unroll
+        for (int i = 0; i < GJ_R; ++i)
+#pragma unroll
+            for (int j = 0; j < GJ_R; ++j) {
+                const int r = ty + 32 * i, c = tx + 32 * j;
+                if (r == k) a[i][j] = (c == k) ? ip : pc[j];
+                else if (c == k) a[i][j] = -cr[i] * ip;
+                else a[i][j] = fmaf(-cr[i], pc[j], a[i][j]);
             }
-        __syncthreads();
-        if (tid == 0) {
-            float p = A[k * n + k];
-            s_ip = p != 0.f ? 1.f / p : 0.f;
-        }
-        for (int r = tid; r < n; r += 1024) colk[r] = A[r * n + k];
-        __syncthreads();
-        const float ip = s_ip;
-        for (int c = tid; c < n; c += 1024) A[k * n + c] = (c == k) ? ip : A[k * n + c] * ip;
-        __syncthreads();
-        for (int r = ty; r < n; r += 32) {
-            if (r == k) continue;
-            const float f = colk[r];
-            for (int c = tx; c < n; c += 32)
-                A[r * n + c] = (c == k) ? -f * ip : A[r * n + c] - f * A[k * n + c];
-        }
-        __syncthreads();
+        __syncthreads();                      // prow / colk are rewritten by the next step
     }
-    // undo the row interchanges as column swaps, in reverse order
+    // undo the row interchanges as column swaps, in reverse order (a warp
+    // holds whole rows: shuffles)
     for (int k = n - 1; k >= 0; --k) {
         const int pr = piv[k];
-        if (pr != k)
-            for (int r = tid; r < n; r += 1024) {
-                float t = A[r * n + k];
-                A[r * n + k] = A[r * n + pr];
-                A[r * n + pr] = t;
+        if (pr == k) continue;
+        const int kj = k >> 5, kt = k & 31, pj = pr >> 5, pt = pr & 31;
+#pragma unroll
+        for (int i = 0; i < GJ_R; ++i) {
+            float vk = 0.f, vp = 0.f;
+#pragma unroll
+            for (int j = 0; j < GJ_R; ++j) {
+                if (j == kj) vk = a[i][j];
+                if (j == pj) vp = a[i][j];
             }
-        __syncthreads();
+            vk = __shfl_sync(0xFFFFFFFFu, vk, kt);
+            vp = __shfl_sync(0xFFFFFFFFu, vp, pt);
+#pragma unroll
+            for (int j = 0; j < GJ_R; ++j) {
+                if (tx == kt && j == kj) a[i][j] = vp;
+                if (tx == pt && j == pj) a[i][j] = vk;
+            }
+        }
     }
-    for (int i = tid; i < n * n; i += 1024) G[i] = A[i];
+#pragma unroll
+    for (int i = 0; i < GJ_R; ++i)
+#pragma unroll
+        for (int j = 0; j < GJ_R; ++j) {
+            const int r = ty + 32 * i, c = tx + 32 * j;
+            if (r < n && c < n) G[r * n + c] = a[i][j];
+        }
 }
 
 // z (3N layout, caller order) = Minv v (v in the system layout nc x N); one
@@ -231,15 +302,7 @@ ddm_status pb_prepare(ddm_ctx *ctx, ddm_tree *t, double dt, int sys, cudaStream_
     dim3 g((unsigned)((mm + 127) / 128), (unsigned)t->n_pblk);
     k_pb_assemble<<<g, 128, 0, s>>>(ctx->kf, wf, geo, t->self_blk, t->pb_off, t->pb_elem, t->pb_moff, nc, sys,
                                     t->pb_inv);
-    const int nmax = nc * t->pb_max;
-    const size_t smem = (size_t)nmax * nmax * sizeof(float);
-    static bool attr[64] = {false};
-    if (!attr[ctx->device & 63]) {
-        DDM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_pb_invert, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)(INV_MAX * INV_MAX * sizeof(float))));
-        attr[ctx->device & 63] = true;
-    }
-    k_pb_invert<<<(unsigned)t->n_pblk, dim3(32, 32), smem, s>>>(t->pb_off, t->pb_moff, nc, t->pb_inv);
+    k_pb_invert<<<(unsigned)t->n_pblk, dim3(32, 32), 0, s>>>(t->pb_off, t->pb_moff, nc, t->pb_inv);
     prof_end(ctx, 8, 4);
     dfree(geo, s);
     DDM_CUDA_TRY(ctx, cudaGetLastError());
