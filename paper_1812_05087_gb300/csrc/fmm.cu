@@ -1093,13 +1093,19 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
     Win<double> wd = make_win<double>(ctx, lo, hi);
     // own-element blocks of this time window (FP64 closed form), computed
     // once per window and cached
+    const unsigned long long now = ++t->win_clock;
     int slot = -1;
-    for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < ddm_tree::WIN_CACHE; ++k)
         if (t->win_blk[k] && t->win_lo[k] == lo && t->win_hi[k] == hi) slot = k;
+    if (slot >= 0) t->win_use[slot] = now;
     if (slot < 0) {
         prof_begin(ctx, 1);
-        slot = t->win_next;
-        t->win_next = (t->win_next + 1) % 4;
+        slot = 0;                                  // an empty slot, else the least recently used
+        for (int k = 0; k < ddm_tree::WIN_CACHE; ++k) {
+            if (!t->win_blk[k]) { slot = k; break; }
+            if (t->win_use[k] < t->win_use[slot]) slot = k;
+        }
+        t->win_use[slot] = now;
         if (!t->win_blk[slot]) DDM_CUDA_TRY(ctx, dalloc(&t->win_blk[slot], 9 * N * sizeof(double), t->stream));
         k_self_blocks<<<(N + TB - 1) / TB, TB, 0, s>>>(ctx->kd, wd, t->xy_caller, N, t->win_blk[slot]);
         t->win_lo[slot] = lo;
@@ -1147,21 +1153,36 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
         // M2L on every level >= 2: operators of this window, then one GEMM launch
         int nk = t->n_keys;
         size_t opsz = (size_t)nk * 16 * n2 * n2;
-        if (t->ops_n != n || !t->m2l_ops) {
-            dfree(t->m2l_ops, t->stream);
-            t->m2l_ops = nullptr;
-            DDM_CUDA_TRY(ctx, dalloc(&t->m2l_ops, opsz * sizeof(float), t->stream));
+        if (t->ops_n != n) {                       // new order: drop the cached sets
+            for (int k = 0; k < ddm_tree::WIN_CACHE; ++k) {
+                dfree(t->ops_set[k], t->stream);
+                t->ops_set[k] = nullptr;
+            }
             t->ops_n = n;
-            t->ops_lo = t->ops_hi = -1.0;
+            // up to 4 GB of operator sets (at least one)
+            t->ops_cap = (int)std::max<size_t>(1, std::min<size_t>(ddm_tree::WIN_CACHE, ((size_t)4 << 30) /
+                                                                   std::max<size_t>(1, opsz * sizeof(float))));
         }
-        if (t->ops_lo != lo || t->ops_hi != hi) {
+        int os = -1;
+        for (int k = 0; k < t->ops_cap; ++k)
+            if (t->ops_set[k] && t->ops_lo[k] == lo && t->ops_hi[k] == hi) os = k;
+        if (os >= 0) t->ops_use[os] = now;
+        if (os < 0) {
+            os = 0;
+            for (int k = 0; k < t->ops_cap; ++k) {
+                if (!t->ops_set[k]) { os = k; break; }
+                if (t->ops_use[k] < t->ops_use[os]) os = k;
+            }
+            t->ops_use[os] = now;
+            if (!t->ops_set[os]) DDM_CUDA_TRY(ctx, dalloc(&t->ops_set[os], opsz * sizeof(float), t->stream));
             prof_begin(ctx, 3);
             dim3 g((unsigned)((n2 * n2 + 127) / 128), (unsigned)nk);
-            k_m2l_ops<<<g, 128, 0, s>>>(kf, wf, L, t->h0, n, t->mk_off, t->m2l_ops);
-            t->ops_lo = lo;
-            t->ops_hi = hi;
+            k_m2l_ops<<<g, 128, 0, s>>>(kf, wf, L, t->h0, n, t->mk_off, t->ops_set[os]);
+            t->ops_lo[os] = lo;
+            t->ops_hi[os] = hi;
             prof_end(ctx, 3, 1);
         }
+        const float *ops = t->ops_set[os];
         prof_begin(ctx, 4);
         DDM_CUDA_TRY(ctx, cudaMemsetAsync(t->Fl, 0, (size_t)t->n_cells * 4 * n2 * sizeof(float), s));
         if (t->n_work > 0) {
@@ -1172,7 +1193,7 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
                 attr[ctx->device & 63] = true;
             }
             dim3 g((unsigned)t->n_work, (unsigned)((4 * n2 + tc::BM - 1) / tc::BM));
-            k_m2l_tc<<<g, tc::THREADS, tc::SMEM_BYTES, s>>>(t->mk_work, t->mk_off, t->mk_pair, n, t->m2l_ops, t->W,
+            k_m2l_tc<<<g, tc::THREADS, tc::SMEM_BYTES, s>>>(t->mk_work, t->mk_off, t->mk_pair, n, ops, t->W,
                                                             t->Fl, ctx->d_err);
         }
         prof_end(ctx, 4, 2);

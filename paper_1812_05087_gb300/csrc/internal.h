@@ -64,9 +64,13 @@ struct ddm_tree {
     double *xy_caller;         // 4 x n FP64 end points, caller order (copy of the input)
     double *self_blk;          // 9 x n FP64 own-element blocks at the last dt (cache)
     double self_dt;            // dt of the cached self blocks (<0: none)
-    double *win_blk[4] = {nullptr, nullptr, nullptr, nullptr};   // own-element blocks per time window
-    double win_lo[4] = {-1, -1, -1, -1}, win_hi[4] = {-1, -1, -1, -1};
-    int win_next = 0;
+    // Per time window (tau_lo, tau_hi) caches, least recently used first out:
+    // own-element 3x3 blocks and M2L operator sets.  A time-marching run sees
+    // the same lag windows every step, and the history sum one per lag.
+    static constexpr int WIN_CACHE = 128;
+    double *win_blk[WIN_CACHE] = {};
+    double win_lo[WIN_CACHE], win_hi[WIN_CACHE];
+    unsigned long long win_use[WIN_CACHE] = {};
     int64_t n_m2l, n_p2p;
     // preconditioner blocks: runs of <= 64 elements along chains of elements
     // that share end points (one fracture), caller element indices
@@ -87,9 +91,12 @@ struct ddm_tree {
     int2 *mk_work;             // (key, first pair) of every 64-pair column tile
     int n_work;
     // M2L operators of the current time window, one (4n^2 x 4n^2) matrix per key
-    float *m2l_ops;
-    double ops_lo, ops_hi;
-    int ops_n;
+    float *ops_set[WIN_CACHE] = {};
+    double ops_lo[WIN_CACHE], ops_hi[WIN_CACHE];
+    unsigned long long ops_use[WIN_CACHE] = {};
+    int ops_n;                 // n_cheb of the cached operator sets
+    int ops_cap;               // sets allowed by the memory budget
+    unsigned long long win_clock;
     // per-tree workspaces
     float *W;                  // multipole weights, 4 n^2 per cell
     float *Fl;                 // local expansions, 4 n^2 per cell

@@ -526,11 +526,12 @@ static void find_chains(const double *hxy, int64_t n, Chains &out) {
 
 void tree_free(ddm_tree *t) {
     if (!t) return;
-    void *ps[] = {t->mk_work, t->pb_off, t->pb_elem, t->pb_moff, t->pb_inv, t->mk_off, t->mk_pair, t->m2l_ops, t->grp_off, t->grp_leaf, t->perm, t->cell_key, t->cell_ix, t->cell_iy, t->cell_start, t->cell_end, t->cell_parent, t->cell_child0, t->cell_nchild, t->up_cnt,
+    void *ps[] = {t->mk_work, t->pb_off, t->pb_elem, t->pb_moff, t->pb_inv, t->mk_off, t->mk_pair, t->grp_off, t->grp_leaf, t->perm, t->cell_key, t->cell_ix, t->cell_iy, t->cell_start, t->cell_end, t->cell_parent, t->cell_child0, t->cell_nchild, t->up_cnt,
                   t->il_off, t->il_idx, t->nb_off, t->nb_idx, t->nb_tab, t->elem_leaf, t->g_rel, t->g_frame,
                   t->xy_sorted, t->xy_caller, t->self_blk, t->W, t->Fl, t->chg};
     for (void *p : ps) dfree(p, t->stream);
     for (double *p : t->win_blk) dfree(p, t->stream);
+    for (float *p : t->ops_set) dfree(p, t->stream);
     delete t;
 }
 
@@ -796,8 +797,9 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
             k_mkeys<<<(ncm + 255) / 256, 256, 0, st>>>(t->il_off, t->il_idx, t->cell_ix, t->cell_iy, lo, L, first, ncm,
                                                        t->mk_off, kcur, t->mk_pair, nullptr); ++tl_launches;
         }
-        t->ops_lo = t->ops_hi = -1.0;
         t->ops_n = 0;
+        t->ops_cap = 0;
+        t->win_clock = 0;
         std::vector<int32_t> hk(nk + 1);
         TRY(cudaMemcpyAsync(hk.data(), t->mk_off, (nk + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         TRY(cudaStreamSynchronize(st));
