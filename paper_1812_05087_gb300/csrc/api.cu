@@ -378,6 +378,18 @@ ddm_status ddm_create(ddm_ctx **out, const ddm_material *mat, const ddm_fmm_para
         delete c;
         return DDM_ENOMEM;
     }
+    {   // auxiliary stream (highest priority: the far field is the longer branch)
+        int lo = 0, hi = 0;
+        cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, hi) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaFree(c->cheb_T);
+            cudaFree(c->d_err);
+            delete c;
+            return DDM_ECUDA;
+        }
+    }
     c->gm = new GmresWork();
     *out = c;
     return DDM_OK;
@@ -387,6 +399,9 @@ void ddm_destroy(ddm_ctx *ctx) {
     if (!ctx) return;
     if (ctx->cheb_T) cudaFree(ctx->cheb_T);
     if (ctx->d_err) cudaFree(ctx->d_err);
+    if (ctx->aux) cudaStreamDestroy(ctx->aux);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     if (ctx->h_pin) cudaFreeHost(ctx->h_pin);
     if (ctx->gm) { ctx->gm->release(); delete ctx->gm; }
     delete ctx;

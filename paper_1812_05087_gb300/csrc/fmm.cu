@@ -152,7 +152,7 @@ struct UpSmem {
 //
 // P2M: lane owns node entries (a, b) = lane + 32 j and all 4 components;
 // the UP_W warps take every UP_W-th point and are summed at the end.
-template <int N>
+template <int N, bool PREP>
 __global__ void __launch_bounds__(UP_T) k_up(const int32_t *cstart, const int32_t *cend, int64_t loff, int64_t off3,
                                              const int32_t *cix, const int32_t *ciy, const int32_t *parent,
                                              const int32_t *child0, const int32_t *nchild, int32_t *cnt,
@@ -170,7 +170,8 @@ __global__ void __launch_bounds__(UP_T) k_up(const int32_t *cstart, const int32_
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t leaf = loff + blockIdx.x;
     const int s0 = cstart[leaf], s1 = cend[leaf];
-    for (int i = s0 + tid; i < s1; i += UP_T) prep_elem(i, x, perm, frame, blk, n_elem, scale, overwrite, chg, y);
+    if (PREP)
+        for (int i = s0 + tid; i < s1; i += UP_T) prep_elem(i, x, perm, frame, blk, n_elem, scale, overwrite, chg, y);
     for (int i = tid; i < 2 * N2; i += UP_T) sT[i] = T[i];
     constexpr int nq = N;                     // Gauss points per element
     float acc[NE][4];
@@ -945,6 +946,61 @@ __global__ void __launch_bounds__(NEAR_T, 4) k_near(KConst<float> k, KConst<doub
     y[lane * N + eout] = yold + scale * (((double)vh + (double)vl) + vd);
 }
 
+// L2P alone (products whose near field ran concurrently with the far
+// field): one thread per target, cardinals of the target in registers,
+// y += scale * rotate(sum_m S_m(x) f_m).
+template <int N>
+__global__ void __launch_bounds__(256) k_l2p(const int32_t *elem_leaf, const float4 *grel, const float4 *frame,
+                                             const int64_t *perm, int64_t loff, float wL, const float *F, int64_t Ntot,
+                                             double scale, double *y) {
+    constexpr int N2 = N * N;
+    const int64_t ti = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (ti >= Ntot) return;
+    const float *cheb = c_gl.cheb[N / 2 - 1], *bw = c_gl.bw[N / 2 - 1];
+    const float4 rt = grel[ti];
+    const float hL = 0.5f * wL;
+    const float xh = __fdividef(0.5f * (rt.x + rt.z), hL), yh = __fdividef(0.5f * (rt.y + rt.w), hL);
+    float cx[N], cy[N], sx = 0.f, sy = 0.f;
+    int hx = -1, hy = -1;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        float dx = xh - cheb[j], dy = yh - cheb[j];
+        if (fabsf(dx) < 1e-7f) hx = j;
+        if (fabsf(dy) < 1e-7f) hy = j;
+        cx[j] = __fdividef(bw[j], dx);
+        cy[j] = __fdividef(bw[j], dy);
+        sx += cx[j];
+        sy += cy[j];
+    }
+    const float isx = __fdividef(1.f, sx), isy = __fdividef(1.f, sy);
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        cx[j] = hx >= 0 ? (j == hx ? 1.f : 0.f) : cx[j] * isx;
+        cy[j] = hy >= 0 ? (j == hy ? 1.f : 0.f) : cy[j] * isy;
+    }
+    const float *Fc = F + (loff + elem_leaf[ti]) * 4 * N2;
+    float g[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        float sum = 0.f;
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+            float row = 0.f;
+#pragma unroll
+            for (int b = 0; b < N; ++b) row = fmaf(cy[b], Fc[c * N2 + a * N + b], row);
+            sum = fmaf(cx[a], row, sum);
+        }
+        g[c] = sum;
+    }
+    const float4 f = frame[ti];
+    float ss, sn;
+    to_local<float>(f.x, f.y, g, ss, sn);
+    const int64_t e = perm[ti];
+    y[e] += scale * (double)ss;
+    y[Ntot + e] += scale * (double)sn;
+    y[2 * Ntot + e] += scale * (double)g[3];
+}
+
 // -------------------------------------------------------------------- dense
 constexpr int DN_T = 128;
 template <bool PRECISE>
@@ -1137,16 +1193,27 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
         DDM_CUDA_TRY(ctx, cudaGetLastError());
         return DDM_OK;
     }
+    // The near field needs only the charges: unless profiling or capturing
+    // (stream given), it runs on the context stream while the far field
+    // (upward pass, M2L, L2L) runs on the auxiliary stream, and L2P follows
+    // the join.
+    const bool overlap = use_far && stream_override == nullptr && !ctx->prof.on;
+    cudaStream_t fs = overlap ? ctx->aux : s;
     if (use_far) {
-        // upward pass: charges, own elements, P2M and M2M in one launch
         float hL = 0.5f * wL;
         int64_t off3 = L >= 3 ? t->lvl_off[3] : t->n_cells;
+        if (overlap) {
+            k_prep<<<(N + TB - 1) / TB, TB, 0, s>>>(x, t->perm, t->g_frame, blk, N, scale, overwrite, t->chg, y);
+            DDM_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_fork, s));
+            DDM_CUDA_TRY(ctx, cudaStreamWaitEvent(fs, ctx->ev_fork, 0));
+        }
+        // upward pass (with charges and own elements unless done above): P2M and M2M in one launch
         prof_begin(ctx, 2);
 #define DDM_UP(NN)                                                                                          \
-    k_up<NN><<<(unsigned)nleaf, UP_T, 0, s>>>(t->cell_start, t->cell_end, loff, off3, t->cell_ix, t->cell_iy,       \
-                                              t->cell_parent, t->cell_child0, t->cell_nchild, t->up_cnt,          \
-                                              ctx->cheb_T, x, t->perm, t->g_rel, t->g_frame, blk, N, scale,       \
-                                              overwrite, y, t->chg, hL, t->W)
+    (overlap ? k_up<NN, false> : k_up<NN, true>)<<<(unsigned)nleaf, UP_T, 0, fs>>>(                                \
+        t->cell_start, t->cell_end, loff, off3, t->cell_ix, t->cell_iy, t->cell_parent, t->cell_child0,              \
+        t->cell_nchild, t->up_cnt, ctx->cheb_T, x, t->perm, t->g_rel, t->g_frame, blk, N, scale, overwrite, y,       \
+        t->chg, hL, t->W)
         DDM_CHEB_SWITCH(n, DDM_UP);
 #undef DDM_UP
         prof_end(ctx, 2, 1);
@@ -1177,14 +1244,14 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
             if (!t->ops_set[os]) DDM_CUDA_TRY(ctx, dalloc(&t->ops_set[os], opsz * sizeof(float), t->stream));
             prof_begin(ctx, 3);
             dim3 g((unsigned)((n2 * n2 + 127) / 128), (unsigned)nk);
-            k_m2l_ops<<<g, 128, 0, s>>>(kf, wf, L, t->h0, n, t->mk_off, t->ops_set[os]);
+            k_m2l_ops<<<g, 128, 0, fs>>>(kf, wf, L, t->h0, n, t->mk_off, t->ops_set[os]);
             t->ops_lo[os] = lo;
             t->ops_hi[os] = hi;
             prof_end(ctx, 3, 1);
         }
         const float *ops = t->ops_set[os];
         prof_begin(ctx, 4);
-        DDM_CUDA_TRY(ctx, cudaMemsetAsync(t->Fl, 0, (size_t)t->n_cells * 4 * n2 * sizeof(float), s));
+        DDM_CUDA_TRY(ctx, cudaMemsetAsync(t->Fl, 0, (size_t)t->n_cells * 4 * n2 * sizeof(float), fs));
         if (t->n_work > 0) {
             static bool attr[64] = {false};
             if (!attr[ctx->device & 63]) {
@@ -1193,7 +1260,7 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
                 attr[ctx->device & 63] = true;
             }
             dim3 g((unsigned)t->n_work, (unsigned)((4 * n2 + tc::BM - 1) / tc::BM));
-            k_m2l_tc<<<g, tc::THREADS, tc::SMEM_BYTES, s>>>(t->mk_work, t->mk_off, t->mk_pair, n, ops, t->W,
+            k_m2l_tc<<<g, tc::THREADS, tc::SMEM_BYTES, fs>>>(t->mk_work, t->mk_off, t->mk_pair, n, ops, t->W,
                                                             t->Fl, ctx->d_err);
         }
         prof_end(ctx, 4, 2);
@@ -1201,18 +1268,27 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
         if (L >= 3) {
             prof_begin(ctx, 5);
 #define DDM_DOWN(NN)                                                                                        \
-    k_down<NN><<<(unsigned)nleaf, L2L_T, 0, s>>>(loff, L, t->cell_ix, t->cell_iy, t->cell_parent, ctx->cheb_T, t->Fl)
+    k_down<NN><<<(unsigned)nleaf, L2L_T, 0, fs>>>(loff, L, t->cell_ix, t->cell_iy, t->cell_parent, ctx->cheb_T, t->Fl)
             DDM_CHEB_SWITCH(n, DDM_DOWN);
 #undef DDM_DOWN
             prof_end(ctx, 5, 1);
         }
     }
+    if (overlap) DDM_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_join, fs));
     prof_begin(ctx, 6);
     auto knr = precise ? k_near<true> : k_near<false>;
     knr<<<(unsigned)((N + NEAR_W - 1) / NEAR_W), NEAR_T, 0, s>>>(
         kf, ctx->kd, wf, wd, t->nb_off, t->nb_tab, t->elem_leaf, t->g_rel, t->g_frame, t->chg, t->perm, loff, wL, n,
-        ctx->prm.quad_near, t->Fl, use_far, N, scale, y);
+        ctx->prm.quad_near, t->Fl, overlap ? 0 : use_far, N, scale, y);
     prof_end(ctx, 6, 1);
+    if (overlap) {
+        DDM_CUDA_TRY(ctx, cudaStreamWaitEvent(s, ctx->ev_join, 0));
+#define DDM_L2P(NN)                                                                                         \
+    k_l2p<NN><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(t->elem_leaf, t->g_rel, t->g_frame, t->perm, loff, wL, t->Fl, \
+                                                          N, scale, y)
+        DDM_CHEB_SWITCH(n, DDM_L2P);
+#undef DDM_L2P
+    }
     DDM_CUDA_TRY(ctx, cudaGetLastError());
     return DDM_OK;
 }

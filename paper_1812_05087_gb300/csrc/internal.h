@@ -122,6 +122,8 @@ struct Prof {
 struct ddm_ctx {
     int device;
     cudaStream_t stream;
+    cudaStream_t aux = nullptr;   // far field of a product, concurrent with the near field
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     ddm_material mat;
     ddm_fmm_params prm;
     KConst<float> kf;

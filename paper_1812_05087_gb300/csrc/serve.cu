@@ -67,7 +67,10 @@ namespace {
 
 size_t footprint(const ddm_request &r, int ncheb) {
     size_t N = (size_t)r.n;
-    size_t per_tree = N * 400 + (size_t)16 * 49 * 16 * ncheb * ncheb * ncheb * ncheb * 4 / 2;
+    // tree arrays, plus one cached M2L operator set per time window the
+    // request's steps use (about half of the (level, offset) keys occur)
+    size_t opset = (size_t)8 * 49 * 16 * ncheb * ncheb * ncheb * ncheb * 4;
+    size_t per_tree = N * 400 + (size_t)r.steps * opset;
     size_t vectors = N * 3 * 8 * (size_t)(r.steps + 1 + 60);
     return per_tree + vectors;
 }
