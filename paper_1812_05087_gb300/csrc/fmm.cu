@@ -1122,12 +1122,31 @@ static Win<T> make_win(const ddm_ctx *ctx, double lo, double hi) {
     return w;
 }
 
-ddm_status self_blocks(ddm_ctx *ctx, ddm_tree *t, double dt, cudaStream_t s) {
-    if (t->self_dt == dt) return DDM_OK;
-    int64_t n = t->n;
-    k_self_blocks<<<(n + 255) / 256, 256, 0, s>>>(ctx->kd, make_win<double>(ctx, 0.0, dt), t->xy_caller, n, t->self_blk);
-    DDM_CUDA_TRY(ctx, cudaGetLastError());
-    t->self_dt = dt;
+// own-element 3x3 blocks of the time window (lo, hi), from the tree's LRU
+// window cache (computed on a miss, FP64 closed form, caller order)
+ddm_status window_self_blocks(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, cudaStream_t s, const double **out) {
+    const unsigned long long now = ++t->win_clock;
+    int slot = -1;
+    for (int k = 0; k < ddm_tree::WIN_CACHE; ++k)
+        if (t->win_blk[k] && t->win_lo[k] == lo && t->win_hi[k] == hi) slot = k;
+    if (slot < 0) {
+        prof_begin(ctx, 1);
+        slot = 0;                                  // an empty slot, else the least recently used
+        for (int k = 0; k < ddm_tree::WIN_CACHE; ++k) {
+            if (!t->win_blk[k]) { slot = k; break; }
+            if (t->win_use[k] < t->win_use[slot]) slot = k;
+        }
+        const int64_t N = t->n;
+        if (!t->win_blk[slot]) DDM_CUDA_TRY(ctx, dalloc(&t->win_blk[slot], 9 * N * sizeof(double), t->stream));
+        k_self_blocks<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(ctx->kd, make_win<double>(ctx, lo, hi), t->xy_caller,
+                                                                  N, t->win_blk[slot]);
+        DDM_CUDA_TRY(ctx, cudaGetLastError());
+        t->win_lo[slot] = lo;
+        t->win_hi[slot] = hi;
+        prof_end(ctx, 1, 1);
+    }
+    t->win_use[slot] = now;
+    *out = t->win_blk[slot];
     return DDM_OK;
 }
 
@@ -1147,28 +1166,11 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
     KConst<float> kf = ctx->kf;
     Win<float> wf = make_win<float>(ctx, lo, hi);
     Win<double> wd = make_win<double>(ctx, lo, hi);
-    // own-element blocks of this time window (FP64 closed form), computed
-    // once per window and cached
-    const unsigned long long now = ++t->win_clock;
-    int slot = -1;
-    for (int k = 0; k < ddm_tree::WIN_CACHE; ++k)
-        if (t->win_blk[k] && t->win_lo[k] == lo && t->win_hi[k] == hi) slot = k;
-    if (slot >= 0) t->win_use[slot] = now;
-    if (slot < 0) {
-        prof_begin(ctx, 1);
-        slot = 0;                                  // an empty slot, else the least recently used
-        for (int k = 0; k < ddm_tree::WIN_CACHE; ++k) {
-            if (!t->win_blk[k]) { slot = k; break; }
-            if (t->win_use[k] < t->win_use[slot]) slot = k;
-        }
-        t->win_use[slot] = now;
-        if (!t->win_blk[slot]) DDM_CUDA_TRY(ctx, dalloc(&t->win_blk[slot], 9 * N * sizeof(double), t->stream));
-        k_self_blocks<<<(N + TB - 1) / TB, TB, 0, s>>>(ctx->kd, wd, t->xy_caller, N, t->win_blk[slot]);
-        t->win_lo[slot] = lo;
-        t->win_hi[slot] = hi;
-        prof_end(ctx, 1, 1);
-    }
-    const double *blk = t->win_blk[slot];
+    // own-element blocks of this time window (FP64 closed form), cached
+    const double *blk = nullptr;
+    st = window_self_blocks(ctx, t, lo, hi, s, &blk);
+    if (st) return st;
+    const unsigned long long now = t->win_clock;
     const int overwrite = accumulate ? 0 : 1;
     int L = t->depth;
     int64_t loff = t->lvl_off[L], nleaf = t->lvl_off[L + 1] - loff;

@@ -62,8 +62,6 @@ struct ddm_tree {
     float4 *g_frame;           // (tx, ty, half-length, 0)
     double *xy_sorted;         // 4 x n FP64 absolute end points (sorted order)
     double *xy_caller;         // 4 x n FP64 end points, caller order (copy of the input)
-    double *self_blk;          // 9 x n FP64 own-element blocks at the last dt (cache)
-    double self_dt;            // dt of the cached self blocks (<0: none)
     // Per time window (tau_lo, tau_hi) caches, least recently used first out:
     // own-element 3x3 blocks and M2L operator sets.  A time-marching run sees
     // the same lag windows every step, and the history sum one per lag.
@@ -167,7 +165,8 @@ void tree_free(ddm_tree *t);
 // fmm.cu: y = [K(hi) - K(lo)] x  (caller order), accumulate: y += s * (...)
 ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double tau_lo, double tau_hi, const double *d_x,
                     double *d_y, int mode, int accumulate, double scale, cudaStream_t stream = nullptr);
-ddm_status self_blocks(ddm_ctx *ctx, ddm_tree *t, double dt, cudaStream_t s);   // fills t->self_blk (caller order)
+// own-element 3x3 blocks (caller order) of window (lo, hi), from the tree's window cache
+ddm_status window_self_blocks(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, cudaStream_t s, const double **out);
 ddm_status ensure_workspace(ddm_ctx *ctx, ddm_tree *t);
 ddm_status upload_tables(ddm_ctx *ctx);
 // precond.cu: chain-block Jacobi preconditioner (cached per dt and system)

@@ -99,12 +99,19 @@ __global__ void k_pb_assemble(KConst<float> kf, Win<float> wf, const PbGeo *geo,
 
 // In-place Gauss-Jordan inversion with partial pivoting, one CTA per
 // matrix (n <= 192) held in registers: 32 x 32 threads, thread (tx, ty)
-// owns rows ty + 32 i and columns tx + 32 j (i, j < 6).  Each step
-// broadcasts the pivot row and column through shared memory; row swaps go
-// through shared memory, the final column swaps through warp shuffles.
+// owns rows ty + 32 i and columns tx + 32 j (i, j < 6).  Step k:
+//   1. the owners of column k post their best pivot candidate; every warp
+//      reduces the 32 candidates itself (same result everywhere);
+//   2. the pivot row (pre-swap row pr), the old row k and column k go to
+//      shared memory;
+//   3. every thread updates its entries; the swap is folded in: row k takes
+//      the scaled pivot row, row pr takes the old row k, and the column-k
+//      multipliers of rows k and pr are exchanged.
+// The band of 32 columns (i = k / 32) is a compile-time index (unrolled
+// outer loop), so the pivot column lives in fixed registers.
 constexpr int INV_MAX = 3 * 64, GJ_R = INV_MAX / 32;
 __global__ void __launch_bounds__(1024, 1) k_pb_invert(const int32_t *boff, const int64_t *moff, int nc, float *M) {
-    __shared__ float prow[INV_MAX], colk[INV_MAX], cand_v[32];
+    __shared__ float prow[INV_MAX], orow[INV_MAX], colk[INV_MAX], cand_v[32];
     __shared__ int piv[INV_MAX], cand_r[32];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int b = blockIdx.x;
@@ -118,97 +125,82 @@ __global__ void __launch_bounds__(1024, 1) k_pb_invert(const int32_t *boff, cons
             const int r = ty + 32 * i, c = tx + 32 * j;
             a[i][j] = (r < n && c < n) ? G[r * n + c] : 0.f;
         }
-    for (int k = 0; k < n; ++k) {
-        const int ki = k >> 5, kt = k & 31;
-        // pivot: largest |A[r][k]|, r >= k; candidates from the owners of column k
-        if (tx == kt) {
-            float best = -1.f;
-            int bi = k;
 #pragma unroll
-            for (int i = 0; i < GJ_R; ++i) {
-                float v = 0.f;
+    for (int ki = 0; ki < GJ_R; ++ki) {
+        for (int kt = 0; kt < 32; ++kt) {
+            const int k = 32 * ki + kt;
+            if (k >= n) break;
+            // 1. pivot candidates of the column-k owners, reduced by every warp
+            if (tx == kt) {
+                float best = -1.f;
+                int bi = k;
 #pragma unroll
-                for (int j = 0; j < GJ_R; ++j)
-                    if (j == ki) v = a[i][j];
-                const int r = ty + 32 * i;
-                if (r >= k && r < n && fabsf(v) > best) { best = fabsf(v); bi = r; }
+                for (int i = 0; i < GJ_R; ++i) {
+                    const int r = ty + 32 * i;
+                    if (r >= k && r < n && fabsf(a[i][ki]) > best) { best = fabsf(a[i][ki]); bi = r; }
+                }
+                cand_v[ty] = best;
+                cand_r[ty] = bi;
             }
-            cand_v[ty] = best;
-            cand_r[ty] = bi;
-        }
-        __syncthreads();
-        if (ty == 0) {
-            float v = cand_v[tx];
-            int r = cand_r[tx];
+            __syncthreads();
+            float pv = cand_v[tx];
+            int pr = cand_r[tx];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                const float ov = __shfl_xor_sync(0xFFFFFFFFu, v, o);
-                const int orr = __shfl_xor_sync(0xFFFFFFFFu, r, o);
-                if (ov > v || (ov == v && orr < r)) { v = ov; r = orr; }
+                const float ov = __shfl_xor_sync(0xFFFFFFFFu, pv, o);
+                const int orr = __shfl_xor_sync(0xFFFFFFFFu, pr, o);
+                if (ov > pv || (ov == pv && orr < pr)) { pv = ov; pr = orr; }
             }
-            if (tx == 0) piv[k] = r;
-        }
-        __syncthreads();
-        const int pr = piv[k], pi = pr >> 5, pt = pr & 31;
-        if (pr != k) {                        // swap rows k and pr through shared memory
-            if (ty == kt)
+            if (tx == 0 && ty == 0) piv[k] = pr;
+            const int pi = pr >> 5, pt = pr & 31;
+            // 2. pivot row, old row k, column k
+            if (ty == pt)
 #pragma unroll
                 for (int i = 0; i < GJ_R; ++i)
-                    if (i == ki)
+                    if (i == pi)
 #pragma unroll
                         for (int j = 0; j < GJ_R; ++j) prow[tx + 32 * j] = a[i][j];
-            if (ty == pt)
+            if (ty == kt && pr != k)
 #pragma unroll
-                for (int i = 0; i < GJ_R; ++i)
-                    if (i == pi)
+                for (int j = 0; j < GJ_R; ++j) orow[tx + 32 * j] = a[ki][j];
+            if (tx == kt)
 #pragma unroll
-                        for (int j = 0; j < GJ_R; ++j) colk[tx + 32 * j] = a[i][j];
+                for (int i = 0; i < GJ_R; ++i) colk[ty + 32 * i] = a[i][ki];
             __syncthreads();
-            if (ty == kt)
+            // 3. update: one FMA per entry, then the rows k and pr and the
+            //    column k are overwritten (row k <- scaled pivot row, row pr
+            //    <- old row k eliminated, column k <- -multiplier / pivot)
+            const float p = prow[k];
+            const float ip = p != 0.f ? 1.f / p : 0.f;
+            float pc[GJ_R], m[GJ_R];
 #pragma unroll
-                for (int i = 0; i < GJ_R; ++i)
-                    if (i == ki)
+            for (int j = 0; j < GJ_R; ++j) pc[j] = prow[tx + 32 * j] * ip;
 #pragma unroll
-                        for (int j = 0; j < GJ_R; ++j) a[i][j] = colk[tx + 32 * j];
-            if (ty == pt)
-#pragma unroll
-                for (int i = 0; i < GJ_R; ++i)
-                    if (i == pi)
-#pragma unroll
-                        for (int j = 0; j < GJ_R; ++j) a[i][j] = prow[tx + 32 * j];
-            __syncthreads();
-        }
-        // pivot row and column to shared memory
-        if (ty == kt)
-#pragma unroll
-            for (int i = 0; i < GJ_R; ++i)
-                if (i == ki)
-#pragma unroll
-                    for (int j = 0; j < GJ_R; ++j) prow[tx + 32 * j] = a[i][j];
-        if (tx == kt)
+            for (int i = 0; i < GJ_R; ++i) m[i] = colk[ty + 32 * i];
 #pragma unroll
             for (int i = 0; i < GJ_R; ++i)
 #pragma unroll
-                for (int j = 0; j < GJ_R; ++j)
-                    if (j == ki) colk[ty + 32 * i] = a[i][j];
-        __syncthreads();
-        const float p = prow[k];
-        const float ip = p != 0.f ? 1.f / p : 0.f;
-        float pc[GJ_R], cr[GJ_R];
+                for (int j = 0; j < GJ_R; ++j) a[i][j] = fmaf(-m[i], pc[j], a[i][j]);
+            if (ty == pt && pr != k) {            // row pr: the old row k, eliminated
+                const float mp = colk[k];
 #pragma unroll
-        for (int j = 0; j < GJ_R; ++j) pc[j] = prow[tx + 32 * j] * ip;
+                for (int i = 0; i < GJ_R; ++i)
+                    if (i == pi) {
+                        m[i] = mp;
 #pragma unroll
-        for (int i = 0; i < GJ_R; ++i) cr[i] = colk[ty + 32 * i];
-#pragma unroll
-        for (int i = 0; i < GJ_R; ++i)
-#pragma unroll
-            for (int j = 0; j < GJ_R; ++j) {
-                const int r = ty + 32 * i, c = tx + 32 * j;
-                if (r == k) a[i][j] = (c == k) ? ip : pc[j];
-                else if (c == k) a[i][j] = -cr[i] * ip;
-                else a[i][j] = fmaf(-cr[i], pc[j], a[i][j]);
+                        for (int j = 0; j < GJ_R; ++j) a[i][j] = fmaf(-mp, pc[j], orow[tx + 32 * j]);
+                    }
             }
-        __syncthreads();                      // prow / colk are rewritten by the next step
+            if (tx == kt)                         // column k
+#pragma unroll
+                for (int i = 0; i < GJ_R; ++i) a[i][ki] = -m[i] * ip;
+            if (ty == kt) {                       // row k (and the pivot position)
+#pragma unroll
+                for (int j = 0; j < GJ_R; ++j) a[ki][j] = pc[j];
+                if (tx == kt) a[ki][ki] = ip;
+            }
+            __syncthreads();                  // shared rows are rewritten by the next step
+        }
     }
     // undo the row interchanges as column swaps, in reverse order (a warp
     // holds whole rows: shuffles)
@@ -293,14 +285,15 @@ ddm_status pb_prepare(ddm_ctx *ctx, ddm_tree *t, double dt, int sys, cudaStream_
     w.g_lo = 0.0;
     w.elastic = 1;
     Win<float> wf{(float)w.ct_hi, 0.f, (float)w.g_hi, 0.f, 1};
-    ddm_status st = self_blocks(ctx, t, dt, s);   // own elements, FP64, cached per dt
+    const double *selfblk = nullptr;                // own elements (window (0, dt)), FP64, cached
+    ddm_status st = window_self_blocks(ctx, t, 0.0, dt, s, &selfblk);
     if (st) return st;
     PbGeo *geo = nullptr;
     DDM_CUDA_TRY(ctx, dalloc(&geo, (size_t)t->n * sizeof(PbGeo), s));
     k_pb_geom<<<(unsigned)((t->n + 255) / 256), 256, 0, s>>>(t->xy_caller, t->n, geo);
     int64_t mm = (int64_t)t->pb_max * t->pb_max;
     dim3 g((unsigned)((mm + 127) / 128), (unsigned)t->n_pblk);
-    k_pb_assemble<<<g, 128, 0, s>>>(ctx->kf, wf, geo, t->self_blk, t->pb_off, t->pb_elem, t->pb_moff, nc, sys,
+    k_pb_assemble<<<g, 128, 0, s>>>(ctx->kf, wf, geo, selfblk, t->pb_off, t->pb_elem, t->pb_moff, nc, sys,
                                     t->pb_inv);
     k_pb_invert<<<(unsigned)t->n_pblk, dim3(32, 32), 0, s>>>(t->pb_off, t->pb_moff, nc, t->pb_inv);
     prof_end(ctx, 8, 4);

@@ -528,7 +528,7 @@ void tree_free(ddm_tree *t) {
     if (!t) return;
     void *ps[] = {t->mk_work, t->pb_off, t->pb_elem, t->pb_moff, t->pb_inv, t->mk_off, t->mk_pair, t->grp_off, t->grp_leaf, t->perm, t->cell_key, t->cell_ix, t->cell_iy, t->cell_start, t->cell_end, t->cell_parent, t->cell_child0, t->cell_nchild, t->up_cnt,
                   t->il_off, t->il_idx, t->nb_off, t->nb_idx, t->nb_tab, t->elem_leaf, t->g_rel, t->g_frame,
-                  t->xy_sorted, t->xy_caller, t->self_blk, t->W, t->Fl, t->chg};
+                  t->xy_sorted, t->xy_caller, t->W, t->Fl, t->chg};
     for (void *p : ps) dfree(p, t->stream);
     for (double *p : t->win_blk) dfree(p, t->stream);
     for (float *p : t->ops_set) dfree(p, t->stream);
@@ -541,7 +541,6 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
     cudaStream_t st = ctx->stream;
     ddm_tree *t = new ddm_tree();
     t->n = n;
-    t->self_dt = -1.0;
     Scratch S;
     S.st = st;
     t->stream = st;
@@ -822,7 +821,6 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
     TRY(dalloc(&t->g_rel, n * sizeof(float4), st));
     TRY(dalloc(&t->g_frame, n * sizeof(float4), st));
     TRY(dalloc(&t->xy_sorted, 4 * n * sizeof(double), st));
-    TRY(dalloc(&t->self_blk, 9 * n * sizeof(double), st));
     TRY(dalloc(&t->xy_caller, 4 * n * sizeof(double), st));
     TRY(cudaMemcpyAsync(t->xy_caller, d_xy, 4 * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     TRY(dalloc(&t->chg, n * sizeof(float4), st));
