@@ -62,3 +62,23 @@ def test_fmm_forced_depth(mid_set, depth):
     y2 = ctx.matvec(tree, x, 0.0, 10.0, mode="fmm").cpu().numpy()
     assert block_rel_err(y2, ref, N) < 1e-5
     ctx.device_check()
+
+
+def test_overlapped_product_equals_serial(mid_set):
+    """The default product runs the near field concurrently with the far field
+    (two streams); with stage profiling on it runs serially.  Both schedules
+    compute the same sums (up to the order of the M2L atomics)."""
+    xy = mid_set
+    N = xy.shape[1]
+    ctx = Context(inputs.MATERIAL, n_cheb=8, leaf_size=16)
+    tree = ctx.build_tree(dev(xy))
+    assert tree.info()["depth"] >= 3
+    x = dev(inputs.unknowns(N, seed=43))
+    for lo, hi in ((0.0, 10.0), (20.0, 50.0)):
+        y_par = ctx.matvec(tree, x, lo, hi, mode="fmm").cpu().numpy()
+        ctx.profile(True)
+        y_ser = ctx.matvec(tree, x, lo, hi, mode="fmm").cpu().numpy()
+        ctx.profile(False)
+        ctx.profile_read()
+        assert block_rel_err(y_par, y_ser, N) < 1e-6
+    ctx.device_check()

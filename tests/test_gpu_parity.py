@@ -75,14 +75,17 @@ def test_history_apply(ctx, rset, mode):
     assert block_rel_err(corr_got, corr_ref, N) < MATVEC_TOL[mode]
 
 
-@pytest.mark.parametrize("system", ["pressure", "impermeable"])
+@pytest.mark.parametrize("system", ["pressure", "impermeable", "rate"])
 @pytest.mark.parametrize("mode", ["dense", "fmm"])
 def test_gmres_matches_direct_solve(ctx, crack, system, mode):
     N = crack.shape[1]
     tree = ctx.build_tree(dev(crack))
     dt = 10.0
-    b = ctx.rhs(tree, sigma_H=0.0, sigma_h=0.0, p_f=1e6, p0=0.0, system=system)
-    b_ref = oracle.rhs(crack, p_f=1e6, system=system)
+    # RATE rows carry only the far field and p0 (the injection is a given Dq):
+    # give it in-situ stresses so that the system is not trivial
+    loads = dict(sigma_H=3e6, sigma_h=2e6, p_f=1e6, p0=5e5) if system == "rate" else dict(p_f=1e6)
+    b = ctx.rhs(tree, **{"sigma_H": 0.0, "sigma_h": 0.0, "p0": 0.0, **loads}, system=system)
+    b_ref = oracle.rhs(crack, **loads, system=system)
     assert np.allclose(b.cpu().numpy(), b_ref, rtol=1e-14, atol=1e-6)
     x, info = ctx.gmres_solve(tree, dt, b, system=system, tol=1e-5, mode=mode)
     assert info["converged"]
