@@ -946,6 +946,180 @@ __global__ void __launch_bounds__(NEAR_T, 4) k_near(KConst<float> k, KConst<doub
     y[lane * N + eout] = yold + scale * (((double)vh + (double)vl) + vd);
 }
 
+// Near field for two targets per warp (non-precise products): a work item is
+// a pair of consecutive targets of one leaf (or a single), so the two share
+// the neighbour table, the walk over the sources and every source load,
+// and each warp carries twice the independent work through the same chain
+// of dependent loads.  Close pairs are queued per (source, target) and
+// evaluated afterwards as units, as in k_near.  L2P runs separately
+// (k_l2p).
+__global__ void __launch_bounds__(NEAR_T, 4) k_near2(KConst<float> k, Win<float> w, const int32_t *nboff,
+                                                     const int4 *nbtab, const int32_t *elem_leaf, const float4 *grel,
+                                                     const float4 *frame, const float4 *chg, const int64_t *perm,
+                                                     float wL, int nq, const int2 *items, int64_t n_items, int64_t N,
+                                                     double scale, double *y) {
+    constexpr unsigned FULL = 0xFFFFFFFFu;
+    __shared__ int sst[NEAR_W][9], spre[NEAR_W][10];
+    __shared__ float sox[NEAR_W][9], soy[NEAR_W][9];
+    __shared__ int2 sq[NEAR_W][NEAR_Q];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t item = (int64_t)blockIdx.x * NEAR_W + wid;
+    if (item >= n_items) return;              // whole warp leaves together
+    const int2 it = items[item];
+    const int t0 = it.x, t1 = it.y >= 0 ? it.y : it.x;
+    const bool two = it.y >= 0;
+    const int32_t leaf = elem_leaf[t0];
+    const int q0 = nboff[leaf], nb = nboff[leaf + 1] - q0;
+    {   // neighbour table: one lane per neighbour leaf, counts prefix-summed
+        int4 tb = lane < nb ? nbtab[q0 + lane] : make_int4(0, 0, 0, 0);
+        int incl = tb.y;
+#pragma unroll
+        for (int o = 1; o < 16; o <<= 1) {
+            int v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane < nb) {
+            sst[wid][lane] = tb.x;
+            spre[wid][lane + 1] = incl;
+            sox[wid][lane] = wL * (float)tb.z;
+            soy[wid][lane] = wL * (float)tb.w;
+        }
+        if (lane == 0) spre[wid][0] = 0;
+    }
+    __syncwarp();
+    const float4 ra = grel[t0], rb = grel[t1];
+    const float mx0 = 0.5f * (ra.x + ra.z), my0 = 0.5f * (ra.y + ra.w);
+    const float mx1 = 0.5f * (rb.x + rb.z), my1 = 0.5f * (rb.y + rb.w);
+    const int S = spre[wid][nb];
+    // lanes 0-2 write target 0's rows, lanes 3-5 target 1's: fetch what they need now
+    const bool writer = lane < 3 || (two && lane < 6);
+    const int tw = lane < 3 ? t0 : t1, row = lane < 3 ? lane : lane - 3;
+    int64_t eout = 0;
+    float4 fout = make_float4(0.f, 0.f, 0.f, 0.f);
+    double yold = 0.0;
+    if (writer) {
+        eout = perm[tw];
+        fout = frame[tw];
+        yold = y[row * N + eout];
+    }
+    float acc0[4] = {0, 0, 0, 0}, acc1[4] = {0, 0, 0, 0};
+    double dummy[4];
+    int qn = 0, slot = 0;
+    bool anyq = false;
+    for (int base = 0; base < S; base += 32) {
+        const int c = base + lane;
+        bool close0 = false, close1 = false, hasq = false;
+        int sj = -1;
+        if (c < S) {
+            while (c >= spre[wid][slot + 1]) ++slot;
+            sj = sst[wid][slot] + (c - spre[wid][slot]);
+            const float4 r = grel[sj], f = frame[sj], cg = chg[sj];
+            const float cxs = 0.5f * (r.x + r.z) + sox[wid][slot], cys = 0.5f * (r.y + r.w) + soy[wid][slot];
+            const float lim = 64.f * f.z * f.z;
+            hasq = cg.z != 0.f;
+            if (sj != t0) {
+                const float dx = mx0 - cxs, dy = my0 - cys, r2 = dx * dx + dy * dy;
+                if (r2 > lim) far_pair<false>(k, KConst<double>{}, w, Win<double>{}, dx, dy, r2, f.z, f.x, f.y, cg.x,
+                                              cg.y, cg.z, acc0, dummy);
+                else close0 = true;
+            }
+            if (two && sj != t1) {
+                const float dx = mx1 - cxs, dy = my1 - cys, r2 = dx * dx + dy * dy;
+                if (r2 > lim) far_pair<false>(k, KConst<double>{}, w, Win<double>{}, dx, dy, r2, f.z, f.x, f.y, cg.x,
+                                              cg.y, cg.z, acc1, dummy);
+                else close1 = true;
+            }
+        }
+        // queue the close (source, target) pairs: entry (source, slot | target << 8)
+#pragma unroll
+        for (int tg = 0; tg < 2; ++tg) {
+            const bool cl = tg ? close1 : close0;
+            const unsigned m = __ballot_sync(FULL, cl);
+            if (m) {
+                anyq = anyq || __ballot_sync(FULL, cl && hasq) != 0u;
+                const int pos = qn + __popc(m & ((1u << lane) - 1u));
+                if (cl) {
+                    if (pos < NEAR_Q) {
+                        sq[wid][pos] = make_int2(sj, slot | (tg << 8));
+                    } else {                  // queue full: this pair in place
+                        const float4 r = grel[sj], f = frame[sj], cg = chg[sj];
+                        const float ox = sox[wid][slot], oy = soy[wid][slot];
+                        const int nu = 2 + (cg.z != 0.f ? nq : 0);
+                        float a4[4] = {0, 0, 0, 0};
+                        for (int u = 0; u < nu; ++u)
+                            near_unit<false>(u, nq, k, KConst<double>{}, w, Win<double>{}, tg ? mx1 : mx0,
+                                             tg ? my1 : my0, r.x + ox, r.y + oy, r.z + ox, r.w + oy, f.z, f.x, f.y,
+                                             cg.x, cg.y, cg.z, a4, dummy);
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            acc0[c] += tg ? 0.f : a4[c];
+                            acc1[c] += tg ? a4[c] : 0.f;
+                        }
+                    }
+                }
+                qn += __popc(m);
+            }
+        }
+    }
+    __syncwarp();
+    const int nqd = qn < NEAR_Q ? qn : NEAR_Q;
+    if (nqd > 0) {
+        // units: first the 2 dislocations of every queued pair, then the
+        // fluid-source points (only if some queued source carries q)
+        const int nf = anyq ? nq : 0, nd = 2 * nqd, U = nd + nf * nqd;
+        for (int base = 0; base < U; base += 32) {
+            const int u = base + lane;
+            if (u < U) {
+                int pi, unit;
+                if (u < nd) {
+                    pi = u >> 1;
+                    unit = u & 1;
+                } else {
+                    pi = (u - nd) / nf;
+                    unit = 2 + (u - nd) - pi * nf;
+                }
+                const int2 e = sq[wid][pi];
+                const int sl = e.y & 0xFF, tg = e.y >> 8;
+                const float4 r = grel[e.x], f = frame[e.x], cg = chg[e.x];
+                const float ox = sox[wid][sl], oy = soy[wid][sl];
+                float a4[4] = {0, 0, 0, 0};
+                near_unit<false>(unit, nq, k, KConst<double>{}, w, Win<double>{}, tg ? mx1 : mx0, tg ? my1 : my0,
+                                 r.x + ox, r.y + oy, r.z + ox, r.w + oy, f.z, f.x, f.y, cg.x, cg.y, cg.z, a4, dummy);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    acc0[c] += tg ? 0.f : a4[c];
+                    acc1[c] += tg ? a4[c] : 0.f;
+                }
+            }
+        }
+    }
+    float hl[8][2];                           // per-lane sums as FP32 pairs
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        hl[c][0] = acc0[c];
+        hl[4 + c][0] = acc1[c];
+        hl[c][1] = hl[4 + c][1] = 0.f;
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) warp_sum_ds(hl[c][0], hl[c][1]);
+    if (!writer) return;
+    const int b0 = lane < 3 ? 0 : 4;
+    const float4 f = fout;
+    const float nx = -f.y, ny = f.x;
+    float vh, vl;
+    if (row == 2) {
+        vh = hl[b0 + 3][0];
+        vl = hl[b0 + 3][1];
+    } else {
+        // sigma_n = g . (n n), sigma_s = g . sym(t n)
+        const float cxx = row ? nx * nx : f.x * nx, cyy = row ? ny * ny : f.y * ny;
+        const float cxy = row ? 2.f * nx * ny : f.x * ny + f.y * nx;
+        vh = cxx * hl[b0][0] + cyy * hl[b0 + 1][0] + cxy * hl[b0 + 2][0];
+        vl = cxx * hl[b0][1] + cyy * hl[b0 + 1][1] + cxy * hl[b0 + 2][1];
+    }
+    y[row * N + eout] = yold + scale * ((double)vh + (double)vl);
+}
+
 // L2P alone (products whose near field ran concurrently with the far
 // field): one thread per target, cardinals of the target in registers,
 // y += scale * rotate(sum_m S_m(x) f_m).
@@ -1278,13 +1452,17 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
     }
     if (overlap) DDM_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_join, fs));
     prof_begin(ctx, 6);
-    auto knr = precise ? k_near<true> : k_near<false>;
-    knr<<<(unsigned)((N + NEAR_W - 1) / NEAR_W), NEAR_T, 0, s>>>(
-        kf, ctx->kd, wf, wd, t->nb_off, t->nb_tab, t->elem_leaf, t->g_rel, t->g_frame, t->chg, t->perm, loff, wL, n,
-        ctx->prm.quad_near, t->Fl, overlap ? 0 : use_far, N, scale, y);
+    if (precise)
+        k_near<true><<<(unsigned)((N + NEAR_W - 1) / NEAR_W), NEAR_T, 0, s>>>(
+            kf, ctx->kd, wf, wd, t->nb_off, t->nb_tab, t->elem_leaf, t->g_rel, t->g_frame, t->chg, t->perm, loff, wL,
+            n, ctx->prm.quad_near, t->Fl, 0, N, scale, y);
+    else
+        k_near2<<<(unsigned)((t->n_items + NEAR_W - 1) / NEAR_W), NEAR_T, 0, s>>>(
+            kf, wf, t->nb_off, t->nb_tab, t->elem_leaf, t->g_rel, t->g_frame, t->chg, t->perm, wL, ctx->prm.quad_near,
+            t->near_items, t->n_items, N, scale, y);
     prof_end(ctx, 6, 1);
-    if (overlap) {
-        DDM_CUDA_TRY(ctx, cudaStreamWaitEvent(s, ctx->ev_join, 0));
+    if (use_far) {
+        if (overlap) DDM_CUDA_TRY(ctx, cudaStreamWaitEvent(s, ctx->ev_join, 0));
 #define DDM_L2P(NN)                                                                                         \
     k_l2p<NN><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(t->elem_leaf, t->g_rel, t->g_frame, t->perm, loff, wL, t->Fl, \
                                                           N, scale, y)

@@ -54,6 +54,8 @@ struct ddm_tree {
     int32_t *il_off, *il_idx;  // interaction lists (CSR over cells)
     int32_t *nb_off, *nb_idx;  // neighbour lists of leaves incl. self (CSR over leaves, leaf-local)
     int4 *nb_tab;              // per neighbour entry: (element start, count, cell dx, cell dy)
+    int2 *near_items;          // near-field work items: target pairs of one leaf (second -1: single)
+    int64_t n_items;
     int32_t *elem_leaf;        // sorted element -> leaf index (leaf-local)
     int64_t n_groups;          // groups of 32 consecutive sorted targets
     int32_t *grp_off, *grp_leaf; // per group: union of the neighbour leaves of its targets (CSR, leaf-local)

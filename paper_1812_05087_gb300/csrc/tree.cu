@@ -288,6 +288,22 @@ __global__ void k_children(const int32_t *parent, int64_t first, int64_t ncell, 
     if (parent[c - 1] != p) child0[p] = (int32_t)c;
 }
 
+// near-field work items: consecutive target pairs of one leaf (a leaf with an
+// odd count ends with a single, second index -1)
+__global__ void k_items_count(const int32_t *cstart, const int32_t *cend, int64_t loff, int64_t nleaf, int32_t *cnt) {
+    int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (L >= nleaf) return;
+    cnt[L] = (cend[loff + L] - cstart[loff + L] + 1) / 2;
+}
+__global__ void k_items_fill(const int32_t *cstart, const int32_t *cend, int64_t loff, int64_t nleaf,
+                             const int32_t *ioff, int2 *items) {
+    int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (L >= nleaf) return;
+    const int s0 = cstart[loff + L], s1 = cend[loff + L];
+    int o = ioff[L];
+    for (int e = s0; e < s1; e += 2) items[o++] = make_int2(e, e + 1 < s1 ? e + 1 : -1);
+}
+
 // per neighbour entry of every leaf: the neighbour's element range and its
 // cell offset from the leaf, so the near field reads one record per entry
 __global__ void k_nbtab(const int32_t *nboff, const int32_t *nbidx, const int32_t *cstart, const int32_t *cend,
@@ -527,7 +543,7 @@ static void find_chains(const double *hxy, int64_t n, Chains &out) {
 void tree_free(ddm_tree *t) {
     if (!t) return;
     void *ps[] = {t->mk_work, t->pb_off, t->pb_elem, t->pb_moff, t->pb_inv, t->mk_off, t->mk_pair, t->grp_off, t->grp_leaf, t->perm, t->cell_key, t->cell_ix, t->cell_iy, t->cell_start, t->cell_end, t->cell_parent, t->cell_child0, t->cell_nchild, t->up_cnt,
-                  t->il_off, t->il_idx, t->nb_off, t->nb_idx, t->nb_tab, t->elem_leaf, t->g_rel, t->g_frame,
+                  t->il_off, t->il_idx, t->nb_off, t->nb_idx, t->nb_tab, t->near_items, t->elem_leaf, t->g_rel, t->g_frame,
                   t->xy_sorted, t->xy_caller, t->W, t->Fl, t->chg};
     for (void *p : ps) dfree(p, t->stream);
     for (double *p : t->win_blk) dfree(p, t->stream);
@@ -751,6 +767,16 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
     TRY(dalloc(&t->nb_idx, std::max(nbtot, 1) * sizeof(int32_t), st));
     k_neigh<<<lb, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, loff, nleaf, side, t->nb_off, t->nb_idx, nullptr); ++tl_launches;
     TRY(dalloc(&t->nb_tab, std::max(nbtot, 1) * sizeof(int4), st));
+    {   // near-field work items (target pairs per leaf)
+        int32_t *icnt = S.get<int32_t>(nleaf + 1), *ioff = S.get<int32_t>(nleaf + 1);
+        TRY(S.err);
+        k_items_count<<<lb, TB, 0, st>>>(t->cell_start, t->cell_end, loff, nleaf, icnt); ++tl_launches;
+        int32_t itot = 0;
+        TRY(scan_excl(S, st, icnt, ioff, nleaf, &itot));
+        TRY(dalloc(&t->near_items, std::max(itot, 1) * sizeof(int2), st));
+        k_items_fill<<<lb, TB, 0, st>>>(t->cell_start, t->cell_end, loff, nleaf, ioff, t->near_items); ++tl_launches;
+        t->n_items = itot;
+    }
     k_nbtab<<<lb, TB, 0, st>>>(t->nb_off, t->nb_idx, t->cell_start, t->cell_end, t->cell_ix, t->cell_iy, loff, nleaf,
                                t->nb_tab); ++tl_launches;
 
