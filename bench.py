@@ -39,7 +39,7 @@ METRIC = "FMM matvec Melem/s & solves/s vs dense GPU DDM at <=1e-3 rel err; p50/
 WORKLOAD = "random pressurised fractures: 200 cracks x 100 elements (N=20000), dt=10 s"
 DT = 10.0
 LOADS = dict(sigma_H=30e6, sigma_h=25e6, p_f=10e6, p0=0.0)
-STAGE_KERNEL = {"leaf": "k_near", "m2l": "k_m2l_tc", "up": "k_up", "down": "k_down"}
+STAGE_KERNEL = {"leaf": "k_near2", "m2l": "k_m2l_tc", "up": "k_up", "down": "k_down"}
 
 
 def parse():
@@ -396,9 +396,9 @@ def main():
         peak_note = ("TF32 dense = measured" if bf16 else "TF32 dense = fallback") + \
             " bf16 GEMM peak x 0.5 (nominal TF32/BF16 ratio)"
     else:
-        fpp = rec[kname]["fp32_flops_per_pair"] if rec else 604
+        fpp = rec[kname]["fp32_flops_per_pair"] if (rec and kname in rec) else 373
         flop = float(info["n_p2p_pairs"]) * fpp
-        flop_note = f"{fpp} FP32 flops per near pair (ncu-measured thread-level FP32 ops of k_near)"
+        flop_note = f"{fpp} FP32 flops per near pair (ncu-counted fadd + 2 ffma + fmul of {kname} per pair)"
     achieved = flop / (dom_ms * 1e-3) / 1e12
     roof = {"kernel": kname, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak,

@@ -292,7 +292,9 @@ __global__ void __launch_bounds__(UP_T) k_up(const int32_t *cstart, const int32_
 constexpr int L2L_T = 128;
 template <int N>
 __global__ void __launch_bounds__(L2L_T) k_down(int64_t loff, int L, const int32_t *cix, const int32_t *ciy,
-                                               const int32_t *parent, const float *T, float *F) {
+                                                const int32_t *parent, const float *T, const float *F,
+                                                const int32_t *cstart, const int32_t *cend, const float4 *grel,
+                                                float wL, float4 *far4) {
     constexpr int N2 = N * N, NOUT = 4 * N2, KO = (NOUT + L2L_T - 1) / L2L_T;
     __shared__ float sT[2 * N2], sf[NOUT], tmp[NOUT];
     __shared__ int64_t anc[DDM_MAX_LEVELS + 1];
@@ -343,8 +345,48 @@ __global__ void __launch_bounds__(L2L_T) k_down(int64_t loff, int L, const int32
         }
         __syncthreads();
     }
-    float *Fl = F + leaf * NOUT;
-    for (int i = tid; i < NOUT; i += L2L_T) Fl[i] = sf[i];
+    // L2P at the leaf's targets (global sxx, syy, sxy, p; rotated by the caller)
+    const float *cheb = c_gl.cheb[N / 2 - 1], *bw = c_gl.bw[N / 2 - 1];
+    const float hL = 0.5f * wL;
+    for (int ti = cstart[leaf] + tid; ti < cend[leaf]; ti += L2L_T) {
+        const float4 rt = grel[ti];
+        const float xh = __fdividef(0.5f * (rt.x + rt.z), hL), yh = __fdividef(0.5f * (rt.y + rt.w), hL);
+        float cx[N], cy[N], sx = 0.f, sy = 0.f;
+        int hx = -1, hy = -1;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            float dx = xh - cheb[j], dy = yh - cheb[j];
+            if (fabsf(dx) < 1e-7f) hx = j;
+            if (fabsf(dy) < 1e-7f) hy = j;
+            cx[j] = __fdividef(bw[j], dx);
+            cy[j] = __fdividef(bw[j], dy);
+            sx += cx[j];
+            sy += cy[j];
+        }
+        const float isx = __fdividef(1.f, sx), isy = __fdividef(1.f, sy);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            cx[j] = hx >= 0 ? (j == hx ? 1.f : 0.f) : cx[j] * isx;
+            cy[j] = hy >= 0 ? (j == hy ? 1.f : 0.f) : cy[j] * isy;
+        }
+        float g4[4];
+#pragma unroll 1
+        for (int c = 0; c < 4; ++c) {
+            float sum = 0.f;
+#pragma unroll
+            for (int a = 0; a < N; ++a) {
+                float row = 0.f;
+#pragma unroll
+                for (int b = 0; b < N; ++b) row = fmaf(cy[b], sf[c * N2 + a * N + b], row);
+                sum = fmaf(cx[a], row, sum);
+            }
+            if (c == 0) g4[0] = sum;
+            else if (c == 1) g4[1] = sum;
+            else if (c == 2) g4[2] = sum;
+            else g4[3] = sum;
+        }
+        far4[ti] = make_float4(g4[0], g4[1], g4[2], g4[3]);
+    }
 }
 
 // ---------------------------------------------------------------------- M2L
@@ -1120,59 +1162,20 @@ __global__ void __launch_bounds__(NEAR_T, 4) k_near2(KConst<float> k, Win<float>
     y[row * N + eout] = yold + scale * ((double)vh + (double)vl);
 }
 
-// L2P alone (products whose near field ran concurrently with the far
-// field): one thread per target, cardinals of the target in registers,
-// y += scale * rotate(sum_m S_m(x) f_m).
-template <int N>
-__global__ void __launch_bounds__(256) k_l2p(const int32_t *elem_leaf, const float4 *grel, const float4 *frame,
-                                             const int64_t *perm, int64_t loff, float wL, const float *F, int64_t Ntot,
-                                             double scale, double *y) {
-    constexpr int N2 = N * N;
+// far field at the targets (from k_down) rotated to each target frame and
+// added: y += scale * (sigma_s, sigma_n, p)
+__global__ void k_far_add(const float4 *far4, const float4 *frame, const int64_t *perm, int64_t Ntot, double scale,
+                          double *y) {
     const int64_t ti = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (ti >= Ntot) return;
-    const float *cheb = c_gl.cheb[N / 2 - 1], *bw = c_gl.bw[N / 2 - 1];
-    const float4 rt = grel[ti];
-    const float hL = 0.5f * wL;
-    const float xh = __fdividef(0.5f * (rt.x + rt.z), hL), yh = __fdividef(0.5f * (rt.y + rt.w), hL);
-    float cx[N], cy[N], sx = 0.f, sy = 0.f;
-    int hx = -1, hy = -1;
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-        float dx = xh - cheb[j], dy = yh - cheb[j];
-        if (fabsf(dx) < 1e-7f) hx = j;
-        if (fabsf(dy) < 1e-7f) hy = j;
-        cx[j] = __fdividef(bw[j], dx);
-        cy[j] = __fdividef(bw[j], dy);
-        sx += cx[j];
-        sy += cy[j];
-    }
-    const float isx = __fdividef(1.f, sx), isy = __fdividef(1.f, sy);
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-        cx[j] = hx >= 0 ? (j == hx ? 1.f : 0.f) : cx[j] * isx;
-        cy[j] = hy >= 0 ? (j == hy ? 1.f : 0.f) : cy[j] * isy;
-    }
-    const float *Fc = F + (loff + elem_leaf[ti]) * 4 * N2;
-    float g[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        float sum = 0.f;
-#pragma unroll
-        for (int a = 0; a < N; ++a) {
-            float row = 0.f;
-#pragma unroll
-            for (int b = 0; b < N; ++b) row = fmaf(cy[b], Fc[c * N2 + a * N + b], row);
-            sum = fmaf(cx[a], row, sum);
-        }
-        g[c] = sum;
-    }
-    const float4 f = frame[ti];
+    const float4 g4 = far4[ti], f = frame[ti];
+    const float g[4] = {g4.x, g4.y, g4.z, g4.w};
     float ss, sn;
     to_local<float>(f.x, f.y, g, ss, sn);
     const int64_t e = perm[ti];
     y[e] += scale * (double)ss;
     y[Ntot + e] += scale * (double)sn;
-    y[2 * Ntot + e] += scale * (double)g[3];
+    y[2 * Ntot + e] += scale * (double)g4.w;
 }
 
 // -------------------------------------------------------------------- dense
@@ -1278,6 +1281,8 @@ ddm_status ensure_workspace(ddm_ctx *ctx, ddm_tree *t) {
     dfree(t->Fl, t->stream);
     t->W = t->Fl = nullptr;
     size_t sz = (size_t)t->n_cells * 4 * n * n * sizeof(float);
+    if (!t->far4 && dalloc(&t->far4, (size_t)t->n * sizeof(float4), t->stream) != cudaSuccess)
+        return ctx_fail(ctx, DDM_ENOMEM, "FMM workspace allocation failed");
     if (dalloc(&t->W, sz, t->stream) != cudaSuccess || dalloc(&t->Fl, sz, t->stream) != cudaSuccess)
         return ctx_fail(ctx, DDM_ENOMEM, "FMM workspace allocation failed");
     t->ncheb_alloc = n;
@@ -1440,15 +1445,14 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
                                                             t->Fl, ctx->d_err);
         }
         prof_end(ctx, 4, 2);
-        // downward pass: L2L chains to the leaves in one launch
-        if (L >= 3) {
-            prof_begin(ctx, 5);
+        // downward pass: L2L chains to the leaves and L2P at their targets, one launch
+        prof_begin(ctx, 5);
 #define DDM_DOWN(NN)                                                                                        \
-    k_down<NN><<<(unsigned)nleaf, L2L_T, 0, fs>>>(loff, L, t->cell_ix, t->cell_iy, t->cell_parent, ctx->cheb_T, t->Fl)
-            DDM_CHEB_SWITCH(n, DDM_DOWN);
+    k_down<NN><<<(unsigned)nleaf, L2L_T, 0, fs>>>(loff, L, t->cell_ix, t->cell_iy, t->cell_parent, ctx->cheb_T, t->Fl, \
+                                                  t->cell_start, t->cell_end, t->g_rel, wL, t->far4)
+        DDM_CHEB_SWITCH(n, DDM_DOWN);
 #undef DDM_DOWN
-            prof_end(ctx, 5, 1);
-        }
+        prof_end(ctx, 5, 1);
     }
     if (overlap) DDM_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_join, fs));
     prof_begin(ctx, 6);
@@ -1463,11 +1467,7 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
     prof_end(ctx, 6, 1);
     if (use_far) {
         if (overlap) DDM_CUDA_TRY(ctx, cudaStreamWaitEvent(s, ctx->ev_join, 0));
-#define DDM_L2P(NN)                                                                                         \
-    k_l2p<NN><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(t->elem_leaf, t->g_rel, t->g_frame, t->perm, loff, wL, t->Fl, \
-                                                          N, scale, y)
-        DDM_CHEB_SWITCH(n, DDM_L2P);
-#undef DDM_L2P
+        k_far_add<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(t->far4, t->g_frame, t->perm, N, scale, y);
     }
     DDM_CUDA_TRY(ctx, cudaGetLastError());
     return DDM_OK;

@@ -100,6 +100,7 @@ struct ddm_tree {
     // per-tree workspaces
     float *W;                  // multipole weights, 4 n^2 per cell
     float *Fl;                 // local expansions, 4 n^2 per cell
+    float4 *far4;              // far field (global sxx, syy, sxy, p) at each sorted target
     float4 *chg;               // sorted charges (Dx, Dy, q, 0) per element
     int ncheb_alloc;
 };

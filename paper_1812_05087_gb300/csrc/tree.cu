@@ -544,7 +544,7 @@ void tree_free(ddm_tree *t) {
     if (!t) return;
     void *ps[] = {t->mk_work, t->pb_off, t->pb_elem, t->pb_moff, t->pb_inv, t->mk_off, t->mk_pair, t->grp_off, t->grp_leaf, t->perm, t->cell_key, t->cell_ix, t->cell_iy, t->cell_start, t->cell_end, t->cell_parent, t->cell_child0, t->cell_nchild, t->up_cnt,
                   t->il_off, t->il_idx, t->nb_off, t->nb_idx, t->nb_tab, t->near_items, t->elem_leaf, t->g_rel, t->g_frame,
-                  t->xy_sorted, t->xy_caller, t->W, t->Fl, t->chg};
+                  t->xy_sorted, t->xy_caller, t->W, t->Fl, t->far4, t->chg};
     for (void *p : ps) dfree(p, t->stream);
     for (double *p : t->win_blk) dfree(p, t->stream);
     for (float *p : t->ops_set) dfree(p, t->stream);
