@@ -436,6 +436,8 @@ __global__ void k_m2l_ops(KConst<float> k, Win<float> w, int L, double h0, int n
 // still releases its tensor memory.
 namespace tc {
 constexpr int BM = 128, BN = 64, BK = 32, THREADS = 128, NSTAGE = 2;
+constexpr int KSPLIT = 1;                                  // CTAs sharing one tile's K range (sums meet in the atomics)
+constexpr int ROWB = BK * 4, CPR = ROWB / 16;             // bytes and 16-byte chunks per tile row
 constexpr int A_BYTES = BM * BK * 4, B_BYTES = BN * BK * 4;
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;     // hi and lo of both operands
 constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024;    // + room to align to 1024 B
@@ -449,16 +451,23 @@ constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// Tiles are K-major with one ROWB-byte row per matrix row, swizzled in the
+// hardware's pattern for that row width: 128-byte rows (BK = 32) XOR the
+// 16-byte chunk index with (row mod 8), 1024 B between 8-row groups, swizzle
+// mode 2; 64-byte rows (BK = 16) XOR it with (row / 2 mod 4), 512 B between
+// 8-row groups, swizzle mode 4.
 // shared-memory matrix descriptor: start address >> 4 (bits 0-13), leading
-// byte offset (unused for swizzled K-major, 16 B), stride byte offset 1024 B
-// between 8-row groups (bits 32-45), descriptor version 1 (bit 46),
-// 128-byte swizzle (bits 61-63 = 2)
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
-    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+// byte offset (unused for swizzled K-major, 16 B), stride byte offset
+// (bits 32-45), descriptor version 1 (bit 46), swizzle mode (bits 61-63)
+__device__ __forceinline__ uint64_t sw_desc(uint32_t addr) {
+    constexpr uint64_t sbo = ROWB == 128 ? 1024 : 512, mode = ROWB == 128 ? 2 : 4;
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((sbo >> 4) << 32) | ((uint64_t)1 << 46) |
+           (mode << 61);
 }
-// byte offset of 16-byte chunk c of row r in a 128-byte-swizzled tile
-__device__ __forceinline__ uint32_t sw128_off(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
+// byte offset of 16-byte chunk c of row r in a swizzled tile
+__device__ __forceinline__ uint32_t sw_off(int r, int c) {
+    return ROWB == 128 ? (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)) : (uint32_t)(r * 64 + ((c ^ ((r >> 1) & 3)) << 4));
+}
 
 __device__ __forceinline__ void split4(float4 v, float4 &h, float4 &l) {
     h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
@@ -562,42 +571,45 @@ __global__ void __launch_bounds__(tc::THREADS) k_m2l_tc(const int2 *work, const 
     __syncthreads();
     fence_after_sync();
     const uint32_t tmem = s_tmem;
-    const int nkb = (ld + BK - 1) / BK;
+    // this CTA's share of the K chunks
+    const int nkt = (ld + BK - 1) / BK, per = (nkt + KSPLIT - 1) / KSPLIT;
+    const int kbeg = blockIdx.z * per, nkb = max(0, min(nkt, kbeg + per) - kbeg);
     for (int kb = 0; kb < nkb; ++kb) {
         const int st = kb % NSTAGE;
         uint8_t *a_hi = base + st * STAGE_BYTES, *a_lo = a_hi + A_BYTES, *b_hi = a_lo + A_BYTES,
                 *b_lo = b_hi + B_BYTES;
-        const int k0 = kb * BK;
-        float4 va[8], vb[4];
+        const int k0 = (kbeg + kb) * BK;
+        constexpr int NA = BM * CPR / THREADS, NB = BN * CPR / THREADS;   // float4 per thread
+        float4 va[NA], vb[NB];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {        // operator rows r0.., 8 float4 per 32-wide K chunk
-            int idx = tid + i * THREADS, row = idx >> 3, c = idx & 7, gr = r0 + row, gk = k0 + 4 * c;
+        for (int i = 0; i < NA; ++i) {       // operator rows r0.., CPR float4 per K chunk
+            int idx = tid + i * THREADS, row = idx / CPR, c = idx % CPR, gr = r0 + row, gk = k0 + 4 * c;
             va[i] = (gr < ld && gk < ld) ? __ldg(reinterpret_cast<const float4 *>(K + (int64_t)gr * ld + gk))
                                          : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {        // source weights, one column per pair
-            int idx = tid + i * THREADS, col = idx >> 3, c = idx & 7, J = sJ[col], gk = k0 + 4 * c;
+        for (int i = 0; i < NB; ++i) {       // source weights, one column per pair
+            int idx = tid + i * THREADS, col = idx / CPR, c = idx % CPR, J = sJ[col], gk = k0 + 4 * c;
             vb[i] = (J >= 0 && gk < ld) ? __ldg(reinterpret_cast<const float4 *>(W + (int64_t)J * ld + gk))
                                         : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         // the MMAs that last read this stage (issued NSTAGE chunks ago) must be done
         if (kb >= NSTAGE) mbar_wait(&bar[st], (uint32_t)((kb / NSTAGE - 1) & 1), verr);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            int idx = tid + i * THREADS, row = idx >> 3, c = idx & 7;
+        for (int i = 0; i < NA; ++i) {
+            int idx = tid + i * THREADS, row = idx / CPR, c = idx % CPR;
             float4 h, l;
             split4(va[i], h, l);
-            uint32_t off = sw128_off(row, c);
+            uint32_t off = sw_off(row, c);
             *reinterpret_cast<float4 *>(a_hi + off) = h;
             *reinterpret_cast<float4 *>(a_lo + off) = l;
         }
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            int idx = tid + i * THREADS, col = idx >> 3, c = idx & 7;
+        for (int i = 0; i < NB; ++i) {
+            int idx = tid + i * THREADS, col = idx / CPR, c = idx % CPR;
             float4 h, l;
             split4(vb[i], h, l);
-            uint32_t off = sw128_off(col, c);
+            uint32_t off = sw_off(col, c);
             *reinterpret_cast<float4 *>(b_hi + off) = h;
             *reinterpret_cast<float4 *>(b_lo + off) = l;
         }
@@ -609,18 +621,18 @@ __global__ void __launch_bounds__(tc::THREADS) k_m2l_tc(const int2 *work, const 
 #pragma unroll
             for (int kk = 0; kk < BK / 8; ++kk) {   // K = 8 per MMA: 32 bytes along the swizzled row
                 const uint32_t o = 32u * kk;
-                mma_tf32(tmem, sw128_desc(al + o), sw128_desc(bh + o), (kb | kk) != 0);
-                mma_tf32(tmem, sw128_desc(ah + o), sw128_desc(bl + o), 1u);
-                mma_tf32(tmem, sw128_desc(ah + o), sw128_desc(bh + o), 1u);
+                mma_tf32(tmem, sw_desc(al + o), sw_desc(bh + o), (kb | kk) != 0);
+                mma_tf32(tmem, sw_desc(ah + o), sw_desc(bl + o), 1u);
+                mma_tf32(tmem, sw_desc(ah + o), sw_desc(bh + o), 1u);
             }
             mma_commit(&bar[st]);
         }
     }
     // all MMAs done (the last commit covers every earlier one of the thread)
-    mbar_wait(&bar[(nkb - 1) % NSTAGE], (uint32_t)(((nkb - 1) / NSTAGE) & 1), verr);
+    if (nkb > 0) mbar_wait(&bar[(nkb - 1) % NSTAGE], (uint32_t)(((nkb - 1) / NSTAGE) & 1), verr);
     fence_after_sync();
     const int row = r0 + warp * 32 + lane;
-    const bool ok = *verr == 0;
+    const bool ok = *verr == 0 && nkb > 0;
 #pragma unroll
     for (int c0 = 0; c0 < BN; c0 += 16) {
         float v[16];
@@ -637,7 +649,7 @@ __global__ void __launch_bounds__(tc::THREADS) k_m2l_tc(const int2 *work, const 
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
-    if (tid == 0 && !ok) atomicExch(err, 1);
+    if (tid == 0 && *verr) atomicExch(err, 1);
 }
 
 // ----------------------------------------------------------- leaf L2P + P2P
@@ -1440,7 +1452,8 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
                                                        tc::SMEM_BYTES));
                 attr[ctx->device & 63] = true;
             }
-            dim3 g((unsigned)t->n_work, (unsigned)((4 * n2 + tc::BM - 1) / tc::BM));
+            dim3 g((unsigned)t->n_work, (unsigned)((4 * n2 + tc::BM - 1) / tc::BM),
+                   (unsigned)std::min(tc::KSPLIT, (4 * n2 + tc::BK - 1) / tc::BK));
             k_m2l_tc<<<g, tc::THREADS, tc::SMEM_BYTES, fs>>>(t->mk_work, t->mk_off, t->mk_pair, n, ops, t->W,
                                                             t->Fl, ctx->d_err);
         }
