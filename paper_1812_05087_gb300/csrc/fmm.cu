@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(UP_T) k_up(const int32_t *cstart, const int32_
                                              const float *T, const double *x, const int64_t *perm,
                                              const float4 *grel, const float4 *frame, const double *blk,
                                              int64_t n_elem, double scale, int overwrite, double *y, float4 *chg,
-                                             float hL, float *W) {
+                                             float hL, float *W, float *Fz) {
     using S = UpSmem<N>;
     constexpr int N2 = S::N2, NOUT = S::NOUT, SXS = S::SXS, NE = (N2 + 31) / 32, KO = (NOUT + UP_T - 1) / UP_T;
     __shared__ __align__(16) float sm[S::SIZE];
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(UP_T) k_up(const int32_t *cstart, const int32_
             for (int c = 0; c < 4; ++c) red[warp * NOUT + c * N2 + ent] = acc[j][c];
     }
     __syncthreads();
-    float *Wc = W + leaf * NOUT;
+    float *Wc = W + leaf * NOUT, *Fc = Fz + leaf * NOUT;
 #pragma unroll
     for (int k = 0; k < KO; ++k) {
         int o = tid + k * UP_T;
@@ -230,6 +230,7 @@ __global__ void __launch_bounds__(UP_T) k_up(const int32_t *cstart, const int32_
 #pragma unroll
             for (int w = 0; w < UP_W; ++w) v += red[w * NOUT + o];
             Wc[o] = v;
+            Fc[o] = 0.f;                          // local expansion: M2L adds into it next
         }
     }
     float *sw = sm, *tmp = sm + 4 * NOUT;
@@ -264,11 +265,12 @@ __global__ void __launch_bounds__(UP_T) k_up(const int32_t *cstart, const int32_
         }
         __syncthreads();
         // W^p[c][a][b] = sum_ch sum_b' Ty[b][b'] tmp[ch][c][a][b']
-        float *Wp = W + (int64_t)p * NOUT;
+        float *Wp = W + (int64_t)p * NOUT, *Fp = Fz + (int64_t)p * NOUT;
 #pragma unroll
         for (int k = 0; k < KO; ++k) {
             int o = tid + k * UP_T;
             if (o < NOUT) {
+                Fp[o] = 0.f;
                 int c = o / N2, a = (o / N) % N, b = o % N;
                 float s = 0.f;
                 for (int ch = 0; ch < nc; ++ch) {
@@ -1406,7 +1408,7 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
     (overlap ? k_up<NN, false> : k_up<NN, true>)<<<(unsigned)nleaf, UP_T, 0, fs>>>(                                \
         t->cell_start, t->cell_end, loff, off3, t->cell_ix, t->cell_iy, t->cell_parent, t->cell_child0,              \
         t->cell_nchild, t->up_cnt, ctx->cheb_T, x, t->perm, t->g_rel, t->g_frame, blk, N, scale, overwrite, y,       \
-        t->chg, hL, t->W)
+        t->chg, hL, t->W, t->Fl)
         DDM_CHEB_SWITCH(n, DDM_UP);
 #undef DDM_UP
         prof_end(ctx, 2, 1);
@@ -1444,7 +1446,7 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
         }
         const float *ops = t->ops_set[os];
         prof_begin(ctx, 4);
-        DDM_CUDA_TRY(ctx, cudaMemsetAsync(t->Fl, 0, (size_t)t->n_cells * 4 * n2 * sizeof(float), fs));
+        // (the local expansions of every cell at levels >= 2 were zeroed by k_up)
         if (t->n_work > 0) {
             static bool attr[64] = {false};
             if (!attr[ctx->device & 63]) {
@@ -1457,7 +1459,7 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
             k_m2l_tc<<<g, tc::THREADS, tc::SMEM_BYTES, fs>>>(t->mk_work, t->mk_off, t->mk_pair, n, ops, t->W,
                                                             t->Fl, ctx->d_err);
         }
-        prof_end(ctx, 4, 2);
+        prof_end(ctx, 4, 1);
         // downward pass: L2L chains to the leaves and L2P at their targets, one launch
         prof_begin(ctx, 5);
 #define DDM_DOWN(NN)                                                                                        \
