@@ -132,18 +132,25 @@ __global__ void k_dots_final(const double *part, int G, int pld, int nv, double 
         if (hcol) hcol[v] = accumulate ? hcol[v] + sum : sum;
     }
 }
-// One Arnoldi orthogonalisation step as a single cooperative kernel (its
-// blocks meet at grid barriers, so it is launched cooperatively, which
-// guarantees they are all resident):
-//   1. partial dot products of w with V[0..nv) per block chunk;
-//   2. block v sums vector v's partials: h[v], hcol[v] (= or += h[v]);
-//   3. w -= V h per chunk, partial ||w||^2;
-//   4. every block sums the norm partials and takes the same decision
-//      (Daniel-Gragg-Kaufman-Stewart): a second pass (1-3 again, hcol
-//      accumulating) when ||w_new||^2 < (||w_new||^2 + |h|^2) / 2;
-//   5. V[nv] = w / ||w||, hcol[nv] = ||w||.
-// The barriers give up after a bounded number of polls and raise the error
-// word (the results are then invalid, nothing hangs).
+// One Arnoldi orthogonalisation step as a single cooperative kernel, one
+// block per SM (its blocks meet at grid barriers, so it is launched
+// cooperatively, which guarantees they are all resident).  A pass:
+//   1. partial dot products of w with V[0..nv) and with itself over the
+//      block's chunk (warp q takes vectors q, q + OR_W, ...);   barrier
+//   2. every block sums all partials itself, in the same order, so h and
+//      ||w||^2 are identical everywhere (block 0 records hcol = or += h);
+//      w -= V h on the chunk;
+//   3. ||w_new||^2 = ||w||^2 - |h|^2 (V orthonormal) and the
+//      Daniel-Gragg-Kaufman-Stewart decision, the same in every block: a
+//      second pass when ||w_new||^2 < |h|^2, i.e. when more than half of
+//      ||w||^2 was removed.  Without a second pass the difference keeps at
+//      least half of ||w||^2, so it is accurate to a few rounding units; in
+//      the second pass h is small against the explicit ||w||^2.
+// Then V[nv] = w / ||w||, hcol[nv] = ||w||: one grid barrier per pass.  The
+// partials are stored by vector (part[v G + block]) for coalesced sums, each
+// pass in its own half of part[] (2 (nv + 1) G doubles).  The
+// barriers give up after a bounded number of polls and raise the error word
+// (the results are then invalid, nothing hangs).
 constexpr long long GB_POLLS = 1ll << 22;
 __device__ __forceinline__ void grid_barrier(unsigned *bar, int *err) {
     __syncthreads();
@@ -166,113 +173,64 @@ __device__ __forceinline__ void grid_barrier(unsigned *bar, int *err) {
     }
     __syncthreads();
 }
-__global__ void __launch_bounds__(DP_T) k_arnoldi_orth(double *V, int64_t len, int nv, double *w, int64_t chunk,
-                                                       double *part, int pld, double *h, double *hcol,
-                                                       unsigned *bar, int *err) {
-    __shared__ double red[DP_T / 32][DP_V];
-    __shared__ double sh[512];
-    __shared__ double s_nrm, s_hh;
+constexpr int OR_T = 512, OR_W = OR_T / 32;
+__global__ void __launch_bounds__(OR_T) k_arnoldi_orth(double *V, int64_t len, int nv, double *w, int64_t chunk,
+                                                       double *part, double *hcol, unsigned *bar, int *err) {
+    __shared__ double sh[512 + 1];
+    __shared__ double s_hh;
     const int64_t i0 = blockIdx.x * chunk, i1 = i0 + chunk < len ? i0 + chunk : len;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int G = gridDim.x;
     double nrm2 = 0.0;
     for (int pass = 0; pass < 2; ++pass) {
-        // 1. partial dots
-        for (int v0 = 0; v0 < nv; v0 += DP_V) {
-            double acc[DP_V];
+        // each pass its own partials: a block may start the second pass while
+        // another still sums the first pass's
+        double *pp = part + (int64_t)pass * (nv + 1) * G;
+        // 1. partial dots; vector nv is w itself
+        for (int v = wid; v <= nv; v += OR_W) {
+            const double *Vv = v < nv ? V + (int64_t)v * len : w;
+            double acc = 0.0;
+            for (int64_t i = i0 + lane; i < i1; i += 32) acc = fma(Vv[i], w[i], acc);
 #pragma unroll
-            for (int q = 0; q < DP_V; ++q) acc[q] = 0.0;
-            for (int64_t i = i0 + threadIdx.x; i < i1; i += DP_T) {
-                const double wi = w[i];
-#pragma unroll
-                for (int q = 0; q < DP_V; ++q)
-                    if (v0 + q < nv) acc[q] = fma(V[(int64_t)(v0 + q) * len + i], wi, acc[q]);
-            }
-#pragma unroll
-            for (int q = 0; q < DP_V; ++q)
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xFFFFFFFFu, acc[q], o);
-            if (lane == 0)
-#pragma unroll
-                for (int q = 0; q < DP_V; ++q) red[wid][q] = acc[q];
-            __syncthreads();
-            if (threadIdx.x < DP_V && v0 + threadIdx.x < nv) {
-                double sum = 0.0;
-#pragma unroll
-                for (int k = 0; k < DP_T / 32; ++k) sum += red[k][threadIdx.x];
-                part[(int64_t)blockIdx.x * pld + v0 + threadIdx.x] = sum;
-            }
-            __syncthreads();
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+            if (lane == 0) pp[(int64_t)v * G + blockIdx.x] = acc;
         }
         grid_barrier(bar, err);
-        // 2. block v reduces vector v
-        for (int v = blockIdx.x; v < nv; v += G) {
+        // 2. h and ||w||^2 (every block, same order)
+        for (int v = wid; v <= nv; v += OR_W) {
             double sum = 0.0;
-            for (int b = threadIdx.x; b < G; b += DP_T) sum += __ldcg(part + (int64_t)b * pld + v);
+            for (int b = lane; b < G; b += 32) sum += __ldcg(pp + (int64_t)v * G + b);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
-            if (lane == 0) red[wid][0] = sum;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                double tot = 0.0;
-#pragma unroll
-                for (int k = 0; k < DP_T / 32; ++k) tot += red[k][0];
-                h[v] = tot;
-                hcol[v] = pass ? hcol[v] + tot : tot;
-            }
-            __syncthreads();
+            if (lane == 0) sh[v] = sum;
         }
-        grid_barrier(bar, err);
-        // 3. w -= V h, partial norms
-        for (int v = threadIdx.x; v < nv; v += DP_T) sh[v] = __ldcg(h + v);
         __syncthreads();
-        double acc = 0.0;
-        for (int64_t i = i0 + threadIdx.x; i < i1; i += DP_T) {
+        if (wid == 0) {
+            double hh = 0.0;
+            for (int v = lane; v < nv; v += 32) hh = fma(sh[v], sh[v], hh);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) hh += __shfl_xor_sync(0xFFFFFFFFu, hh, o);
+            if (lane == 0) s_hh = hh;
+        }
+        if (blockIdx.x == 0)
+            for (int v = tid; v < nv; v += OR_T) hcol[v] = pass ? hcol[v] + sh[v] : sh[v];
+        for (int64_t i = i0 + tid; i < i1; i += OR_T) {
             double sum = 0.0;
             for (int v = 0; v < nv; ++v) sum = fma(sh[v], V[(int64_t)v * len + i], sum);
-            const double wi = w[i] - sum;
-            w[i] = wi;
-            acc = fma(wi, wi, acc);
+            w[i] -= sum;
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
-        if (lane == 0) red[wid][0] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double tot = 0.0;
-#pragma unroll
-            for (int k = 0; k < DP_T / 32; ++k) tot += red[k][0];
-            part[(int64_t)blockIdx.x * pld] = tot;
-        }
-        grid_barrier(bar, err);
-        // 4. norm and the second-pass decision, the same in every block
-        if (wid == 0) {
-            double sum = 0.0, hh = 0.0;
-            for (int b = lane; b < G; b += 32) sum += __ldcg(part + (int64_t)b * pld);
-            for (int v = lane; v < nv; v += 32) hh += sh[v] * sh[v];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
-                hh += __shfl_xor_sync(0xFFFFFFFFu, hh, o);
-            }
-            if (lane == 0) {
-                s_nrm = sum;
-                s_hh = hh;
-            }
-        }
-        __syncthreads();
-        nrm2 = s_nrm;
-        const bool again = pass == 0 && nrm2 < 0.5 * (nrm2 + s_hh);
-        // the norm partials in part[] are read by every block before any
-        // block overwrites part[] in the next pass
-        grid_barrier(bar, err);
-        if (!again) break;
+        __syncthreads();                      // s_hh written; w updated before the next pass reads it
+        // 3. norm and the second-pass decision
+        const double hh = s_hh, rest = sh[nv] - hh;
+        nrm2 = rest > 0.0 ? rest : 0.0;
+        if (!(pass == 0 && rest < hh)) break;
+        __syncthreads();                      // sh is rewritten by the next pass
     }
-    // 5. next basis vector
-    const double nrm = sqrt(nrm2);
-    if (blockIdx.x == 0 && threadIdx.x == 0) hcol[nv] = nrm;
+    // next basis vector
+    const double nrm = sqrt(nrm2), inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    if (blockIdx.x == 0 && tid == 0) hcol[nv] = nrm;
     double *out = V + (int64_t)nv * len;
-    for (int64_t i = i0 + threadIdx.x; i < i1; i += DP_T) out[i] = nrm > 0.0 ? w[i] / nrm : 0.0;
+    for (int64_t i = i0 + tid; i < i1; i += OR_T) out[i] = w[i] * inv;
 }
 // restrict a 3N product to the system rows (RATE: sigma_n + p)
 // (combine = 1 for products, 0 for a right-hand side, whose rows are already
@@ -305,10 +263,10 @@ struct GmresWork {
     int cap_m = 0;
     cudaStream_t st = nullptr;
     double *V = nullptr, *w = nullptr, *z = nullptr, *full = nullptr, *y3 = nullptr, *b = nullptr;
-    double *h = nullptr, *hcol = nullptr, *nrm = nullptr, *Minv = nullptr, *yv = nullptr, *part = nullptr;
+    double *hcol = nullptr, *nrm = nullptr, *Minv = nullptr, *yv = nullptr, *part = nullptr;
     unsigned *cnt = nullptr;   // 2 last-block counters (zero between launches), then the DGKS flag
     void release() {
-        double *ps[] = {V, w, z, full, y3, b, h, hcol, nrm, Minv, yv, part};
+        double *ps[] = {V, w, z, full, y3, b, hcol, nrm, Minv, yv, part};
         cudaStream_t s = st;
         for (double *p : ps) dfree(p, s);
         dfree(cnt, s);
@@ -526,12 +484,12 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
         bool ok = dalloc(&g.V, (size_t)(m + 1) * len * sizeof(double), s) == cudaSuccess &&
                   dalloc(&g.w, v3, s) == cudaSuccess && dalloc(&g.z, v3, s) == cudaSuccess &&
                   dalloc(&g.full, v3, s) == cudaSuccess && dalloc(&g.y3, v3, s) == cudaSuccess &&
-                  dalloc(&g.b, v3, s) == cudaSuccess && dalloc(&g.h, (m + 2) * sizeof(double), s) == cudaSuccess &&
+                  dalloc(&g.b, v3, s) == cudaSuccess &&
                   dalloc(&g.hcol, (m + 2) * sizeof(double), s) == cudaSuccess &&
                   dalloc(&g.nrm, sizeof(double), s) == cudaSuccess &&
                   dalloc(&g.Minv, 9 * N * sizeof(double), s) == cudaSuccess &&
                   dalloc(&g.yv, (m + 1) * sizeof(double), s) == cudaSuccess &&
-                  dalloc(&g.part, (size_t)DP_G * (m + 2) * sizeof(double), s) == cudaSuccess &&
+                  dalloc(&g.part, (size_t)2 * DP_G * (m + 2) * sizeof(double), s) == cudaSuccess &&
                   dalloc(&g.cnt, 4 * sizeof(unsigned), s) == cudaSuccess &&
                   cudaMemsetAsync(g.cnt, 0, 4 * sizeof(unsigned), s) == cudaSuccess;
         if (!ok) { g.release(); return ctx_fail(ctx, DDM_ENOMEM, "GMRES workspace allocation failed"); }
@@ -554,9 +512,10 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
     int orth_grid = DP_G;
     {
         int per_sm = 0, nsm = 0;
-        DDM_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi_orth, DP_T, 0));
+        DDM_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi_orth, OR_T, 0));
         DDM_CUDA_TRY(ctx, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
-        orth_grid = std::max(1, std::min(DP_G, per_sm * nsm));
+        if (per_sm < 1) return ctx_fail(ctx, DDM_ECUDA, "ddm_gmres_solve: orthogonalisation kernel cannot be resident");
+        orth_grid = std::max(1, std::min(DP_G, nsm));
     }
     const int64_t orth_chunk = (len + orth_grid - 1) / orth_grid;
     // h[v] = V[v] . w, v < nv (hcol: see k_dots_final)
@@ -634,6 +593,7 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
         int j = 0;
         for (; j < m && iters < P.max_iters; ++j, ++iters) {
             double *vj = g.V + (int64_t)j * len;
+            prof_begin(ctx, 8);
             if ((st = pb_apply(ctx, t, sys, vj, g.full, s))) return st;
             if (sys == DDM_SYS_PRESSURE) {        // the 3N product is already the system's rows
                 if ((st = op_apply(ctx, t, 0.0, dt, g.full, g.w, mode, 0, 1.0))) return st;
@@ -642,17 +602,18 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
                 k_restrict<<<nblk(N), 256, 0, s>>>(g.y3, N, sys, 1, g.w);
             }
             // orthogonalise against V[0..j] and normalise (one cooperative kernel)
+            prof_begin(ctx, 8);
             {
-                double *Vp = g.V, *wp = g.w, *pp = g.part, *hp = g.h, *hcp = g.hcol;
-                int nvj = j + 1, pl = pld;
+                double *Vp = g.V, *wp = g.w, *pp = g.part, *hcp = g.hcol;
+                int nvj = j + 1;
                 int64_t ln = len, ch = orth_chunk;
                 unsigned *bp = g.cnt;
                 int *ep = ctx->d_err;
-                void *args[] = {&Vp, &ln, &nvj, &wp, &ch, &pp, &pl, &hp, &hcp, &bp, &ep};
-                DDM_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void *)k_arnoldi_orth, dim3(orth_grid), dim3(DP_T),
+                void *args[] = {&Vp, &ln, &nvj, &wp, &ch, &pp, &hcp, &bp, &ep};
+                DDM_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void *)k_arnoldi_orth, dim3(orth_grid), dim3(OR_T),
                                                               args, 0, s));
             }
-            prof_end(ctx, 8, 2);      // precond, orthogonalisation
+            prof_end(ctx, 8, 1);      // orthogonalisation
             DDM_CUDA_TRY(ctx, cudaMemcpyAsync(hc.data(), g.hcol, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
             DDM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
             // Givens rotations on the new column

@@ -88,9 +88,15 @@ __device__ __forceinline__ void prep_elem(int64_t i, const double *x, const int6
 }
 
 __global__ void k_prep(const double *x, const int64_t *perm, const float4 *frame, const double *blk, int64_t n,
-                       double scale, int overwrite, float4 *chg, double *y) {
+                       double scale, int overwrite, float4 *chg, double *y, float *Wz, float *Fz, int64_t nz) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) prep_elem(i, x, perm, frame, blk, n, scale, overwrite, chg, y);
+    // zero the weights and local expansions of the cells above the leaves
+    // (the upward pass adds into them)
+    for (int64_t z = i; z < nz; z += (int64_t)gridDim.x * blockDim.x) {
+        Wz[z] = 0.f;
+        Fz[z] = 0.f;
+    }
 }
 
 // --------------------------------------------------------- own element (FP64)
@@ -127,59 +133,47 @@ __device__ __forceinline__ void cardinal_col(float x, float *col, int stride) {
 }
 
 constexpr int UP_T = 256, UP_W = UP_T / 32;
-// shared-memory floats of the fused passes: the P2M staging (cardinals of
-// 128 points in x and y, 128 point weights) and the M2M staging (weights of
-// up to 4 children and their half-transferred copies) share one buffer
+// shared-memory floats of the upward pass: the P2M staging (cardinals of
+// UP_T points in x and y, UP_T point weights), the warps' partial weights
+// and the M2M staging (leaf weights and their half-transferred copy) share
+// one buffer
 template <int N>
 struct UpSmem {
     static constexpr int N2 = N * N, NOUT = 4 * N2, SXS = UP_T + 1;
     static constexpr int P2M = 2 * N * SXS + 4 * UP_T;
-    static constexpr int M2M = 8 * NOUT;
+    static constexpr int M2M = 2 * NOUT;
     static constexpr int RED = UP_W * NOUT;
     static constexpr int SIZE = (P2M > M2M ? P2M : M2M) > RED ? (P2M > M2M ? P2M : M2M) : RED;
 };
 
-// One block per leaf: charges and own-element terms of the leaf's elements,
-// P2M of the leaf (paper Sec. 3.3: W_m = sum_j int S_n(ybar_m, y) b_j ds,
-// Gauss rule with n points per element, exact for the polynomial
-// cardinals), then M2M towards level 2.  The block that completes the
-// last child of a parent (counted with a device-scope atomic after a
-// fence) computes the parent's weights from all its children in a fixed
-// order, so the whole upward pass is one launch, needs no zeroed buffer
-// and sums in the same order every time.  Nothing waits: the other blocks
-// simply finish.  The last block resets the parent's counter for the next
-// pass.
+// One block per leaf: P2M of the leaf (paper Sec. 3.3: W_m = sum_j int
+// S_n(ybar_m, y) b_j ds, Gauss rule with n points per element, exact for the
+// polynomial cardinals), then the leaf's share of every ancestor's weights
+// down to level 2 (M2M).  The charges come from the charge kernel, which
+// also zeroed the ancestors' weights.
 //
 // P2M: lane owns node entries (a, b) = lane + 32 j and all 4 components;
 // the UP_W warps take every UP_W-th point and are summed at the end.
-template <int N, bool PREP>
-__global__ void __launch_bounds__(UP_T) k_up(const int32_t *cstart, const int32_t *cend, int64_t loff, int64_t off3,
+template <int N>
+__global__ void __launch_bounds__(UP_T) k_up(const int32_t *cstart, const int32_t *cend, int64_t loff, int L,
                                              const int32_t *cix, const int32_t *ciy, const int32_t *parent,
-                                             const int32_t *child0, const int32_t *nchild, int32_t *cnt,
-                                             const float *T, const double *x, const int64_t *perm,
-                                             const float4 *grel, const float4 *frame, const double *blk,
-                                             int64_t n_elem, double scale, int overwrite, double *y, float4 *chg,
-                                             float hL, float *W, float *Fz) {
+                                             const float4 *grel, const float4 *frame, const float4 *chg, float hL,
+                                             float *W, float *Fz) {
     using S = UpSmem<N>;
     constexpr int N2 = S::N2, NOUT = S::NOUT, SXS = S::SXS, NE = (N2 + 31) / 32, KO = (NOUT + UP_T - 1) / UP_T;
     __shared__ __align__(16) float sm[S::SIZE];
-    __shared__ float sT[2 * N2];
-    __shared__ int s_last, s_q[4];
+    __shared__ float sTx[N * N], sTy[N * N];   // leaf -> ancestor transfer, x and y
     float *sx = sm, *sy = sm + N * SXS;
     float4 *wd = reinterpret_cast<float4 *>(sm + 2 * N * SXS);   // 16-byte aligned: 2 N SXS is a multiple of 4
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t leaf = loff + blockIdx.x;
     const int s0 = cstart[leaf], s1 = cend[leaf];
-    if (PREP)
-        for (int i = s0 + tid; i < s1; i += UP_T) prep_elem(i, x, perm, frame, blk, n_elem, scale, overwrite, chg, y);
-    for (int i = tid; i < 2 * N2; i += UP_T) sT[i] = T[i];
     constexpr int nq = N;                     // Gauss points per element
     float acc[NE][4];
 #pragma unroll
     for (int j = 0; j < NE; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
     const float ih = 1.f / hL;
     const int npts = (s1 - s0) * nq;
-    __syncthreads();                          // charges of the leaf written
     for (int base = 0; base < npts; base += UP_T) {
         int p = base + tid;
         if (p < npts) {
@@ -222,68 +216,90 @@ __global__ void __launch_bounds__(UP_T) k_up(const int32_t *cstart, const int32_
     }
     __syncthreads();
     float *Wc = W + leaf * NOUT, *Fc = Fz + leaf * NOUT;
+    float wv[KO];
 #pragma unroll
     for (int k = 0; k < KO; ++k) {
         int o = tid + k * UP_T;
+        wv[k] = 0.f;
         if (o < NOUT) {
-            float v = 0.f;
 #pragma unroll
-            for (int w = 0; w < UP_W; ++w) v += red[w * NOUT + o];
-            Wc[o] = v;
+            for (int w = 0; w < UP_W; ++w) wv[k] += red[w * NOUT + o];
+            Wc[o] = wv[k];
             Fc[o] = 0.f;                          // local expansion: M2L adds into it next
         }
     }
-    float *sw = sm, *tmp = sm + 4 * NOUT;
-    int64_t cur = leaf;
-    while (cur >= off3) {                     // cur at level >= 3: its parent needs weights
-        __threadfence();                      // this thread's weights visible device-wide
-        __syncthreads();
-        if (tid == 0) {
-            int p = parent[cur];
-            int last = atomicAdd(&cnt[p], 1) == nchild[p] - 1;
-            if (last) cnt[p] = 0;
-            s_last = last;
+    // M2M straight to every ancestor down to level 2: the transfer from the
+    // leaf grid to an ancestor grid k levels up is again a separable
+    // Chebyshev interpolation, Tx[a][b'] = S_a(ancestor) at the leaf node b'
+    // (exact for the leaf's polynomial interpolant, as each M2M step is), so
+    // the leaves add into their ancestors directly (atomically; the internal
+    // cells were zeroed by the charge kernel) instead of level after level.
+    float *lw = sm + NOUT, *tmp = sm;          // leaf weights, scratch
+    __syncthreads();                           // the warp partials are read
+#pragma unroll
+    for (int k = 0; k < KO; ++k)
+        if (tid + k * UP_T < NOUT) lw[tid + k * UP_T] = wv[k];
+    const float *cheb = c_gl.cheb[N / 2 - 1], *bw = c_gl.bw[N / 2 - 1];
+    const int lx = cix[leaf], ly = ciy[leaf];
+    int64_t anc = leaf;
+    for (int l = L - 1; l >= 2; --l) {
+        anc = parent[anc];
+        const int k = L - l;                       // levels up
+        const float sc = 1.f / (float)(1 << k);
+        // leaf centre in the ancestor's [-1, 1] coordinates
+        const float cxl = 2.f * (((float)(lx - ((lx >> k) << k)) + 0.5f) * sc) - 1.f;
+        const float cyl = 2.f * (((float)(ly - ((ly >> k) << k)) + 0.5f) * sc) - 1.f;
+        __syncthreads();                           // tmp and the transfer matrices are rewritten
+        for (int e = tid; e < 2 * N * N; e += UP_T) {
+            const int dim = e / (N * N), ab = e % (N * N), aa = ab / N, bp = ab % N;
+            const float xp = (dim ? cyl : cxl) + cheb[bp] * sc;   // leaf node b' in ancestor coordinates
+            float sum = 0.f, va = 0.f;
+            int hit = -1;
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                const float d = xp - cheb[j];
+                if (fabsf(d) < 1e-7f) hit = j;
+                const float t = __fdividef(bw[j], d);
+                sum += t;
+                if (j == aa) va = t;
+            }
+            const float v = hit >= 0 ? (aa == hit ? 1.f : 0.f) : va * __fdividef(1.f, sum);
+            (dim ? sTy : sTx)[aa * N + bp] = v;
         }
         __syncthreads();
-        if (!s_last) return;
-        __threadfence();
-        const int p = parent[cur], c0 = child0[p], nc = nchild[p];
-        // the children's weights are contiguous; written by other blocks: via L2
-        const float *Wch = W + (int64_t)c0 * NOUT;
-        for (int i = tid; i < nc * NOUT; i += UP_T) sw[i] = __ldcg(Wch + i);
-        if (tid < nc) s_q[tid] = ((cix[c0 + tid] & 1) ? 1 : 0) | ((ciy[c0 + tid] & 1) ? 2 : 0);
-        __syncthreads();
-        // tmp[ch][c][a][b'] = sum_a' Tx[a][a'] W^ch[c][a'][b']
-        for (int i = tid; i < nc * NOUT; i += UP_T) {
-            int ch = i / NOUT, r = i % NOUT, c = r / N2, a = (r / N) % N, b = r % N;
-            const float *Tx = sT + ((s_q[ch] & 1) ? N2 : 0) + a * N;
-            const float *src = sw + ch * NOUT + c * N2 + b;
-            float s = 0.f;
+        float o[KO];
+        {
+            // tmp[c][a][b'] = sum_a' Tx[a][a'] lw[c][a'][b'];  out = sum_b' Ty[b][b'] tmp[c][a][b']
+            for (int i = tid; i < NOUT; i += UP_T) {
+                const int c = i / N2, aa = (i / N) % N, bb = i % N;
+                const float *src = lw + c * N2 + bb;
+                float sacc = 0.f;
 #pragma unroll
-            for (int k = 0; k < N; ++k) s = fmaf(Tx[k], src[k * N], s);
-            tmp[i] = s;
-        }
-        __syncthreads();
-        // W^p[c][a][b] = sum_ch sum_b' Ty[b][b'] tmp[ch][c][a][b']
-        float *Wp = W + (int64_t)p * NOUT, *Fp = Fz + (int64_t)p * NOUT;
+                for (int kk = 0; kk < N; ++kk) sacc = fmaf(sTx[aa * N + kk], src[kk * N], sacc);
+                tmp[i] = sacc;
+            }
+            __syncthreads();
 #pragma unroll
-        for (int k = 0; k < KO; ++k) {
-            int o = tid + k * UP_T;
-            if (o < NOUT) {
-                Fp[o] = 0.f;
-                int c = o / N2, a = (o / N) % N, b = o % N;
-                float s = 0.f;
-                for (int ch = 0; ch < nc; ++ch) {
-                    const float *Ty = sT + ((s_q[ch] & 2) ? N2 : 0) + b * N;
-                    const float *tc = tmp + ch * NOUT + c * N2 + a * N;
+            for (int kk = 0; kk < KO; ++kk) {
+                const int oi = tid + kk * UP_T;
+                float sacc = 0.f;
+                if (oi < NOUT) {
+                    const int c = oi / N2, aa = (oi / N) % N, bb = oi % N;
+                    const float *tc = tmp + c * N2 + aa * N;
 #pragma unroll
-                    for (int j = 0; j < N; ++j) s = fmaf(Ty[j], tc[j], s);
+                    for (int j = 0; j < N; ++j) sacc = fmaf(sTy[bb * N + j], tc[j], sacc);
                 }
-                Wp[o] = s;
+                o[kk] = sacc;
             }
         }
-        cur = p;
+        float *Wa = W + anc * NOUT;
+#pragma unroll
+        for (int kk = 0; kk < KO; ++kk) {
+            const int oi = tid + kk * UP_T;
+            if (oi < NOUT) atomicAdd(Wa + oi, o[kk]);
+        }
     }
+
 }
 
 // ----------------------------------------------------- downward pass (fused)
@@ -1369,9 +1385,14 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
     int64_t loff = t->lvl_off[L], nleaf = t->lvl_off[L + 1] - loff;
     float wL = (float)(2.0 * t->h0 / (double)(1 << L));
     int use_far = mode != DDM_MODE_DENSE && L >= 2;
-    if (!use_far) {
+    {
+        // charges; for the far field also zero the weights and local
+        // expansions of the cells on levels 2 .. L-1
+        const int64_t z0 = use_far ? t->lvl_off[2] : 0, z1 = use_far ? t->lvl_off[L] : 0;
+        const int64_t nz = (z1 - z0) * 4 * (int64_t)n2;
         prof_begin(ctx, 0);
-        k_prep<<<(N + TB - 1) / TB, TB, 0, s>>>(x, t->perm, t->g_frame, blk, N, scale, overwrite, t->chg, y);
+        k_prep<<<(unsigned)std::max<int64_t>((N + TB - 1) / TB, 1), TB, 0, s>>>(
+            x, t->perm, t->g_frame, blk, N, scale, overwrite, t->chg, y, t->W + z0 * 4 * n2, t->Fl + z0 * 4 * n2, nz);
         prof_end(ctx, 0, 1);
     }
     if (mode == DDM_MODE_DENSE) {
@@ -1396,19 +1417,15 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
     cudaStream_t fs = overlap ? ctx->aux : s;
     if (use_far) {
         float hL = 0.5f * wL;
-        int64_t off3 = L >= 3 ? t->lvl_off[3] : t->n_cells;
         if (overlap) {
-            k_prep<<<(N + TB - 1) / TB, TB, 0, s>>>(x, t->perm, t->g_frame, blk, N, scale, overwrite, t->chg, y);
             DDM_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_fork, s));
             DDM_CUDA_TRY(ctx, cudaStreamWaitEvent(fs, ctx->ev_fork, 0));
         }
-        // upward pass (with charges and own elements unless done above): P2M and M2M in one launch
+        // upward pass: P2M and M2M in one launch
         prof_begin(ctx, 2);
 #define DDM_UP(NN)                                                                                          \
-    (overlap ? k_up<NN, false> : k_up<NN, true>)<<<(unsigned)nleaf, UP_T, 0, fs>>>(                                \
-        t->cell_start, t->cell_end, loff, off3, t->cell_ix, t->cell_iy, t->cell_parent, t->cell_child0,              \
-        t->cell_nchild, t->up_cnt, ctx->cheb_T, x, t->perm, t->g_rel, t->g_frame, blk, N, scale, overwrite, y,       \
-        t->chg, hL, t->W, t->Fl)
+    k_up<NN><<<(unsigned)nleaf, UP_T, 0, fs>>>(t->cell_start, t->cell_end, loff, L, t->cell_ix, t->cell_iy,         \
+                                               t->cell_parent, t->g_rel, t->g_frame, t->chg, hL, t->W, t->Fl)
         DDM_CHEB_SWITCH(n, DDM_UP);
 #undef DDM_UP
         prof_end(ctx, 2, 1);

@@ -48,9 +48,6 @@ struct ddm_tree {
     int32_t *cell_ix, *cell_iy;// integer cell coordinates at the cell's level
     int32_t *cell_start, *cell_end;   // sorted element range
     int32_t *cell_parent;      // global cell index of the parent (-1 at level 0)
-    int32_t *cell_child0;      // global index of the first child (cells of one parent are contiguous)
-    int32_t *cell_nchild;      // number of non-empty children
-    int32_t *up_cnt;           // per cell: children done in the running upward pass (0 between passes)
     int32_t *il_off, *il_idx;  // interaction lists (CSR over cells)
     int32_t *nb_off, *nb_idx;  // neighbour lists of leaves incl. self (CSR over leaves, leaf-local)
     int4 *nb_tab;              // per neighbour entry: (element start, count, cell dx, cell dy)

@@ -234,40 +234,50 @@ __global__ void __launch_bounds__(1024, 1) k_pb_invert(const int32_t *boff, cons
         }
 }
 
-// z (3N layout, caller order) = Minv v (v in the system layout nc x N); one
-// warp per row, lanes along the row (coalesced); the unknown blocks beyond
-// nc are set to zero
-__global__ void k_pb_apply(const int32_t *boff, const int64_t *belem, const int64_t *moff, int nc, const float *Minv,
-                           const double *v, int64_t N, double *z, int zero_rest) {
+// z (3N layout, caller order) = Minv v (v in the system layout nc x N);
+// PA_S CTAs per chain block, each a slice of its rows; a warp takes PA_R rows
+// at a time, lanes along the rows (coalesced); the unknown blocks beyond nc
+// are set to zero
+constexpr int PA_T = 256, PA_WARPS = PA_T / 32, PA_R = 4, PA_S = 2;
+__global__ void __launch_bounds__(PA_T) k_pb_apply(const int32_t *boff, const int64_t *belem, const int64_t *moff,
+                                                   int nc, const float *Minv, const double *v, int64_t N, double *z,
+                                                   int zero_rest) {
     __shared__ float sv[INV_MAX];
-    const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int m = boff[b + 1] - boff[b], n = nc * m;
     const int64_t *el = belem + boff[b];
-    for (int c = threadIdx.x; c < n; c += blockDim.x) sv[c] = (float)v[(c / m) * N + el[c % m]];
+    for (int c = threadIdx.x; c < n; c += PA_T) sv[c] = (float)v[(c / m) * N + el[c % m]];
     __syncthreads();
     const float *A = Minv + moff[b];
-    // two rows per warp step, all loads of both rows issued up front
-    for (int r = 2 * warp; r < n; r += 2 * nw) {
-        const float *A0 = A + (int64_t)r * n;
-        const bool two = r + 1 < n;
-        const float *A1 = two ? A0 + n : A0;
-        float s0 = 0.f, s1 = 0.f;
-#pragma unroll 6
+    // this CTA's rows: slice blockIdx.y of PA_S; PA_R rows per warp step, all
+    // their loads issued before the first multiply
+    const int rs = (n + PA_S - 1) / PA_S, r0 = blockIdx.y * rs, r1 = min(n, r0 + rs);
+    for (int rb = r0 + PA_R * warp; rb < r1; rb += PA_R * PA_WARPS) {
+        float s[PA_R];
+        const float *Ar[PA_R];
+#pragma unroll
+        for (int q = 0; q < PA_R; ++q) {
+            s[q] = 0.f;
+            Ar[q] = A + (int64_t)min(rb + q, r1 - 1) * n;
+        }
+#pragma unroll 3
         for (int c = lane; c < n; c += 32) {
-            const float v = sv[c];
-            s0 = fmaf(A0[c], v, s0);
-            s1 = fmaf(A1[c], v, s1);
+            const float x = sv[c];
+#pragma unroll
+            for (int q = 0; q < PA_R; ++q) s[q] = fmaf(Ar[q][c], x, s[q]);
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            s0 += __shfl_xor_sync(0xFFFFFFFFu, s0, o);
-            s1 += __shfl_xor_sync(0xFFFFFFFFu, s1, o);
+        for (int q = 0; q < PA_R; ++q)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s[q] += __shfl_xor_sync(0xFFFFFFFFu, s[q], o);
+#pragma unroll
+        for (int q = 0; q < PA_R; ++q) {
+            const int r = rb + q;
+            if (lane == q && r < r1) z[(r / m) * N + el[r % m]] = (double)s[q];
         }
-        if (lane == 0) z[(r / m) * N + el[r % m]] = (double)s0;
-        if (lane == 1 && two) z[((r + 1) / m) * N + el[(r + 1) % m]] = (double)s1;
     }
-    if (zero_rest && nc < 3)
-        for (int e = threadIdx.x; e < m; e += blockDim.x) z[2 * N + el[e]] = 0.0;
+    if (zero_rest && nc < 3 && blockIdx.y == 0)
+        for (int e = threadIdx.x; e < m; e += PA_T) z[2 * N + el[e]] = 0.0;
 }
 
 }  // namespace
@@ -290,6 +300,7 @@ ddm_status pb_prepare(ddm_ctx *ctx, ddm_tree *t, double dt, int sys, cudaStream_
     if (st) return st;
     PbGeo *geo = nullptr;
     DDM_CUDA_TRY(ctx, dalloc(&geo, (size_t)t->n * sizeof(PbGeo), s));
+    prof_begin(ctx, 8);
     k_pb_geom<<<(unsigned)((t->n + 255) / 256), 256, 0, s>>>(t->xy_caller, t->n, geo);
     int64_t mm = (int64_t)t->pb_max * t->pb_max;
     dim3 g((unsigned)((mm + 127) / 128), (unsigned)t->n_pblk);
@@ -307,7 +318,7 @@ ddm_status pb_prepare(ddm_ctx *ctx, ddm_tree *t, double dt, int sys, cudaStream_
 // z = M^-1 v : v in the system layout (nc blocks of N), z in the 3N layout
 ddm_status pb_apply(ddm_ctx *ctx, ddm_tree *t, int sys, const double *v, double *z, cudaStream_t s) {
     int nc = sys == DDM_SYS_PRESSURE ? 3 : 2;
-    k_pb_apply<<<(unsigned)t->n_pblk, 512, 0, s>>>(t->pb_off, t->pb_elem, t->pb_moff, nc, t->pb_inv, v, t->n, z, 1);
+    k_pb_apply<<<dim3((unsigned)t->n_pblk, PA_S), PA_T, 0, s>>>(t->pb_off, t->pb_elem, t->pb_moff, nc, t->pb_inv, v, t->n, z, 1);
     prof_end(ctx, 8, 1);
     DDM_CUDA_TRY(ctx, cudaGetLastError());
     return DDM_OK;

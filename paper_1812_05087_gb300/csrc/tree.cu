@@ -277,17 +277,6 @@ __global__ void k_parent(const int32_t *cstart, int64_t off, int64_t ncell, cons
     parent[off + c] = (int32_t)(off_up + elem_cell_up[cstart[off + c]]);
 }
 
-// children of every cell at levels 1..L: count and first index (the cells
-// of one parent are contiguous because cells are sorted by Morton key)
-__global__ void k_children(const int32_t *parent, int64_t first, int64_t ncell, int32_t *child0, int32_t *nchild) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= ncell) return;
-    int64_t c = first + i;
-    int32_t p = parent[c];
-    atomicAdd(&nchild[p], 1);
-    if (parent[c - 1] != p) child0[p] = (int32_t)c;
-}
-
 // near-field work items: consecutive target pairs of one leaf (a leaf with an
 // odd count ends with a single, second index -1)
 __global__ void k_items_count(const int32_t *cstart, const int32_t *cend, int64_t loff, int64_t nleaf, int32_t *cnt) {
@@ -542,7 +531,7 @@ static void find_chains(const double *hxy, int64_t n, Chains &out) {
 
 void tree_free(ddm_tree *t) {
     if (!t) return;
-    void *ps[] = {t->mk_work, t->pb_off, t->pb_elem, t->pb_moff, t->pb_inv, t->mk_off, t->mk_pair, t->grp_off, t->grp_leaf, t->perm, t->cell_key, t->cell_ix, t->cell_iy, t->cell_start, t->cell_end, t->cell_parent, t->cell_child0, t->cell_nchild, t->up_cnt,
+    void *ps[] = {t->mk_work, t->pb_off, t->pb_elem, t->pb_moff, t->pb_inv, t->mk_off, t->mk_pair, t->grp_off, t->grp_leaf, t->perm, t->cell_key, t->cell_ix, t->cell_iy, t->cell_start, t->cell_end, t->cell_parent,
                   t->il_off, t->il_idx, t->nb_off, t->nb_idx, t->nb_tab, t->near_items, t->elem_leaf, t->g_rel, t->g_frame,
                   t->xy_sorted, t->xy_caller, t->W, t->Fl, t->far4, t->chg};
     for (void *p : ps) dfree(p, t->stream);
@@ -738,19 +727,6 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
         t->lvl_off.resize(L + 2);
         NC = t->lvl_off[L + 1];      // cells of the levels kept
         t->n_cells = NC;
-    }
-
-    // child ranges and upward-pass counters
-    TRY(dalloc(&t->cell_child0, NC * sizeof(int32_t), st));
-    TRY(dalloc(&t->cell_nchild, NC * sizeof(int32_t), st));
-    TRY(dalloc(&t->up_cnt, NC * sizeof(int32_t), st));
-    TRY(cudaMemsetAsync(t->cell_child0, 0xFF, NC * sizeof(int32_t), st));
-    TRY(cudaMemsetAsync(t->cell_nchild, 0, NC * sizeof(int32_t), st));
-    TRY(cudaMemsetAsync(t->up_cnt, 0, NC * sizeof(int32_t), st));
-    if (L >= 1) {
-        int64_t nc = NC - t->lvl_off[1];
-        k_children<<<(nc + TB - 1) / TB, TB, 0, st>>>(t->cell_parent, t->lvl_off[1], nc, t->cell_child0,
-                                                     t->cell_nchild); ++tl_launches;
     }
 
     // neighbours of leaves

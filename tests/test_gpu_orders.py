@@ -58,7 +58,7 @@ def test_fmm_forced_depth(mid_set, depth):
     err = block_rel_err(y, ref, N)
     print(f"depth={depth} err={err:.2e}")
     assert err < 1e-5
-    # a second product reuses the upward-pass counters reset by the first
+    # a second product on the same tree (internal cells zeroed again)
     y2 = ctx.matvec(tree, x, 0.0, 10.0, mode="fmm").cpu().numpy()
     assert block_rel_err(y2, ref, N) < 1e-5
     ctx.device_check()
