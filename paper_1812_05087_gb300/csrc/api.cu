@@ -262,14 +262,19 @@ struct GmresWork {
     int64_t cap_len = 0;
     int cap_m = 0;
     cudaStream_t st = nullptr;
-    double *V = nullptr, *w = nullptr, *z = nullptr, *full = nullptr, *y3 = nullptr, *b = nullptr;
-    double *hcol = nullptr, *nrm = nullptr, *Minv = nullptr, *yv = nullptr, *part = nullptr;
-    unsigned *cnt = nullptr;   // 2 last-block counters (zero between launches), then the DGKS flag
+    double *V = nullptr, *w = nullptr, *full = nullptr, *y3 = nullptr, *b = nullptr;
+    double *hcol = nullptr, *nrm = nullptr, *yv = nullptr, *part = nullptr;
+    unsigned *cnt = nullptr;   // grid-barrier counter and generation (zero between launches)
+    double *hpin = nullptr;    // pinned host slots of the Hessenberg column / a norm (2 (m + 2))
+    cudaEvent_t ev[2] = {nullptr, nullptr};   // one per pinned slot
     void release() {
-        double *ps[] = {V, w, z, full, y3, b, hcol, nrm, Minv, yv, part};
+        double *ps[] = {V, w, full, y3, b, hcol, nrm, yv, part};
         cudaStream_t s = st;
         for (double *p : ps) dfree(p, s);
         dfree(cnt, s);
+        if (hpin) cudaFreeHost(hpin);
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
         *this = GmresWork();
         st = s;
     }
@@ -482,16 +487,18 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
         size_t v3 = 3 * N * sizeof(double);
         g.st = s;
         bool ok = dalloc(&g.V, (size_t)(m + 1) * len * sizeof(double), s) == cudaSuccess &&
-                  dalloc(&g.w, v3, s) == cudaSuccess && dalloc(&g.z, v3, s) == cudaSuccess &&
+                  dalloc(&g.w, v3, s) == cudaSuccess &&
                   dalloc(&g.full, v3, s) == cudaSuccess && dalloc(&g.y3, v3, s) == cudaSuccess &&
                   dalloc(&g.b, v3, s) == cudaSuccess &&
                   dalloc(&g.hcol, (m + 2) * sizeof(double), s) == cudaSuccess &&
                   dalloc(&g.nrm, sizeof(double), s) == cudaSuccess &&
-                  dalloc(&g.Minv, 9 * N * sizeof(double), s) == cudaSuccess &&
                   dalloc(&g.yv, (m + 1) * sizeof(double), s) == cudaSuccess &&
                   dalloc(&g.part, (size_t)2 * DP_G * (m + 2) * sizeof(double), s) == cudaSuccess &&
                   dalloc(&g.cnt, 4 * sizeof(unsigned), s) == cudaSuccess &&
-                  cudaMemsetAsync(g.cnt, 0, 4 * sizeof(unsigned), s) == cudaSuccess;
+                  cudaMemsetAsync(g.cnt, 0, 4 * sizeof(unsigned), s) == cudaSuccess &&
+                  cudaMallocHost(&g.hpin, 2 * (m + 2) * sizeof(double)) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&g.ev[0], cudaEventDisableTiming) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&g.ev[1], cudaEventDisableTiming) == cudaSuccess;
         if (!ok) { g.release(); return ctx_fail(ctx, DDM_ENOMEM, "GMRES workspace allocation failed"); }
         g.cap_len = len; g.cap_m = m;
     }
@@ -525,9 +532,9 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
     };
     auto norm = [&](const double *v, double &out) -> ddm_status {
         dots(v, 1, v, g.nrm, nullptr, 0);
-        DDM_CUDA_TRY(ctx, cudaMemcpyAsync(&out, g.nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+        DDM_CUDA_TRY(ctx, cudaMemcpyAsync(g.hpin, g.nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
         DDM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-        out = sqrt(out);
+        out = sqrt(g.hpin[0]);
         return DDM_OK;
     };
     // preconditioner: inverted chain blocks of this (dt, system)
@@ -590,22 +597,28 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
         k_axpy<<<nblk(len), 256, 0, s>>>(-1.0 / beta, g.w, g.V, len);
         std::fill(gv.begin(), gv.end(), 0.0);
         gv[0] = beta;
-        int j = 0;
-        for (; j < m && iters < P.max_iters; ++j, ++iters) {
-            double *vj = g.V + (int64_t)j * len;
+        // One Arnoldi step: preconditioner, product, orthogonalisation (V[jj+1],
+        // Hessenberg column jj on the device), then the column into pinned
+        // slot jj % 2 and its event.  Steps only depend on each other through
+        // the device, so step j + 1 is enqueued before the host reads column
+        // j: the GPU never waits for the host's Givens rotations, and a cycle
+        // that ends at column j leaves one discarded step behind.
+        auto step = [&](int jj) -> ddm_status {
+            double *vj = g.V + (int64_t)jj * len;
             prof_begin(ctx, 8);
-            if ((st = pb_apply(ctx, t, sys, vj, g.full, s))) return st;
+            ddm_status e = pb_apply(ctx, t, sys, vj, g.full, s);
+            if (e) return e;
             if (sys == DDM_SYS_PRESSURE) {        // the 3N product is already the system's rows
-                if ((st = op_apply(ctx, t, 0.0, dt, g.full, g.w, mode, 0, 1.0))) return st;
+                if ((e = op_apply(ctx, t, 0.0, dt, g.full, g.w, mode, 0, 1.0))) return e;
             } else {
-                if ((st = op_apply(ctx, t, 0.0, dt, g.full, g.y3, mode, 0, 1.0))) return st;
+                if ((e = op_apply(ctx, t, 0.0, dt, g.full, g.y3, mode, 0, 1.0))) return e;
                 k_restrict<<<nblk(N), 256, 0, s>>>(g.y3, N, sys, 1, g.w);
             }
-            // orthogonalise against V[0..j] and normalise (one cooperative kernel)
+            // orthogonalise against V[0..jj] and normalise (one cooperative kernel)
             prof_begin(ctx, 8);
             {
                 double *Vp = g.V, *wp = g.w, *pp = g.part, *hcp = g.hcol;
-                int nvj = j + 1;
+                int nvj = jj + 1;
                 int64_t ln = len, ch = orth_chunk;
                 unsigned *bp = g.cnt;
                 int *ep = ctx->d_err;
@@ -614,8 +627,19 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
                                                               args, 0, s));
             }
             prof_end(ctx, 8, 1);      // orthogonalisation
-            DDM_CUDA_TRY(ctx, cudaMemcpyAsync(hc.data(), g.hcol, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
-            DDM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+            DDM_CUDA_TRY(ctx, cudaMemcpyAsync(g.hpin + (jj & 1) * (m + 2), g.hcol, (jj + 2) * sizeof(double),
+                                              cudaMemcpyDeviceToHost, s));
+            DDM_CUDA_TRY(ctx, cudaEventRecord(g.ev[jj & 1], s));
+            return DDM_OK;
+        };
+        int j = 0;
+        bool pending = j < m && iters < P.max_iters;
+        if (pending && (st = step(0))) return st;
+        while (pending) {
+            const bool more = j + 1 < m && iters + 1 < P.max_iters;
+            if (more && (st = step(j + 1))) return st;
+            DDM_CUDA_TRY(ctx, cudaEventSynchronize(g.ev[j & 1]));
+            std::copy(g.hpin + (j & 1) * (m + 2), g.hpin + (j & 1) * (m + 2) + j + 2, hc.begin());
             // Givens rotations on the new column
             for (int i = 0; i < j; ++i) {
                 double a = cs[i] * hc[i] + sn[i] * hc[i + 1];
@@ -631,7 +655,11 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
             gv[j] = cs[j] * gv[j];
             for (int i = 0; i <= j; ++i) H[i * m + j] = hc[i];
             rel = fabs(gv[j + 1]) / bnorm;
-            if (fabs(gv[j + 1]) < inner || r == 0) { ++j; ++iters; break; }
+            const bool done = fabs(gv[j + 1]) < inner || r == 0;
+            ++j;
+            ++iters;
+            if (done) break;
+            pending = more;
         }
         // least squares: upper triangular solve, x += M^-1 V y
         std::vector<double> yv(j, 0.0);

@@ -260,11 +260,20 @@ __global__ void __launch_bounds__(PA_T) k_pb_apply(const int32_t *boff, const in
             s[q] = 0.f;
             Ar[q] = A + (int64_t)min(rb + q, r1 - 1) * n;
         }
-#pragma unroll 3
-        for (int c = lane; c < n; c += 32) {
-            const float x = sv[c];
+        // n <= INV_MAX: every load of the PA_R rows is issued up front
+        float a[INV_MAX / 32][PA_R];
 #pragma unroll
-            for (int q = 0; q < PA_R; ++q) s[q] = fmaf(Ar[q][c], x, s[q]);
+        for (int k = 0; k < INV_MAX / 32; ++k) {
+            const int c = lane + 32 * k;
+#pragma unroll
+            for (int q = 0; q < PA_R; ++q) a[k][q] = c < n ? Ar[q][c] : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < INV_MAX / 32; ++k) {
+            const int c = lane + 32 * k;
+            const float x = c < n ? sv[c] : 0.f;
+#pragma unroll
+            for (int q = 0; q < PA_R; ++q) s[q] = fmaf(a[k][q], x, s[q]);
         }
 #pragma unroll
         for (int q = 0; q < PA_R; ++q)
