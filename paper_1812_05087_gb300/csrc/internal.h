@@ -54,8 +54,6 @@ struct ddm_tree {
     int2 *near_items;          // near-field work items: target pairs of one leaf (second -1: single)
     int64_t n_items;
     int32_t *elem_leaf;        // sorted element -> leaf index (leaf-local)
-    int64_t n_groups;          // groups of 32 consecutive sorted targets
-    int32_t *grp_off, *grp_leaf; // per group: union of the neighbour leaves of its targets (CSR, leaf-local)
     // sorted element geometry, FP32 relative to the element's leaf centre
     float4 *g_rel;             // (x0, y0, x1, y1) rel. to leaf centre
     float4 *g_frame;           // (tx, ty, half-length, 0)

@@ -203,6 +203,7 @@ cudaError_t radix_sort(Scratch &S, cudaStream_t st, uint32_t *key, int32_t *val,
     int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
     uint32_t *k2 = S.get<uint32_t>(n);
     int32_t *v2 = S.get<int32_t>(n), *hist = S.get<int32_t>(256 * ntiles), *offs = S.get<int32_t>(256 * ntiles);
+    int32_t *dtot = S.get<int32_t>(1);         // the scans' totals (n) stay on the device
     if (S.err) return S.err;
     uint32_t *ka = key, *kb = k2;
     int32_t *va = val, *vb = v2;
@@ -210,8 +211,7 @@ cudaError_t radix_sort(Scratch &S, cudaStream_t st, uint32_t *key, int32_t *val,
     for (int p = 0; p < passes; ++p) {
         int shift = 8 * p;
         k_rs_hist<<<ntiles, RS_TILE, 0, st>>>(ka, n, shift, hist, ntiles); ++tl_launches;
-        int32_t tot;
-        cudaError_t e = scan_excl(S, st, hist, offs, 256 * ntiles, &tot);
+        cudaError_t e = scan_excl_dev(S, st, hist, offs, 256 * ntiles, dtot);
         if (e) return e;
         k_rs_scatter<<<ntiles, RS_TILE, 0, st>>>(ka, va, n, shift, offs, ntiles, kb, vb); ++tl_launches;
         std::swap(ka, kb);
@@ -327,62 +327,74 @@ __global__ void k_sum_range(const int32_t *cnt, int64_t ncell, unsigned long lon
 // elements of the cells sharing a vertex (incl. itself)
 __global__ void k_p2p_estimate(const uint32_t *ckey, const int32_t *cix, const int32_t *ciy, const int32_t *cstart,
                                const int32_t *cend, int64_t off, int64_t ncell, int side, unsigned long long *total) {
-    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    unsigned long long v = 0;
-    if (c < ncell) {
-        int ix = cix[off + c], iy = ciy[off + c];
-        long long nb = 0;
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-                int jx = ix + dx, jy = iy + dy;
-                if (jx < 0 || jy < 0 || jx >= side || jy >= side) continue;
-                int32_t j = find_key(ckey, off, ncell, spread2(jx) | (spread2(jy) << 1));
-                if (j >= 0) nb += cend[off + j] - cstart[off + j];
-            }
-        v = (unsigned long long)(cend[off + c] - cstart[off + c]) * (unsigned long long)nb;
+    // one warp per cell, lane k < 9 looks up neighbour (k / 3 - 1, k % 3 - 1)
+    const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (c >= ncell) return;                   // whole warp
+    const int ix = cix[off + c], iy = ciy[off + c];
+    long long nb = 0;
+    if (lane < 9) {
+        const int jx = ix + lane % 3 - 1, jy = iy + lane / 3 - 1;
+        if (jx >= 0 && jy >= 0 && jx < side && jy < side) {
+            const int32_t j = find_key(ckey, off, ncell, spread2(jx) | (spread2(jy) << 1));
+            if (j >= 0) nb = cend[off + j] - cstart[off + j];
+        }
     }
-    if (v) atomicAdd(total, v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nb += __shfl_xor_sync(0xFFFFFFFFu, nb, o);
+    const unsigned long long v = (unsigned long long)(cend[off + c] - cstart[off + c]) * (unsigned long long)nb;
+    if (lane == 0 && v) atomicAdd(total, v);
 }
 
-// neighbours of each leaf (incl. itself): pass 0 counts, pass 1 fills
+// neighbours of each leaf (incl. itself): pass 0 counts, pass 1 fills.  One
+// warp per cell; lane k < 9 looks up neighbour (dx, dy) = (k % 3 - 1,
+// k / 3 - 1) and a ballot keeps the lists in that order.
 __global__ void k_neigh(const uint32_t *ckey, const int32_t *cix, const int32_t *ciy, int64_t off,
                         int64_t ncell, int side, const int32_t *nboff, int32_t *nbidx, int32_t *cnt) {
-    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
-    int ix = cix[off + c], iy = ciy[off + c], m = 0;
-    for (int dy = -1; dy <= 1; ++dy)
-        for (int dx = -1; dx <= 1; ++dx) {
-            int jx = ix + dx, jy = iy + dy;
-            if (jx < 0 || jy < 0 || jx >= side || jy >= side) continue;
-            int32_t j = find_key(ckey, off, ncell, spread2(jx) | (spread2(jy) << 1));
-            if (j < 0) continue;
-            if (nbidx) nbidx[nboff[c] + m] = j;
-            ++m;
-        }
-    if (cnt) cnt[c] = m;
+    const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (c >= ncell) return;                   // whole warp
+    const int ix = cix[off + c], iy = ciy[off + c];
+    int32_t j = -1;
+    if (lane < 9) {
+        const int jx = ix + lane % 3 - 1, jy = iy + lane / 3 - 1;
+        if (jx >= 0 && jy >= 0 && jx < side && jy < side)
+            j = find_key(ckey, off, ncell, spread2(jx) | (spread2(jy) << 1));
+    }
+    const unsigned mask = __ballot_sync(0xFFFFFFFFu, j >= 0);
+    if (nbidx && j >= 0) nbidx[nboff[c] + __popc(mask & ((1u << lane) - 1u))] = j;
+    if (cnt && lane == 0) cnt[c] = __popc(mask);
 }
 
-// interaction lists of the cells of one level (global cell indices)
+// interaction lists of the cells of one level (global cell indices): the
+// children of the parent's neighbours that are not neighbours of the cell.
+// One warp per cell; candidate k < 36 is child k % 4 of parent neighbour
+// (dx, dy) = ((k / 4) % 3 - 1, (k / 4) / 3 - 1), and a ballot keeps the list
+// in candidate order.
 __global__ void k_ilist(const uint32_t *ckey, const int32_t *cix, const int32_t *ciy, int64_t off,
                         int64_t ncell, int side, const int32_t *iloff, int32_t *ilidx, int32_t *cnt) {
-    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
-    int ix = cix[off + c], iy = ciy[off + c], px = ix >> 1, py = iy >> 1, m = 0;
-    int pside = side >> 1;
-    for (int dy = -1; dy <= 1; ++dy)
-        for (int dx = -1; dx <= 1; ++dx) {
-            int qx = px + dx, qy = py + dy;
-            if (qx < 0 || qy < 0 || qx >= pside || qy >= pside) continue;
-            for (int ch = 0; ch < 4; ++ch) {
-                int jx = 2 * qx + (ch & 1), jy = 2 * qy + (ch >> 1);
-                if (abs(jx - ix) <= 1 && abs(jy - iy) <= 1) continue;    // neighbour (or itself)
-                int32_t j = find_key(ckey, off, ncell, spread2(jx) | (spread2(jy) << 1));
-                if (j < 0) continue;
-                if (ilidx) ilidx[iloff[off + c] + m] = (int32_t)(off + j);
-                ++m;
+    const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (c >= ncell) return;                   // whole warp
+    const int ix = cix[off + c], iy = ciy[off + c], px = ix >> 1, py = iy >> 1, pside = side >> 1;
+    int m = 0;
+    for (int base = 0; base < 36; base += 32) {
+        const int k = base + lane;
+        int32_t j = -1;
+        if (k < 36) {
+            const int q = k >> 2, ch = k & 3;
+            const int qx = px + q % 3 - 1, qy = py + q / 3 - 1;
+            if (qx >= 0 && qy >= 0 && qx < pside && qy < pside) {
+                const int jx = 2 * qx + (ch & 1), jy = 2 * qy + (ch >> 1);
+                if (abs(jx - ix) > 1 || abs(jy - iy) > 1)      // not a neighbour (or itself)
+                    j = find_key(ckey, off, ncell, spread2(jx) | (spread2(jy) << 1));
             }
         }
-    if (cnt) cnt[off + c] = m;
+        const unsigned mask = __ballot_sync(0xFFFFFFFFu, j >= 0);
+        if (ilidx && j >= 0) ilidx[iloff[off + c] + m + __popc(mask & ((1u << lane) - 1u))] = (int32_t)(off + j);
+        m += __popc(mask);
+    }
+    if (cnt && lane == 0) cnt[off + c] = m;
 }
 
 __global__ void k_geom(const double *xy, int64_t n, const int32_t *idx, const int32_t *elem_leaf,
@@ -399,31 +411,6 @@ __global__ void k_geom(const double *xy, int64_t n, const int32_t *idx, const in
     g_rel[i] = make_float4((float)(ax - ccx), (float)(ay - ccy), (float)(bx - ccx), (float)(by - ccy));
     double L = hypot(bx - ax, by - ay);
     g_frame[i] = make_float4((float)((bx - ax) / L), (float)((by - ay) / L), (float)(0.5 * L), 0.f);
-}
-
-// union of the neighbour leaves of 32 consecutive sorted targets
-__global__ void k_groups(const int32_t *elem_leaf, int64_t n, int64_t ngroups, const int32_t *nboff,
-                         const int32_t *nbidx, const int32_t *goff, int32_t *gleaf, int32_t *cnt) {
-    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (g >= ngroups) return;
-    int32_t set[32 * 9];
-    int m = 0, last = -1;
-    int64_t i1 = min(n, 32 * g + 32);
-    for (int64_t i = 32 * g; i < i1; ++i) {
-        int32_t lf = elem_leaf[i];
-        if (lf == last) continue;
-        last = lf;
-        for (int k = nboff[lf]; k < nboff[lf + 1]; ++k) {
-            int32_t j = nbidx[k];
-            bool seen = false;
-            for (int q = 0; q < m; ++q)
-                if (set[q] == j) { seen = true; break; }
-            if (!seen && m < 32 * 9) set[m++] = j;
-        }
-    }
-    if (cnt) cnt[g] = m;
-    if (gleaf)
-        for (int q = 0; q < m; ++q) gleaf[goff[g] + q] = set[q];
 }
 
 // group interaction-list entries by (level, offset)
@@ -531,7 +518,7 @@ static void find_chains(const double *hxy, int64_t n, Chains &out) {
 
 void tree_free(ddm_tree *t) {
     if (!t) return;
-    void *ps[] = {t->mk_work, t->pb_off, t->pb_elem, t->pb_moff, t->pb_inv, t->mk_off, t->mk_pair, t->grp_off, t->grp_leaf, t->perm, t->cell_key, t->cell_ix, t->cell_iy, t->cell_start, t->cell_end, t->cell_parent,
+    void *ps[] = {t->mk_work, t->pb_off, t->pb_elem, t->pb_moff, t->pb_inv, t->mk_off, t->mk_pair, t->perm, t->cell_key, t->cell_ix, t->cell_iy, t->cell_start, t->cell_end, t->cell_parent,
                   t->il_off, t->il_idx, t->nb_off, t->nb_idx, t->nb_tab, t->near_items, t->elem_leaf, t->g_rel, t->g_frame,
                   t->xy_sorted, t->xy_caller, t->W, t->Fl, t->far4, t->chg};
     for (void *p : ps) dfree(p, t->stream);
@@ -689,22 +676,24 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
     // depth; shallower depths trade M2L and tree passes for more direct
     // pairs.  Costs per unit measured on GB300 for n = 8 (near pair 19.4 ps,
     // interaction pair 3.5 ns scaling with n^4, cell 25 ns).
+    int32_t *il_cnt = nullptr;                 // interaction-list counts of the depth choice, kept
     if (L >= 3 && ctx->prm.max_depth == 0) {
         const int L0 = std::max(2, L - 4), NCAND = L - L0 + 1;
         int32_t *ccnt = S.get<int32_t>(NC + 1);
+        il_cnt = ccnt;
         unsigned long long *dsum = S.get<unsigned long long>(2 * (L + 1));   // M2L pairs per level, near pairs per depth
         TRY(S.err);
         TRY(cudaMemsetAsync(dsum, 0, 2 * (L + 1) * sizeof(unsigned long long), st));
         TRY(cudaMemsetAsync(ccnt, 0, (NC + 1) * sizeof(int32_t), st));
         for (int l = 2; l <= L; ++l) {
             int64_t nc = ncl[l];
-            k_ilist<<<(nc + TB - 1) / TB, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, t->lvl_off[l], nc, 1 << l,
-                                                      nullptr, nullptr, ccnt); ++tl_launches;
+            k_ilist<<<(32 * nc + TB - 1) / TB, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, t->lvl_off[l], nc,
+                                                           1 << l, nullptr, nullptr, ccnt); ++tl_launches;
             k_sum_range<<<(nc + TB - 1) / TB, TB, 0, st>>>(ccnt, nc, dsum + l); ++tl_launches;
         }
         for (int Lc = L0; Lc <= L; ++Lc) {
             int64_t nc = ncl[Lc];
-            k_p2p_estimate<<<(nc + TB - 1) / TB, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, t->cell_start,
+            k_p2p_estimate<<<(32 * nc + TB - 1) / TB, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, t->cell_start,
                                                              t->cell_end, t->lvl_off[Lc], nc, 1 << Lc,
                                                              dsum + (L + 1) + Lc); ++tl_launches;
         }
@@ -736,12 +725,13 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
     TRY(S.err);
     TRY(dalloc(&t->nb_off, (nleaf + 1) * sizeof(int32_t), st));
     int64_t lb = (nleaf + TB - 1) / TB;
-    k_neigh<<<lb, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, loff, nleaf, side, nullptr, nullptr, cnt); ++tl_launches;
+    const int64_t lbw = (32 * nleaf + TB - 1) / TB;   // one warp per leaf
+    k_neigh<<<lbw, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, loff, nleaf, side, nullptr, nullptr, cnt); ++tl_launches;
     int32_t nbtot;
     TRY(scan_excl(S, st, cnt, t->nb_off, nleaf, &nbtot));
     TRY(cudaMemcpyAsync(t->nb_off + nleaf, &nbtot, sizeof(int32_t), cudaMemcpyHostToDevice, st));
     TRY(dalloc(&t->nb_idx, std::max(nbtot, 1) * sizeof(int32_t), st));
-    k_neigh<<<lb, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, loff, nleaf, side, t->nb_off, t->nb_idx, nullptr); ++tl_launches;
+    k_neigh<<<lbw, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, loff, nleaf, side, t->nb_off, t->nb_idx, nullptr); ++tl_launches;
     TRY(dalloc(&t->nb_tab, std::max(nbtot, 1) * sizeof(int4), st));
     {   // near-field work items (target pairs per leaf)
         int32_t *icnt = S.get<int32_t>(nleaf + 1), *ioff = S.get<int32_t>(nleaf + 1);
@@ -756,12 +746,18 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
     k_nbtab<<<lb, TB, 0, st>>>(t->nb_off, t->nb_idx, t->cell_start, t->cell_end, t->cell_ix, t->cell_iy, loff, nleaf,
                                t->nb_tab); ++tl_launches;
 
-    // interaction lists, levels >= 2
-    TRY(cudaMemsetAsync(cnt, 0, NC * sizeof(int32_t), st));
-    for (int l = 2; l <= L; ++l) {
-        int64_t nc = ncl[l];
-        k_ilist<<<(nc + TB - 1) / TB, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, t->lvl_off[l], nc,
-                                                  1 << l, nullptr, nullptr, cnt); ++tl_launches;
+    // interaction lists, levels >= 2: the counts (the depth choice already
+    // counted every level it kept; the cells of those levels keep their
+    // indices), then the lists
+    if (il_cnt) {
+        TRY(cudaMemcpyAsync(cnt, il_cnt, NC * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    } else {
+        TRY(cudaMemsetAsync(cnt, 0, NC * sizeof(int32_t), st));
+        for (int l = 2; l <= L; ++l) {
+            int64_t nc = ncl[l];
+            k_ilist<<<(32 * nc + TB - 1) / TB, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, t->lvl_off[l], nc,
+                                                           1 << l, nullptr, nullptr, cnt); ++tl_launches;
+        }
     }
     TRY(dalloc(&t->il_off, (NC + 1) * sizeof(int32_t), st));
     int32_t iltot;
@@ -770,8 +766,8 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
     TRY(dalloc(&t->il_idx, std::max(iltot, 1) * sizeof(int32_t), st));
     for (int l = 2; l <= L; ++l) {
         int64_t nc = ncl[l];
-        k_ilist<<<(nc + TB - 1) / TB, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, t->lvl_off[l], nc,
-                                                  1 << l, t->il_off, t->il_idx, nullptr); ++tl_launches;
+        k_ilist<<<(32 * nc + TB - 1) / TB, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, t->lvl_off[l], nc,
+                                                       1 << l, t->il_off, t->il_idx, nullptr); ++tl_launches;
     }
     t->n_m2l = iltot;
     // M2L pairs grouped by (level, offset)
@@ -830,20 +826,6 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
     double wl = 2.0 * h0 / (double)side;
     k_geom<<<nbk, TB, 0, st>>>(d_xy, n, idx, t->elem_leaf, t->cell_ix, t->cell_iy, loff, X0, Y0, wl, t->perm,
                               t->g_rel, t->g_frame, t->xy_sorted); ++tl_launches;
-    // target groups for the near field
-    {
-        int64_t ng = (n + 31) / 32;
-        t->n_groups = ng;
-        int32_t *gc = S.get<int32_t>(ng + 1);
-        TRY(S.err);
-        TRY(dalloc(&t->grp_off, (ng + 1) * sizeof(int32_t), st));
-        k_groups<<<(ng + 127) / 128, 128, 0, st>>>(t->elem_leaf, n, ng, t->nb_off, t->nb_idx, nullptr, nullptr, gc); ++tl_launches;
-        int32_t gtot;
-        TRY(scan_excl(S, st, gc, t->grp_off, ng, &gtot));
-        TRY(cudaMemcpyAsync(t->grp_off + ng, &gtot, sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        TRY(dalloc(&t->grp_leaf, std::max(gtot, 1) * sizeof(int32_t), st));
-        k_groups<<<(ng + 127) / 128, 128, 0, st>>>(t->elem_leaf, n, ng, t->nb_off, t->nb_idx, t->grp_off, t->grp_leaf, nullptr); ++tl_launches;
-    }
     // preconditioner blocks: the chain search (host worker thread, started
     // after the bounding box) is joined here
     {
