@@ -726,22 +726,23 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
     TRY(dalloc(&t->nb_off, (nleaf + 1) * sizeof(int32_t), st));
     int64_t lb = (nleaf + TB - 1) / TB;
     const int64_t lbw = (32 * nleaf + TB - 1) / TB;   // one warp per leaf
+    // (list sizes are bounded from above, so that the totals can stay on the
+    // device until the one read-back below)
     k_neigh<<<lbw, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, loff, nleaf, side, nullptr, nullptr, cnt); ++tl_launches;
-    int32_t nbtot;
-    TRY(scan_excl(S, st, cnt, t->nb_off, nleaf, &nbtot));
-    TRY(cudaMemcpyAsync(t->nb_off + nleaf, &nbtot, sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    TRY(dalloc(&t->nb_idx, std::max(nbtot, 1) * sizeof(int32_t), st));
+    TRY(scan_excl_dev(S, st, cnt, t->nb_off, nleaf, t->nb_off + nleaf));
+    const int64_t nb_cap = std::max<int64_t>(9 * nleaf, 1);          // <= 9 neighbours per leaf
+    TRY(dalloc(&t->nb_idx, nb_cap * sizeof(int32_t), st));
     k_neigh<<<lbw, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, loff, nleaf, side, t->nb_off, t->nb_idx, nullptr); ++tl_launches;
-    TRY(dalloc(&t->nb_tab, std::max(nbtot, 1) * sizeof(int4), st));
+    TRY(dalloc(&t->nb_tab, nb_cap * sizeof(int4), st));
+    const int32_t *d_itot = nullptr;
     {   // near-field work items (target pairs per leaf)
         int32_t *icnt = S.get<int32_t>(nleaf + 1), *ioff = S.get<int32_t>(nleaf + 1);
         TRY(S.err);
         k_items_count<<<lb, TB, 0, st>>>(t->cell_start, t->cell_end, loff, nleaf, icnt); ++tl_launches;
-        int32_t itot = 0;
-        TRY(scan_excl(S, st, icnt, ioff, nleaf, &itot));
-        TRY(dalloc(&t->near_items, std::max(itot, 1) * sizeof(int2), st));
+        TRY(scan_excl_dev(S, st, icnt, ioff, nleaf, ioff + nleaf));
+        TRY(dalloc(&t->near_items, std::max<int64_t>(n, 1) * sizeof(int2), st));   // <= one item per element
         k_items_fill<<<lb, TB, 0, st>>>(t->cell_start, t->cell_end, loff, nleaf, ioff, t->near_items); ++tl_launches;
-        t->n_items = itot;
+        d_itot = ioff + nleaf;
     }
     k_nbtab<<<lb, TB, 0, st>>>(t->nb_off, t->nb_idx, t->cell_start, t->cell_end, t->cell_ix, t->cell_iy, loff, nleaf,
                                t->nb_tab); ++tl_launches;
@@ -760,16 +761,18 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
         }
     }
     TRY(dalloc(&t->il_off, (NC + 1) * sizeof(int32_t), st));
-    int32_t iltot;
-    TRY(scan_excl(S, st, cnt, t->il_off, NC, &iltot));
-    TRY(cudaMemcpyAsync(t->il_off + NC, &iltot, sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    TRY(dalloc(&t->il_idx, std::max(iltot, 1) * sizeof(int32_t), st));
+    TRY(scan_excl_dev(S, st, cnt, t->il_off, NC, t->il_off + NC));
+    // <= 27 entries per cell of levels >= 2
+    const int64_t il_cap = std::max<int64_t>(27 * (NC - (L >= 2 ? t->lvl_off[2] : NC)), 1);
+    TRY(dalloc(&t->il_idx, il_cap * sizeof(int32_t), st));
     for (int l = 2; l <= L; ++l) {
         int64_t nc = ncl[l];
         k_ilist<<<(32 * nc + TB - 1) / TB, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, t->lvl_off[l], nc,
                                                        1 << l, t->il_off, t->il_idx, nullptr); ++tl_launches;
     }
-    t->n_m2l = iltot;
+    // host sources of uploads, alive until the synchronisation that ends the build
+    std::vector<int2> work;
+    std::vector<int64_t> moff;
     // M2L pairs grouped by (level, offset)
     {
         int nk = (L + 1) * 49;
@@ -781,15 +784,13 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
         TRY(cudaMemsetAsync(kc, 0, (nk + 1) * sizeof(int32_t), st));
         TRY(cudaMemsetAsync(kcur, 0, nk * sizeof(int32_t), st));
         TRY(dalloc(&t->mk_off, (nk + 1) * sizeof(int32_t), st));
-        TRY(dalloc(&t->mk_pair, std::max(iltot, 1) * sizeof(int2), st));
+        TRY(dalloc(&t->mk_pair, il_cap * sizeof(int2), st));
         int64_t first = L >= 2 ? t->lvl_off[2] : NC, ncm = NC - first;
         if (ncm > 0) {
             k_mkeys<<<(ncm + 255) / 256, 256, 0, st>>>(t->il_off, t->il_idx, t->cell_ix, t->cell_iy, lo, L, first, ncm,
                                                        nullptr, nullptr, nullptr, kc); ++tl_launches;
         }
-        int32_t ktot;
-        TRY(scan_excl(S, st, kc, t->mk_off, nk, &ktot));
-        TRY(cudaMemcpyAsync(t->mk_off + nk, &ktot, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        TRY(scan_excl_dev(S, st, kc, t->mk_off, nk, t->mk_off + nk));
         if (ncm > 0) {
             k_mkeys<<<(ncm + 255) / 256, 256, 0, st>>>(t->il_off, t->il_idx, t->cell_ix, t->cell_iy, lo, L, first, ncm,
                                                        t->mk_off, kcur, t->mk_pair, nullptr); ++tl_launches;
@@ -797,11 +798,19 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
         t->ops_n = 0;
         t->ops_cap = 0;
         t->win_clock = 0;
-        std::vector<int32_t> hk(nk + 1);
-        TRY(cudaMemcpyAsync(hk.data(), t->mk_off, (nk + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        // one read-back: the group offsets, the near-field item count and the
+        // interaction-list total
+        int32_t *hdev = S.get<int32_t>(nk + 3);
+        TRY(S.err);
+        TRY(cudaMemcpyAsync(hdev, t->mk_off, (nk + 1) * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+        TRY(cudaMemcpyAsync(hdev + nk + 1, d_itot, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+        TRY(cudaMemcpyAsync(hdev + nk + 2, t->il_off + NC, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+        std::vector<int32_t> hk(nk + 3);
+        TRY(cudaMemcpyAsync(hk.data(), hdev, (nk + 3) * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         TRY(cudaStreamSynchronize(st));
+        t->n_items = hk[nk + 1];
+        t->n_m2l = hk[nk + 2];
         t->max_group = 0;
-        std::vector<int2> work;
         for (int k = 0; k < nk; ++k) {
             t->max_group = std::max(t->max_group, hk[k + 1] - hk[k]);
             for (int p0 = hk[k]; p0 < hk[k + 1]; p0 += 64) work.push_back(make_int2(k, p0));
@@ -810,7 +819,6 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
         TRY(dalloc(&t->mk_work, std::max<size_t>(work.size(), 1) * sizeof(int2), st));
         if (!work.empty())
             TRY(cudaMemcpyAsync(t->mk_work, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
-        TRY(cudaStreamSynchronize(st));
     }
 
     // sorted geometry
@@ -834,7 +842,7 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
         if (!chain_ok) { tree_free(t); return ctx_fail(ctx, DDM_ECUDA, "tree build: end point copy failed"); }
         std::vector<int32_t> &boff = chains.boff;
         std::vector<int64_t> &belem = chains.belem;
-        std::vector<int64_t> moff{0};
+        moff.assign(1, 0);
         t->n_pblk = (int64_t)boff.size() - 1;
         t->pb_max = 0;
         for (int64_t b = 0; b < t->n_pblk; ++b) {
@@ -849,7 +857,6 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
         TRY(cudaMemcpyAsync(t->pb_off, boff.data(), boff.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         TRY(cudaMemcpyAsync(t->pb_elem, belem.data(), belem.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
         TRY(cudaMemcpyAsync(t->pb_moff, moff.data(), moff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-        TRY(cudaStreamSynchronize(st));
         t->pb_inv = nullptr;
         t->pb_dt = -1.0;
         t->pb_sys = -1;
