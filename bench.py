@@ -157,6 +157,31 @@ def oracle_sample(xy, x, rows_elems):
     return A @ x, rows, dt
 
 
+def replica_seed(rank):
+    """Seed of rank's own fracture set: the path shards only across
+    independent problems (replicas, no data-path collective)."""
+    from paper_1812_05087_gb300 import inputs
+    return inputs.SEED + rank
+
+
+def max_over_ranks(dist, vals, device):
+    """Element-wise maximum of per-rank timings over all ranks (identity
+    without a process group); device is where the collective's tensor lives
+    ("cuda" for NCCL, "cpu" for gloo)."""
+    if dist is None:
+        return [float(v) for v in vals]
+    import torch
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def whole_job_melem_s(world, n_per_rank, ms):
+    """Elements of all ranks' products per second (Melem/s) at the slowest
+    rank's time per product."""
+    return world * n_per_rank / (ms * 1e-3) / 1e6
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -202,7 +227,7 @@ def main():
     from paper_1812_05087_gb300 import inputs
     from paper_1812_05087_gb300.ddm import Context
 
-    xy, segs = inputs.random_fractures(seed=inputs.SEED + rank)
+    xy, segs = inputs.random_fractures(seed=replica_seed(rank))
     N = xy.shape[1]
     tips = inputs.tips_of(segs)
     stream = torch.cuda.current_stream()
@@ -425,14 +450,10 @@ def main():
                "sample": f"{k} target elements (3 rows each) x {N} sources, FP64 adaptive element quadrature"}
 
     # ---------------- max over ranks
-    tot_ms = ms_fmm
-    if dist:
-        tt = torch.tensor([ms_fmm, ms_e2e], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        tot_ms, ms_e2e = float(tt[0]), float(tt[1])
+    tot_ms, ms_e2e = max_over_ranks(dist, [ms_fmm, ms_e2e], "cuda")
     if rank != 0:
         return
-    value = world * N / (tot_ms * 1e-3) / 1e6
+    value = whole_job_melem_s(world, N, tot_ms)
     solves_s = 1e3 / float(np.mean(lat_ms))
     line = {
         "metric": METRIC, "value": value, "unit": "Melem/s", "n_gpus": world, "steps": args.steps,
@@ -452,7 +473,7 @@ def main():
         "error": err,
         "stages_ms_per_matvec": {k: v[0] / 3 for k, v in stages.items() if v[1] > 0},
         "roofline": roof, "cpu_baseline": cpu,
-        "e2e": {"value": world * N / (ms_e2e * 1e-3) / 1e6, "unit": "Melem/s",
+        "e2e": {"value": whole_job_melem_s(world, N, ms_e2e), "unit": "Melem/s",
                 "h2d_bytes_per_step": int(x.numel() * 8), "d2h_bytes_per_step": int(y.numel() * 8)},
         "gpu_launches": int(round(per_matvec_launches * args.steps)),
         "clocks": clocks,
