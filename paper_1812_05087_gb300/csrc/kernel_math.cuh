@@ -322,6 +322,22 @@ DEV void disl_field(const KConst<T> &k, T zx, T zy, T Dx, T Dy, const Win<T> &w,
         acc[2] -= C * (x2 - y2) * (Dx * zx + Dy * zy);
     }
     const int sides = w.ct_lo > T(0) ? 2 : 1;
+    if (sides == 2 && (zx * zx + zy * zy) * w.g_hi > Big<T>::U) {
+        // Both sides beyond u = Big (the hi side has the smaller u): there the
+        // transient functions are their asymptotic forms (F0 = 1/u,
+        // F1 = -1/u^2, F2 = 2/u^3, e^-u = 0).  Each side is the same
+        // t-independent term (the undrained - drained difference) plus a term
+        // linear in 4ct/r^2; the former cancels exactly between the sides,
+        // and evaluated side by side it would cost ~log10(u) digits.  What is
+        // left, written out: 2 G2 K2 (4 ct_hi - 4 ct_lo) / r^4 times the
+        // dislocation's angular factors; the pressure terms cancel.
+        const T l = Dx * zy - Dy * zx;
+        const T f = s * T(8) * k.G2 * k.K2 * (w.ct_hi - w.ct_lo) * ir2 * ir2;
+        acc[0] -= f * (T(2) * Dx * zy + l - T(4) * l * zy * zy * ir2);
+        acc[1] -= f * (l - T(2) * Dy * zx - T(4) * l * zx * zx * ir2);
+        acc[2] += f * (Dx * zx - Dy * zy - T(4) * l * zx * zy * ir2);
+        return;
+    }
 #pragma unroll 1
     for (int sd = 0; sd < sides; ++sd)
         disl_transient<T>(k, zx, zy, ir2, Dx, Dy, sd ? w.g_lo : w.g_hi, T(4) * (sd ? w.ct_lo : w.ct_hi),
