@@ -104,7 +104,12 @@ ddm_status ddm_device_check(ddm_ctx *ctx);
  * quarter of a leaf), empty ("zero") cells dropped, children in Z order,
  * neighbour and interaction lists of paper Sec. 3.1.  Built on the device
  * (Morton keys + radix sort).  d_xy: 4N doubles [x0(N), y0(N), x1(N), y1(N)].
- * Synchronises the stream.  The tree keeps its own copy of the geometry. */
+ * Below the occupancy depth, the depth minimising a measured cost model of
+ * near pairs, interaction pairs and cells is taken (unless max_depth is set).
+ * Synchronises the stream.  The tree keeps its own copy of the geometry.
+ * DDM_EINVAL (nothing allocated, the context stays usable) for n <= 0,
+ * n > 2^30, a null pointer, or an element of zero length or with a
+ * non-finite end point. */
 ddm_status ddm_build_tree(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **out);
 void ddm_tree_destroy(ddm_tree *tree);
 
