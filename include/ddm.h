@@ -126,8 +126,14 @@ ddm_status ddm_tree_get_info(const ddm_tree *tree, ddm_tree_info *info);
 
 #define DDM_MODE_FMM 0     /* Chebyshev FMM (paper Sec. 3) */
 #define DDM_MODE_DENSE 1   /* every pair evaluated on the fly (conventional PDDM) */
-#define DDM_MODE_PRECISE 16 /* OR-ed flag: DD part of every directly summed pair
-                               in FP64, for accurate residuals */
+#define DDM_MODE_PRECISE 16 /* OR-ed flag for accurate residuals.  With
+                               DDM_MODE_FMM: the DD part of every directly
+                               summed pair in FP64.  With DDM_MODE_DENSE: the
+                               whole product in FP64 from the caller's FP64
+                               geometry, every pair's DD part by its exact
+                               element integral (a dislocation pair) and its
+                               fluid source by an 8-point Gauss rule, O(N^2)
+                               FP64 work */
 
 /* d_y = [K(tau_hi) - K(tau_lo)] d_x  (paper Eqs. 2.3-2.5, left-hand sums for
  * tau_lo = 0, tau_hi = dt; one history term otherwise).  0 <= tau_lo < tau_hi.
@@ -189,7 +195,9 @@ typedef struct {
  * the residual recomputed at each restart) uses the requested mode, and
  * each restart's inner solve runs to 0.3 tol ||b||.  A restart that fails
  * to reduce the recomputed residual by 10% switches the residuals (and the
- * convergence test) to the operator with DDM_MODE_PRECISE, inner solves then
+ * convergence test) to an accurate operator (problems of <= 10,000 elements:
+ * DDM_MODE_DENSE | DDM_MODE_PRECISE; larger ones: the requested mode with
+ * DDM_MODE_PRECISE), inner solves then
  * running to max(0.3 tol ||b||, 1e-4 of the restart's residual); a further
  * such restart makes the Arnoldi products precise as well.  Returns
  * DDM_ENOTCONV (x and info still written) when max_iters is reached or three

@@ -573,7 +573,7 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
             DDM_CUDA_TRY(ctx, cudaMemsetAsync(g.w, 0, len * sizeof(double), s));
             x_zero = false;
         } else {
-            if ((st = apply(d_x, g.w, level >= 1 ? (mode | DDM_MODE_PRECISE) : mode))) return st;
+            if ((st = apply(d_x, g.w, residual_mode(mode, level, N)))) return st;
         }
         k_axpy<<<nblk(len), 256, 0, s>>>(-1.0, g.b, g.w, len);          // w = A x - b
         double beta;

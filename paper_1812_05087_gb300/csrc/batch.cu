@@ -346,7 +346,7 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
             int64_t n = B->N[p];
             k_copy_to3<<<nb(n), BT, 0, ps>>>(d_x + B->off3[p], n, nc, B->full + B->off3[p]);
             ddm_status e = op_apply(ctx, B->trees[p], 0.0, dt, B->full + B->off3[p], B->y3 + B->off3[p],
-                                    mode | (level[p] >= 1 ? DDM_MODE_PRECISE : 0), 0, 1.0, ps);
+                                    residual_mode(mode, level[p], n), 0, 1.0, ps);
             if (e) return e;
             k_restrict_b<<<nb(n), BT, 0, ps>>>(B->y3 + B->off3[p], n, sys, 1, B->tmp + B->offs[p]);
             return DDM_OK;

@@ -33,6 +33,7 @@ struct GLTab {
     float xn[MAXGL + 1][MAXGL], wn[MAXGL + 1][MAXGL];   // near rule (fluid source), [points][i]
     float xc[DDM_MAX_CHEB / 2][DDM_MAX_CHEB], wc[DDM_MAX_CHEB / 2][DDM_MAX_CHEB];   // P2M rule, n points, [n/2-1]
     float cheb[DDM_MAX_CHEB / 2][DDM_MAX_CHEB], bw[DDM_MAX_CHEB / 2][DDM_MAX_CHEB]; // roots of T_n, barycentric weights
+    double x8[8], w8[8];                                 // 8-point Gauss-Legendre rule in FP64 (exact products)
 };
 __constant__ GLTab c_gl;
 
@@ -1268,6 +1269,98 @@ __global__ void __launch_bounds__(DN_T) k_dense(KConst<float> k, KConst<double> 
     }
 }
 
+// Fluid source at a point in FP64 (both sides of the window), the q terms of
+// the point kernel: p = Q E1(u) / (4 pi kappa),
+// sigma = -(eta Q / (4 pi kappa)) (2 F n n + (E1 - F) I).
+__device__ __forceinline__ void q_point_d(const KConst<double> &k, double zx, double zy, double q,
+                                          const Win<double> &w, double acc[4]) {
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {
+        const double ct = side == 0 ? w.ct_hi : w.ct_lo;
+        if (ct <= 0.0) continue;
+        const double x2 = zx * zx, y2 = zy * zy, r2 = x2 + y2, ir2 = 1.0 / r2;
+        const double u = r2 * (side == 0 ? w.g_hi : w.g_lo), iu = 4.0 * ct * ir2;
+        double e, F0, F1, F2;
+        f_funcs<double>(u, iu, e, F0, F1, F2);
+        const double E1 = e1x<double>(u, iu);
+        const double pre = (side == 0 ? 1.0 : -1.0) * q * k.i4pk, nn = 2.0 * F0 * ir2;
+        acc[0] -= pre * k.eta * (nn * x2 + E1 - F0);
+        acc[1] -= pre * k.eta * (nn * y2 + E1 - F0);
+        acc[2] -= pre * k.eta * (nn * zx * zy);
+        acc[3] += pre * E1;
+    }
+}
+
+// Dense product with exact element integrals, all in FP64 (DDM_MODE_DENSE |
+// DDM_MODE_PRECISE): FP64 end points and unknowns in caller order; the DD
+// part of every pair as its dislocation pair (the exact element integral at
+// any distance), the fluid source by the 8-point Gauss-Legendre rule; the
+// own element comes from the cached closed-form blocks (k_prep).  The FMM and
+// the FP32 dense path carry FP32 geometry and pair arithmetic; this is the
+// operator that escalated GMRES residuals of small problems use.  One thread
+// per target, sources tiled through shared memory, blockIdx.y a source chunk.
+constexpr int DX_T = 128;
+__global__ void __launch_bounds__(DX_T) k_dense_exact(KConst<double> kd, Win<double> wd, const double *xy,
+                                                      const double *x, int64_t N, int64_t chunk, double scale,
+                                                      double *y) {
+    __shared__ double sx0[DX_T], sy0[DX_T], sx1[DX_T], sy1[DX_T], sDx[DX_T], sDy[DX_T], sq[DX_T];
+    const int64_t ti = blockIdx.x * (int64_t)DX_T + threadIdx.x;
+    const bool act = ti < N;
+    double mx = 0.0, my = 0.0, tx = 1.0, ty = 0.0;
+    if (act) {
+        const double ax = xy[ti], ay = xy[N + ti], bx = xy[2 * N + ti], by = xy[3 * N + ti];
+        const double L = hypot(bx - ax, by - ay);
+        mx = 0.5 * (ax + bx);
+        my = 0.5 * (ay + by);
+        tx = (bx - ax) / L;
+        ty = (by - ay) / L;
+    }
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    const int64_t s0 = blockIdx.y * chunk, s1 = s0 + chunk < N ? s0 + chunk : N;
+    for (int64_t sb = s0; sb < s1; sb += DX_T) {
+        __syncthreads();
+        const int64_t sj = sb + threadIdx.x;
+        if (sj < s1) {
+            const double ax = xy[sj], ay = xy[N + sj], bx = xy[2 * N + sj], by = xy[3 * N + sj];
+            const double L = hypot(bx - ax, by - ay), ux = (bx - ax) / L, uy = (by - ay) / L;
+            const double Ds = x[sj], Dn = x[N + sj];
+            sx0[threadIdx.x] = ax;
+            sy0[threadIdx.x] = ay;
+            sx1[threadIdx.x] = bx;
+            sy1[threadIdx.x] = by;
+            sDx[threadIdx.x] = Ds * ux - Dn * uy;          // D = Ds t + Dn n, n = (-t_y, t_x)
+            sDy[threadIdx.x] = Ds * uy + Dn * ux;
+            sq[threadIdx.x] = x[2 * N + sj];
+        }
+        __syncthreads();
+        const int cnt = (int)(s1 - sb < DX_T ? s1 - sb : DX_T);
+        if (act) {
+            for (int j = 0; j < cnt; ++j) {
+                if (sb + j == ti) continue;
+                disl_field<double>(kd, mx - sx0[j], my - sy0[j], sDx[j], sDy[j], wd, 1.0, acc);    // start point
+                disl_field<double>(kd, mx - sx1[j], my - sy1[j], sDx[j], sDy[j], wd, -1.0, acc);   // end point
+                const double q = sq[j];
+                if (q != 0.0) {
+                    const double cx = 0.5 * (sx0[j] + sx1[j]), cy = 0.5 * (sy0[j] + sy1[j]);
+                    const double hx = 0.5 * (sx1[j] - sx0[j]), hy = 0.5 * (sy1[j] - sy0[j]);   // a t
+                    const double a = hypot(hx, hy);
+#pragma unroll 1
+                    for (int g = 0; g < 8; ++g)
+                        q_point_d(kd, mx - cx - c_gl.x8[g] * hx, my - cy - c_gl.x8[g] * hy, c_gl.w8[g] * a * q, wd,
+                                  acc);
+                }
+            }
+        }
+    }
+    if (act) {
+        double ss, sn;
+        to_local<double>(tx, ty, acc, ss, sn);
+        atomicAdd(&y[ti], scale * ss);
+        atomicAdd(&y[N + ti], scale * sn);
+        atomicAdd(&y[2 * N + ti], scale * acc[3]);
+    }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------- host
@@ -1298,6 +1391,7 @@ ddm_status upload_tables(ddm_ctx *ctx) {
             h.bw[o][j] = (float)(((j & 1) ? -1.0 : 1.0) * sin(th));
         }
     }
+    gauss_legendre(8, h.x8, h.w8);
     DDM_CUDA_TRY(ctx, cudaMemcpyToSymbolAsync(c_gl, &h, sizeof(h), 0, cudaMemcpyHostToDevice, ctx->stream));
     DDM_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     g_tab_done[dv] = true;
@@ -1395,13 +1489,25 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
             x, t->perm, t->g_frame, blk, N, scale, overwrite, t->chg, y, t->W + z0 * 4 * n2, t->Fl + z0 * 4 * n2, nz);
         prof_end(ctx, 0, 1);
     }
+    if (mode == DDM_MODE_DENSE && precise) {
+        const int64_t tiles = (N + DX_T - 1) / DX_T;
+        int64_t chunks = std::max<int64_t>(1, std::min<int64_t>((4 * 152 + tiles - 1) / tiles, tiles));
+        int64_t chunk = ((N + chunks - 1) / chunks + DX_T - 1) / DX_T * DX_T;
+        chunks = (N + chunk - 1) / chunk;
+        prof_begin(ctx, 7);
+        k_dense_exact<<<dim3((unsigned)tiles, (unsigned)chunks), DX_T, 0, s>>>(ctx->kd, wd, t->xy_caller, x, N, chunk,
+                                                                               scale, y);
+        prof_end(ctx, 7, 1);
+        DDM_CUDA_TRY(ctx, cudaGetLastError());
+        return DDM_OK;
+    }
     if (mode == DDM_MODE_DENSE) {
         int64_t tiles = (N + DN_T - 1) / DN_T;
         int64_t chunks = std::max<int64_t>(1, std::min<int64_t>((4 * 152 + tiles - 1) / tiles, (N + DN_T - 1) / DN_T));
         int64_t chunk = ((N + chunks - 1) / chunks + DN_T - 1) / DN_T * DN_T;
         chunks = (N + chunk - 1) / chunk;
         prof_begin(ctx, 7);
-        auto kdn = precise ? k_dense<true> : k_dense<false>;
+        auto kdn = k_dense<false>;          // precise dense products take k_dense_exact above
         kdn<<<dim3((unsigned)tiles, (unsigned)chunks), DN_T, 0, s>>>(kf, ctx->kd, wf, wd, ctx->prm.quad_near, loff, t->elem_leaf, t->cell_ix, t->cell_iy,
                                                                         t->g_rel, t->g_frame, t->chg, t->perm, wL, N,
                                                                         chunk, scale, y);

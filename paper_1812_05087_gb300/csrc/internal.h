@@ -137,6 +137,16 @@ struct ddm_ctx {
 };
 
 // begin/end a profiled stage (no-ops unless profiling is on); count launches
+// Escalated GMRES residuals (precision level >= 1) of problems up to this many
+// elements use the exact FP64 dense product (DDM_MODE_DENSE | DDM_MODE_PRECISE):
+// its cost is O(N^2) FP64 pair integrals, taken once per restart.  Larger
+// problems keep the precise FMM product.
+constexpr int64_t EXACT_RES_MAX = 10000;
+inline int residual_mode(int mode, int level, int64_t n) {
+    if (level < 1) return mode;
+    return (n <= EXACT_RES_MAX ? DDM_MODE_DENSE : (mode & ~DDM_MODE_PRECISE)) | DDM_MODE_PRECISE;
+}
+
 void prof_begin(ddm_ctx *ctx, int stage);
 void prof_end(ddm_ctx *ctx, int stage, int launches);
 

@@ -108,3 +108,21 @@ def test_bad_geometry_rejected_context_stays_usable(ctx, kind):
     assert block_rel_err(y, oracle.matvec(MAT, xy, x, 0.0, 10.0), 40) < TOL["fmm"]
     tree.close()
     ctx.device_check()
+
+
+@pytest.mark.parametrize("geom", ["crack", "random"])
+@pytest.mark.parametrize("win", [(0.0, 10.0), (5.0, 20.0)])
+def test_exact_dense_matches_oracle_tightly(ctx, geom, win):
+    """DDM_MODE_DENSE | DDM_MODE_PRECISE: FP64 geometry, dislocation pairs
+    (the exact element integral) at every distance and an 8-point FP64
+    Gauss rule for the fluid source, i.e. the oracle's product up to its
+    quadrature tolerance; the FP32 paths are held to 2e-5 / 2e-4."""
+    from gpu_common import small_random_set
+    xy = inputs.single_crack(200, 1.0) if geom == "crack" else small_random_set()[0]
+    n = xy.shape[1]
+    tree = ctx.build_tree(dev(xy))
+    x = inputs.unknowns(n, seed=21)
+    y = ctx.matvec(tree, dev(x), win[0], win[1], mode="dense+precise").cpu().numpy()
+    ref = oracle.matvec(MAT, xy, x, win[0], win[1])
+    assert block_rel_err(y, ref, n) < 1e-7
+    tree.close()
