@@ -43,6 +43,7 @@
 #ifndef DDM_GB300_H
 #define DDM_GB300_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus

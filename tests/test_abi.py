@@ -24,3 +24,16 @@ def test_library_exports_every_declared_symbol():
     missing = [n for n in header_functions() if not hasattr(lib, n)]
     assert not missing, missing
     assert set(header_functions()) <= set(ddm.EXPORTS) | {"ddm_submit", "ddm_poll"}
+
+
+def test_header_compiles_standalone_as_c_and_cpp(tmp_path):
+    """A C or C++ caller includes ddm.h on its own: it must bring every type
+    it uses (size_t, int64_t) and declare the functions with C linkage."""
+    import shutil
+    import subprocess
+    hdr = os.path.join(ROOT, "include", "ddm.h")
+    for comp, args in (("gcc", ["-x", "c", "-std=c99"]), ("g++", ["-x", "c++"])):
+        if shutil.which(comp) is None:
+            continue
+        r = subprocess.run([comp, "-fsyntax-only", "-Wall", "-Werror", *args, hdr], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
