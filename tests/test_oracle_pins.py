@@ -301,3 +301,102 @@ def test_march_matches_single_solve_for_one_step():
     x1 = oracle.march(MAT, xy, [0.0, 10.0], [b])[0]
     x2 = oracle.solve(oracle.assemble(MAT, xy, 10.0), b, N)
     assert np.allclose(x1, x2, rtol=1e-12)
+
+
+# ----------------------------------------------------------------------------
+# far-field loads resolved on inclined cracks, and the RATE system
+# ----------------------------------------------------------------------------
+def _resolved(angle, sigma_H, sigma_h):
+    """Cauchy resolution of the far field diag(sigma_H, sigma_h)
+    (compression positive) on a crack with tangent (cos, sin) and normal
+    (-sin, cos): compressive normal stress and tension-positive shear."""
+    s, c = math.sin(angle), math.cos(angle)
+    return sigma_H * s * s + sigma_h * c * c, (sigma_H - sigma_h) * s * c
+
+
+def _profile(nu_eff, load, xm, a):
+    return 2 * (1 - nu_eff) * load / MAT[0] * np.sqrt(a * a - xm ** 2)
+
+
+@pytest.mark.parametrize("angle", [0.3, 0.9, 2.2])
+def test_far_field_on_inclined_crack_drained(angle):
+    """oracle.rhs under sigma_H != sigma_h plus p_f (paper Sec. 4 far-field
+    transform) on an inclined crack, drained limit: the opening follows
+    Sneddon with the net load p_f - sigma_nn, the sliding follows the shear
+    analogue with the resolved shear (sign included), and Eq. 2.6 gives
+    K_I = (p_f - sigma_nn) sqrt(pi a), K_II = tau sqrt(pi a)."""
+    N, a = 120, 1.0
+    sH, sh, pf = 3e6, 2e6, 5e6
+    xy, xm = crack(N, a, angle, x0=3.0, y0=-2.0)
+    A = oracle.assemble(MAT, xy, 1e12)
+    x = oracle.solve(A, oracle.rhs(xy, sigma_H=sH, sigma_h=sh, p_f=pf, system="impermeable"), N, "impermeable")
+    snn, tau = _resolved(angle, sH, sh)
+    mid = np.abs(xm) <= 0.8 * a
+    wn, ws = _profile(MAT[1], pf - snn, xm, a), _profile(MAT[1], tau, xm, a)
+    assert np.max(np.abs(x[N:2 * N][mid] / wn[mid] - 1)) < 0.012
+    assert np.max(np.abs(x[:N][mid] / ws[mid] - 1)) < 0.012
+    KI, KII = oracle.sif(MAT, xy, x, [0, N - 1])
+    assert np.all(np.abs(KI / ((pf - snn) * math.sqrt(math.pi * a)) - 1) < 0.02)
+    assert np.all(np.abs(KII / (tau * math.sqrt(math.pi * a)) - 1) < 0.02)
+
+
+def test_rate_system_drained_reduces_to_sneddon():
+    """RATE system (rows sigma_s and sigma_n + p, D_q prescribed) with
+    D_q = 0 in the drained limit: the DDs induce no pore pressure, so the
+    solution is Sneddon's with the net load p0 - sigma_nn and the shear
+    analogue with the resolved shear."""
+    N, a, angle = 120, 1.0, 0.7
+    sH, sh, p0 = 3e6, 2e6, 6e6
+    xy, xm = crack(N, a, angle)
+    A = oracle.assemble(MAT, xy, 1e12)
+    x = oracle.solve(A, oracle.rhs(xy, sigma_H=sH, sigma_h=sh, p0=p0, system="rate"), N, "rate", Dq=0.0)
+    snn, tau = _resolved(angle, sH, sh)
+    mid = np.abs(xm) <= 0.8 * a
+    assert np.max(np.abs(x[N:2 * N][mid] / _profile(MAT[1], p0 - snn, xm, a)[mid] - 1)) < 0.012
+    assert np.max(np.abs(x[:N][mid] / _profile(MAT[1], tau, xm, a)[mid] - 1)) < 0.012
+    assert np.all(x[2 * N:] == 0.0)
+
+
+def test_rate_system_undrained_skempton():
+    """RATE system with D_q = 0 in the undrained limit.  On the faces of a
+    uniformly pressurised Griffith crack both in-plane stresses equal -p_net
+    (Westergaard), so Skempton's undrained pore pressure in plane strain is
+    p = -B (1 + nu_u)(sigma_xx + sigma_yy) / 3 = 2 B (1 + nu_u) p_net / 3 and
+    the row sigma_n + p = -(1 - 2 B (1 + nu_u) / 3) p_net.  The opening is
+    then Sneddon's with nu_u and p_net = (p0 - sigma_nn) / (1 - 2B(1+nu_u)/3);
+    a system that dropped the pressure row would be 3.4 times too stiff."""
+    N, a, angle = 120, 1.0, 0.7
+    G, nu, nuu, B = MAT[:4]
+    sH, sh, p0 = 3e6, 2e6, 6e6
+    xy, xm = crack(N, a, angle)
+    A = oracle.assemble(MAT, xy, 1e-4)
+    x = oracle.solve(A, oracle.rhs(xy, sigma_H=sH, sigma_h=sh, p0=p0, system="rate"), N, "rate", Dq=0.0)
+    snn, tau = _resolved(angle, sH, sh)
+    skempton = 1 - 2 * B * (1 + nuu) / 3
+    pnet = (p0 - snn) / skempton
+    mid = np.abs(xm) <= 0.8 * a
+    assert np.max(np.abs(x[N:2 * N][mid] / _profile(nuu, pnet, xm, a)[mid] - 1)) < 0.012
+    assert np.max(np.abs(x[:N][mid] / _profile(nuu, tau, xm, a)[mid] - 1)) < 0.012
+    p_mid = (A @ x)[2 * N + N // 2]
+    assert abs(p_mid / (2 * B * (1 + nuu) / 3 * pnet) - 1) < 1e-4
+
+
+@pytest.mark.parametrize("system", ["rate", "impermeable"])
+def test_two_unknown_systems_satisfy_their_rows(system):
+    """With a non-zero prescribed D_q at a finite time, the returned 3N
+    vector satisfies the system's own rows of the full product A x:
+    sigma_s = b_s and sigma_n (+ p for RATE) = b_n; the prescribed D_q is
+    returned unchanged."""
+    N = 40
+    xy, _ = crack(N, 0.5, 0.4)
+    A = oracle.assemble(MAT, xy, 30.0)
+    rng = np.random.default_rng(7)
+    Dq = 1e-6 * (1 + rng.random(N))
+    b = oracle.rhs(xy, sigma_H=3e6, sigma_h=2e6, p_f=5e6, p0=1e6, system=system)
+    x = oracle.solve(A, b, N, system, Dq=Dq)
+    y = A @ x
+    assert np.array_equal(x[2 * N:], Dq)
+    row_n = y[N:2 * N] + (y[2 * N:] if system == "rate" else 0.0)
+    scale = np.abs(b[:2 * N]).max()
+    assert np.abs(y[:N] - b[:N]).max() < 1e-9 * scale
+    assert np.abs(row_n - b[N:2 * N]).max() < 1e-9 * scale
