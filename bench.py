@@ -50,7 +50,9 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n-cheb", type=int, default=8)
     ap.add_argument("--leaf", type=int, default=32)
-    ap.add_argument("--solves", type=int, default=10)
+    ap.add_argument("--solves", type=int, default=100)
+    ap.add_argument("--orders", default="12,16", help="extra Chebyshev orders timed beside --n-cheb ('' = none)")
+    ap.add_argument("--well-steps", type=int, default=100, help="time steps of the horizontal-well march (0 = skip)")
     ap.add_argument("--oracle-rows", type=int, default=12)
     ap.add_argument("--no-oracle", action="store_true")
     ap.add_argument("--hist-lags", type=int, default=10)
@@ -144,6 +146,42 @@ def ncu_record():
 def alu_peak_tflops(sm_mhz):
     """FP32 FMA peak: 152 SMs x 128 FP32 lanes x 2 flop x clock."""
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def near_pair_flops(quad_near):
+    """Algorithmic FP32 work of one element-integrated 4 x 3 kernel block
+    (one near pair): ~150 flops for the elastic part plus ~60 per Gauss
+    point of the transient part."""
+    return 150 + 60 * quad_near
+
+
+def well_march(ctx, tree, N, steps, half_length, torch):
+    """Horizontal-well time march (paper Sec. 4/5): per step the history of
+    all previous steps is subtracted from the right-hand side, then the RATE
+    system is solved (x0 = previous solution).  Returns per-step (history
+    ms, solve ms) and the GMRES infos."""
+    from paper_1812_05087_gb300 import inputs
+    hist = torch.zeros(steps, 3 * N, dtype=torch.float64, device="cuda")
+    b0 = ctx.rhs(tree, system="rate", **inputs.WELL_LOADS)
+    times = [inputs.WELL_DT * k for k in range(steps + 1)]
+    x = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
+    x[2 * N:] = inputs.well_source(half_length)
+    t_hist, t_solve, infos = [], [], []
+    for h in range(1, steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b = b0.clone()
+        if h > 1:
+            ctx.history_apply(tree, hist[:h - 1], times[:h + 1], b)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        x, info = ctx.gmres_solve(tree, inputs.WELL_DT, b, x, system="rate", tol=1e-5, raise_on_notconv=False)
+        hist[h - 1] = x
+        torch.cuda.synchronize()
+        t_hist.append(1e3 * (t1 - t0))
+        t_solve.append(1e3 * (time.perf_counter() - t1))
+        infos.append(info)
+    return t_hist, t_solve, infos
 
 
 def oracle_sample(xy, x, rows_elems):
@@ -277,6 +315,39 @@ def main():
     ctx.profile(False)
     ms_fmm = float(np.mean(t_fmm))
     y_fmm = y.cpu().numpy()
+    # building the per-window operators of a new time window (M2L operator
+    # set, own-element blocks): once per window, cached on the tree; the
+    # timed product above reuses the cached window
+    ctx.profile(True)
+    ctx.matvec(tree, x, 0.0, 1.1 * DT, mode="fmm", out=torch.empty_like(y))
+    wst = ctx.profile_read()
+    ctx.profile(False)
+    window_setup = {"m2l_ops_ms": wst["m2l_ops"][0], "self_blocks_ms": wst["self_blocks"][0],
+                    "note": "per new time window, cached on the tree (excluded from the timed product)"}
+
+    # ---------------- other Chebyshev orders (same workload, own context and tree)
+    orders = {}
+    for nn in [int(v) for v in args.orders.split(",") if v.strip()]:
+        if nn == args.n_cheb:
+            continue
+        octx = Context(inputs.MATERIAL, n_cheb=nn, leaf_size=args.leaf)
+        otree = octx.build_tree(d_xy)
+        oy = torch.empty_like(y)
+        ofn = lambda: octx.matvec(otree, x, 0.0, DT, mode="fmm", out=oy)
+        ot = timed(ofn, args.steps, args.warmup)
+        octx.profile(True)
+        for _ in range(3):
+            ofn()
+        ost = octx.profile_read()
+        octx.profile(False)
+        oinfo = otree.info()
+        oms = float(np.mean(ot))
+        orders[nn] = {"ms_per_matvec": oms, "melem_s": world * N / (oms * 1e-3) / 1e6, "depth": oinfo["depth"],
+                      "m2l_pairs": oinfo["n_m2l_pairs"], "p2p_pairs": oinfo["n_p2p_pairs"],
+                      "stages_ms_per_matvec": {k: v[0] / 3 for k, v in ost.items() if v[1] > 0},
+                      "y": oy.cpu().numpy()}
+        otree.close()
+        octx.close()
 
     # ---------------- dense product on the GPU (conventional PDDM)
     dense = lambda: ctx.matvec(tree, x, 0.0, DT, mode="dense", out=y)
@@ -327,6 +398,24 @@ def main():
     rhs_h = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
     t_hist = timed(lambda: ctx.history_apply(tree, hist, times, rhs_h), 3, 1)
     ms_hist = float(np.mean(t_hist))
+
+    # ---------------- horizontal-well march (10 x 2,000 elements, 60 s steps)
+    well_res = None
+    if args.well_steps > 0:
+        wxy, _ = inputs.parallel_fractures(n_frac=10, spacing=20.0, half_length=100.0, elems=2000)
+        wN = wxy.shape[1]
+        wtree = ctx.build_tree(torch.as_tensor(wxy, device="cuda"))
+        th, ts, winf = well_march(ctx, wtree, wN, args.well_steps, 100.0, torch)
+        wtree.close()
+        lags = args.well_steps * (args.well_steps - 1) // 2
+        tot = sum(th) + sum(ts)
+        well_res = {"workload": "10 parallel fractures x 2000 elements (N=20000), RATE system, 60 s steps",
+                    "steps": args.well_steps, "ms_per_step": tot / args.well_steps,
+                    "history_ms_per_step": sum(th) / args.well_steps, "history_share": sum(th) / tot,
+                    "solve_ms_per_step": sum(ts) / args.well_steps,
+                    "history_melem_lags_per_s": wN * lags / (sum(th) * 1e-3) / 1e6 if lags else None,
+                    "converged": int(sum(i["converged"] for i in winf)),
+                    "gmres_iterations_mean": float(np.mean([i["iterations"] for i in winf]))}
 
     # ---------------- batched uneven problems (one graph launch per product)
     batch_res = None
@@ -412,6 +501,7 @@ def main():
     kname = STAGE_KERNEL[dom]
     bound, peak, peak_note = "alu", alu_peak_tflops(sm_mhz), \
         f"FP32 peak 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (median SM clock sampled under load)"
+    exe = None
     if dom == "m2l":
         flop = 2.0 * (4 * n * n) ** 2 * info["n_m2l_pairs"]
         flop_note = "2 (4n^2)^2 flops per interaction pair (the 3xTF32 split issues 3x this on the tensor cores)"
@@ -421,14 +511,19 @@ def main():
         peak_note = ("TF32 dense = measured" if bf16 else "TF32 dense = fallback") + \
             " bf16 GEMM peak x 0.5 (nominal TF32/BF16 ratio)"
     else:
-        fpp = rec[kname]["fp32_flops_per_pair"] if (rec and kname in rec) else 373
+        fpp = near_pair_flops(6)
         flop = float(info["n_p2p_pairs"]) * fpp
-        flop_note = f"{fpp} FP32 flops per near pair (ncu-counted fadd + 2 ffma + fmul of {kname} per pair)"
+        flop_note = (f"{fpp} algorithmic FP32 flops per near pair (one element-integrated 4x3 kernel block: "
+                     f"~150 elastic + 60 per Gauss point x 6 transient points)")
+        if rec and kname in rec and "fp32_flops_per_pair" in rec[kname]:
+            exe = {"flops_per_pair": rec[kname]["fp32_flops_per_pair"],
+                   "achieved": float(info["n_p2p_pairs"]) * rec[kname]["fp32_flops_per_pair"] / (dom_ms * 1e-3) / 1e12,
+                   "note": f"ncu-counted FP32 flops of {kname} per pair (fadd + 2 ffma + fmul)"}
     achieved = flop / (dom_ms * 1e-3) / 1e12
     roof = {"kernel": kname, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak,
             "traffic": (rec[kname]["dram_bytes"] if (rec and rec_ok and kname in rec) else None),
-            "flops_per_launch": flop, "flop_note": flop_note,
+            "flops_per_launch": flop, "flop_note": flop_note, "executed": exe,
             "peak_note": peak_note,
             "ms_per_launch": dom_ms}
 
@@ -445,6 +540,9 @@ def main():
         err = {"fmm_vs_oracle": max(e_f[b * k:(b + 1) * k].max() / scale[b] for b in range(3)),
                "dense_vs_oracle": max(e_d[b * k:(b + 1) * k].max() / scale[b] for b in range(3)),
                "rows": int(rows.size)}
+        for nn, o in orders.items():
+            e_o = np.abs(o["y"][rows] - ref)
+            o["error_vs_oracle"] = max(e_o[b * k:(b + 1) * k].max() / scale[b] for b in range(3))
         import oracle
         cpu = {"value": k / dt_or / 1e6, "unit": "Melem/s", "cores": oracle.num_threads(), "kind": "oracle",
                "sample": f"{k} target elements (3 rows each) x {N} sources, FP64 adaptive element quadrature"}
@@ -462,13 +560,16 @@ def main():
         "config": {"workload": WORKLOAD, "N": N, "n_cheb": n, "leaf": args.leaf, "depth": info["depth"],
                    "m2l_pairs": info["n_m2l_pairs"], "p2p_pairs": info["n_p2p_pairs"],
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
-        "solves_per_s": world * solves_s, "solve_p50_ms": lat_ms[len(lat_ms) // 2],
+        "solves_per_s": world * solves_s, "solves_timed": len(lat_ms), "solve_p50_ms": lat_ms[len(lat_ms) // 2],
         "solve_p99_ms": lat_ms[min(len(lat_ms) - 1, int(0.99 * len(lat_ms)))],
         "gmres_iterations": infos[-1]["iterations"], "gmres_rel_residual": infos[-1]["rel_residual"],
         "dense_melem_s": world * N / (ms_dense * 1e-3) / 1e6, "dense_ms_per_matvec": ms_dense,
         "dense_solve_ms": dense_solve_ms, "dense_gmres_iterations": dinfo["iterations"],
         "fmm_speedup_vs_dense": ms_dense / ms_fmm,
         "history": {"lags": H, "ms": ms_hist, "melem_lags_per_s": N * H / (ms_hist * 1e-3) / 1e6},
+        "window_setup": window_setup,
+        "orders": {str(nn): {k: v for k, v in o.items() if k != "y"} for nn, o in orders.items()},
+        "well": well_res,
         "batched": batch_res, "serving": serve_res,
         "error": err,
         "stages_ms_per_matvec": {k: v[0] / 3 for k, v in stages.items() if v[1] > 0},

@@ -99,6 +99,14 @@ const char *ddm_last_error(const ddm_ctx *ctx);
  * check, else DDM_OK.  No counterpart in the paper. */
 ddm_status ddm_device_check(ddm_ctx *ctx);
 
+/* Poll limit of the grid barriers in the GMRES orthogonalisation kernel
+ * (cooperative launch, every block resident): a block that has polled this
+ * many times gives up, raises the error word and carries on, so a wait never
+ * hangs.  polls = 0 restores the default (2^22 polls of about 64 ns).  A very
+ * small limit makes the waits give up on purpose (a test of the failure
+ * path: the solve then returns DDM_ETIMEOUT).  No counterpart in the paper. */
+ddm_status ddm_set_wait_limit(ddm_ctx *ctx, int64_t polls);
+
 /* Build the quadtree of paper Sec. 3.1 over the element midpoints: level-0
  * square covering all midpoints, uniform depth (smallest depth whose leaves
  * hold <= leaf_size elements, capped so that no element is longer than a
@@ -203,7 +211,14 @@ typedef struct {
  * such restart makes the Arnoldi products precise as well.  Returns
  * DDM_ENOTCONV (x and info still written) when max_iters is reached or three
  * further restarts in a row fail to reduce the residual by 10%.
- * Synchronises the stream (reads the Hessenberg columns back). */
+ * Arnoldi orthogonalisation, Givens rotations, the residual estimate and the
+ * least-squares solve run on the device in FP64; the host reads one status
+ * triple per Arnoldi step (live flag, residual estimate, the context's
+ * error word) and one norm per restart, so the call synchronises the
+ * stream.  DDM_ETIMEOUT when a grid barrier of the orthogonalisation gave
+ * up (see ddm_set_wait_limit): x is then invalid, and the barrier and the
+ * error word are reset before the call returns, so the context stays
+ * usable. */
 ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const double *d_rhs,
                            double *d_x, const ddm_gmres_params *prm, ddm_gmres_info *info);
 
@@ -284,11 +299,16 @@ void ddm_server_destroy(ddm_server *server);
  * elements (about 3 MB, held by every GPU that loads the library until the
  * process exits); n outside [1, DDM_STATIC_MAX_ELEMENTS] gives DDM_EINVAL.
  * The call uses no cudaMalloc/cudaFree or other allocating routine.  The
- * first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the array: calls whose work
- * overlaps on the GPU (other streams, other threads) race, so serialise
- * them.  Each call rewrites the entries it reads; nothing needs clearing. */
+ * context's device must be current (else DDM_EINVAL).  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  All
+ * calls share the array: calls whose work overlaps on the GPU (other
+ * streams, other threads) race, so serialise them.  Each call rewrites the
+ * entries it reads; nothing needs clearing.  d_x and d_y ranges that overlap
+ * give DDM_EINVAL.  The geometry is checked on the device without
+ * synchronising: an element of zero length or with a non-finite end point
+ * makes every output NaN (ddm_matvec rejects such geometry at the tree
+ * build instead). */
 #define DDM_STATIC_MAX_ELEMENTS 65536
 ddm_status ddm_matvec_dense_static(ddm_ctx *ctx, const double *d_xy, int64_t n, double tau_lo,
                                    double tau_hi, const double *d_x, double *d_y);

@@ -149,10 +149,10 @@ __global__ void k_dots_final(const double *part, int G, int pld, int nv, double 
 // Then V[nv] = w / ||w||, hcol[nv] = ||w||: one grid barrier per pass.  The
 // partials are stored by vector (part[v G + block]) for coalesced sums, each
 // pass in its own half of part[] (2 (nv + 1) G doubles).  The
-// barriers give up after a bounded number of polls and raise the error word
-// (the results are then invalid, nothing hangs).
-constexpr long long GB_POLLS = 1ll << 22;
-__device__ __forceinline__ void grid_barrier(unsigned *bar, int *err) {
+// barriers give up after max_polls polls (ddm_set_wait_limit) and raise the
+// error word (the results are then invalid, nothing hangs; the solve that
+// reads the word resets the barrier counters).
+__device__ __forceinline__ void grid_barrier(unsigned *bar, int *err, long long max_polls) {
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile unsigned *vb = bar;
@@ -165,7 +165,7 @@ __device__ __forceinline__ void grid_barrier(unsigned *bar, int *err) {
         } else {
             long long polls = 0;
             while (vb[1] == gen) {
-                if (++polls > GB_POLLS) { atomicExch(err, 1); break; }
+                if (++polls > max_polls) { atomicExch(err, 1); break; }
                 __nanosleep(64);
             }
         }
@@ -175,7 +175,8 @@ __device__ __forceinline__ void grid_barrier(unsigned *bar, int *err) {
 }
 constexpr int OR_T = 512, OR_W = OR_T / 32;
 __global__ void __launch_bounds__(OR_T) k_arnoldi_orth(double *V, int64_t len, int nv, double *w, int64_t chunk,
-                                                       double *part, double *hcol, unsigned *bar, int *err) {
+                                                       double *part, double *hcol, unsigned *bar, int *err,
+                                                       long long max_polls) {
     __shared__ double sh[512 + 1];
     __shared__ double s_hh;
     const int64_t i0 = blockIdx.x * chunk, i1 = i0 + chunk < len ? i0 + chunk : len;
@@ -195,7 +196,7 @@ __global__ void __launch_bounds__(OR_T) k_arnoldi_orth(double *V, int64_t len, i
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
             if (lane == 0) pp[(int64_t)v * G + blockIdx.x] = acc;
         }
-        grid_barrier(bar, err);
+        grid_barrier(bar, err, max_polls);
         // 2. h and ||w||^2 (every block, same order)
         for (int v = wid; v <= nv; v += OR_W) {
             double sum = 0.0;
@@ -263,15 +264,17 @@ struct GmresWork {
     int cap_m = 0;
     cudaStream_t st = nullptr;
     double *V = nullptr, *w = nullptr, *full = nullptr, *y3 = nullptr, *b = nullptr;
-    double *hcol = nullptr, *nrm = nullptr, *yv = nullptr, *part = nullptr;
+    double *hcol = nullptr, *nrm = nullptr, *part = nullptr;
     unsigned *cnt = nullptr;   // grid-barrier counter and generation (zero between launches)
-    double *hpin = nullptr;    // pinned host slots of the Hessenberg column / a norm (2 (m + 2))
-    cudaEvent_t ev[2] = {nullptr, nullptr};   // one per pinned slot
+    double *hpin = nullptr;    // pinned host slots: a norm, and per step the least-squares status (2 x 4)
+    cudaEvent_t ev[2] = {nullptr, nullptr};   // one per pinned status slot
+    LsqDev lsq;                // device least squares (krylov.cu)
     void release() {
-        double *ps[] = {V, w, full, y3, b, hcol, nrm, yv, part};
+        double *ps[] = {V, w, full, y3, b, hcol, nrm, part};
         cudaStream_t s = st;
         for (double *p : ps) dfree(p, s);
         dfree(cnt, s);
+        lsq_free(lsq, s);
         if (hpin) cudaFreeHost(hpin);
         for (cudaEvent_t e : ev)
             if (e) cudaEventDestroy(e);
@@ -382,6 +385,12 @@ ddm_status ddm_device_check(ddm_ctx *ctx) {
     return ctx_fail(ctx, DDM_ETIMEOUT, "a bounded device wait expired (results of the affected calls are invalid)");
 }
 
+ddm_status ddm_set_wait_limit(ddm_ctx *ctx, int64_t polls) {
+    if (!ctx || polls < 0) return ctx_fail(ctx, DDM_EINVAL, "ddm_set_wait_limit: bad arguments");
+    ctx->grid_polls = polls == 0 ? (1ll << 22) : (long long)polls;
+    return DDM_OK;
+}
+
 ddm_status ddm_profile(ddm_ctx *ctx, int enable) {
     if (!ctx) return DDM_EINVAL;
     ctx->prof.on = enable ? 1 : 0;
@@ -482,6 +491,7 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
     int64_t len = nc * N;
     int m = P.restart;
     GmresWork &g = *ctx->gm;
+    ddm_status st0;
     if (g.cap_len < len || g.cap_m < m) {
         g.release();
         size_t v3 = 3 * N * sizeof(double);
@@ -492,16 +502,16 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
                   dalloc(&g.b, v3, s) == cudaSuccess &&
                   dalloc(&g.hcol, (m + 2) * sizeof(double), s) == cudaSuccess &&
                   dalloc(&g.nrm, sizeof(double), s) == cudaSuccess &&
-                  dalloc(&g.yv, (m + 1) * sizeof(double), s) == cudaSuccess &&
                   dalloc(&g.part, (size_t)2 * DP_G * (m + 2) * sizeof(double), s) == cudaSuccess &&
                   dalloc(&g.cnt, 4 * sizeof(unsigned), s) == cudaSuccess &&
                   cudaMemsetAsync(g.cnt, 0, 4 * sizeof(unsigned), s) == cudaSuccess &&
-                  cudaMallocHost(&g.hpin, 2 * (m + 2) * sizeof(double)) == cudaSuccess &&
+                  cudaMallocHost(&g.hpin, 12 * sizeof(double)) == cudaSuccess &&
                   cudaEventCreateWithFlags(&g.ev[0], cudaEventDisableTiming) == cudaSuccess &&
                   cudaEventCreateWithFlags(&g.ev[1], cudaEventDisableTiming) == cudaSuccess;
         if (!ok) { g.release(); return ctx_fail(ctx, DDM_ENOMEM, "GMRES workspace allocation failed"); }
         g.cap_len = len; g.cap_m = m;
     }
+    if ((st0 = lsq_alloc(ctx, g.lsq, 1, m, s))) return st0;
     int mode = P.mode & ~DDM_MODE_PRECISE, sys = P.system;
     ddm_status st;
     // operator y(len) = restrict(A(dt) [v; 0]) ; the 3N layout keeps blocks of N
@@ -555,8 +565,7 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
     bool x_zero = xnorm == 0.0;
     int iters = 0, restarts = 0;
     double rel = 1e300;
-    std::vector<double> H((m + 1) * m), cs(m), sn(m), gv(m + 1), hc(m + 2);
-    bool conv = false;
+    bool conv = false, timed_out = false;
     double best = 1e300;
     int stall = 0;
     // Precision escalates only when a restart cycle stalls (the residual
@@ -567,6 +576,8 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
     // three more stalls end the solve.  Long fractures, whose element
     // contributions cancel strongly, are what reach levels 1 and 2.
     int level = 0;
+    if ((st = lsq_reset_iters(ctx, g.lsq, s))) return st;
+    DDM_CUDA_TRY(ctx, cudaMemsetAsync(g.cnt, 0, 4 * sizeof(unsigned), s));   // grid barrier starts at zero
     while (iters < P.max_iters) {
         // r = b - A x
         if (x_zero) {
@@ -592,17 +603,18 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
         else if (++stall >= 3) break;
         // inner target: the tolerance, or (refinement) two decades below beta
         double inner = level == 0 ? 0.3 * P.tol * bnorm : std::max(0.3 * P.tol * bnorm, 1e-4 * beta);
-        // v0 = -w / beta
+        // v0 = -w / beta; g = (beta, 0, ...) on the device
         DDM_CUDA_TRY(ctx, cudaMemsetAsync(g.V, 0, len * sizeof(double), s));
         k_axpy<<<nblk(len), 256, 0, s>>>(-1.0 / beta, g.w, g.V, len);
-        std::fill(gv.begin(), gv.end(), 0.0);
-        gv[0] = beta;
+        if ((st = lsq_begin(ctx, g.lsq, 1, &beta, &inner, nullptr, s))) return st;
         // One Arnoldi step: preconditioner, product, orthogonalisation (V[jj+1],
-        // Hessenberg column jj on the device), then the column into pinned
-        // slot jj % 2 and its event.  Steps only depend on each other through
-        // the device, so step j + 1 is enqueued before the host reads column
-        // j: the GPU never waits for the host's Givens rotations, and a cycle
-        // that ends at column j leaves one discarded step behind.
+        // Hessenberg column jj), the Givens step on the device, then the
+        // status triple (live, |g_{jj+1}|, error word) into pinned slot jj % 2
+        // and its event.  Steps only depend on each other through the device,
+        // so step j + 1 is enqueued before the host reads the status of step
+        // j: the GPU never waits for the host, and a cycle that ends at
+        // column j leaves one discarded step behind (its Givens step sees the
+        // problem no longer live and changes nothing).
         auto step = [&](int jj) -> ddm_status {
             double *vj = g.V + (int64_t)jj * len;
             prof_begin(ctx, 8);
@@ -622,12 +634,14 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
                 int64_t ln = len, ch = orth_chunk;
                 unsigned *bp = g.cnt;
                 int *ep = ctx->d_err;
-                void *args[] = {&Vp, &ln, &nvj, &wp, &ch, &pp, &hcp, &bp, &ep};
+                long long polls = ctx->grid_polls;
+                void *args[] = {&Vp, &ln, &nvj, &wp, &ch, &pp, &hcp, &bp, &ep, &polls};
                 DDM_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void *)k_arnoldi_orth, dim3(orth_grid), dim3(OR_T),
                                                               args, 0, s));
             }
-            prof_end(ctx, 8, 1);      // orthogonalisation
-            DDM_CUDA_TRY(ctx, cudaMemcpyAsync(g.hpin + (jj & 1) * (m + 2), g.hcol, (jj + 2) * sizeof(double),
+            if ((e = lsq_step(ctx, g.lsq, 1, g.hcol, m + 2, jj, P.max_iters, false, true, s))) return e;
+            prof_end(ctx, 8, 2);      // orthogonalisation + Givens step
+            DDM_CUDA_TRY(ctx, cudaMemcpyAsync(g.hpin + 4 + (jj & 1) * 4, g.lsq.stat, 3 * sizeof(double),
                                               cudaMemcpyDeviceToHost, s));
             DDM_CUDA_TRY(ctx, cudaEventRecord(g.ev[jj & 1], s));
             return DDM_OK;
@@ -639,47 +653,38 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
             const bool more = j + 1 < m && iters + 1 < P.max_iters;
             if (more && (st = step(j + 1))) return st;
             DDM_CUDA_TRY(ctx, cudaEventSynchronize(g.ev[j & 1]));
-            std::copy(g.hpin + (j & 1) * (m + 2), g.hpin + (j & 1) * (m + 2) + j + 2, hc.begin());
-            // Givens rotations on the new column
-            for (int i = 0; i < j; ++i) {
-                double a = cs[i] * hc[i] + sn[i] * hc[i + 1];
-                hc[i + 1] = -sn[i] * hc[i] + cs[i] * hc[i + 1];
-                hc[i] = a;
-            }
-            double r = hypot(hc[j], hc[j + 1]);
-            cs[j] = r > 0 ? hc[j] / r : 1.0;
-            sn[j] = r > 0 ? hc[j + 1] / r : 0.0;
-            hc[j] = r;
-            hc[j + 1] = 0;
-            gv[j + 1] = -sn[j] * gv[j];
-            gv[j] = cs[j] * gv[j];
-            for (int i = 0; i <= j; ++i) H[i * m + j] = hc[i];
-            rel = fabs(gv[j + 1]) / bnorm;
-            const bool done = fabs(gv[j + 1]) < inner || r == 0;
+            const double *stat = g.hpin + 4 + (j & 1) * 4;
+            rel = stat[1] / bnorm;
             ++j;
             ++iters;
-            if (done) break;
+            if (stat[2] != 0.0) { timed_out = true; break; }
+            if (stat[0] == 0.0) break;
             pending = more;
         }
-        // least squares: upper triangular solve, x += M^-1 V y
-        std::vector<double> yv(j, 0.0);
-        for (int i = j - 1; i >= 0; --i) {
-            double sum = gv[i];
-            for (int k = i + 1; k < j; ++k) sum -= H[i * m + k] * yv[k];
-            yv[i] = sum / H[i * m + i];
-        }
+        if (timed_out) break;
+        // least squares on the device (y = R^-1 g), x += M^-1 V y
         if (j > 0) {
-            DDM_CUDA_TRY(ctx, cudaMemcpyAsync(g.yv, yv.data(), j * sizeof(double), cudaMemcpyHostToDevice, s));
-            k_comb<<<nblk(len), 256, 0, s>>>(g.V, len, j, g.yv, g.w, len);
+            if ((st = lsq_solve(ctx, g.lsq, 1, s))) return st;
+            k_comb<<<nblk(len), 256, 0, s>>>(g.V, len, j, g.lsq.y, g.w, len);
             if ((st = pb_apply(ctx, t, sys, g.w, g.full, s))) return st;
             k_axpy<<<nblk(len), 256, 0, s>>>(1.0, g.full, d_x, len);
-            DDM_CUDA_TRY(ctx, cudaStreamSynchronize(s));    // yv host buffer goes out of scope
         }
         ++restarts;
-        if (rel < P.tol) {
-            // confirm with the true residual
-            continue;
+    }
+    if (timed_out) {
+        // a grid barrier gave up: the solve's results are invalid; the
+        // barrier counters and the error word are reset after the work
+        // already enqueued, so that the context stays usable
+        DDM_CUDA_TRY(ctx, cudaMemsetAsync(g.cnt, 0, 4 * sizeof(unsigned), s));
+        DDM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), s));
+        DDM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        if (info) {
+            info->iterations = iters;
+            info->restarts = restarts;
+            info->rel_residual = rel;
+            info->converged = 0;
         }
+        return ctx_fail(ctx, DDM_ETIMEOUT, "ddm_gmres_solve: a bounded device wait expired (the solution is invalid)");
     }
     if (info) {
         info->iterations = iters;

@@ -5,8 +5,9 @@
 // forked streams, so that small problems overlap on the device) and the
 // whole batch is advanced by one graph launch.  GMRES runs in lockstep over
 // an arena that concatenates the problems' vectors: Arnoldi in FP64 with
-// segmented (per-problem) reductions, one Hessenberg column per problem read
-// back per iteration, Givens rotations and convergence per problem.
+// segmented (per-problem) reductions, then Givens rotations, convergence
+// and least squares per problem on the device (krylov.cu); the host reads
+// the number of problems still live after each step.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -118,7 +119,8 @@ struct ddm_batch {
     int nblk = 0;
     double *V = nullptr, *w = nullptr, *vin = nullptr, *b = nullptr, *tmp = nullptr;
     double *full = nullptr, *y3 = nullptr, *Minv = nullptr;
-    double *h = nullptr, *hcol = nullptr, *nrm = nullptr, *coef = nullptr, *Y = nullptr;
+    double *h = nullptr, *hcol = nullptr, *nrm = nullptr, *coef = nullptr;
+    LsqDev lsq;                           // device least squares of every problem
     std::vector<int64_t> minv_off;
     // graphs
     cudaGraphExec_t g_op = nullptr, g_prod = nullptr, g_res = nullptr;
@@ -133,9 +135,10 @@ struct ddm_batch {
     cudaStream_t ast = nullptr;            // stream of the arena allocations
     cudaEvent_t ev_fork[NSTREAMS] = {}, ev_join[NSTREAMS] = {};
     void free_solver() {
-        void *ps[] = {prob, blk, V, w, vin, b, tmp, Minv, h, hcol, nrm, coef, Y};
+        void *ps[] = {prob, blk, V, w, vin, b, tmp, Minv, h, hcol, nrm, coef};
         for (void *p : ps) dfree(p, ast);
-        prob = nullptr; blk = nullptr; V = w = vin = b = tmp = Minv = h = hcol = nrm = coef = Y = nullptr;
+        lsq_free(lsq, ast);
+        prob = nullptr; blk = nullptr; V = w = vin = b = tmp = Minv = h = hcol = nrm = coef = nullptr;
         sys = -1; m = 0;
     }
     void free_graphs() {
@@ -310,8 +313,7 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
                   dalloc(&B->h, (size_t)P * hs * sizeof(double), s) == cudaSuccess &&
                   dalloc(&B->hcol, (size_t)P * hs * sizeof(double), s) == cudaSuccess &&
                   dalloc(&B->nrm, (size_t)P * hs * sizeof(double), s) == cudaSuccess &&
-                  dalloc(&B->coef, P * sizeof(double), s) == cudaSuccess &&
-                  dalloc(&B->Y, (size_t)P * hs * sizeof(double), s) == cudaSuccess;
+                  dalloc(&B->coef, P * sizeof(double), s) == cudaSuccess;
         if (!ok) { B->free_solver(); return ctx_fail(ctx, DDM_ENOMEM, "batch GMRES arena allocation failed"); }
         cudaMemcpyAsync(B->prob, hp.data(), L * sizeof(int32_t), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(B->blk, hb.data(), hb.size() * sizeof(SegBlk), cudaMemcpyHostToDevice, s);
@@ -388,10 +390,9 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
     for (double &x : bn)
         if (x == 0) x = 1;
     std::vector<int> iters(P, 0), restarts(P, 0), conv(P, 0), stall(P, 0), active(P, 1);
-    std::vector<double> rel(P, 1e300), best(P, 1e300);
-    std::vector<double> H((size_t)P * (m + 1) * m), cs((size_t)P * m), sn((size_t)P * m), gv((size_t)P * (m + 1));
-    std::vector<double> hc((size_t)P * hs), coef(P), Yh((size_t)P * hs);
-    std::vector<int> jend(P);
+    std::vector<double> rel(P, 1e300), best(P, 1e300), coef(P), inner(P);
+    if ((st = lsq_alloc(ctx, B->lsq, P, m, s)) || (st = lsq_reset_iters(ctx, B->lsq, s))) return st;
+    int *h_still = B->lsq.hint, *h_iters = B->lsq.hint + 1;
     int total = 0;
     while (true) {
         // residuals (operator of each problem's level): tmp = A x, w = A x - b
@@ -399,7 +400,9 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
         prof_end(ctx, 6, (int)B->k_res);
         DDM_CUDA_TRY(ctx, cudaMemcpyAsync(B->w, B->tmp, L * sizeof(double), cudaMemcpyDeviceToDevice, s));
         k_axpy_b<<<nb(L), BT, 0, s>>>(-1.0, B->b, B->w, L);
-        if ((st = seg_norms(B->w, beta))) return st;
+        DDM_CUDA_TRY(ctx, cudaMemcpyAsync(h_iters, B->lsq.iters, P * sizeof(int), cudaMemcpyDeviceToHost, s));
+        if ((st = seg_norms(B->w, beta))) return st;      // synchronises: h_iters is current
+        std::copy(h_iters, h_iters + P, iters.begin());
         int nact = 0;
         bool reprec = false;
         std::vector<int> remeasure(P, 0);   // switched to precise residuals: no cycle until re-measured
@@ -433,22 +436,18 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
         for (int p = 0; p < P; ++p) coef[p] = active[p] && beta[p] > 0 ? -1.0 / beta[p] : 0.0;
         DDM_CUDA_TRY(ctx, cudaMemcpyAsync(B->coef, coef.data(), P * sizeof(double), cudaMemcpyHostToDevice, s));
         k_v0_seg<<<nb(L), BT, 0, s>>>(B->w, B->coef, B->prob, L, B->V);
-        std::fill(gv.begin(), gv.end(), 0.0);
-        std::vector<double> inner(P);
+        std::vector<int> live(P);
         for (int p = 0; p < P; ++p) {
-            gv[(size_t)p * (m + 1)] = active[p] ? beta[p] : 0.0;
-            jend[p] = 0;
+            live[p] = active[p] && !remeasure[p];
             inner[p] = level[p] == 0 ? 0.3 * Pm.tol * bn[p] : std::max(0.3 * Pm.tol * bn[p], 1e-4 * beta[p]);
         }
-        std::vector<int> live = active;
-        for (int p = 0; p < P; ++p)
-            if (remeasure[p]) live[p] = 0;
+        if ((st = lsq_begin(ctx, B->lsq, P, beta.data(), inner.data(), live.data(), s))) return st;
         int j = 0;
         for (; j < m; ++j) {
             DDM_CUDA_TRY(ctx, cudaMemcpyAsync(B->vin, B->V + (int64_t)j * L, L * sizeof(double), cudaMemcpyDeviceToDevice, s));
             DDM_CUDA_TRY(ctx, cudaGraphLaunch(B->g_op, s));
             prof_end(ctx, 6, (int)B->k_op);
-            prof_end(ctx, 8, 9);
+            prof_end(ctx, 8, 10);
             DDM_CUDA_TRY(ctx, cudaMemsetAsync(B->hcol, 0, (size_t)P * hs * sizeof(double), s));
             for (int pass = 0; pass < 2; ++pass) {
                 DDM_CUDA_TRY(ctx, cudaMemsetAsync(B->h, 0, (size_t)P * hs * sizeof(double), s));
@@ -460,60 +459,29 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
             k_dots_seg<<<dim3(B->nblk, 1), BT, 0, s>>>(B->w, 0, B->w, B->blk, 1, B->nrm, 1);
             k_scale_seg<<<nb(std::max<int64_t>(L, P)), BT, 0, s>>>(B->w, B->nrm, B->prob, L, B->V + (int64_t)(j + 1) * L,
                                                                    B->hcol, hs, j + 1, P);
-            DDM_CUDA_TRY(ctx, cudaMemcpyAsync(hc.data(), B->hcol, (size_t)P * hs * sizeof(double), cudaMemcpyDeviceToHost, s));
+            // Givens step of every live problem on the device; read how many stay live
+            if ((st = lsq_step(ctx, B->lsq, P, B->hcol, hs, j, Pm.max_iters, true, false, s))) return st;
+            DDM_CUDA_TRY(ctx, cudaMemcpyAsync(h_still, B->lsq.still, sizeof(int), cudaMemcpyDeviceToHost, s));
             DDM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
             ++total;
-            int still = 0;
-            for (int p = 0; p < P; ++p) {
-                if (!live[p]) continue;
-                double *c = &hc[(size_t)p * hs];
-                double *csp = &cs[(size_t)p * m], *snp = &sn[(size_t)p * m], *g = &gv[(size_t)p * (m + 1)];
-                for (int i = 0; i < j; ++i) {
-                    double a = csp[i] * c[i] + snp[i] * c[i + 1];
-                    c[i + 1] = -snp[i] * c[i] + csp[i] * c[i + 1];
-                    c[i] = a;
-                }
-                double r = hypot(c[j], c[j + 1]);
-                csp[j] = r > 0 ? c[j] / r : 1.0;
-                snp[j] = r > 0 ? c[j + 1] / r : 0.0;
-                c[j] = r;
-                g[j + 1] = -snp[j] * g[j];
-                g[j] = csp[j] * g[j];
-                for (int i = 0; i <= j; ++i) H[((size_t)p * (m + 1) + i) * m + j] = c[i];
-                ++iters[p];
-                jend[p] = j + 1;
-                if (fabs(g[j + 1]) < inner[p] || r == 0 || iters[p] >= Pm.max_iters) live[p] = 0;
-                else ++still;
-            }
-            if (still == 0) { ++j; break; }
+            if (*h_still == 0) { ++j; break; }
         }
-        // per-problem least squares and update x += M^-1 V y
-        std::fill(Yh.begin(), Yh.end(), 0.0);
-        for (int p = 0; p < P; ++p) {
-            if (!active[p]) continue;
-            int jp = jend[p];
-            double *y = &Yh[(size_t)p * hs];
-            for (int i = jp - 1; i >= 0; --i) {
-                double sum = gv[(size_t)p * (m + 1) + i];
-                for (int k = i + 1; k < jp; ++k) sum -= H[((size_t)p * (m + 1) + i) * m + k] * y[k];
-                double d = H[((size_t)p * (m + 1) + i) * m + i];
-                y[i] = d != 0 ? sum / d : 0.0;
-            }
-            ++restarts[p];
-        }
-        int jm = 0;
-        for (int p = 0; p < P; ++p) jm = std::max(jm, active[p] ? jend[p] : 0);
-        if (jm > 0) {
-            DDM_CUDA_TRY(ctx, cudaMemcpyAsync(B->Y, Yh.data(), (size_t)P * hs * sizeof(double), cudaMemcpyHostToDevice, s));
-            k_comb_seg<<<nb(L), BT, 0, s>>>(B->V, L, jm, B->Y, hs, B->prob, L, B->tmp);
+        // per-problem least squares on the device and update x += M^-1 V y
+        if ((st = lsq_solve(ctx, B->lsq, P, s))) return st;
+        for (int p = 0; p < P; ++p)
+            if (active[p]) ++restarts[p];
+        if (j > 0) {
+            k_comb_seg<<<nb(L), BT, 0, s>>>(B->V, L, j, B->lsq.y, m + 2, B->prob, L, B->tmp);
             for (int p = 0; p < P; ++p)
                 if (active[p]) {
                     if ((st = pb_apply(ctx, B->trees[p], sys, B->tmp + B->offs[p], B->full + B->off3[p], s))) return st;
                     k_axpy_b<<<nb(nc * B->N[p]), BT, 0, s>>>(1.0, B->full + B->off3[p], d_x + B->off3[p], nc * B->N[p]);
                 }
-            DDM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
         }
     }
+    DDM_CUDA_TRY(ctx, cudaMemcpyAsync(h_iters, B->lsq.iters, P * sizeof(int), cudaMemcpyDeviceToHost, s));
+    DDM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    std::copy(h_iters, h_iters + P, iters.begin());
     bool all = true;
     for (int p = 0; p < P; ++p) {
         if (infos) {

@@ -1624,7 +1624,8 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
 // 3 MB), which every GPU that loads the library holds until the process
 // exits.  All calls share the array, so calls whose work overlaps on the GPU
 // race; each call rewrites the entries of its n elements before reading them,
-// and nothing in the array needs to start at zero.
+// and nothing in the array needs to start at zero.  A one-word flag beside
+// it, cleared by every call, marks invalid geometry.
 // ---------------------------------------------------------------------------
 namespace {
 struct StaticElem {
@@ -1633,15 +1634,20 @@ struct StaticElem {
     float4 chg;      // global DD vector (x, y), fluid source, unused
 };
 static __device__ __align__(256) StaticElem g_static_scratch[DDM_STATIC_MAX_ELEMENTS];
+// raised by the preparation kernel for an element of zero length or with a
+// non-finite end point (cleared at the start of every call)
+static __device__ int g_static_bad;
 
 std::mutex g_static_mu;
 StaticElem *g_static_ptr[256] = {nullptr};   // device address of the array, per device
+int *g_static_bad_ptr[256] = {nullptr};      // device address of the flag, per device
 
-__global__ void k_static_prep(const double *xy, const double *x, int64_t n, StaticElem *sc) {
+__global__ void k_static_prep(const double *xy, const double *x, int64_t n, StaticElem *sc, int *bad) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= n) return;
     double ax = xy[e], ay = xy[n + e], bx = xy[2 * n + e], by = xy[3 * n + e];
     double L = hypot(bx - ax, by - ay), tx = (bx - ax) / L, ty = (by - ay) / L;
+    if (!(L > 0.0) || !isfinite(L) || !isfinite(ax) || !isfinite(ay)) *bad = 1;
     float Ds = (float)x[e], Dn = (float)x[n + e], Dq = (float)x[2 * n + e];
     float ftx = (float)tx, fty = (float)ty;
     StaticElem s;
@@ -1656,9 +1662,13 @@ __global__ void k_static_prep(const double *xy, const double *x, int64_t n, Stat
 constexpr int ST_T = 128;
 __global__ void __launch_bounds__(ST_T) k_static_dense(KConst<float> k, KConst<double> kd, Win<float> w,
                                                        Win<double> wd, int nq, const StaticElem *sc, const double *x,
-                                                       int64_t n, double *y) {
+                                                       int64_t n, double *y, const int *bad) {
     __shared__ StaticElem tile[ST_T];
     int64_t ti = blockIdx.x * (int64_t)ST_T + threadIdx.x;
+    if (*bad) {          // invalid geometry: every output is NaN, nothing else is read
+        if (ti < n) y[ti] = y[n + ti] = y[2 * n + ti] = __longlong_as_double(0x7ff8000000000000ll);
+        return;
+    }
     bool act = ti < n;
     StaticElem me = act ? sc[ti] : sc[0];
     double accd[4] = {0, 0, 0, 0};
@@ -1696,37 +1706,50 @@ __global__ void __launch_bounds__(ST_T) k_static_dense(KConst<float> k, KConst<d
 
 extern "C" ddm_status ddm_matvec_dense_static(ddm_ctx *ctx, const double *d_xy, int64_t n, double tau_lo,
                                               double tau_hi, const double *d_x, double *d_y) {
-    if (!ctx || !d_xy || !d_x || !d_y || d_x == d_y)
+    if (!ctx || !d_xy || !d_x || !d_y)
         return ctx_fail(ctx, DDM_EINVAL, "ddm_matvec_dense_static: bad arguments");
     if (n <= 0 || n > DDM_STATIC_MAX_ELEMENTS)
         return ctx_fail(ctx, DDM_EINVAL, "ddm_matvec_dense_static: n must be in [1, " +
                                              std::to_string(DDM_STATIC_MAX_ELEMENTS) + "], got " + std::to_string(n));
+    {   // d_y is written while d_x is still read: the 3n ranges must not overlap
+        const uintptr_t xa = (uintptr_t)d_x, ya = (uintptr_t)d_y, len = (uintptr_t)(3 * n) * sizeof(double);
+        if (xa < ya + len && ya < xa + len)
+            return ctx_fail(ctx, DDM_EINVAL, "ddm_matvec_dense_static: d_x and d_y overlap");
+    }
     if (!(tau_hi > tau_lo) || tau_lo < 0.0)
         return ctx_fail(ctx, DDM_EINVAL, "ddm_matvec_dense_static: need 0 <= tau_lo < tau_hi");
     int dev = 0;
     DDM_CUDA_TRY(ctx, cudaGetDevice(&dev));
+    if (dev != ctx->device)
+        return ctx_fail(ctx, DDM_EINVAL, "ddm_matvec_dense_static: the context's device must be current");
     if (dev < 0 || dev >= 256) return ctx_fail(ctx, DDM_EINVAL, "ddm_matvec_dense_static: device index out of range");
     StaticElem *sc = nullptr;
+    int *bad = nullptr;
     {
         // set-up, once per device, with that device current: the host-side
-        // name of the array is not a device address; ask the runtime for it
+        // names of the array and the flag are not device addresses; ask the
+        // runtime for them
         std::lock_guard<std::mutex> lk(g_static_mu);
         if (!g_static_ptr[dev]) {
-            void *p = nullptr;
+            void *p = nullptr, *q = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+            if (e == cudaSuccess) e = cudaGetSymbolAddress(&q, g_static_bad);
             if (e != cudaSuccess)
                 return ctx_fail(ctx, DDM_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            g_static_bad_ptr[dev] = (int *)q;
             g_static_ptr[dev] = (StaticElem *)p;
         }
         sc = g_static_ptr[dev];
+        bad = g_static_bad_ptr[dev];
     }
     ddm_status st = upload_tables(ctx);
     if (st) return st;
     cudaStream_t s = ctx->stream;
     Win<float> wf = make_win<float>(ctx, tau_lo, tau_hi);
     Win<double> wd = make_win<double>(ctx, tau_lo, tau_hi);
-    k_static_prep<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_xy, d_x, n, sc);
-    k_static_dense<<<(unsigned)((n + ST_T - 1) / ST_T), ST_T, 0, s>>>(ctx->kf, ctx->kd, wf, wd, ctx->prm.quad_near, sc, d_x, n, d_y);
+    DDM_CUDA_TRY(ctx, cudaMemsetAsync(bad, 0, sizeof(int), s));
+    k_static_prep<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_xy, d_x, n, sc, bad);
+    k_static_dense<<<(unsigned)((n + ST_T - 1) / ST_T), ST_T, 0, s>>>(ctx->kf, ctx->kd, wf, wd, ctx->prm.quad_near, sc, d_x, n, d_y, bad);
     prof_end(ctx, 7, 2);
     DDM_CUDA_TRY(ctx, cudaGetLastError());
     return DDM_OK;

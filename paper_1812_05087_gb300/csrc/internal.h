@@ -102,6 +102,35 @@ struct ddm_tree {
 
 struct GmresWork;
 
+// Device state of the GMRES least squares (krylov.cu), P problems of
+// restart m: rotated Hessenberg columns H (row-major (m + 1) x m each),
+// Givens cosines and sines, the rotated right-hand side g, the solution y of
+// R y = g (m + 2 per problem, zero past the cycle's columns), the inner
+// targets, the residual estimates |g_{j+1}|, the live flags, the cycle's
+// column counts, the iteration counts, the number of problems still live
+// after a step, and a status triple of problem 0 (live, |g_{j+1}|, the
+// context's error word) for the single solve's per-step read.
+struct LsqDev {
+    int P = 0, m = 0;
+    double *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
+    double *inner = nullptr, *res = nullptr, *stat = nullptr, *hbuf_dev = nullptr;
+    int *live = nullptr, *jend = nullptr, *iters = nullptr, *still = nullptr;
+    double *hbuf = nullptr;    // pinned staging of (beta, inner, live0) per problem
+    double *hstat = nullptr;   // pinned: two slots of the status triple (plus padding)
+    int *hint = nullptr;       // pinned: the still-live count, then P iteration counts
+};
+ddm_status lsq_alloc(ddm_ctx *ctx, LsqDev &L, int P, int m, cudaStream_t s);
+void lsq_free(LsqDev &L, cudaStream_t s);
+ddm_status lsq_reset_iters(ddm_ctx *ctx, LsqDev &L, cudaStream_t s);
+// start a cycle from host values beta, inner (P each) and live0 (P, or NULL = all)
+ddm_status lsq_begin(ddm_ctx *ctx, LsqDev &L, int P, const double *beta, const double *inner, const int *live0,
+                     cudaStream_t s);
+// Givens step on column j (hcol[p * hstride + i], i <= j + 1) of every live problem
+ddm_status lsq_step(ddm_ctx *ctx, LsqDev &L, int P, const double *hcol, int hstride, int j, int max_iters,
+                    bool count_still, bool write_stat, cudaStream_t s);
+// y = R^{-1} g per problem
+ddm_status lsq_solve(ddm_ctx *ctx, LsqDev &L, int P, cudaStream_t s);
+
 // Optional stage timing (CUDA events on the context stream) and launch
 // counting.  Stages: 0 prep (charges + own elements), 1 own-element blocks,
 // 2 up (fused with prep, P2M, M2M), 3 M2L operators, 4 m2l, 5 down, 6 leaf,
@@ -132,6 +161,7 @@ struct ddm_ctx {
     GmresWork *gm;
     Prof prof;
     int *d_err;                // device word raised by a kernel whose bounded wait expired
+    long long grid_polls = 1ll << 22;   // poll limit of the GMRES grid barriers (ddm_set_wait_limit)
     double *h_pin = nullptr;   // pinned host staging (tree build: element end points)
     int64_t h_pin_cap = 0;
 };

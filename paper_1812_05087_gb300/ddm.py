@@ -29,7 +29,7 @@ EXPORTS = ("ddm_create", "ddm_destroy", "ddm_last_error", "ddm_device_check", "d
            "ddm_tree_get_info", "ddm_matvec", "ddm_history_apply", "ddm_rhs", "ddm_gmres_solve", "ddm_sif",
            "ddm_profile", "ddm_profile_read", "ddm_batch_create", "ddm_batch_destroy", "ddm_batch_matvec",
            "ddm_batch_gmres_solve", "ddm_server_create", "ddm_submit", "ddm_poll", "ddm_server_destroy",
-           "ddm_matvec_dense_static")
+           "ddm_matvec_dense_static", "ddm_set_wait_limit")
 STATIC_MAX_ELEMENTS = 65536
 NSTAGES = 10
 STAGES = ("prep", "self_blocks", "up", "m2l_ops", "m2l", "down", "leaf", "dense", "krylov", "tree")
@@ -112,6 +112,7 @@ def load(build_if_missing: bool = True):
                                       ctypes.POINTER(ddm_gmres_info)]
         L.ddm_sif.argtypes = [_VP, _VP, _VP, _VP, ctypes.c_int, _VP, _VP]
         L.ddm_profile.argtypes = [_VP, ctypes.c_int]
+        L.ddm_set_wait_limit.argtypes = [_VP, ctypes.c_int64]
         L.ddm_matvec_dense_static.argtypes = [_VP, _VP, ctypes.c_int64, ctypes.c_double, ctypes.c_double, _VP, _VP]
         L.ddm_server_create.argtypes = [_VP, ctypes.c_size_t, ctypes.c_int, ctypes.c_double, ctypes.POINTER(_VP)]
         L.ddm_submit.argtypes = [_VP, ctypes.POINTER(ddm_request), ctypes.POINTER(ctypes.c_uint64)]
@@ -242,6 +243,11 @@ def ddm_device_check(ctx):
     _check(ctx, load().ddm_device_check(ctx), "ddm_device_check")
 
 
+def ddm_set_wait_limit(ctx, polls=0):
+    """Poll limit of the GMRES grid barriers (0 = the default)."""
+    _check(ctx, load().ddm_set_wait_limit(ctx, int(polls)), "ddm_set_wait_limit")
+
+
 def ddm_profile_read(ctx) -> dict:
     ms = (ctypes.c_double * NSTAGES)()
     n = (ctypes.c_int64 * NSTAGES)()
@@ -255,7 +261,7 @@ def ddm_matvec_dense_static(ctx, xy, tau_lo, tau_hi, x, y):
     n = xy.numel() // 4
     _check(ctx, load().ddm_matvec_dense_static(ctx, _VP(_dev(xy, 4 * n, "xy")), n, float(tau_lo), float(tau_hi),
                                                _VP(_dev(x, 3 * n, "x")), _VP(_dev(y, 3 * n, "y"))),
-           "ddm_matvec_dense_static")
+           "ddm_matvec_dense_static", "ddm_set_wait_limit")
 
 
 def ddm_batch_create(ctx, trees):
@@ -452,6 +458,9 @@ class Context:
 
     def device_check(self):
         ddm_device_check(self.ptr)
+
+    def set_wait_limit(self, polls=0):
+        ddm_set_wait_limit(self.ptr, polls)
 
     def close(self):
         if self.ptr:

@@ -120,6 +120,20 @@ def parallel_fractures(n_frac=10, spacing=20.0, half_length=100.0, elems=2000):
     return assemble(segs), segs
 
 
+# Horizontal-well example (paper Sec. 5, Table 2): in-situ stresses and
+# initial pore pressure; constant injection per fracture (per unit
+# thickness) split uniformly along the fracture, time steps of 60 s.
+WELL_LOADS = {"sigma_H": 58.60e6, "sigma_h": 55.15e6, "p0": 48.26e6}
+WELL_INJECTION = 0.01     # m^3/s per fracture
+WELL_DT = 60.0
+
+
+def well_source(half_length=100.0, injection=WELL_INJECTION):
+    """Fluid source per unit element length (m^2/s per m) of a fracture of
+    the given half-length carrying `injection` split uniformly."""
+    return injection / (2.0 * half_length)
+
+
 def batch_problems(n_problems=512, nmin=100, nmax=20000, seed=SEED + 4):
     """Uneven fracture sets: N log-uniform in [nmin, nmax], fracture count
     U{1..100} capped at N/10, box side scaled with sqrt(N / 20000) * 200 m so

@@ -126,3 +126,31 @@ def test_exact_dense_matches_oracle_tightly(ctx, geom, win):
     ref = oracle.matvec(MAT, xy, x, win[0], win[1])
     assert block_rel_err(y, ref, n) < 1e-7
     tree.close()
+
+
+def test_grid_barrier_timeout_reported_and_context_recovers(ctx):
+    """A poll limit of one makes the grid barriers of the GMRES
+    orthogonalisation give up (no kernel is broken: the waits return early
+    and raise the context's error word).  The solve reports DDM_ETIMEOUT,
+    resets the barrier and the word, and the next solve on the same context,
+    at the default limit, converges to the oracle's direct solution."""
+    from paper_1812_05087_gb300.ddm import DDM_ETIMEOUT
+    xy = inputs.single_crack(64, 1.0)
+    N = xy.shape[1]
+    tree = ctx.build_tree(dev(xy))
+    b = ctx.rhs(tree, p_f=1e6, system="impermeable")
+    ctx.set_wait_limit(1)
+    try:
+        with pytest.raises(DDMError) as e:
+            ctx.gmres_solve(tree, 10.0, b, system="impermeable", tol=1e-8)
+        assert e.value.status == DDM_ETIMEOUT
+    finally:
+        ctx.set_wait_limit(0)
+    ctx.device_check()                     # the word was cleared by the solve
+    x, info = ctx.gmres_solve(tree, 10.0, b, system="impermeable", tol=1e-8)
+    assert info["converged"]
+    ref = oracle.solve(oracle.assemble(MAT, xy, 10.0), oracle.rhs(xy, p_f=1e6, system="impermeable"), N,
+                       "impermeable")
+    assert block_rel_err(x.cpu().numpy(), ref, N, blocks=2) < 1e-4
+    ctx.device_check()
+    tree.close()

@@ -94,16 +94,6 @@ def test_gmres_matches_direct_solve(ctx, crack, system, mode):
     assert block_rel_err(x.cpu().numpy(), ref, N, nb) < 1e-3
 
 
-def test_sif_matches_oracle(ctx, crack):
-    N = crack.shape[1]
-    tree = ctx.build_tree(dev(crack))
-    x = inputs.unknowns(N, seed=3)
-    KI, KII = ctx.sif(tree, dev(x), [0, N - 1, 17])
-    rI, rII = oracle.sif(MAT, crack, x, [0, N - 1, 17])
-    assert np.allclose(KI.cpu().numpy(), rI, rtol=1e-13)
-    assert np.allclose(KII.cpu().numpy(), rII, rtol=1e-13)
-
-
 def test_tree_partitions_elements(ctx, rset):
     xy, _ = rset
     tree = ctx.build_tree(dev(xy))
