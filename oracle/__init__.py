@@ -227,14 +227,17 @@ def _restrict(A, N, system):
 
 def solve(A, b, N, system="pressure", Dq=None) -> np.ndarray:
     """Solve the boundary system with a direct LU solve (numpy).  Returns the
-    full 3N vector [Ds, Dn, Dq] (Dq prescribed for the 2N systems)."""
+    full 3N vector [Ds, Dn, Dq] (Dq prescribed for the 2N systems).  b holds
+    row values [sigma_s, sigma_n, p]; the RATE system's second row is
+    sigma_n + p, so its right-hand side is b_n + b_p (b_p is zero for a
+    first step and carries the pressure part of a subtracted history)."""
     if system == "pressure":
         return np.linalg.solve(A, b)
     Asub, Aq = _restrict(A, N, system)
     Dq = np.zeros(N) if Dq is None else np.broadcast_to(np.asarray(Dq, float), (N,))
     bb = b[:2 * N].copy()
     if system == "rate":
-        bb[N:] = b[N:2 * N]
+        bb[N:] = b[N:2 * N] + b[2 * N:]
     bb = bb - Aq @ Dq
     x = np.linalg.solve(Asub, bb)
     return np.concatenate([x, Dq])

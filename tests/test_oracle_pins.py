@@ -400,3 +400,23 @@ def test_two_unknown_systems_satisfy_their_rows(system):
     scale = np.abs(b[:2 * N]).max()
     assert np.abs(y[:N] - b[:N]).max() < 1e-9 * scale
     assert np.abs(row_n - b[N:2 * N]).max() < 1e-9 * scale
+
+
+def test_rate_march_satisfies_rows_with_history():
+    """Two time steps of the RATE system (paper Sec. 4 marching; rows sigma_s
+    and sigma_n + p with the fluid source prescribed): at the second step the
+    solutions satisfy the system's rows of the complete equations, every time
+    element included, i.e. the pressure part of the history term enters the
+    sigma_n + p row."""
+    N = 30
+    xy, _ = crack(N, 0.5, 0.3)
+    times = np.array([0.0, 40.0, 90.0])
+    b = oracle.rhs(xy, sigma_H=3e6, sigma_h=2e6, p0=1e6, system="rate")
+    dq = [np.full(N, 2e-9), np.full(N, 3e-9)]
+    sols = oracle.march(MAT, xy, times, [b, b], system="rate", Dq_steps=dq)
+    A = lambda t: oracle.assemble(MAT, xy, t)
+    y = (A(90.0) - A(50.0)) @ sols[0] + A(50.0) @ sols[1]
+    row_n = y[N:2 * N] + y[2 * N:]
+    scale = np.abs(b[:2 * N]).max()
+    assert np.abs(y[:N] - b[:N]).max() < 1e-9 * scale
+    assert np.abs(row_n - b[N:2 * N]).max() < 1e-9 * scale
