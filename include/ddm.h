@@ -120,6 +120,13 @@ ddm_status ddm_set_wait_limit(ddm_ctx *ctx, int64_t polls);
  * n > 2^30, a null pointer, or an element of zero length or with a
  * non-finite end point. */
 ddm_status ddm_build_tree(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **out);
+/* The same with the tree's own FMM parameters (Chebyshev order, leaf size,
+ * depth cap, near-field rule; fields <= 0 take the context's): every
+ * product, history sum and solve on this tree uses them.  Lets one context
+ * serve problems of different sizes at the order and leaf size that suit
+ * each (see ddm_autotune).  DDM_EINVAL for an odd or out-of-range order. */
+ddm_status ddm_build_tree_params(ddm_ctx *ctx, const double *d_xy, int64_t n, const ddm_fmm_params *prm,
+                                 ddm_tree **out);
 void ddm_tree_destroy(ddm_tree *tree);
 
 typedef struct {
@@ -198,7 +205,10 @@ typedef struct {
  * end points are cut into blocks of <= 64 elements whose own influence
  * matrices are inverted on the device (FP32) once per (dt, system); an
  * element on no chain is a block of its own.
- * d_rhs: 3N doubles (rows not in the system are ignored).  d_x: 3N doubles,
+ * d_rhs: 3N doubles of row values [sigma_s, sigma_n, p]; rows not in the
+ * system are ignored, and for RATE the second system row is
+ * d_rhs[N:2N] + d_rhs[2N:3N] (sigma_n + p: a history term subtracted from
+ * all three rows stays complete).  d_x: 3N doubles,
  * in: initial guess (and the prescribed Dq for 2N systems), out: solution.
  * Precision escalates on stalls: at first every product (Arnoldi steps and
  * the residual recomputed at each restart) uses the requested mode, and
@@ -312,6 +322,21 @@ void ddm_server_destroy(ddm_server *server);
 #define DDM_STATIC_MAX_ELEMENTS 65536
 ddm_status ddm_matvec_dense_static(ddm_ctx *ctx, const double *d_xy, int64_t n, double tau_lo,
                                    double tau_hi, const double *d_x, double *d_y);
+
+/* Autotuner (no counterpart in the paper): for a representative problem of
+ * a size bucket (d_xy: 4N geometry, d_x: a 3N vector, both device; dt the
+ * time step), build a tree for every candidate Chebyshev order (orders,
+ * n_orders; NULL = 4, 6, 8, 10, 12) and leaf size (leaves, n_leaves;
+ * NULL = 16, 32, 64), time its FMM product on the device (CUDA events,
+ * after a warm-up that builds the window caches) and measure its error
+ * against the on-the-fly dense product (max over the output blocks of
+ * max|y - y_dense| / max|y_dense|).  *best receives the fastest candidate
+ * whose error is <= max_rel_err (other fields from the context), with its
+ * time per product and error.  DDM_ENOTCONV when no candidate meets the
+ * bound.  Synchronises the stream; allocates and frees its own trees. */
+ddm_status ddm_autotune(ddm_ctx *ctx, const double *d_xy, int64_t n, const double *d_x, double dt,
+                        const int *orders, int n_orders, const int *leaves, int n_leaves, double max_rel_err,
+                        ddm_fmm_params *best, double *best_ms, double *best_err);
 
 /* Stage timing for profiling (no counterpart in the paper): when enabled,
  * CUDA events bracket each stage on the context stream.  ddm_profile_read

@@ -233,9 +233,9 @@ __global__ void __launch_bounds__(OR_T) k_arnoldi_orth(double *V, int64_t len, i
     double *out = V + (int64_t)nv * len;
     for (int64_t i = i0 + tid; i < i1; i += OR_T) out[i] = w[i] * inv;
 }
-// restrict a 3N product to the system rows (RATE: sigma_n + p)
-// (combine = 1 for products, 0 for a right-hand side, whose rows are already
-// the system's)
+// restrict a 3N product or right-hand side to the system rows (RATE:
+// sigma_n + p when combine = 1; a right-hand side carries the p part of a
+// subtracted history term in its third block)
 __global__ void k_restrict(const double *y, int64_t n, int sys, int combine, double *out) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= n) return;
@@ -260,7 +260,8 @@ inline unsigned nblk(int64_t len, int t = 256) { return (unsigned)((len + t - 1)
 }  // namespace
 
 struct GmresWork {
-    int64_t cap_len = 0;
+    int64_t cap_len = 0;       // system length (nc N) the basis was sized for
+    int64_t cap_n = 0;         // elements the 3N vectors were sized for
     int cap_m = 0;
     cudaStream_t st = nullptr;
     double *V = nullptr, *w = nullptr, *full = nullptr, *y3 = nullptr, *b = nullptr;
@@ -339,6 +340,23 @@ ddm_status ddm_create(ddm_ctx **out, const ddm_material *mat, const ddm_fmm_para
                 T[q * n * n + a * n + ap] = (float)cheb_S(n, xi[a], 0.5 * (xi[ap] + (q ? 1.0 : -1.0)));
     if (cudaMalloc(&c->cheb_T, T.size() * sizeof(float)) != cudaSuccess) { delete c; return DDM_ENOMEM; }
     cudaMemcpy(c->cheb_T, T.data(), T.size() * sizeof(float), cudaMemcpyHostToDevice);
+    // the same transfer matrices for every even order (trees may carry their own order)
+    for (int nn = 2; nn <= DDM_MAX_CHEB; nn += 2) {
+        std::vector<double> xn(nn);
+        for (int j = 0; j < nn; ++j) xn[j] = cos((2 * j + 1) * M_PI / (2.0 * nn));
+        std::vector<float> Tn(2 * nn * nn);
+        for (int q = 0; q < 2; ++q)
+            for (int a = 0; a < nn; ++a)
+                for (int ap = 0; ap < nn; ++ap)
+                    Tn[q * nn * nn + a * nn + ap] = (float)cheb_S(nn, xn[a], 0.5 * (xn[ap] + (q ? 1.0 : -1.0)));
+        if (cudaMalloc(&c->cheb_Tn[nn / 2 - 1], Tn.size() * sizeof(float)) != cudaSuccess) {
+            for (float *p : c->cheb_Tn) if (p) cudaFree(p);
+            cudaFree(c->cheb_T);
+            delete c;
+            return DDM_ENOMEM;
+        }
+        cudaMemcpy(c->cheb_Tn[nn / 2 - 1], Tn.data(), Tn.size() * sizeof(float), cudaMemcpyHostToDevice);
+    }
     if (cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess || cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess) {
         cudaFree(c->cheb_T);
         delete c;
@@ -364,6 +382,8 @@ ddm_status ddm_create(ddm_ctx **out, const ddm_material *mat, const ddm_fmm_para
 void ddm_destroy(ddm_ctx *ctx) {
     if (!ctx) return;
     if (ctx->cheb_T) cudaFree(ctx->cheb_T);
+    for (float *p : ctx->cheb_Tn)
+        if (p) cudaFree(p);
     if (ctx->d_err) cudaFree(ctx->d_err);
     if (ctx->aux) cudaStreamDestroy(ctx->aux);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
@@ -414,7 +434,20 @@ ddm_status ddm_profile_read(ddm_ctx *ctx, double *ms, int64_t *launches) {
 
 ddm_status ddm_build_tree(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **out) {
     if (!ctx) return DDM_EINVAL;
-    return tree_build(ctx, d_xy, n, out);
+    return tree_build(ctx, d_xy, n, ctx->prm, out);
+}
+
+ddm_status ddm_build_tree_params(ddm_ctx *ctx, const double *d_xy, int64_t n, const ddm_fmm_params *prm,
+                                 ddm_tree **out) {
+    if (!ctx) return DDM_EINVAL;
+    if (!prm) return tree_build(ctx, d_xy, n, ctx->prm, out);
+    ddm_fmm_params p = *prm;
+    if (p.n_cheb <= 0) p.n_cheb = ctx->prm.n_cheb;
+    if (p.leaf_size <= 0) p.leaf_size = ctx->prm.leaf_size;
+    if (p.quad_near <= 0) p.quad_near = ctx->prm.quad_near;
+    if (p.n_cheb < 2 || p.n_cheb > DDM_MAX_CHEB || (p.n_cheb & 1) || p.quad_near > 16 || p.max_depth < 0)
+        return ctx_fail(ctx, DDM_EINVAL, "ddm_build_tree_params: bad FMM parameters");
+    return tree_build(ctx, d_xy, n, p, out);
 }
 
 void ddm_tree_destroy(ddm_tree *tree) { tree_free(tree); }
@@ -492,7 +525,7 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
     int m = P.restart;
     GmresWork &g = *ctx->gm;
     ddm_status st0;
-    if (g.cap_len < len || g.cap_m < m) {
+    if (g.cap_len < len || g.cap_n < N || g.cap_m < m) {
         g.release();
         size_t v3 = 3 * N * sizeof(double);
         g.st = s;
@@ -509,7 +542,7 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
                   cudaEventCreateWithFlags(&g.ev[0], cudaEventDisableTiming) == cudaSuccess &&
                   cudaEventCreateWithFlags(&g.ev[1], cudaEventDisableTiming) == cudaSuccess;
         if (!ok) { g.release(); return ctx_fail(ctx, DDM_ENOMEM, "GMRES workspace allocation failed"); }
-        g.cap_len = len; g.cap_m = m;
+        g.cap_len = len; g.cap_n = N; g.cap_m = m;
     }
     if ((st0 = lsq_alloc(ctx, g.lsq, 1, m, s))) return st0;
     int mode = P.mode & ~DDM_MODE_PRECISE, sys = P.system;
@@ -550,7 +583,7 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
     // preconditioner: inverted chain blocks of this (dt, system)
     if ((st = pb_prepare(ctx, t, dt, sys, s))) return st;
     // b = restrict(rhs) - restrict(A [0; 0; Dq]) for the 2N systems
-    k_restrict<<<nblk(N), 256, 0, s>>>(d_rhs, N, sys, 0, g.b);
+    k_restrict<<<nblk(N), 256, 0, s>>>(d_rhs, N, sys, 1, g.b);   // RATE: sigma_n + p rows of the RHS
     if (sys != DDM_SYS_PRESSURE) {
         DDM_CUDA_TRY(ctx, cudaMemsetAsync(g.full, 0, 2 * N * sizeof(double), s));
         DDM_CUDA_TRY(ctx, cudaMemcpyAsync(g.full + 2 * N, d_x + 2 * N, N * sizeof(double), cudaMemcpyDeviceToDevice, s));

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <vector>
 
 #include "internal.h"
@@ -103,7 +104,49 @@ __global__ void k_restrict_b(const double *y, int64_t n, int sys, int combine, d
 }
 inline unsigned nb(int64_t n) { return (unsigned)((n + BT - 1) / BT); }
 
+// element-wise arena kernels of many problems in one launch: items
+// (p, 0, a, b) cover elements [a, b) of problem p
+struct SegD {
+    const double *src;
+    double *dst;
+    int64_t n;
+};
+constexpr int SEG_EL = 1024;
+__global__ void k_restrict_bb(const SegD *D, const int4 *items, int nitems, int sys) {
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int4 w = items[it];
+        const SegD &d = D[w.x];
+        for (int64_t e = w.z + threadIdx.x; e < w.w; e += BT) {
+            d.dst[e] = d.src[e];
+            d.dst[d.n + e] = d.src[d.n + e] + (sys == DDM_SYS_RATE ? d.src[2 * d.n + e] : 0.0);
+            if (sys == DDM_SYS_PRESSURE) d.dst[2 * d.n + e] = d.src[2 * d.n + e];
+        }
+    }
+}
+__global__ void k_copy3_bb(const SegD *D, const int4 *items, int nitems, int nc) {
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int4 w = items[it];
+        const SegD &d = D[w.x];
+        for (int64_t e = w.z + threadIdx.x; e < w.w; e += BT)
+            for (int r = 0; r < 3; ++r) d.dst[r * d.n + e] = r < nc ? d.src[r * d.n + e] : 0.0;
+    }
+}
+
 }  // namespace
+
+// arena segments of many problems (device descriptors and element items)
+struct SegBatch {
+    SegD *desc = nullptr;
+    int4 *items = nullptr;
+    int n = 0;
+    void release(cudaStream_t s) {
+        dfree(desc, s);
+        dfree(items, s);
+        desc = nullptr;
+        items = nullptr;
+        n = 0;
+    }
+};
 
 struct ddm_batch {
     int P = 0;
@@ -134,6 +177,21 @@ struct ddm_batch {
     cudaStream_t cap = nullptr;
     cudaStream_t ast = nullptr;            // stream of the arena allocations
     cudaEvent_t ev_fork[NSTREAMS] = {}, ev_join[NSTREAMS] = {};
+    // work lists of the one-launch-per-stage graphs (product, Arnoldi
+    // operator, residual): FMM products grouped by order, preconditioner,
+    // arena copies and restrictions
+    std::vector<BatchFmm *> bf[3];          // 0 product, 1 Arnoldi operator, 2 residual
+    BatchPb *bp = nullptr;                  // preconditioner of the Arnoldi operator
+    SegBatch seg[4];                        // 1 operator restriction, 2 residual copy, 3 residual restriction
+    void free_lists(int k) {
+        for (BatchFmm *f : bf[k]) bfmm_free(f, ast);
+        bf[k].clear();
+        if (k == 1) {
+            seg[1].release(ast);
+            if (bp) { bpb_free(bp, ast); bp = nullptr; }
+        }
+        if (k == 2) { seg[2].release(ast); seg[3].release(ast); }
+    }
     void free_solver() {
         void *ps[] = {prob, blk, V, w, vin, b, tmp, Minv, h, hcol, nrm, coef};
         for (void *p : ps) dfree(p, ast);
@@ -146,6 +204,7 @@ struct ddm_batch {
         if (g_prod) cudaGraphExecDestroy(g_prod);
         if (g_res) cudaGraphExecDestroy(g_res);
         g_op = g_prod = g_res = nullptr;
+        for (int k = 0; k < 3; ++k) free_lists(k);
     }
 };
 
@@ -196,6 +255,76 @@ ddm_status warm(ddm_ctx *ctx, ddm_batch *B, double dt, int mode) {
     }
     return DDM_OK;
 }
+
+ddm_status seg_build(ddm_ctx *ctx, ddm_batch *B, const std::vector<int> &idx, const double *src, const int64_t *soff,
+                     double *dst, const int64_t *doff, SegBatch &out) {
+    std::vector<SegD> hd(B->P);
+    std::vector<int4> hi;
+    for (int p = 0; p < B->P; ++p) hd[p] = SegD{src + soff[p], dst + doff[p], B->N[p]};
+    for (int p : idx)
+        for (int64_t a = 0; a < B->N[p]; a += SEG_EL)
+            hi.push_back(make_int4(p, 0, (int)a, (int)std::min<int64_t>(B->N[p], a + SEG_EL)));
+    out.release(B->ast);
+    cudaStream_t s = B->ast;
+    bool ok = dalloc(&out.desc, hd.size() * sizeof(SegD), s) == cudaSuccess &&
+              dalloc(&out.items, std::max<size_t>(1, hi.size()) * sizeof(int4), s) == cudaSuccess &&
+              cudaMemcpyAsync(out.desc, hd.data(), hd.size() * sizeof(SegD), cudaMemcpyHostToDevice, s) == cudaSuccess &&
+              (hi.empty() || cudaMemcpyAsync(out.items, hi.data(), hi.size() * sizeof(int4), cudaMemcpyHostToDevice, s) ==
+                                 cudaSuccess) &&
+              cudaStreamSynchronize(s) == cudaSuccess;
+    if (!ok) return ctx_fail(ctx, DDM_ENOMEM, "batch: arena work list allocation failed");
+    out.n = (int)hi.size();
+    return DDM_OK;
+}
+
+// products y_p = [K(dt)] x_p of the problems in idx whose mode is plain FMM,
+// grouped by Chebyshev order: one work-list set per order
+ddm_status fmm_groups(ddm_ctx *ctx, ddm_batch *B, const std::vector<int> &idx, double dt, const double *x,
+                      const int64_t *xoff, double *y, std::vector<BatchFmm *> &out) {
+    std::map<int, std::vector<int>> by_n;
+    for (int p : idx) by_n[B->trees[p]->prm.n_cheb].push_back(p);
+    for (auto &g : by_n) {
+        std::vector<ddm_tree *> tr;
+        std::vector<const double *> xs;
+        std::vector<double *> ys;
+        for (int p : g.second) {
+            tr.push_back(B->trees[p]);
+            xs.push_back(x + xoff[p]);
+            ys.push_back(y + B->off3[p]);
+        }
+        BatchFmm *f = nullptr;
+        ddm_status st = bfmm_build(ctx, tr.data(), (int)tr.size(), 0.0, dt, xs.data(), ys.data(), B->ast, &f);
+        if (st) return st;
+        out.push_back(f);
+    }
+    return DDM_OK;
+}
+
+// capture body() on the batch's capture stream into one graph (the FMM far
+// branch may fork to B->fork[0])
+template <class Fn>
+ddm_status capture_seq(ddm_ctx *ctx, ddm_batch *B, cudaGraphExec_t *out, long long *kernels, Fn body) {
+    cudaStream_t s = B->cap;
+    DDM_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    if (*out) { cudaGraphExecDestroy(*out); *out = nullptr; }
+    long long before[DDM_NSTAGES];
+    for (int k = 0; k < DDM_NSTAGES; ++k) before[k] = ctx->prof.launches[k];
+    cudaGraph_t g;
+    DDM_CUDA_TRY(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    ddm_status st = body(s);
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    long long kern = 0;
+    for (int k = 0; k < DDM_NSTAGES; ++k) { kern += ctx->prof.launches[k] - before[k]; ctx->prof.launches[k] = before[k]; }
+    *kernels = kern;
+    if (st) { if (e == cudaSuccess) cudaGraphDestroy(g); return st; }
+    if (e != cudaSuccess) return ctx_fail(ctx, DDM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return ctx_fail(ctx, DDM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    return DDM_OK;
+}
+
+inline unsigned seg_grid(int n) { return (unsigned)std::max(1, std::min(n, 152 * 8)); }
 
 }  // namespace
 
@@ -249,15 +378,29 @@ ddm_status ddm_batch_matvec(ddm_ctx *ctx, ddm_batch *B, double dt, const double 
     ddm_status st = upload_tables(ctx);
     if (st) return st;
     if (!B->g_prod || B->g_prod_dt != dt || B->g_prod_mode != mode || B->g_prod_x != d_x || B->g_prod_y != d_y) {
-        if ((st = warm(ctx, B, dt, mode))) return st;
-        DDM_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
         int saved = ctx->prof.on;
         ctx->prof.on = 0;
         std::vector<int> all(B->P);
         for (int p = 0; p < B->P; ++p) all[p] = p;
-        st = capture(ctx, B, &B->g_prod, &B->k_prod, all, [&](int p, cudaStream_t s) {
-            return op_apply(ctx, B->trees[p], 0.0, dt, d_x + B->off3[p], d_y + B->off3[p], mode, 0, 1.0, s);
-        });
+        if (mode == DDM_MODE_FMM) {
+            // one launch per stage over every problem (work lists by order)
+            B->free_lists(0);
+            st = fmm_groups(ctx, B, all, dt, d_x, B->off3.data(), d_y, B->bf[0]);
+            if (!st)
+                st = capture_seq(ctx, B, &B->g_prod, &B->k_prod, [&](cudaStream_t cs) -> ddm_status {
+                    for (BatchFmm *f : B->bf[0]) {
+                        ddm_status e = bfmm_launch(ctx, f, cs, B->fork[0]);
+                        if (e) return e;
+                    }
+                    return DDM_OK;
+                });
+        } else {
+            if ((st = warm(ctx, B, dt, mode))) { ctx->prof.on = saved; return st; }
+            DDM_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+            st = capture(ctx, B, &B->g_prod, &B->k_prod, all, [&](int p, cudaStream_t s) {
+                return op_apply(ctx, B->trees[p], 0.0, dt, d_x + B->off3[p], d_y + B->off3[p], mode, 0, 1.0, s);
+            });
+        }
         ctx->prof.on = saved;
         if (st) return st;
         B->g_prod_dt = dt; B->g_prod_mode = mode; B->g_prod_x = d_x; B->g_prod_y = d_y;
@@ -331,7 +474,72 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
     // per problem precision level, as in ddm_gmres_solve: 0 requested
     // products throughout, 1 precise residuals, 2 precise inner products too
     std::vector<int> level(P, 0);
+    // Plain-FMM solves: every stage of all problems' operator (preconditioner,
+    // product, restriction) is one launch over a work list, captured into one
+    // graph; problems whose precision escalated take their own products.
+    const bool batched = mode == DDM_MODE_FMM;
+    auto capture_op_b = [&](const std::vector<int> &idx) -> ddm_status {
+        B->free_lists(1);
+        std::vector<int> plain, prec;
+        std::vector<ddm_tree *> tr;
+        std::vector<const double *> vs;
+        std::vector<double *> zs;
+        for (int p : idx) {
+            (level[p] >= 2 ? prec : plain).push_back(p);
+            tr.push_back(B->trees[p]);
+            vs.push_back(B->vin + B->offs[p]);
+            zs.push_back(B->full + B->off3[p]);
+        }
+        ddm_status e = bpb_build(ctx, tr.data(), (int)tr.size(), sys, vs.data(), zs.data(), B->ast, &B->bp);
+        if (!e) e = fmm_groups(ctx, B, plain, dt, B->full, B->off3.data(), B->y3, B->bf[1]);
+        if (!e) e = seg_build(ctx, B, idx, B->y3, B->off3.data(), B->w, B->offs.data(), B->seg[1]);
+        if (e) return e;
+        for (int p : prec)         // caches of the precise products, outside the capture
+            if ((e = op_apply(ctx, B->trees[p], 0.0, dt, B->full + B->off3[p], B->y3 + B->off3[p],
+                              mode | DDM_MODE_PRECISE, 0, 1.0)))
+                return e;
+        return capture_seq(ctx, B, &B->g_op, &B->k_op, [&](cudaStream_t cs) -> ddm_status {
+            ddm_status r = bpb_launch(ctx, B->bp, cs);
+            for (BatchFmm *f : B->bf[1])
+                if (!r) r = bfmm_launch(ctx, f, cs, B->fork[0]);
+            for (int p : prec)
+                if (!r) r = op_apply(ctx, B->trees[p], 0.0, dt, B->full + B->off3[p], B->y3 + B->off3[p],
+                                     mode | DDM_MODE_PRECISE, 0, 1.0, cs);
+            if (r) return r;
+            k_restrict_bb<<<seg_grid(B->seg[1].n), BT, 0, cs>>>(B->seg[1].desc, B->seg[1].items, B->seg[1].n, sys);
+            prof_end(ctx, 8, 1);
+            return DDM_OK;
+        });
+    };
+    auto capture_res_b = [&](const std::vector<int> &idx) -> ddm_status {
+        B->free_lists(2);
+        std::vector<int> plain, other;
+        for (int p : idx) (residual_mode(mode, level[p], B->N[p]) == DDM_MODE_FMM ? plain : other).push_back(p);
+        ddm_status e = fmm_groups(ctx, B, plain, dt, B->full, B->off3.data(), B->y3, B->bf[2]);
+        if (!e) e = seg_build(ctx, B, idx, d_x, B->off3.data(), B->full, B->off3.data(), B->seg[2]);
+        if (!e) e = seg_build(ctx, B, idx, B->y3, B->off3.data(), B->tmp, B->offs.data(), B->seg[3]);
+        if (e) return e;
+        for (int p : other)
+            if ((e = op_apply(ctx, B->trees[p], 0.0, dt, B->full + B->off3[p], B->y3 + B->off3[p],
+                              residual_mode(mode, level[p], B->N[p]), 0, 1.0)))
+                return e;
+        return capture_seq(ctx, B, &B->g_res, &B->k_res, [&](cudaStream_t cs) -> ddm_status {
+            k_copy3_bb<<<seg_grid(B->seg[2].n), BT, 0, cs>>>(B->seg[2].desc, B->seg[2].items, B->seg[2].n, nc);
+            prof_end(ctx, 8, 1);
+            ddm_status r = DDM_OK;
+            for (BatchFmm *f : B->bf[2])
+                if (!r) r = bfmm_launch(ctx, f, cs, B->fork[0]);
+            for (int p : other)
+                if (!r) r = op_apply(ctx, B->trees[p], 0.0, dt, B->full + B->off3[p], B->y3 + B->off3[p],
+                                     residual_mode(mode, level[p], B->N[p]), 0, 1.0, cs);
+            if (r) return r;
+            k_restrict_bb<<<seg_grid(B->seg[3].n), BT, 0, cs>>>(B->seg[3].desc, B->seg[3].items, B->seg[3].n, sys);
+            prof_end(ctx, 8, 1);
+            return DDM_OK;
+        });
+    };
     auto capture_op = [&](const std::vector<int> &idx) -> ddm_status {
+        if (batched) return capture_op_b(idx);
         return capture(ctx, B, &B->g_op, &B->k_op, idx, [&](int p, cudaStream_t ps) -> ddm_status {
             int64_t n = B->N[p];
             ddm_status e = pb_apply(ctx, B->trees[p], sys, B->vin + B->offs[p], B->full + B->off3[p], ps);
@@ -344,6 +552,7 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
         });
     };
     auto capture_res = [&](const std::vector<int> &idx) -> ddm_status {
+        if (batched) return capture_res_b(idx);
         return capture(ctx, B, &B->g_res, &B->k_res, idx, [&](int p, cudaStream_t ps) -> ddm_status {
             int64_t n = B->N[p];
             k_copy_to3<<<nb(n), BT, 0, ps>>>(d_x + B->off3[p], n, nc, B->full + B->off3[p]);
@@ -356,7 +565,10 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
     };
     std::vector<int> every(P);
     for (int p = 0; p < P; ++p) every[p] = p;
-    if ((st = warm(ctx, B, dt, mode)) || (st = warm(ctx, B, dt, mode | DDM_MODE_PRECISE))) { ctx->prof.on = saved; return st; }
+    if (!batched && ((st = warm(ctx, B, dt, mode)) || (st = warm(ctx, B, dt, mode | DDM_MODE_PRECISE)))) {
+        ctx->prof.on = saved;
+        return st;
+    }
     DDM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     if ((st = capture_op(every)) || (st = capture_res(every))) { ctx->prof.on = saved; return st; }
     B->op_set = every;
@@ -364,7 +576,7 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
     // b = restrict(rhs) (- restrict(A [0; 0; Dq]) for the 2N systems)
     for (int p = 0; p < P; ++p) {
         int64_t n = B->N[p];
-        k_restrict_b<<<nb(n), BT, 0, s>>>(d_rhs + B->off3[p], n, sys, 0, B->b + B->offs[p]);
+        k_restrict_b<<<nb(n), BT, 0, s>>>(d_rhs + B->off3[p], n, sys, 1, B->b + B->offs[p]);
         if (sys != DDM_SYS_PRESSURE) {
             DDM_CUDA_TRY(ctx, cudaMemsetAsync(B->full + B->off3[p], 0, 2 * n * sizeof(double), s));
             DDM_CUDA_TRY(ctx, cudaMemcpyAsync(B->full + B->off3[p] + 2 * n, d_x + B->off3[p] + 2 * n, n * sizeof(double),

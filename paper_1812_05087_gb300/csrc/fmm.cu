@@ -156,10 +156,10 @@ struct UpSmem {
 // P2M: lane owns node entries (a, b) = lane + 32 j and all 4 components;
 // the UP_W warps take every UP_W-th point and are summed at the end.
 template <int N>
-__global__ void __launch_bounds__(UP_T) k_up(const int32_t *cstart, const int32_t *cend, int64_t loff, int L,
-                                             const int32_t *cix, const int32_t *ciy, const int32_t *parent,
-                                             const float4 *grel, const float4 *frame, const float4 *chg, float hL,
-                                             float *W, float *Fz) {
+__device__ __forceinline__ void up_body(const int32_t *cstart, const int32_t *cend, int64_t loff, int L,
+                                        const int32_t *cix, const int32_t *ciy, const int32_t *parent,
+                                        const float4 *grel, const float4 *frame, const float4 *chg, float hL, float *W,
+                                        float *Fz, int64_t bid) {
     using S = UpSmem<N>;
     constexpr int N2 = S::N2, NOUT = S::NOUT, SXS = S::SXS, NE = (N2 + 31) / 32, KO = (NOUT + UP_T - 1) / UP_T;
     __shared__ __align__(16) float sm[S::SIZE];
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(UP_T) k_up(const int32_t *cstart, const int32_
     float *sx = sm, *sy = sm + N * SXS;
     float4 *wd = reinterpret_cast<float4 *>(sm + 2 * N * SXS);   // 16-byte aligned: 2 N SXS is a multiple of 4
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t leaf = loff + blockIdx.x;
+    const int64_t leaf = loff + bid;
     const int s0 = cstart[leaf], s1 = cend[leaf];
     constexpr int nq = N;                     // Gauss points per element
     float acc[NE][4];
@@ -302,6 +302,13 @@ __global__ void __launch_bounds__(UP_T) k_up(const int32_t *cstart, const int32_
     }
 
 }
+template <int N>
+__global__ void __launch_bounds__(UP_T) k_up(const int32_t *cstart, const int32_t *cend, int64_t loff, int L,
+                                             const int32_t *cix, const int32_t *ciy, const int32_t *parent,
+                                             const float4 *grel, const float4 *frame, const float4 *chg, float hL,
+                                             float *W, float *Fz) {
+    up_body<N>(cstart, cend, loff, L, cix, ciy, parent, grel, frame, chg, hL, W, Fz, blockIdx.x);
+}
 
 // ----------------------------------------------------- downward pass (fused)
 // One block per leaf: f = g at the level-2 ancestor, then down the chain
@@ -310,16 +317,16 @@ __global__ void __launch_bounds__(UP_T) k_up(const int32_t *cstart, const int32_
 // ancestors' values are only read, so leaves sharing them need no order.
 constexpr int L2L_T = 128;
 template <int N>
-__global__ void __launch_bounds__(L2L_T) k_down(int64_t loff, int L, const int32_t *cix, const int32_t *ciy,
-                                                const int32_t *parent, const float *T, const float *F,
-                                                const int32_t *cstart, const int32_t *cend, const float4 *grel,
-                                                float wL, float4 *far4) {
+__device__ __forceinline__ void down_body(int64_t loff, int L, const int32_t *cix, const int32_t *ciy,
+                                          const int32_t *parent, const float *T, const float *F,
+                                          const int32_t *cstart, const int32_t *cend, const float4 *grel, float wL,
+                                          float4 *far4, int64_t bid) {
     constexpr int N2 = N * N, NOUT = 4 * N2, KO = (NOUT + L2L_T - 1) / L2L_T;
     __shared__ float sT[2 * N2], sf[NOUT], tmp[NOUT];
     __shared__ int64_t anc[DDM_MAX_LEVELS + 1];
     __shared__ int squad[DDM_MAX_LEVELS + 1];
     const int tid = threadIdx.x;
-    const int64_t leaf = loff + blockIdx.x;
+    const int64_t leaf = loff + bid;
     if (tid == 0) {
         int64_t c = leaf;
         for (int l = L; l >= 2; --l) {
@@ -406,6 +413,13 @@ __global__ void __launch_bounds__(L2L_T) k_down(int64_t loff, int L, const int32
         }
         far4[ti] = make_float4(g4[0], g4[1], g4[2], g4[3]);
     }
+}
+template <int N>
+__global__ void __launch_bounds__(L2L_T) k_down(int64_t loff, int L, const int32_t *cix, const int32_t *ciy,
+                                                const int32_t *parent, const float *T, const float *F,
+                                                const int32_t *cstart, const int32_t *cend, const float4 *grel,
+                                                float wL, float4 *far4) {
+    down_body<N>(loff, L, cix, ciy, parent, T, F, cstart, cend, grel, wL, far4, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------- M2L
@@ -552,9 +566,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
 }
 }  // namespace tc
 
-__global__ void __launch_bounds__(tc::THREADS) k_m2l_tc(const int2 *work, const int32_t *koff, const int2 *pairs,
-                                                        int n, const float *ops, const float *W, float *F,
-                                                        int *err) {
+__device__ __forceinline__ void m2l_body(const int2 *work, const int32_t *koff, const int2 *pairs, int n,
+                                         const float *ops, const float *W, float *F, int *err, int64_t wi) {
     using namespace tc;
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t bar[NSTAGE];
@@ -565,7 +578,7 @@ __global__ void __launch_bounds__(tc::THREADS) k_m2l_tc(const int2 *work, const 
     const uint32_t raw = smem_u32(smem_raw);
     uint8_t *base = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int2 wk = work[blockIdx.x];
+    const int2 wk = work[wi];
     const int key = wk.x, p0 = wk.y, p1 = min(koff[key + 1], p0 + BN);
     const int n2 = n * n, ld = 4 * n2;
     const int r0 = blockIdx.y * BM;
@@ -669,6 +682,11 @@ __global__ void __launch_bounds__(tc::THREADS) k_m2l_tc(const int2 *work, const 
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
     if (tid == 0 && *verr) atomicExch(err, 1);
+}
+__global__ void __launch_bounds__(tc::THREADS) k_m2l_tc(const int2 *work, const int32_t *koff, const int2 *pairs,
+                                                        int n, const float *ops, const float *W, float *F,
+                                                        int *err) {
+    m2l_body(work, koff, pairs, n, ops, W, F, err, blockIdx.x);
 }
 
 // ----------------------------------------------------------- leaf L2P + P2P
@@ -1026,18 +1044,16 @@ __global__ void __launch_bounds__(NEAR_T, 4) k_near(KConst<float> k, KConst<doub
 // of dependent loads.  Close pairs are queued per (source, target) and
 // evaluated afterwards as units, as in k_near.  L2P runs separately
 // (k_l2p).
-__global__ void __launch_bounds__(NEAR_T, 4) k_near2(KConst<float> k, Win<float> w, const int32_t *nboff,
-                                                     const int4 *nbtab, const int32_t *elem_leaf, const float4 *grel,
-                                                     const float4 *frame, const float4 *chg, const int64_t *perm,
-                                                     float wL, int nq, const int2 *items, int64_t n_items, int64_t N,
-                                                     double scale, double *y) {
+__device__ __forceinline__ void near2_body(const KConst<float> &k, const Win<float> &w, const int32_t *nboff,
+                                           const int4 *nbtab, const int32_t *elem_leaf, const float4 *grel,
+                                           const float4 *frame, const float4 *chg, const int64_t *perm, float wL,
+                                           int nq, const int2 *items, int64_t N, double scale, double *y,
+                                           int64_t item) {
     constexpr unsigned FULL = 0xFFFFFFFFu;
     __shared__ int sst[NEAR_W][9], spre[NEAR_W][10];
     __shared__ float sox[NEAR_W][9], soy[NEAR_W][9];
     __shared__ int2 sq[NEAR_W][NEAR_Q];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t item = (int64_t)blockIdx.x * NEAR_W + wid;
-    if (item >= n_items) return;              // whole warp leaves together
     const int2 it = items[item];
     const int t0 = it.x, t1 = it.y >= 0 ? it.y : it.x;
     const bool two = it.y >= 0;
@@ -1191,6 +1207,15 @@ __global__ void __launch_bounds__(NEAR_T, 4) k_near2(KConst<float> k, Win<float>
         vl = cxx * hl[b0][1] + cyy * hl[b0 + 1][1] + cxy * hl[b0 + 2][1];
     }
     y[row * N + eout] = yold + scale * ((double)vh + (double)vl);
+}
+__global__ void __launch_bounds__(NEAR_T, 4) k_near2(KConst<float> k, Win<float> w, const int32_t *nboff,
+                                                     const int4 *nbtab, const int32_t *elem_leaf, const float4 *grel,
+                                                     const float4 *frame, const float4 *chg, const int64_t *perm,
+                                                     float wL, int nq, const int2 *items, int64_t n_items, int64_t N,
+                                                     double scale, double *y) {
+    const int64_t item = (int64_t)blockIdx.x * NEAR_W + (threadIdx.x >> 5);
+    if (item >= n_items) return;              // whole warp leaves together
+    near2_body(k, w, nboff, nbtab, elem_leaf, grel, frame, chg, perm, wL, nq, items, N, scale, y, item);
 }
 
 // far field at the targets (from k_down) rotated to each target frame and
@@ -1399,7 +1424,7 @@ ddm_status upload_tables(ddm_ctx *ctx) {
 }
 
 ddm_status ensure_workspace(ddm_ctx *ctx, ddm_tree *t) {
-    int n = ctx->prm.n_cheb;
+    int n = t->prm.n_cheb;
     if (t->ncheb_alloc == n && t->W) return DDM_OK;
     dfree(t->W, t->stream);
     dfree(t->Fl, t->stream);
@@ -1453,6 +1478,46 @@ ddm_status window_self_blocks(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, c
     return DDM_OK;
 }
 
+// M2L operator set of window (lo, hi) for tree t from the tree's LRU cache,
+// built on stream s when missing (one (4n^2)^2 matrix per (level, offset))
+ddm_status window_ops(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, cudaStream_t s, const float **out) {
+    const int n = t->prm.n_cheb, n2 = n * n, L = t->depth;
+    const int nk = t->n_keys;
+    const size_t opsz = (size_t)nk * 16 * n2 * n2;
+    const unsigned long long now = t->win_clock;
+    if (t->ops_n != n) {                       // new order: drop the cached sets
+        for (int k = 0; k < ddm_tree::WIN_CACHE; ++k) {
+            dfree(t->ops_set[k], t->stream);
+            t->ops_set[k] = nullptr;
+        }
+        t->ops_n = n;
+        // up to 4 GB of operator sets (at least one)
+        t->ops_cap = (int)std::max<size_t>(1, std::min<size_t>(ddm_tree::WIN_CACHE, ((size_t)4 << 30) /
+                                                               std::max<size_t>(1, opsz * sizeof(float))));
+    }
+    int os = -1;
+    for (int k = 0; k < t->ops_cap; ++k)
+        if (t->ops_set[k] && t->ops_lo[k] == lo && t->ops_hi[k] == hi) os = k;
+    if (os >= 0) t->ops_use[os] = now;
+    if (os < 0) {
+        os = 0;
+        for (int k = 0; k < t->ops_cap; ++k) {
+            if (!t->ops_set[k]) { os = k; break; }
+            if (t->ops_use[k] < t->ops_use[os]) os = k;
+        }
+        t->ops_use[os] = now;
+        if (!t->ops_set[os]) DDM_CUDA_TRY(ctx, dalloc(&t->ops_set[os], opsz * sizeof(float), t->stream));
+        prof_begin(ctx, 3);
+        dim3 g((unsigned)((n2 * n2 + 127) / 128), (unsigned)nk);
+        k_m2l_ops<<<g, 128, 0, s>>>(ctx->kf, make_win<float>(ctx, lo, hi), L, t->h0, n, t->mk_off, t->ops_set[os]);
+        t->ops_lo[os] = lo;
+        t->ops_hi[os] = hi;
+        prof_end(ctx, 3, 1);
+    }
+    *out = t->ops_set[os];
+    return DDM_OK;
+}
+
 ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const double *x, double *y, int mode,
                     int accumulate, double scale, cudaStream_t stream_override) {
     const bool precise = (mode & DDM_MODE_PRECISE) != 0;
@@ -1464,7 +1529,8 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
     if (st) return st;
     cudaStream_t s = stream_override ? stream_override : ctx->stream;
     int64_t N = t->n;
-    int n = ctx->prm.n_cheb, n2 = n * n;
+    int n = t->prm.n_cheb, n2 = n * n;
+    const int nq = t->prm.quad_near;
     const int TB = 256;
     KConst<float> kf = ctx->kf;
     Win<float> wf = make_win<float>(ctx, lo, hi);
@@ -1473,7 +1539,6 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
     const double *blk = nullptr;
     st = window_self_blocks(ctx, t, lo, hi, s, &blk);
     if (st) return st;
-    const unsigned long long now = t->win_clock;
     const int overwrite = accumulate ? 0 : 1;
     int L = t->depth;
     int64_t loff = t->lvl_off[L], nleaf = t->lvl_off[L + 1] - loff;
@@ -1508,7 +1573,7 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
         chunks = (N + chunk - 1) / chunk;
         prof_begin(ctx, 7);
         auto kdn = k_dense<false>;          // precise dense products take k_dense_exact above
-        kdn<<<dim3((unsigned)tiles, (unsigned)chunks), DN_T, 0, s>>>(kf, ctx->kd, wf, wd, ctx->prm.quad_near, loff, t->elem_leaf, t->cell_ix, t->cell_iy,
+        kdn<<<dim3((unsigned)tiles, (unsigned)chunks), DN_T, 0, s>>>(kf, ctx->kd, wf, wd, nq, loff, t->elem_leaf, t->cell_ix, t->cell_iy,
                                                                         t->g_rel, t->g_frame, t->chg, t->perm, wL, N,
                                                                         chunk, scale, y);
         prof_end(ctx, 7, 1);
@@ -1536,38 +1601,8 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
 #undef DDM_UP
         prof_end(ctx, 2, 1);
         // M2L on every level >= 2: operators of this window, then one GEMM launch
-        int nk = t->n_keys;
-        size_t opsz = (size_t)nk * 16 * n2 * n2;
-        if (t->ops_n != n) {                       // new order: drop the cached sets
-            for (int k = 0; k < ddm_tree::WIN_CACHE; ++k) {
-                dfree(t->ops_set[k], t->stream);
-                t->ops_set[k] = nullptr;
-            }
-            t->ops_n = n;
-            // up to 4 GB of operator sets (at least one)
-            t->ops_cap = (int)std::max<size_t>(1, std::min<size_t>(ddm_tree::WIN_CACHE, ((size_t)4 << 30) /
-                                                                   std::max<size_t>(1, opsz * sizeof(float))));
-        }
-        int os = -1;
-        for (int k = 0; k < t->ops_cap; ++k)
-            if (t->ops_set[k] && t->ops_lo[k] == lo && t->ops_hi[k] == hi) os = k;
-        if (os >= 0) t->ops_use[os] = now;
-        if (os < 0) {
-            os = 0;
-            for (int k = 0; k < t->ops_cap; ++k) {
-                if (!t->ops_set[k]) { os = k; break; }
-                if (t->ops_use[k] < t->ops_use[os]) os = k;
-            }
-            t->ops_use[os] = now;
-            if (!t->ops_set[os]) DDM_CUDA_TRY(ctx, dalloc(&t->ops_set[os], opsz * sizeof(float), t->stream));
-            prof_begin(ctx, 3);
-            dim3 g((unsigned)((n2 * n2 + 127) / 128), (unsigned)nk);
-            k_m2l_ops<<<g, 128, 0, fs>>>(kf, wf, L, t->h0, n, t->mk_off, t->ops_set[os]);
-            t->ops_lo[os] = lo;
-            t->ops_hi[os] = hi;
-            prof_end(ctx, 3, 1);
-        }
-        const float *ops = t->ops_set[os];
+        const float *ops = nullptr;
+        if ((st = window_ops(ctx, t, lo, hi, fs, &ops))) return st;
         prof_begin(ctx, 4);
         // (the local expansions of every cell at levels >= 2 were zeroed by k_up)
         if (t->n_work > 0) {
@@ -1586,7 +1621,7 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
         // downward pass: L2L chains to the leaves and L2P at their targets, one launch
         prof_begin(ctx, 5);
 #define DDM_DOWN(NN)                                                                                        \
-    k_down<NN><<<(unsigned)nleaf, L2L_T, 0, fs>>>(loff, L, t->cell_ix, t->cell_iy, t->cell_parent, ctx->cheb_T, t->Fl, \
+    k_down<NN><<<(unsigned)nleaf, L2L_T, 0, fs>>>(loff, L, t->cell_ix, t->cell_iy, t->cell_parent, ctx->cheb_Tn[n / 2 - 1], t->Fl, \
                                                   t->cell_start, t->cell_end, t->g_rel, wL, t->far4)
         DDM_CHEB_SWITCH(n, DDM_DOWN);
 #undef DDM_DOWN
@@ -1597,16 +1632,272 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
     if (precise)
         k_near<true><<<(unsigned)((N + NEAR_W - 1) / NEAR_W), NEAR_T, 0, s>>>(
             kf, ctx->kd, wf, wd, t->nb_off, t->nb_tab, t->elem_leaf, t->g_rel, t->g_frame, t->chg, t->perm, loff, wL,
-            n, ctx->prm.quad_near, t->Fl, 0, N, scale, y);
+            n, nq, t->Fl, 0, N, scale, y);
     else
         k_near2<<<(unsigned)((t->n_items + NEAR_W - 1) / NEAR_W), NEAR_T, 0, s>>>(
-            kf, wf, t->nb_off, t->nb_tab, t->elem_leaf, t->g_rel, t->g_frame, t->chg, t->perm, wL, ctx->prm.quad_near,
+            kf, wf, t->nb_off, t->nb_tab, t->elem_leaf, t->g_rel, t->g_frame, t->chg, t->perm, wL, nq,
             t->near_items, t->n_items, N, scale, y);
     prof_end(ctx, 6, 1);
     if (use_far) {
         if (overlap) DDM_CUDA_TRY(ctx, cudaStreamWaitEvent(s, ctx->ev_join, 0));
         k_far_add<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(t->far4, t->g_frame, t->perm, N, scale, y);
     }
+    DDM_CUDA_TRY(ctx, cudaGetLastError());
+    return DDM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Many problems' FMM products in one launch per stage.
+//
+// A batch of independent problems (trees of the same Chebyshev order) is
+// advanced stage by stage: charges and own elements, upward pass, M2L,
+// downward pass, near field, far-field add.  Each stage is one launch over a
+// work list of (problem, local unit) entries built once on the host; the
+// per-problem arrays are reached through a descriptor table.  The upward and
+// downward passes, the near field and the element stages run persistent
+// grids (a multiple of the SM count) that stride over the list, the M2L one
+// CTA per (problem, column tile) as in a single product.  Small problems thus
+// share the device with large ones instead of running one narrow grid each.
+// ---------------------------------------------------------------------------
+namespace {
+struct BDesc {
+    const double *x;
+    double *y;
+    const int64_t *perm;
+    const float4 *g_frame, *g_rel;
+    const double *blk;
+    float4 *chg;
+    float *W, *Fl;
+    float4 *far4;
+    const int32_t *cstart, *cend, *cix, *ciy, *parent;
+    const int32_t *nb_off;
+    const int4 *nb_tab;
+    const int32_t *elem_leaf;
+    const int2 *near_items;
+    const int2 *mk_work;
+    const int32_t *mk_off;
+    const int2 *mk_pair;
+    const float *ops;
+    int64_t n, loff, zoff;
+    int L, nq;
+    float wL, hL;
+};
+constexpr int BE_T = 256, BE_CHUNK = 1024;
+// items (p, kind, a, b): kind 0 prepares elements [a, b), kind 1 zeroes the
+// expansions of the internal cells, floats [zoff + a, zoff + b)
+__global__ void __launch_bounds__(BE_T) k_prep_b(const BDesc *D, const int4 *items, int nitems, double scale,
+                                                 int overwrite) {
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int4 w = items[it];
+        const BDesc &d = D[w.x];
+        if (w.y == 0) {
+            for (int64_t i = w.z + threadIdx.x; i < w.w; i += BE_T)
+                prep_elem(i, d.x, d.perm, d.g_frame, d.blk, d.n, scale, overwrite, d.chg, d.y);
+        } else {
+            for (int64_t z = w.z + threadIdx.x; z < w.w; z += BE_T) {
+                d.W[d.zoff + z] = 0.f;
+                d.Fl[d.zoff + z] = 0.f;
+            }
+        }
+    }
+}
+template <int N>
+__global__ void __launch_bounds__(UP_T) k_up_b(const BDesc *D, const int2 *items, int nitems) {
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int2 w = items[it];
+        const BDesc &d = D[w.x];
+        up_body<N>(d.cstart, d.cend, d.loff, d.L, d.cix, d.ciy, d.parent, d.g_rel, d.g_frame, d.chg, d.hL, d.W, d.Fl,
+                   w.y);
+        __syncthreads();                      // shared staging is reused by the next item
+    }
+}
+template <int N>
+__global__ void __launch_bounds__(L2L_T) k_down_b(const BDesc *D, const int2 *items, int nitems, const float *T) {
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int2 w = items[it];
+        const BDesc &d = D[w.x];
+        down_body<N>(d.loff, d.L, d.cix, d.ciy, d.parent, T, d.Fl, d.cstart, d.cend, d.g_rel, d.wL, d.far4, w.y);
+        __syncthreads();
+    }
+}
+__global__ void __launch_bounds__(tc::THREADS) k_m2l_tc_b(const BDesc *D, const int2 *items, int n, int *err) {
+    const int2 w = items[blockIdx.x];
+    const BDesc &d = D[w.x];
+    m2l_body(d.mk_work, d.mk_off, d.mk_pair, n, d.ops, d.W, d.Fl, err, w.y);
+}
+__global__ void __launch_bounds__(NEAR_T, 4) k_near2_b(KConst<float> k, Win<float> win, const BDesc *D,
+                                                       const int2 *items, int64_t nitems, double scale) {
+    for (int64_t g = (int64_t)blockIdx.x * NEAR_W + (threadIdx.x >> 5); g < nitems;
+         g += (int64_t)gridDim.x * NEAR_W) {
+        const int2 w = items[g];
+        const BDesc &d = D[w.x];
+        near2_body(k, win, d.nb_off, d.nb_tab, d.elem_leaf, d.g_rel, d.g_frame, d.chg, d.perm, d.wL, d.nq,
+                   d.near_items, d.n, scale, d.y, w.y);
+        __syncwarp();                         // the warp's shared rows are reused by its next item
+    }
+}
+// items (p, 0, a, b): far field of elements [a, b) into y
+__global__ void __launch_bounds__(BE_T) k_far_add_b(const BDesc *D, const int4 *items, int nitems, double scale) {
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int4 w = items[it];
+        const BDesc &d = D[w.x];
+        for (int64_t ti = w.z + threadIdx.x; ti < w.w; ti += BE_T) {
+            const float4 g4 = d.far4[ti], f = d.g_frame[ti];
+            const float g[4] = {g4.x, g4.y, g4.z, g4.w};
+            float ss, sn;
+            to_local<float>(f.x, f.y, g, ss, sn);
+            const int64_t e = d.perm[ti];
+            d.y[e] += scale * (double)ss;
+            d.y[d.n + e] += scale * (double)sn;
+            d.y[2 * d.n + e] += scale * (double)g4.w;
+        }
+    }
+}
+}  // namespace
+
+struct BatchFmm {
+    int n = 0, np = 0, nsm = 152;
+    double lo = 0, hi = 0;
+    BDesc *desc = nullptr;
+    int4 *prep = nullptr, *far = nullptr;
+    int2 *leaf = nullptr, *m2l = nullptr, *near = nullptr;
+    int n_prep = 0, n_far = 0, n_leaf = 0, n_m2l = 0;
+    int64_t n_near = 0;
+    long long launches = 0;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+};
+
+void bfmm_free(BatchFmm *b, cudaStream_t s) {
+    if (!b) return;
+    void *ps[] = {b->desc, b->prep, b->far, b->leaf, b->m2l, b->near};
+    for (void *p : ps) dfree(p, s);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
+    delete b;
+}
+
+ddm_status bfmm_build(ddm_ctx *ctx, ddm_tree *const *trees, int np, double lo, double hi, const double *const *xs,
+                      double *const *ys, cudaStream_t s, BatchFmm **out) {
+    *out = nullptr;
+    if (np <= 0) return ctx_fail(ctx, DDM_EINVAL, "batched product: no problems");
+    const int n = trees[0]->prm.n_cheb, n2 = n * n;
+    ddm_status st = upload_tables(ctx);
+    if (st) return st;
+    std::vector<BDesc> hd(np);
+    std::vector<int4> hprep, hfar;
+    std::vector<int2> hleaf, hm2l, hnear;
+    for (int p = 0; p < np; ++p) {
+        ddm_tree *t = trees[p];
+        if (t->prm.n_cheb != n) return ctx_fail(ctx, DDM_EINVAL, "batched product: trees of different orders");
+        if ((st = ensure_workspace(ctx, t))) return st;
+        const double *blk = nullptr;
+        if ((st = window_self_blocks(ctx, t, lo, hi, s, &blk))) return st;
+        const int L = t->depth;
+        const bool far = L >= 2;
+        const float *ops = nullptr;
+        if (far && (st = window_ops(ctx, t, lo, hi, s, &ops))) return st;
+        const int64_t loff = t->lvl_off[L], nleaf = t->lvl_off[L + 1] - loff;
+        const float wL = (float)(2.0 * t->h0 / (double)(1 << L));
+        BDesc &d = hd[p];
+        d.x = xs[p]; d.y = ys[p];
+        d.perm = t->perm; d.g_frame = t->g_frame; d.g_rel = t->g_rel; d.blk = blk;
+        d.chg = t->chg; d.W = t->W; d.Fl = t->Fl; d.far4 = t->far4;
+        d.cstart = t->cell_start; d.cend = t->cell_end; d.cix = t->cell_ix; d.ciy = t->cell_iy;
+        d.parent = t->cell_parent;
+        d.nb_off = t->nb_off; d.nb_tab = t->nb_tab; d.elem_leaf = t->elem_leaf; d.near_items = t->near_items;
+        d.mk_work = t->mk_work; d.mk_off = t->mk_off; d.mk_pair = t->mk_pair; d.ops = ops;
+        d.n = t->n; d.loff = loff; d.L = L; d.nq = t->prm.quad_near; d.wL = wL; d.hL = 0.5f * wL;
+        d.zoff = far ? t->lvl_off[2] * 4 * n2 : 0;
+        for (int64_t a = 0; a < t->n; a += BE_CHUNK) {
+            const int b = (int)std::min<int64_t>(t->n, a + BE_CHUNK);
+            hprep.push_back(make_int4(p, 0, (int)a, b));
+            if (far) hfar.push_back(make_int4(p, 0, (int)a, b));
+        }
+        if (far) {
+            const int64_t nz = (t->lvl_off[L] - t->lvl_off[2]) * 4 * n2;
+            for (int64_t a = 0; a < nz; a += 8 * BE_CHUNK)
+                hprep.push_back(make_int4(p, 1, (int)a, (int)std::min<int64_t>(nz, a + 8 * BE_CHUNK)));
+            for (int64_t l = 0; l < nleaf; ++l) hleaf.push_back(make_int2(p, (int)l));
+            for (int w = 0; w < t->n_work; ++w) hm2l.push_back(make_int2(p, w));
+        }
+        for (int64_t i = 0; i < t->n_items; ++i) hnear.push_back(make_int2(p, (int)i));
+    }
+    {   // (outside any stream capture: the batch's launches may be captured later)
+        static bool attr[64] = {false};
+        if (!attr[ctx->device & 63]) {
+            DDM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_m2l_tc_b, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   tc::SMEM_BYTES));
+            attr[ctx->device & 63] = true;
+        }
+    }
+    BatchFmm *b = new BatchFmm();
+    b->n = n; b->np = np; b->lo = lo; b->hi = hi;
+    cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+    b->n_prep = (int)hprep.size(); b->n_far = (int)hfar.size(); b->n_leaf = (int)hleaf.size();
+    b->n_m2l = (int)hm2l.size(); b->n_near = (int64_t)hnear.size();
+    auto up = [&](void **dst, const void *src, size_t bytes) -> bool {
+        if (dalloc(dst, bytes ? bytes : 16, s) != cudaSuccess) return false;
+        return !bytes || cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    };
+    bool ok = up((void **)&b->desc, hd.data(), hd.size() * sizeof(BDesc)) &&
+              up((void **)&b->prep, hprep.data(), hprep.size() * sizeof(int4)) &&
+              up((void **)&b->far, hfar.data(), hfar.size() * sizeof(int4)) &&
+              up((void **)&b->leaf, hleaf.data(), hleaf.size() * sizeof(int2)) &&
+              up((void **)&b->m2l, hm2l.data(), hm2l.size() * sizeof(int2)) &&
+              up((void **)&b->near, hnear.data(), hnear.size() * sizeof(int2)) &&
+              cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) == cudaSuccess &&
+              cudaStreamSynchronize(s) == cudaSuccess;       // host item lists go out of scope
+    if (!ok) {
+        bfmm_free(b, s);
+        return ctx_fail(ctx, DDM_ENOMEM, "batched product: work list allocation failed");
+    }
+    *out = b;
+    return DDM_OK;
+}
+
+// The stages of every problem's product y = [K(hi) - K(lo)] x (overwrite)
+// on stream s, the far branch (upward pass, M2L, downward pass) forked to
+// aux when given (aux = nullptr: all on s).
+ddm_status bfmm_launch(ddm_ctx *ctx, BatchFmm *b, cudaStream_t s, cudaStream_t aux) {
+    const int n = b->n;
+    const int nsm = b->nsm;
+    auto grid = [&](int64_t items, int per_sm) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)nsm * per_sm)); };
+    long long launches = 0;
+    k_prep_b<<<grid(b->n_prep, 8), BE_T, 0, s>>>(b->desc, b->prep, b->n_prep, 1.0, 1);
+    ++launches;
+    cudaStream_t fs = aux ? aux : s;
+    if (b->n_leaf > 0) {
+        if (aux) {
+            DDM_CUDA_TRY(ctx, cudaEventRecord(b->ev_fork, s));
+            DDM_CUDA_TRY(ctx, cudaStreamWaitEvent(fs, b->ev_fork, 0));
+        }
+#define DDM_UPB(NN) k_up_b<NN><<<grid(b->n_leaf, 4), UP_T, 0, fs>>>(b->desc, b->leaf, b->n_leaf)
+        DDM_CHEB_SWITCH(n, DDM_UPB);
+#undef DDM_UPB
+        if (b->n_m2l > 0) {
+            dim3 g((unsigned)b->n_m2l, (unsigned)((4 * n * n + tc::BM - 1) / tc::BM), 1);
+            k_m2l_tc_b<<<g, tc::THREADS, tc::SMEM_BYTES, fs>>>(b->desc, b->m2l, n, ctx->d_err);
+            ++launches;
+        }
+#define DDM_DOWNB(NN) k_down_b<NN><<<grid(b->n_leaf, 8), L2L_T, 0, fs>>>(b->desc, b->leaf, b->n_leaf, ctx->cheb_Tn[NN / 2 - 1])
+        DDM_CHEB_SWITCH(n, DDM_DOWNB);
+#undef DDM_DOWNB
+        launches += 2;
+        if (aux) DDM_CUDA_TRY(ctx, cudaEventRecord(b->ev_join, fs));
+    }
+    if (b->n_near > 0) {
+        k_near2_b<<<grid((b->n_near + NEAR_W - 1) / NEAR_W, 4), NEAR_T, 0, s>>>(
+            ctx->kf, make_win<float>(ctx, b->lo, b->hi), b->desc, b->near, b->n_near, 1.0);
+        ++launches;
+    }
+    if (b->n_leaf > 0) {
+        if (aux) DDM_CUDA_TRY(ctx, cudaStreamWaitEvent(s, b->ev_join, 0));
+        k_far_add_b<<<grid(b->n_far, 8), BE_T, 0, s>>>(b->desc, b->far, b->n_far, 1.0);
+        ++launches;
+    }
+    prof_end(ctx, 6, (int)launches);
+    b->launches = launches;
     DDM_CUDA_TRY(ctx, cudaGetLastError());
     return DDM_OK;
 }

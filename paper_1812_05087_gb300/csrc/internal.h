@@ -36,6 +36,7 @@ struct Win {
 
 struct ddm_tree {
     cudaStream_t stream;       // stream of the build; frees are ordered on it
+    ddm_fmm_params prm;        // FMM parameters of this tree (order, leaf size, depth cap, near rule)
     int64_t n;                 // elements
     int depth;                 // leaf level L
     double cx, cy, h0;         // root square centre and half-width
@@ -78,6 +79,14 @@ struct ddm_tree {
     float *pb_inv;             // inverted system blocks of the cached (dt, system), FP32
     double pb_dt;
     int pb_sys;
+    // coarse level of the preconditioner: the blocks of long chains (at least
+    // PC_MIN_BLOCKS blocks), pc_modes Legendre modes per block and unknown
+    // component; pc_inv = inverse of the Galerkin coarse matrix Z^T A Z of the
+    // cached (dt, system), FP32, dimension n_pc * nc * pc_modes
+    int64_t n_pc;
+    int pc_modes;
+    int32_t *pc_blk;           // block index of every coarse block
+    float *pc_inv;
     // M2L pairs grouped by (level, cell offset): key = level * 49 + (dx+3)*7 + (dy+3)
     int n_keys;                // (L + 1) * 49
     int32_t *mk_off;           // CSR over keys
@@ -99,6 +108,11 @@ struct ddm_tree {
     float4 *chg;               // sorted charges (Dx, Dy, q, 0) per element
     int ncheb_alloc;
 };
+
+// coarse level of the preconditioner (precond.cu): chains of at least
+// PC_MIN_BLOCKS blocks take PC_MODES modes per block (fewer when the coarse
+// dimension would exceed PC_MAX_DIM; none below one mode)
+constexpr int PC_MIN_BLOCKS = 3, PC_MODES = 3, PC_MAX_DIM = 4096;
 
 struct GmresWork;
 
@@ -157,7 +171,8 @@ struct ddm_ctx {
     // Chebyshev tables (device): nodes, M2M/L2L transfer matrices T[q][a][a']
     float *cheb_nodes;         // n
     float *cheb_bw;            // barycentric weights, n
-    float *cheb_T;             // 2 x n x n
+    float *cheb_T;             // 2 x n x n of the context's order
+    float *cheb_Tn[DDM_MAX_CHEB / 2] = {};   // the same for every even order n (index n / 2 - 1)
     GmresWork *gm;
     Prof prof;
     int *d_err;                // device word raised by a kernel whose bounded wait expired
@@ -196,8 +211,8 @@ ddm_status ctx_fail(ddm_ctx *ctx, ddm_status st, const std::string &msg);
             return ctx_fail(ctx, DDM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(_e)); \
     } while (0)
 
-// tree.cu
-ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **out);
+// tree.cu (prm: the tree's FMM parameters, validated by the caller)
+ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, const ddm_fmm_params &prm, ddm_tree **out);
 void tree_free(ddm_tree *t);
 
 // fmm.cu: y = [K(hi) - K(lo)] x  (caller order), accumulate: y += s * (...)
@@ -206,7 +221,22 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double tau_lo, double tau_hi, con
 // own-element 3x3 blocks (caller order) of window (lo, hi), from the tree's window cache
 ddm_status window_self_blocks(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, cudaStream_t s, const double **out);
 ddm_status ensure_workspace(ddm_ctx *ctx, ddm_tree *t);
+// M2L operator set of window (lo, hi) for tree t (cached per window)
+ddm_status window_ops(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, cudaStream_t s, const float **out);
+// many problems' FMM products, one launch per stage (trees of one order):
+// y_p = [K(hi) - K(lo)] x_p for every problem p (fmm.cu)
+struct BatchFmm;
+ddm_status bfmm_build(ddm_ctx *ctx, ddm_tree *const *trees, int np, double lo, double hi, const double *const *xs,
+                      double *const *ys, cudaStream_t s, BatchFmm **out);
+ddm_status bfmm_launch(ddm_ctx *ctx, BatchFmm *b, cudaStream_t s, cudaStream_t aux);
+void bfmm_free(BatchFmm *b, cudaStream_t s);
 ddm_status upload_tables(ddm_ctx *ctx);
 // precond.cu: chain-block Jacobi preconditioner (cached per dt and system)
 ddm_status pb_prepare(ddm_ctx *ctx, ddm_tree *t, double dt, int sys, cudaStream_t s);
 ddm_status pb_apply(ddm_ctx *ctx, ddm_tree *t, int sys, const double *v, double *z3, cudaStream_t s);
+// the same for many problems in one launch per stage (precond.cu)
+struct BatchPb;
+ddm_status bpb_build(ddm_ctx *ctx, ddm_tree *const *trees, int np, int sys, const double *const *vs,
+                     double *const *zs, cudaStream_t s, BatchPb **out);
+ddm_status bpb_launch(ddm_ctx *ctx, BatchPb *b, cudaStream_t s);
+void bpb_free(BatchPb *b, cudaStream_t s);

@@ -95,6 +95,30 @@ DEV void f_funcs(T u, T iu, T &e, T &F0, T &F1, T &F2) {
     }
 }
 
+// Remainders of F, F', F'' beyond their large-u forms 1/u, -1/u^2, 2/u^3
+// (exponentially small, u >= 1): F = 1/u + F0r, F' = -1/u^2 + F1r,
+// F'' = 2/u^3 + F2r with F0r = -e/u, F1r = e (1/u + 1/u^2),
+// F2r = -e/u - 2 F1r/u.  A transient written with these in place of F,
+// F', F'' (ghat, P2h likewise below) is the part of one side of a time
+// window that is not a polynomial in c t: the polynomial parts of the two
+// sides are subtracted in closed form instead (no cancellation).
+template <class T>
+DEV void f_rem(T u, T iu, T &e, T &F0, T &F1, T &F2) {
+    e = u > Big<T>::U ? T(0) : dexp<T>(-u);
+    F0 = -e * iu;
+    F1 = e * iu * (T(1) + iu);
+    F2 = -e * iu - T(2) * F1 * iu;
+}
+// ghat = 1/u - 1/u^2 + g0r, ghat' = -1/u^2 + 2/u^3 + g1r,
+// ghat'' = 2/u^3 - 6/u^4 + g2r, P2h = 1/u^2 + p2r
+template <class T>
+DEV void g_rem(T u, T iu, T e, T F0, T F1, T F2, T &g0, T &g1, T &g2, T &p2h) {
+    g0 = -F0 * iu;
+    g1 = -(F1 + g0) * iu;
+    g2 = -(F2 + T(2) * g1) * iu;
+    p2h = -(T(1) + u) * e * iu * iu;
+}
+
 // ghat = (1 - F)/u and its two derivatives; P2h = P(2,u)/u^2.
 // ghat = sum (-1)^k u^k/(k+2)!, ghat' = sum_{k>=1} (-1)^k k u^(k-1)/(k+2)!,
 // ghat'' = sum_{k>=2} (-1)^k k(k-1) u^(k-2)/(k+2)!,
@@ -192,15 +216,21 @@ template <> DEV float e1x<float>(float u, float iu) { return e1f(u, iu); }
 // ---------------------------------------------------------------------------
 // point kernel, potency form
 // ---------------------------------------------------------------------------
-// g0c = 1/(4ct), ct4 = 4ct, ir2 = 1/r^2 (precomputed by the caller)
-template <class T>
+// g0c = 1/(4ct), ct4 = 4ct, ir2 = 1/r^2 (precomputed by the caller).
+// REM: only the remainder beyond the polynomial large-u form (u >= 1).
+template <class T, bool REM = false>
 DEV void pot_transient(const KConst<T> &k, T x, T y, T ir2, T Pxx, T Pyy, T Pxy, T q, T g0c, T ct4, T s,
                        T acc[4]) {
     T x2 = x * x, y2 = y * y, xy = x * y, r2 = x2 + y2;
     T u = r2 * g0c, iu = ct4 * ir2;
     T e, F0, F1, F2, gh0, gh1, gh2, p2h;
-    f_funcs<T>(u, iu, e, F0, F1, F2);
-    g_funcs<T>(u, iu, e, F0, F1, F2, gh0, gh1, gh2, p2h);
+    if (REM) {
+        f_rem<T>(u, iu, e, F0, F1, F2);
+        g_rem<T>(u, iu, e, F0, F1, F2, gh0, gh1, gh2, p2h);
+    } else {
+        f_funcs<T>(u, iu, e, F0, F1, F2);
+        g_funcs<T>(u, iu, e, F0, F1, F2, gh0, gh1, gh2, p2h);
+    }
     T dP = Pyy - Pxx, trP = Pxx + Pyy;
     T a = dP * (x2 - y2) - T(4) * Pxy * xy;
     T ax = T(2) * dP * x - T(4) * Pxy * y;
@@ -227,10 +257,45 @@ DEV void pot_transient(const KConst<T> &k, T x, T y, T ir2, T Pxx, T Pyy, T Pxy,
     }
 }
 
+// The part of a time window (t_lo > 0) of the point kernel that is
+// polynomial in c t at large u: the t-free terms of the two sides cancel,
+// what is left is linear in d4ct = 4c (t_hi - t_lo):
+//   d4ct * 6 G2 K2 / r^8 * (Q, -Q, -2 R, 0)
+//   + fluid source: -eta q/(4 pi kappa) d4ct / r^4 * (x^2-y^2, y^2-x^2, 2xy, 0)
+// with Q = (Pxx-Pyy)(x^4 - 6x^2y^2 + y^4) + 8 Pxy xy (x^2-y^2),
+//      R = Pxy (x^4 - 6x^2y^2 + y^4) - 2 (Pxx-Pyy) xy (x^2-y^2).
+template <class T>
+DEV void pot_asym(const KConst<T> &k, T x, T y, T Pxx, T Pyy, T Pxy, T q, T d4ct, T acc[4]) {
+    T x2 = x * x, y2 = y * y, xy = x * y;
+    T ir2 = T(1) / (x2 + y2), ir4 = ir2 * ir2;
+    T d = x2 - y2, dPm = Pxx - Pyy;
+    T c4 = d * d - T(4) * x2 * y2, s4 = T(4) * xy * d;
+    T f = T(6) * k.G2 * k.K2 * d4ct * ir4 * ir4;
+    T Q = dPm * c4 + T(2) * Pxy * s4, R = Pxy * c4 - T(0.5) * dPm * s4;
+    T fq = -k.eta * k.i4pk * q * d4ct * ir4;
+    acc[0] += f * Q + fq * d;
+    acc[1] -= f * Q + fq * d;
+    acc[2] += fq * T(2) * xy - T(2) * f * R;
+}
+
 template <class T>
 DEV void pot_kernel(const KConst<T> &k, T x, T y, T Pxx, T Pyy, T Pxy, T q, const Win<T> &w,
                     T acc[4]) {
     T ir2 = T(1) / (x * x + y * y);
+    if (w.ct_lo > T(0) && (x * x + y * y) * w.g_hi >= T(1)) {
+        // time element (t_lo > 0), u >= 1 on both sides (the hi side has the
+        // smaller u): the polynomial parts of the two sides in closed form,
+        // plus each side's exponentially small remainder.  Evaluated side by
+        // side, the two sides' common t-free term (the undrained - drained
+        // difference) would cancel and take the small window difference with
+        // it.
+        pot_asym<T>(k, x, y, Pxx, Pyy, Pxy, q, T(4) * (w.ct_hi - w.ct_lo), acc);
+        if ((x * x + y * y) * w.g_hi <= Big<T>::U) {
+            pot_transient<T, true>(k, x, y, ir2, Pxx, Pyy, Pxy, q, w.g_hi, T(4) * w.ct_hi, T(1), acc);
+            pot_transient<T, true>(k, x, y, ir2, Pxx, Pyy, Pxy, q, w.g_lo, T(4) * w.ct_lo, T(-1), acc);
+        }
+        return;
+    }
     if (w.elastic) {
         T x2 = x * x, y2 = y * y, xy = x * y;
         T C = k.Cel * ir2 * ir2 * ir2;
@@ -278,25 +343,22 @@ DEV void pot_bigu(const KConst<float> &k, float x, float y, float Pxx, float Pyy
                        Pyy * xy * (2.f * x2 - 6.f * y2));
         acc[3] += k.aS * k.Ce * (dPm * d + 4.f * Pxy * xy) * ir4;
     }
-    float c4 = d * d - 4.f * x2 * y2, s4 = 4.f * xy * d;
-    float f = 6.f * k.G2 * k.K2 * d4ct * ir4 * ir4;
-    float Q = dPm * c4 + 2.f * Pxy * s4, R = Pxy * c4 - 0.5f * dPm * s4;
-    float fq = -k.eta * k.i4pk * q * d4ct * ir4;
-    acc[0] += f * Q + fq * d;
-    acc[1] -= f * Q + fq * d;
-    acc[2] += fq * 2.f * xy - 2.f * f * R;
+    pot_asym<float>(k, x, y, Pxx, Pyy, Pxy, q, d4ct, acc);
 }
 
 // ---------------------------------------------------------------------------
 // half-line DD (edge dislocation), DD vector (Dx, Dy)
 // ---------------------------------------------------------------------------
-template <class T>
+// REM: only the remainder beyond the polynomial large-u form (u >= 1; the
+// pressure's 1 - e^-u = u F becomes -e^-u)
+template <class T, bool REM = false>
 DEV void disl_transient(const KConst<T> &k, T zx, T zy, T ir2, T Dx, T Dy, T g0c, T ct4, T s, T acc[4]) {
     T r2 = zx * zx + zy * zy;
     T beta = T(2) * g0c;                        // 1/(2ct)
     T u = r2 * g0c, iu = ct4 * ir2;
     T e, F0, F1, F2;
-    f_funcs<T>(u, iu, e, F0, F1, F2);
+    if (REM) f_rem<T>(u, iu, e, F0, F1, F2);
+    else f_funcs<T>(u, iu, e, F0, F1, F2);
     T V1 = F0 + F1, V2 = F1 + F2;
     T l = Dx * zy - Dy * zx, lx = -Dy, ly = Dx;
     T cm = -k.K2 * beta;
@@ -322,20 +384,26 @@ DEV void disl_field(const KConst<T> &k, T zx, T zy, T Dx, T Dy, const Win<T> &w,
         acc[2] -= C * (x2 - y2) * (Dx * zx + Dy * zy);
     }
     const int sides = w.ct_lo > T(0) ? 2 : 1;
-    if (sides == 2 && (zx * zx + zy * zy) * w.g_hi > Big<T>::U) {
-        // Both sides beyond u = Big (the hi side has the smaller u): there the
-        // transient functions are their asymptotic forms (F0 = 1/u,
-        // F1 = -1/u^2, F2 = 2/u^3, e^-u = 0).  Each side is the same
+    if (sides == 2 && (zx * zx + zy * zy) * w.g_hi >= T(1)) {
+        // u >= 1 on both sides (the hi side has the smaller u).  Written with
+        // the large-u forms of the transient functions (F0 = 1/u,
+        // F1 = -1/u^2, F2 = 2/u^3, e^-u = 0), each side is the same
         // t-independent term (the undrained - drained difference) plus a term
         // linear in 4ct/r^2; the former cancels exactly between the sides,
         // and evaluated side by side it would cost ~log10(u) digits.  What is
-        // left, written out: 2 G2 K2 (4 ct_hi - 4 ct_lo) / r^4 times the
-        // dislocation's angular factors; the pressure terms cancel.
+        // left of the polynomial part, written out: 2 G2 K2 (4 ct_hi -
+        // 4 ct_lo) / r^4 times the dislocation's angular factors (the
+        // pressure terms cancel); then each side's exponentially small
+        // remainder (zero beyond u = Big).
         const T l = Dx * zy - Dy * zx;
         const T f = s * T(8) * k.G2 * k.K2 * (w.ct_hi - w.ct_lo) * ir2 * ir2;
         acc[0] -= f * (T(2) * Dx * zy + l - T(4) * l * zy * zy * ir2);
         acc[1] -= f * (l - T(2) * Dy * zx - T(4) * l * zx * zx * ir2);
         acc[2] += f * (Dx * zx - Dy * zy - T(4) * l * zx * zy * ir2);
+        if ((zx * zx + zy * zy) * w.g_hi <= Big<T>::U) {
+            disl_transient<T, true>(k, zx, zy, ir2, Dx, Dy, w.g_hi, T(4) * w.ct_hi, s, acc);
+            disl_transient<T, true>(k, zx, zy, ir2, Dx, Dy, w.g_lo, T(4) * w.ct_lo, -s, acc);
+        }
         return;
     }
 #pragma unroll 1

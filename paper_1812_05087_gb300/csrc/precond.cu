@@ -11,6 +11,17 @@
 // at 64x the FP64 rate.  Applying the preconditioner is
 // one small dense product per block.  Elements that belong to no chain form
 // 1-element blocks, i.e. the own-element 3x3 block Jacobi.
+//
+// Long chains (at least PC_MIN_BLOCKS blocks) add a coarse level: on each of
+// their blocks, Legendre modes of degree < pc_modes in the block's element
+// index, one set per unknown component, span the coarse space Z; the
+// Galerkin matrix A_c = Z^T A Z (all element pairs of every pair of coarse
+// blocks) is assembled and inverted on the device once per (dt, system),
+// and the preconditioner becomes additive two-level,
+// M^-1 = blockdiag^-1 + Z A_c^-1 Z^T.  Block Jacobi alone leaves the long-
+// wavelength modes of a long fracture (and the coupling between parallel
+// fractures) to the Krylov iteration, whose count then grows with the chain
+// length; the coarse level carries them.
 #include <cmath>
 #include <vector>
 
@@ -239,11 +250,11 @@ __global__ void __launch_bounds__(1024, 1) k_pb_invert(const int32_t *boff, cons
 // at a time, lanes along the rows (coalesced); the unknown blocks beyond nc
 // are set to zero
 constexpr int PA_T = 256, PA_WARPS = PA_T / 32, PA_R = 4, PA_S = 2;
-__global__ void __launch_bounds__(PA_T) k_pb_apply(const int32_t *boff, const int64_t *belem, const int64_t *moff,
-                                                   int nc, const float *Minv, const double *v, int64_t N, double *z,
-                                                   int zero_rest) {
+__device__ __forceinline__ void pb_apply_body(const int32_t *boff, const int64_t *belem, const int64_t *moff, int nc,
+                                              const float *Minv, const double *v, int64_t N, double *z,
+                                              int zero_rest, int b) {
     __shared__ float sv[INV_MAX];
-    const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int m = boff[b + 1] - boff[b], n = nc * m;
     const int64_t *el = belem + boff[b];
     for (int c = threadIdx.x; c < n; c += PA_T) sv[c] = (float)v[(c / m) * N + el[c % m]];
@@ -288,8 +299,438 @@ __global__ void __launch_bounds__(PA_T) k_pb_apply(const int32_t *boff, const in
     if (zero_rest && nc < 3 && blockIdx.y == 0)
         for (int e = threadIdx.x; e < m; e += PA_T) z[2 * N + el[e]] = 0.0;
 }
+__global__ void __launch_bounds__(PA_T) k_pb_apply(const int32_t *boff, const int64_t *belem, const int64_t *moff,
+                                                   int nc, const float *Minv, const double *v, int64_t N, double *z,
+                                                   int zero_rest) {
+    pb_apply_body(boff, belem, moff, nc, Minv, v, N, z, zero_rest, blockIdx.x);
+}
+
+// ------------------------------------------------------------ coarse level
+// Legendre polynomial P_k (k < 3) at the centre of element i of an m-element
+// block, mapped to [-1, 1]
+__device__ __forceinline__ float leg(int k, int i, int m) {
+    const float t = -1.f + (2.f * i + 1.f) / (float)m;
+    return k == 0 ? 1.f : (k == 1 ? t : 1.5f * t * t - 0.5f);
+}
+constexpr int PC_T = 128, PC_MAXQ = 3 * PC_MODES;
+// A_c[(I nc + c) K + k][(J nc + d) K + l] = sum_{i in I, j in J}
+//     P_k(t_i) A_{(c, i), (d, j)} P_l(t_j): one CTA per (coarse block I,
+// coarse block J), the element pairs split over the threads
+__global__ void __launch_bounds__(PC_T) k_pc_assemble(KConst<float> kf, Win<float> wf, const PbGeo *geo,
+                                                      const double *selfblk, const int32_t *boff,
+                                                      const int64_t *belem, const int32_t *pcb, int nc, int sys,
+                                                      int K, int64_t dim, float *Ac) {
+    __shared__ float red[PC_T / 32][PC_MAXQ * PC_MAXQ];
+    const int I = blockIdx.x, J = blockIdx.y;
+    const int bI = pcb[I], bJ = pcb[J];
+    const int mI = boff[bI + 1] - boff[bI], mJ = boff[bJ + 1] - boff[bJ];
+    const int64_t *elI = belem + boff[bI], *elJ = belem + boff[bJ];
+    const int Q = nc * K;
+    float acc[PC_MAXQ][PC_MAXQ];
+#pragma unroll
+    for (int a = 0; a < PC_MAXQ; ++a)
+#pragma unroll
+        for (int b = 0; b < PC_MAXQ; ++b) acc[a][b] = 0.f;
+    for (int p = threadIdx.x; p < mI * mJ; p += PC_T) {
+        const int i = p / mJ, j = p % mJ;
+        const int64_t ei = elI[i], ej = elJ[j];
+        float o[3][3];
+        if (ei == ej) {
+            for (int r = 0; r < 3; ++r)
+                for (int c = 0; c < 3; ++c) o[r][c] = (float)selfblk[9 * ei + 3 * r + c];
+        } else {
+            pair_block(kf, wf, geo[ei], geo[ej], o);
+        }
+        if (sys == DDM_SYS_RATE)
+            for (int c = 0; c < 3; ++c) o[1][c] += o[2][c];
+        float pi[PC_MODES], pj[PC_MODES];
+#pragma unroll
+        for (int k = 0; k < PC_MODES; ++k) { pi[k] = leg(k, i, mI); pj[k] = leg(k, j, mJ); }
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int k = 0; k < PC_MODES; ++k)
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+#pragma unroll
+                    for (int l = 0; l < PC_MODES; ++l)
+                        if (c < nc && d < nc && k < K && l < K)
+                            acc[c * PC_MODES + k][d * PC_MODES + l] =
+                                fmaf(o[c][d] * pi[k], pj[l], acc[c * PC_MODES + k][d * PC_MODES + l]);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int a = 0; a < PC_MAXQ; ++a)
+#pragma unroll
+        for (int b = 0; b < PC_MAXQ; ++b) {
+            float v = acc[a][b];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+            if (lane == 0) red[warp][a * PC_MAXQ + b] = v;
+        }
+    __syncthreads();
+    for (int q = threadIdx.x; q < Q * Q; q += PC_T) {
+        const int a = q / Q, b = q % Q;              // a = c K + k, b = d K + l
+        const int c = a / K, k = a % K, d = b / K, l = b % K;
+        float v = 0.f;
+#pragma unroll
+        for (int w = 0; w < PC_T / 32; ++w) v += red[w][(c * PC_MODES + k) * PC_MAXQ + d * PC_MODES + l];
+        Ac[((int64_t)I * Q + a) * dim + (int64_t)J * Q + b] = v;
+    }
+}
+
+// In-place Gauss-Jordan inversion of the coarse matrix (FP32, partial
+// pivoting), one step per pair of launches: the pivot kernel (one CTA)
+// swaps the pivot row into place and stages row k (scaled by 1/pivot) and
+// column k; the update kernel then rewrites every entry from the staged
+// copies, so that no entry is read after it was overwritten.
+constexpr int GJ_T = 1024;
+__global__ void __launch_bounds__(GJ_T) k_gj_pivot(float *A, int64_t n, int64_t k, int32_t *piv, float *rowk,
+                                                   float *colk, float *ipiv) {
+    __shared__ float bv[GJ_T / 32];
+    __shared__ int64_t bi[GJ_T / 32];
+    __shared__ int64_t s_p;
+    float best = -1.f;
+    int64_t bidx = k;
+    for (int64_t i = k + threadIdx.x; i < n; i += GJ_T) {
+        const float v = fabsf(A[i * n + k]);
+        if (v > best) { best = v; bidx = i; }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xFFFFFFFFu, best, o);
+        const int64_t oi = __shfl_xor_sync(0xFFFFFFFFu, bidx, o);
+        if (ov > best || (ov == best && oi < bidx)) { best = ov; bidx = oi; }
+    }
+    if (lane == 0) { bv[warp] = best; bi[warp] = bidx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float b = bv[0];
+        int64_t p = bi[0];
+        for (int w = 1; w < GJ_T / 32; ++w)
+            if (bv[w] > b || (bv[w] == b && bi[w] < p)) { b = bv[w]; p = bi[w]; }
+        s_p = p;
+        piv[k] = (int32_t)p;
+    }
+    __syncthreads();
+    const int64_t p = s_p;
+    if (p != k)
+        for (int64_t j = threadIdx.x; j < n; j += GJ_T) {
+            const float a = A[k * n + j];
+            A[k * n + j] = A[p * n + j];
+            A[p * n + j] = a;
+        }
+    __syncthreads();
+    const float pv = A[k * n + k];
+    const float ip = pv != 0.f ? 1.f / pv : 0.f;
+    for (int64_t j = threadIdx.x; j < n; j += GJ_T) {
+        rowk[j] = A[k * n + j] * ip;
+        colk[j] = A[j * n + k];
+    }
+    if (threadIdx.x == 0) *ipiv = ip;
+}
+__global__ void k_gj_update(float *A, int64_t n, int64_t k, const float *rowk, const float *colk, const float *ipiv) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= n * n) return;
+    const int64_t i = q / n, j = q % n;
+    const float ip = *ipiv;
+    float v;
+    if (i == k) v = j == k ? ip : rowk[j];
+    else v = j == k ? -colk[i] * ip : fmaf(-colk[i], rowk[j], A[q]);
+    A[q] = v;
+}
+// The same Gauss-Jordan steps in one CTA (row k and column k staged in
+// shared memory), for coarse matrices of up to GJ1_MAX rows, where one
+// launch per step would cost more than the arithmetic.
+constexpr int GJ1_MAX = 1536;
+__global__ void __launch_bounds__(GJ_T) k_gj_cta(float *A, int64_t n, int32_t *piv) {
+    __shared__ float rowk[GJ1_MAX], colk[GJ1_MAX];
+    __shared__ float bv[GJ_T / 32];
+    __shared__ int64_t bi[GJ_T / 32];
+    __shared__ int64_t s_p;
+    __shared__ float s_ip;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t k = 0; k < n; ++k) {
+        float best = -1.f;
+        int64_t bidx = k;
+        for (int64_t i = k + threadIdx.x; i < n; i += GJ_T) {
+            const float v = fabsf(A[i * n + k]);
+            if (v > best) { best = v; bidx = i; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xFFFFFFFFu, best, o);
+            const int64_t oi = __shfl_xor_sync(0xFFFFFFFFu, bidx, o);
+            if (ov > best || (ov == best && oi < bidx)) { best = ov; bidx = oi; }
+        }
+        if (lane == 0) { bv[warp] = best; bi[warp] = bidx; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float b = bv[0];
+            int64_t p = bi[0];
+            for (int w = 1; w < GJ_T / 32; ++w)
+                if (bv[w] > b || (bv[w] == b && bi[w] < p)) { b = bv[w]; p = bi[w]; }
+            s_p = p;
+            piv[k] = (int32_t)p;
+        }
+        __syncthreads();
+        const int64_t p = s_p;
+        if (p != k)
+            for (int64_t j = threadIdx.x; j < n; j += GJ_T) {
+                const float a = A[k * n + j];
+                A[k * n + j] = A[p * n + j];
+                A[p * n + j] = a;
+            }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const float pv = A[k * n + k];
+            s_ip = pv != 0.f ? 1.f / pv : 0.f;
+        }
+        __syncthreads();
+        const float ip = s_ip;
+        for (int64_t j = threadIdx.x; j < n; j += GJ_T) {
+            rowk[j] = A[k * n + j] * ip;
+            colk[j] = A[j * n + k];
+        }
+        __syncthreads();
+        for (int64_t q = threadIdx.x; q < n * n; q += GJ_T) {
+            const int64_t i = q / n, j = q % n;
+            float v;
+            if (i == k) v = j == k ? ip : rowk[j];
+            else v = j == k ? -colk[i] * ip : fmaf(-colk[i], rowk[j], A[q]);
+            A[q] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// undo the row interchanges as column swaps, in reverse order (a thread per row)
+__global__ void k_gj_unpivot(float *A, int64_t n, const int32_t *piv) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float *row = A + i * n;
+    for (int64_t k = n - 1; k >= 0; --k) {
+        const int64_t p = piv[k];
+        if (p != k) { const float a = row[k]; row[k] = row[p]; row[p] = a; }
+    }
+}
+
+// coarse residual r_c = Z^T v (FP64 sums), one CTA per coarse block
+__global__ void k_pc_restrict(const double *v, int64_t N, const int32_t *boff, const int64_t *belem,
+                              const int32_t *pcb, int nc, int K, float *rc) {
+    __shared__ double red[2][PC_MAXQ];
+    const int I = blockIdx.x, b = pcb[I], m = boff[b + 1] - boff[b];
+    const int64_t *el = belem + boff[b];
+    double acc[PC_MAXQ];
+#pragma unroll
+    for (int q = 0; q < PC_MAXQ; ++q) acc[q] = 0.0;
+    for (int i = threadIdx.x; i < m; i += 64)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            if (c < nc) {
+                const double x = v[c * N + el[i]];
+#pragma unroll
+                for (int k = 0; k < PC_MODES; ++k)
+                    if (k < K) acc[c * PC_MODES + k] += (double)leg(k, i, m) * x;
+            }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < PC_MAXQ; ++q) {
+        double a = acc[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+        if (lane == 0) red[warp][q] = a;
+    }
+    __syncthreads();
+    const int Q = nc * K;
+    if (threadIdx.x < Q) {
+        const int c = threadIdx.x / K, k = threadIdx.x % K;
+        rc[(int64_t)I * Q + threadIdx.x] = (float)(red[0][c * PC_MODES + k] + red[1][c * PC_MODES + k]);
+    }
+}
+// y_c = A_c^-1 r_c, a warp per row
+__global__ void k_pc_gemv(const float *Ainv, const float *rc, int64_t n, float *yc) {
+    const int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    const float *row = Ainv + r * n;
+    float s = 0.f;
+    for (int64_t j = lane; j < n; j += 32) s = fmaf(row[j], rc[j], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+    if (lane == 0) yc[r] = s;
+}
+// z += Z y_c
+__global__ void k_pc_prolong(const float *yc, int64_t N, const int32_t *boff, const int64_t *belem,
+                             const int32_t *pcb, int nc, int K, double *z) {
+    const int I = blockIdx.x, b = pcb[I], m = boff[b + 1] - boff[b];
+    const int64_t *el = belem + boff[b];
+    const int Q = nc * K;
+    for (int i = threadIdx.x; i < m; i += 64)
+        for (int c = 0; c < nc; ++c) {
+            float s = 0.f;
+            for (int k = 0; k < K; ++k) s = fmaf(leg(k, i, m), yc[(int64_t)I * Q + c * K + k], s);
+            z[c * N + el[i]] += (double)s;
+        }
+}
+
+// ---- batched apply: every problem of a batch in one launch per stage
+struct PbDesc {
+    const int32_t *boff, *pcb;
+    const int64_t *belem, *moff;
+    const float *Minv, *Ainv;
+    float *rc, *yc;
+    const double *v;
+    double *z;
+    int64_t N, dim;
+    int K;
+};
+// one CTA per (problem, block) x row slice
+__global__ void __launch_bounds__(PA_T) k_pb_apply_b(const PbDesc *D, const int2 *items, int nc) {
+    const int2 w = items[blockIdx.x];
+    const PbDesc &d = D[w.x];
+    pb_apply_body(d.boff, d.belem, d.moff, nc, d.Minv, d.v, d.N, d.z, 1, w.y);
+}
+// items (p, coarse block I)
+__global__ void k_pc_restrict_b(const PbDesc *D, const int2 *items, int nc) {
+    const int2 w = items[blockIdx.x];
+    const PbDesc &d = D[w.x];
+    __shared__ double red[2][PC_MAXQ];
+    const int I = w.y, b = d.pcb[I], m = d.boff[b + 1] - d.boff[b], K = d.K;
+    const int64_t *el = d.belem + d.boff[b];
+    double acc[PC_MAXQ];
+#pragma unroll
+    for (int q = 0; q < PC_MAXQ; ++q) acc[q] = 0.0;
+    for (int i = threadIdx.x; i < m; i += 64)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            if (c < nc) {
+                const double x = d.v[c * d.N + el[i]];
+#pragma unroll
+                for (int k = 0; k < PC_MODES; ++k)
+                    if (k < K) acc[c * PC_MODES + k] += (double)leg(k, i, m) * x;
+            }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < PC_MAXQ; ++q) {
+        double a = acc[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+        if (lane == 0) red[warp][q] = a;
+    }
+    __syncthreads();
+    const int Q = nc * K;
+    if (threadIdx.x < Q) {
+        const int c = threadIdx.x / K, k = threadIdx.x % K;
+        d.rc[(int64_t)I * Q + threadIdx.x] = (float)(red[0][c * PC_MODES + k] + red[1][c * PC_MODES + k]);
+    }
+}
+// items (p, first of 8 rows); a warp per row
+__global__ void k_pc_gemv_b(const PbDesc *D, const int2 *items) {
+    const int2 w = items[blockIdx.x];
+    const PbDesc &d = D[w.x];
+    const int64_t r = (int64_t)w.y + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= d.dim) return;
+    const float *row = d.Ainv + r * d.dim;
+    float sacc = 0.f;
+    for (int64_t j = lane; j < d.dim; j += 32) sacc = fmaf(row[j], d.rc[j], sacc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xFFFFFFFFu, sacc, o);
+    if (lane == 0) d.yc[r] = sacc;
+}
+__global__ void k_pc_prolong_b(const PbDesc *D, const int2 *items, int nc) {
+    const int2 w = items[blockIdx.x];
+    const PbDesc &d = D[w.x];
+    const int I = w.y, b = d.pcb[I], m = d.boff[b + 1] - d.boff[b], K = d.K;
+    const int64_t *el = d.belem + d.boff[b];
+    const int Q = nc * K;
+    for (int i = threadIdx.x; i < m; i += 64)
+        for (int c = 0; c < nc; ++c) {
+            float sacc = 0.f;
+            for (int k = 0; k < K; ++k) sacc = fmaf(leg(k, i, m), d.yc[(int64_t)I * Q + c * K + k], sacc);
+            d.z[c * d.N + el[i]] += (double)sacc;
+        }
+}
 
 }  // namespace
+
+struct BatchPb {
+    int np = 0, nc = 0;
+    PbDesc *desc = nullptr;
+    int2 *blk = nullptr, *pc = nullptr, *gemv = nullptr;
+    int n_blk = 0, n_pc = 0, n_gemv = 0;
+};
+
+void bpb_free(BatchPb *b, cudaStream_t s) {
+    if (!b) return;
+    void *ps[] = {b->desc, b->blk, b->pc, b->gemv};
+    for (void *p : ps) dfree(p, s);
+    delete b;
+}
+
+// the batched preconditioner of problems p (prepared for the same (dt,
+// system)) from v_p (system layout) into z_p (3N layout)
+ddm_status bpb_build(ddm_ctx *ctx, ddm_tree *const *trees, int np, int sys, const double *const *vs,
+                     double *const *zs, cudaStream_t s, BatchPb **out) {
+    *out = nullptr;
+    const int nc = sys == DDM_SYS_PRESSURE ? 3 : 2;
+    std::vector<PbDesc> hd(np);
+    std::vector<int2> hblk, hpc, hgemv;
+    for (int p = 0; p < np; ++p) {
+        ddm_tree *t = trees[p];
+        if (!t->pb_inv || t->pb_sys != sys) return ctx_fail(ctx, DDM_EINVAL, "batched preconditioner: not prepared");
+        PbDesc &d = hd[p];
+        d.boff = t->pb_off; d.belem = t->pb_elem; d.moff = t->pb_moff; d.Minv = t->pb_inv;
+        d.v = vs[p]; d.z = zs[p]; d.N = t->n;
+        d.pcb = t->pc_blk; d.K = t->pc_modes; d.Ainv = t->pc_inv; d.dim = 0; d.rc = d.yc = nullptr;
+        for (int64_t b = 0; b < t->n_pblk; ++b) hblk.push_back(make_int2(p, (int)b));
+        if (t->n_pc > 0) {
+            const int K = t->pc_modes;
+            d.dim = t->n_pc * nc * K;
+            d.rc = t->pc_inv + (size_t)t->n_pc * 3 * K * t->n_pc * 3 * K;
+            d.yc = d.rc + t->n_pc * 3 * K;
+            for (int64_t I = 0; I < t->n_pc; ++I) hpc.push_back(make_int2(p, (int)I));
+            for (int64_t r = 0; r < d.dim; r += 8) hgemv.push_back(make_int2(p, (int)r));
+        }
+    }
+    BatchPb *b = new BatchPb();
+    b->np = np; b->nc = nc;
+    b->n_blk = (int)hblk.size(); b->n_pc = (int)hpc.size(); b->n_gemv = (int)hgemv.size();
+    auto up = [&](void **dst, const void *src, size_t bytes) -> bool {
+        if (dalloc(dst, bytes ? bytes : 16, s) != cudaSuccess) return false;
+        return !bytes || cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    };
+    bool ok = up((void **)&b->desc, hd.data(), hd.size() * sizeof(PbDesc)) &&
+              up((void **)&b->blk, hblk.data(), hblk.size() * sizeof(int2)) &&
+              up((void **)&b->pc, hpc.data(), hpc.size() * sizeof(int2)) &&
+              up((void **)&b->gemv, hgemv.data(), hgemv.size() * sizeof(int2)) &&
+              cudaStreamSynchronize(s) == cudaSuccess;
+    if (!ok) {
+        bpb_free(b, s);
+        return ctx_fail(ctx, DDM_ENOMEM, "batched preconditioner: work list allocation failed");
+    }
+    *out = b;
+    return DDM_OK;
+}
+
+ddm_status bpb_launch(ddm_ctx *ctx, BatchPb *b, cudaStream_t s) {
+    int launches = 0;
+    if (b->n_blk > 0) {
+        k_pb_apply_b<<<dim3((unsigned)b->n_blk, PA_S), PA_T, 0, s>>>(b->desc, b->blk, b->nc);
+        ++launches;
+    }
+    if (b->n_pc > 0) {
+        k_pc_restrict_b<<<(unsigned)b->n_pc, 64, 0, s>>>(b->desc, b->pc, b->nc);
+        k_pc_gemv_b<<<(unsigned)b->n_gemv, 256, 0, s>>>(b->desc, b->gemv);
+        k_pc_prolong_b<<<(unsigned)b->n_pc, 64, 0, s>>>(b->desc, b->pc, b->nc);
+        launches += 3;
+    }
+    prof_end(ctx, 8, launches);
+    DDM_CUDA_TRY(ctx, cudaGetLastError());
+    return DDM_OK;
+}
 
 // prepare the inverted blocks of (dt, system) for tree t (cached)
 ddm_status pb_prepare(ddm_ctx *ctx, ddm_tree *t, double dt, int sys, cudaStream_t s) {
@@ -317,6 +758,36 @@ ddm_status pb_prepare(ddm_ctx *ctx, ddm_tree *t, double dt, int sys, cudaStream_
                                     t->pb_inv);
     k_pb_invert<<<(unsigned)t->n_pblk, dim3(32, 32), 0, s>>>(t->pb_off, t->pb_moff, nc, t->pb_inv);
     prof_end(ctx, 8, 4);
+    if (t->n_pc > 0) {
+        // coarse level: Galerkin matrix of the long chains' blocks, inverted
+        const int K = t->pc_modes;
+        const int64_t dim = t->n_pc * nc * K;
+        if (!t->pc_inv)
+            DDM_CUDA_TRY(ctx, dalloc(&t->pc_inv, ((size_t)t->n_pc * 3 * K * t->n_pc * 3 * K + 2 * t->n_pc * 3 * K) *
+                                                     sizeof(float), t->stream));
+        int32_t *piv = nullptr;
+        float *stage = nullptr;
+        DDM_CUDA_TRY(ctx, dalloc(&piv, (size_t)dim * sizeof(int32_t), s));
+        DDM_CUDA_TRY(ctx, dalloc(&stage, (size_t)(2 * dim + 1) * sizeof(float), s));
+        prof_begin(ctx, 8);
+        k_pc_assemble<<<dim3((unsigned)t->n_pc, (unsigned)t->n_pc), PC_T, 0, s>>>(
+            ctx->kf, wf, geo, selfblk, t->pb_off, t->pb_elem, t->pc_blk, nc, sys, K, dim, t->pc_inv);
+        int launches = 3;
+        if (dim <= GJ1_MAX) {
+            k_gj_cta<<<1, GJ_T, 0, s>>>(t->pc_inv, dim, piv);
+        } else {
+            const unsigned ug = (unsigned)((dim * dim + 255) / 256);
+            for (int64_t k = 0; k < dim; ++k) {
+                k_gj_pivot<<<1, GJ_T, 0, s>>>(t->pc_inv, dim, k, piv, stage, stage + dim, stage + 2 * dim);
+                k_gj_update<<<ug, 256, 0, s>>>(t->pc_inv, dim, k, stage, stage + dim, stage + 2 * dim);
+            }
+            launches = (int)(2 * dim + 2);
+        }
+        k_gj_unpivot<<<(unsigned)((dim + 255) / 256), 256, 0, s>>>(t->pc_inv, dim, piv);
+        prof_end(ctx, 8, launches);
+        dfree(piv, s);
+        dfree(stage, s);
+    }
     dfree(geo, s);
     DDM_CUDA_TRY(ctx, cudaGetLastError());
     t->pb_dt = dt;
@@ -329,6 +800,15 @@ ddm_status pb_apply(ddm_ctx *ctx, ddm_tree *t, int sys, const double *v, double 
     int nc = sys == DDM_SYS_PRESSURE ? 3 : 2;
     k_pb_apply<<<dim3((unsigned)t->n_pblk, PA_S), PA_T, 0, s>>>(t->pb_off, t->pb_elem, t->pb_moff, nc, t->pb_inv, v, t->n, z, 1);
     prof_end(ctx, 8, 1);
+    if (t->n_pc > 0) {             // + Z A_c^-1 Z^T v
+        const int K = t->pc_modes;
+        const int64_t dim = t->n_pc * nc * K;
+        float *rc = t->pc_inv + (size_t)t->n_pc * 3 * K * t->n_pc * 3 * K, *yc = rc + t->n_pc * 3 * K;
+        k_pc_restrict<<<(unsigned)t->n_pc, 64, 0, s>>>(v, t->n, t->pb_off, t->pb_elem, t->pc_blk, nc, K, rc);
+        k_pc_gemv<<<(unsigned)((dim + 7) / 8), 256, 0, s>>>(t->pc_inv, rc, dim, yc);
+        k_pc_prolong<<<(unsigned)t->n_pc, 64, 0, s>>>(yc, t->n, t->pb_off, t->pb_elem, t->pc_blk, nc, K, z);
+        prof_end(ctx, 8, 3);
+    }
     DDM_CUDA_TRY(ctx, cudaGetLastError());
     return DDM_OK;
 }

@@ -458,6 +458,8 @@ __global__ void k_p2p_count(const int32_t *cstart, const int32_t *cend, int64_t 
 struct Chains {
     std::vector<int32_t> boff{0};
     std::vector<int64_t> belem;
+    std::vector<int32_t> chain_blk0{0};   // first block of every chain (CSR over chains)
+    std::vector<int32_t> pc;              // coarse-level blocks (upload source, lives until the build ends)
 };
 static void find_chains(const double *hxy, int64_t n, Chains &out) {
     std::vector<int32_t> &boff = out.boff;
@@ -509,6 +511,7 @@ static void find_chains(const double *hxy, int64_t n, Chains &out) {
             }
         }
         if (cnt) boff.push_back((int32_t)belem.size());
+        out.chain_blk0.push_back((int32_t)boff.size() - 1);
     };
     for (int64_t e = 0; e < n; ++e)
         if (!prevc[e]) emit_chain(e);
@@ -518,7 +521,7 @@ static void find_chains(const double *hxy, int64_t n, Chains &out) {
 
 void tree_free(ddm_tree *t) {
     if (!t) return;
-    void *ps[] = {t->mk_work, t->pb_off, t->pb_elem, t->pb_moff, t->pb_inv, t->mk_off, t->mk_pair, t->perm, t->cell_key, t->cell_ix, t->cell_iy, t->cell_start, t->cell_end, t->cell_parent,
+    void *ps[] = {t->mk_work, t->pb_off, t->pb_elem, t->pb_moff, t->pb_inv, t->pc_blk, t->pc_inv, t->mk_off, t->mk_pair, t->perm, t->cell_key, t->cell_ix, t->cell_iy, t->cell_start, t->cell_end, t->cell_parent,
                   t->il_off, t->il_idx, t->nb_off, t->nb_idx, t->nb_tab, t->near_items, t->elem_leaf, t->g_rel, t->g_frame,
                   t->xy_sorted, t->xy_caller, t->W, t->Fl, t->far4, t->chg};
     for (void *p : ps) dfree(p, t->stream);
@@ -527,12 +530,13 @@ void tree_free(ddm_tree *t) {
     delete t;
 }
 
-ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **out) {
+ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, const ddm_fmm_params &prm, ddm_tree **out) {
     if (!ctx || !d_xy || !out || n <= 0 || n > (int64_t)1 << 30)
         return ctx_fail(ctx, DDM_EINVAL, "ddm_build_tree: bad arguments");
     cudaStream_t st = ctx->stream;
     ddm_tree *t = new ddm_tree();
     t->n = n;
+    t->prm = prm;
     Scratch S;
     S.st = st;
     t->stream = st;
@@ -604,7 +608,7 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
     // longest element is at most a quarter of a leaf
     int Lcap = (int)std::floor(std::log2(2.0 * h0 / (4.0 * lmax)) + 1e-12);
     Lcap = std::max(0, std::min(Lcap, KEY_LEVELS));
-    if (ctx->prm.max_depth > 0) Lcap = std::min(Lcap, ctx->prm.max_depth);
+    if (prm.max_depth > 0) Lcap = std::min(Lcap, prm.max_depth);
     int32_t *runmax = S.get<int32_t>(KEY_LEVELS + 1);
     TRY(S.err);
     TRY(cudaMemsetAsync(runmax, 0, (KEY_LEVELS + 1) * sizeof(int32_t), st));
@@ -614,7 +618,7 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
     TRY(cudaStreamSynchronize(st));
     int L = Lcap;
     for (int l = 0; l <= Lcap; ++l)
-        if (hrun[l] <= ctx->prm.leaf_size) { L = l; break; }
+        if (hrun[l] <= prm.leaf_size) { L = l; break; }
     t->depth = L;
 
     // cells of every level
@@ -677,7 +681,7 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
     // pairs.  Costs per unit measured on GB300 for n = 8 (near pair 19.4 ps,
     // interaction pair 3.5 ns scaling with n^4, cell 25 ns).
     int32_t *il_cnt = nullptr;                 // interaction-list counts of the depth choice, kept
-    if (L >= 3 && ctx->prm.max_depth == 0) {
+    if (L >= 3 && prm.max_depth == 0) {
         const int L0 = std::max(2, L - 4), NCAND = L - L0 + 1;
         int32_t *ccnt = S.get<int32_t>(NC + 1);
         il_cnt = ccnt;
@@ -700,7 +704,7 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
         std::vector<unsigned long long> hs(2 * (L + 1));
         TRY(cudaMemcpyAsync(hs.data(), dsum, hs.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
         TRY(cudaStreamSynchronize(st));
-        double nfac = std::pow(ctx->prm.n_cheb / 8.0, 4.0);
+        double nfac = std::pow(prm.n_cheb / 8.0, 4.0);
         double best = 1e300;
         int bestL = L;
         (void)NCAND;
@@ -860,6 +864,22 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **ou
         t->pb_inv = nullptr;
         t->pb_dt = -1.0;
         t->pb_sys = -1;
+        // coarse level: the blocks of every chain of at least PC_MIN_BLOCKS blocks
+        std::vector<int32_t> &pc = chains.pc;
+        for (size_t c = 0; c + 1 < chains.chain_blk0.size(); ++c)
+            if (chains.chain_blk0[c + 1] - chains.chain_blk0[c] >= PC_MIN_BLOCKS)
+                for (int32_t b = chains.chain_blk0[c]; b < chains.chain_blk0[c + 1]; ++b) pc.push_back(b);
+        t->n_pc = (int64_t)pc.size();
+        t->pc_modes = 0;
+        for (int k = PC_MODES; k >= 1 && !t->pc_modes; --k)
+            if (t->n_pc * 3 * k <= PC_MAX_DIM) t->pc_modes = k;
+        if (!t->pc_modes) t->n_pc = 0;
+        t->pc_blk = nullptr;
+        t->pc_inv = nullptr;
+        if (t->n_pc) {
+            TRY(dalloc(&t->pc_blk, pc.size() * sizeof(int32_t), st));
+            TRY(cudaMemcpyAsync(t->pc_blk, pc.data(), pc.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        }
     }
     unsigned long long *ptot = S.get<unsigned long long>(1);
     TRY(S.err);

@@ -29,7 +29,7 @@ EXPORTS = ("ddm_create", "ddm_destroy", "ddm_last_error", "ddm_device_check", "d
            "ddm_tree_get_info", "ddm_matvec", "ddm_history_apply", "ddm_rhs", "ddm_gmres_solve", "ddm_sif",
            "ddm_profile", "ddm_profile_read", "ddm_batch_create", "ddm_batch_destroy", "ddm_batch_matvec",
            "ddm_batch_gmres_solve", "ddm_server_create", "ddm_submit", "ddm_poll", "ddm_server_destroy",
-           "ddm_matvec_dense_static", "ddm_set_wait_limit")
+           "ddm_matvec_dense_static", "ddm_set_wait_limit", "ddm_build_tree_params", "ddm_autotune")
 STATIC_MAX_ELEMENTS = 65536
 NSTAGES = 10
 STAGES = ("prep", "self_blocks", "up", "m2l_ops", "m2l", "down", "leaf", "dense", "krylov", "tree")
@@ -113,6 +113,11 @@ def load(build_if_missing: bool = True):
         L.ddm_sif.argtypes = [_VP, _VP, _VP, _VP, ctypes.c_int, _VP, _VP]
         L.ddm_profile.argtypes = [_VP, ctypes.c_int]
         L.ddm_set_wait_limit.argtypes = [_VP, ctypes.c_int64]
+        L.ddm_build_tree_params.argtypes = [_VP, _VP, ctypes.c_int64, ctypes.POINTER(ddm_fmm_params), ctypes.POINTER(_VP)]
+        L.ddm_autotune.argtypes = [_VP, _VP, ctypes.c_int64, _VP, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
+                                   ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_double,
+                                   ctypes.POINTER(ddm_fmm_params), ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double)]
         L.ddm_matvec_dense_static.argtypes = [_VP, _VP, ctypes.c_int64, ctypes.c_double, ctypes.c_double, _VP, _VP]
         L.ddm_server_create.argtypes = [_VP, ctypes.c_size_t, ctypes.c_int, ctypes.c_double, ctypes.POINTER(_VP)]
         L.ddm_submit.argtypes = [_VP, ctypes.POINTER(ddm_request), ctypes.POINTER(ctypes.c_uint64)]
@@ -179,6 +184,30 @@ def ddm_build_tree(ctx, xy: torch.Tensor):
     out = _VP()
     _check(ctx, load().ddm_build_tree(ctx, _VP(_dev(xy, 4 * n, "xy")), n, ctypes.byref(out)), "ddm_build_tree")
     return out
+
+
+def ddm_build_tree_params(ctx, xy: torch.Tensor, n_cheb=0, leaf_size=0, max_depth=0, quad_near=0):
+    """Tree with its own FMM parameters (0 = the context's)."""
+    n = xy.numel() // 4
+    out = _VP()
+    prm = ddm_fmm_params(int(n_cheb), int(leaf_size), int(max_depth), int(quad_near))
+    _check(ctx, load().ddm_build_tree_params(ctx, _VP(_dev(xy, 4 * n, "xy")), n, ctypes.byref(prm), ctypes.byref(out)),
+           "ddm_build_tree_params")
+    return out
+
+
+def ddm_autotune(ctx, xy: torch.Tensor, x: torch.Tensor, dt, orders=None, leaves=None, max_rel_err=1e-3) -> dict:
+    """Fastest (order, leaf size) for this problem within the error bound."""
+    n = xy.numel() // 4
+    o = (ctypes.c_int * len(orders))(*orders) if orders else None
+    lv = (ctypes.c_int * len(leaves))(*leaves) if leaves else None
+    best = ddm_fmm_params()
+    ms, err = ctypes.c_double(), ctypes.c_double()
+    _check(ctx, load().ddm_autotune(ctx, _VP(_dev(xy, 4 * n, "xy")), n, _VP(_dev(x, 3 * n, "x")), float(dt), o,
+                                    len(orders) if orders else 0, lv, len(leaves) if leaves else 0,
+                                    float(max_rel_err), ctypes.byref(best), ctypes.byref(ms), ctypes.byref(err)),
+           "ddm_autotune")
+    return {"n_cheb": best.n_cheb, "leaf_size": best.leaf_size, "ms": ms.value, "err": err.value}
 
 
 def ddm_tree_destroy(tree):
@@ -261,7 +290,7 @@ def ddm_matvec_dense_static(ctx, xy, tau_lo, tau_hi, x, y):
     n = xy.numel() // 4
     _check(ctx, load().ddm_matvec_dense_static(ctx, _VP(_dev(xy, 4 * n, "xy")), n, float(tau_lo), float(tau_hi),
                                                _VP(_dev(x, 3 * n, "x")), _VP(_dev(y, 3 * n, "y"))),
-           "ddm_matvec_dense_static", "ddm_set_wait_limit")
+           "ddm_matvec_dense_static")
 
 
 def ddm_batch_create(ctx, trees):
@@ -353,10 +382,13 @@ class Server:
 
 # ---------------------------------------------------------------- wrappers
 class Tree:
-    def __init__(self, ctx: "Context", xy: torch.Tensor):
+    def __init__(self, ctx: "Context", xy: torch.Tensor, n_cheb=0, leaf_size=0):
         self.ctx = ctx
         self.n = xy.numel() // 4
-        self.ptr = ddm_build_tree(ctx.ptr, xy)
+        if n_cheb or leaf_size:
+            self.ptr = ddm_build_tree_params(ctx.ptr, xy, n_cheb, leaf_size)
+        else:
+            self.ptr = ddm_build_tree(ctx.ptr, xy)
 
     def info(self) -> dict:
         return ddm_tree_get_info(self.ptr)
@@ -415,8 +447,11 @@ class Context:
     def __init__(self, material, n_cheb=8, leaf_size=32, max_depth=0, quad_near=6, stream=None):
         self.ptr = ddm_create(material, n_cheb, leaf_size, max_depth, quad_near, stream)
 
-    def build_tree(self, xy: torch.Tensor) -> Tree:
-        return Tree(self, xy.contiguous())
+    def build_tree(self, xy: torch.Tensor, n_cheb=0, leaf_size=0) -> Tree:
+        return Tree(self, xy.contiguous(), n_cheb, leaf_size)
+
+    def autotune(self, xy: torch.Tensor, x: torch.Tensor, dt, orders=None, leaves=None, max_rel_err=1e-3) -> dict:
+        return ddm_autotune(self.ptr, xy.contiguous(), x, dt, orders, leaves, max_rel_err)
 
     def matvec(self, tree: Tree, x, tau_lo=0.0, tau_hi=1.0, mode="fmm", out=None):
         out = torch.empty_like(x) if out is None else out

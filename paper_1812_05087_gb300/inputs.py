@@ -121,17 +121,20 @@ def parallel_fractures(n_frac=10, spacing=20.0, half_length=100.0, elems=2000):
 
 
 # Horizontal-well example (paper Sec. 5, Table 2): in-situ stresses and
-# initial pore pressure; constant injection per fracture (per unit
-# thickness) split uniformly along the fracture, time steps of 60 s.
+# initial pore pressure; a constant injection of 0.01 m^3/s per fracture,
+# carried by the plane-strain model per unit thickness over a fracture
+# height of 100 m and split uniformly along the fracture; time steps of 60 s.
 WELL_LOADS = {"sigma_H": 58.60e6, "sigma_h": 55.15e6, "p0": 48.26e6}
 WELL_INJECTION = 0.01     # m^3/s per fracture
+WELL_HEIGHT = 100.0       # m
 WELL_DT = 60.0
 
 
-def well_source(half_length=100.0, injection=WELL_INJECTION):
+def well_source(half_length=100.0, injection=WELL_INJECTION, height=WELL_HEIGHT):
     """Fluid source per unit element length (m^2/s per m) of a fracture of
-    the given half-length carrying `injection` split uniformly."""
-    return injection / (2.0 * half_length)
+    the given half-length carrying `injection` over `height`, split
+    uniformly."""
+    return injection / (height * 2.0 * half_length)
 
 
 def batch_problems(n_problems=512, nmin=100, nmax=20000, seed=SEED + 4):

@@ -3,7 +3,8 @@ horizontal-well instance (paper Sec. 5 example, geometry of the
 multi-stage configuration scaled down): 10 parallel fractures at 20 m
 spacing, half-length 100 m, 40 constant elements each; RATE system (rows
 sigma_s and sigma_n + p, the fluid source prescribed by the injection of
-0.01 m^3/s per fracture split uniformly); Table 2 stresses and initial pore
+0.01 m^3/s per fracture over a 100 m fracture height, split uniformly
+along the fracture); Table 2 stresses and initial pore
 pressure; 100 time steps of 60 s, the history of all previous steps
 subtracted at every step (oracle.march: dense matrices, direct solves).
 
@@ -41,6 +42,7 @@ def main():
                   "paper Sec. 5 example, Table 2 loads; written by tests/golden/make_well_march.py",
         "n_frac": N_FRAC, "elems": ELEMS, "spacing": 20.0, "half_length": 100.0, "dt": inputs.WELL_DT,
         "steps": STEPS, "loads": inputs.WELL_LOADS, "injection": inputs.WELL_INJECTION,
+        "height": inputs.WELL_HEIGHT,
         "tips": tips.tolist(),
         "D": {str(h): [float("%.13e" % v) for v in sols[h - 1][:2 * N]] for h in KEEP_D},
         "KI": {}, "KII": {},

@@ -64,3 +64,45 @@ def test_batch_gmres_equals_alone_and_oracle(ctx, system):
             ref = oracle.solve(oracle.assemble(MAT, g, 10.0),
                                oracle.rhs(g, sigma_H=3e6, sigma_h=2e6, p_f=5e6, system=system), n, system)
             assert block_rel_err(seg, ref, n, nb) < 1e-3
+
+
+def test_batch_mixed_orders_equals_alone(ctx):
+    """Trees with their own Chebyshev orders and leaf sizes in one batch:
+    the batched product (one work list per order) equals every problem's
+    product alone, and a tree built with order 12 gives the product of a
+    context of order 12."""
+    geos = problems()
+    prm = [(6, 16), (8, 32), (12, 16), (8, 16), (10, 64)]
+    trees = [ctx.build_tree(dev(g), n_cheb=o, leaf_size=lf) for g, (o, lf) in zip(geos, prm)]
+    xs = [inputs.unknowns(g.shape[1], seed=17 + i) for i, g in enumerate(geos)]
+    batch = ctx.batch(trees)
+    y = batch.matvec(dev(np.concatenate(xs)), 10.0, mode="fmm").cpu().numpy()
+    for i, (t, g) in enumerate(zip(trees, geos)):
+        alone = ctx.matvec(t, dev(xs[i]), 0.0, 10.0, mode="fmm").cpu().numpy()
+        assert block_rel_err(y[batch.offsets[i]:batch.offsets[i + 1]], alone, g.shape[1]) < 1e-5
+    c12 = Context(inputs.MATERIAL, n_cheb=12, leaf_size=16)
+    t12 = c12.build_tree(dev(geos[2]))
+    ref12 = c12.matvec(t12, dev(xs[2]), 0.0, 10.0, mode="fmm").cpu().numpy()
+    got12 = ctx.matvec(trees[2], dev(xs[2]), 0.0, 10.0, mode="fmm").cpu().numpy()
+    assert block_rel_err(got12, ref12, geos[2].shape[1]) < 1e-5
+
+
+def test_autotune_meets_bound_and_oracle(ctx):
+    """The tuner's choice for a random fracture set meets its error bound
+    against the dense product, and its product matches the FP64 oracle."""
+    segs = inputs.random_fracture_segments(30, 40.0, 2.0, 8.0, 40, seed=123)
+    g = inputs.assemble(segs)
+    n = g.shape[1]
+    x = inputs.unknowns(n, seed=5)
+    best = ctx.autotune(dev(g), dev(x), 10.0, orders=[4, 6, 8], leaves=[16, 32], max_rel_err=1e-4)
+    assert best["n_cheb"] in (4, 6, 8) and best["leaf_size"] in (16, 32)
+    assert best["err"] <= 1e-4 and best["ms"] > 0
+    t = ctx.build_tree(dev(g), n_cheb=best["n_cheb"], leaf_size=best["leaf_size"])
+    y = ctx.matvec(t, dev(x), 0.0, 10.0, mode="fmm").cpu().numpy()
+    rows = np.arange(0, n, 97)
+    el_rows = np.concatenate([rows + b * n for b in range(3)])
+    ref = oracle.matvec(MAT, g, x, 0.0, 10.0, rows=el_rows)
+    k = rows.size
+    for b in range(3):
+        r = ref[b * k:(b + 1) * k]
+        assert np.abs(y[el_rows][b * k:(b + 1) * k] - r).max() < 2e-4 * np.abs(r).max()
