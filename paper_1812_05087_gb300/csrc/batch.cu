@@ -326,6 +326,26 @@ ddm_status capture_seq(ddm_ctx *ctx, ddm_batch *B, cudaGraphExec_t *out, long lo
 
 inline unsigned seg_grid(int n) { return (unsigned)std::max(1, std::min(n, 152 * 8)); }
 
+// per-problem products (escalated precision) inside a capture, spread over
+// the batch's forked streams 1.. so that they overlap each other and the
+// batched stages on the capture stream and fork stream 0
+template <class Fn>
+ddm_status fork_each(ddm_ctx *ctx, ddm_batch *B, cudaStream_t cs, const std::vector<int> &idx, Fn fn) {
+    if (idx.empty()) return DDM_OK;
+    const int ns = std::max(1, std::min<int>(NSTREAMS - 1, (int)idx.size()));
+    DDM_CUDA_TRY(ctx, cudaEventRecord(B->ev_fork[0], cs));
+    for (int k = 0; k < ns; ++k) DDM_CUDA_TRY(ctx, cudaStreamWaitEvent(B->fork[1 + k], B->ev_fork[0], 0));
+    for (size_t q = 0; q < idx.size(); ++q) {
+        ddm_status e = fn(idx[q], B->fork[1 + q % ns]);
+        if (e) return e;
+    }
+    for (int k = 0; k < ns; ++k) {
+        DDM_CUDA_TRY(ctx, cudaEventRecord(B->ev_join[1 + k], B->fork[1 + k]));
+        DDM_CUDA_TRY(ctx, cudaStreamWaitEvent(cs, B->ev_join[1 + k], 0));
+    }
+    return DDM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -354,6 +374,7 @@ ddm_status ddm_batch_create(ddm_ctx *ctx, ddm_tree *const *trees, int n, ddm_bat
     for (int k = 0; k < NSTREAMS; ++k) {
         cudaStreamCreateWithFlags(&B->fork[k], cudaStreamNonBlocking);
         cudaEventCreateWithFlags(&B->ev_join[k], cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&B->ev_fork[k], cudaEventDisableTiming);
     }
     *out = B;
     return DDM_OK;
@@ -369,6 +390,7 @@ void ddm_batch_destroy(ddm_batch *B) {
     for (int k = 0; k < NSTREAMS; ++k) {
         if (B->fork[k]) cudaStreamDestroy(B->fork[k]);
         if (B->ev_join[k]) cudaEventDestroy(B->ev_join[k]);
+        if (B->ev_fork[k]) cudaEventDestroy(B->ev_fork[k]);
     }
     delete B;
 }
@@ -467,7 +489,8 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
     const int64_t L = B->L;
     // preconditioner blocks per problem (inverted fracture-chain blocks)
     for (int p = 0; p < P; ++p)
-        if ((st = pb_prepare(ctx, B->trees[p], dt, sys, s))) return st;
+        if ((st = pb_prepare(ctx, B->trees[p], dt, sys, s, true))) return st;
+    if ((st = pc_invert_many(ctx, B->trees.data(), P, s))) return st;
     // graphs: preconditioned operator vin -> w, residual operator (precise) x -> tmp
     int saved = ctx->prof.on;
     ctx->prof.on = 0;
@@ -500,11 +523,12 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
                 return e;
         return capture_seq(ctx, B, &B->g_op, &B->k_op, [&](cudaStream_t cs) -> ddm_status {
             ddm_status r = bpb_launch(ctx, B->bp, cs);
+            if (!r) r = fork_each(ctx, B, cs, prec, [&](int p, cudaStream_t ps) {
+                return op_apply(ctx, B->trees[p], 0.0, dt, B->full + B->off3[p], B->y3 + B->off3[p],
+                                mode | DDM_MODE_PRECISE, 0, 1.0, ps);
+            });
             for (BatchFmm *f : B->bf[1])
                 if (!r) r = bfmm_launch(ctx, f, cs, B->fork[0]);
-            for (int p : prec)
-                if (!r) r = op_apply(ctx, B->trees[p], 0.0, dt, B->full + B->off3[p], B->y3 + B->off3[p],
-                                     mode | DDM_MODE_PRECISE, 0, 1.0, cs);
             if (r) return r;
             k_restrict_bb<<<seg_grid(B->seg[1].n), BT, 0, cs>>>(B->seg[1].desc, B->seg[1].items, B->seg[1].n, sys);
             prof_end(ctx, 8, 1);
@@ -526,12 +550,12 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
         return capture_seq(ctx, B, &B->g_res, &B->k_res, [&](cudaStream_t cs) -> ddm_status {
             k_copy3_bb<<<seg_grid(B->seg[2].n), BT, 0, cs>>>(B->seg[2].desc, B->seg[2].items, B->seg[2].n, nc);
             prof_end(ctx, 8, 1);
-            ddm_status r = DDM_OK;
+            ddm_status r = fork_each(ctx, B, cs, other, [&](int p, cudaStream_t ps) {
+                return op_apply(ctx, B->trees[p], 0.0, dt, B->full + B->off3[p], B->y3 + B->off3[p],
+                                residual_mode(mode, level[p], B->N[p]), 0, 1.0, ps);
+            });
             for (BatchFmm *f : B->bf[2])
                 if (!r) r = bfmm_launch(ctx, f, cs, B->fork[0]);
-            for (int p : other)
-                if (!r) r = op_apply(ctx, B->trees[p], 0.0, dt, B->full + B->off3[p], B->y3 + B->off3[p],
-                                     residual_mode(mode, level[p], B->N[p]), 0, 1.0, cs);
             if (r) return r;
             k_restrict_bb<<<seg_grid(B->seg[3].n), BT, 0, cs>>>(B->seg[3].desc, B->seg[3].items, B->seg[3].n, sys);
             prof_end(ctx, 8, 1);

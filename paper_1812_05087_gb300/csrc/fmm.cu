@@ -1044,11 +1044,15 @@ __global__ void __launch_bounds__(NEAR_T, 4) k_near(KConst<float> k, KConst<doub
 // of dependent loads.  Close pairs are queued per (source, target) and
 // evaluated afterwards as units, as in k_near.  L2P runs separately
 // (k_l2p).
-__device__ __forceinline__ void near2_body(const KConst<float> &k, const Win<float> &w, const int32_t *nboff,
+// TWO: the window may start after 0 (history terms); otherwise t_lo = 0 is
+// known at compile time and the two-sided code paths drop out of the kernel
+template <bool TWO>
+__device__ __forceinline__ void near2_body(const KConst<float> &k, const Win<float> &win, const int32_t *nboff,
                                            const int4 *nbtab, const int32_t *elem_leaf, const float4 *grel,
                                            const float4 *frame, const float4 *chg, const int64_t *perm, float wL,
                                            int nq, const int2 *items, int64_t N, double scale, double *y,
                                            int64_t item) {
+    const Win<float> w = TWO ? win : Win<float>{win.ct_hi, 0.f, win.g_hi, 0.f, 1};
     constexpr unsigned FULL = 0xFFFFFFFFu;
     __shared__ int sst[NEAR_W][9], spre[NEAR_W][10];
     __shared__ float sox[NEAR_W][9], soy[NEAR_W][9];
@@ -1208,6 +1212,7 @@ __device__ __forceinline__ void near2_body(const KConst<float> &k, const Win<flo
     }
     y[row * N + eout] = yold + scale * ((double)vh + (double)vl);
 }
+template <bool TWO>
 __global__ void __launch_bounds__(NEAR_T, 4) k_near2(KConst<float> k, Win<float> w, const int32_t *nboff,
                                                      const int4 *nbtab, const int32_t *elem_leaf, const float4 *grel,
                                                      const float4 *frame, const float4 *chg, const int64_t *perm,
@@ -1215,7 +1220,7 @@ __global__ void __launch_bounds__(NEAR_T, 4) k_near2(KConst<float> k, Win<float>
                                                      double scale, double *y) {
     const int64_t item = (int64_t)blockIdx.x * NEAR_W + (threadIdx.x >> 5);
     if (item >= n_items) return;              // whole warp leaves together
-    near2_body(k, w, nboff, nbtab, elem_leaf, grel, frame, chg, perm, wL, nq, items, N, scale, y, item);
+    near2_body<TWO>(k, w, nboff, nbtab, elem_leaf, grel, frame, chg, perm, wL, nq, items, N, scale, y, item);
 }
 
 // far field at the targets (from k_down) rotated to each target frame and
@@ -1634,7 +1639,7 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
             kf, ctx->kd, wf, wd, t->nb_off, t->nb_tab, t->elem_leaf, t->g_rel, t->g_frame, t->chg, t->perm, loff, wL,
             n, nq, t->Fl, 0, N, scale, y);
     else
-        k_near2<<<(unsigned)((t->n_items + NEAR_W - 1) / NEAR_W), NEAR_T, 0, s>>>(
+        (lo > 0.0 ? k_near2<true> : k_near2<false>)<<<(unsigned)((t->n_items + NEAR_W - 1) / NEAR_W), NEAR_T, 0, s>>>(
             kf, wf, t->nb_off, t->nb_tab, t->elem_leaf, t->g_rel, t->g_frame, t->chg, t->perm, wL, nq,
             t->near_items, t->n_items, N, scale, y);
     prof_end(ctx, 6, 1);
@@ -1725,16 +1730,16 @@ __global__ void __launch_bounds__(tc::THREADS) k_m2l_tc_b(const BDesc *D, const 
     const BDesc &d = D[w.x];
     m2l_body(d.mk_work, d.mk_off, d.mk_pair, n, d.ops, d.W, d.Fl, err, w.y);
 }
+template <bool TWO>
 __global__ void __launch_bounds__(NEAR_T, 4) k_near2_b(KConst<float> k, Win<float> win, const BDesc *D,
                                                        const int2 *items, int64_t nitems, double scale) {
-    for (int64_t g = (int64_t)blockIdx.x * NEAR_W + (threadIdx.x >> 5); g < nitems;
-         g += (int64_t)gridDim.x * NEAR_W) {
-        const int2 w = items[g];
-        const BDesc &d = D[w.x];
-        near2_body(k, win, d.nb_off, d.nb_tab, d.elem_leaf, d.g_rel, d.g_frame, d.chg, d.perm, d.wL, d.nq,
-                   d.near_items, d.n, scale, d.y, w.y);
-        __syncwarp();                         // the warp's shared rows are reused by its next item
-    }
+    // one item per warp (a loop over items would cost the body registers)
+    const int64_t g = (int64_t)blockIdx.x * NEAR_W + (threadIdx.x >> 5);
+    if (g >= nitems) return;
+    const int2 w = items[g];
+    const BDesc &d = D[w.x];
+    near2_body<TWO>(k, win, d.nb_off, d.nb_tab, d.elem_leaf, d.g_rel, d.g_frame, d.chg, d.perm, d.wL, d.nq,
+                    d.near_items, d.n, scale, d.y, w.y);
 }
 // items (p, 0, a, b): far field of elements [a, b) into y
 __global__ void __launch_bounds__(BE_T) k_far_add_b(const BDesc *D, const int4 *items, int nitems, double scale) {
@@ -1887,7 +1892,8 @@ ddm_status bfmm_launch(ddm_ctx *ctx, BatchFmm *b, cudaStream_t s, cudaStream_t a
         if (aux) DDM_CUDA_TRY(ctx, cudaEventRecord(b->ev_join, fs));
     }
     if (b->n_near > 0) {
-        k_near2_b<<<grid((b->n_near + NEAR_W - 1) / NEAR_W, 4), NEAR_T, 0, s>>>(
+        auto kn = b->lo > 0.0 ? k_near2_b<true> : k_near2_b<false>;
+        kn<<<(unsigned)((b->n_near + NEAR_W - 1) / NEAR_W), NEAR_T, 0, s>>>(
             ctx->kf, make_win<float>(ctx, b->lo, b->hi), b->desc, b->near, b->n_near, 1.0);
         ++launches;
     }

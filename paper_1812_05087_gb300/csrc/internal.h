@@ -87,6 +87,7 @@ struct ddm_tree {
     int pc_modes;
     int32_t *pc_blk;           // block index of every coarse block
     float *pc_inv;
+    bool pc_pending = false;   // coarse matrix assembled, not yet inverted
     // M2L pairs grouped by (level, cell offset): key = level * 49 + (dx+3)*7 + (dy+3)
     int n_keys;                // (L + 1) * 49
     int32_t *mk_off;           // CSR over keys
@@ -232,7 +233,9 @@ ddm_status bfmm_launch(ddm_ctx *ctx, BatchFmm *b, cudaStream_t s, cudaStream_t a
 void bfmm_free(BatchFmm *b, cudaStream_t s);
 ddm_status upload_tables(ddm_ctx *ctx);
 // precond.cu: chain-block Jacobi preconditioner (cached per dt and system)
-ddm_status pb_prepare(ddm_ctx *ctx, ddm_tree *t, double dt, int sys, cudaStream_t s);
+ddm_status pb_prepare(ddm_ctx *ctx, ddm_tree *t, double dt, int sys, cudaStream_t s, bool defer_coarse = false);
+// invert the pending coarse matrices of many trees together
+ddm_status pc_invert_many(ddm_ctx *ctx, ddm_tree *const *trees, int count, cudaStream_t s);
 ddm_status pb_apply(ddm_ctx *ctx, ddm_tree *t, int sys, const double *v, double *z3, cudaStream_t s);
 // the same for many problems in one launch per stage (precond.cu)
 struct BatchPb;

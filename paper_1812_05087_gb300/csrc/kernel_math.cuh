@@ -278,22 +278,32 @@ DEV void pot_asym(const KConst<T> &k, T x, T y, T Pxx, T Pyy, T Pxy, T q, T d4ct
     acc[2] += fq * T(2) * xy - T(2) * f * R;
 }
 
+// Time element (t_lo > 0) with u >= 1 on both sides (the hi side has the
+// smaller u): the polynomial parts of the two sides in closed form, plus
+// each side's exponentially small remainder.  Evaluated side by side, the
+// two sides' common t-free term (the undrained - drained difference) would
+// cancel and take the small window difference with it.  (Kernels that only
+// see windows starting at 0 instantiate with t_lo known to be 0, which
+// removes this branch from their code.)
+template <class T>
+DEV Quad<T> pot_window_rem(KConst<T> k, T x, T y, T Pxx, T Pyy, T Pxy, T q, Win<T> w) {
+    const T r2 = x * x + y * y, ir2 = T(1) / r2;
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    pot_asym<T>(k, x, y, Pxx, Pyy, Pxy, q, T(4) * (w.ct_hi - w.ct_lo), acc);
+    if (r2 * w.g_hi <= Big<T>::U) {
+        pot_transient<T, true>(k, x, y, ir2, Pxx, Pyy, Pxy, q, w.g_hi, T(4) * w.ct_hi, T(1), acc);
+        pot_transient<T, true>(k, x, y, ir2, Pxx, Pyy, Pxy, q, w.g_lo, T(4) * w.ct_lo, T(-1), acc);
+    }
+    return Quad<T>{acc[0], acc[1], acc[2], acc[3]};
+}
+
 template <class T>
 DEV void pot_kernel(const KConst<T> &k, T x, T y, T Pxx, T Pyy, T Pxy, T q, const Win<T> &w,
                     T acc[4]) {
     T ir2 = T(1) / (x * x + y * y);
     if (w.ct_lo > T(0) && (x * x + y * y) * w.g_hi >= T(1)) {
-        // time element (t_lo > 0), u >= 1 on both sides (the hi side has the
-        // smaller u): the polynomial parts of the two sides in closed form,
-        // plus each side's exponentially small remainder.  Evaluated side by
-        // side, the two sides' common t-free term (the undrained - drained
-        // difference) would cancel and take the small window difference with
-        // it.
-        pot_asym<T>(k, x, y, Pxx, Pyy, Pxy, q, T(4) * (w.ct_hi - w.ct_lo), acc);
-        if ((x * x + y * y) * w.g_hi <= Big<T>::U) {
-            pot_transient<T, true>(k, x, y, ir2, Pxx, Pyy, Pxy, q, w.g_hi, T(4) * w.ct_hi, T(1), acc);
-            pot_transient<T, true>(k, x, y, ir2, Pxx, Pyy, Pxy, q, w.g_lo, T(4) * w.ct_lo, T(-1), acc);
-        }
+        const Quad<T> r = pot_window_rem<T>(k, x, y, Pxx, Pyy, Pxy, q, w);
+        acc[0] += r.a; acc[1] += r.b; acc[2] += r.c; acc[3] += r.d;
         return;
     }
     if (w.elastic) {
@@ -373,6 +383,31 @@ DEV void disl_transient(const KConst<T> &k, T zx, T zy, T ir2, T Dx, T Dy, T g0c
     acc[3] -= s * k.aS * k.Ce * l * ir2 * (u * F0);      // 1 - e^-u = u F(u)
 }
 
+// u >= 1 on both sides of a time element (the hi side has the smaller u).
+// Written with the large-u forms of the transient functions (F0 = 1/u,
+// F1 = -1/u^2, F2 = 2/u^3, e^-u = 0), each side is the same t-independent
+// term (the undrained - drained difference) plus a term linear in 4ct/r^2;
+// the former cancels exactly between the sides, and evaluated side by side
+// it would cost ~log10(u) digits.  What is left of the polynomial part,
+// written out: 2 G2 K2 (4 ct_hi - 4 ct_lo) / r^4 times the dislocation's
+// angular factors (the pressure terms cancel); then each side's
+// exponentially small remainder (zero beyond u = Big).
+template <class T>
+DEV Quad<T> disl_window_rem(KConst<T> k, T zx, T zy, T Dx, T Dy, Win<T> w, T s) {
+    const T r2 = zx * zx + zy * zy, ir2 = T(1) / r2;
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    const T l = Dx * zy - Dy * zx;
+    const T f = s * T(8) * k.G2 * k.K2 * (w.ct_hi - w.ct_lo) * ir2 * ir2;
+    acc[0] -= f * (T(2) * Dx * zy + l - T(4) * l * zy * zy * ir2);
+    acc[1] -= f * (l - T(2) * Dy * zx - T(4) * l * zx * zx * ir2);
+    acc[2] += f * (Dx * zx - Dy * zy - T(4) * l * zx * zy * ir2);
+    if (r2 * w.g_hi <= Big<T>::U) {
+        disl_transient<T, true>(k, zx, zy, ir2, Dx, Dy, w.g_hi, T(4) * w.ct_hi, s, acc);
+        disl_transient<T, true>(k, zx, zy, ir2, Dx, Dy, w.g_lo, T(4) * w.ct_lo, -s, acc);
+    }
+    return Quad<T>{acc[0], acc[1], acc[2], acc[3]};
+}
+
 template <class T>
 DEV void disl_field(const KConst<T> &k, T zx, T zy, T Dx, T Dy, const Win<T> &w, T s, T acc[4]) {
     T ir2 = T(1) / (zx * zx + zy * zy);
@@ -385,25 +420,8 @@ DEV void disl_field(const KConst<T> &k, T zx, T zy, T Dx, T Dy, const Win<T> &w,
     }
     const int sides = w.ct_lo > T(0) ? 2 : 1;
     if (sides == 2 && (zx * zx + zy * zy) * w.g_hi >= T(1)) {
-        // u >= 1 on both sides (the hi side has the smaller u).  Written with
-        // the large-u forms of the transient functions (F0 = 1/u,
-        // F1 = -1/u^2, F2 = 2/u^3, e^-u = 0), each side is the same
-        // t-independent term (the undrained - drained difference) plus a term
-        // linear in 4ct/r^2; the former cancels exactly between the sides,
-        // and evaluated side by side it would cost ~log10(u) digits.  What is
-        // left of the polynomial part, written out: 2 G2 K2 (4 ct_hi -
-        // 4 ct_lo) / r^4 times the dislocation's angular factors (the
-        // pressure terms cancel); then each side's exponentially small
-        // remainder (zero beyond u = Big).
-        const T l = Dx * zy - Dy * zx;
-        const T f = s * T(8) * k.G2 * k.K2 * (w.ct_hi - w.ct_lo) * ir2 * ir2;
-        acc[0] -= f * (T(2) * Dx * zy + l - T(4) * l * zy * zy * ir2);
-        acc[1] -= f * (l - T(2) * Dy * zx - T(4) * l * zx * zx * ir2);
-        acc[2] += f * (Dx * zx - Dy * zy - T(4) * l * zx * zy * ir2);
-        if ((zx * zx + zy * zy) * w.g_hi <= Big<T>::U) {
-            disl_transient<T, true>(k, zx, zy, ir2, Dx, Dy, w.g_hi, T(4) * w.ct_hi, s, acc);
-            disl_transient<T, true>(k, zx, zy, ir2, Dx, Dy, w.g_lo, T(4) * w.ct_lo, -s, acc);
-        }
+        const Quad<T> r = disl_window_rem<T>(k, zx, zy, Dx, Dy, w, s);
+        acc[0] += r.a; acc[1] += r.b; acc[2] += r.c; acc[3] += r.d;
         return;
     }
 #pragma unroll 1

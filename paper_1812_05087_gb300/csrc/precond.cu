@@ -22,6 +22,7 @@
 // wavelength modes of a long fracture (and the coupling between parallel
 // fractures) to the Krylov iteration, whose count then grows with the chain
 // length; the coarse level carries them.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -379,14 +380,26 @@ __global__ void __launch_bounds__(PC_T) k_pc_assemble(KConst<float> kf, Win<floa
     }
 }
 
-// In-place Gauss-Jordan inversion of the coarse matrix (FP32, partial
-// pivoting), one step per pair of launches: the pivot kernel (one CTA)
-// swaps the pivot row into place and stages row k (scaled by 1/pivot) and
-// column k; the update kernel then rewrites every entry from the staged
-// copies, so that no entry is read after it was overwritten.
+// In-place Gauss-Jordan inversion of the coarse matrices (FP32, partial
+// pivoting).  For one step k the pivot kernel swaps the pivot row into
+// place and stages row k (scaled by 1/pivot) and column k; the update
+// kernel then rewrites every entry from the staged copies, so that no entry
+// is read after it was overwritten.
 constexpr int GJ_T = 1024;
-__global__ void __launch_bounds__(GJ_T) k_gj_pivot(float *A, int64_t n, int64_t k, int32_t *piv, float *rowk,
-                                                   float *colk, float *ipiv) {
+// The same steps for many coarse matrices at once: at step k the problems
+// whose dimension exceeds k (a prefix: they are sorted by dimension,
+// largest first) take part; one CTA per problem stages its pivot row and
+// column, then one flat grid over all their entries updates them.
+struct GjDesc {
+    float *A;          // dim x dim, row-major
+    float *stage;      // 2 dim + 1: row k / pivot, column k, 1 / pivot
+    int32_t *piv;
+    int64_t dim;
+};
+__global__ void __launch_bounds__(GJ_T) k_gjb_pivot(const GjDesc *D, int64_t k) {
+    const GjDesc d = D[blockIdx.x];
+    float *A = d.A;
+    const int64_t n = d.dim;
     __shared__ float bv[GJ_T / 32];
     __shared__ int64_t bi[GJ_T / 32];
     __shared__ int64_t s_p;
@@ -411,7 +424,7 @@ __global__ void __launch_bounds__(GJ_T) k_gj_pivot(float *A, int64_t n, int64_t 
         for (int w = 1; w < GJ_T / 32; ++w)
             if (bv[w] > b || (bv[w] == b && bi[w] < p)) { b = bv[w]; p = bi[w]; }
         s_p = p;
-        piv[k] = (int32_t)p;
+        d.piv[k] = (int32_t)p;
     }
     __syncthreads();
     const int64_t p = s_p;
@@ -425,93 +438,38 @@ __global__ void __launch_bounds__(GJ_T) k_gj_pivot(float *A, int64_t n, int64_t 
     const float pv = A[k * n + k];
     const float ip = pv != 0.f ? 1.f / pv : 0.f;
     for (int64_t j = threadIdx.x; j < n; j += GJ_T) {
-        rowk[j] = A[k * n + j] * ip;
-        colk[j] = A[j * n + k];
+        d.stage[j] = A[k * n + j] * ip;
+        d.stage[n + j] = A[j * n + k];
     }
-    if (threadIdx.x == 0) *ipiv = ip;
+    if (threadIdx.x == 0) d.stage[2 * n] = ip;
 }
-__global__ void k_gj_update(float *A, int64_t n, int64_t k, const float *rowk, const float *colk, const float *ipiv) {
-    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (q >= n * n) return;
-    const int64_t i = q / n, j = q % n;
-    const float ip = *ipiv;
-    float v;
-    if (i == k) v = j == k ? ip : rowk[j];
-    else v = j == k ? -colk[i] * ip : fmaf(-colk[i], rowk[j], A[q]);
-    A[q] = v;
-}
-// The same Gauss-Jordan steps in one CTA (row k and column k staged in
-// shared memory), for coarse matrices of up to GJ1_MAX rows, where one
-// launch per step would cost more than the arithmetic.
-constexpr int GJ1_MAX = 1536;
-__global__ void __launch_bounds__(GJ_T) k_gj_cta(float *A, int64_t n, int32_t *piv) {
-    __shared__ float rowk[GJ1_MAX], colk[GJ1_MAX];
-    __shared__ float bv[GJ_T / 32];
-    __shared__ int64_t bi[GJ_T / 32];
-    __shared__ int64_t s_p;
-    __shared__ float s_ip;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t k = 0; k < n; ++k) {
-        float best = -1.f;
-        int64_t bidx = k;
-        for (int64_t i = k + threadIdx.x; i < n; i += GJ_T) {
-            const float v = fabsf(A[i * n + k]);
-            if (v > best) { best = v; bidx = i; }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ov = __shfl_xor_sync(0xFFFFFFFFu, best, o);
-            const int64_t oi = __shfl_xor_sync(0xFFFFFFFFu, bidx, o);
-            if (ov > best || (ov == best && oi < bidx)) { best = ov; bidx = oi; }
-        }
-        if (lane == 0) { bv[warp] = best; bi[warp] = bidx; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            float b = bv[0];
-            int64_t p = bi[0];
-            for (int w = 1; w < GJ_T / 32; ++w)
-                if (bv[w] > b || (bv[w] == b && bi[w] < p)) { b = bv[w]; p = bi[w]; }
-            s_p = p;
-            piv[k] = (int32_t)p;
-        }
-        __syncthreads();
-        const int64_t p = s_p;
-        if (p != k)
-            for (int64_t j = threadIdx.x; j < n; j += GJ_T) {
-                const float a = A[k * n + j];
-                A[k * n + j] = A[p * n + j];
-                A[p * n + j] = a;
-            }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const float pv = A[k * n + k];
-            s_ip = pv != 0.f ? 1.f / pv : 0.f;
-        }
-        __syncthreads();
-        const float ip = s_ip;
-        for (int64_t j = threadIdx.x; j < n; j += GJ_T) {
-            rowk[j] = A[k * n + j] * ip;
-            colk[j] = A[j * n + k];
-        }
-        __syncthreads();
-        for (int64_t q = threadIdx.x; q < n * n; q += GJ_T) {
-            const int64_t i = q / n, j = q % n;
-            float v;
-            if (i == k) v = j == k ? ip : rowk[j];
-            else v = j == k ? -colk[i] * ip : fmaf(-colk[i], rowk[j], A[q]);
-            A[q] = v;
-        }
-        __syncthreads();
+constexpr int GJB_CH = 2048;          // entries per CTA of the update
+__global__ void __launch_bounds__(256) k_gjb_update(const GjDesc *D, const int64_t *cum, int m, int64_t k) {
+    // the CTA's problem: first p with cum[p + 1] > blockIdx.x (cum[0] = 0)
+    int lo = 0, hi = m - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (cum[mid + 1] > (int64_t)blockIdx.x) hi = mid; else lo = mid + 1;
+    }
+    const GjDesc d = D[lo];
+    const int64_t n = d.dim, base = ((int64_t)blockIdx.x - cum[lo]) * GJB_CH;
+    const float ip = d.stage[2 * n];
+    for (int64_t q = base + threadIdx.x; q < base + GJB_CH && q < n * n; q += 256) {
+        const int64_t i = q / n, j = q % n;
+        float v;
+        if (i == k) v = j == k ? ip : d.stage[j];
+        else v = j == k ? -d.stage[n + i] * ip : fmaf(-d.stage[n + i], d.stage[j], d.A[q]);
+        d.A[q] = v;
     }
 }
-
-// undo the row interchanges as column swaps, in reverse order (a thread per row)
-__global__ void k_gj_unpivot(float *A, int64_t n, const int32_t *piv) {
+// column swaps of every problem, a thread per row (grid.y = problem)
+__global__ void k_gjb_unpivot(const GjDesc *D) {
+    const GjDesc d = D[blockIdx.y];
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float *row = A + i * n;
-    for (int64_t k = n - 1; k >= 0; --k) {
-        const int64_t p = piv[k];
+    if (i >= d.dim) return;
+    float *row = d.A + i * d.dim;
+    for (int64_t k = d.dim - 1; k >= 0; --k) {
+        const int64_t p = d.piv[k];
         if (p != k) { const float a = row[k]; row[k] = row[p]; row[p] = a; }
     }
 }
@@ -732,8 +690,65 @@ ddm_status bpb_launch(ddm_ctx *ctx, BatchPb *b, cudaStream_t s) {
     return DDM_OK;
 }
 
-// prepare the inverted blocks of (dt, system) for tree t (cached)
-ddm_status pb_prepare(ddm_ctx *ctx, ddm_tree *t, double dt, int sys, cudaStream_t s) {
+// invert the pending coarse matrices of the given trees together (batched
+// Gauss-Jordan: 2 max_dim + 1 launches for all of them)
+ddm_status pc_invert_many(ddm_ctx *ctx, ddm_tree *const *trees, int count, cudaStream_t s) {
+    std::vector<ddm_tree *> pend;
+    for (int i = 0; i < count; ++i)
+        if (trees[i]->n_pc > 0 && trees[i]->pc_pending) pend.push_back(trees[i]);
+    if (pend.empty()) return DDM_OK;
+    auto dim_of = [](const ddm_tree *t) { return t->n_pc * (t->pb_sys == DDM_SYS_PRESSURE ? 3 : 2) * t->pc_modes; };
+    std::sort(pend.begin(), pend.end(), [&](const ddm_tree *a, const ddm_tree *b) { return dim_of(a) > dim_of(b); });
+    const int P = (int)pend.size();
+    std::vector<GjDesc> hd(P);
+    std::vector<int64_t> dims(P), cum(P + 1, 0);
+    int64_t scratch = 0;
+    for (int p = 0; p < P; ++p) {
+        dims[p] = dim_of(pend[p]);
+        scratch += 2 * dims[p] + 1;
+    }
+    float *stage = nullptr;
+    int32_t *piv = nullptr;
+    GjDesc *dd = nullptr;
+    int64_t *dcum = nullptr;
+    int64_t tot_piv = 0;
+    for (int p = 0; p < P; ++p) tot_piv += dims[p];
+    DDM_CUDA_TRY(ctx, dalloc(&stage, (size_t)scratch * sizeof(float), s));
+    DDM_CUDA_TRY(ctx, dalloc(&piv, (size_t)tot_piv * sizeof(int32_t), s));
+    DDM_CUDA_TRY(ctx, dalloc(&dd, (size_t)P * sizeof(GjDesc), s));
+    DDM_CUDA_TRY(ctx, dalloc(&dcum, (size_t)(P + 1) * sizeof(int64_t), s));
+    int64_t so = 0, po = 0;
+    for (int p = 0; p < P; ++p) {
+        hd[p] = GjDesc{pend[p]->pc_inv, stage + so, piv + po, dims[p]};
+        so += 2 * dims[p] + 1;
+        po += dims[p];
+        cum[p + 1] = cum[p] + (dims[p] * dims[p] + GJB_CH - 1) / GJB_CH;
+    }
+    DDM_CUDA_TRY(ctx, cudaMemcpyAsync(dd, hd.data(), P * sizeof(GjDesc), cudaMemcpyHostToDevice, s));
+    DDM_CUDA_TRY(ctx, cudaMemcpyAsync(dcum, cum.data(), (P + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    prof_begin(ctx, 8);
+    const int64_t maxd = dims[0];
+    int m = P;
+    for (int64_t k = 0; k < maxd; ++k) {
+        while (m > 0 && dims[m - 1] <= k) --m;          // problems still eliminating
+        k_gjb_pivot<<<m, GJ_T, 0, s>>>(dd, k);
+        k_gjb_update<<<(unsigned)cum[m], 256, 0, s>>>(dd, dcum, m, k);
+    }
+    k_gjb_unpivot<<<dim3((unsigned)((maxd + 255) / 256), (unsigned)P), 256, 0, s>>>(dd);
+    prof_end(ctx, 8, (int)(2 * maxd + 1));
+    DDM_CUDA_TRY(ctx, cudaGetLastError());
+    DDM_CUDA_TRY(ctx, cudaStreamSynchronize(s));    // host descriptor vectors go out of scope
+    dfree(stage, s);
+    dfree(piv, s);
+    dfree(dd, s);
+    dfree(dcum, s);
+    for (ddm_tree *t : pend) t->pc_pending = false;
+    return DDM_OK;
+}
+
+// prepare the inverted blocks of (dt, system) for tree t (cached); with
+// defer_coarse the coarse matrix is assembled and left for pc_invert_many
+ddm_status pb_prepare(ddm_ctx *ctx, ddm_tree *t, double dt, int sys, cudaStream_t s, bool defer_coarse) {
     if (t->pb_inv && t->pb_dt == dt && t->pb_sys == sys) return DDM_OK;
     int nc = sys == DDM_SYS_PRESSURE ? 3 : 2;
     if (!t->pb_inv) DDM_CUDA_TRY(ctx, dalloc(&t->pb_inv, std::max<int64_t>(t->pb_msize, 1) * sizeof(float), t->stream));
@@ -765,33 +780,17 @@ ddm_status pb_prepare(ddm_ctx *ctx, ddm_tree *t, double dt, int sys, cudaStream_
         if (!t->pc_inv)
             DDM_CUDA_TRY(ctx, dalloc(&t->pc_inv, ((size_t)t->n_pc * 3 * K * t->n_pc * 3 * K + 2 * t->n_pc * 3 * K) *
                                                      sizeof(float), t->stream));
-        int32_t *piv = nullptr;
-        float *stage = nullptr;
-        DDM_CUDA_TRY(ctx, dalloc(&piv, (size_t)dim * sizeof(int32_t), s));
-        DDM_CUDA_TRY(ctx, dalloc(&stage, (size_t)(2 * dim + 1) * sizeof(float), s));
         prof_begin(ctx, 8);
         k_pc_assemble<<<dim3((unsigned)t->n_pc, (unsigned)t->n_pc), PC_T, 0, s>>>(
             ctx->kf, wf, geo, selfblk, t->pb_off, t->pb_elem, t->pc_blk, nc, sys, K, dim, t->pc_inv);
-        int launches = 3;
-        if (dim <= GJ1_MAX) {
-            k_gj_cta<<<1, GJ_T, 0, s>>>(t->pc_inv, dim, piv);
-        } else {
-            const unsigned ug = (unsigned)((dim * dim + 255) / 256);
-            for (int64_t k = 0; k < dim; ++k) {
-                k_gj_pivot<<<1, GJ_T, 0, s>>>(t->pc_inv, dim, k, piv, stage, stage + dim, stage + 2 * dim);
-                k_gj_update<<<ug, 256, 0, s>>>(t->pc_inv, dim, k, stage, stage + dim, stage + 2 * dim);
-            }
-            launches = (int)(2 * dim + 2);
-        }
-        k_gj_unpivot<<<(unsigned)((dim + 255) / 256), 256, 0, s>>>(t->pc_inv, dim, piv);
-        prof_end(ctx, 8, launches);
-        dfree(piv, s);
-        dfree(stage, s);
+        prof_end(ctx, 8, 1);
+        t->pc_pending = true;
     }
     dfree(geo, s);
     DDM_CUDA_TRY(ctx, cudaGetLastError());
     t->pb_dt = dt;
     t->pb_sys = sys;
+    if (t->n_pc > 0 && !defer_coarse) return pc_invert_many(ctx, &t, 1, s);
     return DDM_OK;
 }
 
