@@ -112,9 +112,11 @@ struct SegD {
     int64_t n;
 };
 constexpr int SEG_EL = 1024;
-__global__ void k_restrict_bb(const SegD *D, const int4 *items, int nitems, int sys) {
+// act (may be null): problems whose flag is 0 are skipped
+__global__ void k_restrict_bb(const SegD *D, const int4 *items, int nitems, int sys, const int *act) {
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const int4 w = items[it];
+        if (act && !act[w.x]) continue;
         const SegD &d = D[w.x];
         for (int64_t e = w.z + threadIdx.x; e < w.w; e += BT) {
             d.dst[e] = d.src[e];
@@ -123,12 +125,23 @@ __global__ void k_restrict_bb(const SegD *D, const int4 *items, int nitems, int 
         }
     }
 }
-__global__ void k_copy3_bb(const SegD *D, const int4 *items, int nitems, int nc) {
+__global__ void k_copy3_bb(const SegD *D, const int4 *items, int nitems, int nc, const int *act) {
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const int4 w = items[it];
+        if (act && !act[w.x]) continue;
         const SegD &d = D[w.x];
         for (int64_t e = w.z + threadIdx.x; e < w.w; e += BT)
             for (int r = 0; r < 3; ++r) d.dst[r * d.n + e] = r < nc ? d.src[r * d.n + e] : 0.0;
+    }
+}
+// dst += src on the first nc blocks of each problem's 3N layout
+__global__ void k_axpy3_bb(const SegD *D, const int4 *items, int nitems, int nc, const int *act) {
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int4 w = items[it];
+        if (act && !act[w.x]) continue;
+        const SegD &d = D[w.x];
+        for (int64_t e = w.z + threadIdx.x; e < w.w; e += BT)
+            for (int r = 0; r < nc; ++r) d.dst[r * d.n + e] += d.src[r * d.n + e];
     }
 }
 
@@ -181,20 +194,28 @@ struct ddm_batch {
     // operator, residual): FMM products grouped by order, preconditioner,
     // arena copies and restrictions
     std::vector<BatchFmm *> bf[3];          // 0 product, 1 Arnoldi operator, 2 residual
-    BatchPb *bp = nullptr;                  // preconditioner of the Arnoldi operator
-    SegBatch seg[4];                        // 1 operator restriction, 2 residual copy, 3 residual restriction
+    BatchPb *bp = nullptr, *bpx = nullptr;  // preconditioner of the Arnoldi operator / of the update of x
+    SegBatch seg[5];                        // 1 operator restriction, 2 residual copy, 3 residual
+                                            // restriction, 4 update of x
+    int *d_act = nullptr, *h_act = nullptr; // 3P flags (device, pinned host): FMM products of the
+                                            // operator, FMM products of the residual, problems still active
     void free_lists(int k) {
         for (BatchFmm *f : bf[k]) bfmm_free(f, ast);
         bf[k].clear();
         if (k == 1) {
             seg[1].release(ast);
+            seg[4].release(ast);
             if (bp) { bpb_free(bp, ast); bp = nullptr; }
+            if (bpx) { bpb_free(bpx, ast); bpx = nullptr; }
         }
         if (k == 2) { seg[2].release(ast); seg[3].release(ast); }
     }
     void free_solver() {
-        void *ps[] = {prob, blk, V, w, vin, b, tmp, Minv, h, hcol, nrm, coef};
+        void *ps[] = {prob, blk, V, w, vin, b, tmp, Minv, h, hcol, nrm, coef, d_act};
         for (void *p : ps) dfree(p, ast);
+        if (h_act) cudaFreeHost(h_act);
+        h_act = nullptr;
+        d_act = nullptr;
         lsq_free(lsq, ast);
         prob = nullptr; blk = nullptr; V = w = vin = b = tmp = Minv = h = hcol = nrm = coef = nullptr;
         sys = -1; m = 0;
@@ -280,20 +301,19 @@ ddm_status seg_build(ddm_ctx *ctx, ddm_batch *B, const std::vector<int> &idx, co
 // products y_p = [K(dt)] x_p of the problems in idx whose mode is plain FMM,
 // grouped by Chebyshev order: one work-list set per order
 ddm_status fmm_groups(ddm_ctx *ctx, ddm_batch *B, const std::vector<int> &idx, double dt, const double *x,
-                      const int64_t *xoff, double *y, std::vector<BatchFmm *> &out) {
+                      const int64_t *xoff, double *y, std::vector<BatchFmm *> &out, const int *act = nullptr) {
     std::map<int, std::vector<int>> by_n;
     for (int p : idx) by_n[B->trees[p]->prm.n_cheb].push_back(p);
+    std::vector<const double *> xs(B->P);
+    std::vector<double *> ys(B->P);
+    for (int p = 0; p < B->P; ++p) {
+        xs[p] = x + xoff[p];
+        ys[p] = y + B->off3[p];
+    }
     for (auto &g : by_n) {
-        std::vector<ddm_tree *> tr;
-        std::vector<const double *> xs;
-        std::vector<double *> ys;
-        for (int p : g.second) {
-            tr.push_back(B->trees[p]);
-            xs.push_back(x + xoff[p]);
-            ys.push_back(y + B->off3[p]);
-        }
         BatchFmm *f = nullptr;
-        ddm_status st = bfmm_build(ctx, tr.data(), (int)tr.size(), 0.0, dt, xs.data(), ys.data(), B->ast, &f);
+        ddm_status st = bfmm_build(ctx, B->trees.data(), B->P, g.second.data(), (int)g.second.size(), 0.0, dt,
+                                   xs.data(), ys.data(), act, B->ast, &f);
         if (st) return st;
         out.push_back(f);
     }
@@ -478,7 +498,9 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
                   dalloc(&B->h, (size_t)P * hs * sizeof(double), s) == cudaSuccess &&
                   dalloc(&B->hcol, (size_t)P * hs * sizeof(double), s) == cudaSuccess &&
                   dalloc(&B->nrm, (size_t)P * hs * sizeof(double), s) == cudaSuccess &&
-                  dalloc(&B->coef, P * sizeof(double), s) == cudaSuccess;
+                  dalloc(&B->coef, P * sizeof(double), s) == cudaSuccess &&
+                  dalloc(&B->d_act, 3 * (size_t)P * sizeof(int), s) == cudaSuccess &&
+                  cudaMallocHost(&B->h_act, 3 * (size_t)P * sizeof(int)) == cudaSuccess;
         if (!ok) { B->free_solver(); return ctx_fail(ctx, DDM_ENOMEM, "batch GMRES arena allocation failed"); }
         cudaMemcpyAsync(B->prob, hp.data(), L * sizeof(int32_t), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(B->blk, hb.data(), hb.size() * sizeof(SegBlk), cudaMemcpyHostToDevice, s);
@@ -498,72 +520,53 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
     // products throughout, 1 precise residuals, 2 precise inner products too
     std::vector<int> level(P, 0);
     // Plain-FMM solves: every stage of all problems' operator (preconditioner,
-    // product, restriction) is one launch over a work list, captured into one
-    // graph; problems whose precision escalated take their own products.
+    // product, restriction) and of their residual is one launch over a work
+    // list built once per solve and captured once; per-problem flags on the
+    // device select the problems each launch computes (still active, plain
+    // or escalated precision), so nothing is rebuilt as problems converge.
+    // Problems whose precision escalated take their own products, launched
+    // beside the graphs on the batch's forked streams.
     const bool batched = mode == DDM_MODE_FMM;
-    auto capture_op_b = [&](const std::vector<int> &idx) -> ddm_status {
+    int *act_op = B->d_act, *act_res = B->d_act + P, *act_all = B->d_act + 2 * P;
+    auto build_batched = [&]() -> ddm_status {
         B->free_lists(1);
-        std::vector<int> plain, prec;
-        std::vector<ddm_tree *> tr;
-        std::vector<const double *> vs;
-        std::vector<double *> zs;
-        for (int p : idx) {
-            (level[p] >= 2 ? prec : plain).push_back(p);
-            tr.push_back(B->trees[p]);
-            vs.push_back(B->vin + B->offs[p]);
-            zs.push_back(B->full + B->off3[p]);
+        B->free_lists(2);
+        std::vector<int> all(P);
+        std::vector<const double *> vs(P), ts(P);
+        std::vector<double *> zs(P);
+        for (int p = 0; p < P; ++p) {
+            all[p] = p;
+            vs[p] = B->vin + B->offs[p];
+            ts[p] = B->tmp + B->offs[p];
+            zs[p] = B->full + B->off3[p];
         }
-        ddm_status e = bpb_build(ctx, tr.data(), (int)tr.size(), sys, vs.data(), zs.data(), B->ast, &B->bp);
-        if (!e) e = fmm_groups(ctx, B, plain, dt, B->full, B->off3.data(), B->y3, B->bf[1]);
-        if (!e) e = seg_build(ctx, B, idx, B->y3, B->off3.data(), B->w, B->offs.data(), B->seg[1]);
+        ddm_status e = bpb_build(ctx, B->trees.data(), P, sys, vs.data(), zs.data(), act_all, B->ast, &B->bp);
+        if (!e) e = bpb_build(ctx, B->trees.data(), P, sys, ts.data(), zs.data(), act_all, B->ast, &B->bpx);
+        if (!e) e = fmm_groups(ctx, B, all, dt, B->full, B->off3.data(), B->y3, B->bf[1], act_op);
+        if (!e) e = fmm_groups(ctx, B, all, dt, B->full, B->off3.data(), B->y3, B->bf[2], act_res);
+        if (!e) e = seg_build(ctx, B, all, B->y3, B->off3.data(), B->w, B->offs.data(), B->seg[1]);
+        if (!e) e = seg_build(ctx, B, all, d_x, B->off3.data(), B->full, B->off3.data(), B->seg[2]);
+        if (!e) e = seg_build(ctx, B, all, B->y3, B->off3.data(), B->tmp, B->offs.data(), B->seg[3]);
+        if (!e) e = seg_build(ctx, B, all, B->full, B->off3.data(), d_x, B->off3.data(), B->seg[4]);
         if (e) return e;
-        for (int p : prec)         // caches of the precise products, outside the capture
-            if ((e = op_apply(ctx, B->trees[p], 0.0, dt, B->full + B->off3[p], B->y3 + B->off3[p],
-                              mode | DDM_MODE_PRECISE, 0, 1.0)))
-                return e;
-        return capture_seq(ctx, B, &B->g_op, &B->k_op, [&](cudaStream_t cs) -> ddm_status {
+        e = capture_seq(ctx, B, &B->g_op, &B->k_op, [&](cudaStream_t cs) -> ddm_status {
             ddm_status r = bpb_launch(ctx, B->bp, cs);
-            if (!r) r = fork_each(ctx, B, cs, prec, [&](int p, cudaStream_t ps) {
-                return op_apply(ctx, B->trees[p], 0.0, dt, B->full + B->off3[p], B->y3 + B->off3[p],
-                                mode | DDM_MODE_PRECISE, 0, 1.0, ps);
-            });
             for (BatchFmm *f : B->bf[1])
                 if (!r) r = bfmm_launch(ctx, f, cs, B->fork[0]);
-            if (r) return r;
-            k_restrict_bb<<<seg_grid(B->seg[1].n), BT, 0, cs>>>(B->seg[1].desc, B->seg[1].items, B->seg[1].n, sys);
-            prof_end(ctx, 8, 1);
-            return DDM_OK;
+            return r;
         });
-    };
-    auto capture_res_b = [&](const std::vector<int> &idx) -> ddm_status {
-        B->free_lists(2);
-        std::vector<int> plain, other;
-        for (int p : idx) (residual_mode(mode, level[p], B->N[p]) == DDM_MODE_FMM ? plain : other).push_back(p);
-        ddm_status e = fmm_groups(ctx, B, plain, dt, B->full, B->off3.data(), B->y3, B->bf[2]);
-        if (!e) e = seg_build(ctx, B, idx, d_x, B->off3.data(), B->full, B->off3.data(), B->seg[2]);
-        if (!e) e = seg_build(ctx, B, idx, B->y3, B->off3.data(), B->tmp, B->offs.data(), B->seg[3]);
         if (e) return e;
-        for (int p : other)
-            if ((e = op_apply(ctx, B->trees[p], 0.0, dt, B->full + B->off3[p], B->y3 + B->off3[p],
-                              residual_mode(mode, level[p], B->N[p]), 0, 1.0)))
-                return e;
         return capture_seq(ctx, B, &B->g_res, &B->k_res, [&](cudaStream_t cs) -> ddm_status {
-            k_copy3_bb<<<seg_grid(B->seg[2].n), BT, 0, cs>>>(B->seg[2].desc, B->seg[2].items, B->seg[2].n, nc);
+            k_copy3_bb<<<seg_grid(B->seg[2].n), BT, 0, cs>>>(B->seg[2].desc, B->seg[2].items, B->seg[2].n, nc,
+                                                            act_all);
             prof_end(ctx, 8, 1);
-            ddm_status r = fork_each(ctx, B, cs, other, [&](int p, cudaStream_t ps) {
-                return op_apply(ctx, B->trees[p], 0.0, dt, B->full + B->off3[p], B->y3 + B->off3[p],
-                                residual_mode(mode, level[p], B->N[p]), 0, 1.0, ps);
-            });
+            ddm_status r = DDM_OK;
             for (BatchFmm *f : B->bf[2])
                 if (!r) r = bfmm_launch(ctx, f, cs, B->fork[0]);
-            if (r) return r;
-            k_restrict_bb<<<seg_grid(B->seg[3].n), BT, 0, cs>>>(B->seg[3].desc, B->seg[3].items, B->seg[3].n, sys);
-            prof_end(ctx, 8, 1);
-            return DDM_OK;
+            return r;
         });
     };
     auto capture_op = [&](const std::vector<int> &idx) -> ddm_status {
-        if (batched) return capture_op_b(idx);
         return capture(ctx, B, &B->g_op, &B->k_op, idx, [&](int p, cudaStream_t ps) -> ddm_status {
             int64_t n = B->N[p];
             ddm_status e = pb_apply(ctx, B->trees[p], sys, B->vin + B->offs[p], B->full + B->off3[p], ps);
@@ -576,7 +579,6 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
         });
     };
     auto capture_res = [&](const std::vector<int> &idx) -> ddm_status {
-        if (batched) return capture_res_b(idx);
         return capture(ctx, B, &B->g_res, &B->k_res, idx, [&](int p, cudaStream_t ps) -> ddm_status {
             int64_t n = B->N[p];
             k_copy_to3<<<nb(n), BT, 0, ps>>>(d_x + B->off3[p], n, nc, B->full + B->off3[p]);
@@ -594,7 +596,9 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
         return st;
     }
     DDM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-    if ((st = capture_op(every)) || (st = capture_res(every))) { ctx->prof.on = saved; return st; }
+    if (batched) st = build_batched();
+    else if (!(st = capture_op(every))) st = capture_res(every);
+    if (st) { ctx->prof.on = saved; return st; }
     B->op_set = every;
     ctx->prof.on = saved;
     // b = restrict(rhs) (- restrict(A [0; 0; Dq]) for the 2N systems)
@@ -630,9 +634,43 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
     if ((st = lsq_alloc(ctx, B->lsq, P, m, s)) || (st = lsq_reset_iters(ctx, B->lsq, s))) return st;
     int *h_still = B->lsq.hint, *h_iters = B->lsq.hint + 1;
     int total = 0;
+    // batched: the flags of the launches (the pinned mirror is only rewritten
+    // after a synchronisation, when its previous copy is complete)
+    auto set_flags = [&]() -> ddm_status {
+        for (int p = 0; p < P; ++p) {
+            B->h_act[p] = active[p] && level[p] < 2;
+            B->h_act[P + p] = active[p] && residual_mode(mode, level[p], B->N[p]) == DDM_MODE_FMM;
+            B->h_act[2 * P + p] = active[p];
+        }
+        DDM_CUDA_TRY(ctx, cudaMemcpyAsync(B->d_act, B->h_act, 3 * (size_t)P * sizeof(int), cudaMemcpyHostToDevice, s));
+        return DDM_OK;
+    };
+    std::vector<int> prec_op, other_res;
+    auto escalated = [&]() {
+        prec_op.clear();
+        other_res.clear();
+        for (int p = 0; p < P; ++p) {
+            if (!active[p]) continue;
+            if (level[p] >= 2) prec_op.push_back(p);
+            if (residual_mode(mode, level[p], B->N[p]) != DDM_MODE_FMM) other_res.push_back(p);
+        }
+    };
     while (true) {
         // residuals (operator of each problem's level): tmp = A x, w = A x - b
-        DDM_CUDA_TRY(ctx, cudaGraphLaunch(B->g_res, s));
+        if (batched) {
+            escalated();
+            if ((st = set_flags())) return st;
+            DDM_CUDA_TRY(ctx, cudaGraphLaunch(B->g_res, s));
+            st = fork_each(ctx, B, s, other_res, [&](int p, cudaStream_t ps) {
+                return op_apply(ctx, B->trees[p], 0.0, dt, B->full + B->off3[p], B->y3 + B->off3[p],
+                                residual_mode(mode, level[p], B->N[p]), 0, 1.0, ps);
+            });
+            if (st) return st;
+            k_restrict_bb<<<seg_grid(B->seg[3].n), BT, 0, s>>>(B->seg[3].desc, B->seg[3].items, B->seg[3].n, sys,
+                                                             act_all);
+        } else {
+            DDM_CUDA_TRY(ctx, cudaGraphLaunch(B->g_res, s));
+        }
         prof_end(ctx, 6, (int)B->k_res);
         DDM_CUDA_TRY(ctx, cudaMemcpyAsync(B->w, B->tmp, L * sizeof(double), cudaMemcpyDeviceToDevice, s));
         k_axpy_b<<<nb(L), BT, 0, s>>>(-1.0, B->b, B->w, L);
@@ -659,7 +697,10 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
         if (nact == 0 || total >= Pm.max_iters) break;
         // drop converged problems from the graphs once a quarter of them left
         // (and re-capture when a problem switched to precise inner products)
-        if (reprec || nact < 0.75 * (double)B->op_set.size()) {
+        if (batched) {
+            escalated();
+            if ((st = set_flags())) return st;
+        } else if (reprec || nact < 0.75 * (double)B->op_set.size()) {
             std::vector<int> act;
             for (int p = 0; p < P; ++p)
                 if (active[p]) act.push_back(p);
@@ -682,6 +723,15 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
         for (; j < m; ++j) {
             DDM_CUDA_TRY(ctx, cudaMemcpyAsync(B->vin, B->V + (int64_t)j * L, L * sizeof(double), cudaMemcpyDeviceToDevice, s));
             DDM_CUDA_TRY(ctx, cudaGraphLaunch(B->g_op, s));
+            if (batched) {
+                st = fork_each(ctx, B, s, prec_op, [&](int p, cudaStream_t ps) {
+                    return op_apply(ctx, B->trees[p], 0.0, dt, B->full + B->off3[p], B->y3 + B->off3[p],
+                                    mode | DDM_MODE_PRECISE, 0, 1.0, ps);
+                });
+                if (st) return st;
+                k_restrict_bb<<<seg_grid(B->seg[1].n), BT, 0, s>>>(B->seg[1].desc, B->seg[1].items, B->seg[1].n,
+                                                                 sys, act_all);
+            }
             prof_end(ctx, 6, (int)B->k_op);
             prof_end(ctx, 8, 10);
             DDM_CUDA_TRY(ctx, cudaMemsetAsync(B->hcol, 0, (size_t)P * hs * sizeof(double), s));
@@ -706,7 +756,12 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
         if ((st = lsq_solve(ctx, B->lsq, P, s))) return st;
         for (int p = 0; p < P; ++p)
             if (active[p]) ++restarts[p];
-        if (j > 0) {
+        if (j > 0 && batched) {
+            k_comb_seg<<<nb(L), BT, 0, s>>>(B->V, L, j, B->lsq.y, m + 2, B->prob, L, B->tmp);
+            if ((st = bpb_launch(ctx, B->bpx, s))) return st;
+            k_axpy3_bb<<<seg_grid(B->seg[4].n), BT, 0, s>>>(B->seg[4].desc, B->seg[4].items, B->seg[4].n, nc,
+                                                          act_all);
+        } else if (j > 0) {
             k_comb_seg<<<nb(L), BT, 0, s>>>(B->V, L, j, B->lsq.y, m + 2, B->prob, L, B->tmp);
             for (int p = 0; p < P; ++p)
                 if (active[p]) {

@@ -1690,10 +1690,13 @@ struct BDesc {
 constexpr int BE_T = 256, BE_CHUNK = 1024;
 // items (p, kind, a, b): kind 0 prepares elements [a, b), kind 1 zeroes the
 // expansions of the internal cells, floats [zoff + a, zoff + b)
+// act (may be null): per-problem flags, items of problems whose flag is 0
+// are skipped (the same work lists serve every subset of the problems)
 __global__ void __launch_bounds__(BE_T) k_prep_b(const BDesc *D, const int4 *items, int nitems, double scale,
-                                                 int overwrite) {
+                                                 int overwrite, const int *act) {
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const int4 w = items[it];
+        if (act && !act[w.x]) continue;
         const BDesc &d = D[w.x];
         if (w.y == 0) {
             for (int64_t i = w.z + threadIdx.x; i < w.w; i += BE_T)
@@ -1707,9 +1710,10 @@ __global__ void __launch_bounds__(BE_T) k_prep_b(const BDesc *D, const int4 *ite
     }
 }
 template <int N>
-__global__ void __launch_bounds__(UP_T) k_up_b(const BDesc *D, const int2 *items, int nitems) {
+__global__ void __launch_bounds__(UP_T) k_up_b(const BDesc *D, const int2 *items, int nitems, const int *act) {
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const int2 w = items[it];
+        if (act && !act[w.x]) continue;      // uniform over the block
         const BDesc &d = D[w.x];
         up_body<N>(d.cstart, d.cend, d.loff, d.L, d.cix, d.ciy, d.parent, d.g_rel, d.g_frame, d.chg, d.hL, d.W, d.Fl,
                    w.y);
@@ -1717,34 +1721,42 @@ __global__ void __launch_bounds__(UP_T) k_up_b(const BDesc *D, const int2 *items
     }
 }
 template <int N>
-__global__ void __launch_bounds__(L2L_T) k_down_b(const BDesc *D, const int2 *items, int nitems, const float *T) {
+__global__ void __launch_bounds__(L2L_T) k_down_b(const BDesc *D, const int2 *items, int nitems, const float *T,
+                                                  const int *act) {
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const int2 w = items[it];
+        if (act && !act[w.x]) continue;
         const BDesc &d = D[w.x];
         down_body<N>(d.loff, d.L, d.cix, d.ciy, d.parent, T, d.Fl, d.cstart, d.cend, d.g_rel, d.wL, d.far4, w.y);
         __syncthreads();
     }
 }
-__global__ void __launch_bounds__(tc::THREADS) k_m2l_tc_b(const BDesc *D, const int2 *items, int n, int *err) {
+__global__ void __launch_bounds__(tc::THREADS) k_m2l_tc_b(const BDesc *D, const int2 *items, int n, int *err,
+                                                          const int *act) {
     const int2 w = items[blockIdx.x];
+    if (act && !act[w.x]) return;            // whole CTA, before any tensor-memory allocation
     const BDesc &d = D[w.x];
     m2l_body(d.mk_work, d.mk_off, d.mk_pair, n, d.ops, d.W, d.Fl, err, w.y);
 }
 template <bool TWO>
 __global__ void __launch_bounds__(NEAR_T, 4) k_near2_b(KConst<float> k, Win<float> win, const BDesc *D,
-                                                       const int2 *items, int64_t nitems, double scale) {
+                                                       const int2 *items, int64_t nitems, double scale,
+                                                       const int *act) {
     // one item per warp (a loop over items would cost the body registers)
     const int64_t g = (int64_t)blockIdx.x * NEAR_W + (threadIdx.x >> 5);
     if (g >= nitems) return;
     const int2 w = items[g];
+    if (act && !act[w.x]) return;
     const BDesc &d = D[w.x];
     near2_body<TWO>(k, win, d.nb_off, d.nb_tab, d.elem_leaf, d.g_rel, d.g_frame, d.chg, d.perm, d.wL, d.nq,
                     d.near_items, d.n, scale, d.y, w.y);
 }
 // items (p, 0, a, b): far field of elements [a, b) into y
-__global__ void __launch_bounds__(BE_T) k_far_add_b(const BDesc *D, const int4 *items, int nitems, double scale) {
+__global__ void __launch_bounds__(BE_T) k_far_add_b(const BDesc *D, const int4 *items, int nitems, double scale,
+                                                    const int *act) {
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const int4 w = items[it];
+        if (act && !act[w.x]) continue;
         const BDesc &d = D[w.x];
         for (int64_t ti = w.z + threadIdx.x; ti < w.w; ti += BE_T) {
             const float4 g4 = d.far4[ti], f = d.g_frame[ti];
@@ -1769,6 +1781,7 @@ struct BatchFmm {
     int n_prep = 0, n_far = 0, n_leaf = 0, n_m2l = 0;
     int64_t n_near = 0;
     long long launches = 0;
+    const int *act = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
@@ -1781,17 +1794,19 @@ void bfmm_free(BatchFmm *b, cudaStream_t s) {
     delete b;
 }
 
-ddm_status bfmm_build(ddm_ctx *ctx, ddm_tree *const *trees, int np, double lo, double hi, const double *const *xs,
-                      double *const *ys, cudaStream_t s, BatchFmm **out) {
+ddm_status bfmm_build(ddm_ctx *ctx, ddm_tree *const *trees, int np, const int *idx, int nidx, double lo, double hi,
+                      const double *const *xs, double *const *ys, const int *act, cudaStream_t s, BatchFmm **out) {
     *out = nullptr;
-    if (np <= 0) return ctx_fail(ctx, DDM_EINVAL, "batched product: no problems");
-    const int n = trees[0]->prm.n_cheb, n2 = n * n;
+    if (np <= 0 || nidx <= 0) return ctx_fail(ctx, DDM_EINVAL, "batched product: no problems");
+    const int n = trees[idx[0]]->prm.n_cheb, n2 = n * n;
     ddm_status st = upload_tables(ctx);
     if (st) return st;
     std::vector<BDesc> hd(np);
+    std::memset(hd.data(), 0, hd.size() * sizeof(BDesc));
     std::vector<int4> hprep, hfar;
     std::vector<int2> hleaf, hm2l, hnear;
-    for (int p = 0; p < np; ++p) {
+    for (int q = 0; q < nidx; ++q) {
+        const int p = idx[q];
         ddm_tree *t = trees[p];
         if (t->prm.n_cheb != n) return ctx_fail(ctx, DDM_EINVAL, "batched product: trees of different orders");
         if ((st = ensure_workspace(ctx, t))) return st;
@@ -1836,7 +1851,7 @@ ddm_status bfmm_build(ddm_ctx *ctx, ddm_tree *const *trees, int np, double lo, d
         }
     }
     BatchFmm *b = new BatchFmm();
-    b->n = n; b->np = np; b->lo = lo; b->hi = hi;
+    b->n = n; b->np = np; b->lo = lo; b->hi = hi; b->act = act;
     cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, ctx->device);
     b->n_prep = (int)hprep.size(); b->n_far = (int)hfar.size(); b->n_leaf = (int)hleaf.size();
     b->n_m2l = (int)hm2l.size(); b->n_near = (int64_t)hnear.size();
@@ -1869,7 +1884,7 @@ ddm_status bfmm_launch(ddm_ctx *ctx, BatchFmm *b, cudaStream_t s, cudaStream_t a
     const int nsm = b->nsm;
     auto grid = [&](int64_t items, int per_sm) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)nsm * per_sm)); };
     long long launches = 0;
-    k_prep_b<<<grid(b->n_prep, 8), BE_T, 0, s>>>(b->desc, b->prep, b->n_prep, 1.0, 1);
+    k_prep_b<<<grid(b->n_prep, 8), BE_T, 0, s>>>(b->desc, b->prep, b->n_prep, 1.0, 1, b->act);
     ++launches;
     cudaStream_t fs = aux ? aux : s;
     if (b->n_leaf > 0) {
@@ -1877,15 +1892,15 @@ ddm_status bfmm_launch(ddm_ctx *ctx, BatchFmm *b, cudaStream_t s, cudaStream_t a
             DDM_CUDA_TRY(ctx, cudaEventRecord(b->ev_fork, s));
             DDM_CUDA_TRY(ctx, cudaStreamWaitEvent(fs, b->ev_fork, 0));
         }
-#define DDM_UPB(NN) k_up_b<NN><<<grid(b->n_leaf, 4), UP_T, 0, fs>>>(b->desc, b->leaf, b->n_leaf)
+#define DDM_UPB(NN) k_up_b<NN><<<grid(b->n_leaf, 4), UP_T, 0, fs>>>(b->desc, b->leaf, b->n_leaf, b->act)
         DDM_CHEB_SWITCH(n, DDM_UPB);
 #undef DDM_UPB
         if (b->n_m2l > 0) {
             dim3 g((unsigned)b->n_m2l, (unsigned)((4 * n * n + tc::BM - 1) / tc::BM), 1);
-            k_m2l_tc_b<<<g, tc::THREADS, tc::SMEM_BYTES, fs>>>(b->desc, b->m2l, n, ctx->d_err);
+            k_m2l_tc_b<<<g, tc::THREADS, tc::SMEM_BYTES, fs>>>(b->desc, b->m2l, n, ctx->d_err, b->act);
             ++launches;
         }
-#define DDM_DOWNB(NN) k_down_b<NN><<<grid(b->n_leaf, 8), L2L_T, 0, fs>>>(b->desc, b->leaf, b->n_leaf, ctx->cheb_Tn[NN / 2 - 1])
+#define DDM_DOWNB(NN) k_down_b<NN><<<grid(b->n_leaf, 8), L2L_T, 0, fs>>>(b->desc, b->leaf, b->n_leaf, ctx->cheb_Tn[NN / 2 - 1], b->act)
         DDM_CHEB_SWITCH(n, DDM_DOWNB);
 #undef DDM_DOWNB
         launches += 2;
@@ -1894,12 +1909,12 @@ ddm_status bfmm_launch(ddm_ctx *ctx, BatchFmm *b, cudaStream_t s, cudaStream_t a
     if (b->n_near > 0) {
         auto kn = b->lo > 0.0 ? k_near2_b<true> : k_near2_b<false>;
         kn<<<(unsigned)((b->n_near + NEAR_W - 1) / NEAR_W), NEAR_T, 0, s>>>(
-            ctx->kf, make_win<float>(ctx, b->lo, b->hi), b->desc, b->near, b->n_near, 1.0);
+            ctx->kf, make_win<float>(ctx, b->lo, b->hi), b->desc, b->near, b->n_near, 1.0, b->act);
         ++launches;
     }
     if (b->n_leaf > 0) {
         if (aux) DDM_CUDA_TRY(ctx, cudaStreamWaitEvent(s, b->ev_join, 0));
-        k_far_add_b<<<grid(b->n_far, 8), BE_T, 0, s>>>(b->desc, b->far, b->n_far, 1.0);
+        k_far_add_b<<<grid(b->n_far, 8), BE_T, 0, s>>>(b->desc, b->far, b->n_far, 1.0, b->act);
         ++launches;
     }
     prof_end(ctx, 6, (int)launches);

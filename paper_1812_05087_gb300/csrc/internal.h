@@ -111,9 +111,11 @@ struct ddm_tree {
 };
 
 // coarse level of the preconditioner (precond.cu): chains of at least
-// PC_MIN_BLOCKS blocks take PC_MODES modes per block (fewer when the coarse
-// dimension would exceed PC_MAX_DIM; none below one mode)
-constexpr int PC_MIN_BLOCKS = 3, PC_MODES = 3, PC_MAX_DIM = 4096;
+// PC_MIN_BLOCKS blocks (long fractures, where block Jacobi leaves the
+// long-wavelength modes to the Krylov iteration) take PC_MODES modes per
+// block, fewer when the coarse dimension would exceed PC_MAX_DIM (its
+// set-up is O(dim^3)), none below one mode
+constexpr int PC_MIN_BLOCKS = 4, PC_MODES = 3, PC_MAX_DIM = 2048;
 
 struct GmresWork;
 
@@ -227,8 +229,12 @@ ddm_status window_ops(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, cudaStrea
 // many problems' FMM products, one launch per stage (trees of one order):
 // y_p = [K(hi) - K(lo)] x_p for every problem p (fmm.cu)
 struct BatchFmm;
-ddm_status bfmm_build(ddm_ctx *ctx, ddm_tree *const *trees, int np, double lo, double hi, const double *const *xs,
-                      double *const *ys, cudaStream_t s, BatchFmm **out);
+// act (device, may be null): per-problem flags read at launch time; problems
+// whose flag is 0 are skipped
+// trees, xs, ys: all np problems; idx: the nidx members of this work list
+// (one order); the descriptor table and act are indexed by problem
+ddm_status bfmm_build(ddm_ctx *ctx, ddm_tree *const *trees, int np, const int *idx, int nidx, double lo, double hi,
+                      const double *const *xs, double *const *ys, const int *act, cudaStream_t s, BatchFmm **out);
 ddm_status bfmm_launch(ddm_ctx *ctx, BatchFmm *b, cudaStream_t s, cudaStream_t aux);
 void bfmm_free(BatchFmm *b, cudaStream_t s);
 ddm_status upload_tables(ddm_ctx *ctx);
@@ -240,6 +246,6 @@ ddm_status pb_apply(ddm_ctx *ctx, ddm_tree *t, int sys, const double *v, double 
 // the same for many problems in one launch per stage (precond.cu)
 struct BatchPb;
 ddm_status bpb_build(ddm_ctx *ctx, ddm_tree *const *trees, int np, int sys, const double *const *vs,
-                     double *const *zs, cudaStream_t s, BatchPb **out);
+                     double *const *zs, const int *act, cudaStream_t s, BatchPb **out);
 ddm_status bpb_launch(ddm_ctx *ctx, BatchPb *b, cudaStream_t s);
 void bpb_free(BatchPb *b, cudaStream_t s);

@@ -545,14 +545,17 @@ struct PbDesc {
     int K;
 };
 // one CTA per (problem, block) x row slice
-__global__ void __launch_bounds__(PA_T) k_pb_apply_b(const PbDesc *D, const int2 *items, int nc) {
+// act (may be null): problems whose flag is 0 are skipped
+__global__ void __launch_bounds__(PA_T) k_pb_apply_b(const PbDesc *D, const int2 *items, int nc, const int *act) {
     const int2 w = items[blockIdx.x];
+    if (act && !act[w.x]) return;
     const PbDesc &d = D[w.x];
     pb_apply_body(d.boff, d.belem, d.moff, nc, d.Minv, d.v, d.N, d.z, 1, w.y);
 }
 // items (p, coarse block I)
-__global__ void k_pc_restrict_b(const PbDesc *D, const int2 *items, int nc) {
+__global__ void k_pc_restrict_b(const PbDesc *D, const int2 *items, int nc, const int *act) {
     const int2 w = items[blockIdx.x];
+    if (act && !act[w.x]) return;
     const PbDesc &d = D[w.x];
     __shared__ double red[2][PC_MAXQ];
     const int I = w.y, b = d.pcb[I], m = d.boff[b + 1] - d.boff[b], K = d.K;
@@ -585,8 +588,9 @@ __global__ void k_pc_restrict_b(const PbDesc *D, const int2 *items, int nc) {
     }
 }
 // items (p, first of 8 rows); a warp per row
-__global__ void k_pc_gemv_b(const PbDesc *D, const int2 *items) {
+__global__ void k_pc_gemv_b(const PbDesc *D, const int2 *items, const int *act) {
     const int2 w = items[blockIdx.x];
+    if (act && !act[w.x]) return;
     const PbDesc &d = D[w.x];
     const int64_t r = (int64_t)w.y + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -598,8 +602,9 @@ __global__ void k_pc_gemv_b(const PbDesc *D, const int2 *items) {
     for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xFFFFFFFFu, sacc, o);
     if (lane == 0) d.yc[r] = sacc;
 }
-__global__ void k_pc_prolong_b(const PbDesc *D, const int2 *items, int nc) {
+__global__ void k_pc_prolong_b(const PbDesc *D, const int2 *items, int nc, const int *act) {
     const int2 w = items[blockIdx.x];
+    if (act && !act[w.x]) return;
     const PbDesc &d = D[w.x];
     const int I = w.y, b = d.pcb[I], m = d.boff[b + 1] - d.boff[b], K = d.K;
     const int64_t *el = d.belem + d.boff[b];
@@ -616,6 +621,7 @@ __global__ void k_pc_prolong_b(const PbDesc *D, const int2 *items, int nc) {
 
 struct BatchPb {
     int np = 0, nc = 0;
+    const int *act = nullptr;
     PbDesc *desc = nullptr;
     int2 *blk = nullptr, *pc = nullptr, *gemv = nullptr;
     int n_blk = 0, n_pc = 0, n_gemv = 0;
@@ -631,7 +637,7 @@ void bpb_free(BatchPb *b, cudaStream_t s) {
 // the batched preconditioner of problems p (prepared for the same (dt,
 // system)) from v_p (system layout) into z_p (3N layout)
 ddm_status bpb_build(ddm_ctx *ctx, ddm_tree *const *trees, int np, int sys, const double *const *vs,
-                     double *const *zs, cudaStream_t s, BatchPb **out) {
+                     double *const *zs, const int *act, cudaStream_t s, BatchPb **out) {
     *out = nullptr;
     const int nc = sys == DDM_SYS_PRESSURE ? 3 : 2;
     std::vector<PbDesc> hd(np);
@@ -654,7 +660,7 @@ ddm_status bpb_build(ddm_ctx *ctx, ddm_tree *const *trees, int np, int sys, cons
         }
     }
     BatchPb *b = new BatchPb();
-    b->np = np; b->nc = nc;
+    b->np = np; b->nc = nc; b->act = act;
     b->n_blk = (int)hblk.size(); b->n_pc = (int)hpc.size(); b->n_gemv = (int)hgemv.size();
     auto up = [&](void **dst, const void *src, size_t bytes) -> bool {
         if (dalloc(dst, bytes ? bytes : 16, s) != cudaSuccess) return false;
@@ -676,13 +682,13 @@ ddm_status bpb_build(ddm_ctx *ctx, ddm_tree *const *trees, int np, int sys, cons
 ddm_status bpb_launch(ddm_ctx *ctx, BatchPb *b, cudaStream_t s) {
     int launches = 0;
     if (b->n_blk > 0) {
-        k_pb_apply_b<<<dim3((unsigned)b->n_blk, PA_S), PA_T, 0, s>>>(b->desc, b->blk, b->nc);
+        k_pb_apply_b<<<dim3((unsigned)b->n_blk, PA_S), PA_T, 0, s>>>(b->desc, b->blk, b->nc, b->act);
         ++launches;
     }
     if (b->n_pc > 0) {
-        k_pc_restrict_b<<<(unsigned)b->n_pc, 64, 0, s>>>(b->desc, b->pc, b->nc);
-        k_pc_gemv_b<<<(unsigned)b->n_gemv, 256, 0, s>>>(b->desc, b->gemv);
-        k_pc_prolong_b<<<(unsigned)b->n_pc, 64, 0, s>>>(b->desc, b->pc, b->nc);
+        k_pc_restrict_b<<<(unsigned)b->n_pc, 64, 0, s>>>(b->desc, b->pc, b->nc, b->act);
+        k_pc_gemv_b<<<(unsigned)b->n_gemv, 256, 0, s>>>(b->desc, b->gemv, b->act);
+        k_pc_prolong_b<<<(unsigned)b->n_pc, 64, 0, s>>>(b->desc, b->pc, b->nc, b->act);
         launches += 3;
     }
     prof_end(ctx, 8, launches);
