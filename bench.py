@@ -454,27 +454,47 @@ def main():
     window_setup = {"m2l_ops_ms": wst["m2l_ops"][0], "self_blocks_ms": wst["self_blocks"][0],
                     "note": "per new time window, cached on the tree (excluded from the timed product)"}
 
-    # ---------------- other Chebyshev orders (same workload, own context and tree)
+    # ---------------- other Chebyshev orders (same workload, own context and
+    # tree), each with the full and the compressed M2L operators
     orders = {}
-    for nn in [int(v) for v in args.orders.split(",") if v.strip()]:
-        if nn == args.n_cheb:
-            continue
+    extra = [int(v) for v in args.orders.split(",") if v.strip()]
+    for nn in [args.n_cheb] + [v for v in extra if v != args.n_cheb]:
         octx = Context(inputs.MATERIAL, n_cheb=nn, leaf_size=args.leaf)
         otree = octx.build_tree(d_xy)
         oy = torch.empty_like(y)
         ofn = lambda: octx.matvec(otree, x, 0.0, DT, mode="fmm", out=oy)
-        ot = timed(ofn, args.steps, args.warmup)
-        octx.profile(True)
-        for _ in range(3):
-            ofn()
-        ost = octx.profile_read()
-        octx.profile(False)
+
+        def stages():
+            octx.profile_read()
+            octx.profile(True)
+            for _ in range(3):
+                ofn()
+            ost = octx.profile_read()
+            octx.profile(False)
+            return {k: v[0] / 3 for k, v in ost.items() if v[1] > 0}
+
         oinfo = otree.info()
-        oms = float(np.mean(ot))
-        orders[nn] = {"ms_per_matvec": oms, "melem_s": world * N / (oms * 1e-3) / 1e6, "depth": oinfo["depth"],
-                      "m2l_pairs": oinfo["n_m2l_pairs"], "p2p_pairs": oinfo["n_p2p_pairs"],
-                      "stages_ms_per_matvec": {k: v[0] / 3 for k, v in ost.items() if v[1] > 0},
-                      "y": oy.cpu().numpy()}
+        rec = {"depth": oinfo["depth"], "m2l_pairs": oinfo["n_m2l_pairs"], "p2p_pairs": oinfo["n_p2p_pairs"]}
+        if nn != args.n_cheb:
+            octx.set_m2l_compression(0)
+            oms = float(np.mean(timed(ofn, args.steps, args.warmup)))
+            rec.update({"ms_per_matvec": oms, "melem_s": world * N / (oms * 1e-3) / 1e6,
+                        "stages_ms_per_matvec": stages(), "y": oy.cpu().numpy()})
+        if nn >= 8:
+            octx.set_m2l_compression(1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ofn()
+            torch.cuda.synchronize()
+            first = (time.perf_counter() - t0) * 1e3
+            cms = float(np.mean(timed(ofn, args.steps, args.warmup)))
+            rec["compressed_m2l"] = {"rank": 64 + 4 * (nn - 8), "ms_per_matvec": cms,
+                                     "melem_s": world * N / (cms * 1e-3) / 1e6,
+                                     "first_product_ms": first, "stages_ms_per_matvec": stages(),
+                                     "note": "SVD-compressed M2L (ddm_set_m2l_compression mode 1); first product "
+                                             "includes the set-up of the window's bases and cores",
+                                     "y": oy.cpu().numpy()}
+        orders[nn] = rec
         otree.close()
         octx.close()
 
@@ -642,8 +662,10 @@ def main():
                "dense_vs_oracle": max(e_d[b * k:(b + 1) * k].max() / scale[b] for b in range(3)),
                "rows": int(rows.size)}
         for nn, o in orders.items():
-            e_o = np.abs(o["y"][rows] - ref)
-            o["error_vs_oracle"] = max(e_o[b * k:(b + 1) * k].max() / scale[b] for b in range(3))
+            for rec in (o, o.get("compressed_m2l", {})):
+                if "y" in rec:
+                    e_o = np.abs(rec["y"][rows] - ref)
+                    rec["error_vs_oracle"] = max(e_o[b * k:(b + 1) * k].max() / scale[b] for b in range(3))
         import oracle
         cpu = {"value": k / dt_or / 1e6, "unit": "Melem/s", "cores": oracle.num_threads(), "kind": "oracle",
                "sample": f"{k} target elements (3 rows each) x {N} sources, FP64 adaptive element quadrature"}
@@ -669,7 +691,8 @@ def main():
         "fmm_speedup_vs_dense": ms_dense / ms_fmm,
         "history": {"lags": H, "ms": ms_hist, "melem_lags_per_s": N * H / (ms_hist * 1e-3) / 1e6},
         "window_setup": window_setup,
-        "orders": {str(nn): {k: v for k, v in o.items() if k != "y"} for nn, o in orders.items()},
+        "orders": {str(nn): {k: ({kk: vv for kk, vv in v.items() if kk != "y"} if isinstance(v, dict) else v)
+                             for k, v in o.items() if k != "y"} for nn, o in orders.items()},
         "well": well_res,
         "batched": batch_res, "serving": serve_res,
         "error": err,

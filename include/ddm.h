@@ -107,6 +107,26 @@ ddm_status ddm_device_check(ddm_ctx *ctx);
  * path: the solve then returns DDM_ETIMEOUT).  No counterpart in the paper. */
 ddm_status ddm_set_wait_limit(ddm_ctx *ctx, int64_t polls);
 
+/* Compressed M2L operators (the SVD compression of black-box FMM operators
+ * that paper Sec. 3 cites as the further step of the Chebyshev FMM; the
+ * paper applies the full operators).  Per tree level and time window the
+ * (4n^2 x 4n^2) operators of all cell offsets are replaced by shared bases
+ * of rank k and k x k cores, built on the device from the window's full
+ * operators (randomized range finder on the component-equilibrated
+ * operators, FP32) and cached per (tree, window) like the operators.
+ *   rank: 0 for the default k = 64 + 4 (n - 8), else a multiple of 8 up to
+ *         512 (capped at 4n^2); a new rank drops the tree's cached sets.
+ *   mode 0: never; the M2L applies the full operators.
+ *   mode 1: for every order n >= 8, from a window's first product.
+ *   mode 2 (default): for orders n >= 10, once a window's full operators
+ *           have served 128 products (the set-up costs tens of products, so
+ *           only a window that keeps being applied pays for it).
+ * Products of FMM mode (ddm_matvec, the operator of ddm_gmres_solve, history
+ * windows) take it; batched problems keep the full operators.  A stream in
+ * CUDA-graph capture never starts a set-up.  Errors: DDM_EINVAL for another
+ * mode or rank.  No counterpart in the paper. */
+ddm_status ddm_set_m2l_compression(ddm_ctx *ctx, int mode, int rank);
+
 /* Build the quadtree of paper Sec. 3.1 over the element midpoints: level-0
  * square covering all midpoints, uniform depth (smallest depth whose leaves
  * hold <= leaf_size elements, capped so that no element is longer than a

@@ -411,6 +411,14 @@ ddm_status ddm_set_wait_limit(ddm_ctx *ctx, int64_t polls) {
     return DDM_OK;
 }
 
+ddm_status ddm_set_m2l_compression(ddm_ctx *ctx, int mode, int rank) {
+    if (!ctx || mode < 0 || mode > 2 || rank < 0 || rank > 512 || rank % 8)
+        return ctx_fail(ctx, DDM_EINVAL, "ddm_set_m2l_compression: mode 0, 1 or 2; rank 0 or a multiple of 8 up to 512");
+    ctx->m2l_compress = mode;
+    ctx->m2l_rank = rank;
+    return DDM_OK;
+}
+
 ddm_status ddm_profile(ddm_ctx *ctx, int enable) {
     if (!ctx) return DDM_EINVAL;
     ctx->prof.on = enable ? 1 : 0;

@@ -566,8 +566,13 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
 }
 }  // namespace tc
 
-__device__ __forceinline__ void m2l_body(const int2 *work, const int32_t *koff, const int2 *pairs, int n,
-                                         const float *ops, const float *W, float *F, int *err, int64_t wi) {
+// The grouped gathered product G[:, I] += K_key W[:, J] over the pairs (I, J)
+// of one work item, for an operator of M rows and Kd columns per key (at
+// ops + key * M * Kd, row-major), sources of stride Kd and targets of stride
+// M.  The M2L of a product is M = Kd = 4 n^2; the compressed M2L uses the
+// same body for its three stages (bases and cores of other shapes).
+__device__ __forceinline__ void tc_group_body(const int2 *work, const int32_t *koff, const int2 *pairs, int M, int Kd,
+                                              const float *ops, const float *W, float *F, int *err, int64_t wi) {
     using namespace tc;
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t bar[NSTAGE];
@@ -580,9 +585,8 @@ __device__ __forceinline__ void m2l_body(const int2 *work, const int32_t *koff, 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int2 wk = work[wi];
     const int key = wk.x, p0 = wk.y, p1 = min(koff[key + 1], p0 + BN);
-    const int n2 = n * n, ld = 4 * n2;
     const int r0 = blockIdx.y * BM;
-    const float *K = ops + (int64_t)key * 16 * n2 * n2;
+    const float *K = ops + (int64_t)key * M * Kd;
     if (tid < BN) {
         int p = p0 + tid;
         sI[tid] = p < p1 ? pairs[p].x : -1;
@@ -604,7 +608,7 @@ __device__ __forceinline__ void m2l_body(const int2 *work, const int32_t *koff, 
     fence_after_sync();
     const uint32_t tmem = s_tmem;
     // this CTA's share of the K chunks
-    const int nkt = (ld + BK - 1) / BK, per = (nkt + KSPLIT - 1) / KSPLIT;
+    const int nkt = (Kd + BK - 1) / BK, per = (nkt + KSPLIT - 1) / KSPLIT;
     const int kbeg = blockIdx.z * per, nkb = max(0, min(nkt, kbeg + per) - kbeg);
     for (int kb = 0; kb < nkb; ++kb) {
         const int st = kb % NSTAGE;
@@ -616,13 +620,13 @@ __device__ __forceinline__ void m2l_body(const int2 *work, const int32_t *koff, 
 #pragma unroll
         for (int i = 0; i < NA; ++i) {       // operator rows r0.., CPR float4 per K chunk
             int idx = tid + i * THREADS, row = idx / CPR, c = idx % CPR, gr = r0 + row, gk = k0 + 4 * c;
-            va[i] = (gr < ld && gk < ld) ? __ldg(reinterpret_cast<const float4 *>(K + (int64_t)gr * ld + gk))
+            va[i] = (gr < M && gk < Kd) ? __ldg(reinterpret_cast<const float4 *>(K + (int64_t)gr * Kd + gk))
                                          : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
         for (int i = 0; i < NB; ++i) {       // source weights, one column per pair
             int idx = tid + i * THREADS, col = idx / CPR, c = idx % CPR, J = sJ[col], gk = k0 + 4 * c;
-            vb[i] = (J >= 0 && gk < ld) ? __ldg(reinterpret_cast<const float4 *>(W + (int64_t)J * ld + gk))
+            vb[i] = (J >= 0 && gk < Kd) ? __ldg(reinterpret_cast<const float4 *>(W + (int64_t)J * Kd + gk))
                                         : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         // the MMAs that last read this stage (issued NSTAGE chunks ago) must be done
@@ -669,11 +673,11 @@ __device__ __forceinline__ void m2l_body(const int2 *work, const int32_t *koff, 
     for (int c0 = 0; c0 < BN; c0 += 16) {
         float v[16];
         tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-        if (ok && row < ld) {
+        if (ok && row < M) {
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 int I = sI[c0 + j];
-                if (I >= 0) atomicAdd(&F[(int64_t)I * ld + row], v[j]);
+                if (I >= 0) atomicAdd(&F[(int64_t)I * M + row], v[j]);
             }
         }
     }
@@ -683,10 +687,20 @@ __device__ __forceinline__ void m2l_body(const int2 *work, const int32_t *koff, 
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
     if (tid == 0 && *verr) atomicExch(err, 1);
 }
+__device__ __forceinline__ void m2l_body(const int2 *work, const int32_t *koff, const int2 *pairs, int n,
+                                         const float *ops, const float *W, float *F, int *err, int64_t wi) {
+    tc_group_body(work, koff, pairs, 4 * n * n, 4 * n * n, ops, W, F, err, wi);
+}
 __global__ void __launch_bounds__(tc::THREADS) k_m2l_tc(const int2 *work, const int32_t *koff, const int2 *pairs,
                                                         int n, const float *ops, const float *W, float *F,
                                                         int *err) {
     m2l_body(work, koff, pairs, n, ops, W, F, err, blockIdx.x);
+}
+// the same for operators of M x Kd (compressed M2L stages)
+__global__ void __launch_bounds__(tc::THREADS) k_tc_group(const int2 *work, const int32_t *koff, const int2 *pairs,
+                                                          int M, int Kd, const float *ops, const float *W, float *F,
+                                                          int *err) {
+    tc_group_body(work, koff, pairs, M, Kd, ops, W, F, err, blockIdx.x);
 }
 
 // ----------------------------------------------------------- leaf L2P + P2P
@@ -1517,9 +1531,106 @@ ddm_status window_ops(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, cudaStrea
         k_m2l_ops<<<g, 128, 0, s>>>(ctx->kf, make_win<float>(ctx, lo, hi), L, t->h0, n, t->mk_off, t->ops_set[os]);
         t->ops_lo[os] = lo;
         t->ops_hi[os] = hi;
+        t->ops_cnt[os] = 0;
         prof_end(ctx, 3, 1);
     }
     *out = t->ops_set[os];
+    return DDM_OK;
+}
+
+// Whether the M2L of window (lo, hi) on tree t takes the compressed
+// operators: never (mode 0), whenever the order has a rank (mode 1), or
+// (mode 2, the default) for orders n >= 10 once the window's full operators
+// have served SVD_AUTO_USES products, so that only a window that keeps being
+// applied (the operator of repeated solves at one time step) pays for the
+// set-up.  A stream in capture never starts a set-up; it takes what is cached.
+bool want_svd(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, cudaStream_t s) {
+    const int n = t->prm.n_cheb;
+    const int k = svd_rank(ctx, n);
+    if (k <= 0 || ctx->m2l_compress == 0) return false;
+    if (t->svd_k == k)
+        for (int q = 0; q < ddm_tree::WIN_CACHE; ++q)
+            if (t->svd_set[q] && t->svd_lo[q] == lo && t->svd_hi[q] == hi) return true;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
+    if (ctx->m2l_compress == 1) return true;
+    if (n < 10 || t->ops_n != n) return false;
+    for (int k = 0; k < t->ops_cap; ++k)
+        if (t->ops_set[k] && t->ops_lo[k] == lo && t->ops_hi[k] == hi) return ++t->ops_cnt[k] > SVD_AUTO_USES;
+    return false;
+}
+
+// Compressed M2L of window (lo, hi) for tree t: bases and cores from the
+// tree's LRU cache (built from the window's full operators when missing),
+// the per-level cell lists of the pre- and post-stages and the k-per-cell
+// work arrays (once per tree).
+ddm_status window_svd(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, cudaStream_t s, const float **pre,
+                      const float **post, const float **core) {
+    const int n = t->prm.n_cheb, ld = 4 * n * n, k = svd_rank(ctx, n), L = t->depth;
+    if (t->svd_k != k) {                 // another rank: drop the cached sets and work arrays
+        if (t->svd_k) DDM_CUDA_TRY(ctx, cudaDeviceSynchronize());   // products in flight may read them
+        for (int q = 0; q < ddm_tree::WIN_CACHE; ++q) {
+            dfree(t->svd_set[q], t->stream);
+            t->svd_set[q] = nullptr;
+        }
+        dfree(t->Wc, t->stream);
+        dfree(t->Gc, t->stream);
+        t->Wc = t->Gc = nullptr;
+        t->svd_k = k;
+    }
+    if (!t->Wc) {
+        DDM_CUDA_TRY(ctx, dalloc(&t->Wc, (size_t)t->n_cells * k * sizeof(float), t->stream));
+        DDM_CUDA_TRY(ctx, dalloc(&t->Gc, (size_t)t->n_cells * k * sizeof(float), t->stream));
+    }
+    if (!t->lv_off) {
+        std::vector<int32_t> off(L + 2, 0);
+        std::vector<int2> pairs, work;
+        for (int l = 0; l <= L; ++l) {
+            off[l] = (int32_t)pairs.size();
+            if (l < 2) continue;
+            for (int64_t c = t->lvl_off[l]; c < t->lvl_off[l + 1]; ++c) pairs.push_back(make_int2((int)c, (int)c));
+            for (int32_t p = off[l]; p < (int32_t)pairs.size(); p += 64) work.push_back(make_int2(l, p));
+        }
+        off[L + 1] = (int32_t)pairs.size();
+        t->n_lv_work = (int)work.size();
+        DDM_CUDA_TRY(ctx, dalloc(&t->lv_off, off.size() * sizeof(int32_t), t->stream));
+        DDM_CUDA_TRY(ctx, dalloc(&t->lv_pair, std::max<size_t>(1, pairs.size()) * sizeof(int2), t->stream));
+        DDM_CUDA_TRY(ctx, dalloc(&t->lv_work, std::max<size_t>(1, work.size()) * sizeof(int2), t->stream));
+        DDM_CUDA_TRY(ctx, cudaMemcpyAsync(t->lv_off, off.data(), off.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                          t->stream));
+        if (!pairs.empty())
+            DDM_CUDA_TRY(ctx, cudaMemcpyAsync(t->lv_pair, pairs.data(), pairs.size() * sizeof(int2),
+                                              cudaMemcpyHostToDevice, t->stream));
+        if (!work.empty())
+            DDM_CUDA_TRY(ctx, cudaMemcpyAsync(t->lv_work, work.data(), work.size() * sizeof(int2),
+                                              cudaMemcpyHostToDevice, t->stream));
+        DDM_CUDA_TRY(ctx, cudaStreamSynchronize(t->stream));   // host lists go out of scope
+    }
+    const size_t npre = (size_t)(L + 1) * k * ld, ncore = (size_t)t->n_keys * k * k;
+    const unsigned long long now = t->win_clock;
+    int os = -1;
+    for (int q = 0; q < ddm_tree::WIN_CACHE; ++q)
+        if (t->svd_set[q] && t->svd_lo[q] == lo && t->svd_hi[q] == hi) os = q;
+    if (os >= 0) t->svd_use[os] = now;
+    if (os < 0) {
+        os = 0;
+        for (int q = 0; q < ddm_tree::WIN_CACHE; ++q) {
+            if (!t->svd_set[q]) { os = q; break; }
+            if (t->svd_use[q] < t->svd_use[os]) os = q;
+        }
+        t->svd_use[os] = now;
+        if (!t->svd_set[os]) DDM_CUDA_TRY(ctx, dalloc(&t->svd_set[os], (2 * npre + ncore) * sizeof(float), t->stream));
+        const float *ops = nullptr;
+        ddm_status st = window_ops(ctx, t, lo, hi, s, &ops);
+        if (st) return st;
+        float *b = t->svd_set[os];
+        if ((st = svd_build(ctx, t, ops, k, s, b, b + npre, b + 2 * npre))) return st;
+        t->svd_lo[os] = lo;
+        t->svd_hi[os] = hi;
+    }
+    *pre = t->svd_set[os];
+    *post = t->svd_set[os] + npre;
+    *core = t->svd_set[os] + 2 * npre;
     return DDM_OK;
 }
 
@@ -1606,11 +1717,37 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
 #undef DDM_UP
         prof_end(ctx, 2, 1);
         // M2L on every level >= 2: operators of this window, then one GEMM launch
-        const float *ops = nullptr;
-        if ((st = window_ops(ctx, t, lo, hi, fs, &ops))) return st;
+        // (compressed: three)
+        const int kr = want_svd(ctx, t, lo, hi, fs) ? svd_rank(ctx, n) : 0;
+        const float *ops = nullptr, *spre = nullptr, *spost = nullptr, *score = nullptr;
+        if (kr > 0) {
+            if ((st = window_svd(ctx, t, lo, hi, fs, &spre, &spost, &score))) return st;
+        } else if ((st = window_ops(ctx, t, lo, hi, fs, &ops))) {
+            return st;
+        }
         prof_begin(ctx, 4);
         // (the local expansions of every cell at levels >= 2 were zeroed by k_up)
-        if (t->n_work > 0) {
+        if (t->n_work > 0 && kr > 0) {
+            static bool attr_g[64] = {false};
+            if (!attr_g[ctx->device & 63]) {
+                DDM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_tc_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       tc::SMEM_BYTES));
+                attr_g[ctx->device & 63] = true;
+            }
+            // W' = (V^T D_in^-1) W per cell, G' = C W' per pair, F += (D_out^-1 U) G' per cell
+            DDM_CUDA_TRY(ctx, cudaMemsetAsync(t->Wc, 0, (size_t)t->n_cells * kr * sizeof(float), fs));
+            DDM_CUDA_TRY(ctx, cudaMemsetAsync(t->Gc, 0, (size_t)t->n_cells * kr * sizeof(float), fs));
+            const int ld = 4 * n2;
+            k_tc_group<<<dim3((unsigned)t->n_lv_work, (unsigned)((kr + tc::BM - 1) / tc::BM)), tc::THREADS,
+                         tc::SMEM_BYTES, fs>>>(t->lv_work, t->lv_off, t->lv_pair, kr, ld, spre, t->W, t->Wc,
+                                               ctx->d_err);
+            k_tc_group<<<dim3((unsigned)t->n_work, (unsigned)((kr + tc::BM - 1) / tc::BM)), tc::THREADS,
+                         tc::SMEM_BYTES, fs>>>(t->mk_work, t->mk_off, t->mk_pair, kr, kr, score, t->Wc, t->Gc,
+                                               ctx->d_err);
+            k_tc_group<<<dim3((unsigned)t->n_lv_work, (unsigned)((ld + tc::BM - 1) / tc::BM)), tc::THREADS,
+                         tc::SMEM_BYTES, fs>>>(t->lv_work, t->lv_off, t->lv_pair, ld, kr, spost, t->Gc, t->Fl,
+                                               ctx->d_err);
+        } else if (t->n_work > 0) {
             static bool attr[64] = {false};
             if (!attr[ctx->device & 63]) {
                 DDM_CUDA_TRY(ctx, cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1622,7 +1759,7 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
             k_m2l_tc<<<g, tc::THREADS, tc::SMEM_BYTES, fs>>>(t->mk_work, t->mk_off, t->mk_pair, n, ops, t->W,
                                                             t->Fl, ctx->d_err);
         }
-        prof_end(ctx, 4, 1);
+        prof_end(ctx, 4, (t->n_work > 0 && kr > 0) ? 3 : 1);
         // downward pass: L2L chains to the leaves and L2P at their targets, one launch
         prof_begin(ctx, 5);
 #define DDM_DOWN(NN)                                                                                        \

@@ -99,9 +99,24 @@ struct ddm_tree {
     float *ops_set[WIN_CACHE] = {};
     double ops_lo[WIN_CACHE], ops_hi[WIN_CACHE];
     unsigned long long ops_use[WIN_CACHE] = {};
+    unsigned ops_cnt[WIN_CACHE] = {};  // products served by each set (compression policy)
     int ops_n;                 // n_cheb of the cached operator sets
     int ops_cap;               // sets allowed by the memory budget
     unsigned long long win_clock;
+    // compressed M2L (svd.cu) of the cached windows: per level a pre-operator
+    // (k x 4n^2) and a post-operator (4n^2 x k), per (level, offset) key a
+    // k x k core, in one allocation per window
+    float *svd_set[WIN_CACHE] = {};
+    double svd_lo[WIN_CACHE], svd_hi[WIN_CACHE];
+    unsigned long long svd_use[WIN_CACHE] = {};
+    std::vector<int32_t> h_mk_off;     // host copy of mk_off (key counts)
+    // cells of levels >= 2 as (cell, cell) pairs grouped by level (key =
+    // level) with 64-cell work items: the pre- and post-stages
+    int32_t *lv_off = nullptr;
+    int2 *lv_pair = nullptr, *lv_work = nullptr;
+    int n_lv_work = 0;
+    float *Wc = nullptr, *Gc = nullptr;  // compressed weights / local sums, k per cell
+    int svd_k = 0;                       // rank of the cached compressed sets and of Wc, Gc
     // per-tree workspaces
     float *W;                  // multipole weights, 4 n^2 per cell
     float *Fl;                 // local expansions, 4 n^2 per cell
@@ -180,6 +195,8 @@ struct ddm_ctx {
     Prof prof;
     int *d_err;                // device word raised by a kernel whose bounded wait expired
     long long grid_polls = 1ll << 22;   // poll limit of the GMRES grid barriers (ddm_set_wait_limit)
+    int m2l_compress = 2;      // compressed M2L: 0 never, 1 always, 2 automatic (ddm_set_m2l_compression)
+    int m2l_rank = 0;          // its rank (0: the default per order)
     double *h_pin = nullptr;   // pinned host staging (tree build: element end points)
     int64_t h_pin_cap = 0;
 };
@@ -226,6 +243,14 @@ ddm_status window_self_blocks(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, c
 ddm_status ensure_workspace(ddm_ctx *ctx, ddm_tree *t);
 // M2L operator set of window (lo, hi) for tree t (cached per window)
 ddm_status window_ops(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, cudaStream_t s, const float **out);
+// compressed M2L (svd.cu): rank per order (0 = no compression), and the
+// bases and cores of one window from its full operators
+int svd_rank(const ddm_ctx *ctx, int n);
+// products a window's full operators serve before the automatic mode compresses them
+constexpr unsigned SVD_AUTO_USES = 128;
+bool want_svd(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, cudaStream_t s);
+ddm_status svd_build(ddm_ctx *ctx, ddm_tree *t, const float *ops, int k, cudaStream_t s, float *pre, float *post,
+                     float *core);
 // many problems' FMM products, one launch per stage (trees of one order):
 // y_p = [K(hi) - K(lo)] x_p for every problem p (fmm.cu)
 struct BatchFmm;

@@ -523,10 +523,12 @@ void tree_free(ddm_tree *t) {
     if (!t) return;
     void *ps[] = {t->mk_work, t->pb_off, t->pb_elem, t->pb_moff, t->pb_inv, t->pc_blk, t->pc_inv, t->mk_off, t->mk_pair, t->perm, t->cell_key, t->cell_ix, t->cell_iy, t->cell_start, t->cell_end, t->cell_parent,
                   t->il_off, t->il_idx, t->nb_off, t->nb_idx, t->nb_tab, t->near_items, t->elem_leaf, t->g_rel, t->g_frame,
-                  t->xy_sorted, t->xy_caller, t->W, t->Fl, t->far4, t->chg};
+                  t->xy_sorted, t->xy_caller, t->W, t->Fl, t->far4, t->chg, t->lv_off, t->lv_pair, t->lv_work,
+                  t->Wc, t->Gc};
     for (void *p : ps) dfree(p, t->stream);
     for (double *p : t->win_blk) dfree(p, t->stream);
     for (float *p : t->ops_set) dfree(p, t->stream);
+    for (float *p : t->svd_set) dfree(p, t->stream);
     delete t;
 }
 

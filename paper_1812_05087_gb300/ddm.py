@@ -29,7 +29,8 @@ EXPORTS = ("ddm_create", "ddm_destroy", "ddm_last_error", "ddm_device_check", "d
            "ddm_tree_get_info", "ddm_matvec", "ddm_history_apply", "ddm_rhs", "ddm_gmres_solve", "ddm_sif",
            "ddm_profile", "ddm_profile_read", "ddm_batch_create", "ddm_batch_destroy", "ddm_batch_matvec",
            "ddm_batch_gmres_solve", "ddm_server_create", "ddm_submit", "ddm_poll", "ddm_server_destroy",
-           "ddm_matvec_dense_static", "ddm_set_wait_limit", "ddm_build_tree_params", "ddm_autotune")
+           "ddm_matvec_dense_static", "ddm_set_wait_limit", "ddm_build_tree_params", "ddm_autotune",
+           "ddm_set_m2l_compression")
 STATIC_MAX_ELEMENTS = 65536
 NSTAGES = 10
 STAGES = ("prep", "self_blocks", "up", "m2l_ops", "m2l", "down", "leaf", "dense", "krylov", "tree")
@@ -113,6 +114,7 @@ def load(build_if_missing: bool = True):
         L.ddm_sif.argtypes = [_VP, _VP, _VP, _VP, ctypes.c_int, _VP, _VP]
         L.ddm_profile.argtypes = [_VP, ctypes.c_int]
         L.ddm_set_wait_limit.argtypes = [_VP, ctypes.c_int64]
+        L.ddm_set_m2l_compression.argtypes = [_VP, ctypes.c_int, ctypes.c_int]
         L.ddm_build_tree_params.argtypes = [_VP, _VP, ctypes.c_int64, ctypes.POINTER(ddm_fmm_params), ctypes.POINTER(_VP)]
         L.ddm_autotune.argtypes = [_VP, _VP, ctypes.c_int64, _VP, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
                                    ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_double,
@@ -275,6 +277,12 @@ def ddm_device_check(ctx):
 def ddm_set_wait_limit(ctx, polls=0):
     """Poll limit of the GMRES grid barriers (0 = the default)."""
     _check(ctx, load().ddm_set_wait_limit(ctx, int(polls)), "ddm_set_wait_limit")
+
+
+def ddm_set_m2l_compression(ctx, mode=2, rank=0):
+    """Compressed M2L operators: mode 0 never, 1 always (n >= 8), 2 automatic;
+    rank 0 = the default per order."""
+    _check(ctx, load().ddm_set_m2l_compression(ctx, int(mode), int(rank)), "ddm_set_m2l_compression")
 
 
 def ddm_profile_read(ctx) -> dict:
@@ -496,6 +504,9 @@ class Context:
 
     def set_wait_limit(self, polls=0):
         ddm_set_wait_limit(self.ptr, polls)
+
+    def set_m2l_compression(self, mode=2, rank=0):
+        ddm_set_m2l_compression(self.ptr, mode, rank)
 
     def close(self):
         if self.ptr:
