@@ -869,12 +869,12 @@ __device__ __forceinline__ void warp_sum_ds(float &h, float &l) {
 template <bool PRECISE>
 __global__ void __launch_bounds__(NEAR_T, 4) k_near(KConst<float> k, KConst<double> kd, Win<float> w, Win<double> wd,
                                                  const int32_t *nboff, const int4 *nbtab, const int32_t *elem_leaf,
-                                                 const float4 *grel, const float4 *frame, const float4 *chg,
+                                                 const float4 *grel, const float4 *gloc, const float2 *ggrid,
+                                                 float g16, const float4 *frame, const float4 *chg,
                                                  const int64_t *perm, int64_t loff, float wL, int n, int nq,
                                                  const float *F, int use_far, int64_t N, double scale, double *y) {
     constexpr unsigned FULL = 0xFFFFFFFFu;
     __shared__ int sst[NEAR_W][9], spre[NEAR_W][10];
-    __shared__ float sox[NEAR_W][9], soy[NEAR_W][9];
     __shared__ int2 sq[NEAR_W][NEAR_Q];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t ti = (int64_t)blockIdx.x * NEAR_W + wid;
@@ -892,14 +892,15 @@ __global__ void __launch_bounds__(NEAR_T, 4) k_near(KConst<float> k, KConst<doub
         if (lane < nb) {
             sst[wid][lane] = tb.x;
             spre[wid][lane + 1] = incl;
-            sox[wid][lane] = wL * (float)tb.z;
-            soy[wid][lane] = wL * (float)tb.w;
         }
         if (lane == 0) spre[wid][0] = 0;
     }
     __syncwarp();
-    const float4 rt = grel[ti];
-    const float mx = 0.5f * (rt.x + rt.z), my = 0.5f * (rt.y + rt.w);
+    // pairs: positions relative to the target's grid point (exact grid
+    // differences times g16); L2P: the target relative to its leaf centre
+    const float4 lt = gloc[ti];
+    const float2 gt = ggrid[ti];
+    const float mx = 0.5f * (lt.x + lt.z), my = 0.5f * (lt.y + lt.w);
     const int S = spre[wid][nb];
     // lanes 0, 1, 2 write sigma_s, sigma_n, p at the end: fetch what they need now
     int64_t eout = 0;
@@ -924,11 +925,12 @@ __global__ void __launch_bounds__(NEAR_T, 4) k_near(KConst<float> k, KConst<doub
             while (c >= spre[wid][slot + 1]) ++slot;
             sj = sst[wid][slot] + (c - spre[wid][slot]);
             if (sj != (int)ti) {
-                r = grel[sj];
+                r = gloc[sj];
                 f = frame[sj];
                 cg = chg[sj];
-                ox = sox[wid][slot];
-                oy = soy[wid][slot];
+                const float2 gs = ggrid[sj];
+                ox = g16 * (gs.x - gt.x);
+                oy = g16 * (gs.y - gt.y);
                 float dx = mx - 0.5f * (r.x + r.z) - ox, dy = my - 0.5f * (r.y + r.w) - oy;
                 float r2 = dx * dx + dy * dy;
                 if (r2 > 64.f * f.z * f.z)
@@ -974,8 +976,9 @@ __global__ void __launch_bounds__(NEAR_T, 4) k_near(KConst<float> k, KConst<doub
                     unit = 2 + (u - nd) - pi * nf;
                 }
                 const int2 e = sq[wid][pi];
-                const float4 r = grel[e.x], f = frame[e.x], cg = chg[e.x];
-                const float ox = sox[wid][e.y], oy = soy[wid][e.y];
+                const float4 r = gloc[e.x], f = frame[e.x], cg = chg[e.x];
+                const float2 gs = ggrid[e.x];
+                const float ox = g16 * (gs.x - gt.x), oy = g16 * (gs.y - gt.y);
                 near_unit<PRECISE>(unit, nq, k, kd, w, wd, mx, my, r.x + ox, r.y + oy, r.z + ox, r.w + oy, f.z, f.x,
                                    f.y, cg.x, cg.y, cg.z, acc, accd);
             }
@@ -999,7 +1002,9 @@ __global__ void __launch_bounds__(NEAR_T, 4) k_near(KConst<float> k, KConst<doub
         float tv = 0.f;
         bool hit = false;
         if (j < n) {
-            float d = __fdividef(isy ? my : mx, hL) - cheb[j];
+            const float4 rt = grel[ti];
+            const float lx = 0.5f * (rt.x + rt.z), ly = 0.5f * (rt.y + rt.w);
+            float d = __fdividef(isy ? ly : lx, hL) - cheb[j];
             hit = fabsf(d) < 1e-7f;
             tv = hit ? 0.f : __fdividef(bw[j], d);
         }
@@ -1062,14 +1067,13 @@ __global__ void __launch_bounds__(NEAR_T, 4) k_near(KConst<float> k, KConst<doub
 // known at compile time and the two-sided code paths drop out of the kernel
 template <bool TWO>
 __device__ __forceinline__ void near2_body(const KConst<float> &k, const Win<float> &win, const int32_t *nboff,
-                                           const int4 *nbtab, const int32_t *elem_leaf, const float4 *grel,
-                                           const float4 *frame, const float4 *chg, const int64_t *perm, float wL,
-                                           int nq, const int2 *items, int64_t N, double scale, double *y,
-                                           int64_t item) {
+                                           const int4 *nbtab, const int32_t *elem_leaf, const float4 *gloc,
+                                           const float2 *ggrid, const float4 *frame, const float4 *chg,
+                                           const int64_t *perm, float g16, int nq, const int2 *items, int64_t N,
+                                           double scale, double *y, int64_t item) {
     const Win<float> w = TWO ? win : Win<float>{win.ct_hi, 0.f, win.g_hi, 0.f, 1};
     constexpr unsigned FULL = 0xFFFFFFFFu;
     __shared__ int sst[NEAR_W][9], spre[NEAR_W][10];
-    __shared__ float sox[NEAR_W][9], soy[NEAR_W][9];
     __shared__ int2 sq[NEAR_W][NEAR_Q];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int2 it = items[item];
@@ -1088,15 +1092,17 @@ __device__ __forceinline__ void near2_body(const KConst<float> &k, const Win<flo
         if (lane < nb) {
             sst[wid][lane] = tb.x;
             spre[wid][lane + 1] = incl;
-            sox[wid][lane] = wL * (float)tb.z;
-            soy[wid][lane] = wL * (float)tb.w;
         }
         if (lane == 0) spre[wid][0] = 0;
     }
     __syncwarp();
-    const float4 ra = grel[t0], rb = grel[t1];
+    // every position below is relative to target 0's grid point: an
+    // element's own offset from its grid point plus the exact grid
+    // difference times g16 (rounded once, relative to the distance)
+    const float4 ra = gloc[t0], rb = gloc[t1];
+    const float2 ga = ggrid[t0], gb = ggrid[t1];
     const float mx0 = 0.5f * (ra.x + ra.z), my0 = 0.5f * (ra.y + ra.w);
-    const float mx1 = 0.5f * (rb.x + rb.z), my1 = 0.5f * (rb.y + rb.w);
+    const float mx1 = fmaf(gb.x - ga.x, g16, 0.5f * (rb.x + rb.z)), my1 = fmaf(gb.y - ga.y, g16, 0.5f * (rb.y + rb.w));
     const int S = spre[wid][nb];
     // lanes 0-2 write target 0's rows, lanes 3-5 target 1's: fetch what they need now
     const bool writer = lane < 3 || (two && lane < 6);
@@ -1120,8 +1126,9 @@ __device__ __forceinline__ void near2_body(const KConst<float> &k, const Win<flo
         if (c < S) {
             while (c >= spre[wid][slot + 1]) ++slot;
             sj = sst[wid][slot] + (c - spre[wid][slot]);
-            const float4 r = grel[sj], f = frame[sj], cg = chg[sj];
-            const float cxs = 0.5f * (r.x + r.z) + sox[wid][slot], cys = 0.5f * (r.y + r.w) + soy[wid][slot];
+            const float4 r = gloc[sj], f = frame[sj], cg = chg[sj];
+            const float2 gs = ggrid[sj];
+            const float cxs = fmaf(gs.x - ga.x, g16, 0.5f * (r.x + r.z)), cys = fmaf(gs.y - ga.y, g16, 0.5f * (r.y + r.w));
             const float lim = 64.f * f.z * f.z;
             hasq = cg.z != 0.f;
             if (sj != t0) {
@@ -1149,8 +1156,9 @@ __device__ __forceinline__ void near2_body(const KConst<float> &k, const Win<flo
                     if (pos < NEAR_Q) {
                         sq[wid][pos] = make_int2(sj, slot | (tg << 8));
                     } else {                  // queue full: this pair in place
-                        const float4 r = grel[sj], f = frame[sj], cg = chg[sj];
-                        const float ox = sox[wid][slot], oy = soy[wid][slot];
+                        const float4 r = gloc[sj], f = frame[sj], cg = chg[sj];
+                        const float2 gs = ggrid[sj];
+                        const float ox = g16 * (gs.x - ga.x), oy = g16 * (gs.y - ga.y);
                         const int nu = 2 + (cg.z != 0.f ? nq : 0);
                         float a4[4] = {0, 0, 0, 0};
                         for (int u = 0; u < nu; ++u)
@@ -1186,9 +1194,10 @@ __device__ __forceinline__ void near2_body(const KConst<float> &k, const Win<flo
                     unit = 2 + (u - nd) - pi * nf;
                 }
                 const int2 e = sq[wid][pi];
-                const int sl = e.y & 0xFF, tg = e.y >> 8;
-                const float4 r = grel[e.x], f = frame[e.x], cg = chg[e.x];
-                const float ox = sox[wid][sl], oy = soy[wid][sl];
+                const int tg = e.y >> 8;
+                const float4 r = gloc[e.x], f = frame[e.x], cg = chg[e.x];
+                const float2 gs = ggrid[e.x];
+                const float ox = g16 * (gs.x - ga.x), oy = g16 * (gs.y - ga.y);
                 float a4[4] = {0, 0, 0, 0};
                 near_unit<false>(unit, nq, k, KConst<double>{}, w, Win<double>{}, tg ? mx1 : mx0, tg ? my1 : my0,
                                  r.x + ox, r.y + oy, r.z + ox, r.w + oy, f.z, f.x, f.y, cg.x, cg.y, cg.z, a4, dummy);
@@ -1228,13 +1237,13 @@ __device__ __forceinline__ void near2_body(const KConst<float> &k, const Win<flo
 }
 template <bool TWO>
 __global__ void __launch_bounds__(NEAR_T, 4) k_near2(KConst<float> k, Win<float> w, const int32_t *nboff,
-                                                     const int4 *nbtab, const int32_t *elem_leaf, const float4 *grel,
-                                                     const float4 *frame, const float4 *chg, const int64_t *perm,
-                                                     float wL, int nq, const int2 *items, int64_t n_items, int64_t N,
-                                                     double scale, double *y) {
+                                                     const int4 *nbtab, const int32_t *elem_leaf, const float4 *gloc,
+                                                     const float2 *ggrid, const float4 *frame, const float4 *chg,
+                                                     const int64_t *perm, float g16, int nq, const int2 *items,
+                                                     int64_t n_items, int64_t N, double scale, double *y) {
     const int64_t item = (int64_t)blockIdx.x * NEAR_W + (threadIdx.x >> 5);
     if (item >= n_items) return;              // whole warp leaves together
-    near2_body<TWO>(k, w, nboff, nbtab, elem_leaf, grel, frame, chg, perm, wL, nq, items, N, scale, y, item);
+    near2_body<TWO>(k, w, nboff, nbtab, elem_leaf, gloc, ggrid, frame, chg, perm, g16, nq, items, N, scale, y, item);
 }
 
 // far field at the targets (from k_down) rotated to each target frame and
@@ -1256,22 +1265,22 @@ __global__ void k_far_add(const float4 *far4, const float4 *frame, const int64_t
 // -------------------------------------------------------------------- dense
 constexpr int DN_T = 128;
 template <bool PRECISE>
-__global__ void __launch_bounds__(DN_T) k_dense(KConst<float> k, KConst<double> kd, Win<float> w, Win<double> wd, int nq, int64_t loff, const int32_t *elem_leaf,
-                                                const int32_t *cix, const int32_t *ciy, const float4 *grel,
+__global__ void __launch_bounds__(DN_T) k_dense(KConst<float> k, KConst<double> kd, Win<float> w, Win<double> wd,
+                                                int nq, const float4 *gloc, const float2 *ggrid, float g16,
                                                 const float4 *frame, const float4 *chg, const int64_t *perm,
-                                                float wL, int64_t N, int64_t chunk, double scale, double *y) {
+                                                int64_t N, int64_t chunk, double scale, double *y) {
     __shared__ SrcTile tile[DN_T];
-    __shared__ int sjx[DN_T], sjy[DN_T];
+    __shared__ float sgx[DN_T], sgy[DN_T];
     int64_t ti = blockIdx.x * (int64_t)DN_T + threadIdx.x;
     bool act = ti < N;
     float mx = 0, my = 0, ttx = 1, tty = 0;
-    int ixI = 0, iyI = 0;
-    if (act) {
-        float4 r = grel[ti], f = frame[ti];
+    float gtx = 0.f, gty = 0.f;
+    if (act) {                                // positions relative to the target's grid point
+        float4 r = gloc[ti], f = frame[ti];
         mx = 0.5f * (r.x + r.z); my = 0.5f * (r.y + r.w);
         ttx = f.x; tty = f.y;
-        int32_t c = elem_leaf[ti];
-        ixI = cix[loff + c]; iyI = ciy[loff + c];
+        const float2 g = ggrid[ti];
+        gtx = g.x; gty = g.y;
     }
     double accd[4] = {0, 0, 0, 0};
     int64_t s0 = blockIdx.y * chunk;
@@ -1280,14 +1289,14 @@ __global__ void __launch_bounds__(DN_T) k_dense(KConst<float> k, KConst<double> 
         __syncthreads();
         int64_t sj = sb + threadIdx.x;
         if (sj < s1) {
-            float4 r = grel[sj], f = frame[sj], c = chg[sj];
+            float4 r = gloc[sj], f = frame[sj], c = chg[sj];
             SrcTile s;
             s.x0 = r.x; s.y0 = r.y; s.x1 = r.z; s.y1 = r.w;
             s.Dx = c.x; s.Dy = c.y; s.q = c.z; s.a = f.z; s.tx = f.x; s.ty = f.y; s.idx = (int)sj;
             tile[threadIdx.x] = s;
-            int32_t cl = elem_leaf[sj];
-            sjx[threadIdx.x] = cix[loff + cl];
-            sjy[threadIdx.x] = ciy[loff + cl];
+            const float2 g = ggrid[sj];
+            sgx[threadIdx.x] = g.x;
+            sgy[threadIdx.x] = g.y;
         }
         __syncthreads();
         int cnt = (int)(s1 - sb < DN_T ? s1 - sb : DN_T);
@@ -1296,7 +1305,7 @@ __global__ void __launch_bounds__(DN_T) k_dense(KConst<float> k, KConst<double> 
             for (int j = 0; j < cnt; ++j) {
                 if (tile[j].idx == (int)ti) continue;
                 SrcTile s = tile[j];
-                float ox = wL * (float)(sjx[j] - ixI), oy = wL * (float)(sjy[j] - iyI);
+                const float ox = g16 * (sgx[j] - gtx), oy = g16 * (sgy[j] - gty);
                 s.x0 += ox; s.y0 += oy; s.x1 += ox; s.y1 += oy;
                 pair_field<PRECISE>(k, kd, w, wd, nq, mx, my, s, acc, accd);
             }
@@ -1689,9 +1698,9 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
         chunks = (N + chunk - 1) / chunk;
         prof_begin(ctx, 7);
         auto kdn = k_dense<false>;          // precise dense products take k_dense_exact above
-        kdn<<<dim3((unsigned)tiles, (unsigned)chunks), DN_T, 0, s>>>(kf, ctx->kd, wf, wd, nq, loff, t->elem_leaf, t->cell_ix, t->cell_iy,
-                                                                        t->g_rel, t->g_frame, t->chg, t->perm, wL, N,
-                                                                        chunk, scale, y);
+        kdn<<<dim3((unsigned)tiles, (unsigned)chunks), DN_T, 0, s>>>(kf, ctx->kd, wf, wd, nq, t->g_loc, t->g_grid,
+                                                                     t->g16, t->g_frame, t->chg, t->perm, N, chunk,
+                                                                     scale, y);
         prof_end(ctx, 7, 1);
         DDM_CUDA_TRY(ctx, cudaGetLastError());
         return DDM_OK;
@@ -1773,11 +1782,11 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
     prof_begin(ctx, 6);
     if (precise)
         k_near<true><<<(unsigned)((N + NEAR_W - 1) / NEAR_W), NEAR_T, 0, s>>>(
-            kf, ctx->kd, wf, wd, t->nb_off, t->nb_tab, t->elem_leaf, t->g_rel, t->g_frame, t->chg, t->perm, loff, wL,
-            n, nq, t->Fl, 0, N, scale, y);
+            kf, ctx->kd, wf, wd, t->nb_off, t->nb_tab, t->elem_leaf, t->g_rel, t->g_loc, t->g_grid, t->g16,
+            t->g_frame, t->chg, t->perm, loff, wL, n, nq, t->Fl, 0, N, scale, y);
     else
         (lo > 0.0 ? k_near2<true> : k_near2<false>)<<<(unsigned)((t->n_items + NEAR_W - 1) / NEAR_W), NEAR_T, 0, s>>>(
-            kf, wf, t->nb_off, t->nb_tab, t->elem_leaf, t->g_rel, t->g_frame, t->chg, t->perm, wL, nq,
+            kf, wf, t->nb_off, t->nb_tab, t->elem_leaf, t->g_loc, t->g_grid, t->g_frame, t->chg, t->perm, t->g16, nq,
             t->near_items, t->n_items, N, scale, y);
     prof_end(ctx, 6, 1);
     if (use_far) {
@@ -1806,7 +1815,8 @@ struct BDesc {
     const double *x;
     double *y;
     const int64_t *perm;
-    const float4 *g_frame, *g_rel;
+    const float4 *g_frame, *g_rel, *g_loc;
+    const float2 *g_grid;
     const double *blk;
     float4 *chg;
     float *W, *Fl;
@@ -1822,7 +1832,7 @@ struct BDesc {
     const float *ops;
     int64_t n, loff, zoff;
     int L, nq;
-    float wL, hL;
+    float wL, hL, g16;
 };
 constexpr int BE_T = 256, BE_CHUNK = 1024;
 // items (p, kind, a, b): kind 0 prepares elements [a, b), kind 1 zeroes the
@@ -1885,8 +1895,8 @@ __global__ void __launch_bounds__(NEAR_T, 4) k_near2_b(KConst<float> k, Win<floa
     const int2 w = items[g];
     if (act && !act[w.x]) return;
     const BDesc &d = D[w.x];
-    near2_body<TWO>(k, win, d.nb_off, d.nb_tab, d.elem_leaf, d.g_rel, d.g_frame, d.chg, d.perm, d.wL, d.nq,
-                    d.near_items, d.n, scale, d.y, w.y);
+    near2_body<TWO>(k, win, d.nb_off, d.nb_tab, d.elem_leaf, d.g_loc, d.g_grid, d.g_frame, d.chg, d.perm, d.g16,
+                    d.nq, d.near_items, d.n, scale, d.y, w.y);
 }
 // items (p, 0, a, b): far field of elements [a, b) into y
 __global__ void __launch_bounds__(BE_T) k_far_add_b(const BDesc *D, const int4 *items, int nitems, double scale,
@@ -1958,6 +1968,7 @@ ddm_status bfmm_build(ddm_ctx *ctx, ddm_tree *const *trees, int np, const int *i
         BDesc &d = hd[p];
         d.x = xs[p]; d.y = ys[p];
         d.perm = t->perm; d.g_frame = t->g_frame; d.g_rel = t->g_rel; d.blk = blk;
+        d.g_loc = t->g_loc; d.g_grid = t->g_grid; d.g16 = t->g16;
         d.chg = t->chg; d.W = t->W; d.Fl = t->Fl; d.far4 = t->far4;
         d.cstart = t->cell_start; d.cend = t->cell_end; d.cix = t->cell_ix; d.ciy = t->cell_iy;
         d.parent = t->cell_parent;

@@ -56,8 +56,16 @@ struct ddm_tree {
     int64_t n_items;
     int32_t *elem_leaf;        // sorted element -> leaf index (leaf-local)
     // sorted element geometry, FP32 relative to the element's leaf centre
-    float4 *g_rel;             // (x0, y0, x1, y1) rel. to leaf centre
+    float4 *g_rel;             // (x0, y0, x1, y1) rel. to leaf centre (expansions)
     float4 *g_frame;           // (tx, ty, half-length, 0)
+    // pair geometry of the near field and the dense product: the element's
+    // grid point (midpoint cell of the 2^16 x 2^16 key grid, index as exact
+    // floats) and its end points relative to that point, so that the
+    // displacement of two elements is (g_s - g_t) g16 + (loc_s - loc_t),
+    // exact to FP32 rounding of the displacement itself
+    float2 *g_grid = nullptr;
+    float4 *g_loc = nullptr;
+    float g16 = 0.f;
     double *xy_sorted;         // 4 x n FP64 absolute end points (sorted order)
     double *xy_caller;         // 4 x n FP64 end points, caller order (copy of the input)
     // Per time window (tau_lo, tau_hi) caches, least recently used first out:

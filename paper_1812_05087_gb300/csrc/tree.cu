@@ -399,7 +399,8 @@ __global__ void k_ilist(const uint32_t *ckey, const int32_t *cix, const int32_t 
 
 __global__ void k_geom(const double *xy, int64_t n, const int32_t *idx, const int32_t *elem_leaf,
                        const int32_t *cix, const int32_t *ciy, int64_t loff, double x0, double y0,
-                       double wl, int64_t *perm, float4 *g_rel, float4 *g_frame, double *xys) {
+                       double wl, double w16, int64_t *perm, float4 *g_rel, float4 *g_frame, float2 *g_grid,
+                       float4 *g_loc, double *xys) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     int64_t e = idx[i];
@@ -409,6 +410,11 @@ __global__ void k_geom(const double *xy, int64_t n, const int32_t *idx, const in
     int32_t c = elem_leaf[i];
     double ccx = x0 + (cix[loff + c] + 0.5) * wl, ccy = y0 + (ciy[loff + c] + 0.5) * wl;
     g_rel[i] = make_float4((float)(ax - ccx), (float)(ay - ccy), (float)(bx - ccx), (float)(by - ccy));
+    const double gx = fmin(fmax(floor((0.5 * (ax + bx) - x0) / w16), 0.0), 65535.0);
+    const double gy = fmin(fmax(floor((0.5 * (ay + by) - y0) / w16), 0.0), 65535.0);
+    const double hx = x0 + (gx + 0.5) * w16, hy = y0 + (gy + 0.5) * w16;
+    g_grid[i] = make_float2((float)gx, (float)gy);
+    g_loc[i] = make_float4((float)(ax - hx), (float)(ay - hy), (float)(bx - hx), (float)(by - hy));
     double L = hypot(bx - ax, by - ay);
     g_frame[i] = make_float4((float)((bx - ax) / L), (float)((by - ay) / L), (float)(0.5 * L), 0.f);
 }
@@ -522,7 +528,7 @@ static void find_chains(const double *hxy, int64_t n, Chains &out) {
 void tree_free(ddm_tree *t) {
     if (!t) return;
     void *ps[] = {t->mk_work, t->pb_off, t->pb_elem, t->pb_moff, t->pb_inv, t->pc_blk, t->pc_inv, t->mk_off, t->mk_pair, t->perm, t->cell_key, t->cell_ix, t->cell_iy, t->cell_start, t->cell_end, t->cell_parent,
-                  t->il_off, t->il_idx, t->nb_off, t->nb_idx, t->nb_tab, t->near_items, t->elem_leaf, t->g_rel, t->g_frame,
+                  t->il_off, t->il_idx, t->nb_off, t->nb_idx, t->nb_tab, t->near_items, t->elem_leaf, t->g_rel, t->g_frame, t->g_grid, t->g_loc,
                   t->xy_sorted, t->xy_caller, t->W, t->Fl, t->far4, t->chg, t->lv_off, t->lv_pair, t->lv_work,
                   t->Wc, t->Gc};
     for (void *p : ps) dfree(p, t->stream);
@@ -832,14 +838,17 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, const ddm_fmm
     TRY(dalloc(&t->elem_leaf, n * sizeof(int32_t), st));
     TRY(dalloc(&t->g_rel, n * sizeof(float4), st));
     TRY(dalloc(&t->g_frame, n * sizeof(float4), st));
+    TRY(dalloc(&t->g_grid, n * sizeof(float2), st));
+    TRY(dalloc(&t->g_loc, n * sizeof(float4), st));
     TRY(dalloc(&t->xy_sorted, 4 * n * sizeof(double), st));
     TRY(dalloc(&t->xy_caller, 4 * n * sizeof(double), st));
     TRY(cudaMemcpyAsync(t->xy_caller, d_xy, 4 * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     TRY(dalloc(&t->chg, n * sizeof(float4), st));
     TRY(cudaMemcpyAsync(t->elem_leaf, ecell[L], n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
     double wl = 2.0 * h0 / (double)side;
-    k_geom<<<nbk, TB, 0, st>>>(d_xy, n, idx, t->elem_leaf, t->cell_ix, t->cell_iy, loff, X0, Y0, wl, t->perm,
-                              t->g_rel, t->g_frame, t->xy_sorted); ++tl_launches;
+    k_geom<<<nbk, TB, 0, st>>>(d_xy, n, idx, t->elem_leaf, t->cell_ix, t->cell_iy, loff, X0, Y0, wl, w16, t->perm,
+                              t->g_rel, t->g_frame, t->g_grid, t->g_loc, t->xy_sorted); ++tl_launches;
+    t->g16 = (float)w16;
     // preconditioner blocks: the chain search (host worker thread, started
     // after the bounding box) is joined here
     {
