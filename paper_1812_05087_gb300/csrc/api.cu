@@ -389,6 +389,8 @@ void ddm_destroy(ddm_ctx *ctx) {
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     if (ctx->h_pin) cudaFreeHost(ctx->h_pin);
+    if (ctx->hist_M) cudaFree(ctx->hist_M);
+    if (ctx->hist_C) cudaFree(ctx->hist_C);
     if (ctx->gm) { ctx->gm->release(); delete ctx->gm; }
     delete ctx;
 }
@@ -488,6 +490,7 @@ ddm_status ddm_history_apply(ddm_ctx *ctx, const ddm_tree *tree, const double *d
     for (int k = 0; k <= H; ++k)
         if (!(h_times[k + 1] > h_times[k])) return ctx_fail(ctx, DDM_EINVAL, "ddm_history_apply: times must increase");
     ddm_tree *t = const_cast<ddm_tree *>(tree);
+    if (ctx->hist_E > 0 && H > ctx->hist_E) return history_compressed(ctx, t, d_hist, h_times, H, d_rhs, mode);
     int64_t N = t->n;
     double tobs = h_times[H + 1];
     for (int eta = 1; eta <= H; ++eta) {

@@ -205,6 +205,13 @@ struct ddm_ctx {
     long long grid_polls = 1ll << 22;   // poll limit of the GMRES grid barriers (ddm_set_wait_limit)
     int m2l_compress = 2;      // compressed M2L: 0 never, 1 always, 2 automatic (ddm_set_m2l_compression)
     int m2l_rank = 0;          // its rank (0: the default per order)
+    // time-compressed history (history.cu, ddm_set_history_compression):
+    // exact most recent steps (0 = off), nodes per block, block ratio; moment
+    // and weight workspaces
+    int hist_E = 0, hist_p = 10;
+    double hist_rho = 2.0;
+    double *hist_M = nullptr, *hist_C = nullptr;
+    int64_t hist_M_cap = 0, hist_C_cap = 0;
     double *h_pin = nullptr;   // pinned host staging (tree build: element end points)
     int64_t h_pin_cap = 0;
 };
@@ -257,6 +264,9 @@ int svd_rank(const ddm_ctx *ctx, int n);
 // products a window's full operators serve before the automatic mode compresses them
 constexpr unsigned SVD_AUTO_USES = 128;
 bool want_svd(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, cudaStream_t s);
+// history sum with the older steps interpolated in log time (history.cu)
+ddm_status history_compressed(ddm_ctx *ctx, ddm_tree *t, const double *d_hist, const double *h_times, int H,
+                              double *d_rhs, int mode);
 ddm_status svd_build(ddm_ctx *ctx, ddm_tree *t, const float *ops, int k, cudaStream_t s, float *pre, float *post,
                      float *core);
 // many problems' FMM products, one launch per stage (trees of one order):

@@ -30,7 +30,7 @@ EXPORTS = ("ddm_create", "ddm_destroy", "ddm_last_error", "ddm_device_check", "d
            "ddm_profile", "ddm_profile_read", "ddm_batch_create", "ddm_batch_destroy", "ddm_batch_matvec",
            "ddm_batch_gmres_solve", "ddm_server_create", "ddm_submit", "ddm_poll", "ddm_server_destroy",
            "ddm_matvec_dense_static", "ddm_set_wait_limit", "ddm_build_tree_params", "ddm_autotune",
-           "ddm_set_m2l_compression")
+           "ddm_set_m2l_compression", "ddm_set_history_compression")
 STATIC_MAX_ELEMENTS = 65536
 NSTAGES = 10
 STAGES = ("prep", "self_blocks", "up", "m2l_ops", "m2l", "down", "leaf", "dense", "krylov", "tree")
@@ -115,6 +115,7 @@ def load(build_if_missing: bool = True):
         L.ddm_profile.argtypes = [_VP, ctypes.c_int]
         L.ddm_set_wait_limit.argtypes = [_VP, ctypes.c_int64]
         L.ddm_set_m2l_compression.argtypes = [_VP, ctypes.c_int, ctypes.c_int]
+        L.ddm_set_history_compression.argtypes = [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_double]
         L.ddm_build_tree_params.argtypes = [_VP, _VP, ctypes.c_int64, ctypes.POINTER(ddm_fmm_params), ctypes.POINTER(_VP)]
         L.ddm_autotune.argtypes = [_VP, _VP, ctypes.c_int64, _VP, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
                                    ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_double,
@@ -283,6 +284,13 @@ def ddm_set_m2l_compression(ctx, mode=2, rank=0):
     """Compressed M2L operators: mode 0 never, 1 always (n >= 8), 2 automatic;
     rank 0 = the default per order."""
     _check(ctx, load().ddm_set_m2l_compression(ctx, int(mode), int(rank)), "ddm_set_m2l_compression")
+
+
+def ddm_set_history_compression(ctx, exact_steps=0, nodes=10, ratio=2.0):
+    """Time-compressed history sum: exact_steps most recent steps exact (0 =
+    off), older steps interpolated in log time at `nodes` points per block."""
+    _check(ctx, load().ddm_set_history_compression(ctx, int(exact_steps), int(nodes), float(ratio)),
+           "ddm_set_history_compression")
 
 
 def ddm_profile_read(ctx) -> dict:
@@ -507,6 +515,9 @@ class Context:
 
     def set_m2l_compression(self, mode=2, rank=0):
         ddm_set_m2l_compression(self.ptr, mode, rank)
+
+    def set_history_compression(self, exact_steps=0, nodes=10, ratio=2.0):
+        ddm_set_history_compression(self.ptr, exact_steps, nodes, ratio)
 
     def close(self):
         if self.ptr:
