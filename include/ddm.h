@@ -57,7 +57,8 @@ typedef enum {
     DDM_ENOTCONV = 3,   /* GMRES did not reach tol; solution and residual still written */
     DDM_ETIMEOUT = 4,   /* a bounded device wait expired */
     DDM_ECUDA = 5,
-    DDM_PENDING = 6     /* ddm_poll: request still running */
+    DDM_PENDING = 6,    /* ddm_poll: request still running */
+    DDM_ECANCELED = 7   /* ddm_poll: request cancelled (ddm_server_cancel) */
 } ddm_status;
 
 /* Poroelastic rock (paper Table 1 quantities): shear modulus G, drained and
@@ -336,6 +337,26 @@ ddm_status ddm_server_create(ddm_ctx *ctx, size_t hbm_budget_bytes, int max_acti
                              ddm_server **out);
 ddm_status ddm_submit(ddm_server *server, const ddm_request *req, uint64_t *ticket);
 ddm_status ddm_poll(ddm_server *server, uint64_t ticket, ddm_result *result);
+/* Cancel every request not finished: queued ones leave the queue, active
+ * ones stop before their next time step (a round in flight completes);
+ * their status becomes DDM_ECANCELED and their x_out holds no result.
+ * Later submissions are served as usual.  ddm_server_destroy alone waits
+ * for every submitted request to finish. */
+ddm_status ddm_server_cancel(ddm_server *server);
+
+/* Where the server thread's time went since its start (host clock, ms):
+ * rounds, time-step solves done, admission (tree builds), history sums and
+ * right-hand sides, batch set-up, batched GMRES, and the rest. */
+typedef struct {
+    int64_t rounds;
+    int64_t solves;
+    double ms_admit;
+    double ms_history;
+    double ms_setup;
+    double ms_solve;
+    double ms_other;
+} ddm_server_stats;
+ddm_status ddm_server_get_stats(ddm_server *server, ddm_server_stats *stats);
 void ddm_server_destroy(ddm_server *server);
 
 /* Dense influence product that allocates nothing (no counterpart in the

@@ -59,6 +59,9 @@ struct ddm_server {
     std::map<uint64_t, Req *> all;
     uint64_t next_id = 1;
     bool stop = false;
+    bool cancel_active = false;          // ddm_server_cancel: drop the active requests before the next round
+    ddm_server_stats stats{};            // guarded by mu
+    Clock::time_point t_start = Clock::now();
     std::thread th;
     long long rounds = 0;
 };
@@ -70,7 +73,8 @@ size_t footprint(const ddm_request &r, int ncheb) {
     // tree arrays, plus one cached M2L operator set per time window the
     // request's steps use (about half of the (level, offset) keys occur)
     size_t opset = (size_t)8 * 49 * 16 * ncheb * ncheb * ncheb * ncheb * 4;
-    size_t per_tree = N * 400 + (size_t)r.steps * opset;
+    // (the tree's operator cache holds at most 4 GB of sets)
+    size_t per_tree = N * 400 + std::min((size_t)r.steps * opset, std::max(opset, (size_t)4 << 30));
     size_t vectors = N * 3 * 8 * (size_t)(r.steps + 1 + 60);
     return per_tree + vectors;
 }
@@ -106,7 +110,9 @@ void serve_loop(ddm_server *S) {
                     st = DDM_ENOMEM;
                 if (!st && dalloc(&q->rhs, (size_t)3 * q->r.n * sizeof(double), s) != cudaSuccess) st = DDM_ENOMEM;
                 if (!st) cudaMemsetAsync(q->hist, 0, (size_t)q->r.steps * 3 * q->r.n * sizeof(double), s);
+                cudaStreamSynchronize(s);
                 lk.lock();
+                S->stats.ms_admit += ms_since(q->t_admit, Clock::now());
                 if (st) {
                     release(q, s);
                     S->used -= q->footprint;
@@ -117,13 +123,31 @@ void serve_loop(ddm_server *S) {
                 }
             }
         }
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            if (S->cancel_active) {
+                for (Req *q : active) {
+                    release(q, s);
+                    S->used -= q->footprint;
+                    q->status = DDM_ECANCELED;
+                    q->t_done = Clock::now();
+                }
+                active.clear();
+                S->cancel_active = false;
+                S->cv.notify_all();
+            }
+        }
         if (active.empty()) continue;
         // one round: one time step of every active request (same dt per round
         // group; requests are grouped by dt and system)
         std::map<std::pair<double, int>, std::vector<Req *>> groups;
         for (Req *q : active) groups[{q->r.dt, q->r.loads.system}].push_back(q);
+        double t_hist = 0.0, t_setup = 0.0, t_solve = 0.0;
+        int64_t n_solves = 0;
+        const auto t_round = Clock::now();
         for (auto &g : groups) {
             std::vector<Req *> &rs = g.second;
+            auto t0 = Clock::now();
             double dt = g.first.first;
             int sys = g.first.second;
             ddm_status st = DDM_OK;
@@ -155,12 +179,21 @@ void serve_loop(ddm_server *S) {
             }
             ddm_batch *B = nullptr;
             std::vector<ddm_gmres_info> infos(rs.size());
+            cudaStreamSynchronize(s);
+            auto t1 = Clock::now();
+            t_hist += ms_since(t0, t1);
             if (!st) st = ddm_batch_create(S->ctx, trees.data(), (int)trees.size(), &B);
+            cudaStreamSynchronize(s);
+            auto t2 = Clock::now();
+            t_setup += ms_since(t1, t2);
             if (!st) {
                 ddm_gmres_params prm{sys, 50, 2000, S->tol, DDM_MODE_FMM};
                 st = ddm_batch_gmres_solve(S->ctx, B, dt, rhs, x, &prm, infos.data());
                 if (st == DDM_ENOTCONV) st = DDM_OK;      // per-request status below
             }
+            cudaStreamSynchronize(s);
+            t_solve += ms_since(t2, Clock::now());
+            n_solves += (int64_t)rs.size();
             o = 0;
             for (size_t i = 0; i < rs.size(); ++i) {
                 Req *q = rs[i];
@@ -187,6 +220,12 @@ void serve_loop(ddm_server *S) {
         // retire finished requests
         std::lock_guard<std::mutex> lk(S->mu);
         ++S->rounds;
+        S->stats.rounds += 1;
+        S->stats.solves += n_solves;
+        S->stats.ms_history += t_hist;
+        S->stats.ms_setup += t_setup;
+        S->stats.ms_solve += t_solve;
+        S->stats.ms_other += ms_since(t_round, Clock::now()) - t_hist - t_setup - t_solve;
         std::vector<Req *> keep;
         for (Req *q : active) {
             if (q->step >= q->r.steps) {
@@ -214,6 +253,13 @@ ddm_status ddm_server_create(ddm_ctx *ctx, size_t hbm_budget_bytes, int max_acti
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) { delete S; return DDM_ECUDA; }
     ddm_status r = ddm_create(&S->ctx, &ctx->mat, &ctx->prm, st);
     if (r) { cudaStreamDestroy(st); delete S; return r; }
+    // the server context takes the creating context's runtime settings
+    S->ctx->grid_polls = ctx->grid_polls;
+    S->ctx->m2l_compress = ctx->m2l_compress;
+    S->ctx->m2l_rank = ctx->m2l_rank;
+    S->ctx->hist_E = ctx->hist_E;
+    S->ctx->hist_p = ctx->hist_p;
+    S->ctx->hist_rho = ctx->hist_rho;
     S->budget = hbm_budget_bytes ? hbm_budget_bytes : ((size_t)64 << 30);
     S->max_active = max_active;
     S->tol = tol;
@@ -255,6 +301,27 @@ ddm_status ddm_poll(ddm_server *S, uint64_t ticket, ddm_result *res) {
     res->latency_ms = done ? ms_since(q->t_submit, q->t_done) : -1.0;
     if (!done) return DDM_PENDING;
     return q->status;
+}
+
+ddm_status ddm_server_get_stats(ddm_server *S, ddm_server_stats *out) {
+    if (!S || !out) return DDM_EINVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    *out = S->stats;
+    return DDM_OK;
+}
+
+ddm_status ddm_server_cancel(ddm_server *S) {
+    if (!S) return DDM_EINVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    const auto now = Clock::now();
+    for (Req *q : S->queue) {
+        q->status = DDM_ECANCELED;
+        q->t_done = now;
+    }
+    S->queue.clear();
+    S->cancel_active = true;
+    S->cv.notify_all();
+    return DDM_OK;
 }
 
 void ddm_server_destroy(ddm_server *S) {

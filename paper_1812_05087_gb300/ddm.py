@@ -19,7 +19,7 @@ import torch
 
 from . import build as _build
 
-DDM_OK, DDM_EINVAL, DDM_ENOMEM, DDM_ENOTCONV, DDM_ETIMEOUT, DDM_ECUDA, DDM_PENDING = range(7)
+DDM_OK, DDM_EINVAL, DDM_ENOMEM, DDM_ENOTCONV, DDM_ETIMEOUT, DDM_ECUDA, DDM_PENDING, DDM_ECANCELED = range(8)
 MODE_FMM, MODE_DENSE, MODE_PRECISE = 0, 1, 16
 SYS_PRESSURE, SYS_IMPERMEABLE, SYS_RATE = 0, 1, 2
 _MODES = {"fmm": MODE_FMM, "dense": MODE_DENSE, "fmm+precise": MODE_FMM | MODE_PRECISE,
@@ -30,7 +30,8 @@ EXPORTS = ("ddm_create", "ddm_destroy", "ddm_last_error", "ddm_device_check", "d
            "ddm_profile", "ddm_profile_read", "ddm_batch_create", "ddm_batch_destroy", "ddm_batch_matvec",
            "ddm_batch_gmres_solve", "ddm_server_create", "ddm_submit", "ddm_poll", "ddm_server_destroy",
            "ddm_matvec_dense_static", "ddm_set_wait_limit", "ddm_build_tree_params", "ddm_autotune",
-           "ddm_set_m2l_compression", "ddm_set_history_compression")
+           "ddm_set_m2l_compression", "ddm_set_history_compression", "ddm_server_cancel",
+           "ddm_server_get_stats")
 STATIC_MAX_ELEMENTS = 65536
 NSTAGES = 10
 STAGES = ("prep", "self_blocks", "up", "m2l_ops", "m2l", "down", "leaf", "dense", "krylov", "tree")
@@ -64,6 +65,12 @@ class ddm_gmres_params(ctypes.Structure):
 class ddm_request(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("d_xy", ctypes.c_void_p), ("loads", ddm_loads), ("dt", ctypes.c_double),
                 ("steps", ctypes.c_int), ("d_x", ctypes.c_void_p)]
+
+
+class ddm_server_stats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int64), ("solves", ctypes.c_int64), ("ms_admit", ctypes.c_double),
+                ("ms_history", ctypes.c_double), ("ms_setup", ctypes.c_double), ("ms_solve", ctypes.c_double),
+                ("ms_other", ctypes.c_double)]
 
 
 class ddm_result(ctypes.Structure):
@@ -127,6 +134,8 @@ def load(build_if_missing: bool = True):
         L.ddm_poll.argtypes = [_VP, ctypes.c_uint64, ctypes.POINTER(ddm_result)]
         L.ddm_server_destroy.argtypes = [_VP]
         L.ddm_server_destroy.restype = None
+        L.ddm_server_cancel.argtypes = [_VP]
+        L.ddm_server_get_stats.argtypes = [_VP, ctypes.POINTER(ddm_server_stats)]
         L.ddm_batch_create.argtypes = [_VP, ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP)]
         L.ddm_batch_destroy.argtypes = [_VP]
         L.ddm_batch_destroy.restype = None
@@ -365,6 +374,12 @@ def ddm_poll(server, ticket) -> dict:
     return d
 
 
+def ddm_server_cancel(server):
+    st = load().ddm_server_cancel(server)
+    if st:
+        raise DDMError(st, "ddm_server_cancel failed")
+
+
 def ddm_server_destroy(server):
     load().ddm_server_destroy(server)
 
@@ -383,6 +398,17 @@ class Server:
 
     def poll(self, ticket) -> dict:
         return ddm_poll(self.ptr, ticket)
+
+    def stats(self) -> dict:
+        s = ddm_server_stats()
+        st = load().ddm_server_get_stats(self.ptr, ctypes.byref(s))
+        if st:
+            raise DDMError(st, "ddm_server_get_stats failed")
+        return {k: getattr(s, k) for k, _ in ddm_server_stats._fields_}
+
+    def cancel(self):
+        """Cancel every unfinished request (status DDM_ECANCELED)."""
+        ddm_server_cancel(self.ptr)
 
     def close(self):
         if self.ptr:

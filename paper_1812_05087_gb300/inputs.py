@@ -70,9 +70,20 @@ def random_fracture_segments(n_frac=200, box=200.0, lmin=2.0, lmax=10.0, elems=1
     centre uniform (whole segment inside), length U[lmin, lmax], angle
     U[0, pi); a candidate is rejected if it intersects an accepted crack or
     lies closer to it than one element length of either.  Returns a list of
-    (p0, p1, n_elems)."""
+    (p0, p1, n_elems).  Accepted cracks are bucketed on a grid of cell side
+    >= lmax so that a candidate is tested only against cracks near it (the
+    same draws and the same accept/reject decisions as testing all)."""
     rng = np.random.default_rng(seed)
     segs = []
+    cell = max(lmax, 1e-12)
+    margin = lmax / elems                     # the largest separation a rejection can need
+    grid = {}
+
+    def cells(x0, y0, x1, y1):
+        for i in range(int(math.floor(x0 / cell)), int(math.floor(x1 / cell)) + 1):
+            for j in range(int(math.floor(y0 / cell)), int(math.floor(y1 / cell)) + 1):
+                yield (i, j)
+
     tries = 0
     while len(segs) < n_frac:
         tries += 1
@@ -85,13 +96,25 @@ def random_fracture_segments(n_frac=200, box=200.0, lmin=2.0, lmax=10.0, elems=1
         cy = rng.uniform(abs(hy), box - abs(hy))
         p0, p1 = (cx - hx, cy - hy), (cx + hx, cy + hy)
         ok = True
-        for (q0, q1, _) in segs:
-            sep = max(L, math.hypot(q1[0] - q0[0], q1[1] - q0[1])) / elems
-            if _seg_dist(p0, p1, q0, q1) < sep:
-                ok = False
+        seen = set()
+        for c in cells(min(p0[0], p1[0]), min(p0[1], p1[1]), max(p0[0], p1[0]), max(p0[1], p1[1])):
+            for k in grid.get(c, ()):
+                if k in seen:
+                    continue
+                seen.add(k)
+                q0, q1, _ = segs[k]
+                sep = max(L, math.hypot(q1[0] - q0[0], q1[1] - q0[1])) / elems
+                if _seg_dist(p0, p1, q0, q1) < sep:
+                    ok = False
+                    break
+            if not ok:
                 break
         if ok:
+            k = len(segs)
             segs.append((p0, p1, elems))
+            for c in cells(min(p0[0], p1[0]) - margin, min(p0[1], p1[1]) - margin,
+                           max(p0[0], p1[0]) + margin, max(p0[1], p1[1]) + margin):
+                grid.setdefault(c, []).append(k)
     return segs
 
 
@@ -164,6 +187,17 @@ def serving_trace(duration=60.0, rate=50.0, nmin=1000, nmax=200000, seed=SEED + 
         N = int(round(math.exp(rng.uniform(math.log(nmin), math.log(nmax)))))
         out.append({"t": t, "N": N, "steps": int(rng.integers(1, 101)), "seed": int(rng.integers(1 << 30))})
     return out
+
+
+def serving_geometry(n_target, seed):
+    """Fracture set of one serving request: about n_target elements as
+    n_target / 100 random fractures of 100 elements (lengths U[2, 10] m, the
+    element size of the 20,000-element set) in a box whose side grows with
+    sqrt(n_target), so the fracture density stays that of the 20,000-element
+    set at every size."""
+    nf = max(1, n_target // 100)
+    box = 200.0 * (n_target / 20000.0) ** 0.5 + 12.0
+    return assemble(random_fracture_segments(nf, box, 2.0, min(10.0, box / 2), 100, seed=seed))
 
 
 def unknowns(n, seed=SEED, dd_scale=1e-4, q_scale=1e-9):

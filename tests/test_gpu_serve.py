@@ -75,3 +75,80 @@ def test_mix_equals_alone_and_oracle():
     b = oracle.rhs(g, system="pressure", **LOADS)
     ref = oracle.march(MAT, g, times, [b] * steps)[-1]
     assert block_rel_err(mix[0], ref, n) < 1e-3
+
+
+def fracture_set(n_target, seed):
+    """A random fracture set of about n_target elements (the serving trace's
+    recipe, inputs.serving_geometry)."""
+    return inputs.serving_geometry(n_target, seed)
+
+
+def test_cancel_stops_queued_and_active_requests():
+    ctx = Context(inputs.MATERIAL, n_cheb=8, leaf_size=32)
+    srv = Server(ctx, max_active=2, tol=1e-5)
+    xys = [dev(fracture_set(3000, 700 + k)) for k in range(8)]
+    outs = [torch.zeros(3 * (g.numel() // 4), dtype=torch.float64, device="cuda") for g in xys]
+    tickets = [srv.submit(g, o, 10.0, 50, **LOADS) for g, o in zip(xys, outs)]
+    t0 = time.time()
+    while srv.poll(tickets[0])["steps_done"] < 2:
+        assert time.time() - t0 < 120.0
+        time.sleep(0.01)
+    srv.cancel()
+    res = wait(srv, tickets, limit=60.0)
+    st = [res[t]["status"] for t in tickets]
+    assert all(s in (0, 7) for s in st) and st.count(7) >= 6, st
+    # the server keeps serving after a cancel
+    g = dev(fracture_set(1000, 799))
+    o = torch.zeros(3 * (g.numel() // 4), dtype=torch.float64, device="cuda")
+    t = srv.submit(g, o, 10.0, 2, **LOADS)
+    assert wait(srv, [t])[t]["status"] == 0
+    srv.close()
+
+
+def test_large_request_equals_direct_solve():
+    """A request of ~200,000 elements (the top of the serving trace's size
+    range) through the server, against the same step solved directly."""
+    ctx = Context(inputs.MATERIAL, n_cheb=8, leaf_size=32)
+    xy = fracture_set(200000, 901)
+    N = xy.shape[1]
+    assert N > 150000
+    g = dev(xy)
+    srv = Server(ctx, max_active=4, tol=1e-5)
+    o = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
+    t = srv.submit(g, o, 10.0, 1, **LOADS)
+    r = wait(srv, [t], limit=300.0)[t]
+    srv.close()
+    assert r["status"] == 0
+    tree = ctx.build_tree(g)
+    b = ctx.rhs(tree, system="pressure", **LOADS)
+    x, info = ctx.gmres_solve(tree, 10.0, b, system="pressure", tol=1e-5)
+    assert info["converged"]
+    assert block_rel_err(o.cpu().numpy(), x.cpu().numpy(), N) < 1e-3
+
+
+def test_server_takes_history_compression_of_its_context():
+    """A 40-step request in a server created from a context with the
+    time-compressed history sum equals the same march run on that context."""
+    ctx = Context(inputs.MATERIAL, n_cheb=8, leaf_size=16)
+    ctx.set_history_compression(8, 8, 2.0)
+    xy = fracture_set(1500, 950)
+    N = xy.shape[1]
+    g = dev(xy)
+    steps, dt = 40, 10.0
+    srv = Server(ctx, max_active=2, tol=1e-6)
+    o = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
+    t = srv.submit(g, o, dt, steps, **LOADS)
+    r = wait(srv, [t], limit=300.0)[t]
+    srv.close()
+    assert r["status"] == 0
+    tree = ctx.build_tree(g)
+    b0 = ctx.rhs(tree, system="pressure", **LOADS)
+    hist = torch.zeros(steps, 3 * N, dtype=torch.float64, device="cuda")
+    x = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
+    for h in range(1, steps + 1):
+        b = b0.clone()
+        if h > 1:
+            ctx.history_apply(tree, hist[:h - 1], [dt * k for k in range(h + 1)], b)
+        x, info = ctx.gmres_solve(tree, dt, b, x, system="pressure", tol=1e-6)
+        hist[h - 1] = x
+    assert block_rel_err(o.cpu().numpy(), x.cpu().numpy(), N) < 1e-3
