@@ -326,9 +326,13 @@ ddm_status ddm_create(ddm_ctx **out, const ddm_material *mat, const ddm_fmm_para
     kd.eta = eta;
     kd.i4pk = 1 / (4 * M_PI * kappa);
     kd.c = kappa / S;
+    kd.Cu = kd.Cel + 2 * kd.G2 * kd.K2;
+    kd.pS = kd.aS * kd.Ce;
+    kd.a6 = 6 * kd.G2 * kd.K2;
+    kd.qe = kd.eta * kd.i4pk;
     c->kd = kd;
     c->kf = KConst<float>{(float)kd.G2, (float)kd.Cel, (float)kd.Ce, (float)kd.K2, (float)kd.aS, (float)kd.eta,
-                          (float)kd.i4pk, (float)kd.c};
+                          (float)kd.i4pk, (float)kd.c, (float)kd.Cu, (float)kd.pS, (float)kd.a6, (float)kd.qe};
     // M2M / L2L transfer matrices T[q][a][a'] = S_n(xi_a, (xi_a' + q)/2)
     int n = p.n_cheb;
     std::vector<double> xi(n);

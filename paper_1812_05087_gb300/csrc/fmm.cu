@@ -748,11 +748,52 @@ __device__ __forceinline__ void far_node(int ng, int g, float &xi, float &wt) {
         wt = 1.f;
     }
 }
+// A source element as the far-pair rule needs it, built once per source
+// and shared by every target: potency per unit length as trace, Pxx - Pyy
+// and 2 Pxy (DD vector D, normal n: P = sym(D n)), fluid source,
+// half-length and tangent, and the squared distances below which 3 Gauss
+// points are taken (24 a) and beyond which every Gauss point is at u > Big
+// on both sides of the window ((a + rbig)^2).
+struct FarSrc {
+    float Pd, P2, Tr, q, a, tx, ty, r2_3pt, r2_big;
+};
+__device__ __forceinline__ FarSrc far_src(float a, float tx, float ty, float Dx, float Dy, float q, float rbig) {
+    const float nx = -ty, ny = tx, pxx = Dx * nx, pyy = Dy * ny, rb = a + rbig;
+    return FarSrc{pxx - pyy, Dx * ny + Dy * nx, pxx + pyy, q, a, tx, ty, 576.f * a * a, rb * rb};
+}
+// FP32 far pair from a prepared source
+__device__ __forceinline__ void far_pair_f(const KConst<float> &k, const Win<float> &w, float dx, float dy, float r2,
+                                           const FarSrc &s, float acc[4]) {
+    const int ng = r2 <= s.r2_3pt ? 3 : 2;
+    if (r2 > s.r2_big) {
+        // every Gauss point at u > Big: the rational (complex) form
+        const float d4ct = 4.f * (w.ct_hi - w.ct_lo);
+        const float ce = w.elastic ? k.Cu : 0.f, pc = w.elastic ? k.pS : 0.f;
+        float o[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+        for (int g = 0; g < ng; ++g) {
+            float xi, wt;
+            far_node(ng, g, xi, wt);
+            const float sg = xi * s.a;
+            pot_bigu(dx - sg * s.tx, dy - sg * s.ty, s.Pd, s.P2, s.Tr, s.q, ce, pc, k.a6 * d4ct, -k.qe * d4ct, wt, o);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[c] = fmaf(s.a, o[c], acc[c]);
+        return;
+    }
+    const float Pxx = 0.5f * (s.Tr + s.Pd), Pyy = 0.5f * (s.Tr - s.Pd), Pxy = 0.5f * s.P2;
+#pragma unroll 1
+    for (int g = 0; g < ng; ++g) {
+        float xi, wt;
+        far_node(ng, g, xi, wt);
+        const float sg = xi * s.a, wg = wt * s.a;
+        pot_kernel<float>(k, dx - sg * s.tx, dy - sg * s.ty, wg * Pxx, wg * Pyy, wg * Pxy, wg * s.q, w, acc);
+    }
+}
 template <bool PRECISE>
 __device__ __forceinline__ void far_pair(const KConst<float> &k, const KConst<double> &kd, const Win<float> &w,
                                          const Win<double> &wd, float dx, float dy, float r2, float a, float tx,
                                          float ty, float Dx, float Dy, float q, float acc[4], double accd[4]) {
-    const int ng = (PRECISE || r2 <= 576.f * a * a) ? 3 : 2;
     if (PRECISE) {
         double nx = -(double)ty, ny = (double)tx;
         double Pxx = Dx * nx, Pyy = Dy * ny, Pxy = 0.5 * (Dx * ny + Dy * nx);
@@ -766,29 +807,7 @@ __device__ __forceinline__ void far_pair(const KConst<float> &k, const KConst<do
         }
         return;
     }
-    float nx = -ty, ny = tx;
-    float Pxx = Dx * nx, Pyy = Dy * ny, Pxy = 0.5f * (Dx * ny + Dy * nx);
-    // every Gauss point at u > 30 on both sides (the hi side has the smaller
-    // u): the rational form of the kernel (pot_bigu)
-    float rmin = sqrtf(r2) - a;
-    if (rmin * rmin * w.g_hi > Big<float>::U) {
-        const float d4ct = 4.f * (w.ct_hi - w.ct_lo);
-#pragma unroll 1
-        for (int g = 0; g < ng; ++g) {
-            float xi, wt;
-            far_node(ng, g, xi, wt);
-            float sg = xi * a, wg = wt * a;
-            pot_bigu(k, dx - sg * tx, dy - sg * ty, wg * Pxx, wg * Pyy, wg * Pxy, wg * q, w.elastic, d4ct, acc);
-        }
-        return;
-    }
-#pragma unroll 1
-    for (int g = 0; g < ng; ++g) {
-        float xi, wt;
-        far_node(ng, g, xi, wt);
-        float sg = xi * a, wg = wt * a;
-        pot_kernel<float>(k, dx - sg * tx, dy - sg * ty, wg * Pxx, wg * Pyy, wg * Pxy, wg * q, w, acc);
-    }
+    far_pair_f(k, w, dx, dy, r2, far_src(a, tx, ty, Dx, Dy, q, w.rbig), acc);
 }
 
 // Close pairs (r <= 8 a), split into units: unit 0 / 1 = the dislocation
@@ -1071,7 +1090,7 @@ __device__ __forceinline__ void near2_body(const KConst<float> &k, const Win<flo
                                            const float2 *ggrid, const float4 *frame, const float4 *chg,
                                            const int64_t *perm, float g16, int nq, const int2 *items, int64_t N,
                                            double scale, double *y, int64_t item) {
-    const Win<float> w = TWO ? win : Win<float>{win.ct_hi, 0.f, win.g_hi, 0.f, 1};
+    const Win<float> w = TWO ? win : Win<float>{win.ct_hi, 0.f, win.g_hi, 0.f, 1, win.rbig};
     constexpr unsigned FULL = 0xFFFFFFFFu;
     __shared__ int sst[NEAR_W][9], spre[NEAR_W][10];
     __shared__ int2 sq[NEAR_W][NEAR_Q];
@@ -1130,17 +1149,16 @@ __device__ __forceinline__ void near2_body(const KConst<float> &k, const Win<flo
             const float2 gs = ggrid[sj];
             const float cxs = fmaf(gs.x - ga.x, g16, 0.5f * (r.x + r.z)), cys = fmaf(gs.y - ga.y, g16, 0.5f * (r.y + r.w));
             const float lim = 64.f * f.z * f.z;
+            const FarSrc fs = far_src(f.z, f.x, f.y, cg.x, cg.y, cg.z, w.rbig);
             hasq = cg.z != 0.f;
             if (sj != t0) {
                 const float dx = mx0 - cxs, dy = my0 - cys, r2 = dx * dx + dy * dy;
-                if (r2 > lim) far_pair<false>(k, KConst<double>{}, w, Win<double>{}, dx, dy, r2, f.z, f.x, f.y, cg.x,
-                                              cg.y, cg.z, acc0, dummy);
+                if (r2 > lim) far_pair_f(k, w, dx, dy, r2, fs, acc0);
                 else close0 = true;
             }
             if (two && sj != t1) {
                 const float dx = mx1 - cxs, dy = my1 - cys, r2 = dx * dx + dy * dy;
-                if (r2 > lim) far_pair<false>(k, KConst<double>{}, w, Win<double>{}, dx, dy, r2, f.z, f.x, f.y, cg.x,
-                                              cg.y, cg.z, acc1, dummy);
+                if (r2 > lim) far_pair_f(k, w, dx, dy, r2, fs, acc1);
                 else close1 = true;
             }
         }
@@ -1475,6 +1493,7 @@ static Win<T> make_win(const ddm_ctx *ctx, double lo, double hi) {
     w.g_hi = (T)(1.0 / (4.0 * c * hi));
     w.g_lo = (T)(lo > 0.0 ? 1.0 / (4.0 * c * lo) : 0.0);
     w.elastic = lo > 0.0 ? 0 : 1;
+    w.rbig = (T)std::sqrt((double)Big<T>::U * 4.0 * c * hi);
     return w;
 }
 

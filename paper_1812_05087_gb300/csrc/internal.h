@@ -22,6 +22,11 @@ struct KConst {
     T eta;     // poroelastic stress coefficient alpha (1 - 2nu) / (2 (1 - nu))
     T i4pk;    // 1 / (4 pi kappa)                 line-source pressure prefactor
     T c;       // hydraulic diffusivity kappa / S
+    // products of the above used by the large-u point kernel
+    T Cu;      // Cel + 2 G2 K2                    undrained elastic prefactor
+    T pS;      // aS Ce                            undrained pressure prefactor
+    T a6;      // 6 G2 K2                          linear-in-time stress term
+    T qe;      // eta / (4 pi kappa)               linear-in-time fluid-source stress term
 };
 
 // Time window of one product: [K(tau_hi) - K(tau_lo)], K(0) = 0.
@@ -32,6 +37,7 @@ struct Win {
     T ct_hi, ct_lo;
     T g_hi, g_lo;      // 1/(4 ct_*) (0 when ct_* = 0)
     int elastic;
+    T rbig;            // distance beyond which u > Big on both sides: sqrt(Big / g_hi)
 };
 
 struct ddm_tree {

@@ -337,23 +337,34 @@ DEV void pot_kernel(const KConst<T> &k, T x, T y, T Pxx, T Pyy, T Pxy, T q, cons
 //      R = Pxy (x^4 - 6x^2y^2 + y^4) - 2 (Pxx-Pyy) xy (x^2-y^2),
 // d4ct = 4c (t_hi - t_lo) (t_lo = 0 for the elastic window): the t-free
 // transient terms of the two sides cancel in a time element.
-DEV void pot_bigu(const KConst<float> &k, float x, float y, float Pxx, float Pyy, float Pxy, float q, int elastic,
-                  float d4ct, float acc[4]) {
-    float x2 = x * x, y2 = y * y, xy = x * y;
-    float ir2 = __fdividef(1.f, x2 + y2), ir4 = ir2 * ir2;
-    float d = x2 - y2, dPm = Pxx - Pyy;
-    if (elastic) {
-        float C = (k.Cel + 2.f * k.G2 * k.K2) * ir4 * ir2;
-        float A1 = x2 * x2, B1 = y2 * y2, Cm = x2 * y2;
-        acc[0] -= C * (Pxx * (3.f * A1 - 6.f * Cm - B1) + Pyy * (-A1 + 6.f * Cm - B1) +
-                       Pxy * xy * (12.f * x2 - 4.f * y2));
-        acc[1] += C * (Pxx * (A1 - 6.f * Cm + B1) + Pyy * (A1 + 6.f * Cm - 3.f * B1) +
-                       Pxy * xy * (4.f * x2 - 12.f * y2));
-        acc[2] += C * (Pxx * xy * (-6.f * x2 + 2.f * y2) + 2.f * Pxy * (A1 - 6.f * Cm + B1) +
-                       Pyy * xy * (2.f * x2 - 6.f * y2));
-        acc[3] += k.aS * k.Ce * (dPm * d + 4.f * Pxy * xy) * ir4;
-    }
-    pot_asym<float>(k, x, y, Pxx, Pyy, Pxy, q, d4ct, acc);
+//
+// Evaluated in complex form: with z = x + i y, the potency written as its
+// trace Tr = Pxx + Pyy and Pi = (Pxx - Pyy) + 2 i Pxy, and conj(Pi) z^2,
+// conj(Pi) z^4 the only angular factors, the elastic stresses are
+//   sxx + syy = -2 C Re(conj(Pi) z^2) / r^4,
+//   syy - sxx =  2 C (Tr Re(z^2) / r^4 + Re(conj(Pi) z^4) / r^6),
+//   sxy       = -  C (Tr Im(z^2) / r^4 + Im(conj(Pi) z^4) / r^6),
+// the pressure is aS Ce Re(conj(Pi) z^2) / r^4, and Q = Re(conj(Pi) z^4),
+// -2 R = Im(conj(Pi) z^4) (the same expansion regrouped; checked against the
+// Cartesian form above to 1e-14 in FP64).  The terms are accumulated times
+// the quadrature weight wt into o; ce = C (0 in a time element), pc = aS Ce
+// (0 in a time element), fa0 = 6 G2 K2 d4ct, fq0 = -eta d4ct / (4 pi kappa).
+DEV void pot_bigu(float x, float y, float Pd, float P2, float Tr, float q, float ce, float pc, float fa0, float fq0,
+                  float wt, float o[4]) {
+    const float x2 = x * x, y2 = y * y;
+    const float ir2 = __fdividef(1.f, x2 + y2), ir4 = ir2 * ir2, ir6 = ir4 * ir2, ir8 = ir4 * ir4;
+    const float re2 = x2 - y2, im2 = 2.f * x * y;
+    const float re4 = re2 * re2 - im2 * im2, im4 = 2.f * re2 * im2;
+    const float pr2 = Pd * re2 + P2 * im2, pr4 = Pd * re4 + P2 * im4, pi4 = Pd * im4 - P2 * re4;
+    const float s = ce * pr2 * ir4;
+    const float dv = ce * (Tr * re2 * ir4 + pr4 * ir6);
+    const float sxy = -ce * (Tr * im2 * ir4 + pi4 * ir6);
+    const float fa = fa0 * ir8, fq = fq0 * q * ir4;
+    const float t0 = fa * pr4 + fq * re2;
+    o[0] = fmaf(wt, -s - dv + t0, o[0]);
+    o[1] = fmaf(wt, -s + dv - t0, o[1]);
+    o[2] = fmaf(wt, sxy + fa * pi4 + fq * im2, o[2]);
+    o[3] = fmaf(wt, pc * pr2 * ir4, o[3]);
 }
 
 // ---------------------------------------------------------------------------
