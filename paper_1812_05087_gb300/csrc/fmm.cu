@@ -755,32 +755,27 @@ __device__ __forceinline__ void far_node(int ng, int g, float &xi, float &wt) {
 // points are taken (24 a) and beyond which every Gauss point is at u > Big
 // on both sides of the window ((a + rbig)^2).
 struct FarSrc {
-    float Pd, P2, Tr, q, a, tx, ty, r2_3pt, r2_big;
+    float Pd, P2, Tr, q, a, tx, ty, r2_big, a2tr, a2ti;
 };
 __device__ __forceinline__ FarSrc far_src(float a, float tx, float ty, float Dx, float Dy, float q, float rbig) {
-    const float nx = -ty, ny = tx, pxx = Dx * nx, pyy = Dy * ny, rb = a + rbig;
-    return FarSrc{pxx - pyy, Dx * ny + Dy * nx, pxx + pyy, q, a, tx, ty, 576.f * a * a, rb * rb};
+    const float nx = -ty, ny = tx, pxx = Dx * nx, pyy = Dy * ny, rb = a + rbig, a2 = a * a;
+    return FarSrc{pxx - pyy, Dx * ny + Dy * nx, pxx + pyy, q, a, tx, ty, rb * rb, a2 * (tx * tx - ty * ty),
+                  2.f * a2 * tx * ty};
 }
-// FP32 far pair from a prepared source
+// FP32 pair from a prepared source, the target at (dx, dy) from its
+// midpoint: where u > Big along the whole element (r > a + rbig), the exact
+// element integral of the rational kernel (at any distance); otherwise
+// (only for r > 8 a) the Gauss rule of the full point kernel
 __device__ __forceinline__ void far_pair_f(const KConst<float> &k, const Win<float> &w, float dx, float dy, float r2,
                                            const FarSrc &s, float acc[4]) {
-    const int ng = r2 <= s.r2_3pt ? 3 : 2;
     if (r2 > s.r2_big) {
-        // every Gauss point at u > Big: the rational (complex) form
         const float d4ct = 4.f * (w.ct_hi - w.ct_lo);
         const float ce = w.elastic ? k.Cu : 0.f, pc = w.elastic ? k.pS : 0.f;
-        float o[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 1
-        for (int g = 0; g < ng; ++g) {
-            float xi, wt;
-            far_node(ng, g, xi, wt);
-            const float sg = xi * s.a;
-            pot_bigu(dx - sg * s.tx, dy - sg * s.ty, s.Pd, s.P2, s.Tr, s.q, ce, pc, k.a6 * d4ct, -k.qe * d4ct, wt, o);
-        }
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[c] = fmaf(s.a, o[c], acc[c]);
+        elem_bigu(dx, dy, s.a2tr, s.a2ti, s.a * s.a, 2.f * s.a, s.Pd, s.P2, s.Tr, s.q, ce, pc, k.a6 * d4ct,
+                  -k.qe * d4ct, acc);
         return;
     }
+    const int ng = r2 <= 576.f * s.a * s.a ? 3 : 2;
     const float Pxx = 0.5f * (s.Tr + s.Pd), Pyy = 0.5f * (s.Tr - s.Pd), Pxy = 0.5f * s.P2;
 #pragma unroll 1
     for (int g = 0; g < ng; ++g) {
@@ -842,7 +837,8 @@ __device__ __forceinline__ void pair_field(const KConst<float> &k, const KConst<
                                            float acc[4], double accd[4]) {
     float dx = mx - 0.5f * (s.x0 + s.x1), dy = my - 0.5f * (s.y0 + s.y1);
     float r2 = dx * dx + dy * dy;
-    if (r2 > 64.f * s.a * s.a) {
+    const float rb = s.a + w.rbig;            // beyond: u > Big along the element (exact integral)
+    if (r2 > 64.f * s.a * s.a || (!PRECISE && r2 > rb * rb)) {
         far_pair<PRECISE>(k, kd, w, wd, dx, dy, r2, s.a, s.tx, s.ty, s.Dx, s.Dy, s.q, acc, accd);
     } else {
         int nu = 2 + (s.q != 0.f ? nq : 0);
@@ -1151,14 +1147,16 @@ __device__ __forceinline__ void near2_body(const KConst<float> &k, const Win<flo
             const float lim = 64.f * f.z * f.z;
             const FarSrc fs = far_src(f.z, f.x, f.y, cg.x, cg.y, cg.z, w.rbig);
             hasq = cg.z != 0.f;
+            // beyond 8 a, or anywhere u > Big along the element: at once
+            const float lim2 = fminf(lim, fs.r2_big);
             if (sj != t0) {
                 const float dx = mx0 - cxs, dy = my0 - cys, r2 = dx * dx + dy * dy;
-                if (r2 > lim) far_pair_f(k, w, dx, dy, r2, fs, acc0);
+                if (r2 > lim2) far_pair_f(k, w, dx, dy, r2, fs, acc0);
                 else close0 = true;
             }
             if (two && sj != t1) {
                 const float dx = mx1 - cxs, dy = my1 - cys, r2 = dx * dx + dy * dy;
-                if (r2 > lim) far_pair_f(k, w, dx, dy, r2, fs, acc1);
+                if (r2 > lim2) far_pair_f(k, w, dx, dy, r2, fs, acc1);
                 else close1 = true;
             }
         }

@@ -346,25 +346,49 @@ DEV void pot_kernel(const KConst<T> &k, T x, T y, T Pxx, T Pyy, T Pxy, T q, cons
 //   sxy       = -  C (Tr Im(z^2) / r^4 + Im(conj(Pi) z^4) / r^6),
 // the pressure is aS Ce Re(conj(Pi) z^2) / r^4, and Q = Re(conj(Pi) z^4),
 // -2 R = Im(conj(Pi) z^4) (the same expansion regrouped; checked against the
-// Cartesian form above to 1e-14 in FP64).  The terms are accumulated times
-// the quadrature weight wt into o; ce = C (0 in a time element), pc = aS Ce
-// (0 in a time element), fa0 = 6 G2 K2 d4ct, fq0 = -eta d4ct / (4 pi kappa).
-DEV void pot_bigu(float x, float y, float Pd, float P2, float Tr, float q, float ce, float pc, float fa0, float fq0,
-                  float wt, float o[4]) {
-    const float x2 = x * x, y2 = y * y;
-    const float ir2 = __fdividef(1.f, x2 + y2), ir4 = ir2 * ir2, ir6 = ir4 * ir2, ir8 = ir4 * ir4;
-    const float re2 = x2 - y2, im2 = 2.f * x * y;
-    const float re4 = re2 * re2 - im2 * im2, im4 = 2.f * re2 * im2;
-    const float pr2 = Pd * re2 + P2 * im2, pr4 = Pd * re4 + P2 * im4, pi4 = Pd * im4 - P2 * re4;
-    const float s = ce * pr2 * ir4;
-    const float dv = ce * (Tr * re2 * ir4 + pr4 * ir6);
-    const float sxy = -ce * (Tr * im2 * ir4 + pi4 * ir6);
-    const float fa = fa0 * ir8, fq = fq0 * q * ir4;
-    const float t0 = fa * pr4 + fq * re2;
-    o[0] = fmaf(wt, -s - dv + t0, o[0]);
-    o[1] = fmaf(wt, -s + dv - t0, o[1]);
-    o[2] = fmaf(wt, sxy + fa * pi4 + fq * im2, o[2]);
-    o[3] = fmaf(wt, pc * pr2 * ir4, o[3]);
+// Cartesian form above to 1e-14 in FP64).  Constants below: ce = C (0 in a
+// time element), pc = aS Ce (0 in a time element), fa0 = 6 G2 K2 d4ct,
+// fq0 = -eta d4ct / (4 pi kappa).
+//
+// Exact integral of this large-u point kernel over a straight source element (half-length
+// a, unit tangent t = tx + i ty, target at z = zx + i zy from the element's
+// midpoint, s over [-a, a]): with D = z^2 - a^2 t^2,
+//   int (z - s t)^-2 ds = 2a / D,
+//   int (z - s t)^-4 ds = 2a (z^2 + a^2 t^2 / 3) / D^3,
+//   int conj(z - s t) (z - s t)^-3 ds = 2a (|z|^2 - a^2) / D^2
+// (the last after writing conj(z - s t) = conj(z) - conj(t)^2 (z - (z - s t))),
+// and the complex-form terms above are Re/Im of Pi or Tr times these
+// (Re(conj(Pi) z^2) / r^4 = Re(Pi / z^2), conj(Pi) z^4 / r^6 = conj(Pi conj(z) / z^3),
+// conj(Pi) z^4 / r^8 = conj(Pi / z^4), z^2 / r^4 = conj(1 / z^2)).  Valid
+// where u > Big along the whole element; exact at any distance there, and
+// free of the cancellation of an end-point difference (checked against a
+// 60-point Gauss rule of the point kernel to 5e-14 in FP64 from 1.3 a outward).
+// a2t2 = a^2 t^2 (complex), a2 = a^2, ta = 2a; acc += the element's field.
+DEV void elem_bigu(float zx, float zy, float a2tr, float a2ti, float a2, float ta, float Pd, float P2, float Tr,
+                   float q, float ce, float pc, float fa0, float fq0, float acc[4]) {
+    const float z2r = zx * zx - zy * zy, z2i = 2.f * zx * zy, zz = zx * zx + zy * zy;
+    const float dr = z2r - a2tr, di = z2i - a2ti;
+    const float inv = __fdividef(1.f, dr * dr + di * di);
+    const float ir = dr * inv, ii = -di * inv;                        // 1 / D
+    const float jr = ir * ir - ii * ii, ji = 2.f * ir * ii;            // 1 / D^2
+    const float kr = jr * ir - ji * ii, ki = jr * ii + ji * ir;        // 1 / D^3
+    const float i2r = ta * ir, i2i = ta * ii;
+    const float m = ta * (zz - a2);
+    const float imr = m * jr, imi = m * ji;
+    const float er = fmaf(a2tr, 1.f / 3.f, z2r), ei = fmaf(a2ti, 1.f / 3.f, z2i);
+    const float i4r = ta * (er * kr - ei * ki), i4i = ta * (er * ki + ei * kr);
+    const float A = Pd * i2r - P2 * i2i;                               // Re(Pi I2)
+    const float rv = Pd * imr - P2 * imi, iv = -(Pd * imi + P2 * imr);  // (Re, -Im)(Pi IM)
+    const float q4 = Pd * i4r - P2 * i4i, r4 = -(Pd * i4i + P2 * i4r);  // (Re, -Im)(Pi I4)
+    const float s = ce * A;
+    const float dv = ce * (Tr * i2r + rv);
+    const float sxy = ce * (Tr * i2i - iv);
+    const float fq = fq0 * q;
+    const float t0 = fa0 * q4 + fq * i2r;
+    acc[0] += -s - dv + t0;
+    acc[1] += -s + dv - t0;
+    acc[2] += sxy + fa0 * r4 - fq * i2i;
+    acc[3] += pc * A;
 }
 
 // ---------------------------------------------------------------------------
