@@ -159,11 +159,11 @@ template <int N>
 __device__ __forceinline__ void up_body(const int32_t *cstart, const int32_t *cend, int64_t loff, int L,
                                         const int32_t *cix, const int32_t *ciy, const int32_t *parent,
                                         const float4 *grel, const float4 *frame, const float4 *chg, float hL, float *W,
-                                        float *Fz, int64_t bid) {
+                                        float *Fz, const float *T, int64_t bid) {
     using S = UpSmem<N>;
     constexpr int N2 = S::N2, NOUT = S::NOUT, SXS = S::SXS, NE = (N2 + 31) / 32, KO = (NOUT + UP_T - 1) / UP_T;
     __shared__ __align__(16) float sm[S::SIZE];
-    __shared__ float sTx[N * N], sTy[N * N];   // leaf -> ancestor transfer, x and y
+    __shared__ float sT0[N * N], sT1[N * N];   // child -> parent transfer of the lower and upper half
     float *sx = sm, *sy = sm + N * SXS;
     float4 *wd = reinterpret_cast<float4 *>(sm + 2 * N * SXS);   // 16-byte aligned: 2 N SXS is a multiple of 4
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -229,85 +229,67 @@ __device__ __forceinline__ void up_body(const int32_t *cstart, const int32_t *ce
             Fc[o] = 0.f;                          // local expansion: M2L adds into it next
         }
     }
-    // M2M straight to every ancestor down to level 2: the transfer from the
-    // leaf grid to an ancestor grid k levels up is again a separable
-    // Chebyshev interpolation, Tx[a][b'] = S_a(ancestor) at the leaf node b'
-    // (exact for the leaf's polynomial interpolant, as each M2M step is), so
-    // the leaves add into their ancestors directly (atomically; the internal
-    // cells were zeroed by the charge kernel) instead of level after level.
-    float *lw = sm + NOUT, *tmp = sm;          // leaf weights, scratch
+    // M2M up the chain of ancestors down to level 2: the leaf's own
+    // contribution takes one child -> parent transfer per level (T[q][a][a'],
+    // q = the child's half in x and in y, the same tables as L2L) and is
+    // added atomically into each ancestor (the internal cells were zeroed by
+    // the charge kernel), so no leaf waits for another.  Composed, the
+    // transfers are the direct leaf -> ancestor interpolation, exactly.
+    float *lw = sm + NOUT, *tmp = sm;          // running contribution, scratch
     __syncthreads();                           // the warp partials are read
 #pragma unroll
     for (int k = 0; k < KO; ++k)
         if (tid + k * UP_T < NOUT) lw[tid + k * UP_T] = wv[k];
-    const float *cheb = c_gl.cheb[N / 2 - 1], *bw = c_gl.bw[N / 2 - 1];
-    const int lx = cix[leaf], ly = ciy[leaf];
-    int64_t anc = leaf;
+    for (int e = tid; e < N * N; e += UP_T) {
+        sT0[e] = T[e];
+        sT1[e] = T[N * N + e];
+    }
+    int64_t child = leaf;
     for (int l = L - 1; l >= 2; --l) {
-        anc = parent[anc];
-        const int k = L - l;                       // levels up
-        const float sc = 1.f / (float)(1 << k);
-        // leaf centre in the ancestor's [-1, 1] coordinates
-        const float cxl = 2.f * (((float)(lx - ((lx >> k) << k)) + 0.5f) * sc) - 1.f;
-        const float cyl = 2.f * (((float)(ly - ((ly >> k) << k)) + 0.5f) * sc) - 1.f;
-        __syncthreads();                           // tmp and the transfer matrices are rewritten
-        for (int e = tid; e < 2 * N * N; e += UP_T) {
-            const int dim = e / (N * N), ab = e % (N * N), aa = ab / N, bp = ab % N;
-            const float xp = (dim ? cyl : cxl) + cheb[bp] * sc;   // leaf node b' in ancestor coordinates
-            float sum = 0.f, va = 0.f;
-            int hit = -1;
+        const int64_t anc = parent[child];
+        const float *Tx = (cix[child] & 1) ? sT1 : sT0, *Ty = (ciy[child] & 1) ? sT1 : sT0;
+        __syncthreads();                           // lw (and the tables) written
+        // tmp[c][a][b'] = sum_a' Tx[a][a'] lw[c][a'][b'];  out = sum_b' Ty[b][b'] tmp[c][a][b']
+        for (int i = tid; i < NOUT; i += UP_T) {
+            const int c = i / N2, aa = (i / N) % N, bb = i % N;
+            const float *src = lw + c * N2 + bb;
+            float sacc = 0.f;
 #pragma unroll
-            for (int j = 0; j < N; ++j) {
-                const float d = xp - cheb[j];
-                if (fabsf(d) < 1e-7f) hit = j;
-                const float t = __fdividef(bw[j], d);
-                sum += t;
-                if (j == aa) va = t;
-            }
-            const float v = hit >= 0 ? (aa == hit ? 1.f : 0.f) : va * __fdividef(1.f, sum);
-            (dim ? sTy : sTx)[aa * N + bp] = v;
+            for (int kk = 0; kk < N; ++kk) sacc = fmaf(Tx[aa * N + kk], src[kk * N], sacc);
+            tmp[i] = sacc;
         }
         __syncthreads();
         float o[KO];
-        {
-            // tmp[c][a][b'] = sum_a' Tx[a][a'] lw[c][a'][b'];  out = sum_b' Ty[b][b'] tmp[c][a][b']
-            for (int i = tid; i < NOUT; i += UP_T) {
-                const int c = i / N2, aa = (i / N) % N, bb = i % N;
-                const float *src = lw + c * N2 + bb;
-                float sacc = 0.f;
 #pragma unroll
-                for (int kk = 0; kk < N; ++kk) sacc = fmaf(sTx[aa * N + kk], src[kk * N], sacc);
-                tmp[i] = sacc;
+        for (int kk = 0; kk < KO; ++kk) {
+            const int oi = tid + kk * UP_T;
+            float sacc = 0.f;
+            if (oi < NOUT) {
+                const int c = oi / N2, aa = (oi / N) % N, bb = oi % N;
+                const float *tc = tmp + c * N2 + aa * N;
+#pragma unroll
+                for (int j = 0; j < N; ++j) sacc = fmaf(Ty[bb * N + j], tc[j], sacc);
             }
-            __syncthreads();
-#pragma unroll
-            for (int kk = 0; kk < KO; ++kk) {
-                const int oi = tid + kk * UP_T;
-                float sacc = 0.f;
-                if (oi < NOUT) {
-                    const int c = oi / N2, aa = (oi / N) % N, bb = oi % N;
-                    const float *tc = tmp + c * N2 + aa * N;
-#pragma unroll
-                    for (int j = 0; j < N; ++j) sacc = fmaf(sTy[bb * N + j], tc[j], sacc);
-                }
-                o[kk] = sacc;
-            }
+            o[kk] = sacc;
         }
         float *Wa = W + anc * NOUT;
 #pragma unroll
         for (int kk = 0; kk < KO; ++kk) {
             const int oi = tid + kk * UP_T;
-            if (oi < NOUT) atomicAdd(Wa + oi, o[kk]);
+            if (oi < NOUT) {
+                lw[oi] = o[kk];
+                atomicAdd(Wa + oi, o[kk]);
+            }
         }
+        child = anc;
     }
-
 }
 template <int N>
 __global__ void __launch_bounds__(UP_T) k_up(const int32_t *cstart, const int32_t *cend, int64_t loff, int L,
                                              const int32_t *cix, const int32_t *ciy, const int32_t *parent,
                                              const float4 *grel, const float4 *frame, const float4 *chg, float hL,
-                                             float *W, float *Fz) {
-    up_body<N>(cstart, cend, loff, L, cix, ciy, parent, grel, frame, chg, hL, W, Fz, blockIdx.x);
+                                             float *W, float *Fz, const float *T) {
+    up_body<N>(cstart, cend, loff, L, cix, ciy, parent, grel, frame, chg, hL, W, Fz, T, blockIdx.x);
 }
 
 // ----------------------------------------------------- downward pass (fused)
@@ -1738,7 +1720,8 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
         prof_begin(ctx, 2);
 #define DDM_UP(NN)                                                                                          \
     k_up<NN><<<(unsigned)nleaf, UP_T, 0, fs>>>(t->cell_start, t->cell_end, loff, L, t->cell_ix, t->cell_iy,         \
-                                               t->cell_parent, t->g_rel, t->g_frame, t->chg, hL, t->W, t->Fl)
+                                               t->cell_parent, t->g_rel, t->g_frame, t->chg, hL, t->W, t->Fl,          \
+                                               ctx->cheb_Tn[NN / 2 - 1])
         DDM_CHEB_SWITCH(n, DDM_UP);
 #undef DDM_UP
         prof_end(ctx, 2, 1);
@@ -1874,13 +1857,14 @@ __global__ void __launch_bounds__(BE_T) k_prep_b(const BDesc *D, const int4 *ite
     }
 }
 template <int N>
-__global__ void __launch_bounds__(UP_T) k_up_b(const BDesc *D, const int2 *items, int nitems, const int *act) {
+__global__ void __launch_bounds__(UP_T) k_up_b(const BDesc *D, const int2 *items, int nitems, const float *T,
+                                               const int *act) {
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const int2 w = items[it];
         if (act && !act[w.x]) continue;      // uniform over the block
         const BDesc &d = D[w.x];
         up_body<N>(d.cstart, d.cend, d.loff, d.L, d.cix, d.ciy, d.parent, d.g_rel, d.g_frame, d.chg, d.hL, d.W, d.Fl,
-                   w.y);
+                   T, w.y);
         __syncthreads();                      // shared staging is reused by the next item
     }
 }
@@ -2057,7 +2041,7 @@ ddm_status bfmm_launch(ddm_ctx *ctx, BatchFmm *b, cudaStream_t s, cudaStream_t a
             DDM_CUDA_TRY(ctx, cudaEventRecord(b->ev_fork, s));
             DDM_CUDA_TRY(ctx, cudaStreamWaitEvent(fs, b->ev_fork, 0));
         }
-#define DDM_UPB(NN) k_up_b<NN><<<grid(b->n_leaf, 4), UP_T, 0, fs>>>(b->desc, b->leaf, b->n_leaf, b->act)
+#define DDM_UPB(NN) k_up_b<NN><<<grid(b->n_leaf, 4), UP_T, 0, fs>>>(b->desc, b->leaf, b->n_leaf, ctx->cheb_Tn[NN / 2 - 1], b->act)
         DDM_CHEB_SWITCH(n, DDM_UPB);
 #undef DDM_UPB
         if (b->n_m2l > 0) {
