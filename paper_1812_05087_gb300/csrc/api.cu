@@ -620,10 +620,13 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
     // falls by less than 10%): level 0 is plain restarted GMRES with the
     // requested products (paper Sec. 4); level 1 recomputes the residuals
     // with the precise products (mixed-precision refinement, inner solves
-    // two decades at a time); level 2 also makes the inner products precise;
-    // three more stalls end the solve.  Long fractures, whose element
-    // contributions cancel strongly, are what reach levels 1 and 2.
+    // two decades at a time); level 2 also makes the Arnoldi products
+    // precise; level 3 (at most EXACT_OP_MAX elements) takes the exact FP64
+    // dense product for them; three more stalls end the solve.  Long
+    // fractures, whose element contributions cancel strongly, are what reach
+    // the higher levels.
     int level = 0;
+    const int mode0 = mode;
     if ((st = lsq_reset_iters(ctx, g.lsq, s))) return st;
     DDM_CUDA_TRY(ctx, cudaMemsetAsync(g.cnt, 0, 4 * sizeof(unsigned), s));   // grid barrier starts at zero
     while (iters < P.max_iters) {
@@ -632,7 +635,7 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
             DDM_CUDA_TRY(ctx, cudaMemsetAsync(g.w, 0, len * sizeof(double), s));
             x_zero = false;
         } else {
-            if ((st = apply(d_x, g.w, residual_mode(mode, level, N)))) return st;
+            if ((st = apply(d_x, g.w, residual_mode(mode0, level, N)))) return st;
         }
         k_axpy<<<nblk(len), 256, 0, s>>>(-1.0, g.b, g.w, len);          // w = A x - b
         double beta;
@@ -640,8 +643,8 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
         rel = beta / bnorm;
         if (rel < P.tol) { conv = true; break; }
         if (rel < 0.9 * best) { best = rel; stall = 0; }
-        else if (level < 2) {
-            if (++level == 2) mode |= DDM_MODE_PRECISE;
+        else if (level < max_level(N)) {
+            mode = arnoldi_mode(mode0, ++level, N);
             stall = 0;
             if (level == 1) {             // re-measure with the precise residual first
                 best = 1e300;

@@ -572,7 +572,7 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
             ddm_status e = pb_apply(ctx, B->trees[p], sys, B->vin + B->offs[p], B->full + B->off3[p], ps);
             if (e) return e;
             e = op_apply(ctx, B->trees[p], 0.0, dt, B->full + B->off3[p], B->y3 + B->off3[p],
-                         mode | (level[p] >= 2 ? DDM_MODE_PRECISE : 0), 0, 1.0, ps);
+                         arnoldi_mode(mode, level[p], n), 0, 1.0, ps);
             if (e) return e;
             k_restrict_b<<<nb(n), BT, 0, ps>>>(B->y3 + B->off3[p], n, sys, 1, B->w + B->offs[p]);
             return DDM_OK;
@@ -685,7 +685,7 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
             rel[p] = beta[p] / bn[p];
             if (rel[p] < Pm.tol) { conv[p] = 1; active[p] = 0; continue; }
             if (rel[p] < 0.9 * best[p]) { best[p] = rel[p]; stall[p] = 0; }
-            else if (level[p] < 2) {
+            else if (level[p] < max_level(B->N[p])) {
                 if (++level[p] == 1) { best[p] = 1e300; remeasure[p] = 1; }
                 stall[p] = 0;
                 reprec = true;
@@ -726,7 +726,7 @@ ddm_status ddm_batch_gmres_solve(ddm_ctx *ctx, ddm_batch *B, double dt, const do
             if (batched) {
                 st = fork_each(ctx, B, s, prec_op, [&](int p, cudaStream_t ps) {
                     return op_apply(ctx, B->trees[p], 0.0, dt, B->full + B->off3[p], B->y3 + B->off3[p],
-                                    mode | DDM_MODE_PRECISE, 0, 1.0, ps);
+                                    arnoldi_mode(mode, level[p], B->N[p]), 0, 1.0, ps);
                 });
                 if (st) return st;
                 k_restrict_bb<<<seg_grid(B->seg[1].n), BT, 0, s>>>(B->seg[1].desc, B->seg[1].items, B->seg[1].n,

@@ -753,8 +753,8 @@ __device__ __forceinline__ void far_pair_f(const KConst<float> &k, const Win<flo
     if (r2 > s.r2_big) {
         const float d4ct = 4.f * (w.ct_hi - w.ct_lo);
         const float ce = w.elastic ? k.Cu : 0.f, pc = w.elastic ? k.pS : 0.f;
-        elem_bigu(dx, dy, s.a2tr, s.a2ti, s.a * s.a, 2.f * s.a, s.Pd, s.P2, s.Tr, s.q, ce, pc, k.a6 * d4ct,
-                  -k.qe * d4ct, acc);
+        elem_bigu<float>(dx, dy, s.a2tr, s.a2ti, s.a * s.a, 2.f * s.a, s.Pd, s.P2, s.Tr, s.q, ce, pc, k.a6 * d4ct,
+                         -k.qe * d4ct, acc);
         return;
     }
     const int ng = r2 <= 576.f * s.a * s.a ? 3 : 2;
@@ -773,6 +773,17 @@ __device__ __forceinline__ void far_pair(const KConst<float> &k, const KConst<do
                                          float ty, float Dx, float Dy, float q, float acc[4], double accd[4]) {
     if (PRECISE) {
         double nx = -(double)ty, ny = (double)tx;
+        const double ad = a, rb = ad + wd.rbig;
+        if ((double)r2 > rb * rb) {
+            // u > Big along the element: the exact rational integral, all in FP64
+            const double d4ct = 4.0 * (wd.ct_hi - wd.ct_lo);
+            const double pxx = Dx * nx, pyy = Dy * ny;
+            const double tdx = tx, tdy = ty;
+            elem_bigu<double>(dx, dy, ad * ad * (tdx * tdx - tdy * tdy), 2.0 * ad * ad * tdx * tdy, ad * ad, 2.0 * ad,
+                              pxx - pyy, Dx * ny + Dy * nx, pxx + pyy, (double)q, wd.elastic ? kd.Cu : 0.0,
+                              wd.elastic ? kd.pS : 0.0, kd.a6 * d4ct, -kd.qe * d4ct, accd);
+            return;
+        }
         double Pxx = Dx * nx, Pyy = Dy * ny, Pxy = 0.5 * (Dx * ny + Dy * nx);
 #pragma unroll
         for (int g = 0; g < 3; ++g) {
@@ -1386,8 +1397,26 @@ __global__ void __launch_bounds__(DX_T) k_dense_exact(KConst<double> kd, Win<dou
         __syncthreads();
         const int cnt = (int)(s1 - sb < DX_T ? s1 - sb : DX_T);
         if (act) {
+            const double d4ct = 4.0 * (wd.ct_hi - wd.ct_lo);
+            const double ce = wd.elastic ? kd.Cu : 0.0, pc = wd.elastic ? kd.pS : 0.0;
+            const double fa0 = kd.a6 * d4ct, fq0 = -kd.qe * d4ct;
             for (int j = 0; j < cnt; ++j) {
                 if (sb + j == ti) continue;
+                {
+                    // u > Big along the whole element: the exact integral of the
+                    // rational large-u kernel (FP64: the remainders are below e^-70)
+                    const double cx = 0.5 * (sx0[j] + sx1[j]), cy = 0.5 * (sy0[j] + sy1[j]);
+                    const double hx = 0.5 * (sx1[j] - sx0[j]), hy = 0.5 * (sy1[j] - sy0[j]);   // a t
+                    const double zx = mx - cx, zy = my - cy, a2 = hx * hx + hy * hy, a = sqrt(a2);
+                    const double rb = a + wd.rbig;
+                    if (zx * zx + zy * zy > rb * rb) {
+                        const double nx = -hy / a, ny = hx / a;
+                        const double pxx = sDx[j] * nx, pyy = sDy[j] * ny;
+                        elem_bigu<double>(zx, zy, hx * hx - hy * hy, 2.0 * hx * hy, a2, 2.0 * a, pxx - pyy,
+                                          sDx[j] * ny + sDy[j] * nx, pxx + pyy, sq[j], ce, pc, fa0, fq0, acc);
+                        continue;
+                    }
+                }
                 disl_field<double>(kd, mx - sx0[j], my - sy0[j], sDx[j], sDy[j], wd, 1.0, acc);    // start point
                 disl_field<double>(kd, mx - sx1[j], my - sy1[j], sDx[j], sDy[j], wd, -1.0, acc);   // end point
                 const double q = sq[j];

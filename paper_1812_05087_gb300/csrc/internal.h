@@ -225,13 +225,26 @@ struct ddm_ctx {
 // begin/end a profiled stage (no-ops unless profiling is on); count launches
 // Escalated GMRES residuals (precision level >= 1) of problems up to this many
 // elements use the exact FP64 dense product (DDM_MODE_DENSE | DDM_MODE_PRECISE):
-// its cost is O(N^2) FP64 pair integrals, taken once per restart.  Larger
-// problems keep the precise FMM product.
-constexpr int64_t EXACT_RES_MAX = 10000;
+// its cost is O(N^2) FP64 pair integrals, taken once per restart (about
+// 0.1 s at 40,000 elements).  Larger problems keep the precise FMM product.
+constexpr int64_t EXACT_RES_MAX = 40000;
+// largest problem whose escalated Arnoldi products take the exact FP64
+// dense product (one per Arnoldi step instead of one per restart)
+constexpr int64_t EXACT_OP_MAX = 10000;
 inline int residual_mode(int mode, int level, int64_t n) {
     if (level < 1) return mode;
     return (n <= EXACT_RES_MAX ? DDM_MODE_DENSE : (mode & ~DDM_MODE_PRECISE)) | DDM_MODE_PRECISE;
 }
+// Arnoldi products at an escalation level: the requested ones at levels 0
+// and 1, with FP64 direct pairs at level 2, and at level 3 (problems of at
+// most EXACT_OP_MAX elements) the exact FP64 dense product, the operator
+// their residuals already use from level 1 on
+inline int arnoldi_mode(int mode, int level, int64_t n) {
+    if (level < 2) return mode;
+    if (level >= 3 && n <= EXACT_OP_MAX) return DDM_MODE_DENSE | DDM_MODE_PRECISE;
+    return mode | DDM_MODE_PRECISE;
+}
+inline int max_level(int64_t n) { return n <= EXACT_OP_MAX ? 3 : 2; }
 
 void prof_begin(ddm_ctx *ctx, int stage);
 void prof_end(ddm_ctx *ctx, int stage, int launches);

@@ -364,27 +364,31 @@ DEV void pot_kernel(const KConst<T> &k, T x, T y, T Pxx, T Pyy, T Pxy, T q, cons
 // free of the cancellation of an end-point difference (checked against a
 // 60-point Gauss rule of the point kernel to 5e-14 in FP64 from 1.3 a outward).
 // a2t2 = a^2 t^2 (complex), a2 = a^2, ta = 2a; acc += the element's field.
-DEV void elem_bigu(float zx, float zy, float a2tr, float a2ti, float a2, float ta, float Pd, float P2, float Tr,
-                   float q, float ce, float pc, float fa0, float fq0, float acc[4]) {
-    const float z2r = zx * zx - zy * zy, z2i = 2.f * zx * zy, zz = zx * zx + zy * zy;
-    const float dr = z2r - a2tr, di = z2i - a2ti;
-    const float inv = __fdividef(1.f, dr * dr + di * di);
-    const float ir = dr * inv, ii = -di * inv;                        // 1 / D
-    const float jr = ir * ir - ii * ii, ji = 2.f * ir * ii;            // 1 / D^2
-    const float kr = jr * ir - ji * ii, ki = jr * ii + ji * ir;        // 1 / D^3
-    const float i2r = ta * ir, i2i = ta * ii;
-    const float m = ta * (zz - a2);
-    const float imr = m * jr, imi = m * ji;
-    const float er = fmaf(a2tr, 1.f / 3.f, z2r), ei = fmaf(a2ti, 1.f / 3.f, z2i);
-    const float i4r = ta * (er * kr - ei * ki), i4i = ta * (er * ki + ei * kr);
-    const float A = Pd * i2r - P2 * i2i;                               // Re(Pi I2)
-    const float rv = Pd * imr - P2 * imi, iv = -(Pd * imi + P2 * imr);  // (Re, -Im)(Pi IM)
-    const float q4 = Pd * i4r - P2 * i4i, r4 = -(Pd * i4i + P2 * i4r);  // (Re, -Im)(Pi I4)
-    const float s = ce * A;
-    const float dv = ce * (Tr * i2r + rv);
-    const float sxy = ce * (Tr * i2i - iv);
-    const float fq = fq0 * q;
-    const float t0 = fa0 * q4 + fq * i2r;
+template <class T> DEV T rcp_fast(T x);
+template <> DEV float rcp_fast<float>(float x) { return __fdividef(1.f, x); }
+template <> DEV double rcp_fast<double>(double x) { return 1.0 / x; }
+template <class T>
+DEV void elem_bigu(T zx, T zy, T a2tr, T a2ti, T a2, T ta, T Pd, T P2, T Tr, T q, T ce, T pc, T fa0, T fq0,
+                   T acc[4]) {
+    const T z2r = zx * zx - zy * zy, z2i = T(2) * zx * zy, zz = zx * zx + zy * zy;
+    const T dr = z2r - a2tr, di = z2i - a2ti;
+    const T inv = rcp_fast<T>(dr * dr + di * di);
+    const T ir = dr * inv, ii = -di * inv;                             // 1 / D
+    const T jr = ir * ir - ii * ii, ji = T(2) * ir * ii;               // 1 / D^2
+    const T kr = jr * ir - ji * ii, ki = jr * ii + ji * ir;            // 1 / D^3
+    const T i2r = ta * ir, i2i = ta * ii;
+    const T m = ta * (zz - a2);
+    const T imr = m * jr, imi = m * ji;
+    const T er = a2tr * (T(1) / T(3)) + z2r, ei = a2ti * (T(1) / T(3)) + z2i;
+    const T i4r = ta * (er * kr - ei * ki), i4i = ta * (er * ki + ei * kr);
+    const T A = Pd * i2r - P2 * i2i;                                   // Re(Pi I2)
+    const T rv = Pd * imr - P2 * imi, iv = -(Pd * imi + P2 * imr);     // (Re, -Im)(Pi IM)
+    const T q4 = Pd * i4r - P2 * i4i, r4 = -(Pd * i4i + P2 * i4r);     // (Re, -Im)(Pi I4)
+    const T s = ce * A;
+    const T dv = ce * (Tr * i2r + rv);
+    const T sxy = ce * (Tr * i2i - iv);
+    const T fq = fq0 * q;
+    const T t0 = fa0 * q4 + fq * i2r;
     acc[0] += -s - dv + t0;
     acc[1] += -s + dv - t0;
     acc[2] += sxy + fa0 * r4 - fq * i2i;

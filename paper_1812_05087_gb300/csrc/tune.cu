@@ -5,7 +5,8 @@
 // timed on the device with CUDA events (after a warm-up that builds the
 // window caches) and compared with the on-the-fly dense product of the same
 // vector.  The fastest candidate whose relative error stays within the
-// bound wins.  The caller builds the bucket's trees with the winner
+// bound wins; candidates within 3 % of its time count as equally fast and
+// the more accurate of them is taken.  The caller builds the bucket's trees with the winner
 // (ddm_build_tree_params).
 #include <algorithm>
 #include <cmath>
@@ -98,7 +99,11 @@ extern "C" ddm_status ddm_autotune(ddm_ctx *ctx, const double *d_xy, int64_t n, 
                 const double sc = std::max(r, 1e-4 * top);
                 if (sc > 0) err = std::max(err, d / sc);
             }
-            if (err <= max_rel_err && ms < bms) {
+            // within the bound, the fastest; a candidate within 3 % of the
+            // best time wins if it is more accurate (timing noise must not
+            // pick a lower order whose error the sample does not exercise)
+            const bool faster = ms < 0.97 * bms, tie = ms < 1.03 * bms && err < berr;
+            if (err <= max_rel_err && (!found || faster || tie)) {
                 bms = ms;
                 berr = err;
                 bp = p;
