@@ -590,7 +590,7 @@ __device__ __forceinline__ void tc_group_body(const int2 *work, const int32_t *k
     fence_after_sync();
     const uint32_t tmem = s_tmem;
     // this CTA's share of the K chunks
-    const int nkt = (Kd + BK - 1) / BK, per = (nkt + KSPLIT - 1) / KSPLIT;
+    const int nkt = (Kd + BK - 1) / BK, per = (nkt + (int)gridDim.z - 1) / (int)gridDim.z;
     const int kbeg = blockIdx.z * per, nkb = max(0, min(nkt, kbeg + per) - kbeg);
     for (int kb = 0; kb < nkb; ++kb) {
         const int st = kb % NSTAGE;
@@ -1772,19 +1772,30 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
                                                        tc::SMEM_BYTES));
                 attr_g[ctx->device & 63] = true;
             }
-            // W' = (V^T D_in^-1) W per cell, G' = C W' per pair, F += (D_out^-1 U) G' per cell
+            // W' = (V^T D_in^-1) W per cell, G' = C W' per pair, F += (D_out^-1 U) G' per cell.
+            // The per-cell stages have few column tiles (64 cells each): their
+            // K range is split over gridDim.z blocks whose sums meet in the
+            // output atomics
             DDM_CUDA_TRY(ctx, cudaMemsetAsync(t->Wc, 0, (size_t)t->n_cells * kr * sizeof(float), fs));
             DDM_CUDA_TRY(ctx, cudaMemsetAsync(t->Gc, 0, (size_t)t->n_cells * kr * sizeof(float), fs));
             const int ld = 4 * n2;
-            k_tc_group<<<dim3((unsigned)t->n_lv_work, (unsigned)((kr + tc::BM - 1) / tc::BM)), tc::THREADS,
-                         tc::SMEM_BYTES, fs>>>(t->lv_work, t->lv_off, t->lv_pair, kr, ld, spre, t->W, t->Wc,
-                                               ctx->d_err);
+            // (a split that leaves every block at least one K chunk: the
+            // accumulator of a block without one would hold no product)
+            auto ksplit = [](int Kd, int want) {
+                const int nkt = (Kd + tc::BK - 1) / tc::BK, per = (nkt + want - 1) / want;
+                return (nkt + per - 1) / per;
+            };
+            const int kpre = ksplit(ld, std::max(1, std::min(8, (ld + tc::BK - 1) / tc::BK / 2)));
+            const int kpost = ksplit(kr, 4);
+            k_tc_group<<<dim3((unsigned)t->n_lv_work, (unsigned)((kr + tc::BM - 1) / tc::BM), (unsigned)kpre),
+                         tc::THREADS, tc::SMEM_BYTES, fs>>>(t->lv_work, t->lv_off, t->lv_pair, kr, ld, spre, t->W,
+                                                            t->Wc, ctx->d_err);
             k_tc_group<<<dim3((unsigned)t->n_work, (unsigned)((kr + tc::BM - 1) / tc::BM)), tc::THREADS,
                          tc::SMEM_BYTES, fs>>>(t->mk_work, t->mk_off, t->mk_pair, kr, kr, score, t->Wc, t->Gc,
                                                ctx->d_err);
-            k_tc_group<<<dim3((unsigned)t->n_lv_work, (unsigned)((ld + tc::BM - 1) / tc::BM)), tc::THREADS,
-                         tc::SMEM_BYTES, fs>>>(t->lv_work, t->lv_off, t->lv_pair, ld, kr, spost, t->Gc, t->Fl,
-                                               ctx->d_err);
+            k_tc_group<<<dim3((unsigned)t->n_lv_work, (unsigned)((ld + tc::BM - 1) / tc::BM), (unsigned)kpost),
+                         tc::THREADS, tc::SMEM_BYTES, fs>>>(t->lv_work, t->lv_off, t->lv_pair, ld, kr, spost, t->Gc,
+                                                            t->Fl, ctx->d_err);
         } else if (t->n_work > 0) {
             static bool attr[64] = {false};
             if (!attr[ctx->device & 63]) {
