@@ -678,7 +678,7 @@ def main():
     clocks = clk.summary()
     sm_mhz = clocks["sm_mhz"] or peaks().get("sm_max_mhz", 2070.0)
     rec, rec_ok = ncu_record()
-    kname = STAGE_KERNEL[dom]
+    kname = "k_tc_group" if dom == "m2l" and args.m2l == "compressed" else STAGE_KERNEL[dom]
     bound, peak, peak_note = "alu", alu_peak_tflops(sm_mhz), \
         f"FP32 peak 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (median SM clock sampled under load)"
     exe = None
