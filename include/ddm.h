@@ -256,13 +256,13 @@ typedef struct {
  * the residual recomputed at each restart) uses the requested mode, and
  * each restart's inner solve runs to 0.3 tol ||b||.  A restart that fails
  * to reduce the recomputed residual by 10% switches the residuals (and the
- * convergence test) to an accurate operator (problems of <= 40,000 elements:
- * DDM_MODE_DENSE | DDM_MODE_PRECISE, once per restart; larger ones: the
- * requested mode with DDM_MODE_PRECISE), inner solves then running to
- * max(0.3 tol ||b||, 1e-4 of the restart's residual); a further such
- * restart makes the Arnoldi products precise as well (the requested mode
- * with DDM_MODE_PRECISE), and one more, for problems of <= 10,000 elements,
- * makes them the exact FP64 dense product.  Returns DDM_ENOTCONV (x and
+ * convergence test) to an accurate operator (problems of <= 16,384
+ * elements: DDM_MODE_DENSE | DDM_MODE_PRECISE, once per restart; larger
+ * ones: the requested mode with DDM_MODE_PRECISE), inner solves then
+ * running to max(0.3 tol ||b||, 1e-4 of the restart's residual); a further
+ * such restart makes the Arnoldi products precise as well (the requested
+ * mode with DDM_MODE_PRECISE), and one more, for problems of <= 10,000
+ * elements, makes them the exact FP64 dense product.  Returns DDM_ENOTCONV (x and
  * info still written) when max_iters is reached or three further restarts
  * in a row fail to reduce the residual by 10%.
  * Arnoldi orthogonalisation, Givens rotations, the residual estimate and the

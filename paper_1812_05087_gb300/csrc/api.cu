@@ -620,9 +620,9 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
     // falls by less than 10%): level 0 is plain restarted GMRES with the
     // requested products (paper Sec. 4); level 1 recomputes the residuals
     // with the precise products (mixed-precision refinement, inner solves
-    // two decades at a time); level 2 also makes the Arnoldi products
-    // precise; level 3 (at most EXACT_OP_MAX elements) takes the exact FP64
-    // dense product for them; three more stalls end the solve.  Long
+    // two decades at a time; residual_mode); level 2 also makes the Arnoldi
+    // products precise; level 3 (at most EXACT_OP_MAX elements) takes the
+    // exact FP64 dense product for them; three more stalls end the solve.  Long
     // fractures, whose element contributions cancel strongly, are what reach
     // the higher levels.
     int level = 0;

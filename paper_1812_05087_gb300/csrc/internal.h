@@ -224,10 +224,11 @@ struct ddm_ctx {
 
 // begin/end a profiled stage (no-ops unless profiling is on); count launches
 // Escalated GMRES residuals (precision level >= 1) of problems up to this many
-// elements use the exact FP64 dense product (DDM_MODE_DENSE | DDM_MODE_PRECISE):
-// its cost is O(N^2) FP64 pair integrals, taken once per restart (about
-// 0.1 s at 40,000 elements).  Larger problems keep the precise FMM product.
-constexpr int64_t EXACT_RES_MAX = 40000;
+// elements use the exact FP64 dense product (DDM_MODE_DENSE | DDM_MODE_PRECISE),
+// once per restart: O(N^2) FP64 pair integrals, about 0.2 s at this size on
+// GB300 (FP64 runs at 1/64 of the FP32 rate), which bounds the cost of an
+// escalated restart.  Larger problems keep the precise FMM product.
+constexpr int64_t EXACT_RES_MAX = 16384;
 // largest problem whose escalated Arnoldi products take the exact FP64
 // dense product (one per Arnoldi step instead of one per restart)
 constexpr int64_t EXACT_OP_MAX = 10000;
