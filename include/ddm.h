@@ -282,6 +282,30 @@ ddm_status ddm_gmres_solve(ddm_ctx *ctx, const ddm_tree *tree, double dt, const 
 ddm_status ddm_sif(ddm_ctx *ctx, const ddm_tree *tree, const double *d_x, const int64_t *d_tip,
                    int n, double *d_KI, double *d_KII);
 
+/* One fracture growth step (the propagation check of paper Sec. 4's
+ * time-marching algorithm; the paper gives no criterion, this is the
+ * reading): for every tip, given by its element d_tip[i] and the end
+ * d_tip_end[i] (0: (x0, y0), 1: (x1, y1)) that is the fracture tip,
+ * K_I and K_II by Olson's formula (as ddm_sif, drained E and nu) in the
+ * crack-tip frame (x outward along the fracture, y = x turned by +90
+ * degrees), the maximum tangential stress criterion (Erdogan and Sih):
+ *   theta = 2 atan((K_I - sqrt(K_I^2 + 8 K_II^2)) / (4 K_II))  (0 if K_II = 0),
+ *   K_eq  = cos(theta/2) (K_I cos^2(theta/2) - 1.5 K_II sin(theta)),
+ * and a tip with K_I > 0 and K_eq >= K_Ic grows by one element of its tip
+ * element's length, from the tip along x rotated by theta.
+ *   d_xy, n, d_x: the current geometry (4N, caller order) and solution (3N);
+ *   d_xy_out: room for 4 (n + n_tips) doubles (not overlapping d_xy); it
+ *     receives the grown geometry, the n old elements then the new ones
+ *     (rows of stride *n_out);
+ *   d_tip, d_tip_end: updated in place (a grown tip becomes the new
+ *     element, end 1);
+ *   d_theta, d_keq (device, n_tips, may be null): kink angle and K_eq.
+ * The history of a march extends with zeros for the new elements (they did
+ * not exist before).  Errors: DDM_EINVAL, DDM_ENOMEM, DDM_ECUDA. */
+ddm_status ddm_grow(ddm_ctx *ctx, const double *d_xy, int64_t n, const double *d_x, int64_t *d_tip,
+                    int *d_tip_end, int n_tips, double K_Ic, double *d_xy_out, int64_t *n_out,
+                    double *d_theta, double *d_keq);
+
 /* Batches of independent problems (no counterpart in the paper; many
  * uneven fracture sets solved together).  A batch refers to P trees (which
  * must outlive it); vectors of a batch are the problems' 3N vectors

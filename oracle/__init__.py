@@ -301,3 +301,54 @@ def sif(material, xy, D, tip_elems, drained=True):
     f = 0.806 * E / (4.0 * (1.0 - nu * nu)) * np.sqrt(np.pi / (2.0 * a))
     D = np.asarray(D)
     return f * D[N + tip], f * D[tip]
+
+
+def kink(KI, KII):
+    """Maximum tangential stress criterion (Erdogan and Sih; the paper's
+    propagation check in the Sec. 4 algorithm names no criterion, this is
+    the reading): in the crack-tip frame the hoop stress ahead of the tip at
+    angle theta is proportional to
+        s(theta) = cos(theta/2) (K_I cos^2(theta/2) - 1.5 K_II sin(theta));
+    its maximiser theta_c solves K_I sin(theta) + K_II (3 cos(theta) - 1) = 0,
+        theta_c = 2 atan((K_I - sqrt(K_I^2 + 8 K_II^2)) / (4 K_II))  (0 if K_II = 0),
+    and K_eq = s(theta_c).  Returns (theta_c, K_eq) arrays."""
+    KI = np.asarray(KI, dtype=np.float64)
+    KII = np.asarray(KII, dtype=np.float64)
+    safe = np.where(KII != 0.0, KII, 1.0)
+    th = np.where(KII != 0.0, 2.0 * np.arctan((KI - np.sqrt(KI * KI + 8.0 * KII * KII)) / (4.0 * safe)), 0.0)
+    c = np.cos(0.5 * th)
+    return th, c * (KI * c * c - 1.5 * KII * np.sin(th))
+
+
+def grow(material, xy, D, tips, ends, K_Ic):
+    """One growth step (reading of the paper's propagation check, Sec. 4):
+    for every tip (element tips[i], its end ends[i] = 0 for (x0, y0), 1 for
+    (x1, y1)), K_I and K_II by Olson's formula (sif, drained), taken in the
+    crack-tip frame x = outward tangent, y = x turned by +90 degrees (the
+    element frame's signs at either end, as the opening keeps its sign),
+    theta and K_eq by kink(); a tip with K_I > 0 and K_eq >= K_Ic grows by an
+    element as long as its tip element, from the tip along x turned by
+    theta.  Returns (grown xy 4 x (N + grown), tips, ends, theta, K_eq):
+    the old elements first, the new ones in tip order, a grown tip moved to
+    its new element's end 1."""
+    xy = _xy(xy)
+    N = xy.shape[1]
+    tips = np.asarray(tips, dtype=np.int64).copy()
+    ends = np.asarray(ends, dtype=np.int64).copy()
+    KI, KII = sif(material, xy, D, tips)
+    th, keq = kink(KI, KII)
+    new = []
+    for i, e in enumerate(tips):
+        a, b = xy[:2, e], xy[2:, e]
+        L = np.hypot(*(b - a))
+        x_dir = (b - a) / L if ends[i] == 1 else (a - b) / L
+        y_dir = np.array([-x_dir[1], x_dir[0]])
+        p = b if ends[i] == 1 else a
+        if KI[i] > 0.0 and keq[i] >= K_Ic:
+            d = np.cos(th[i]) * x_dir + np.sin(th[i]) * y_dir
+            new.append(np.concatenate([p, p + L * d]))
+            tips[i] = N + len(new) - 1
+            ends[i] = 1
+    if new:
+        xy = np.concatenate([xy, np.array(new).T], axis=1)
+    return xy, tips, ends, th, keq

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libddm_gb300.so")
 SOURCES = ["api.cu", "tree.cu", "fmm.cu", "batch.cu", "serve.cu", "precond.cu", "krylov.cu", "tune.cu", "svd.cu",
-           "history.cu"]
+           "history.cu", "propagate.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -31,7 +31,7 @@ EXPORTS = ("ddm_create", "ddm_destroy", "ddm_last_error", "ddm_device_check", "d
            "ddm_batch_gmres_solve", "ddm_server_create", "ddm_submit", "ddm_poll", "ddm_server_destroy",
            "ddm_matvec_dense_static", "ddm_set_wait_limit", "ddm_build_tree_params", "ddm_autotune",
            "ddm_set_m2l_compression", "ddm_set_history_compression", "ddm_server_cancel",
-           "ddm_server_get_stats")
+           "ddm_server_get_stats", "ddm_grow")
 STATIC_MAX_ELEMENTS = 65536
 NSTAGES = 10
 STAGES = ("prep", "self_blocks", "up", "m2l_ops", "m2l", "down", "leaf", "dense", "krylov", "tree")
@@ -135,6 +135,8 @@ def load(build_if_missing: bool = True):
         L.ddm_server_destroy.argtypes = [_VP]
         L.ddm_server_destroy.restype = None
         L.ddm_server_cancel.argtypes = [_VP]
+        L.ddm_grow.argtypes = [_VP, _VP, ctypes.c_int64, _VP, _VP, _VP, ctypes.c_int, ctypes.c_double, _VP,
+                               ctypes.POINTER(ctypes.c_int64), _VP, _VP]
         L.ddm_server_get_stats.argtypes = [_VP, ctypes.POINTER(ddm_server_stats)]
         L.ddm_batch_create.argtypes = [_VP, ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP)]
         L.ddm_batch_destroy.argtypes = [_VP]
@@ -300,6 +302,23 @@ def ddm_set_history_compression(ctx, exact_steps=0, nodes=10, ratio=2.0):
     off), older steps interpolated in log time at `nodes` points per block."""
     _check(ctx, load().ddm_set_history_compression(ctx, int(exact_steps), int(nodes), float(ratio)),
            "ddm_set_history_compression")
+
+
+def ddm_grow(ctx, xy: torch.Tensor, x: torch.Tensor, tips: torch.Tensor, ends: torch.Tensor, K_Ic):
+    """One growth step: returns (grown geometry 4 x n_out, theta, K_eq);
+    tips (int64) and ends (int32) are updated in place."""
+    n = xy.numel() // 4
+    m = tips.numel()
+    assert tips.dtype == torch.int64 and ends.dtype == torch.int32 and tips.is_contiguous() and ends.is_contiguous()
+    out = torch.empty(4 * (n + m), dtype=torch.float64, device="cuda")
+    theta = torch.empty(max(m, 1), dtype=torch.float64, device="cuda")
+    keq = torch.empty_like(theta)
+    n_out = ctypes.c_int64(0)
+    _check(ctx, load().ddm_grow(ctx, _VP(_dev(xy, 4 * n, "xy")), n, _VP(_dev(x, 3 * n, "x")), _VP(tips.data_ptr()),
+                                _VP(ends.data_ptr()), m, float(K_Ic), _VP(out.data_ptr()), ctypes.byref(n_out),
+                                _VP(theta.data_ptr()), _VP(keq.data_ptr())), "ddm_grow")
+    n2 = n_out.value
+    return out[:4 * n2].view(4, n2), theta[:m], keq[:m]
 
 
 def ddm_profile_read(ctx) -> dict:
@@ -516,6 +535,10 @@ class Context:
         info = ddm_gmres_solve(self.ptr, tree.ptr, dt, rhs, x, _SYSTEMS[system], restart, max_iters, tol,
                                _MODES[mode], raise_on_notconv)
         return x, info
+
+    def grow(self, xy, x, tips, ends, K_Ic):
+        """One fracture growth step (ddm_grow)."""
+        return ddm_grow(self.ptr, xy, x, tips, ends, K_Ic)
 
     def sif(self, tree: Tree, x, tips):
         tips = torch.as_tensor(tips, dtype=torch.int64, device="cuda").contiguous()

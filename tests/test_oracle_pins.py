@@ -420,3 +420,63 @@ def test_rate_march_satisfies_rows_with_history():
     scale = np.abs(b[:2 * N]).max()
     assert np.abs(y[:N] - b[:N]).max() < 1e-9 * scale
     assert np.abs(row_n - b[N:2 * N]).max() < 1e-9 * scale
+
+
+# ---------------------------------------------------------------------------
+# growth step (reading of the propagation check): maximum tangential stress
+# ---------------------------------------------------------------------------
+def test_kink_special_cases():
+    th, keq = oracle.kink([2.0, 0.0, 0.0], [0.0, 1.0, -1.0])
+    assert th[0] == 0.0 and keq[0] == 2.0                                  # pure mode I: straight, K_eq = K_I
+    assert abs(th[1] - (-2.0 * math.atan(1.0 / math.sqrt(2.0)))) < 1e-14   # pure mode II: -70.53 degrees
+    assert abs(th[1] - math.radians(-70.528779)) < 1e-7
+    assert abs(keq[1] - 2.0 / math.sqrt(3.0)) < 1e-13                      # K_eq = (2 / sqrt 3) K_II
+    assert abs(th[2] + th[1]) < 1e-14 and abs(keq[2] - keq[1]) < 1e-13     # K_II -> -K_II mirrors the kink
+
+
+def test_kink_maximises_the_hoop_stress():
+    """theta_c is the maximiser over (-pi, pi) of the hoop-stress factor
+    cos(t/2)(K_I cos^2(t/2) - 1.5 K_II sin t), found by brute force."""
+    rng = np.random.default_rng(5)
+    t = np.linspace(-math.pi + 1e-6, math.pi - 1e-6, 400001)
+    for KI, KII in zip(rng.uniform(0.0, 2.0, 20), rng.uniform(-2.0, 2.0, 20)):
+        s = np.cos(t / 2) * (KI * np.cos(t / 2) ** 2 - 1.5 * KII * np.sin(t))
+        th, keq = oracle.kink(KI, KII)
+        assert abs(t[np.argmax(s)] - th) < 1e-4
+        assert abs(s.max() - keq) < 1e-8 * max(1.0, abs(keq))
+
+
+def test_grow_straight_mode_one():
+    """A straight crack along x with pure opening at its tips grows straight
+    on at both ends by one element of the tip element's length."""
+    xy, _ = crack(10, 1.0)
+    N = xy.shape[1]
+    D = np.zeros(3 * N)
+    D[N:2 * N] = 1e-3                                          # opening only
+    tips, ends = np.array([0, N - 1]), np.array([0, 1])
+    g, t2, e2, th, keq = oracle.grow(MAT, xy, D, tips, ends, 0.0)
+    assert g.shape[1] == N + 2 and list(t2) == [N, N + 1] and list(e2) == [1, 1]
+    L = xy[2, 0] - xy[0, 0]
+    assert np.allclose(g[:, N], [xy[0, 0], 0.0, xy[0, 0] - L, 0.0], atol=1e-15)
+    assert np.allclose(g[:, N + 1], [xy[2, N - 1], 0.0, xy[2, N - 1] + L, 0.0], atol=1e-15)
+    # a toughness above K_eq stops the growth
+    g, t2, _, _, _ = oracle.grow(MAT, xy, D, tips, ends, 1.01 * keq.max())
+    assert g.shape[1] == N and list(t2) == [0, N - 1]
+
+
+def test_grow_turns_toward_the_largest_compression():
+    """A pressurised crack at 45 degrees under sigma_H (x) > sigma_h (y),
+    drained: the opening works against the smaller compression, so the
+    kinks at both tips turn the fracture toward the x axis (the sign of K_II
+    in the tip frame and the direction of the kink, checked by physics)."""
+    xy, _ = crack(40, 1.0, angle=math.pi / 4)
+    N = xy.shape[1]
+    loads = dict(sigma_H=20e6, sigma_h=10e6, p_f=25e6, p0=0.0)
+    D = oracle.solve(oracle.assemble(MAT, xy, 1e12), oracle.rhs(xy, system="impermeable", **loads), N,
+                     "impermeable")
+    g, _, _, th, keq = oracle.grow(MAT, xy, D, [0, N - 1], [0, 1], 0.0)
+    assert g.shape[1] == N + 2
+    for j in (N, N + 1):
+        d = g[2:, j] - g[:2, j]
+        assert abs(d[1]) / abs(d[0]) < 0.9              # closer to the x axis than 45 degrees
+    assert th[0] * th[1] > 0 and abs(abs(th[0]) - abs(th[1])) < 1e-6   # point-symmetric kinks
