@@ -102,3 +102,42 @@ def test_no_growth_cases():
     g, _, _ = ctx.grow(dev(xy), x, torch.empty(0, dtype=torch.int64, device="cuda"),
                        torch.empty(0, dtype=torch.int32, device="cuda"), 0.0)
     assert g.shape[1] == N and np.array_equal(g.cpu().numpy(), xy)
+
+
+def test_growth_inside_time_marching():
+    """Growth inside the time march of paper Sec. 4: after each 10 s step
+    the tips grow (K_Ic = 0) and the next step's history covers the grown
+    geometry, the new elements with zero past displacement discontinuity
+    (they did not exist).  Every step's GPU solution against the oracle's
+    direct solve of that step: A(dt) on the current geometry, the right-hand
+    side minus the oracle's history sum of the zero-padded past solutions."""
+    ctx = Context(inputs.MATERIAL, n_cheb=8, leaf_size=8)
+    xy = inclined(N=24)
+    dt = 10.0
+    tips = torch.tensor([0, xy.shape[1] - 1], dtype=torch.int64, device="cuda")
+    ends = torch.tensor([0, 1], dtype=torch.int32, device="cuda")
+    past = []                                            # host solutions, each at its own N
+    for h in range(1, 5):
+        N = xy.shape[1]
+        hist = np.zeros((len(past), 3 * N))
+        for k, D in enumerate(past):                     # pad every block of 3 with zeros for new elements
+            n0 = D.size // 3
+            for b in range(3):
+                hist[k, b * N:b * N + n0] = D[b * n0:(b + 1) * n0]
+        times = [dt * k for k in range(h + 1)]
+        tree = ctx.build_tree(dev(xy))
+        rhs = ctx.rhs(tree, system="pressure", **LOADS)
+        if past:
+            ctx.history_apply(tree, dev(hist), times, rhs)
+        x, info = ctx.gmres_solve(tree, dt, rhs, system="pressure", tol=1e-8, mode="fmm")
+        assert info["converged"], h
+        b = oracle.rhs(xy, system="pressure", **LOADS)
+        if past:
+            b = b - oracle.history(MAT, xy, hist, times)
+        ref = oracle.solve(oracle.assemble(MAT, xy, dt), b, N)
+        assert block_rel_err(x.cpu().numpy(), ref, N) < 1e-3, h
+        past.append(x.cpu().numpy())
+        g, _, _ = ctx.grow(dev(xy), x, tips, ends, 0.0)
+        xy = np.ascontiguousarray(g.cpu().numpy())
+        assert xy.shape[1] == N + 2
+    ctx.device_check()
