@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-nmax", type=int, default=200000)
     ap.add_argument("--serve-max-steps", type=int, default=100)
+    ap.add_argument("--serve-dense-seconds", type=float, default=30.0,
+                    help="window of the dense-DDM arm on the same request stream")
     ap.add_argument("--serve-rate", type=float, default=50.0)
     return ap.parse_args()
 
@@ -537,6 +539,11 @@ def main():
         tr.close()
         return inf
 
+    # a solve builds its own tree and window: the automatic compression
+    # policy (compress a window once it has served 128 products) leaves a
+    # single ~35-product solve on the full operators, which is cheaper than
+    # a compression set-up per solve
+    ctx.set_m2l_compression(2)
     lat, infos = [], []
     for i in range(args.solves + 2):
         torch.cuda.synchronize()
@@ -626,49 +633,81 @@ def main():
     serve_res = None
     if args.serve_seconds > 0:
         from paper_1812_05087_gb300.ddm import Server
-        trace = inputs.serving_trace(duration=args.serve_seconds, rate=args.serve_rate, nmin=1000,
-                                     nmax=args.serve_nmax)
-        ctx.set_history_compression(8, 8, 2.0)        # the server's context takes it over
-        srv = Server(ctx, budget_bytes=160 << 30, max_active=32, tol=1e-5)
-        ctx.set_history_compression(0)
-        tickets, keep, steps_req, sizes_req = [], [], [], []
-        t0 = time.perf_counter()
-        for rq in trace:
-            g = torch.as_tensor(inputs.serving_geometry(rq["N"], rq["seed"]), device="cuda")
-            o = torch.zeros(3 * (g.numel() // 4), dtype=torch.float64, device="cuda")
-            st_ = 1 + (rq["steps"] - 1) % args.serve_max_steps
-            while time.perf_counter() - t0 < rq["t"]:
-                time.sleep(0.0005)
-            tickets.append(srv.submit(g, o, DT, st_, **LOADS))
-            keep.append((g, o))
-            steps_req.append(st_)
-            sizes_req.append(g.numel() // 4)
-        while time.perf_counter() - t0 < args.serve_seconds:
-            time.sleep(0.01)
-        t_win = time.perf_counter() - t0
-        snap = [srv.poll(tk) for tk in tickets]
-        sstats = srv.stats()
-        srv.cancel()
-        t1 = time.perf_counter()
-        while any(srv.poll(tk)["poll"] == 6 for tk in tickets) and time.perf_counter() - t1 < 300:
-            time.sleep(0.01)
-        srv.close()
-        done = [r for r in snap if r["poll"] == 0]
-        lats = sorted(r["latency_ms"] for r in done)
-        solves = int(sum(r["steps_done"] for r in snap))
-        elem_steps = float(sum(r["steps_done"] * n for r, n in zip(snap, sizes_req)))
-        serve_res = {"requests_arrived": len(tickets), "completed_in_window": len(done),
-                     "offered_time_step_solves": int(sum(steps_req)),
-                     "offered_solves_per_s": sum(steps_req) / args.serve_seconds,
-                     "time_step_solves_in_window": solves, "window_s": t_win,
-                     "solves_per_s": solves / t_win, "element_steps_per_s": elem_steps / t_win,
-                     "p50_ms": lats[len(lats) // 2] if lats else None,
-                     "p99_ms": lats[min(len(lats) - 1, int(0.99 * len(lats)))] if lats else None,
-                     "history": "time-compressed (8 exact steps, 8 nodes, ratio 2)",
-                     "server_time_ms": sstats,
-                     "trace": f"Poisson {args.serve_rate}/s for {args.serve_seconds} s, N log-uniform "
-                              f"[1e3, {args.serve_nmax:g}], 1-{args.serve_max_steps} steps; saturated: the "
-                              f"unfinished requests are cancelled at the end of the window"}
+
+        def serve(mode, seconds):
+            """Replay the trace's first `seconds` of arrivals against a server
+            in the given product mode; unfinished requests are cancelled at
+            the end of the window."""
+            trace = inputs.serving_trace(duration=seconds, rate=args.serve_rate, nmin=1000, nmax=args.serve_nmax)
+            ctx.set_history_compression(8, 8, 2.0)       # the server's context takes it over
+            srv = Server(ctx, budget_bytes=160 << 30, max_active=32, tol=1e-5)
+            ctx.set_history_compression(0)
+            srv.set_mode(mode)
+            tickets, keep, steps_req, sizes_req = [], [], [], []
+            t0 = time.perf_counter()
+            for rq in trace:
+                g = torch.as_tensor(inputs.serving_geometry(rq["N"], rq["seed"]), device="cuda")
+                o = torch.zeros(3 * (g.numel() // 4), dtype=torch.float64, device="cuda")
+                st_ = 1 + (rq["steps"] - 1) % args.serve_max_steps
+                while time.perf_counter() - t0 < rq["t"]:
+                    time.sleep(0.0005)
+                tickets.append(srv.submit(g, o, DT, st_, **LOADS))
+                keep.append((g, o))
+                steps_req.append(st_)
+                sizes_req.append(g.numel() // 4)
+            while time.perf_counter() - t0 < seconds:
+                time.sleep(0.01)
+            t_win = time.perf_counter() - t0
+            snap = [srv.poll(tk) for tk in tickets]
+            sstats = srv.stats()
+            srv.cancel()
+            t1 = time.perf_counter()
+            while any(srv.poll(tk)["poll"] == 6 for tk in tickets) and time.perf_counter() - t1 < 300:
+                time.sleep(0.01)
+            srv.close()
+            done = [k for k, r in enumerate(snap) if r["poll"] == 0]
+            lats = sorted(snap[k]["latency_ms"] for k in done)
+            solves = int(sum(r["steps_done"] for r in snap))
+            elem_steps = float(sum(r["steps_done"] * n for r, n in zip(snap, sizes_req)))
+            res = {"mode": mode, "requests_arrived": len(tickets), "completed_in_window": len(done),
+                   "offered_time_step_solves": int(sum(steps_req)),
+                   "offered_solves_per_s": sum(steps_req) / seconds,
+                   "time_step_solves_in_window": solves, "window_s": t_win,
+                   "solves_per_s": solves / t_win, "element_steps_per_s": elem_steps / t_win,
+                   "p50_ms": lats[len(lats) // 2] if lats else None,
+                   "p99_ms": lats[min(len(lats) - 1, int(0.99 * len(lats)))] if lats else None,
+                   "server_time_ms": sstats}
+            return res, done, keep, steps_req, sizes_req
+
+        serve_res, done, keep, steps_req, sizes_req = serve("fmm", args.serve_seconds)
+        serve_res["history"] = "time-compressed (8 exact steps, 8 nodes, ratio 2)"
+        serve_res["trace"] = (f"Poisson {args.serve_rate}/s for {args.serve_seconds} s, N log-uniform [1e3, "
+                              f"{args.serve_nmax:g}], 1-{args.serve_max_steps} steps; saturated: the unfinished "
+                              f"requests are cancelled at the end of the window")
+        # served results against the exact operator: completed one-step
+        # requests of <= 20,000 elements, the oracle's rows of A(dt) at 6
+        # sampled elements (3 rows each) against the right-hand side
+        if not args.no_oracle:
+            import oracle
+            mat = inputs.material_tuple()
+            chk = [k for k in done if steps_req[k] == 1 and sizes_req[k] <= 20000][:3]
+            errs = []
+            rng_o = np.random.default_rng(17)
+            for k in chk:
+                g, o = keep[k]
+                xy_k = g.cpu().numpy().reshape(4, -1)
+                n_k = xy_k.shape[1]
+                el = rng_o.choice(n_k, 6, replace=False)
+                rows = np.concatenate([el + c * n_k for c in range(3)])
+                Ar = oracle.assemble_rows(mat, xy_k, DT, rows)
+                b = oracle.rhs(xy_k, system="pressure", **LOADS)[rows]
+                errs.append(float(np.abs(Ar @ o.cpu().numpy() - b).max() / np.abs(b).max()))
+            serve_res["oracle_residual"] = {"requests": len(chk), "max_rel_residual": max(errs) if errs else None,
+                                            "note": "completed one-step requests of <= 20,000 elements: |A(dt) x - b| "
+                                                    "on 18 oracle rows, relative to max |b| (GMRES tolerance 1e-5)"}
+        # the conventional dense DDM on the same request stream (a shorter window)
+        dres, _, _, _, _ = serve("dense", args.serve_dense_seconds)
+        serve_res["dense_arm"] = dres
 
     # ---------------- roofline of the dominant kernel
     st = {k: v for k, v in stages.items() if v[1] > 0 and k in ("leaf", "m2l")}

@@ -383,6 +383,11 @@ typedef struct {
     double ms_other;
 } ddm_server_stats;
 ddm_status ddm_server_get_stats(ddm_server *server, ddm_server_stats *stats);
+
+/* Product mode of the server's later rounds (history sums and GMRES):
+ * DDM_MODE_FMM (default) or DDM_MODE_DENSE (the conventional DDM, for a
+ * comparison on the same request stream).  Errors: DDM_EINVAL. */
+ddm_status ddm_server_set_mode(ddm_server *server, int mode);
 void ddm_server_destroy(ddm_server *server);
 
 /* Dense influence product that allocates nothing (no counterpart in the

@@ -10,6 +10,7 @@
 // requests that arrive while others run are admitted as slots and memory
 // free up.  ddm_poll reports completion.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -53,6 +54,7 @@ struct ddm_server {
     size_t budget = 0, used = 0;
     int max_active = 0;
     double tol = 1e-5;
+    std::atomic<int> mode{DDM_MODE_FMM};   // product mode of the rounds (ddm_server_set_mode)
     std::mutex mu;
     std::condition_variable cv;
     std::deque<Req *> queue;
@@ -165,7 +167,7 @@ void serve_loop(ddm_server *S) {
                 if (!st && q->step > 0) {
                     std::vector<double> times(q->step + 2);
                     for (int k = 0; k <= q->step + 1; ++k) times[k] = k * dt;
-                    st = ddm_history_apply(S->ctx, q->tree, q->hist, times.data(), q->step, q->rhs, DDM_MODE_FMM);
+                    st = ddm_history_apply(S->ctx, q->tree, q->hist, times.data(), q->step, q->rhs, S->mode.load());
                 }
                 if (!st) cudaMemcpyAsync(rhs + o, q->rhs, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
                 // initial guess: previous step (Dq of the 2N systems: 0)
@@ -187,7 +189,7 @@ void serve_loop(ddm_server *S) {
             auto t2 = Clock::now();
             t_setup += ms_since(t1, t2);
             if (!st) {
-                ddm_gmres_params prm{sys, 50, 2000, S->tol, DDM_MODE_FMM};
+                ddm_gmres_params prm{sys, 50, 2000, S->tol, S->mode.load()};
                 st = ddm_batch_gmres_solve(S->ctx, B, dt, rhs, x, &prm, infos.data());
                 if (st == DDM_ENOTCONV) st = DDM_OK;      // per-request status below
             }
@@ -301,6 +303,12 @@ ddm_status ddm_poll(ddm_server *S, uint64_t ticket, ddm_result *res) {
     res->latency_ms = done ? ms_since(q->t_submit, q->t_done) : -1.0;
     if (!done) return DDM_PENDING;
     return q->status;
+}
+
+ddm_status ddm_server_set_mode(ddm_server *S, int mode) {
+    if (!S || (mode != DDM_MODE_FMM && mode != DDM_MODE_DENSE)) return DDM_EINVAL;
+    S->mode.store(mode);
+    return DDM_OK;
 }
 
 ddm_status ddm_server_get_stats(ddm_server *S, ddm_server_stats *out) {

@@ -31,7 +31,7 @@ EXPORTS = ("ddm_create", "ddm_destroy", "ddm_last_error", "ddm_device_check", "d
            "ddm_batch_gmres_solve", "ddm_server_create", "ddm_submit", "ddm_poll", "ddm_server_destroy",
            "ddm_matvec_dense_static", "ddm_set_wait_limit", "ddm_build_tree_params", "ddm_autotune",
            "ddm_set_m2l_compression", "ddm_set_history_compression", "ddm_server_cancel",
-           "ddm_server_get_stats", "ddm_grow")
+           "ddm_server_get_stats", "ddm_grow", "ddm_server_set_mode")
 STATIC_MAX_ELEMENTS = 65536
 NSTAGES = 10
 STAGES = ("prep", "self_blocks", "up", "m2l_ops", "m2l", "down", "leaf", "dense", "krylov", "tree")
@@ -135,6 +135,7 @@ def load(build_if_missing: bool = True):
         L.ddm_server_destroy.argtypes = [_VP]
         L.ddm_server_destroy.restype = None
         L.ddm_server_cancel.argtypes = [_VP]
+        L.ddm_server_set_mode.argtypes = [_VP, ctypes.c_int]
         L.ddm_grow.argtypes = [_VP, _VP, ctypes.c_int64, _VP, _VP, _VP, ctypes.c_int, ctypes.c_double, _VP,
                                ctypes.POINTER(ctypes.c_int64), _VP, _VP]
         L.ddm_server_get_stats.argtypes = [_VP, ctypes.POINTER(ddm_server_stats)]
@@ -424,6 +425,12 @@ class Server:
         if st:
             raise DDMError(st, "ddm_server_get_stats failed")
         return {k: getattr(s, k) for k, _ in ddm_server_stats._fields_}
+
+    def set_mode(self, mode="fmm"):
+        """Product mode of later rounds: "fmm" or "dense"."""
+        st = load().ddm_server_set_mode(self.ptr, _MODES[mode])
+        if st:
+            raise DDMError(st, "ddm_server_set_mode: fmm or dense")
 
     def cancel(self):
         """Cancel every unfinished request (status DDM_ECANCELED)."""
