@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--orders", default="12,16", help="extra Chebyshev orders timed beside --n-cheb ('' = none)")
     ap.add_argument("--m2l", default="compressed", choices=["compressed", "full"],
                     help="M2L operators of the headline product and solves")
+    ap.add_argument("--adaptive", type=int, default=1, help="time the adaptive and the uniform tree on the "
+                    "clustered set (0 = skip)")
     ap.add_argument("--well-steps", type=int, default=100, help="time steps of the horizontal-well march (0 = skip)")
     ap.add_argument("--well-tol", type=float, default=3e-4, help="GMRES tolerance of the horizontal-well march "
                     "(its FP32 floor: 1.5e-5 at the first step, ~1.4e-4 from step ~40)")
@@ -524,6 +526,58 @@ def main():
         otree.close()
         octx.close()
 
+    # ---------------- adaptive tree (the quadtree of paper Sec. 3.1 as stated:
+    # cells of more than leaf_size elements split, leaves at any level)
+    # against the uniform tree on a strongly clustered set; products and
+    # solves on both, errors against the GPU dense product (and, on rank 0,
+    # the oracle's sampled rows)
+    adaptive_res = None
+    if args.adaptive:
+        cxy, _ = inputs.clustered_fractures(seed=inputs.SEED + 6 + 100 * rank)
+        cN = cxy.shape[1]
+        d_cxy = torch.as_tensor(cxy, device="cuda")
+        cx_h = inputs.unknowns(cN, seed=98)
+        cx = torch.as_tensor(cx_h, device="cuda")
+        cy = torch.empty_like(cx)
+        actx = Context(inputs.MATERIAL, n_cheb=args.n_cheb, leaf_size=args.leaf)
+        actx.set_m2l_compression(1 if args.m2l == "compressed" else 0)
+        dtree = actx.build_tree(d_cxy)
+        actx.matvec(dtree, cx, 0.0, DT, mode="dense", out=cy)
+        cy_dense = cy.cpu().numpy()
+        dtree.close()
+        adaptive_res = {"workload": "clustered fractures: 4 swarms x 100 cracks of 0.4-1.5 m x 20 elements in "
+                                    "12 m squares + 20 cracks of 10-40 m x 100 elements over 400 m (N=10000)",
+                        "N": cN, "xy": cxy, "x": cx_h}
+        for kind, ad in (("uniform", False), ("adaptive", True)):
+            tr = actx.build_tree(d_cxy, adaptive=ad)
+            ti = tr.info()
+            afn = lambda: actx.matvec(tr, cx, 0.0, DT, mode="fmm", out=cy)
+            ams = float(np.mean(timed(afn, args.steps, args.warmup)))
+            yk = cy.cpu().numpy()
+            e = max(np.abs(yk[b * cN:(b + 1) * cN] - cy_dense[b * cN:(b + 1) * cN]).max() /
+                    np.abs(cy_dense[b * cN:(b + 1) * cN]).max() for b in range(3))
+            b_ = actx.rhs(tr, system="pressure", **LOADS)
+            sts, sinf = [], None
+            for i in range(4):                    # the first builds the tree's window caches
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                _, sinf = actx.gmres_solve(tr, DT, b_, system="pressure", tol=1e-5, mode="fmm",
+                                           raise_on_notconv=False)
+                torch.cuda.synchronize()
+                if i:
+                    sts.append((time.perf_counter() - t0) * 1e3)
+            adaptive_res[kind] = {"depth": ti["depth"], "leaf_level_min": ti["leaf_level_min"],
+                                  "cells": ti["n_cells"], "leaves": ti["n_leaves"], "m2l_pairs": ti["n_m2l_pairs"],
+                                  "p2p_pairs": ti["n_p2p_pairs"], "max_leaf_records": ti["max_leaf_records"],
+                                  "ms_per_matvec": ams, "melem_s": cN / (ams * 1e-3) / 1e6,
+                                  "rel_err_vs_gpu_dense": e, "solve_ms": sorted(sts)[len(sts) // 2],
+                                  "gmres_iterations": sinf["iterations"], "converged": bool(sinf["converged"]),
+                                  "y": yk}
+            tr.close()
+        adaptive_res["product_speedup_adaptive_vs_uniform"] = (adaptive_res["uniform"]["ms_per_matvec"] /
+                                                              adaptive_res["adaptive"]["ms_per_matvec"])
+        actx.close()
+
     # ---------------- dense product on the GPU (conventional PDDM)
     dense = lambda: ctx.matvec(tree, x, 0.0, DT, mode="dense", out=y)
     t_dense = timed(dense, max(2, args.steps // 5), 2)
@@ -764,6 +818,14 @@ def main():
                 if "y" in rec:
                     e_o = np.abs(rec["y"][rows] - ref)
                     rec["error_vs_oracle"] = max(e_o[b * k:(b + 1) * k].max() / scale[b] for b in range(3))
+        if adaptive_res is not None:                 # the clustered set's sampled rows
+            ca = adaptive_res
+            celems = rng.choice(ca["N"], k, replace=False)
+            cref, crows, _ = oracle_sample(ca["xy"], ca["x"], celems)
+            cscale = [np.abs(cref[b * k:(b + 1) * k]).max() for b in range(3)]
+            for kind in ("uniform", "adaptive"):
+                e_c = np.abs(ca[kind]["y"][crows] - cref)
+                ca[kind]["error_vs_oracle"] = max(e_c[b * k:(b + 1) * k].max() / cscale[b] for b in range(3))
         import oracle
         cpu = {"value": k / dt_or / 1e6, "unit": "Melem/s", "cores": oracle.num_threads(), "kind": "oracle",
                "sample": f"{k} target elements (3 rows each) x {N} sources, FP64 adaptive element quadrature"}
@@ -793,6 +855,8 @@ def main():
         "window_setup": window_setup,
         "orders": {str(nn): {k: ({kk: vv for kk, vv in v.items() if kk != "y"} if isinstance(v, dict) else v)
                              for k, v in o.items() if k != "y"} for nn, o in orders.items()},
+        "adaptive_tree": ({k: ({kk: vv for kk, vv in v.items() if kk != "y"} if isinstance(v, dict) else v)
+                           for k, v in adaptive_res.items() if k not in ("xy", "x")} if adaptive_res else None),
         "well": well_res,
         "batched": batch_res, "serving": serve_res,
         "error": err,

@@ -72,15 +72,25 @@ typedef struct {
 /* FMM controls (paper Sec. 3): n_cheb = Chebyshev nodes per dimension
  * (n^2 per cell; even, 2..16), leaf_size = the "prescribed number" of elements above
  * which a cell is split, max_depth fixes the quadtree depth cap (0 =
- * automatic: the deepest depth allowed by leaf_size, then the depth that
- * minimises a cost model of the product measured on GB300).
- * quad_near = Gauss points per element for the fluid-source near field
- * (0 = 6). */
+ * automatic: the deepest depth allowed by leaf_size, then, for a uniform
+ * tree, the depth that minimises a cost model of the product measured on
+ * GB300).  quad_near = Gauss points per element for the fluid-source near
+ * field (0 = 6).
+ * adaptive = 0: a uniform tree, every leaf at one depth (empty cells
+ * dropped).  adaptive = 1: the quadtree of paper Sec. 3.1 as stated, every
+ * cell holding more than leaf_size elements split into four, recursively,
+ * so leaves sit at different levels (a cell whose elements are longer than a
+ * quarter of its children's width is not split).  Two leaves then interact
+ * directly when their ancestors at the coarser leaf's level share a vertex
+ * (or coincide); every other pair goes through the M2L of the first level at
+ * which their ancestors are apart, as in the uniform tree.  The same calls
+ * and kernels serve both. */
 typedef struct {
     int n_cheb;
     int leaf_size;
     int max_depth;
     int quad_near;
+    int adaptive;
 } ddm_fmm_params;
 
 typedef struct ddm_ctx ddm_ctx;
@@ -142,7 +152,8 @@ ddm_status ddm_set_m2l_compression(ddm_ctx *ctx, int mode, int rank);
  * non-finite end point. */
 ddm_status ddm_build_tree(ddm_ctx *ctx, const double *d_xy, int64_t n, ddm_tree **out);
 /* The same with the tree's own FMM parameters (Chebyshev order, leaf size,
- * depth cap, near-field rule; fields <= 0 take the context's): every
+ * depth cap, near-field rule, tree kind; n_cheb, leaf_size and quad_near
+ * <= 0 take the context's, max_depth and adaptive are taken as given): every
  * product, history sum and solve on this tree uses them.  Lets one context
  * serve problems of different sizes at the order and leaf size that suit
  * each (see ddm_autotune).  DDM_EINVAL for an odd or out-of-range order. */
@@ -152,12 +163,16 @@ void ddm_tree_destroy(ddm_tree *tree);
 
 typedef struct {
     int64_t n_elements;
-    int depth;             /* leaf level L */
+    int depth;             /* deepest level (the leaf level of a uniform tree) */
     int64_t n_cells;       /* non-empty cells, all levels */
     int64_t n_leaves;
     int64_t n_m2l_pairs;   /* interaction-list entries, all levels */
     int64_t n_p2p_pairs;   /* (target element, source element) near pairs */
     double root_half_width;
+    int leaf_level_min;    /* coarsest leaf level (= depth for a uniform tree) */
+    int adaptive;
+    int max_leaf_records;  /* most direct-interaction element ranges of one leaf
+                              (<= 9 in a uniform tree) */
 } ddm_tree_info;
 ddm_status ddm_tree_get_info(const ddm_tree *tree, ddm_tree_info *info);
 

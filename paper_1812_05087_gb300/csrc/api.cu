@@ -290,11 +290,12 @@ ddm_status ddm_create(ddm_ctx **out, const ddm_material *mat, const ddm_fmm_para
     if (!out) return DDM_EINVAL;
     *out = nullptr;
     if (valid_material(mat) != DDM_OK) return DDM_EINVAL;
-    ddm_fmm_params p = prm ? *prm : ddm_fmm_params{8, 32, 0, 6};
+    ddm_fmm_params p = prm ? *prm : ddm_fmm_params{8, 32, 0, 6, 0};
     if (p.n_cheb <= 0) p.n_cheb = 8;
     if (p.leaf_size <= 0) p.leaf_size = 32;
     if (p.quad_near <= 0) p.quad_near = 6;
-    if (p.n_cheb < 2 || p.n_cheb > DDM_MAX_CHEB || (p.n_cheb & 1) || p.quad_near > 16 || p.max_depth < 0)
+    if (p.n_cheb < 2 || p.n_cheb > DDM_MAX_CHEB || (p.n_cheb & 1) || p.quad_near > 16 || p.max_depth < 0 ||
+        (p.adaptive != 0 && p.adaptive != 1))
         return DDM_EINVAL;
     ddm_ctx *c = new (std::nothrow) ddm_ctx();
     if (!c) return DDM_ENOMEM;
@@ -459,7 +460,8 @@ ddm_status ddm_build_tree_params(ddm_ctx *ctx, const double *d_xy, int64_t n, co
     if (p.n_cheb <= 0) p.n_cheb = ctx->prm.n_cheb;
     if (p.leaf_size <= 0) p.leaf_size = ctx->prm.leaf_size;
     if (p.quad_near <= 0) p.quad_near = ctx->prm.quad_near;
-    if (p.n_cheb < 2 || p.n_cheb > DDM_MAX_CHEB || (p.n_cheb & 1) || p.quad_near > 16 || p.max_depth < 0)
+    if (p.n_cheb < 2 || p.n_cheb > DDM_MAX_CHEB || (p.n_cheb & 1) || p.quad_near > 16 || p.max_depth < 0 ||
+        (p.adaptive != 0 && p.adaptive != 1))
         return ctx_fail(ctx, DDM_EINVAL, "ddm_build_tree_params: bad FMM parameters");
     return tree_build(ctx, d_xy, n, p, out);
 }
@@ -471,10 +473,13 @@ ddm_status ddm_tree_get_info(const ddm_tree *t, ddm_tree_info *info) {
     info->n_elements = t->n;
     info->depth = t->depth;
     info->n_cells = t->n_cells;
-    info->n_leaves = t->lvl_off[t->depth + 1] - t->lvl_off[t->depth];
+    info->n_leaves = t->n_leaf;
     info->n_m2l_pairs = t->n_m2l;
     info->n_p2p_pairs = t->n_p2p;
     info->root_half_width = t->h0;
+    info->leaf_level_min = t->leaf_level_min;
+    info->adaptive = t->adaptive;
+    info->max_leaf_records = t->max_recs;
     return DDM_OK;
 }
 

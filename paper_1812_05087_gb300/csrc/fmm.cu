@@ -156,9 +156,9 @@ struct UpSmem {
 // P2M: lane owns node entries (a, b) = lane + 32 j and all 4 components;
 // the UP_W warps take every UP_W-th point and are summed at the end.
 template <int N>
-__device__ __forceinline__ void up_body(const int32_t *cstart, const int32_t *cend, int64_t loff, int L,
+__device__ __forceinline__ void up_body(const int32_t *cstart, const int32_t *cend, const int2 *leaf_at, float h0,
                                         const int32_t *cix, const int32_t *ciy, const int32_t *parent,
-                                        const float4 *grel, const float4 *frame, const float4 *chg, float hL, float *W,
+                                        const float4 *grel, const float4 *frame, const float4 *chg, float *W,
                                         float *Fz, const float *T, int64_t bid) {
     using S = UpSmem<N>;
     constexpr int N2 = S::N2, NOUT = S::NOUT, SXS = S::SXS, NE = (N2 + 31) / 32, KO = (NOUT + UP_T - 1) / UP_T;
@@ -167,7 +167,10 @@ __device__ __forceinline__ void up_body(const int32_t *cstart, const int32_t *ce
     float *sx = sm, *sy = sm + N * SXS;
     float4 *wd = reinterpret_cast<float4 *>(sm + 2 * N * SXS);   // 16-byte aligned: 2 N SXS is a multiple of 4
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t leaf = loff + bid;
+    const int2 la = leaf_at[bid];             // the leaf's cell and level
+    const int64_t leaf = la.x;
+    const int L = la.y;
+    const float hL = ldexpf(h0, -L);          // the leaf's half-width
     const int s0 = cstart[leaf], s1 = cend[leaf];
     constexpr int nq = N;                     // Gauss points per element
     float acc[NE][4];
@@ -285,11 +288,11 @@ __device__ __forceinline__ void up_body(const int32_t *cstart, const int32_t *ce
     }
 }
 template <int N>
-__global__ void __launch_bounds__(UP_T) k_up(const int32_t *cstart, const int32_t *cend, int64_t loff, int L,
-                                             const int32_t *cix, const int32_t *ciy, const int32_t *parent,
-                                             const float4 *grel, const float4 *frame, const float4 *chg, float hL,
-                                             float *W, float *Fz, const float *T) {
-    up_body<N>(cstart, cend, loff, L, cix, ciy, parent, grel, frame, chg, hL, W, Fz, T, blockIdx.x);
+__global__ void __launch_bounds__(UP_T) k_up(const int32_t *cstart, const int32_t *cend, const int2 *leaf_at,
+                                             float h0, const int32_t *cix, const int32_t *ciy, const int32_t *parent,
+                                             const float4 *grel, const float4 *frame, const float4 *chg, float *W,
+                                             float *Fz, const float *T) {
+    up_body<N>(cstart, cend, leaf_at, h0, cix, ciy, parent, grel, frame, chg, W, Fz, T, blockIdx.x);
 }
 
 // ----------------------------------------------------- downward pass (fused)
@@ -299,16 +302,18 @@ __global__ void __launch_bounds__(UP_T) k_up(const int32_t *cstart, const int32_
 // ancestors' values are only read, so leaves sharing them need no order.
 constexpr int L2L_T = 128;
 template <int N>
-__device__ __forceinline__ void down_body(int64_t loff, int L, const int32_t *cix, const int32_t *ciy,
+__device__ __forceinline__ void down_body(const int2 *leaf_at, float h0, const int32_t *cix, const int32_t *ciy,
                                           const int32_t *parent, const float *T, const float *F,
-                                          const int32_t *cstart, const int32_t *cend, const float4 *grel, float wL,
+                                          const int32_t *cstart, const int32_t *cend, const float4 *grel,
                                           float4 *far4, int64_t bid) {
     constexpr int N2 = N * N, NOUT = 4 * N2, KO = (NOUT + L2L_T - 1) / L2L_T;
     __shared__ float sT[2 * N2], sf[NOUT], tmp[NOUT];
     __shared__ int64_t anc[DDM_MAX_LEVELS + 1];
     __shared__ int squad[DDM_MAX_LEVELS + 1];
     const int tid = threadIdx.x;
-    const int64_t leaf = loff + bid;
+    const int2 la = leaf_at[bid];             // the leaf's cell and level
+    const int64_t leaf = la.x;
+    const int L = la.y;
     if (tid == 0) {
         int64_t c = leaf;
         for (int l = L; l >= 2; --l) {
@@ -319,8 +324,9 @@ __device__ __forceinline__ void down_body(int64_t loff, int L, const int32_t *ci
     }
     for (int i = tid; i < 2 * N2; i += L2L_T) sT[i] = T[i];
     __syncthreads();
-    const float *F2 = F + anc[2] * NOUT;
-    for (int i = tid; i < NOUT; i += L2L_T) sf[i] = F2[i];
+    // (a leaf above level 2 has no far field: no cell there has an M2L list)
+    const float *F2 = L >= 2 ? F + anc[2] * NOUT : nullptr;
+    for (int i = tid; i < NOUT; i += L2L_T) sf[i] = F2 ? F2[i] : 0.f;
     __syncthreads();
     for (int l = 3; l <= L; ++l) {
         const float *Fc = F + anc[l] * NOUT;
@@ -355,7 +361,7 @@ __device__ __forceinline__ void down_body(int64_t loff, int L, const int32_t *ci
     }
     // L2P at the leaf's targets (global sxx, syy, sxy, p; rotated by the caller)
     const float *cheb = c_gl.cheb[N / 2 - 1], *bw = c_gl.bw[N / 2 - 1];
-    const float hL = 0.5f * wL;
+    const float hL = ldexpf(h0, -L);
     for (int ti = cstart[leaf] + tid; ti < cend[leaf]; ti += L2L_T) {
         const float4 rt = grel[ti];
         const float xh = __fdividef(0.5f * (rt.x + rt.z), hL), yh = __fdividef(0.5f * (rt.y + rt.w), hL);
@@ -397,11 +403,11 @@ __device__ __forceinline__ void down_body(int64_t loff, int L, const int32_t *ci
     }
 }
 template <int N>
-__global__ void __launch_bounds__(L2L_T) k_down(int64_t loff, int L, const int32_t *cix, const int32_t *ciy,
-                                                const int32_t *parent, const float *T, const float *F,
-                                                const int32_t *cstart, const int32_t *cend, const float4 *grel,
-                                                float wL, float4 *far4) {
-    down_body<N>(loff, L, cix, ciy, parent, T, F, cstart, cend, grel, wL, far4, blockIdx.x);
+__global__ void __launch_bounds__(L2L_T) k_down(const int2 *leaf_at, float h0, const int32_t *cix,
+                                                const int32_t *ciy, const int32_t *parent, const float *T,
+                                                const float *F, const int32_t *cstart, const int32_t *cend,
+                                                const float4 *grel, float4 *far4) {
+    down_body<N>(leaf_at, h0, cix, ciy, parent, T, F, cstart, cend, grel, far4, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------- M2L
@@ -874,42 +880,44 @@ __device__ __forceinline__ void warp_sum_ds(float &h, float &l) {
         two_sum_add(h, l, bh, bl);
     }
 }
+// One chunk (up to 32) of a leaf's direct-interaction records into the
+// warp's table: element starts and the prefix sums of the counts (one lane
+// per record).
+constexpr int REC_CHUNK = 32;
+__device__ __forceinline__ void load_recs(const int4 *nbtab, int q, int nc, int lane, int *sst, int *spre) {
+    const int4 tb = lane < nc ? nbtab[q + lane] : make_int4(0, 0, 0, 0);
+    int incl = tb.y;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane < nc) {
+        sst[lane] = tb.x;
+        spre[lane + 1] = incl;
+    }
+    if (lane == 0) spre[0] = 0;
+}
 template <bool PRECISE>
 __global__ void __launch_bounds__(NEAR_T, 4) k_near(KConst<float> k, KConst<double> kd, Win<float> w, Win<double> wd,
                                                  const int32_t *nboff, const int4 *nbtab, const int32_t *elem_leaf,
                                                  const float4 *grel, const float4 *gloc, const float2 *ggrid,
                                                  float g16, const float4 *frame, const float4 *chg,
-                                                 const int64_t *perm, int64_t loff, float wL, int n, int nq,
+                                                 const int64_t *perm, const int2 *leaf_at, float h0, int n, int nq,
                                                  const float *F, int use_far, int64_t N, double scale, double *y) {
     constexpr unsigned FULL = 0xFFFFFFFFu;
-    __shared__ int sst[NEAR_W][9], spre[NEAR_W][10];
+    __shared__ int sst[NEAR_W][REC_CHUNK], spre[NEAR_W][REC_CHUNK + 1];
     __shared__ int2 sq[NEAR_W][NEAR_Q];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t ti = (int64_t)blockIdx.x * NEAR_W + wid;
     if (ti >= N) return;                      // whole warp leaves together
     const int32_t leaf = elem_leaf[ti];
     const int q0 = nboff[leaf], nb = nboff[leaf + 1] - q0;
-    {   // neighbour table: one lane per neighbour leaf, counts prefix-summed
-        int4 tb = lane < nb ? nbtab[q0 + lane] : make_int4(0, 0, 0, 0);
-        int incl = tb.y;
-#pragma unroll
-        for (int o = 1; o < 16; o <<= 1) {
-            int v = __shfl_up_sync(FULL, incl, o);
-            if (lane >= o) incl += v;
-        }
-        if (lane < nb) {
-            sst[wid][lane] = tb.x;
-            spre[wid][lane + 1] = incl;
-        }
-        if (lane == 0) spre[wid][0] = 0;
-    }
-    __syncwarp();
     // pairs: positions relative to the target's grid point (exact grid
     // differences times g16); L2P: the target relative to its leaf centre
     const float4 lt = gloc[ti];
     const float2 gt = ggrid[ti];
     const float mx = 0.5f * (lt.x + lt.z), my = 0.5f * (lt.y + lt.w);
-    const int S = spre[wid][nb];
     // lanes 0, 1, 2 write sigma_s, sigma_n, p at the end: fetch what they need now
     int64_t eout = 0;
     float4 fout = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -921,49 +929,57 @@ __global__ void __launch_bounds__(NEAR_T, 4) k_near(KConst<float> k, KConst<doub
     }
     float acc[4] = {0, 0, 0, 0};
     double accd[4] = {0, 0, 0, 0};
-    int qn = 0, slot = 0;
+    int qn = 0;
     bool anyq = false;
-    for (int base = 0; base < S; base += 32) {
-        const int c = base + lane;
-        bool close = false, hasq = false;
-        int sj = -1;
-        float4 r = make_float4(0.f, 0.f, 0.f, 0.f), f = r, cg = r;
-        float ox = 0.f, oy = 0.f;
-        if (c < S) {
-            while (c >= spre[wid][slot + 1]) ++slot;
-            sj = sst[wid][slot] + (c - spre[wid][slot]);
-            if (sj != (int)ti) {
-                r = gloc[sj];
-                f = frame[sj];
-                cg = chg[sj];
-                const float2 gs = ggrid[sj];
-                ox = g16 * (gs.x - gt.x);
-                oy = g16 * (gs.y - gt.y);
-                float dx = mx - 0.5f * (r.x + r.z) - ox, dy = my - 0.5f * (r.y + r.w) - oy;
-                float r2 = dx * dx + dy * dy;
-                if (r2 > 64.f * f.z * f.z)
-                    far_pair<PRECISE>(k, kd, w, wd, dx, dy, r2, f.z, f.x, f.y, cg.x, cg.y, cg.z, acc, accd);
-                else {
-                    close = true;
-                    hasq = cg.z != 0.f;
+    for (int cb = 0; cb < nb; cb += REC_CHUNK) {   // records in chunks (a uniform tree has <= 9)
+        const int nc = min(REC_CHUNK, nb - cb);
+        __syncwarp();                             // the previous chunk's table is read
+        load_recs(nbtab, q0 + cb, nc, lane, sst[wid], spre[wid]);
+        __syncwarp();
+        const int S = spre[wid][nc];
+        int slot = 0;
+        for (int base = 0; base < S; base += 32) {
+            const int c = base + lane;
+            bool close = false, hasq = false;
+            int sj = -1;
+            float4 r = make_float4(0.f, 0.f, 0.f, 0.f), f = r, cg = r;
+            float ox = 0.f, oy = 0.f;
+            if (c < S) {
+                while (c >= spre[wid][slot + 1]) ++slot;
+                sj = sst[wid][slot] + (c - spre[wid][slot]);
+                if (sj != (int)ti) {
+                    r = gloc[sj];
+                    f = frame[sj];
+                    cg = chg[sj];
+                    const float2 gs = ggrid[sj];
+                    ox = g16 * (gs.x - gt.x);
+                    oy = g16 * (gs.y - gt.y);
+                    float dx = mx - 0.5f * (r.x + r.z) - ox, dy = my - 0.5f * (r.y + r.w) - oy;
+                    float r2 = dx * dx + dy * dy;
+                    if (r2 > 64.f * f.z * f.z)
+                        far_pair<PRECISE>(k, kd, w, wd, dx, dy, r2, f.z, f.x, f.y, cg.x, cg.y, cg.z, acc, accd);
+                    else {
+                        close = true;
+                        hasq = cg.z != 0.f;
+                    }
                 }
             }
-        }
-        const unsigned m = __ballot_sync(FULL, close);
-        if (m) {
-            anyq = anyq || __ballot_sync(FULL, hasq) != 0u;
-            const int pos = qn + __popc(m & ((1u << lane) - 1u));
-            if (close) {
-                if (pos < NEAR_Q) {
-                    sq[wid][pos] = make_int2(sj, slot);
-                } else {                      // queue full: this pair in place
-                    int nu = 2 + (hasq ? nq : 0);
-                    for (int u = 0; u < nu; ++u)
-                        near_unit<PRECISE>(u, nq, k, kd, w, wd, mx, my, r.x + ox, r.y + oy, r.z + ox, r.w + oy, f.z,
-                                           f.x, f.y, cg.x, cg.y, cg.z, acc, accd);
+            const unsigned m = __ballot_sync(FULL, close);
+            if (m) {
+                anyq = anyq || __ballot_sync(FULL, hasq) != 0u;
+                const int pos = qn + __popc(m & ((1u << lane) - 1u));
+                if (close) {
+                    if (pos < NEAR_Q) {
+                        sq[wid][pos] = make_int2(sj, slot);
+                    } else {                      // queue full: this pair in place
+                        int nu = 2 + (hasq ? nq : 0);
+                        for (int u = 0; u < nu; ++u)
+                            near_unit<PRECISE>(u, nq, k, kd, w, wd, mx, my, r.x + ox, r.y + oy, r.z + ox, r.w + oy, f.z,
+                                               f.x, f.y, cg.x, cg.y, cg.z, acc, accd);
+                    }
                 }
+                qn += __popc(m);
             }
-            qn += __popc(m);
         }
     }
     __syncwarp();
@@ -1004,7 +1020,8 @@ __global__ void __launch_bounds__(NEAR_T, 4) k_near(KConst<float> k, KConst<doub
         // lane then fetches the two cardinals of its nodes m = lane,
         // lane + 32, ... by shuffle.
         const float *cheb = c_gl.cheb[(n >> 1) - 1], *bw = c_gl.bw[(n >> 1) - 1];
-        const float hL = 0.5f * wL;
+        const int2 la = leaf_at[leaf];
+        const float hL = ldexpf(h0, -la.y);
         const int j = lane & 15;
         const bool isy = lane >= 16;
         float tv = 0.f;
@@ -1023,7 +1040,7 @@ __global__ void __launch_bounds__(NEAR_T, 4) k_near(KConst<float> k, KConst<doub
         const bool half_hit = isy ? (hm >> 16) != 0u : (hm & 0xFFFFu) != 0u;
         const float card = half_hit ? (hit ? 1.f : 0.f) : tv * __fdividef(1.f, sum);
         const int n2 = n * n;
-        const float *Fc = F + (loff + leaf) * 4 * n2;
+        const float *Fc = F + (int64_t)la.x * 4 * n2;
         float f4[4] = {0, 0, 0, 0};
         for (int base = 0; base < n2; base += 32) {
             const int m = base + lane, mc = m < n2 ? m : n2 - 1;
@@ -1081,7 +1098,7 @@ __device__ __forceinline__ void near2_body(const KConst<float> &k, const Win<flo
                                            double scale, double *y, int64_t item) {
     const Win<float> w = TWO ? win : Win<float>{win.ct_hi, 0.f, win.g_hi, 0.f, 1, win.rbig};
     constexpr unsigned FULL = 0xFFFFFFFFu;
-    __shared__ int sst[NEAR_W][9], spre[NEAR_W][10];
+    __shared__ int sst[NEAR_W][REC_CHUNK], spre[NEAR_W][REC_CHUNK + 1];
     __shared__ int2 sq[NEAR_W][NEAR_Q];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int2 it = items[item];
@@ -1089,21 +1106,6 @@ __device__ __forceinline__ void near2_body(const KConst<float> &k, const Win<flo
     const bool two = it.y >= 0;
     const int32_t leaf = elem_leaf[t0];
     const int q0 = nboff[leaf], nb = nboff[leaf + 1] - q0;
-    {   // neighbour table: one lane per neighbour leaf, counts prefix-summed
-        int4 tb = lane < nb ? nbtab[q0 + lane] : make_int4(0, 0, 0, 0);
-        int incl = tb.y;
-#pragma unroll
-        for (int o = 1; o < 16; o <<= 1) {
-            int v = __shfl_up_sync(FULL, incl, o);
-            if (lane >= o) incl += v;
-        }
-        if (lane < nb) {
-            sst[wid][lane] = tb.x;
-            spre[wid][lane + 1] = incl;
-        }
-        if (lane == 0) spre[wid][0] = 0;
-    }
-    __syncwarp();
     // every position below is relative to target 0's grid point: an
     // element's own offset from its grid point plus the exact grid
     // difference times g16 (rounded once, relative to the distance)
@@ -1111,7 +1113,6 @@ __device__ __forceinline__ void near2_body(const KConst<float> &k, const Win<flo
     const float2 ga = ggrid[t0], gb = ggrid[t1];
     const float mx0 = 0.5f * (ra.x + ra.z), my0 = 0.5f * (ra.y + ra.w);
     const float mx1 = fmaf(gb.x - ga.x, g16, 0.5f * (rb.x + rb.z)), my1 = fmaf(gb.y - ga.y, g16, 0.5f * (rb.y + rb.w));
-    const int S = spre[wid][nb];
     // lanes 0-2 write target 0's rows, lanes 3-5 target 1's: fetch what they need now
     const bool writer = lane < 3 || (two && lane < 6);
     const int tw = lane < 3 ? t0 : t1, row = lane < 3 ? lane : lane - 3;
@@ -1125,63 +1126,71 @@ __device__ __forceinline__ void near2_body(const KConst<float> &k, const Win<flo
     }
     float acc0[4] = {0, 0, 0, 0}, acc1[4] = {0, 0, 0, 0};
     double dummy[4];
-    int qn = 0, slot = 0;
+    int qn = 0;
     bool anyq = false;
-    for (int base = 0; base < S; base += 32) {
-        const int c = base + lane;
-        bool close0 = false, close1 = false, hasq = false;
-        int sj = -1;
-        if (c < S) {
-            while (c >= spre[wid][slot + 1]) ++slot;
-            sj = sst[wid][slot] + (c - spre[wid][slot]);
-            const float4 r = gloc[sj], f = frame[sj], cg = chg[sj];
-            const float2 gs = ggrid[sj];
-            const float cxs = fmaf(gs.x - ga.x, g16, 0.5f * (r.x + r.z)), cys = fmaf(gs.y - ga.y, g16, 0.5f * (r.y + r.w));
-            const float lim = 64.f * f.z * f.z;
-            const FarSrc fs = far_src(f.z, f.x, f.y, cg.x, cg.y, cg.z, w.rbig);
-            hasq = cg.z != 0.f;
-            // beyond 8 a, or anywhere u > Big along the element: at once
-            const float lim2 = fminf(lim, fs.r2_big);
-            if (sj != t0) {
-                const float dx = mx0 - cxs, dy = my0 - cys, r2 = dx * dx + dy * dy;
-                if (r2 > lim2) far_pair_f(k, w, dx, dy, r2, fs, acc0);
-                else close0 = true;
+    for (int cb = 0; cb < nb; cb += REC_CHUNK) {   // records in chunks (a uniform tree has <= 9)
+        const int nc = min(REC_CHUNK, nb - cb);
+        __syncwarp();                             // the previous chunk's table is read
+        load_recs(nbtab, q0 + cb, nc, lane, sst[wid], spre[wid]);
+        __syncwarp();
+        const int S = spre[wid][nc];
+        int slot = 0;
+        for (int base = 0; base < S; base += 32) {
+            const int c = base + lane;
+            bool close0 = false, close1 = false, hasq = false;
+            int sj = -1;
+            if (c < S) {
+                while (c >= spre[wid][slot + 1]) ++slot;
+                sj = sst[wid][slot] + (c - spre[wid][slot]);
+                const float4 r = gloc[sj], f = frame[sj], cg = chg[sj];
+                const float2 gs = ggrid[sj];
+                const float cxs = fmaf(gs.x - ga.x, g16, 0.5f * (r.x + r.z)), cys = fmaf(gs.y - ga.y, g16, 0.5f * (r.y + r.w));
+                const float lim = 64.f * f.z * f.z;
+                const FarSrc fs = far_src(f.z, f.x, f.y, cg.x, cg.y, cg.z, w.rbig);
+                hasq = cg.z != 0.f;
+                // beyond 8 a, or anywhere u > Big along the element: at once
+                const float lim2 = fminf(lim, fs.r2_big);
+                if (sj != t0) {
+                    const float dx = mx0 - cxs, dy = my0 - cys, r2 = dx * dx + dy * dy;
+                    if (r2 > lim2) far_pair_f(k, w, dx, dy, r2, fs, acc0);
+                    else close0 = true;
+                }
+                if (two && sj != t1) {
+                    const float dx = mx1 - cxs, dy = my1 - cys, r2 = dx * dx + dy * dy;
+                    if (r2 > lim2) far_pair_f(k, w, dx, dy, r2, fs, acc1);
+                    else close1 = true;
+                }
             }
-            if (two && sj != t1) {
-                const float dx = mx1 - cxs, dy = my1 - cys, r2 = dx * dx + dy * dy;
-                if (r2 > lim2) far_pair_f(k, w, dx, dy, r2, fs, acc1);
-                else close1 = true;
-            }
-        }
-        // queue the close (source, target) pairs: entry (source, slot | target << 8)
+            // queue the close (source, target) pairs: entry (source, slot | target << 8)
 #pragma unroll
-        for (int tg = 0; tg < 2; ++tg) {
-            const bool cl = tg ? close1 : close0;
-            const unsigned m = __ballot_sync(FULL, cl);
-            if (m) {
-                anyq = anyq || __ballot_sync(FULL, cl && hasq) != 0u;
-                const int pos = qn + __popc(m & ((1u << lane) - 1u));
-                if (cl) {
-                    if (pos < NEAR_Q) {
-                        sq[wid][pos] = make_int2(sj, slot | (tg << 8));
-                    } else {                  // queue full: this pair in place
-                        const float4 r = gloc[sj], f = frame[sj], cg = chg[sj];
-                        const float2 gs = ggrid[sj];
-                        const float ox = g16 * (gs.x - ga.x), oy = g16 * (gs.y - ga.y);
-                        const int nu = 2 + (cg.z != 0.f ? nq : 0);
-                        float a4[4] = {0, 0, 0, 0};
-                        for (int u = 0; u < nu; ++u)
-                            near_unit<false>(u, nq, k, KConst<double>{}, w, Win<double>{}, tg ? mx1 : mx0,
-                                             tg ? my1 : my0, r.x + ox, r.y + oy, r.z + ox, r.w + oy, f.z, f.x, f.y,
-                                             cg.x, cg.y, cg.z, a4, dummy);
+            for (int tg = 0; tg < 2; ++tg) {
+                const bool cl = tg ? close1 : close0;
+                const unsigned m = __ballot_sync(FULL, cl);
+                if (m) {
+                    anyq = anyq || __ballot_sync(FULL, cl && hasq) != 0u;
+                    const int pos = qn + __popc(m & ((1u << lane) - 1u));
+                    if (cl) {
+                        if (pos < NEAR_Q) {
+                            sq[wid][pos] = make_int2(sj, slot | (tg << 8));
+                        } else {                  // queue full: this pair in place
+                            const float4 r = gloc[sj], f = frame[sj], cg = chg[sj];
+                            const float2 gs = ggrid[sj];
+                            const float ox = g16 * (gs.x - ga.x), oy = g16 * (gs.y - ga.y);
+                            const int nu = 2 + (cg.z != 0.f ? nq : 0);
+                            float a4[4] = {0, 0, 0, 0};
+                            for (int u = 0; u < nu; ++u)
+                                near_unit<false>(u, nq, k, KConst<double>{}, w, Win<double>{}, tg ? mx1 : mx0,
+                                                 tg ? my1 : my0, r.x + ox, r.y + oy, r.z + ox, r.w + oy, f.z, f.x, f.y,
+                                                 cg.x, cg.y, cg.z, a4, dummy);
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            acc0[c] += tg ? 0.f : a4[c];
-                            acc1[c] += tg ? a4[c] : 0.f;
+                            for (int c = 0; c < 4; ++c) {
+                                acc0[c] += tg ? 0.f : a4[c];
+                                acc1[c] += tg ? a4[c] : 0.f;
+                            }
                         }
                     }
+                    qn += __popc(m);
                 }
-                qn += __popc(m);
             }
         }
     }
@@ -1693,9 +1702,9 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
     st = window_self_blocks(ctx, t, lo, hi, s, &blk);
     if (st) return st;
     const int overwrite = accumulate ? 0 : 1;
-    int L = t->depth;
-    int64_t loff = t->lvl_off[L], nleaf = t->lvl_off[L + 1] - loff;
-    float wL = (float)(2.0 * t->h0 / (double)(1 << L));
+    const int L = t->depth;                   // deepest level
+    const int64_t nleaf = t->n_leaf;
+    const float h0f = (float)t->h0;           // leaf half-widths h0 2^-level, exact in FP32
     int use_far = mode != DDM_MODE_DENSE && L >= 2;
     {
         // charges; for the far field also zero the weights and local
@@ -1740,7 +1749,6 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
     const bool overlap = use_far && stream_override == nullptr && !ctx->prof.on;
     cudaStream_t fs = overlap ? ctx->aux : s;
     if (use_far) {
-        float hL = 0.5f * wL;
         if (overlap) {
             DDM_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_fork, s));
             DDM_CUDA_TRY(ctx, cudaStreamWaitEvent(fs, ctx->ev_fork, 0));
@@ -1748,8 +1756,8 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
         // upward pass: P2M and M2M in one launch
         prof_begin(ctx, 2);
 #define DDM_UP(NN)                                                                                          \
-    k_up<NN><<<(unsigned)nleaf, UP_T, 0, fs>>>(t->cell_start, t->cell_end, loff, L, t->cell_ix, t->cell_iy,         \
-                                               t->cell_parent, t->g_rel, t->g_frame, t->chg, hL, t->W, t->Fl,          \
+    k_up<NN><<<(unsigned)nleaf, UP_T, 0, fs>>>(t->cell_start, t->cell_end, t->leaf_at, h0f, t->cell_ix, t->cell_iy, \
+                                               t->cell_parent, t->g_rel, t->g_frame, t->chg, t->W, t->Fl,              \
                                                ctx->cheb_Tn[NN / 2 - 1])
         DDM_CHEB_SWITCH(n, DDM_UP);
 #undef DDM_UP
@@ -1812,8 +1820,9 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
         // downward pass: L2L chains to the leaves and L2P at their targets, one launch
         prof_begin(ctx, 5);
 #define DDM_DOWN(NN)                                                                                        \
-    k_down<NN><<<(unsigned)nleaf, L2L_T, 0, fs>>>(loff, L, t->cell_ix, t->cell_iy, t->cell_parent, ctx->cheb_Tn[n / 2 - 1], t->Fl, \
-                                                  t->cell_start, t->cell_end, t->g_rel, wL, t->far4)
+    k_down<NN><<<(unsigned)nleaf, L2L_T, 0, fs>>>(t->leaf_at, h0f, t->cell_ix, t->cell_iy, t->cell_parent,           \
+                                                  ctx->cheb_Tn[n / 2 - 1], t->Fl, t->cell_start, t->cell_end, t->g_rel, \
+                                                  t->far4)
         DDM_CHEB_SWITCH(n, DDM_DOWN);
 #undef DDM_DOWN
         prof_end(ctx, 5, 1);
@@ -1823,7 +1832,7 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
     if (precise)
         k_near<true><<<(unsigned)((N + NEAR_W - 1) / NEAR_W), NEAR_T, 0, s>>>(
             kf, ctx->kd, wf, wd, t->nb_off, t->nb_tab, t->elem_leaf, t->g_rel, t->g_loc, t->g_grid, t->g16,
-            t->g_frame, t->chg, t->perm, loff, wL, n, nq, t->Fl, 0, N, scale, y);
+            t->g_frame, t->chg, t->perm, t->leaf_at, h0f, n, nq, t->Fl, 0, N, scale, y);
     else
         (lo > 0.0 ? k_near2<true> : k_near2<false>)<<<(unsigned)((t->n_items + NEAR_W - 1) / NEAR_W), NEAR_T, 0, s>>>(
             kf, wf, t->nb_off, t->nb_tab, t->elem_leaf, t->g_loc, t->g_grid, t->g_frame, t->chg, t->perm, t->g16, nq,
@@ -1870,9 +1879,10 @@ struct BDesc {
     const int32_t *mk_off;
     const int2 *mk_pair;
     const float *ops;
-    int64_t n, loff, zoff;
+    const int2 *leaf_at;
+    int64_t n, zoff;
     int L, nq;
-    float wL, hL, g16;
+    float h0, g16;
 };
 constexpr int BE_T = 256, BE_CHUNK = 1024;
 // items (p, kind, a, b): kind 0 prepares elements [a, b), kind 1 zeroes the
@@ -1903,7 +1913,7 @@ __global__ void __launch_bounds__(UP_T) k_up_b(const BDesc *D, const int2 *items
         const int2 w = items[it];
         if (act && !act[w.x]) continue;      // uniform over the block
         const BDesc &d = D[w.x];
-        up_body<N>(d.cstart, d.cend, d.loff, d.L, d.cix, d.ciy, d.parent, d.g_rel, d.g_frame, d.chg, d.hL, d.W, d.Fl,
+        up_body<N>(d.cstart, d.cend, d.leaf_at, d.h0, d.cix, d.ciy, d.parent, d.g_rel, d.g_frame, d.chg, d.W, d.Fl,
                    T, w.y);
         __syncthreads();                      // shared staging is reused by the next item
     }
@@ -1915,7 +1925,7 @@ __global__ void __launch_bounds__(L2L_T) k_down_b(const BDesc *D, const int2 *it
         const int2 w = items[it];
         if (act && !act[w.x]) continue;
         const BDesc &d = D[w.x];
-        down_body<N>(d.loff, d.L, d.cix, d.ciy, d.parent, T, d.Fl, d.cstart, d.cend, d.g_rel, d.wL, d.far4, w.y);
+        down_body<N>(d.leaf_at, d.h0, d.cix, d.ciy, d.parent, T, d.Fl, d.cstart, d.cend, d.g_rel, d.far4, w.y);
         __syncthreads();
     }
 }
@@ -2004,8 +2014,7 @@ ddm_status bfmm_build(ddm_ctx *ctx, ddm_tree *const *trees, int np, const int *i
         const bool far = L >= 2;
         const float *ops = nullptr;
         if (far && (st = window_ops(ctx, t, lo, hi, s, &ops))) return st;
-        const int64_t loff = t->lvl_off[L], nleaf = t->lvl_off[L + 1] - loff;
-        const float wL = (float)(2.0 * t->h0 / (double)(1 << L));
+        const int64_t nleaf = t->n_leaf;
         BDesc &d = hd[p];
         d.x = xs[p]; d.y = ys[p];
         d.perm = t->perm; d.g_frame = t->g_frame; d.g_rel = t->g_rel; d.blk = blk;
@@ -2015,7 +2024,7 @@ ddm_status bfmm_build(ddm_ctx *ctx, ddm_tree *const *trees, int np, const int *i
         d.parent = t->cell_parent;
         d.nb_off = t->nb_off; d.nb_tab = t->nb_tab; d.elem_leaf = t->elem_leaf; d.near_items = t->near_items;
         d.mk_work = t->mk_work; d.mk_off = t->mk_off; d.mk_pair = t->mk_pair; d.ops = ops;
-        d.n = t->n; d.loff = loff; d.L = L; d.nq = t->prm.quad_near; d.wL = wL; d.hL = 0.5f * wL;
+        d.n = t->n; d.leaf_at = t->leaf_at; d.L = L; d.nq = t->prm.quad_near; d.h0 = (float)t->h0;
         d.zoff = far ? t->lvl_off[2] * 4 * n2 : 0;
         for (int64_t a = 0; a < t->n; a += BE_CHUNK) {
             const int b = (int)std::min<int64_t>(t->n, a + BE_CHUNK);

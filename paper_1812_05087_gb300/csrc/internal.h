@@ -44,7 +44,8 @@ struct ddm_tree {
     cudaStream_t stream;       // stream of the build; frees are ordered on it
     ddm_fmm_params prm;        // FMM parameters of this tree (order, leaf size, depth cap, near rule)
     int64_t n;                 // elements
-    int depth;                 // leaf level L
+    int depth;                 // deepest level (the leaf level of a uniform tree)
+    int adaptive;              // leaves at any level (cells of > leaf_size elements split)
     double cx, cy, h0;         // root square centre and half-width
     // per level l = 0..L: non-empty cells [lvl_off[l], lvl_off[l+1])
     std::vector<int64_t> lvl_off;
@@ -56,8 +57,15 @@ struct ddm_tree {
     int32_t *cell_start, *cell_end;   // sorted element range
     int32_t *cell_parent;      // global cell index of the parent (-1 at level 0)
     int32_t *il_off, *il_idx;  // interaction lists (CSR over cells)
-    int32_t *nb_off, *nb_idx;  // neighbour lists of leaves incl. self (CSR over leaves, leaf-local)
-    int4 *nb_tab;              // per neighbour entry: (element start, count, cell dx, cell dy)
+    // leaves: (global cell index, level) of each, in cell order
+    int2 *leaf_at = nullptr;
+    int64_t n_leaf = 0;
+    int leaf_level_min = 0;
+    // direct-interaction records of every leaf (CSR over leaves): the element
+    // ranges it interacts with directly, (element start, count, 0, 0)
+    int32_t *nb_off = nullptr;
+    int4 *nb_tab = nullptr;
+    int max_recs = 0;          // most records of one leaf
     int2 *near_items;          // near-field work items: target pairs of one leaf (second -1: single)
     int64_t n_items;
     int32_t *elem_leaf;        // sorted element -> leaf index (leaf-local)

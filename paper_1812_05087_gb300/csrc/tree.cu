@@ -1,9 +1,10 @@
 // Quadtree of paper Sec. 3.1 built on the device: Morton keys of the element
 // midpoints, LSD radix sort, unique key prefixes per level (empty "zero"
-// cells never appear), parent links, neighbour lists (cells sharing a vertex)
-// and interaction lists (children of the parent's neighbours that are not
-// neighbours).  Uniform depth; children in Z order (left-right, then
-// bottom-top).
+// cells never appear), parent links, the direct-interaction records of the
+// leaves and interaction lists (children of the parent's neighbours that are
+// not neighbours).  Uniform depth, or adaptive (cells with more than
+// leaf_size elements split, leaves at any level); children in Z order
+// (left-right, then bottom-top).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -279,31 +280,27 @@ __global__ void k_parent(const int32_t *cstart, int64_t off, int64_t ncell, cons
 
 // near-field work items: consecutive target pairs of one leaf (a leaf with an
 // odd count ends with a single, second index -1)
-__global__ void k_items_count(const int32_t *cstart, const int32_t *cend, int64_t loff, int64_t nleaf, int32_t *cnt) {
+__global__ void k_items_count(const int32_t *cstart, const int32_t *cend, const int2 *leaf_at, int64_t nleaf,
+                              int32_t *cnt) {
     int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (L >= nleaf) return;
-    cnt[L] = (cend[loff + L] - cstart[loff + L] + 1) / 2;
+    const int c = leaf_at[L].x;
+    cnt[L] = (cend[c] - cstart[c] + 1) / 2;
 }
-__global__ void k_items_fill(const int32_t *cstart, const int32_t *cend, int64_t loff, int64_t nleaf,
+__global__ void k_items_fill(const int32_t *cstart, const int32_t *cend, const int2 *leaf_at, int64_t nleaf,
                              const int32_t *ioff, int2 *items) {
     int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (L >= nleaf) return;
-    const int s0 = cstart[loff + L], s1 = cend[loff + L];
+    const int c = leaf_at[L].x;
+    const int s0 = cstart[c], s1 = cend[c];
     int o = ioff[L];
     for (int e = s0; e < s1; e += 2) items[o++] = make_int2(e, e + 1 < s1 ? e + 1 : -1);
 }
 
-// per neighbour entry of every leaf: the neighbour's element range and its
-// cell offset from the leaf, so the near field reads one record per entry
-__global__ void k_nbtab(const int32_t *nboff, const int32_t *nbidx, const int32_t *cstart, const int32_t *cend,
-                        const int32_t *cix, const int32_t *ciy, int64_t loff, int64_t nleaf, int4 *tab) {
-    int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (L >= nleaf) return;
-    int64_t me = loff + L;
-    for (int e = nboff[L]; e < nboff[L + 1]; ++e) {
-        int64_t J = loff + nbidx[e];
-        tab[e] = make_int4(cstart[J], cend[J] - cstart[J], cix[J] - cix[me], ciy[J] - ciy[me]);
-    }
+// the leaves of a uniform tree: every cell of level L
+__global__ void k_leaf_uniform(int64_t loff, int64_t nleaf, int L, int2 *leaf_at) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < nleaf) leaf_at[i] = make_int2((int)(loff + i), L);
 }
 
 __device__ int32_t find_key(const uint32_t *ckey, int64_t off, int64_t ncell, uint32_t k) {
@@ -346,24 +343,50 @@ __global__ void k_p2p_estimate(const uint32_t *ckey, const int32_t *cix, const i
     if (lane == 0 && v) atomicAdd(total, v);
 }
 
-// neighbours of each leaf (incl. itself): pass 0 counts, pass 1 fills.  One
-// warp per cell; lane k < 9 looks up neighbour (dx, dy) = (k % 3 - 1,
-// k / 3 - 1) and a ballot keeps the lists in that order.
-__global__ void k_neigh(const uint32_t *ckey, const int32_t *cix, const int32_t *ciy, int64_t off,
-                        int64_t ncell, int side, const int32_t *nboff, int32_t *nbidx, int32_t *cnt) {
-    const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+// Direct-interaction records of each leaf P (level lp): pass 0 counts, pass
+// 1 fills.  Two leaves interact directly iff their ancestors at the coarser
+// of the two levels share a vertex or coincide, so P's sources are
+//   (a) the cells of level lp sharing a vertex with P (P included): their
+//       whole subtrees, one contiguous element range each (Z order);
+//   (b) for each coarser level m < lp, the leaves of level m that share a
+//       vertex with P's ancestor at level m.
+// Every other pair meets in the M2L of the first level at which its
+// ancestors are apart.  In a uniform tree (b) finds nothing (is_leaf null).
+// One warp per leaf; lane k < 9 looks up offset (k % 3 - 1, k / 3 - 1), and
+// ballots keep the records in that order, level by level.
+__global__ void k_recs(const uint32_t *ckey, const int32_t *cix, const int32_t *ciy, const int32_t *cstart,
+                       const int32_t *cend, const int32_t *is_leaf, const int64_t *lvoff, const int2 *leaf_at,
+                       int64_t nleaf, const int32_t *roff, int4 *tab, int32_t *cnt, int32_t *cmax) {
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (c >= ncell) return;                   // whole warp
-    const int ix = cix[off + c], iy = ciy[off + c];
-    int32_t j = -1;
-    if (lane < 9) {
-        const int jx = ix + lane % 3 - 1, jy = iy + lane / 3 - 1;
-        if (jx >= 0 && jy >= 0 && jx < side && jy < side)
-            j = find_key(ckey, off, ncell, spread2(jx) | (spread2(jy) << 1));
+    if (w >= nleaf) return;                   // whole warp
+    const int2 P = leaf_at[w];
+    const int lp = P.y, ix = cix[P.x], iy = ciy[P.x];
+    int m = 0;
+    for (int l = lp; l >= 1; --l) {
+        if (l < lp && !is_leaf) break;
+        const int sh = lp - l, ax = ix >> sh, ay = iy >> sh, side = 1 << l;
+        int32_t j = -1;
+        if (lane < 9 && (l == lp || lane != 4)) {
+            const int jx = ax + lane % 3 - 1, jy = ay + lane / 3 - 1;
+            if (jx >= 0 && jy >= 0 && jx < side && jy < side) {
+                const int32_t f = find_key(ckey, lvoff[l], lvoff[l + 1] - lvoff[l], morton(jx, jy));
+                if (f >= 0 && (l == lp || is_leaf[lvoff[l] + f])) j = (int32_t)(lvoff[l] + f);
+            }
+        }
+        const unsigned mask = __ballot_sync(0xFFFFFFFFu, j >= 0);
+        if (tab && j >= 0)
+            tab[roff[w] + m + __popc(mask & ((1u << lane) - 1u))] = make_int4(cstart[j], cend[j] - cstart[j], 0, 0);
+        m += __popc(mask);
     }
-    const unsigned mask = __ballot_sync(0xFFFFFFFFu, j >= 0);
-    if (nbidx && j >= 0) nbidx[nboff[c] + __popc(mask & ((1u << lane) - 1u))] = j;
-    if (cnt && lane == 0) cnt[c] = __popc(mask);
+    if (lp == 0) {                            // the root alone: the tree is one leaf
+        if (tab && lane == 0) tab[roff[w]] = make_int4(cstart[P.x], cend[P.x] - cstart[P.x], 0, 0);
+        m = 1;
+    }
+    if (cnt && lane == 0) {
+        cnt[w] = m;
+        atomicMax(cmax, m);
+    }
 }
 
 // interaction lists of the cells of one level (global cell indices): the
@@ -397,9 +420,122 @@ __global__ void k_ilist(const uint32_t *ckey, const int32_t *cix, const int32_t 
     if (cnt && lane == 0) cnt[off + c] = m;
 }
 
+// ------------------------------------------------------------ adaptive tree
+// Paper Sec. 3.1: a cell holding more than the prescribed number of elements
+// is divided into four children, recursively; otherwise it is a leaf.  The
+// cells of every level are first built as for a uniform tree (all non-empty
+// key prefixes down to the occupancy depth); the adaptive tree keeps those
+// whose every ancestor was split, renumbered in the same (level, key) order.
+struct LevelTab {
+    const int32_t *ec[KEY_LEVELS + 1];   // sorted element -> its cell of level l (level-local)
+    int64_t off[KEY_LEVELS + 2];         // first cell of level l (all non-empty cells)
+    int L;                               // deepest level built
+};
+
+// deepest level whose cells are at least four times the element's length
+// (the rule that bounds how far an element extends past its leaf)
+__global__ void k_elem_level(const double *xy, int64_t n, const int32_t *idx, double h0, int32_t *lev) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t e = idx[i];
+    const double len = hypot(xy[2 * n + e] - xy[e], xy[3 * n + e] - xy[n + e]);
+    const double v = floor(log2(2.0 * h0 / (4.0 * len)) + 1e-12);
+    lev[i] = (int32_t)fmin(fmax(v, 0.0), (double)KEY_LEVELS);
+}
+
+// minimum element level of every cell: a segmented minimum over each warp's
+// run of elements of one cell (cells are runs of consecutive sorted
+// elements), then one atomic per run
+__global__ void k_cell_minlev(LevelTab T, int64_t n, const int32_t *lev, int32_t *cmin) {
+    constexpr unsigned FULL = 0xFFFFFFFFu;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool ok = i < n;
+    const int v0 = ok ? lev[i] : KEY_LEVELS;
+    for (int l = 0; l <= T.L; ++l) {
+        const int c = ok ? T.ec[l][i] : -1;
+        int v = v0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int vo = __shfl_down_sync(FULL, v, o), co = __shfl_down_sync(FULL, c, o);
+            if (lane + o < 32 && co == c) v = min(v, vo);
+        }
+        const int cp = __shfl_up_sync(FULL, c, 1);
+        if (ok && (lane == 0 || cp != c)) atomicMin(&cmin[T.off[l] + c], v);
+    }
+}
+
+// a cell of level l is split when it holds more than s elements, l is above
+// the deepest level, and every element allows level l + 1; it exists when
+// every ancestor is split, and is a leaf when it exists and is not split
+__global__ void k_exist(LevelTab T, const int32_t *cstart, const int32_t *cend, const int32_t *parent,
+                        const int32_t *cmin, int s, int64_t NC, int32_t *exist, int32_t *leaf) {
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= NC) return;
+    int l = 0;
+    while (c >= T.off[l + 1]) ++l;
+    auto splits = [&](int64_t a, int la) { return la < T.L && cend[a] - cstart[a] > s && cmin[a] >= la + 1; };
+    bool ex = true;
+    int64_t a = parent[c];
+    for (int la = l - 1; a >= 0; --la) {
+        if (!splits(a, la)) {
+            ex = false;
+            break;
+        }
+        a = parent[a];
+    }
+    exist[c] = ex ? 1 : 0;
+    leaf[c] = (ex && !splits(c, l)) ? 1 : 0;
+}
+
+// the kept cells under their new indices (exclusive scan nidx of exist)
+__global__ void k_compact(int64_t NC, const int32_t *exist, const int32_t *nidx, const uint32_t *key,
+                          const int32_t *ix, const int32_t *iy, const int32_t *cs, const int32_t *ce,
+                          const int32_t *par, const int32_t *leaf, uint32_t *key2, int32_t *ix2, int32_t *iy2,
+                          int32_t *cs2, int32_t *ce2, int32_t *par2, int32_t *leaf2) {
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= NC || !exist[c]) return;
+    const int32_t j = nidx[c];
+    key2[j] = key[c];
+    ix2[j] = ix[c];
+    iy2[j] = iy[c];
+    cs2[j] = cs[c];
+    ce2[j] = ce[c];
+    par2[j] = par[c] >= 0 ? nidx[par[c]] : -1;
+    leaf2[j] = leaf[c];
+}
+
+// per level: first kept cell and first leaf (exclusive scans at the level
+// boundaries), levels 0 .. L + 1
+__global__ void k_level_counts(LevelTab T, const int32_t *nidx, const int32_t *lidx, int64_t *out) {
+    const int l = threadIdx.x;
+    if (l > T.L + 1) return;
+    out[l] = nidx[T.off[l]];
+    out[T.L + 2 + l] = lidx[T.off[l]];
+}
+
+// leaves (cell under its new index, level) and each sorted element's leaf
+__global__ void k_leaf_table(LevelTab T, int64_t NC, const int32_t *leaf, const int32_t *nidx, const int32_t *lidx,
+                             int2 *leaf_at) {
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= NC || !leaf[c]) return;
+    int l = 0;
+    while (c >= T.off[l + 1]) ++l;
+    leaf_at[lidx[c]] = make_int2(nidx[c], l);
+}
+__global__ void k_elem_leaf(LevelTab T, int64_t n, const int32_t *leaf, const int32_t *lidx, int32_t *elem_leaf) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t r = -1;
+    for (int l = 0; l <= T.L && r < 0; ++l) {   // the deepest level's kept cells are leaves
+        const int64_t c = T.off[l] + T.ec[l][i];
+        if (leaf[c]) r = lidx[c];
+    }
+    elem_leaf[i] = r;
+}
+
 __global__ void k_geom(const double *xy, int64_t n, const int32_t *idx, const int32_t *elem_leaf,
-                       const int32_t *cix, const int32_t *ciy, int64_t loff, double x0, double y0,
-                       double wl, double w16, int64_t *perm, float4 *g_rel, float4 *g_frame, float2 *g_grid,
+                       const int2 *leaf_at, const int32_t *cix, const int32_t *ciy, double x0, double y0,
+                       double h0, double w16, int64_t *perm, float4 *g_rel, float4 *g_frame, float2 *g_grid,
                        float4 *g_loc, double *xys) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -407,8 +543,9 @@ __global__ void k_geom(const double *xy, int64_t n, const int32_t *idx, const in
     perm[i] = e;
     double ax = xy[e], ay = xy[n + e], bx = xy[2 * n + e], by = xy[3 * n + e];
     xys[i] = ax; xys[n + i] = ay; xys[2 * n + i] = bx; xys[3 * n + i] = by;
-    int32_t c = elem_leaf[i];
-    double ccx = x0 + (cix[loff + c] + 0.5) * wl, ccy = y0 + (ciy[loff + c] + 0.5) * wl;
+    const int2 lf = leaf_at[elem_leaf[i]];
+    const double wl = ldexp(2.0 * h0, -lf.y);          // the leaf's width
+    double ccx = x0 + (cix[lf.x] + 0.5) * wl, ccy = y0 + (ciy[lf.x] + 0.5) * wl;
     g_rel[i] = make_float4((float)(ax - ccx), (float)(ay - ccy), (float)(bx - ccx), (float)(by - ccy));
     const double gx = fmin(fmax(floor((0.5 * (ax + bx) - x0) / w16), 0.0), 65535.0);
     const double gy = fmin(fmax(floor((0.5 * (ay + by) - y0) / w16), 0.0), 65535.0);
@@ -438,12 +575,13 @@ __global__ void k_mkeys(const int32_t *iloff, const int32_t *ilidx, const int32_
     }
 }
 
-__global__ void k_p2p_count(const int32_t *cstart, const int32_t *cend, int64_t loff, int64_t nleaf,
-                            const int32_t *nboff, const int32_t *nbidx, unsigned long long *tot) {
+__global__ void k_p2p_count(const int32_t *cstart, const int32_t *cend, const int2 *leaf_at, int64_t nleaf,
+                            const int32_t *nboff, const int4 *tab, unsigned long long *tot) {
     int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (c >= nleaf) return;
-    long long nt = cend[loff + c] - cstart[loff + c], ns = 0;
-    for (int k = nboff[c]; k < nboff[c + 1]; ++k) ns += cend[loff + nbidx[k]] - cstart[loff + nbidx[k]];
+    const int lc = leaf_at[c].x;
+    long long nt = cend[lc] - cstart[lc], ns = 0;
+    for (int k = nboff[c]; k < nboff[c + 1]; ++k) ns += tab[k].y;
     atomicAdd(tot, (unsigned long long)(nt * ns));
 }
 
@@ -528,7 +666,7 @@ static void find_chains(const double *hxy, int64_t n, Chains &out) {
 void tree_free(ddm_tree *t) {
     if (!t) return;
     void *ps[] = {t->mk_work, t->pb_off, t->pb_elem, t->pb_moff, t->pb_inv, t->pc_blk, t->pc_inv, t->mk_off, t->mk_pair, t->perm, t->cell_key, t->cell_ix, t->cell_iy, t->cell_start, t->cell_end, t->cell_parent,
-                  t->il_off, t->il_idx, t->nb_off, t->nb_idx, t->nb_tab, t->near_items, t->elem_leaf, t->g_rel, t->g_frame, t->g_grid, t->g_loc,
+                  t->il_off, t->il_idx, t->nb_off, t->leaf_at, t->nb_tab, t->near_items, t->elem_leaf, t->g_rel, t->g_frame, t->g_grid, t->g_loc,
                   t->xy_sorted, t->xy_caller, t->W, t->Fl, t->far4, t->chg, t->lv_off, t->lv_pair, t->lv_work,
                   t->Wc, t->Gc};
     for (void *p : ps) dfree(p, t->stream);
@@ -613,8 +751,9 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, const ddm_fmm
     TRY(radix_sort(S, st, key, idx, n, 32));
 
     // depth: smallest L whose leaves hold <= leaf_size, capped so that the
-    // longest element is at most a quarter of a leaf
-    int Lcap = (int)std::floor(std::log2(2.0 * h0 / (4.0 * lmax)) + 1e-12);
+    // longest element is at most a quarter of a leaf (adaptive: the cap is
+    // applied per cell, below)
+    int Lcap = prm.adaptive ? KEY_LEVELS : (int)std::floor(std::log2(2.0 * h0 / (4.0 * lmax)) + 1e-12);
     Lcap = std::max(0, std::min(Lcap, KEY_LEVELS));
     if (prm.max_depth > 0) Lcap = std::min(Lcap, prm.max_depth);
     int32_t *runmax = S.get<int32_t>(KEY_LEVELS + 1);
@@ -628,6 +767,7 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, const ddm_fmm
     for (int l = 0; l <= Lcap; ++l)
         if (hrun[l] <= prm.leaf_size) { L = l; break; }
     t->depth = L;
+    t->adaptive = prm.adaptive;
 
     // cells of every level
     std::vector<int32_t *> ecell(L + 1);
@@ -689,7 +829,84 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, const ddm_fmm
     // pairs.  Costs per unit measured on GB300 for n = 8 (near pair 19.4 ps,
     // interaction pair 3.5 ns scaling with n^4, cell 25 ns).
     int32_t *il_cnt = nullptr;                 // interaction-list counts of the depth choice, kept
-    if (L >= 3 && prm.max_depth == 0) {
+    int32_t *a_leaf = nullptr, *a_lidx = nullptr;   // adaptive: leaf flags and leaf numbering (all cells)
+    int32_t *is_leaf = nullptr;                      // adaptive: leaf flags of the kept cells
+    LevelTab LT{};
+    if (prm.adaptive) {
+        // keep the cells whose ancestors are all split (k_exist), renumbered
+        for (int l = 0; l <= L; ++l) {
+            LT.ec[l] = ecell[l];
+            LT.off[l] = t->lvl_off[l];
+        }
+        LT.off[L + 1] = NC;
+        LT.L = L;
+        int32_t *lev = S.get<int32_t>(n), *cmin = S.get<int32_t>(NC), *ex = S.get<int32_t>(NC + 1);
+        int32_t *nidx = S.get<int32_t>(NC + 1);
+        a_leaf = S.get<int32_t>(NC + 1);
+        a_lidx = S.get<int32_t>(NC + 1);
+        int64_t *lc = S.get<int64_t>(2 * (L + 2));
+        TRY(S.err);
+        k_elem_level<<<nbk, TB, 0, st>>>(d_xy, n, idx, h0, lev); ++tl_launches;
+        TRY(cudaMemsetAsync(cmin, 0x7F, NC * sizeof(int32_t), st));
+        k_cell_minlev<<<nbk, TB, 0, st>>>(LT, n, lev, cmin); ++tl_launches;
+        const int64_t cb = (NC + TB - 1) / TB;
+        k_exist<<<cb, TB, 0, st>>>(LT, t->cell_start, t->cell_end, t->cell_parent, cmin, prm.leaf_size, NC, ex,
+                                   a_leaf); ++tl_launches;
+        TRY(scan_excl_dev(S, st, ex, nidx, NC, nidx + NC));
+        TRY(scan_excl_dev(S, st, a_leaf, a_lidx, NC, a_lidx + NC));
+        k_level_counts<<<1, 32, 0, st>>>(LT, nidx, a_lidx, lc); ++tl_launches;
+        std::vector<int64_t> hl(2 * (L + 2));
+        TRY(cudaMemcpyAsync(hl.data(), lc, hl.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        TRY(cudaStreamSynchronize(st));
+        const int64_t NCa = hl[L + 1];
+        int La = 0;                               // deepest level with a kept cell
+        for (int l = 0; l <= L; ++l)
+            if (hl[l + 1] > hl[l]) La = l;
+        t->leaf_level_min = -1;
+        for (int l = 0; l <= L && t->leaf_level_min < 0; ++l)
+            if (hl[L + 2 + l + 1] > hl[L + 2 + l]) t->leaf_level_min = l;
+        t->n_leaf = hl[L + 2 + L + 1];
+        is_leaf = S.get<int32_t>(NCa + 1);
+        TRY(S.err);
+        uint32_t *key2 = nullptr;
+        int32_t *a2[5] = {};                      // ix, iy, start, end, parent of the kept cells
+        cudaError_t ae = dalloc(&key2, NCa * sizeof(uint32_t), st);
+        for (int k = 0; k < 5 && ae == cudaSuccess; ++k) ae = dalloc(&a2[k], NCa * sizeof(int32_t), st);
+        if (ae != cudaSuccess) {
+            dfree(key2, st);
+            for (int32_t *p : a2) dfree(p, st);
+            TRY(ae);
+        }
+        k_compact<<<cb, TB, 0, st>>>(NC, ex, nidx, t->cell_key, t->cell_ix, t->cell_iy, t->cell_start, t->cell_end,
+                                     t->cell_parent, a_leaf, key2, a2[0], a2[1], a2[2], a2[3], a2[4], is_leaf);
+        ++tl_launches;
+        dfree(t->cell_key, st);
+        dfree(t->cell_ix, st);
+        dfree(t->cell_iy, st);
+        dfree(t->cell_start, st);
+        dfree(t->cell_end, st);
+        dfree(t->cell_parent, st);
+        t->cell_key = key2;
+        t->cell_ix = a2[0];
+        t->cell_iy = a2[1];
+        t->cell_start = a2[2];
+        t->cell_end = a2[3];
+        t->cell_parent = a2[4];
+        TRY(dalloc(&t->leaf_at, std::max<int64_t>(t->n_leaf, 1) * sizeof(int2), st));
+        k_leaf_table<<<cb, TB, 0, st>>>(LT, NC, a_leaf, nidx, a_lidx, t->leaf_at); ++tl_launches;
+        // (the element -> leaf map, from a_leaf and a_lidx, is written with the geometry below)
+        // the kept tree: its levels, cell counts and leaf flags (compact numbering)
+        L = La;
+        t->depth = L;
+        t->lvl_off.assign(L + 2, 0);
+        ncl.assign(L + 1, 0);
+        for (int l = 0; l <= L; ++l) {
+            t->lvl_off[l + 1] = hl[l + 1];
+            ncl[l] = hl[l + 1] - hl[l];
+        }
+        NC = NCa;
+        t->n_cells = NC;
+    } else if (L >= 3 && prm.max_depth == 0) {
         const int L0 = std::max(2, L - 4), NCAND = L - L0 + 1;
         int32_t *ccnt = S.get<int32_t>(NC + 1);
         il_cnt = ccnt;
@@ -730,34 +947,47 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, const ddm_fmm
         t->n_cells = NC;
     }
 
-    // neighbours of leaves
-    int64_t nleaf = ncl[L], loff = t->lvl_off[L];
-    int side = 1 << L;
+    // leaves (a uniform tree: the cells of level L)
+    int64_t *lvd = S.get<int64_t>(L + 2);     // level offsets on the device
+    TRY(S.err);
+    TRY(cudaMemcpyAsync(lvd, t->lvl_off.data(), (L + 2) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    if (!prm.adaptive) {
+        t->n_leaf = ncl[L];
+        t->leaf_level_min = L;
+        TRY(dalloc(&t->leaf_at, std::max<int64_t>(t->n_leaf, 1) * sizeof(int2), st));
+        k_leaf_uniform<<<(unsigned)std::max<int64_t>((t->n_leaf + TB - 1) / TB, 1), TB, 0, st>>>(
+            t->lvl_off[L], t->n_leaf, L, t->leaf_at); ++tl_launches;
+    }
+    const int64_t nleaf = t->n_leaf;
     int32_t *cnt = S.get<int32_t>(std::max<int64_t>(NC, nleaf) + 1);
     TRY(S.err);
     TRY(dalloc(&t->nb_off, (nleaf + 1) * sizeof(int32_t), st));
     int64_t lb = (nleaf + TB - 1) / TB;
     const int64_t lbw = (32 * nleaf + TB - 1) / TB;   // one warp per leaf
-    // (list sizes are bounded from above, so that the totals can stay on the
-    // device until the one read-back below)
-    k_neigh<<<lbw, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, loff, nleaf, side, nullptr, nullptr, cnt); ++tl_launches;
+    // direct-interaction records: counts, offsets, records (list sizes are
+    // bounded from above, so that the totals can stay on the device until
+    // the one read-back below: 9 same-level cells, 8 leaves per coarser level)
+    int32_t *rmax = S.get<int32_t>(1);
+    TRY(S.err);
+    TRY(cudaMemsetAsync(rmax, 0, sizeof(int32_t), st));
+    k_recs<<<lbw, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, t->cell_start, t->cell_end, is_leaf, lvd,
+                               t->leaf_at, nleaf, nullptr, nullptr, cnt, rmax); ++tl_launches;
     TRY(scan_excl_dev(S, st, cnt, t->nb_off, nleaf, t->nb_off + nleaf));
-    const int64_t nb_cap = std::max<int64_t>(9 * nleaf, 1);          // <= 9 neighbours per leaf
-    TRY(dalloc(&t->nb_idx, nb_cap * sizeof(int32_t), st));
-    k_neigh<<<lbw, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, loff, nleaf, side, t->nb_off, t->nb_idx, nullptr); ++tl_launches;
+    const int64_t nb_cap = std::max<int64_t>((9 + (is_leaf ? 8 * std::max(L - 1, 0) : 0)) * nleaf, 1);
     TRY(dalloc(&t->nb_tab, nb_cap * sizeof(int4), st));
+    k_recs<<<lbw, TB, 0, st>>>(t->cell_key, t->cell_ix, t->cell_iy, t->cell_start, t->cell_end, is_leaf, lvd,
+                               t->leaf_at, nleaf, t->nb_off, t->nb_tab, nullptr, nullptr); ++tl_launches;
     const int32_t *d_itot = nullptr;
     {   // near-field work items (target pairs per leaf)
         int32_t *icnt = S.get<int32_t>(nleaf + 1), *ioff = S.get<int32_t>(nleaf + 1);
         TRY(S.err);
-        k_items_count<<<lb, TB, 0, st>>>(t->cell_start, t->cell_end, loff, nleaf, icnt); ++tl_launches;
+        k_items_count<<<lb, TB, 0, st>>>(t->cell_start, t->cell_end, t->leaf_at, nleaf, icnt); ++tl_launches;
         TRY(scan_excl_dev(S, st, icnt, ioff, nleaf, ioff + nleaf));
         TRY(dalloc(&t->near_items, std::max<int64_t>(n, 1) * sizeof(int2), st));   // <= one item per element
-        k_items_fill<<<lb, TB, 0, st>>>(t->cell_start, t->cell_end, loff, nleaf, ioff, t->near_items); ++tl_launches;
+        k_items_fill<<<lb, TB, 0, st>>>(t->cell_start, t->cell_end, t->leaf_at, nleaf, ioff, t->near_items);
+        ++tl_launches;
         d_itot = ioff + nleaf;
     }
-    k_nbtab<<<lb, TB, 0, st>>>(t->nb_off, t->nb_idx, t->cell_start, t->cell_end, t->cell_ix, t->cell_iy, loff, nleaf,
-                               t->nb_tab); ++tl_launches;
 
     // interaction lists, levels >= 2: the counts (the depth choice already
     // counted every level it kept; the cells of those levels keep their
@@ -790,9 +1020,8 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, const ddm_fmm
         int nk = (L + 1) * 49;
         t->n_keys = nk;
         int32_t *kc = S.get<int32_t>(nk + 1), *kcur = S.get<int32_t>(nk);
-        int64_t *lo = S.get<int64_t>(L + 2);
+        const int64_t *lo = lvd;
         TRY(S.err);
-        TRY(cudaMemcpyAsync(lo, t->lvl_off.data(), (L + 2) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
         TRY(cudaMemsetAsync(kc, 0, (nk + 1) * sizeof(int32_t), st));
         TRY(cudaMemsetAsync(kcur, 0, nk * sizeof(int32_t), st));
         TRY(dalloc(&t->mk_off, (nk + 1) * sizeof(int32_t), st));
@@ -812,16 +1041,18 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, const ddm_fmm
         t->win_clock = 0;
         // one read-back: the group offsets, the near-field item count and the
         // interaction-list total
-        int32_t *hdev = S.get<int32_t>(nk + 3);
+        int32_t *hdev = S.get<int32_t>(nk + 4);
         TRY(S.err);
         TRY(cudaMemcpyAsync(hdev, t->mk_off, (nk + 1) * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
         TRY(cudaMemcpyAsync(hdev + nk + 1, d_itot, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
         TRY(cudaMemcpyAsync(hdev + nk + 2, t->il_off + NC, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
-        std::vector<int32_t> hk(nk + 3);
-        TRY(cudaMemcpyAsync(hk.data(), hdev, (nk + 3) * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        TRY(cudaMemcpyAsync(hdev + nk + 3, rmax, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+        std::vector<int32_t> hk(nk + 4);
+        TRY(cudaMemcpyAsync(hk.data(), hdev, (nk + 4) * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         TRY(cudaStreamSynchronize(st));
         t->n_items = hk[nk + 1];
         t->n_m2l = hk[nk + 2];
+        t->max_recs = hk[nk + 3];
         t->max_group = 0;
         for (int k = 0; k < nk; ++k) {
             t->max_group = std::max(t->max_group, hk[k + 1] - hk[k]);
@@ -844,10 +1075,13 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, const ddm_fmm
     TRY(dalloc(&t->xy_caller, 4 * n * sizeof(double), st));
     TRY(cudaMemcpyAsync(t->xy_caller, d_xy, 4 * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     TRY(dalloc(&t->chg, n * sizeof(float4), st));
-    TRY(cudaMemcpyAsync(t->elem_leaf, ecell[L], n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
-    double wl = 2.0 * h0 / (double)side;
-    k_geom<<<nbk, TB, 0, st>>>(d_xy, n, idx, t->elem_leaf, t->cell_ix, t->cell_iy, loff, X0, Y0, wl, w16, t->perm,
-                              t->g_rel, t->g_frame, t->g_grid, t->g_loc, t->xy_sorted); ++tl_launches;
+    if (prm.adaptive) {
+        k_elem_leaf<<<nbk, TB, 0, st>>>(LT, n, a_leaf, a_lidx, t->elem_leaf); ++tl_launches;
+    } else {                                  // level-local cell index of level L = leaf index
+        TRY(cudaMemcpyAsync(t->elem_leaf, ecell[L], n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    }
+    k_geom<<<nbk, TB, 0, st>>>(d_xy, n, idx, t->elem_leaf, t->leaf_at, t->cell_ix, t->cell_iy, X0, Y0, h0, w16,
+                              t->perm, t->g_rel, t->g_frame, t->g_grid, t->g_loc, t->xy_sorted); ++tl_launches;
     t->g16 = (float)w16;
     // preconditioner blocks: the chain search (host worker thread, started
     // after the bounding box) is joined here
@@ -895,7 +1129,8 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, const ddm_fmm
     unsigned long long *ptot = S.get<unsigned long long>(1);
     TRY(S.err);
     TRY(cudaMemsetAsync(ptot, 0, sizeof(unsigned long long), st));
-    k_p2p_count<<<lb, TB, 0, st>>>(t->cell_start, t->cell_end, loff, nleaf, t->nb_off, t->nb_idx, ptot); ++tl_launches;
+    k_p2p_count<<<lb, TB, 0, st>>>(t->cell_start, t->cell_end, t->leaf_at, nleaf, t->nb_off, t->nb_tab, ptot);
+    ++tl_launches;
     unsigned long long hp2p = 0;
     TRY(cudaMemcpyAsync(&hp2p, ptot, sizeof(hp2p), cudaMemcpyDeviceToHost, st));
     TRY(cudaGetLastError());

@@ -43,13 +43,14 @@ class ddm_material(ctypes.Structure):
 
 class ddm_fmm_params(ctypes.Structure):
     _fields_ = [("n_cheb", ctypes.c_int), ("leaf_size", ctypes.c_int), ("max_depth", ctypes.c_int),
-                ("quad_near", ctypes.c_int)]
+                ("quad_near", ctypes.c_int), ("adaptive", ctypes.c_int)]
 
 
 class ddm_tree_info(ctypes.Structure):
     _fields_ = [("n_elements", ctypes.c_int64), ("depth", ctypes.c_int), ("n_cells", ctypes.c_int64),
                 ("n_leaves", ctypes.c_int64), ("n_m2l_pairs", ctypes.c_int64), ("n_p2p_pairs", ctypes.c_int64),
-                ("root_half_width", ctypes.c_double)]
+                ("root_half_width", ctypes.c_double), ("leaf_level_min", ctypes.c_int), ("adaptive", ctypes.c_int),
+                ("max_leaf_records", ctypes.c_int)]
 
 
 class ddm_loads(ctypes.Structure):
@@ -176,12 +177,12 @@ def _dev(t: torch.Tensor, n=None, name="tensor") -> int:
 
 
 # ---------------------------------------------------------------- C names
-def ddm_create(material, n_cheb=8, leaf_size=32, max_depth=0, quad_near=6, stream=None):
+def ddm_create(material, n_cheb=8, leaf_size=32, max_depth=0, quad_near=6, stream=None, adaptive=False):
     L = load()
     if isinstance(material, dict):
         material = [material[k] for k in ("G", "nu", "nu_u", "B", "perm", "visc")]
     m = ddm_material(*[float(v) for v in material])
-    p = ddm_fmm_params(int(n_cheb), int(leaf_size), int(max_depth), int(quad_near))
+    p = ddm_fmm_params(int(n_cheb), int(leaf_size), int(max_depth), int(quad_near), int(bool(adaptive)))
     s = (stream or torch.cuda.current_stream()).cuda_stream
     out = _VP()
     st = L.ddm_create(ctypes.byref(out), ctypes.byref(m), ctypes.byref(p), _VP(s))
@@ -201,11 +202,12 @@ def ddm_build_tree(ctx, xy: torch.Tensor):
     return out
 
 
-def ddm_build_tree_params(ctx, xy: torch.Tensor, n_cheb=0, leaf_size=0, max_depth=0, quad_near=0):
-    """Tree with its own FMM parameters (0 = the context's)."""
+def ddm_build_tree_params(ctx, xy: torch.Tensor, n_cheb=0, leaf_size=0, max_depth=0, quad_near=0, adaptive=False):
+    """Tree with its own FMM parameters (order, leaf size, quad_near: 0 = the
+    context's; max_depth and adaptive as given)."""
     n = xy.numel() // 4
     out = _VP()
-    prm = ddm_fmm_params(int(n_cheb), int(leaf_size), int(max_depth), int(quad_near))
+    prm = ddm_fmm_params(int(n_cheb), int(leaf_size), int(max_depth), int(quad_near), int(bool(adaptive)))
     _check(ctx, load().ddm_build_tree_params(ctx, _VP(_dev(xy, 4 * n, "xy")), n, ctypes.byref(prm), ctypes.byref(out)),
            "ddm_build_tree_params")
     return out
@@ -450,11 +452,13 @@ class Server:
 
 # ---------------------------------------------------------------- wrappers
 class Tree:
-    def __init__(self, ctx: "Context", xy: torch.Tensor, n_cheb=0, leaf_size=0):
+    def __init__(self, ctx: "Context", xy: torch.Tensor, n_cheb=0, leaf_size=0, adaptive=None, max_depth=None):
         self.ctx = ctx
         self.n = xy.numel() // 4
-        if n_cheb or leaf_size:
-            self.ptr = ddm_build_tree_params(ctx.ptr, xy, n_cheb, leaf_size)
+        if n_cheb or leaf_size or adaptive is not None or max_depth is not None:
+            self.ptr = ddm_build_tree_params(ctx.ptr, xy, n_cheb, leaf_size,
+                                             ctx.max_depth if max_depth is None else max_depth, 0,
+                                             ctx.adaptive if adaptive is None else adaptive)
         else:
             self.ptr = ddm_build_tree(ctx.ptr, xy)
 
@@ -512,11 +516,13 @@ class Batch:
 class Context:
     """A library context on the current CUDA device and stream."""
 
-    def __init__(self, material, n_cheb=8, leaf_size=32, max_depth=0, quad_near=6, stream=None):
-        self.ptr = ddm_create(material, n_cheb, leaf_size, max_depth, quad_near, stream)
+    def __init__(self, material, n_cheb=8, leaf_size=32, max_depth=0, quad_near=6, stream=None, adaptive=False):
+        self.adaptive, self.max_depth = bool(adaptive), int(max_depth)
+        self.ptr = ddm_create(material, n_cheb, leaf_size, max_depth, quad_near, stream, adaptive)
 
-    def build_tree(self, xy: torch.Tensor, n_cheb=0, leaf_size=0) -> Tree:
-        return Tree(self, xy.contiguous(), n_cheb, leaf_size)
+    def build_tree(self, xy: torch.Tensor, n_cheb=0, leaf_size=0, adaptive=None, max_depth=None) -> Tree:
+        """Quadtree of the elements (adaptive / max_depth: None = the context's)."""
+        return Tree(self, xy.contiguous(), n_cheb, leaf_size, adaptive, max_depth)
 
     def autotune(self, xy: torch.Tensor, x: torch.Tensor, dt, orders=None, leaves=None, max_rel_err=1e-3) -> dict:
         return ddm_autotune(self.ptr, xy.contiguous(), x, dt, orders, leaves, max_rel_err)

@@ -136,6 +136,51 @@ def random_fractures(n_frac=200, box=200.0, elems=100, seed=SEED):
     return assemble(segs), segs
 
 
+def clustered_fracture_segments(n_clusters=4, per_cluster=100, cluster_box=12.0, elems_small=20,
+                                n_sparse=20, box=400.0, elems_sparse=100, seed=SEED + 6):
+    """Strongly clustered fracture set: n_clusters swarms of per_cluster
+    small cracks (lengths U[0.4, 1.5] m, elems_small elements each) packed
+    in cluster_box x cluster_box squares, plus n_sparse long cracks
+    (U[10, 40] m, elems_sparse elements) spread over a box x box domain.
+    The swarm centres are drawn uniformly and rejected within 1.5
+    cluster_box of a long crack or of another swarm, so no crack crosses
+    another.  Element sizes span 0.02 to 0.4 m and the densities differ by
+    orders of magnitude across the domain.  Returns (p0, p1, n_elems)
+    segments."""
+    rng = np.random.default_rng(seed)
+    segs = random_fracture_segments(n_sparse, box, 10.0, 40.0, elems_sparse, seed=seed + 1)
+
+    def point_seg(px, py, a, b):
+        ax, ay = a
+        bx, by = b
+        dx, dy = bx - ax, by - ay
+        t = max(0.0, min(1.0, ((px - ax) * dx + (py - ay) * dy) / (dx * dx + dy * dy)))
+        return math.hypot(px - ax - t * dx, py - ay - t * dy)
+
+    centres = []
+    tries = 0
+    while len(centres) < n_clusters:
+        tries += 1
+        if tries > 100000:
+            raise RuntimeError("clustered_fracture_segments: could not place the swarms")
+        cx, cy = rng.uniform(cluster_box, box - cluster_box, size=2)
+        if any(point_seg(cx, cy, p0, p1) < 1.5 * cluster_box for (p0, p1, _) in segs[:n_sparse]):
+            continue
+        if any(math.hypot(cx - qx, cy - qy) < 3.0 * cluster_box for (qx, qy) in centres):
+            continue
+        centres.append((cx, cy))
+    for k, (cx, cy) in enumerate(centres):
+        local = random_fracture_segments(per_cluster, cluster_box, 0.4, 1.5, elems_small, seed=seed + 2 + k)
+        ox, oy = cx - 0.5 * cluster_box, cy - 0.5 * cluster_box
+        segs += [((p0[0] + ox, p0[1] + oy), (p1[0] + ox, p1[1] + oy), n) for (p0, p1, n) in local]
+    return segs
+
+
+def clustered_fractures(**kw):
+    segs = clustered_fracture_segments(**kw)
+    return assemble(segs), segs
+
+
 def parallel_fractures(n_frac=10, spacing=20.0, half_length=100.0, elems=2000):
     """Transverse fractures of a horizontal well along y: fracture k lies on
     y = k * spacing, x in [-half_length, half_length]."""
