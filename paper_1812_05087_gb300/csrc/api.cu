@@ -335,17 +335,7 @@ ddm_status ddm_create(ddm_ctx **out, const ddm_material *mat, const ddm_fmm_para
     c->kf = KConst<float>{(float)kd.G2, (float)kd.Cel, (float)kd.Ce, (float)kd.K2, (float)kd.aS, (float)kd.eta,
                           (float)kd.i4pk, (float)kd.c, (float)kd.Cu, (float)kd.pS, (float)kd.a6, (float)kd.qe};
     // M2M / L2L transfer matrices T[q][a][a'] = S_n(xi_a, (xi_a' + q)/2)
-    int n = p.n_cheb;
-    std::vector<double> xi(n);
-    for (int j = 0; j < n; ++j) xi[j] = cos((2 * j + 1) * M_PI / (2.0 * n));
-    std::vector<float> T(2 * n * n);
-    for (int q = 0; q < 2; ++q)
-        for (int a = 0; a < n; ++a)
-            for (int ap = 0; ap < n; ++ap)
-                T[q * n * n + a * n + ap] = (float)cheb_S(n, xi[a], 0.5 * (xi[ap] + (q ? 1.0 : -1.0)));
-    if (cudaMalloc(&c->cheb_T, T.size() * sizeof(float)) != cudaSuccess) { delete c; return DDM_ENOMEM; }
-    cudaMemcpy(c->cheb_T, T.data(), T.size() * sizeof(float), cudaMemcpyHostToDevice);
-    // the same transfer matrices for every even order (trees may carry their own order)
+    // (q = the child's half), for every even order: trees may carry their own
     for (int nn = 2; nn <= DDM_MAX_CHEB; nn += 2) {
         std::vector<double> xn(nn);
         for (int j = 0; j < nn; ++j) xn[j] = cos((2 * j + 1) * M_PI / (2.0 * nn));
@@ -356,14 +346,13 @@ ddm_status ddm_create(ddm_ctx **out, const ddm_material *mat, const ddm_fmm_para
                     Tn[q * nn * nn + a * nn + ap] = (float)cheb_S(nn, xn[a], 0.5 * (xn[ap] + (q ? 1.0 : -1.0)));
         if (cudaMalloc(&c->cheb_Tn[nn / 2 - 1], Tn.size() * sizeof(float)) != cudaSuccess) {
             for (float *p : c->cheb_Tn) if (p) cudaFree(p);
-            cudaFree(c->cheb_T);
             delete c;
             return DDM_ENOMEM;
         }
         cudaMemcpy(c->cheb_Tn[nn / 2 - 1], Tn.data(), Tn.size() * sizeof(float), cudaMemcpyHostToDevice);
     }
     if (cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess || cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess) {
-        cudaFree(c->cheb_T);
+        for (float *p : c->cheb_Tn) if (p) cudaFree(p);
         delete c;
         return DDM_ENOMEM;
     }
@@ -373,7 +362,7 @@ ddm_status ddm_create(ddm_ctx **out, const ddm_material *mat, const ddm_fmm_para
         if (cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, hi) != cudaSuccess ||
             cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
-            cudaFree(c->cheb_T);
+            for (float *p : c->cheb_Tn) if (p) cudaFree(p);
             cudaFree(c->d_err);
             delete c;
             return DDM_ECUDA;
@@ -386,7 +375,6 @@ ddm_status ddm_create(ddm_ctx **out, const ddm_material *mat, const ddm_fmm_para
 
 void ddm_destroy(ddm_ctx *ctx) {
     if (!ctx) return;
-    if (ctx->cheb_T) cudaFree(ctx->cheb_T);
     for (float *p : ctx->cheb_Tn)
         if (p) cudaFree(p);
     if (ctx->d_err) cudaFree(ctx->d_err);

@@ -147,19 +147,22 @@ struct UpSmem {
     static constexpr int SIZE = (P2M > M2M ? P2M : M2M) > RED ? (P2M > M2M ? P2M : M2M) : RED;
 };
 
-// One block per leaf: P2M of the leaf (paper Sec. 3.3: W_m = sum_j int
-// S_n(ybar_m, y) b_j ds, Gauss rule with n points per element, exact for the
-// polynomial cardinals), then the leaf's share of every ancestor's weights
-// down to level 2 (M2M).  The charges come from the charge kernel, which
-// also zeroed the ancestors' weights.
+// One block per work item, a chunk of at most ~1024 Gauss points of one leaf
+// (large leaves take several blocks, so no block is much longer than the
+// rest): P2M of the chunk (paper Sec. 3.3: W_m = sum_j int S_n(ybar_m, y)
+// b_j ds, Gauss rule with n points per element, exact for the polynomial
+// cardinals) added into the leaf's weights, then the chunk's share of every
+// ancestor's weights down to level 2 (M2M), all atomically: the charge
+// kernel zeroed the weights and local expansions of every cell of levels
+// >= 2.  A leaf above level 2 has no far field and is skipped.
 //
 // P2M: lane owns node entries (a, b) = lane + 32 j and all 4 components;
 // the UP_W warps take every UP_W-th point and are summed at the end.
 template <int N>
-__device__ __forceinline__ void up_body(const int32_t *cstart, const int32_t *cend, const int2 *leaf_at, float h0,
-                                        const int32_t *cix, const int32_t *ciy, const int32_t *parent,
-                                        const float4 *grel, const float4 *frame, const float4 *chg, float *W,
-                                        float *Fz, const float *T, int64_t bid) {
+__device__ __forceinline__ void up_body(const int4 *items, const int2 *leaf_at, float h0, const int32_t *cix,
+                                        const int32_t *ciy, const int32_t *parent, const float4 *grel,
+                                        const float4 *frame, const float4 *chg, float *W, const float *T,
+                                        int64_t bid) {
     using S = UpSmem<N>;
     constexpr int N2 = S::N2, NOUT = S::NOUT, SXS = S::SXS, NE = (N2 + 31) / 32, KO = (NOUT + UP_T - 1) / UP_T;
     __shared__ __align__(16) float sm[S::SIZE];
@@ -167,11 +170,13 @@ __device__ __forceinline__ void up_body(const int32_t *cstart, const int32_t *ce
     float *sx = sm, *sy = sm + N * SXS;
     float4 *wd = reinterpret_cast<float4 *>(sm + 2 * N * SXS);   // 16-byte aligned: 2 N SXS is a multiple of 4
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int2 la = leaf_at[bid];             // the leaf's cell and level
+    const int4 it = items[bid];               // (leaf, first element, end)
+    const int2 la = leaf_at[it.x];            // the leaf's cell and level
     const int64_t leaf = la.x;
     const int L = la.y;
+    if (L < 2) return;                        // (the whole block)
     const float hL = ldexpf(h0, -L);          // the leaf's half-width
-    const int s0 = cstart[leaf], s1 = cend[leaf];
+    const int s0 = it.y, s1 = it.z;
     constexpr int nq = N;                     // Gauss points per element
     float acc[NE][4];
 #pragma unroll
@@ -219,7 +224,7 @@ __device__ __forceinline__ void up_body(const int32_t *cstart, const int32_t *ce
             for (int c = 0; c < 4; ++c) red[warp * NOUT + c * N2 + ent] = acc[j][c];
     }
     __syncthreads();
-    float *Wc = W + leaf * NOUT, *Fc = Fz + leaf * NOUT;
+    float *Wc = W + leaf * NOUT;
     float wv[KO];
 #pragma unroll
     for (int k = 0; k < KO; ++k) {
@@ -228,16 +233,15 @@ __device__ __forceinline__ void up_body(const int32_t *cstart, const int32_t *ce
         if (o < NOUT) {
 #pragma unroll
             for (int w = 0; w < UP_W; ++w) wv[k] += red[w * NOUT + o];
-            Wc[o] = wv[k];
-            Fc[o] = 0.f;                          // local expansion: M2L adds into it next
+            atomicAdd(Wc + o, wv[k]);
         }
     }
-    // M2M up the chain of ancestors down to level 2: the leaf's own
+    // M2M up the chain of ancestors down to level 2: the chunk's
     // contribution takes one child -> parent transfer per level (T[q][a][a'],
     // q = the child's half in x and in y, the same tables as L2L) and is
-    // added atomically into each ancestor (the internal cells were zeroed by
-    // the charge kernel), so no leaf waits for another.  Composed, the
-    // transfers are the direct leaf -> ancestor interpolation, exactly.
+    // added atomically into each ancestor, so no block waits for another.
+    // Composed, the transfers are the direct leaf -> ancestor interpolation,
+    // exactly.
     float *lw = sm + NOUT, *tmp = sm;          // running contribution, scratch
     __syncthreads();                           // the warp partials are read
 #pragma unroll
@@ -288,11 +292,10 @@ __device__ __forceinline__ void up_body(const int32_t *cstart, const int32_t *ce
     }
 }
 template <int N>
-__global__ void __launch_bounds__(UP_T) k_up(const int32_t *cstart, const int32_t *cend, const int2 *leaf_at,
-                                             float h0, const int32_t *cix, const int32_t *ciy, const int32_t *parent,
-                                             const float4 *grel, const float4 *frame, const float4 *chg, float *W,
-                                             float *Fz, const float *T) {
-    up_body<N>(cstart, cend, leaf_at, h0, cix, ciy, parent, grel, frame, chg, W, Fz, T, blockIdx.x);
+__global__ void __launch_bounds__(UP_T) k_up(const int4 *items, const int2 *leaf_at, float h0, const int32_t *cix,
+                                             const int32_t *ciy, const int32_t *parent, const float4 *grel,
+                                             const float4 *frame, const float4 *chg, float *W, const float *T) {
+    up_body<N>(items, leaf_at, h0, cix, ciy, parent, grel, frame, chg, W, T, blockIdx.x);
 }
 
 // ----------------------------------------------------- downward pass (fused)
@@ -1708,8 +1711,9 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
     int use_far = mode != DDM_MODE_DENSE && L >= 2;
     {
         // charges; for the far field also zero the weights and local
-        // expansions of the cells on levels 2 .. L-1
-        const int64_t z0 = use_far ? t->lvl_off[2] : 0, z1 = use_far ? t->lvl_off[L] : 0;
+        // expansions of the cells on levels 2 .. L (the upward pass and the
+        // M2L add into them)
+        const int64_t z0 = use_far ? t->lvl_off[2] : 0, z1 = use_far ? t->lvl_off[L + 1] : 0;
         const int64_t nz = (z1 - z0) * 4 * (int64_t)n2;
         prof_begin(ctx, 0);
         k_prep<<<(unsigned)std::max<int64_t>((N + TB - 1) / TB, 1), TB, 0, s>>>(
@@ -1756,9 +1760,9 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
         // upward pass: P2M and M2M in one launch
         prof_begin(ctx, 2);
 #define DDM_UP(NN)                                                                                          \
-    k_up<NN><<<(unsigned)nleaf, UP_T, 0, fs>>>(t->cell_start, t->cell_end, t->leaf_at, h0f, t->cell_ix, t->cell_iy, \
-                                               t->cell_parent, t->g_rel, t->g_frame, t->chg, t->W, t->Fl,              \
-                                               ctx->cheb_Tn[NN / 2 - 1])
+    k_up<NN><<<(unsigned)t->n_up_items, UP_T, 0, fs>>>(t->up_items, t->leaf_at, h0f, t->cell_ix, t->cell_iy,       \
+                                                       t->cell_parent, t->g_rel, t->g_frame, t->chg, t->W,           \
+                                                       ctx->cheb_Tn[NN / 2 - 1])
         DDM_CHEB_SWITCH(n, DDM_UP);
 #undef DDM_UP
         prof_end(ctx, 2, 1);
@@ -1880,13 +1884,14 @@ struct BDesc {
     const int2 *mk_pair;
     const float *ops;
     const int2 *leaf_at;
+    const int4 *up_items;
     int64_t n, zoff;
     int L, nq;
     float h0, g16;
 };
 constexpr int BE_T = 256, BE_CHUNK = 1024;
 // items (p, kind, a, b): kind 0 prepares elements [a, b), kind 1 zeroes the
-// expansions of the internal cells, floats [zoff + a, zoff + b)
+// expansions of the cells of levels >= 2, floats [zoff + a, zoff + b)
 // act (may be null): per-problem flags, items of problems whose flag is 0
 // are skipped (the same work lists serve every subset of the problems)
 __global__ void __launch_bounds__(BE_T) k_prep_b(const BDesc *D, const int4 *items, int nitems, double scale,
@@ -1913,8 +1918,7 @@ __global__ void __launch_bounds__(UP_T) k_up_b(const BDesc *D, const int2 *items
         const int2 w = items[it];
         if (act && !act[w.x]) continue;      // uniform over the block
         const BDesc &d = D[w.x];
-        up_body<N>(d.cstart, d.cend, d.leaf_at, d.h0, d.cix, d.ciy, d.parent, d.g_rel, d.g_frame, d.chg, d.W, d.Fl,
-                   T, w.y);
+        up_body<N>(d.up_items, d.leaf_at, d.h0, d.cix, d.ciy, d.parent, d.g_rel, d.g_frame, d.chg, d.W, T, w.y);
         __syncthreads();                      // shared staging is reused by the next item
     }
 }
@@ -1975,8 +1979,8 @@ struct BatchFmm {
     double lo = 0, hi = 0;
     BDesc *desc = nullptr;
     int4 *prep = nullptr, *far = nullptr;
-    int2 *leaf = nullptr, *m2l = nullptr, *near = nullptr;
-    int n_prep = 0, n_far = 0, n_leaf = 0, n_m2l = 0;
+    int2 *leaf = nullptr, *upit = nullptr, *m2l = nullptr, *near = nullptr;
+    int n_prep = 0, n_far = 0, n_leaf = 0, n_up = 0, n_m2l = 0;
     int64_t n_near = 0;
     long long launches = 0;
     const int *act = nullptr;
@@ -1985,7 +1989,7 @@ struct BatchFmm {
 
 void bfmm_free(BatchFmm *b, cudaStream_t s) {
     if (!b) return;
-    void *ps[] = {b->desc, b->prep, b->far, b->leaf, b->m2l, b->near};
+    void *ps[] = {b->desc, b->prep, b->far, b->leaf, b->upit, b->m2l, b->near};
     for (void *p : ps) dfree(p, s);
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     if (b->ev_join) cudaEventDestroy(b->ev_join);
@@ -2002,7 +2006,7 @@ ddm_status bfmm_build(ddm_ctx *ctx, ddm_tree *const *trees, int np, const int *i
     std::vector<BDesc> hd(np);
     std::memset(hd.data(), 0, hd.size() * sizeof(BDesc));
     std::vector<int4> hprep, hfar;
-    std::vector<int2> hleaf, hm2l, hnear;
+    std::vector<int2> hleaf, hup, hm2l, hnear;
     for (int q = 0; q < nidx; ++q) {
         const int p = idx[q];
         ddm_tree *t = trees[p];
@@ -2024,7 +2028,7 @@ ddm_status bfmm_build(ddm_ctx *ctx, ddm_tree *const *trees, int np, const int *i
         d.parent = t->cell_parent;
         d.nb_off = t->nb_off; d.nb_tab = t->nb_tab; d.elem_leaf = t->elem_leaf; d.near_items = t->near_items;
         d.mk_work = t->mk_work; d.mk_off = t->mk_off; d.mk_pair = t->mk_pair; d.ops = ops;
-        d.n = t->n; d.leaf_at = t->leaf_at; d.L = L; d.nq = t->prm.quad_near; d.h0 = (float)t->h0;
+        d.n = t->n; d.leaf_at = t->leaf_at; d.up_items = t->up_items; d.L = L; d.nq = t->prm.quad_near; d.h0 = (float)t->h0;
         d.zoff = far ? t->lvl_off[2] * 4 * n2 : 0;
         for (int64_t a = 0; a < t->n; a += BE_CHUNK) {
             const int b = (int)std::min<int64_t>(t->n, a + BE_CHUNK);
@@ -2032,10 +2036,11 @@ ddm_status bfmm_build(ddm_ctx *ctx, ddm_tree *const *trees, int np, const int *i
             if (far) hfar.push_back(make_int4(p, 0, (int)a, b));
         }
         if (far) {
-            const int64_t nz = (t->lvl_off[L] - t->lvl_off[2]) * 4 * n2;
+            const int64_t nz = (t->lvl_off[L + 1] - t->lvl_off[2]) * 4 * n2;
             for (int64_t a = 0; a < nz; a += 8 * BE_CHUNK)
                 hprep.push_back(make_int4(p, 1, (int)a, (int)std::min<int64_t>(nz, a + 8 * BE_CHUNK)));
             for (int64_t l = 0; l < nleaf; ++l) hleaf.push_back(make_int2(p, (int)l));
+            for (int64_t u = 0; u < t->n_up_items; ++u) hup.push_back(make_int2(p, (int)u));
             for (int w = 0; w < t->n_work; ++w) hm2l.push_back(make_int2(p, w));
         }
         for (int64_t i = 0; i < t->n_items; ++i) hnear.push_back(make_int2(p, (int)i));
@@ -2052,6 +2057,7 @@ ddm_status bfmm_build(ddm_ctx *ctx, ddm_tree *const *trees, int np, const int *i
     b->n = n; b->np = np; b->lo = lo; b->hi = hi; b->act = act;
     cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, ctx->device);
     b->n_prep = (int)hprep.size(); b->n_far = (int)hfar.size(); b->n_leaf = (int)hleaf.size();
+    b->n_up = (int)hup.size();
     b->n_m2l = (int)hm2l.size(); b->n_near = (int64_t)hnear.size();
     auto up = [&](void **dst, const void *src, size_t bytes) -> bool {
         if (dalloc(dst, bytes ? bytes : 16, s) != cudaSuccess) return false;
@@ -2061,6 +2067,7 @@ ddm_status bfmm_build(ddm_ctx *ctx, ddm_tree *const *trees, int np, const int *i
               up((void **)&b->prep, hprep.data(), hprep.size() * sizeof(int4)) &&
               up((void **)&b->far, hfar.data(), hfar.size() * sizeof(int4)) &&
               up((void **)&b->leaf, hleaf.data(), hleaf.size() * sizeof(int2)) &&
+              up((void **)&b->upit, hup.data(), hup.size() * sizeof(int2)) &&
               up((void **)&b->m2l, hm2l.data(), hm2l.size() * sizeof(int2)) &&
               up((void **)&b->near, hnear.data(), hnear.size() * sizeof(int2)) &&
               cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
@@ -2090,7 +2097,7 @@ ddm_status bfmm_launch(ddm_ctx *ctx, BatchFmm *b, cudaStream_t s, cudaStream_t a
             DDM_CUDA_TRY(ctx, cudaEventRecord(b->ev_fork, s));
             DDM_CUDA_TRY(ctx, cudaStreamWaitEvent(fs, b->ev_fork, 0));
         }
-#define DDM_UPB(NN) k_up_b<NN><<<grid(b->n_leaf, 4), UP_T, 0, fs>>>(b->desc, b->leaf, b->n_leaf, ctx->cheb_Tn[NN / 2 - 1], b->act)
+#define DDM_UPB(NN) k_up_b<NN><<<grid(b->n_up, 4), UP_T, 0, fs>>>(b->desc, b->upit, b->n_up, ctx->cheb_Tn[NN / 2 - 1], b->act)
         DDM_CHEB_SWITCH(n, DDM_UPB);
 #undef DDM_UPB
         if (b->n_m2l > 0) {

@@ -68,6 +68,8 @@ struct ddm_tree {
     int max_recs = 0;          // most records of one leaf
     int2 *near_items;          // near-field work items: target pairs of one leaf (second -1: single)
     int64_t n_items;
+    int4 *up_items = nullptr;  // upward-pass work items: (leaf, first element, end, 0)
+    int64_t n_up_items = 0;
     int32_t *elem_leaf;        // sorted element -> leaf index (leaf-local)
     // sorted element geometry, FP32 relative to the element's leaf centre
     float4 *g_rel;             // (x0, y0, x1, y1) rel. to leaf centre (expansions)
@@ -208,11 +210,9 @@ struct ddm_ctx {
     KConst<float> kf;
     KConst<double> kd;
     std::string err;
-    // Chebyshev tables (device): nodes, M2M/L2L transfer matrices T[q][a][a']
-    float *cheb_nodes;         // n
-    float *cheb_bw;            // barycentric weights, n
-    float *cheb_T;             // 2 x n x n of the context's order
-    float *cheb_Tn[DDM_MAX_CHEB / 2] = {};   // the same for every even order n (index n / 2 - 1)
+    // M2M / L2L transfer matrices T[q][a][a'] (device) of every even order n
+    // (index n / 2 - 1)
+    float *cheb_Tn[DDM_MAX_CHEB / 2] = {};
     GmresWork *gm;
     Prof prof;
     int *d_err;                // device word raised by a kernel whose bounded wait expired

@@ -297,6 +297,26 @@ __global__ void k_items_fill(const int32_t *cstart, const int32_t *cend, const i
     for (int e = s0; e < s1; e += 2) items[o++] = make_int2(e, e + 1 < s1 ? e + 1 : -1);
 }
 
+// upward-pass work items: each leaf's elements in chunks of at most cpe
+// (leaf, first element, end), so that one block's P2M work is bounded
+// whatever the leaf's size
+__global__ void k_upitems_count(const int32_t *cstart, const int32_t *cend, const int2 *leaf_at, int64_t nleaf,
+                                int cpe, int32_t *cnt) {
+    int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (L >= nleaf) return;
+    const int c = leaf_at[L].x;
+    cnt[L] = (cend[c] - cstart[c] + cpe - 1) / cpe;
+}
+__global__ void k_upitems_fill(const int32_t *cstart, const int32_t *cend, const int2 *leaf_at, int64_t nleaf,
+                               int cpe, const int32_t *ioff, int4 *items) {
+    int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (L >= nleaf) return;
+    const int c = leaf_at[L].x;
+    const int s0 = cstart[c], s1 = cend[c];
+    int o = ioff[L];
+    for (int e = s0; e < s1; e += cpe) items[o++] = make_int4((int)L, e, min(e + cpe, s1), 0);
+}
+
 // the leaves of a uniform tree: every cell of level L
 __global__ void k_leaf_uniform(int64_t loff, int64_t nleaf, int L, int2 *leaf_at) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -666,7 +686,7 @@ static void find_chains(const double *hxy, int64_t n, Chains &out) {
 void tree_free(ddm_tree *t) {
     if (!t) return;
     void *ps[] = {t->mk_work, t->pb_off, t->pb_elem, t->pb_moff, t->pb_inv, t->pc_blk, t->pc_inv, t->mk_off, t->mk_pair, t->perm, t->cell_key, t->cell_ix, t->cell_iy, t->cell_start, t->cell_end, t->cell_parent,
-                  t->il_off, t->il_idx, t->nb_off, t->leaf_at, t->nb_tab, t->near_items, t->elem_leaf, t->g_rel, t->g_frame, t->g_grid, t->g_loc,
+                  t->il_off, t->il_idx, t->nb_off, t->leaf_at, t->nb_tab, t->near_items, t->up_items, t->elem_leaf, t->g_rel, t->g_frame, t->g_grid, t->g_loc,
                   t->xy_sorted, t->xy_caller, t->W, t->Fl, t->far4, t->chg, t->lv_off, t->lv_pair, t->lv_work,
                   t->Wc, t->Gc};
     for (void *p : ps) dfree(p, t->stream);
@@ -988,6 +1008,19 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, const ddm_fmm
         ++tl_launches;
         d_itot = ioff + nleaf;
     }
+    const int32_t *d_utot = nullptr;
+    {   // upward-pass items: about 1024 Gauss points (n per element) per block
+        const int cpe = std::max(1, 1024 / prm.n_cheb);
+        int32_t *ucnt = S.get<int32_t>(nleaf + 1), *uoff = S.get<int32_t>(nleaf + 1);
+        TRY(S.err);
+        k_upitems_count<<<lb, TB, 0, st>>>(t->cell_start, t->cell_end, t->leaf_at, nleaf, cpe, ucnt); ++tl_launches;
+        TRY(scan_excl_dev(S, st, ucnt, uoff, nleaf, uoff + nleaf));
+        // <= one item per leaf plus one per cpe elements
+        TRY(dalloc(&t->up_items, (nleaf + n / cpe + 1) * sizeof(int4), st));
+        k_upitems_fill<<<lb, TB, 0, st>>>(t->cell_start, t->cell_end, t->leaf_at, nleaf, cpe, uoff, t->up_items);
+        ++tl_launches;
+        d_utot = uoff + nleaf;
+    }
 
     // interaction lists, levels >= 2: the counts (the depth choice already
     // counted every level it kept; the cells of those levels keep their
@@ -1041,18 +1074,20 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, const ddm_fmm
         t->win_clock = 0;
         // one read-back: the group offsets, the near-field item count and the
         // interaction-list total
-        int32_t *hdev = S.get<int32_t>(nk + 4);
+        int32_t *hdev = S.get<int32_t>(nk + 5);
         TRY(S.err);
         TRY(cudaMemcpyAsync(hdev, t->mk_off, (nk + 1) * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
         TRY(cudaMemcpyAsync(hdev + nk + 1, d_itot, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
         TRY(cudaMemcpyAsync(hdev + nk + 2, t->il_off + NC, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
         TRY(cudaMemcpyAsync(hdev + nk + 3, rmax, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
-        std::vector<int32_t> hk(nk + 4);
-        TRY(cudaMemcpyAsync(hk.data(), hdev, (nk + 4) * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        TRY(cudaMemcpyAsync(hdev + nk + 4, d_utot, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+        std::vector<int32_t> hk(nk + 5);
+        TRY(cudaMemcpyAsync(hk.data(), hdev, (nk + 5) * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         TRY(cudaStreamSynchronize(st));
         t->n_items = hk[nk + 1];
         t->n_m2l = hk[nk + 2];
         t->max_recs = hk[nk + 3];
+        t->n_up_items = hk[nk + 4];
         t->max_group = 0;
         for (int k = 0; k < nk; ++k) {
             t->max_group = std::max(t->max_group, hk[k + 1] - hk[k]);
