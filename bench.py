@@ -265,7 +265,7 @@ BUCKETS = ((100, 300), (300, 1000), (1000, 3000), (3000, 10000), (10000, 20001))
 
 def run_batched(args, inputs, Context, torch, loads):
     """Config-4 workload: 512 uneven random fracture sets.  A project-written
-    autotuner (ddm_autotune) picks the Chebyshev order and leaf size per size
+    autotuner (ddm_autotune) picks the Chebyshev order, leaf size and tree kind per size
     bucket on a representative problem; every problem's tree takes its
     bucket's choice; the time steps (1-10 per problem) run as lockstep
     batched GMRES solves of the problems still marching (history of each
@@ -308,8 +308,8 @@ def run_batched(args, inputs, Context, torch, loads):
     def params(n):
         for row in table:
             if row["bucket"][0] <= n < row["bucket"][1]:
-                return row["n_cheb"], row["leaf_size"]
-        return args.n_cheb, args.leaf
+                return row["n_cheb"], row["leaf_size"], row["adaptive"]
+        return args.n_cheb, args.leaf, False
 
     # problems sorted by their number of steps (descending): the problems still
     # marching at step k are a prefix, so every step's batch shares the arenas

@@ -434,12 +434,14 @@ ddm_status ddm_matvec_dense_static(ddm_ctx *ctx, const double *d_xy, int64_t n, 
 /* Autotuner (no counterpart in the paper): for a representative problem of
  * a size bucket (d_xy: 4N geometry, d_x: a 3N vector, both device; dt the
  * time step), build a tree for every candidate Chebyshev order (orders,
- * n_orders; NULL = 4, 6, 8, 10, 12) and leaf size (leaves, n_leaves;
- * NULL = 16, 32, 64), time its FMM product on the device (CUDA events,
+ * n_orders; NULL = 4, 6, 8, 10, 12), leaf size (leaves, n_leaves;
+ * NULL = 16, 32, 64) and tree kind (uniform and adaptive, see
+ * ddm_fmm_params), time its FMM product on the device (CUDA events,
  * after a warm-up that builds the window caches) and measure its error
  * against the on-the-fly dense product (max over the output blocks of
  * max|y - y_dense| / max|y_dense|).  *best receives the fastest candidate
- * whose error is <= max_rel_err (other fields from the context), with its
+ * whose error is <= max_rel_err (n_cheb, leaf_size and adaptive; the other
+ * fields from the context, max_depth 0), with its
  * time per product and error.  DDM_ENOTCONV when no candidate meets the
  * bound.  Synchronises the stream; allocates and frees its own trees. */
 ddm_status ddm_autotune(ddm_ctx *ctx, const double *d_xy, int64_t n, const double *d_x, double dt,

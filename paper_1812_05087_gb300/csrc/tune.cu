@@ -1,7 +1,8 @@
 // Autotuner of the FMM parameters (no counterpart in the paper).
 //
 // For one representative problem (a size bucket of uneven problems), every
-// candidate (Chebyshev order, leaf size) gets its own tree; its product is
+// candidate (Chebyshev order, leaf size, tree kind: uniform or adaptive)
+// gets its own tree; its product is
 // timed on the device with CUDA events (after a warm-up that builds the
 // window caches) and compared with the on-the-fly dense product of the same
 // vector.  The fastest candidate whose relative error stays within the
@@ -63,10 +64,11 @@ extern "C" ddm_status ddm_autotune(ddm_ctx *ctx, const double *d_xy, int64_t n, 
     bool have_ref = false;
     const int reps = 5;
     for (int io = 0; io < n_orders && !st; ++io)
-        for (int il = 0; il < n_leaves && !st; ++il) {
+        for (int ic = 0; ic < 2 * n_leaves && !st; ++ic) {
             ddm_fmm_params p = ctx->prm;
             p.n_cheb = orders[io];
-            p.leaf_size = leaves[il];
+            p.leaf_size = leaves[ic >> 1];
+            p.adaptive = ic & 1;
             p.max_depth = 0;
             if (p.n_cheb < 2 || p.n_cheb > DDM_MAX_CHEB || (p.n_cheb & 1) || p.leaf_size <= 0) continue;
             ddm_tree *t = nullptr;

@@ -214,7 +214,7 @@ def ddm_build_tree_params(ctx, xy: torch.Tensor, n_cheb=0, leaf_size=0, max_dept
 
 
 def ddm_autotune(ctx, xy: torch.Tensor, x: torch.Tensor, dt, orders=None, leaves=None, max_rel_err=1e-3) -> dict:
-    """Fastest (order, leaf size) for this problem within the error bound."""
+    """Fastest (order, leaf size, tree kind) for this problem within the error bound."""
     n = xy.numel() // 4
     o = (ctypes.c_int * len(orders))(*orders) if orders else None
     lv = (ctypes.c_int * len(leaves))(*leaves) if leaves else None
@@ -224,7 +224,8 @@ def ddm_autotune(ctx, xy: torch.Tensor, x: torch.Tensor, dt, orders=None, leaves
                                     len(orders) if orders else 0, lv, len(leaves) if leaves else 0,
                                     float(max_rel_err), ctypes.byref(best), ctypes.byref(ms), ctypes.byref(err)),
            "ddm_autotune")
-    return {"n_cheb": best.n_cheb, "leaf_size": best.leaf_size, "ms": ms.value, "err": err.value}
+    return {"n_cheb": best.n_cheb, "leaf_size": best.leaf_size, "adaptive": bool(best.adaptive), "ms": ms.value,
+            "err": err.value}
 
 
 def ddm_tree_destroy(tree):

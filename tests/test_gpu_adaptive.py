@@ -171,3 +171,22 @@ def test_batched_adaptive_equals_alone(ctx):
         alone = ctx.matvec(t, dev(xs[i]), 0.0, 10.0).cpu().numpy()
         assert block_rel_err(y[batch.offsets[i]:batch.offsets[i + 1]], alone, n) < 1e-5
     ctx.device_check()
+
+
+def test_autotune_chooses_tree_kind(clustered10k):
+    """The tuner tries both tree kinds; its choice on the clustered set meets
+    the bound against the dense product, and a tree built with it (kind
+    included) reproduces the tuner's error."""
+    xy = clustered10k
+    N = xy.shape[1]
+    ctx = Context(inputs.MATERIAL, n_cheb=8, leaf_size=32)
+    x = dev(inputs.unknowns(N, seed=55))
+    best = ctx.autotune(dev(xy), x, 10.0, orders=[8], leaves=[16, 32], max_rel_err=1e-5)
+    print("autotune on the clustered set:", best)
+    assert best["err"] <= 1e-5 and best["adaptive"] in (False, True)
+    t = ctx.build_tree(dev(xy), n_cheb=best["n_cheb"], leaf_size=best["leaf_size"], adaptive=best["adaptive"])
+    assert t.info()["adaptive"] == int(best["adaptive"])
+    yd = ctx.matvec(t, x, 0.0, 10.0, mode="dense").cpu().numpy()
+    y = ctx.matvec(t, x, 0.0, 10.0).cpu().numpy()
+    assert block_rel_err(y, yd, N) < 1e-5
+    ctx.device_check()

@@ -88,8 +88,9 @@ def test_batch_mixed_orders_equals_alone(ctx):
 
 
 def test_autotune_meets_bound_and_oracle(ctx):
-    """The tuner's choice for a random fracture set meets its error bound
-    against the dense product, and its product matches the FP64 oracle."""
+    """The tuner's choice (order, leaf size, uniform or adaptive tree) for a
+    random fracture set meets its error bound against the dense product, and
+    its product matches the FP64 oracle."""
     segs = inputs.random_fracture_segments(30, 40.0, 2.0, 8.0, 40, seed=123)
     g = inputs.assemble(segs)
     n = g.shape[1]
@@ -97,7 +98,8 @@ def test_autotune_meets_bound_and_oracle(ctx):
     best = ctx.autotune(dev(g), dev(x), 10.0, orders=[4, 6, 8], leaves=[16, 32], max_rel_err=1e-4)
     assert best["n_cheb"] in (4, 6, 8) and best["leaf_size"] in (16, 32)
     assert best["err"] <= 1e-4 and best["ms"] > 0
-    t = ctx.build_tree(dev(g), n_cheb=best["n_cheb"], leaf_size=best["leaf_size"])
+    assert best["adaptive"] in (False, True)
+    t = ctx.build_tree(dev(g), n_cheb=best["n_cheb"], leaf_size=best["leaf_size"], adaptive=best["adaptive"])
     y = ctx.matvec(t, dev(x), 0.0, 10.0, mode="fmm").cpu().numpy()
     rows = np.arange(0, n, 97)
     el_rows = np.concatenate([rows + b * n for b in range(3)])
