@@ -303,14 +303,22 @@ __global__ void __launch_bounds__(UP_T) k_up(const int4 *items, const int2 *leaf
 // f <- S_n(xbar^child, xbar^parent) f + g^child (paper Sec. 3.3 L2L), and
 // the leaf's complete local expansion replaces its own M2L sum.  The
 // ancestors' values are only read, so leaves sharing them need no order.
+// Then L2P at the leaf's targets, four lanes per target (one per component
+// of the global sxx, syy, sxy, p).  With y null the four components go to
+// far4 (rotated and added after the join); otherwise they are rotated to
+// the target frame here and added into y with atomics (the near field, on
+// the other stream, adds into y atomically too).
 constexpr int L2L_T = 128;
 template <int N>
 __device__ __forceinline__ void down_body(const int2 *leaf_at, float h0, const int32_t *cix, const int32_t *ciy,
                                           const int32_t *parent, const float *T, const float *F,
                                           const int32_t *cstart, const int32_t *cend, const float4 *grel,
-                                          float4 *far4, int64_t bid) {
+                                          float4 *far4, const float4 *frame, const int64_t *perm, int64_t Ntot,
+                                          double scale, double *y, int64_t bid) {
     constexpr int N2 = N * N, NOUT = 4 * N2, KO = (NOUT + L2L_T - 1) / L2L_T;
-    __shared__ float sT[2 * N2], sf[NOUT], tmp[NOUT];
+    constexpr int SP = N2 + 1;                // component stride of sf (padded: the L2P lanes of one target
+                                              // read the four components in different banks)
+    __shared__ float sT[2 * N2], sf[4 * SP], tmp[NOUT];
     __shared__ int64_t anc[DDM_MAX_LEVELS + 1];
     __shared__ int squad[DDM_MAX_LEVELS + 1];
     const int tid = threadIdx.x;
@@ -329,7 +337,7 @@ __device__ __forceinline__ void down_body(const int2 *leaf_at, float h0, const i
     __syncthreads();
     // (a leaf above level 2 has no far field: no cell there has an M2L list)
     const float *F2 = L >= 2 ? F + anc[2] * NOUT : nullptr;
-    for (int i = tid; i < NOUT; i += L2L_T) sf[i] = F2 ? F2[i] : 0.f;
+    for (int i = tid; i < NOUT; i += L2L_T) sf[(i / N2) * SP + i % N2] = F2 ? F2[i] : 0.f;
     __syncthreads();
     for (int l = 3; l <= L; ++l) {
         const float *Fc = F + anc[l] * NOUT;
@@ -340,7 +348,7 @@ __device__ __forceinline__ void down_body(const int2 *leaf_at, float h0, const i
         // tmp[c][a'][b] = sum_a Tx[a][a'] f[c][a][b]
         for (int i = tid; i < NOUT; i += L2L_T) {
             int c = i / N2, a = (i / N) % N, b = i % N;
-            const float *src = sf + c * N2 + b;
+            const float *src = sf + c * SP + b;
             float s = 0.f;
 #pragma unroll
             for (int k = 0; k < N; ++k) s = fmaf(Tx[k * N + a], src[k * N], s);
@@ -357,60 +365,78 @@ __device__ __forceinline__ void down_body(const int2 *leaf_at, float h0, const i
                 float s = g[k];
 #pragma unroll
                 for (int j = 0; j < N; ++j) s = fmaf(Ty[j * N + b], tc[j], s);
-                sf[o] = s;
+                sf[c * SP + a * N + b] = s;
             }
         }
         __syncthreads();
     }
-    // L2P at the leaf's targets (global sxx, syy, sxy, p; rotated by the caller)
+    // L2P at the leaf's targets: lane group 4k .. 4k+3 of a warp takes one
+    // target, lane c of the group contracts component c
+    constexpr unsigned FULL = 0xFFFFFFFFu;
     const float *cheb = c_gl.cheb[N / 2 - 1], *bw = c_gl.bw[N / 2 - 1];
     const float hL = ldexpf(h0, -L);
-    for (int ti = cstart[leaf] + tid; ti < cend[leaf]; ti += L2L_T) {
-        const float4 rt = grel[ti];
-        const float xh = __fdividef(0.5f * (rt.x + rt.z), hL), yh = __fdividef(0.5f * (rt.y + rt.w), hL);
-        float cx[N], cy[N], sx = 0.f, sy = 0.f;
-        int hx = -1, hy = -1;
+    const int t0 = cstart[leaf], nt4 = 4 * (cend[leaf] - t0);
+    for (int base = 0; base < nt4; base += L2L_T) {   // (the same trip count for the whole block)
+        const int w = base + tid, c = w & 3, ti = t0 + (w >> 2);
+        const bool on = w < nt4;
+        float sum = 0.f;
+        if (on) {
+            const float4 rt = grel[ti];
+            const float xh = __fdividef(0.5f * (rt.x + rt.z), hL), yh = __fdividef(0.5f * (rt.y + rt.w), hL);
+            float cx[N], cy[N], sx = 0.f, sy = 0.f;
+            int hx = -1, hy = -1;
 #pragma unroll
-        for (int j = 0; j < N; ++j) {
-            float dx = xh - cheb[j], dy = yh - cheb[j];
-            if (fabsf(dx) < 1e-7f) hx = j;
-            if (fabsf(dy) < 1e-7f) hy = j;
-            cx[j] = __fdividef(bw[j], dx);
-            cy[j] = __fdividef(bw[j], dy);
-            sx += cx[j];
-            sy += cy[j];
-        }
-        const float isx = __fdividef(1.f, sx), isy = __fdividef(1.f, sy);
+            for (int j = 0; j < N; ++j) {
+                float dx = xh - cheb[j], dy = yh - cheb[j];
+                if (fabsf(dx) < 1e-7f) hx = j;
+                if (fabsf(dy) < 1e-7f) hy = j;
+                cx[j] = __fdividef(bw[j], dx);
+                cy[j] = __fdividef(bw[j], dy);
+                sx += cx[j];
+                sy += cy[j];
+            }
+            const float isx = __fdividef(1.f, sx), isy = __fdividef(1.f, sy);
 #pragma unroll
-        for (int j = 0; j < N; ++j) {
-            cx[j] = hx >= 0 ? (j == hx ? 1.f : 0.f) : cx[j] * isx;
-            cy[j] = hy >= 0 ? (j == hy ? 1.f : 0.f) : cy[j] * isy;
-        }
-        float g4[4];
-#pragma unroll 1
-        for (int c = 0; c < 4; ++c) {
-            float sum = 0.f;
+            for (int j = 0; j < N; ++j) {
+                cx[j] = hx >= 0 ? (j == hx ? 1.f : 0.f) : cx[j] * isx;
+                cy[j] = hy >= 0 ? (j == hy ? 1.f : 0.f) : cy[j] * isy;
+            }
+            const float *fc = sf + c * SP;
 #pragma unroll
             for (int a = 0; a < N; ++a) {
                 float row = 0.f;
 #pragma unroll
-                for (int b = 0; b < N; ++b) row = fmaf(cy[b], sf[c * N2 + a * N + b], row);
+                for (int b = 0; b < N; ++b) row = fmaf(cy[b], fc[a * N + b], row);
                 sum = fmaf(cx[a], row, sum);
             }
-            if (c == 0) g4[0] = sum;
-            else if (c == 1) g4[1] = sum;
-            else if (c == 2) g4[2] = sum;
-            else g4[3] = sum;
         }
-        far4[ti] = make_float4(g4[0], g4[1], g4[2], g4[3]);
+        const int lb = (tid & 31) & ~3;       // the group's first lane
+        const float g0 = __shfl_sync(FULL, sum, lb), g1 = __shfl_sync(FULL, sum, lb + 1);
+        const float g2 = __shfl_sync(FULL, sum, lb + 2), g3 = __shfl_sync(FULL, sum, lb + 3);
+        if (!on) continue;
+        if (!y) {
+            if (c == 0) far4[ti] = make_float4(g0, g1, g2, g3);
+        } else if (c < 3) {                   // rows sigma_s, sigma_n, p of the target
+            float v = g3;
+            if (c < 2) {
+                const float4 f = frame[ti];
+                const float g[4] = {g0, g1, g2, g3};
+                float ss, sn;
+                to_local<float>(f.x, f.y, g, ss, sn);
+                v = c ? sn : ss;
+            }
+            atomicAdd(y + c * Ntot + perm[ti], scale * (double)v);
+        }
     }
 }
 template <int N>
 __global__ void __launch_bounds__(L2L_T) k_down(const int2 *leaf_at, float h0, const int32_t *cix,
                                                 const int32_t *ciy, const int32_t *parent, const float *T,
                                                 const float *F, const int32_t *cstart, const int32_t *cend,
-                                                const float4 *grel, float4 *far4) {
-    down_body<N>(leaf_at, h0, cix, ciy, parent, T, F, cstart, cend, grel, far4, blockIdx.x);
+                                                const float4 *grel, float4 *far4, const float4 *frame,
+                                                const int64_t *perm, int64_t Ntot, double scale, double *y) {
+    down_body<N>(leaf_at, h0, cix, ciy, parent, T, F, cstart, cend, grel, far4, frame, perm, Ntot, scale, y,
+                 blockIdx.x);
 }
 
 // ---------------------------------------------------------------------- M2L
@@ -1121,11 +1147,9 @@ __device__ __forceinline__ void near2_body(const KConst<float> &k, const Win<flo
     const int tw = lane < 3 ? t0 : t1, row = lane < 3 ? lane : lane - 3;
     int64_t eout = 0;
     float4 fout = make_float4(0.f, 0.f, 0.f, 0.f);
-    double yold = 0.0;
     if (writer) {
         eout = perm[tw];
         fout = frame[tw];
-        yold = y[row * N + eout];
     }
     float acc0[4] = {0, 0, 0, 0}, acc1[4] = {0, 0, 0, 0};
     double dummy[4];
@@ -1254,7 +1278,8 @@ __device__ __forceinline__ void near2_body(const KConst<float> &k, const Win<flo
         vh = cxx * hl[b0][0] + cyy * hl[b0 + 1][0] + cxy * hl[b0 + 2][0];
         vl = cxx * hl[b0][1] + cyy * hl[b0 + 1][1] + cxy * hl[b0 + 2][1];
     }
-    y[row * N + eout] = yold + scale * ((double)vh + (double)vl);
+    // atomically: the far field of the same product may be added beside it
+    atomicAdd(y + row * N + eout, scale * ((double)vh + (double)vl));
 }
 template <bool TWO>
 __global__ void __launch_bounds__(NEAR_T, 4) k_near2(KConst<float> k, Win<float> w, const int32_t *nboff,
@@ -1826,7 +1851,7 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
 #define DDM_DOWN(NN)                                                                                        \
     k_down<NN><<<(unsigned)nleaf, L2L_T, 0, fs>>>(t->leaf_at, h0f, t->cell_ix, t->cell_iy, t->cell_parent,           \
                                                   ctx->cheb_Tn[n / 2 - 1], t->Fl, t->cell_start, t->cell_end, t->g_rel, \
-                                                  t->far4)
+                                                  t->far4, t->g_frame, t->perm, N, scale, precise ? nullptr : y)
         DDM_CHEB_SWITCH(n, DDM_DOWN);
 #undef DDM_DOWN
         prof_end(ctx, 5, 1);
@@ -1844,7 +1869,9 @@ ddm_status op_apply(ddm_ctx *ctx, ddm_tree *t, double lo, double hi, const doubl
     prof_end(ctx, 6, 1);
     if (use_far) {
         if (overlap) DDM_CUDA_TRY(ctx, cudaStreamWaitEvent(s, ctx->ev_join, 0));
-        k_far_add<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(t->far4, t->g_frame, t->perm, N, scale, y);
+        // (plain products: k_down added the far field into y itself; the
+        // precise near kernel writes y plainly, so its far field follows here)
+        if (precise) k_far_add<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(t->far4, t->g_frame, t->perm, N, scale, y);
     }
     DDM_CUDA_TRY(ctx, cudaGetLastError());
     return DDM_OK;
@@ -1929,7 +1956,8 @@ __global__ void __launch_bounds__(L2L_T) k_down_b(const BDesc *D, const int2 *it
         const int2 w = items[it];
         if (act && !act[w.x]) continue;
         const BDesc &d = D[w.x];
-        down_body<N>(d.leaf_at, d.h0, d.cix, d.ciy, d.parent, T, d.Fl, d.cstart, d.cend, d.g_rel, d.far4, w.y);
+        down_body<N>(d.leaf_at, d.h0, d.cix, d.ciy, d.parent, T, d.Fl, d.cstart, d.cend, d.g_rel, d.far4, nullptr,
+                     nullptr, 0, 0.0, nullptr, w.y);
         __syncthreads();
     }
 }
