@@ -576,6 +576,13 @@ def main():
             tr.close()
         adaptive_res["product_speedup_adaptive_vs_uniform"] = (adaptive_res["uniform"]["ms_per_matvec"] /
                                                               adaptive_res["adaptive"]["ms_per_matvec"])
+        # adaptive = "auto": the kind the library's cost model keeps on each set
+        auto = {}
+        for name, g in (("clustered", d_cxy), ("random_fractures_20k", d_xy)):
+            at = actx.build_tree(g, adaptive="auto")
+            auto[name] = "adaptive" if at.info()["adaptive"] else "uniform"
+            at.close()
+        adaptive_res["auto_kind"] = auto
         # the headline workload (random fractures, N = 20,000) on an adaptive tree
         mtree = actx.build_tree(d_xy, adaptive=True)
         mi = mtree.info()

@@ -84,7 +84,12 @@ typedef struct {
  * directly when their ancestors at the coarser leaf's level share a vertex
  * (or coincide); every other pair goes through the M2L of the first level at
  * which their ancestors are apart, as in the uniform tree.  The same calls
- * and kernels serve both. */
+ * and kernels serve both.
+ * adaptive = 2: both trees are built and the one with the lower value of the
+ * measured cost model of a product (near pairs, interaction pairs scaled by
+ * (n/8)^4, cells: the model that picks the uniform tree's depth) is kept;
+ * the build takes about twice as long, and ddm_tree_get_info reports the
+ * kind kept. */
 typedef struct {
     int n_cheb;
     int leaf_size;
@@ -170,7 +175,7 @@ typedef struct {
     int64_t n_p2p_pairs;   /* (target element, source element) near pairs */
     double root_half_width;
     int leaf_level_min;    /* coarsest leaf level (= depth for a uniform tree) */
-    int adaptive;
+    int adaptive;          /* the kind built: 0 uniform, 1 adaptive */
     int max_leaf_records;  /* most direct-interaction element ranges of one leaf
                               (<= 9 in a uniform tree) */
 } ddm_tree_info;

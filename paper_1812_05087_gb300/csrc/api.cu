@@ -295,7 +295,7 @@ ddm_status ddm_create(ddm_ctx **out, const ddm_material *mat, const ddm_fmm_para
     if (p.leaf_size <= 0) p.leaf_size = 32;
     if (p.quad_near <= 0) p.quad_near = 6;
     if (p.n_cheb < 2 || p.n_cheb > DDM_MAX_CHEB || (p.n_cheb & 1) || p.quad_near > 16 || p.max_depth < 0 ||
-        (p.adaptive != 0 && p.adaptive != 1))
+        p.adaptive < 0 || p.adaptive > 2)
         return DDM_EINVAL;
     ddm_ctx *c = new (std::nothrow) ddm_ctx();
     if (!c) return DDM_ENOMEM;
@@ -449,7 +449,7 @@ ddm_status ddm_build_tree_params(ddm_ctx *ctx, const double *d_xy, int64_t n, co
     if (p.leaf_size <= 0) p.leaf_size = ctx->prm.leaf_size;
     if (p.quad_near <= 0) p.quad_near = ctx->prm.quad_near;
     if (p.n_cheb < 2 || p.n_cheb > DDM_MAX_CHEB || (p.n_cheb & 1) || p.quad_near > 16 || p.max_depth < 0 ||
-        (p.adaptive != 0 && p.adaptive != 1))
+        p.adaptive < 0 || p.adaptive > 2)
         return ctx_fail(ctx, DDM_EINVAL, "ddm_build_tree_params: bad FMM parameters");
     return tree_build(ctx, d_xy, n, p, out);
 }

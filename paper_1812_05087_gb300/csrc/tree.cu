@@ -696,7 +696,8 @@ void tree_free(ddm_tree *t) {
     delete t;
 }
 
-ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, const ddm_fmm_params &prm, ddm_tree **out) {
+static ddm_status tree_build_one(ddm_ctx *ctx, const double *d_xy, int64_t n, const ddm_fmm_params &prm,
+                                 ddm_tree **out) {
     if (!ctx || !d_xy || !out || n <= 0 || n > (int64_t)1 << 30)
         return ctx_fail(ctx, DDM_EINVAL, "ddm_build_tree: bad arguments");
     cudaStream_t st = ctx->stream;
@@ -1173,5 +1174,32 @@ ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, const ddm_fmm
     t->n_p2p = (int64_t)hp2p;
     prof_end(ctx, 9, (int)tl_launches);
     *out = t;
+    return DDM_OK;
+}
+
+// The measured cost model of one product that also picks the uniform tree's
+// depth: near pairs, interaction pairs (scaling with n^4) and cells.
+static double product_cost_model(const ddm_tree *t) {
+    return 21.5e-12 * (double)t->n_p2p + 3.5e-9 * std::pow(t->prm.n_cheb / 8.0, 4.0) * (double)t->n_m2l +
+           25e-9 * (double)t->n_cells;
+}
+
+// adaptive = 2: both trees, the one the cost model prefers is kept
+ddm_status tree_build(ddm_ctx *ctx, const double *d_xy, int64_t n, const ddm_fmm_params &prm, ddm_tree **out) {
+    if (prm.adaptive != 2) return tree_build_one(ctx, d_xy, n, prm, out);
+    if (!out) return ctx_fail(ctx, DDM_EINVAL, "ddm_build_tree: bad arguments");
+    ddm_fmm_params pu = prm, pa = prm;
+    pu.adaptive = 0;
+    pa.adaptive = 1;
+    ddm_tree *tu = nullptr, *ta = nullptr;
+    ddm_status st = tree_build_one(ctx, d_xy, n, pu, &tu);
+    if (st) return st;
+    if ((st = tree_build_one(ctx, d_xy, n, pa, &ta))) {
+        tree_free(tu);
+        return st;
+    }
+    const bool pick_a = product_cost_model(ta) < product_cost_model(tu);
+    tree_free(pick_a ? tu : ta);
+    *out = pick_a ? ta : tu;
     return DDM_OK;
 }

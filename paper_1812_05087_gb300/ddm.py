@@ -177,12 +177,22 @@ def _dev(t: torch.Tensor, n=None, name="tensor") -> int:
 
 
 # ---------------------------------------------------------------- C names
+def _tree_kind(adaptive):
+    """ddm_fmm_params.adaptive: False / 0 uniform, True / 1 adaptive, "auto" / 2
+    both built and the one the library's cost model prefers kept."""
+    if adaptive == "auto":
+        return 2
+    if adaptive in (0, 1, 2):
+        return int(adaptive)
+    raise ValueError(f"adaptive must be False, True or 'auto', not {adaptive!r}")
+
+
 def ddm_create(material, n_cheb=8, leaf_size=32, max_depth=0, quad_near=6, stream=None, adaptive=False):
     L = load()
     if isinstance(material, dict):
         material = [material[k] for k in ("G", "nu", "nu_u", "B", "perm", "visc")]
     m = ddm_material(*[float(v) for v in material])
-    p = ddm_fmm_params(int(n_cheb), int(leaf_size), int(max_depth), int(quad_near), int(bool(adaptive)))
+    p = ddm_fmm_params(int(n_cheb), int(leaf_size), int(max_depth), int(quad_near), _tree_kind(adaptive))
     s = (stream or torch.cuda.current_stream()).cuda_stream
     out = _VP()
     st = L.ddm_create(ctypes.byref(out), ctypes.byref(m), ctypes.byref(p), _VP(s))
@@ -207,7 +217,7 @@ def ddm_build_tree_params(ctx, xy: torch.Tensor, n_cheb=0, leaf_size=0, max_dept
     context's; max_depth and adaptive as given)."""
     n = xy.numel() // 4
     out = _VP()
-    prm = ddm_fmm_params(int(n_cheb), int(leaf_size), int(max_depth), int(quad_near), int(bool(adaptive)))
+    prm = ddm_fmm_params(int(n_cheb), int(leaf_size), int(max_depth), int(quad_near), _tree_kind(adaptive))
     _check(ctx, load().ddm_build_tree_params(ctx, _VP(_dev(xy, 4 * n, "xy")), n, ctypes.byref(prm), ctypes.byref(out)),
            "ddm_build_tree_params")
     return out
@@ -518,7 +528,7 @@ class Context:
     """A library context on the current CUDA device and stream."""
 
     def __init__(self, material, n_cheb=8, leaf_size=32, max_depth=0, quad_near=6, stream=None, adaptive=False):
-        self.adaptive, self.max_depth = bool(adaptive), int(max_depth)
+        self.adaptive, self.max_depth = adaptive, int(max_depth)
         self.ptr = ddm_create(material, n_cheb, leaf_size, max_depth, quad_near, stream, adaptive)
 
     def build_tree(self, xy: torch.Tensor, n_cheb=0, leaf_size=0, adaptive=None, max_depth=None) -> Tree:

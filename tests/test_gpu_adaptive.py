@@ -190,3 +190,37 @@ def test_autotune_chooses_tree_kind(clustered10k):
     y = ctx.matvec(t, x, 0.0, 10.0).cpu().numpy()
     assert block_rel_err(y, yd, N) < 1e-5
     ctx.device_check()
+
+
+def model_cost(info, n=8):
+    """The library's cost model of one product (near pairs, interaction pairs
+    scaled by (n/8)^4, cells), restated."""
+    return 21.5e-12 * info["n_p2p_pairs"] + 3.5e-9 * (n / 8) ** 4 * info["n_m2l_pairs"] + 25e-9 * info["n_cells"]
+
+
+def test_auto_tree_kind(clustered10k):
+    """adaptive = "auto" builds both trees and keeps the one with the lower
+    model cost: the adaptive tree on the clustered set; on an evenly spread
+    random set, whichever the model prefers.  The kept tree is that kind's
+    tree (same counts), and its product matches the dense one."""
+    ctx = Context(inputs.MATERIAL, n_cheb=8, leaf_size=32, adaptive="auto")
+    rand, _ = inputs.random_fractures(n_frac=60, box=110.0, elems=100, seed=77)
+    for name, xy in (("clustered", clustered10k), ("random", rand)):
+        N = xy.shape[1]
+        t = ctx.build_tree(dev(xy))
+        ia = t.info()
+        iu = ctx.build_tree(dev(xy), adaptive=False).info()
+        ic = ctx.build_tree(dev(xy), adaptive=True).info()
+        want = 1 if model_cost(ic) < model_cost(iu) else 0
+        print(name, "kept", ia["adaptive"], "model uniform", model_cost(iu), "adaptive", model_cost(ic))
+        assert ia["adaptive"] == want
+        kept = ic if want else iu
+        assert (ia["n_cells"], ia["n_p2p_pairs"], ia["n_m2l_pairs"]) == \
+            (kept["n_cells"], kept["n_p2p_pairs"], kept["n_m2l_pairs"])
+        if name == "clustered":
+            assert want == 1
+        x = dev(inputs.unknowns(N, seed=56))
+        yd = ctx.matvec(t, x, 0.0, 10.0, mode="dense").cpu().numpy()
+        y = ctx.matvec(t, x, 0.0, 10.0).cpu().numpy()
+        assert block_rel_err(y, yd, N) < FMM_TOL
+    ctx.device_check()
