@@ -37,3 +37,37 @@ def test_header_compiles_standalone_as_c_and_cpp(tmp_path):
             continue
         r = subprocess.run([comp, "-fsyntax-only", "-Wall", "-Werror", *args, hdr], capture_output=True, text=True)
         assert r.returncode == 0, r.stderr
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every ctypes mirror in the binding has the size and field offsets of
+    the C struct it stands for (a field added on one side only would shift
+    every later field silently)."""
+    import shutil
+    import subprocess
+    import ctypes
+    if shutil.which("gcc") is None:
+        return
+    structs = [n for n in dir(ddm) if n.startswith("ddm_") and isinstance(getattr(ddm, n), type)
+               and issubclass(getattr(ddm, n), ctypes.Structure)]
+    assert {"ddm_fmm_params", "ddm_tree_info", "ddm_material", "ddm_request"} <= set(structs)
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{os.path.join(ROOT, "include", "ddm.h")}"',
+             "int main(void) {"]
+    for s in structs:
+        lines.append(f'    printf("{s} size %zu\\n", sizeof({s}));')
+        for f, _ in getattr(ddm, s)._fields_:
+            lines.append(f'    printf("{s} {f} %zu\\n", offsetof({s}, {f}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "probe"
+    r = subprocess.run(["gcc", "-std=c99", "-o", str(exe), str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = [ln for ln in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+           if ln]
+    assert len(out) == sum(1 + len(getattr(ddm, s)._fields_) for s in structs)
+    for line in out:
+        s, f, v = line.split()
+        cls = getattr(ddm, s)
+        got = ctypes.sizeof(cls) if f == "size" else getattr(cls, f).offset
+        assert got == int(v), (s, f, got, v)
