@@ -71,3 +71,13 @@ def test_binding_structs_match_the_header(tmp_path):
         cls = getattr(ddm, s)
         got = ctypes.sizeof(cls) if f == "size" else getattr(cls, f).offset
         assert got == int(v), (s, f, got, v)
+
+
+def test_tree_kind_values():
+    """The binding maps the tree kind onto ddm_fmm_params.adaptive and
+    rejects anything else before it reaches the library."""
+    import pytest
+    assert [ddm._tree_kind(v) for v in (False, True, "auto", 0, 1, 2)] == [0, 1, 2, 0, 1, 2]
+    for bad in ("yes", 3, -1, None):
+        with pytest.raises(ValueError):
+            ddm._tree_kind(bad)
